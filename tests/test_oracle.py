@@ -1,0 +1,301 @@
+"""Pins for the CPU oracle (no GPU).
+
+The oracle is checked against facts that do not come from itself: hand-derived
+values, closed forms for planted roots, the symmetry and multiplicativity of the
+resultant, a planted common factor, brute-force permutation expansion on tiny
+inputs, and sympy where it is installed.  Each check is chosen so that a dropped
+term, a wrong sign or index, or a transposed operand in the oracle fails one of
+them.
+"""
+
+import json
+import math
+import os
+import random
+
+import pytest
+
+import oracle as O
+from oracle.resultant import as_zxy
+from paper_1103_4697_gb300 import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLD = json.load(open(os.path.join(HERE, "golden", "hand_examples.json")))
+
+RES_METHODS = {
+    "bareiss": O.res_bareiss,
+    "subres": O.res_subres,
+    "evalz": O.res_evalz,
+}
+
+
+def _prod_zx(polys):
+    out = (1,)
+    for p in polys:
+        out = O.zx_mul(out, p)
+    return out
+
+
+def _rand_bipoly(rng, m, dx, lo=-3, hi=3):
+    return [[rng.randint(lo, hi) for _ in range(dx + 1)] for _ in range(m + 1)]
+
+
+def _zx_pow(p, e):
+    out = (1,)
+    for _ in range(e):
+        out = O.zx_mul(out, p)
+    return out
+
+
+# --------------------------------------------------------------------------- hand-derived values
+
+
+@pytest.mark.parametrize("method", sorted(RES_METHODS))
+@pytest.mark.parametrize("k", range(len(GOLD["resultants"])))
+def test_hand_resultants(method, k):
+    e = GOLD["resultants"][k]
+    assert RES_METHODS[method](e["f"], e["g"]) == tuple(e["res"])
+
+
+@pytest.mark.parametrize("k", range(len(GOLD["res_at_formal"])))
+def test_hand_res_at_formal_degree(k):
+    e = GOLD["res_at_formal"][k]
+    assert O.res_at(e["f"], e["g"], e["a"]) == e["value"]
+
+
+@pytest.mark.parametrize("k", range(len(GOLD["gcds"])))
+def test_hand_gcds(k):
+    e = GOLD["gcds"][k]
+    assert O.gcd_z(e["p"], e["q"]) == tuple(e["gcd"])
+
+
+# --------------------------------------------------------------------------- closed forms
+
+
+@pytest.mark.parametrize("seed,m,n", [(1, 1, 1), (2, 2, 3), (3, 3, 2), (4, 4, 4), (5, 1, 5), (6, 5, 3)])
+def test_planted_roots_closed_form(seed, m, n):
+    f, g, al, be, a, b = W.planted_roots_pair(seed, m, n)
+    diffs = [(ai[0] - bj[0], ai[1] - bj[1]) for ai in al for bj in be]
+    want = O.zx_mul((a ** n * b ** m,), _prod_zx([O.zx_trim(d) for d in diffs]))
+    for name, fn in RES_METHODS.items():
+        assert fn(f, g) == want, name
+    if m + n <= 7:
+        assert O.res_leibniz(f, g) == want
+
+
+@pytest.mark.parametrize("seed,m", [(11, 2), (12, 3), (13, 4), (14, 5)])
+def test_disc_closed_form(seed, m):
+    """f = a prod (y - alpha_i): res(f, f_y) = a^(2m-1) prod_{i != j} (alpha_i - alpha_j)."""
+    f, _, al, _, a, _ = W.planted_roots_pair(seed, m, 1)
+    diffs = [O.zx_trim((ai[0] - aj[0], ai[1] - aj[1])) for i, ai in enumerate(al)
+             for j, aj in enumerate(al) if i != j]
+    want = O.zx_mul((a ** (2 * m - 1),), _prod_zx(diffs))
+    for method in ("subres", "bareiss", "evalz"):
+        assert O.disc_res(f, method) == want
+
+
+# --------------------------------------------------------------------------- invariants
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_symmetry(seed):
+    rng = random.Random(seed)
+    m, n = rng.randint(1, 4), rng.randint(1, 4)
+    f = _rand_bipoly(rng, m, rng.randint(0, 3))
+    g = _rand_bipoly(rng, n, rng.randint(0, 3))
+    f[-1][0] = f[-1][0] or 1
+    g[-1][0] = g[-1][0] or 1
+    mm, nn = O.ydeg(f), O.ydeg(g)
+    for fn in RES_METHODS.values():
+        r1, r2 = fn(f, g), fn(g, f)
+        assert r2 == (r1 if (mm * nn) % 2 == 0 else O.zx_neg(r1))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_multiplicativity(seed):
+    rng = random.Random(100 + seed)
+    f1 = _rand_bipoly(rng, rng.randint(1, 3), 2)
+    f2 = _rand_bipoly(rng, rng.randint(1, 2), 2)
+    g = _rand_bipoly(rng, rng.randint(1, 3), 2)
+    for p in (f1, f2, g):
+        p[-1][0] = p[-1][0] or 2
+    f12 = W._mul2(f1, f2)
+    for fn in (O.res_subres, O.res_bareiss):
+        assert fn(f12, g) == O.zx_mul(fn(f1, g), fn(f2, g))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_planted_common_factor_is_zero(seed):
+    rng = random.Random(200 + seed)
+    h = _rand_bipoly(rng, rng.randint(1, 2), 2)
+    h[-1][0] = h[-1][0] or 1
+    f = W._mul2(h, _rand_bipoly(rng, 2, 2))
+    g = W._mul2(h, _rand_bipoly(rng, 2, 1))
+    for fn in RES_METHODS.values():
+        assert fn(f, g) == ()
+
+
+def test_factor_in_x_only_does_not_vanish():
+    """A common factor in Z[x] alone (deg_y = 0) does not make the resultant zero."""
+    f = W._mul2([[1, 1]], [[1, 2], [3], [1]])
+    g = W._mul2([[1, 1]], [[-1], [1, 1]])
+    r = O.res_bareiss(f, g)
+    assert r != ()
+    assert O.res_subres(f, g) == r
+
+
+# --------------------------------------------------------------------------- brute force
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_leibniz_brute_force(seed):
+    """Tiny random inputs (degree <= 3, 2-bit coefficients), including zero leading
+    coefficients in x, constant inputs and zero polynomials."""
+    rng = random.Random(300 + seed)
+    m, n = rng.randint(0, 3), rng.randint(0, 3)
+    f = _rand_bipoly(rng, m, rng.randint(0, 2), -2, 1)
+    g = _rand_bipoly(rng, n, rng.randint(0, 2), -2, 1)
+    want = O.res_leibniz(f, g)
+    assert O.res_bareiss(f, g) == want
+    assert O.res_subres(f, g) == want
+    assert O.res_evalz(f, g) == want
+
+
+def test_degenerate_cases():
+    f0 = [[3, 1]]            # m = 0: f = x + 3
+    g = [[1, 2], [0, 1], [5]]   # n = 2
+    assert O.res_bareiss(f0, g) == _zx_pow((3, 1), 2)
+    assert O.res_subres(f0, g) == _zx_pow((3, 1), 2)
+    assert O.res_bareiss(g, f0) == _zx_pow((3, 1), 2)      # n = 0 side, (-1)^(2*0) = 1
+    assert O.res_bareiss([[2]], [[7, 1]]) == (1,)          # m = n = 0: empty determinant
+    assert O.res_subres([[2]], [[7, 1]]) == (1,)
+    assert O.res_bareiss([[0]], g) == ()                   # f = 0
+    assert O.res_subres(g, [[0, 0]]) == ()
+    assert O.res_evalz([[0]], g) == ()
+
+
+def test_res_at_matches_polynomial_everywhere():
+    """R(a) from the determinant at x = a equals the interpolated polynomial at a,
+    including points where lc_y f or lc_y g vanishes (formal y-degrees kept)."""
+    f = [[1, 2, -1], [0, 1], [-6, 1, 1]]      # lc_y f = x^2 + x - 6 = (x-2)(x+3)
+    g = [[2, -1], [1, 0, 1], [-2, 1]]         # lc_y g = x - 2
+    R = O.res_bareiss(f, g)
+    for a in (-3, -1, 0, 1, 2, 3, 7):
+        assert O.res_at(f, g, a) == O.zx_eval(R, a)
+    assert O.res_evalz(f, g) == R
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_coefficients_within_hadamard_bound(seed):
+    """|coeff| <= (sum_i ||f_i||_1^2)^(n/2) (sum_j ||g_j||_1^2)^(m/2) (Hadamard's
+    inequality for the Sylvester matrix on |x| = 1)."""
+    f, g = W.small_dense_pair(40 + seed, 5, 8)
+    F, G = as_zxy(f), as_zxy(g)
+    m, n = len(F) - 1, len(G) - 1
+    sf = sum(sum(abs(c) for c in r) ** 2 for r in F)
+    sg = sum(sum(abs(c) for c in r) ** 2 for r in G)
+    R = O.res_subres(f, g)
+    for c in R:
+        assert c * c <= sf ** n * sg ** m
+
+
+# --------------------------------------------------------------------------- degree-6 workload
+
+
+def test_small_dense_pair_methods_agree():
+    f, g = W.small_dense_pair(1)
+    r = O.res_bareiss(f, g)
+    assert O.res_subres(f, g) == r
+    assert O.res_evalz(f, g) == r
+    assert len(r) - 1 <= 36
+    for a in (-5, 0, 4, 99):
+        assert O.res_at(f, g, a) == O.zx_eval(r, a)
+
+
+# --------------------------------------------------------------------------- sympy cross-check
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_sympy_resultant(seed):
+    sympy = pytest.importorskip("sympy")
+    x, y = sympy.symbols("x y")
+    rng = random.Random(400 + seed)
+    f = _rand_bipoly(rng, rng.randint(1, 4), rng.randint(1, 3), -9, 9)
+    g = _rand_bipoly(rng, rng.randint(1, 4), rng.randint(1, 3), -9, 9)
+    f[-1][-1] = f[-1][-1] or 1
+    g[-1][-1] = g[-1][-1] or 1
+    F = sum(c * x ** i * y ** j for j, r in enumerate(f) for i, c in enumerate(r))
+    G = sum(c * x ** i * y ** j for j, r in enumerate(g) for i, c in enumerate(r))
+    s = sympy.Poly(sympy.resultant(F, G, y), x)
+    want = O.zx_trim(int(c) for c in reversed(s.all_coeffs()))
+    assert O.res_subres(f, g) == want
+    assert O.res_bareiss(f, g) == want
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_sympy_gcd(seed):
+    sympy = pytest.importorskip("sympy")
+    x = sympy.symbols("x")
+    rng = random.Random(500 + seed)
+    h = [rng.randint(-5, 5) for _ in range(rng.randint(1, 4))]
+    h[-1] = h[-1] or 3
+    p = O.zx_mul(tuple(h), tuple(rng.randint(-9, 9) for _ in range(rng.randint(1, 6))))
+    q = O.zx_mul(tuple(h), tuple(rng.randint(-9, 9) for _ in range(rng.randint(1, 6))))
+    s = sympy.Poly(sympy.gcd(sympy.Poly(list(reversed(p)) or [0], x), sympy.Poly(list(reversed(q)) or [0], x)), x)
+    want = O.zx_trim(int(c) for c in reversed(s.all_coeffs()))
+    if want and want[-1] < 0:
+        want = O.zx_neg(want)
+    assert O.gcd_z(p, q) == want
+
+
+# --------------------------------------------------------------------------- gcd invariants
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_gcd_planted_factor_and_cofactors(seed):
+    P, Q, H = W.gcd_batch(seed + 10, 1, lo=8, hi=20, hdeg=3)
+    p, q, h = P[0], Q[0], H[0]
+    G = O.gcd_z(p, q)
+    assert G and G[-1] > 0
+    assert O.divides_z(G, p) and O.divides_z(G, q)
+    assert O.divides_z(h, G)                        # the planted factor divides the gcd
+    cp, cq = O.zx_divexact(O.zx_trim(p), G), O.zx_divexact(O.zx_trim(q), G)
+    assert O.res_univariate(list(cp), list(cq), O.ZZ) != 0   # cofactors coprime
+    assert O.content(cp) and math.gcd(O.content(cp), O.content(cq)) == 1
+
+
+def test_gcd_content_multiplies():
+    p = O.zx_mul((6,), O.zx_mul((1, 1), (2, 0, 1)))      # 6 (x+1)(x^2+2)
+    q = O.zx_mul((4,), O.zx_mul((1, 1), (3, 1)))          # 4 (x+1)(x+3)
+    assert O.gcd_z(p, q) == (2, 2)
+    assert O.gcd_z(O.zx_neg(p), q) == (2, 2)
+
+
+def test_gcd_coprime_is_content_gcd():
+    assert O.gcd_z((3, 6, 9), (6, 0, 12, 6)) == (3,)
+    assert O.gcd_z((1, 1), (1, -1)) == (1,)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_subres_abnormal_sequences(seed):
+    """Polynomials with gaps in their y-support give remainder sequences whose degrees
+    drop by two or more after the first step (delta >= 2 with h != 1), the one branch
+    of the subresultant recurrence the dense inputs never reach."""
+    rng = random.Random(600 + seed)
+    f = [[0]] * 7
+    g = [[0]] * 6
+    f = [list(r) for r in f]
+    g = [list(r) for r in g]
+    f[6] = [rng.choice([1, 2, -3])]
+    f[3] = [rng.randint(-4, 4), rng.randint(-4, 4)]
+    f[0] = [rng.randint(-4, 4), 1]
+    g[5] = [rng.choice([1, -1, 2])]
+    g[2] = [rng.randint(-4, 4), rng.randint(-2, 2)]
+    g[0] = [rng.randint(-4, 4)]
+    want = O.res_bareiss(f, g)
+    assert O.res_subres(f, g) == want
+    assert O.res_evalz(f, g) == want
+    for a in (-2, 0, 3):
+        Fa = [O.zx_eval(O.zx_trim(r), a) for r in f]
+        Ga = [O.zx_eval(O.zx_trim(r), a) for r in g]
+        assert O.res_univariate(Fa, Ga, O.ZZ) == O.zx_eval(want, a)
