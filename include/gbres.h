@@ -1,0 +1,237 @@
+/*
+ * gbres.h - exact multi-modular resultants and gcds on GB300 (sm_103a).
+ *
+ * C ABI of libgbres.so.  The library computes, exactly and with integer
+ * arithmetic only,
+ *
+ *   res_y(f, g) in Z[x]   for f, g in Z[x, y]              (gbr_resultant)
+ *   res_y(f, df/dy)       the projection resultant R        (gbr_discriminant_res)
+ *   gcd(p, q) in Z[x]     for univariate integer polynomials (gbr_gcd)
+ *
+ * These are the two symbolic operations of Berberich, Emeliyanenko, Kobel and
+ * Sagraloff, "Arrangement Computation for Planar Algebraic Curves":
+ * Section 2.1 (Projection Phase) computes R = res(f, f_y, y) and its square-free
+ * factorisation by gcds; Section 3 (Arrangement Computation) computes
+ * R_CD = res(f, g, y); Section 4 (Implementation, "Symbolic Speedups") states
+ * that both run on the GPU by the divide-conquer-combine scheme of Brown and
+ * Collins: modular and evaluation homomorphisms, independent subproblems over
+ * a prime field, then interpolation and Chinese remaindering, and suggests
+ * moving the initial modular reduction to the GPU as well.
+ *
+ * Resultant definition (the value returned): det of the Sylvester matrix of f
+ * and g as polynomials in the eliminated variable, with their degrees taken
+ * over Z[other variable] (so R vanishes where both leading coefficients
+ * vanish, Section 3).  f rows come first, in decreasing powers; hence
+ * res(g, f) = (-1)^(mn) res(f, g).  f = 0 or g = 0 gives the zero polynomial;
+ * m = n = 0 gives 1.
+ *
+ * gcd definition: the gcd in Z[x] including the gcd of the integer contents,
+ * normalised to a positive leading coefficient; gcd(0, 0) = 0.
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - Every call returns a status (GBR_OK or an error below) and never aborts.
+ * - Inputs are caller-owned and only read during the call.
+ * - gbr_bigpoly results are allocated by the library (host memory) and stay
+ *   valid until gbr_free_result.
+ * - Calls on one context are serialised by the context; use one context per
+ *   host thread for concurrency, or the submit/poll serving interface.
+ * - On GBR_EDEVICE the CUDA error text is available from gbr_last_error().
+ */
+#ifndef GBRES_H
+#define GBRES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define GBR_OK        0
+#define GBR_EINVAL    1   /* null pointer, negative extent, words out of range, var not 0/1 */
+#define GBR_ENOMEM    2   /* request exceeds the context's device-memory budget, or host malloc failed */
+#define GBR_EDEVICE   3   /* a CUDA call failed (text in gbr_last_error) */
+#define GBR_ETIMEOUT  4   /* gbr_poll: not finished within timeout_ms */
+#define GBR_EAGAIN    5   /* gbr_poll with timeout 0: not finished yet */
+#define GBR_EVERIFY   6   /* gcd: the exact check still failed after GBR_MAX_PRIMES primes */
+#define GBR_ELIMIT    7   /* input beyond a documented size limit (see GBR_MAX_*) */
+#define GBR_ECANCELED 8   /* serving: the context was shut down before the job ran */
+#define GBR_ENOTFOUND 9   /* serving: unknown ticket */
+
+/* ------------------------------------------------------------------ limits */
+#define GBR_MAX_WORDS   8     /* 64-bit words per input coefficient (512-bit inputs) */
+#define GBR_MAX_YDEG    127   /* degree in the eliminated variable, per polynomial */
+#define GBR_MAX_POINTS  16384 /* evaluation points per resultant = x-degree bound + 1 */
+#define GBR_MAX_PRIMES  2048  /* 31-bit primes per result (about 63 000-bit coefficients) */
+#define GBR_MAX_UDEG    8191  /* degree of a univariate gcd input */
+
+/* ------------------------------------------------------------------ types */
+typedef struct gbr_ctx gbr_ctx;
+
+/* Bivariate integer polynomial, dense.  Coefficient of x^i y^j (0 <= i <= deg_x,
+ * 0 <= j <= deg_y) is the two's-complement little-endian integer held in the
+ * `words` 64-bit words starting at word (j*(deg_x+1) + i)*words of `coef`.
+ * deg_x, deg_y are array extents (>= the actual degrees; zero rows/columns
+ * are allowed).  words = 1 is a plain int64 array. */
+typedef struct {
+    int32_t deg_x, deg_y;
+    int32_t words;
+    const void *coef;
+} gbr_bipoly;
+
+/* Univariate integer polynomial: coefficient of x^i is the two's-complement
+ * integer in words [i*words, (i+1)*words) of `coef`. */
+typedef struct {
+    int32_t deg;
+    int32_t words;
+    const void *coef;
+} gbr_upoly;
+
+/* Exact result in Z[x], sign-magnitude.  deg = -1 for the zero polynomial
+ * (mag and sign are then NULL).  Coefficient i has magnitude
+ * sum_l mag[i*limbs + l] * 2^(32 l) and sign sign[i] in {-1, 0, +1}.
+ * Library-owned: release with gbr_free_result. */
+typedef struct {
+    int32_t deg;
+    int32_t limbs;
+    uint32_t *mag;
+    int8_t *sign;
+} gbr_bigpoly;
+
+/* Per-stage device times of the last synchronous call, in milliseconds,
+ * measured with CUDA events on the context's stream. */
+typedef struct {
+    double bounds_ms, reduce_ms, evalres_ms, interp_ms, crt_ms, gcd_ms, total_ms;
+    int64_t kernels;       /* kernels launched by the last call */
+    int64_t subproblems;   /* (prime, point) subproblems solved by the last call */
+    int64_t modmul;        /* algorithmic modular multiplications of the last call (see DESIGN) */
+} gbr_stats;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device`.
+ * mem_budget_bytes: device memory the context may use for scratch and
+ *   results; requests that do not fit return GBR_ENOMEM (serving: wait).
+ * workspace: NULL, or a caller-owned device allocation of at least
+ *   mem_budget_bytes that the context sub-allocates from (the Python binding
+ *   passes a torch tensor here); with NULL the library allocates the budget
+ *   itself with cudaMalloc at creation.
+ * stream: NULL for the legacy default stream, or a cudaStream_t on `device`
+ *   on which every kernel and copy of the synchronous calls is issued.
+ * Returns GBR_EINVAL (bad arguments), GBR_EDEVICE (CUDA failure, no device). */
+int gbr_create(gbr_ctx **ctx, int device, size_t mem_budget_bytes, void *workspace, void *stream);
+
+/* Stop the serving worker (pending jobs finish with GBR_ECANCELED), free all
+ * device memory the context allocated, and free the context.  NULL is a no-op. */
+void gbr_destroy(gbr_ctx *ctx);
+
+const char *gbr_strerror(int status);
+const char *gbr_last_error(gbr_ctx *ctx);
+
+/* Options (gbr_set_option). */
+#define GBR_OPT_DROP_UNLUCKY 1   /* 0 (default): evaluation points and primes where a leading
+                                    coefficient vanishes are kept and solved with the formal
+                                    degrees; 1: they are detected, dropped and replaced by spare
+                                    points / the next primes (same result, used to test both) */
+#define GBR_OPT_STATS        2   /* 1: record per-stage CUDA-event times (gbr_get_stats) */
+#define GBR_OPT_GRAPH        3   /* 1 (default): replay the device stages of a resident batch from
+                                    a captured CUDA graph when its plan repeats */
+#define GBR_OPT_EXTRA_PRIMES 4   /* add this many primes beyond the bound (tests: k+1 == k) */
+int gbr_set_option(gbr_ctx *ctx, int option, int64_t value);
+int gbr_get_stats(gbr_ctx *ctx, gbr_stats *out);
+
+/* ------------------------------------------------------------------ one-shot calls */
+
+/* res_var(f, g): var = 1 eliminates y (res_y, the paper's R_CD), var = 0
+ * eliminates x.  Bounds, modular reduction, evaluation, per-(prime, point)
+ * resultants, interpolation and Chinese remaindering all run on the device. */
+int gbr_resultant(gbr_ctx *ctx, const gbr_bipoly *f, const gbr_bipoly *g, int var, gbr_bigpoly *out);
+
+/* res_var(f, df/dvar), the projection resultant R of Section 2.1, not divided
+ * by the leading coefficient. */
+int gbr_discriminant_res(gbr_ctx *ctx, const gbr_bipoly *f, int var, gbr_bigpoly *out);
+
+/* gcd(p, q) in Z[x] (Section 2: content removal; Section 2.1: square-free
+ * factorisation).  Modular images over 31-bit primes, Chinese remaindering of
+ * the gcd and both cofactors, and an exact norm check that proves the result
+ * (on failure more primes are added).  Input coefficients: words must be 1. */
+int gbr_gcd(gbr_ctx *ctx, const gbr_upoly *p, const gbr_upoly *q, gbr_bigpoly *out);
+
+/* ------------------------------------------------------------------ batches */
+
+/* n independent resultants in one pass over the device (pairs of any mixed
+ * sizes are bucketed by degree); out[i] receives res_var(f[i], g[i]). */
+int gbr_resultant_batch(gbr_ctx *ctx, int n, const gbr_bipoly *f, const gbr_bipoly *g, int var,
+                        gbr_bigpoly *out);
+int gbr_discriminant_res_batch(gbr_ctx *ctx, int n, const gbr_bipoly *f, int var, gbr_bigpoly *out);
+int gbr_gcd_batch(gbr_ctx *ctx, int n, const gbr_upoly *p, const gbr_upoly *q, gbr_bigpoly *out);
+
+/* Device-resident batches: gbr_upload_pairs copies the inputs into device
+ * memory once; gbr_run_resident then runs the whole path (bounds included) on
+ * them with results left in device memory; gbr_fetch_resident copies results
+ * [first, first+count) back.  disc = 1 computes res(f[i], df[i]/dvar) and
+ * ignores g.  The handle owns its device memory until gbr_free_resident. */
+typedef struct gbr_resident gbr_resident;
+int gbr_upload_pairs(gbr_ctx *ctx, int n, const gbr_bipoly *f, const gbr_bipoly *g, int var, int disc,
+                     gbr_resident **out);
+int gbr_run_resident(gbr_ctx *ctx, gbr_resident *r);
+int gbr_fetch_resident(gbr_ctx *ctx, gbr_resident *r, int first, int count, gbr_bigpoly *out);
+void gbr_free_resident(gbr_ctx *ctx, gbr_resident *r);
+
+void gbr_free_result(gbr_ctx *ctx, gbr_bigpoly *out);
+
+/* ------------------------------------------------------------------ serving */
+
+#define GBR_JOB_RESULTANT 0
+#define GBR_JOB_DISC      1
+#define GBR_JOB_GCD       2
+typedef struct {
+    int32_t kind;      /* GBR_JOB_* */
+    int32_t var;       /* resultants: eliminated variable */
+    gbr_bipoly f, g;   /* resultants (g unused for GBR_JOB_DISC) */
+    gbr_upoly p, q;    /* gcd */
+} gbr_job;
+
+/* Serving (continuous batching): gbr_submit copies the job and returns at once
+ * with a ticket.  A worker thread admits queued jobs while the context's memory
+ * budget allows, launches them in device batches on several streams so that
+ * batches overlap, and keeps residues on the device until each job's result is
+ * copied out.  gbr_poll waits up to timeout_ms (0 = do not wait, <0 = forever)
+ * and returns GBR_OK with the result, GBR_EAGAIN/GBR_ETIMEOUT if not finished,
+ * or the job's own error.  A ticket is consumed by the first successful poll. */
+int gbr_submit(gbr_ctx *ctx, const gbr_job *job, uint64_t *ticket);
+int gbr_poll(gbr_ctx *ctx, uint64_t ticket, gbr_bigpoly *out, int timeout_ms);
+
+/* Serving counters: jobs admitted, batches launched, peak bytes in flight. */
+typedef struct {
+    int64_t submitted, completed, batches, max_batch, peak_bytes, waits_for_memory;
+} gbr_serve_stats;
+int gbr_get_serve_stats(gbr_ctx *ctx, gbr_serve_stats *out);
+
+/* ------------------------------------------------------------------ host-side information */
+
+/* The fixed table of primes used by every context: p_0 > p_1 > ... are the
+ * largest primes below 2^31.  Host only, needs no device. */
+int gbr_num_primes(void);
+int gbr_prime(int index, uint32_t *p);
+
+/* Number of primes from the table whose product exceeds 2^bits (the count a
+ * resultant whose coefficients satisfy |c| < 2^(bits-1) needs). */
+int gbr_primes_for_bits(double bits);
+
+/* Resultant planning for a pair given on the host: actual degrees m, n, the
+ * x-degree bound D (min of n deg_x f + m deg_x g and the total-degree Bezout
+ * bound), log2 of the Hadamard bound B on |coefficients| and the number of
+ * primes k with prod p > 2B + 1.  Host only.  disc = 1 uses g = df/dvar. */
+typedef struct {
+    int32_t m, n, deg_bound, primes, limbs;
+    double log2_bound;
+} gbr_res_info;
+int gbr_resultant_info(const gbr_bipoly *f, const gbr_bipoly *g, int var, int disc, gbr_res_info *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBRES_H */

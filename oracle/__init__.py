@@ -39,13 +39,13 @@ brute force on tiny inputs and, where available, sympy.
 
 from .zpoly import (ZZ, ZX, zx_add, zx_sub, zx_mul, zx_neg, zx_trim, zx_eval, zx_divexact,
                     zx_deg, content, primitive_part)
-from .resultant import (sylvester, det_bareiss, res_bareiss, res_leibniz, res_subres, res_evalz,
+from .resultant import (sylvester, det_bareiss, res_bareiss, res_leibniz, res_subres, res_evalz, res_at_prs,
                         res_at, disc_res, deriv_y, ydeg, xdeg, res_univariate, degree_bound)
 from .gcd import gcd_z, divides_z
 
 __all__ = [
     "ZZ", "ZX", "zx_add", "zx_sub", "zx_mul", "zx_neg", "zx_trim", "zx_eval", "zx_divexact",
     "zx_deg", "content", "primitive_part", "sylvester", "det_bareiss", "res_bareiss", "res_leibniz",
-    "res_subres", "res_evalz", "res_at", "disc_res", "deriv_y", "ydeg", "xdeg", "res_univariate",
+    "res_subres", "res_evalz", "res_at", "res_at_prs", "disc_res", "deriv_y", "ydeg", "xdeg", "res_univariate",
     "degree_bound", "gcd_z", "divides_z",
 ]

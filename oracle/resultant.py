@@ -292,3 +292,14 @@ def disc_res(f, method: str = "subres") -> tuple:
     fy = deriv_y(f)
     fn = {"subres": res_subres, "bareiss": res_bareiss, "evalz": res_evalz}[method]
     return fn(f, fy)
+
+
+def res_at_prs(f, g, a: int) -> int:
+    """R(a) by the integer subresultant sequence when lc_y f(a) lc_y g(a) != 0 (both
+    y-degrees kept), else by the Sylvester determinant (res_at)."""
+    F, G = as_zxy(f), as_zxy(g)
+    if _zero_or_swap(F, G):
+        return 0
+    if zx_eval(F[-1], a) == 0 or zx_eval(G[-1], a) == 0:
+        return res_at(f, g, a)
+    return res_univariate([zx_eval(c, a) for c in F], [zx_eval(c, a) for c in G], ZZ)

@@ -1,0 +1,286 @@
+"""Python binding of libgbres: argument marshalling only.
+
+Every step of the resultant and gcd path runs in the library's CUDA kernels;
+this module converts numpy arrays / Python ints to the C structures of
+include/gbres.h and the sign-magnitude results back to Python ints.  PyTorch
+supplies the device workspace (a uint8 tensor the context sub-allocates from)
+and the stream.
+
+Polynomial conventions: a bivariate polynomial is a 2-D array ``f[j][i]`` =
+coefficient of x^i y^j (numpy int64, or any nested sequence of Python ints of
+any size); a univariate polynomial is a 1-D sequence ``p[i]`` = coefficient of
+x^i.  Results are lists of Python ints, lowest power first, with no trailing
+zeros (the zero polynomial is ``[]``).
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import native as N
+
+_BIPOLY_DT = np.dtype([("deg_x", np.int32), ("deg_y", np.int32), ("words", np.int32), ("pad", np.int32),
+                       ("coef", np.uint64)])
+_UPOLY_DT = np.dtype([("deg", np.int32), ("words", np.int32), ("coef", np.uint64)])
+assert _BIPOLY_DT.itemsize == C.sizeof(N.BiPoly) and _UPOLY_DT.itemsize == C.sizeof(N.UPoly)
+
+_M64 = (1 << 64) - 1
+
+
+def _words_for(vals) -> int:
+    b = max((int(v).bit_length() for v in vals), default=0)
+    return max(1, (b + 1 + 63) // 64)
+
+
+def _to_words(arr, W: int) -> np.ndarray:
+    """Flattened two's-complement words of the integers in `arr` (row-major)."""
+    flat = np.asarray(arr, dtype=object).ravel() if not (isinstance(arr, np.ndarray) and arr.dtype == np.int64) \
+        else arr.ravel()
+    if W == 1:
+        return np.asarray(flat, dtype=np.int64).view(np.uint64)
+    out = np.empty(len(flat) * W, dtype=np.uint64)
+    mask = (1 << (64 * W)) - 1
+    for k, v in enumerate(flat):
+        u = int(v) & mask
+        for w in range(W):
+            out[k * W + w] = (u >> (64 * w)) & _M64
+    return out
+
+
+def _as_2d(f):
+    if isinstance(f, np.ndarray) and f.ndim == 2:
+        return f
+    rows = [list(r) for r in f]
+    width = max((len(r) for r in rows), default=1) or 1
+    big = any(int(c) >= 2 ** 63 or int(c) < -(2 ** 63) for r in rows for c in r)
+    a = np.zeros((max(len(rows), 1), width), dtype=object if big else np.int64)
+    for j, r in enumerate(rows):
+        for i, c in enumerate(r):
+            a[j, i] = int(c)
+    return a
+
+
+class _Packed:
+    """Keeps the coefficient words alive while the C call runs."""
+
+    def __init__(self):
+        self.bufs = []
+
+
+def pack_bipolys(polys, keep: _Packed):
+    """Array of gbr_bipoly for a list of 2-D arrays or a 3-D int64 array."""
+    if isinstance(polys, np.ndarray) and polys.ndim == 3 and polys.dtype == np.int64:
+        arr = np.ascontiguousarray(polys)
+        keep.bufs.append(arr)
+        n, ry, rx = arr.shape
+        desc = np.zeros(n, dtype=_BIPOLY_DT)
+        desc["deg_x"] = rx - 1
+        desc["deg_y"] = ry - 1
+        desc["words"] = 1
+        desc["coef"] = arr.ctypes.data + np.arange(n, dtype=np.uint64) * np.uint64(ry * rx * 8)
+        keep.bufs.append(desc)
+        return desc
+    desc = np.zeros(len(polys), dtype=_BIPOLY_DT)
+    for k, f in enumerate(polys):
+        a = _as_2d(f)
+        W = 1 if a.dtype == np.int64 else _words_for(a.ravel())
+        w = np.ascontiguousarray(_to_words(a, W))
+        keep.bufs.append(w)
+        desc[k] = (a.shape[1] - 1, a.shape[0] - 1, W, 0, w.ctypes.data)
+    keep.bufs.append(desc)
+    return desc
+
+
+def pack_upolys(polys, keep: _Packed):
+    desc = np.zeros(len(polys), dtype=_UPOLY_DT)
+    for k, p in enumerate(polys):
+        vals = [int(c) for c in p] or [0]
+        W = _words_for(vals)
+        w = np.ascontiguousarray(_to_words(np.array(vals, dtype=object), W))
+        keep.bufs.append(w)
+        desc[k] = (len(vals) - 1, W, w.ctypes.data)
+    keep.bufs.append(desc)
+    return desc
+
+
+def bigpoly_to_ints(b: N.BigPoly) -> list[int]:
+    if b.deg < 0:
+        return []
+    n, L = b.deg + 1, b.limbs
+    mag = np.ctypeslib.as_array(b.mag, shape=(n * L,)).reshape(n, L)
+    sgn = np.ctypeslib.as_array(b.sign, shape=(n,))
+    raw = mag.astype("<u4").tobytes()
+    out = []
+    for i in range(n):
+        v = int.from_bytes(raw[i * 4 * L:(i + 1) * 4 * L], "little")
+        out.append(-v if sgn[i] < 0 else v)
+    while out and out[-1] == 0:
+        out.pop()
+    return out
+
+
+def _ptr(desc) -> C.c_void_p:
+    return C.c_void_p(desc.ctypes.data)
+
+
+class Resident:
+    """Inputs uploaded once to device memory (gbr_upload_pairs)."""
+
+    def __init__(self, ctx: "Context", handle: C.c_void_p, n: int):
+        self.ctx, self.handle, self.n = ctx, handle, n
+
+    def run(self):
+        N.check(N.lib().gbr_run_resident(self.ctx.handle, self.handle), self.ctx.handle)
+
+    def fetch(self, first: int = 0, count: int | None = None) -> list[list[int]]:
+        count = self.n - first if count is None else count
+        outs = (N.BigPoly * max(count, 1))()
+        N.check(N.lib().gbr_fetch_resident(self.ctx.handle, self.handle, first, count, outs), self.ctx.handle)
+        return self.ctx._collect(outs, count)
+
+    def free(self):
+        if self.handle:
+            N.lib().gbr_free_resident(self.ctx.handle, self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Context:
+    """A libgbres context on one CUDA device, with a torch-allocated workspace."""
+
+    def __init__(self, device: int = 0, mem_budget: int = 4 << 30, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("libgbres needs a CUDA device; there is no CPU fallback")
+        L = N.lib()
+        self.device = device
+        torch.cuda.set_device(device)
+        self.workspace = torch.empty(int(mem_budget), dtype=torch.uint8, device=f"cuda:{device}")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        h = C.c_void_p()
+        N.check(L.gbr_create(C.byref(h), device, int(mem_budget), C.c_void_p(self.workspace.data_ptr()),
+                             C.c_void_p(self.stream.cuda_stream)))
+        self.handle = h
+
+    # ------------------------------------------------------------- lifecycle
+    def close(self):
+        if getattr(self, "handle", None):
+            N.lib().gbr_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------- helpers
+    def _collect(self, outs, count: int) -> list[list[int]]:
+        L = N.lib()
+        res = []
+        for i in range(count):
+            res.append(bigpoly_to_ints(outs[i]))
+            L.gbr_free_result(self.handle, C.byref(outs[i]))
+        return res
+
+    def set_option(self, opt: int, value: int):
+        N.check(N.lib().gbr_set_option(self.handle, opt, int(value)), self.handle)
+
+    def stats(self) -> dict:
+        s = N.Stats()
+        N.check(N.lib().gbr_get_stats(self.handle, C.byref(s)), self.handle)
+        return {k: getattr(s, k) for k, _ in N.Stats._fields_}
+
+    # ------------------------------------------------------------- resultants
+    def resultant_batch(self, fs, gs, var: int = 1) -> list[list[int]]:
+        keep = _Packed()
+        df, dg = pack_bipolys(fs, keep), pack_bipolys(gs, keep)
+        n = len(df)
+        outs = (N.BigPoly * max(n, 1))()
+        N.check(N.lib().gbr_resultant_batch(self.handle, n, _ptr(df), _ptr(dg), var, outs), self.handle)
+        return self._collect(outs, n)
+
+    def discriminant_res_batch(self, fs, var: int = 1) -> list[list[int]]:
+        keep = _Packed()
+        df = pack_bipolys(fs, keep)
+        n = len(df)
+        outs = (N.BigPoly * max(n, 1))()
+        N.check(N.lib().gbr_discriminant_res_batch(self.handle, n, _ptr(df), var, outs), self.handle)
+        return self._collect(outs, n)
+
+    def resultant(self, f, g, var: int = 1) -> list[int]:
+        keep = _Packed()
+        df, dg = pack_bipolys([f], keep), pack_bipolys([g], keep)
+        out = N.BigPoly()
+        N.check(N.lib().gbr_resultant(self.handle, C.cast(_ptr(df), C.POINTER(N.BiPoly)),
+                                      C.cast(_ptr(dg), C.POINTER(N.BiPoly)), var, C.byref(out)), self.handle)
+        r = bigpoly_to_ints(out)
+        N.lib().gbr_free_result(self.handle, C.byref(out))
+        return r
+
+    def discriminant_res(self, f, var: int = 1) -> list[int]:
+        keep = _Packed()
+        df = pack_bipolys([f], keep)
+        out = N.BigPoly()
+        N.check(N.lib().gbr_discriminant_res(self.handle, C.cast(_ptr(df), C.POINTER(N.BiPoly)), var,
+                                             C.byref(out)), self.handle)
+        r = bigpoly_to_ints(out)
+        N.lib().gbr_free_result(self.handle, C.byref(out))
+        return r
+
+    def upload_pairs(self, fs, gs=None, var: int = 1, disc: bool = False) -> Resident:
+        keep = _Packed()
+        df = pack_bipolys(fs, keep)
+        dg = pack_bipolys(gs, keep) if gs is not None else None
+        h = C.c_void_p()
+        N.check(N.lib().gbr_upload_pairs(self.handle, len(df), _ptr(df), _ptr(dg) if dg is not None else None,
+                                         var, int(disc), C.byref(h)), self.handle)
+        return Resident(self, h, len(df))
+
+    # ------------------------------------------------------------- gcd
+    def gcd_batch(self, ps, qs) -> list[list[int]]:
+        keep = _Packed()
+        dp, dq = pack_upolys(ps, keep), pack_upolys(qs, keep)
+        n = len(dp)
+        outs = (N.BigPoly * max(n, 1))()
+        N.check(N.lib().gbr_gcd_batch(self.handle, n, _ptr(dp), _ptr(dq), outs), self.handle)
+        return self._collect(outs, n)
+
+    def gcd(self, p, q) -> list[int]:
+        return self.gcd_batch([p], [q])[0]
+
+
+def resultant_info(f, g=None, var: int = 1, disc: bool = False) -> dict:
+    """Host-side plan of one resultant (degrees, bound, primes); needs no device."""
+    keep = _Packed()
+    df = pack_bipolys([f], keep)
+    dg = pack_bipolys([g if g is not None else [[0]]], keep)
+    info = N.ResInfo()
+    N.check(N.lib().gbr_resultant_info(C.cast(_ptr(df), C.POINTER(N.BiPoly)), C.cast(_ptr(dg), C.POINTER(N.BiPoly)),
+                                       var, int(disc), C.byref(info)))
+    return {k: getattr(info, k) for k, _ in N.ResInfo._fields_}
+
+
+def primes(k: int) -> list[int]:
+    """The first k primes of the library's fixed table (host only)."""
+    L = N.lib()
+    out = []
+    for i in range(k):
+        p = C.c_uint32()
+        N.check(L.gbr_prime(i, C.byref(p)))
+        out.append(p.value)
+    return out

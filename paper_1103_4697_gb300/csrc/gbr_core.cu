@@ -1,0 +1,970 @@
+// Host driver of libgbres: prime table, device arena, planning, resultant API.
+//
+// Planning (step A0 of the path) happens in two halves: the bounds kernel
+// measures every pair on the device (actual degrees, log2 of the Hadamard
+// bound), and the host turns those numbers into the number of evaluation
+// points P = D + 1, the number of primes k with prod p > 2B + 1, buffer
+// offsets and degree-bucketed work lists.  Everything after that runs in the
+// stage kernels of gbr_res.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/gbres.h"
+#include "gbr_core.h"
+
+namespace gbr {
+
+// ------------------------------------------------------------------ prime table
+
+static std::vector<ModP> g_mods;
+static std::vector<double> g_log2pref;
+static std::once_flag g_once;
+
+static uint32_t powmod32(uint32_t a, uint32_t e, uint32_t n) {
+    uint64_t r = 1, b = a % n;
+    while (e) {
+        if (e & 1) r = r * b % n;
+        b = b * b % n;
+        e >>= 1;
+    }
+    return (uint32_t)r;
+}
+
+// Deterministic Miller-Rabin for n < 2^32 (bases 2, 7, 61 suffice below 4 759 123 141).
+static bool is_prime32(uint32_t n) {
+    if (n < 2) return false;
+    for (uint32_t sp : {2u, 3u, 5u, 7u, 11u, 13u, 61u})
+        if (n % sp == 0) return n == sp;
+    uint32_t d = n - 1;
+    int s = 0;
+    while (!(d & 1)) { d >>= 1; ++s; }
+    for (uint32_t a : {2u, 7u, 61u}) {
+        uint64_t x = powmod32(a, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool comp = true;
+        for (int r = 1; r < s; ++r) {
+            x = x * x % n;
+            if (x == n - 1) { comp = false; break; }
+        }
+        if (comp) return false;
+    }
+    return true;
+}
+
+static ModP make_mod(uint32_t p) {
+    uint32_t inv = p;                  // p * p = 1 mod 8 for odd p
+    for (int i = 0; i < 5; ++i) inv *= 2u - p * inv;
+    ModP M;
+    M.p = p;
+    M.pinv = (uint32_t)(0u - inv);
+    M.r1 = (uint32_t)((1ull << 32) % p);
+    M.r2 = (uint32_t)((uint64_t)M.r1 * M.r1 % p);
+    return M;
+}
+
+static void init_primes() {
+    g_mods.reserve(GBR_MAX_PRIMES);
+    for (uint32_t c = 0x7fffffffu; (int)g_mods.size() < GBR_MAX_PRIMES; c -= 2)
+        if (is_prime32(c)) g_mods.push_back(make_mod(c));
+    g_log2pref.assign(g_mods.size() + 1, 0.0);
+    for (size_t i = 0; i < g_mods.size(); ++i) g_log2pref[i + 1] = g_log2pref[i] + std::log2((double)g_mods[i].p);
+}
+
+int num_primes() {
+    std::call_once(g_once, init_primes);
+    return (int)g_mods.size();
+}
+const ModP *host_mods() {
+    std::call_once(g_once, init_primes);
+    return g_mods.data();
+}
+double log2_prime_prefix(int k) {
+    std::call_once(g_once, init_primes);
+    return g_log2pref[k];
+}
+int primes_for_bits(double bits) {
+    std::call_once(g_once, init_primes);
+    // smallest k >= 1 with sum_{i<k} log2 p_i > bits; the sums are rounded to
+    // double, so demand a margin of 1e-6 bit
+    for (size_t k = 1; k < g_log2pref.size(); ++k)
+        if (g_log2pref[k] > bits + 1e-6) return (int)k;
+    return -1;
+}
+
+static uint32_t to_mont_host(uint32_t x, uint32_t p) { return (uint32_t)(((uint64_t)x << 32) % p); }
+
+static uint32_t inv_mod_host(uint32_t a, uint32_t p) {
+    int64_t t = 0, nt = 1, r = p, nr = a % p;
+    while (nr) {
+        int64_t q = r / nr, tmp;
+        tmp = t - q * nt; t = nt; nt = tmp;
+        tmp = r - q * nr; r = nr; nr = tmp;
+    }
+    if (t < 0) t += p;
+    return (uint32_t)t;
+}
+
+void garner_prefix_table(int K, uint32_t *out) {
+    const ModP *M = host_mods();
+    uint32_t *pm = out + K;
+    for (int i = 0; i < K; ++i) {
+        uint32_t p = M[i].p;
+        uint64_t prod = 1;
+        for (int j = 0; j < i; ++j) {
+            uint32_t pj = M[j].p % p;
+            pm[(int64_t)i * (i - 1) / 2 + j] = to_mont_host(pj, p);
+            prod = prod * pj % p;
+        }
+        out[i] = to_mont_host(inv_mod_host((uint32_t)prod, p), p);
+    }
+}
+
+void inverse_table(int K, int T, uint32_t *out) {
+    const ModP *M = host_mods();
+    std::vector<uint64_t> inv(T > 2 ? T : 2);
+    for (int i = 0; i < K; ++i) {
+        uint64_t p = M[i].p;
+        inv[0] = 0;
+        inv[1] = 1;
+        for (int t = 2; t < T; ++t) inv[t] = (p - (p / t) * inv[p % t] % p) % p;
+        for (int t = 0; t < T; ++t) out[(int64_t)i * T + t] = t ? to_mont_host((uint32_t)inv[t], (uint32_t)p) : 0u;
+    }
+}
+
+// ------------------------------------------------------------------ arena
+
+void Arena::init(void *b, size_t c) {
+    std::lock_guard<std::mutex> g(mu);
+    base = (char *)b;
+    cap = c;
+    free_.clear();
+    used_.clear();
+    if (c) free_[0] = c;
+    inuse = peak = 0;
+}
+
+void *Arena::alloc(size_t bytes) {
+    if (bytes == 0) bytes = 1;
+    bytes = (bytes + 255) & ~(size_t)255;
+    std::lock_guard<std::mutex> g(mu);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+        if (it->second >= bytes) {
+            size_t off = it->first, rem = it->second - bytes;
+            free_.erase(it);
+            if (rem) free_[off + bytes] = rem;
+            used_[off] = bytes;
+            inuse += bytes;
+            if (inuse > peak) peak = inuse;
+            return base + off;
+        }
+    }
+    return nullptr;
+}
+
+void Arena::release(void *p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> g(mu);
+    size_t off = (size_t)((char *)p - base);
+    auto it = used_.find(off);
+    if (it == used_.end()) return;
+    size_t size = it->second;
+    used_.erase(it);
+    inuse -= size;
+    auto nx = free_.lower_bound(off);
+    if (nx != free_.end() && off + size == nx->first) {
+        size += nx->second;
+        nx = free_.erase(nx);
+    }
+    if (nx != free_.begin()) {
+        auto pv = std::prev(nx);
+        if (pv->first + pv->second == off) {
+            pv->second += size;
+            return;
+        }
+    }
+    free_[off] = size;
+}
+
+size_t Arena::largest_free() {
+    std::lock_guard<std::mutex> g(mu);
+    size_t m = 0;
+    for (auto &kv : free_) m = std::max(m, kv.second);
+    return m;
+}
+
+}  // namespace gbr
+
+using namespace gbr;
+
+// ------------------------------------------------------------------ context helpers
+
+int gbr_ctx::fail(int code, const char *what, cudaError_t e) {
+    char buf[512];
+    if (e != cudaSuccess) std::snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+    else std::snprintf(buf, sizeof buf, "%s", what);
+    std::lock_guard<std::mutex> g(err_mu);
+    err = buf;
+    return code;
+}
+
+void *gbr_ctx::dalloc(size_t bytes) { return arena.alloc(bytes); }
+void gbr_ctx::dfree(void *p) { arena.release(p); }
+
+void *gbr_ctx::pinned(size_t bytes, int slot) {
+    if (h_pin_cap[slot] < bytes) {
+        if (h_pin[slot]) cudaFreeHost(h_pin[slot]);
+        size_t cap = std::max(bytes, (size_t)1 << 20);
+        if (cudaHostAlloc(&h_pin[slot], cap, cudaHostAllocDefault) != cudaSuccess) {
+            h_pin[slot] = nullptr;
+            h_pin_cap[slot] = 0;
+            return nullptr;
+        }
+        h_pin_cap[slot] = cap;
+    }
+    return h_pin[slot];
+}
+
+int gbr_ctx::ensure_tables(int K, int T) {
+    if (K > garner_K) {
+        int newK = std::max(K, std::max(64, garner_K * 2));
+        if (newK > num_primes()) newK = num_primes();
+        size_t words = (size_t)newK + (size_t)newK * (newK - 1) / 2;
+        std::vector<uint32_t> h(words);
+        garner_prefix_table(newK, h.data());
+        void *d = dalloc(words * 4);
+        if (!d) return fail(GBR_ENOMEM, "device budget too small for the Garner table");
+        cudaError_t e = cudaMemcpy(d, h.data(), words * 4, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(GBR_EDEVICE, "upload Garner table", e);
+        dfree(d_garner);
+        d_garner = (uint32_t *)d;
+        garner_K = newK;
+    }
+    if (K > invk_K || T > invk_T) {
+        int nK = std::max(K, invk_K), nT = std::max(T, invk_T);
+        nK = std::min(num_primes(), std::max(nK, 64));
+        nT = std::max(nT, 512);
+        size_t words = (size_t)nK * nT;
+        std::vector<uint32_t> h(words);
+        inverse_table(nK, nT, h.data());
+        void *d = dalloc(words * 4);
+        if (!d) return fail(GBR_ENOMEM, "device budget too small for the inverse table");
+        cudaError_t e = cudaMemcpy(d, h.data(), words * 4, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(GBR_EDEVICE, "upload inverse table", e);
+        dfree(d_invk);
+        d_invk = (uint32_t *)d;
+        invk_K = nK;
+        invk_T = nT;
+    }
+    return GBR_OK;
+}
+
+// ------------------------------------------------------------------ status strings
+
+extern "C" const char *gbr_strerror(int s) {
+    switch (s) {
+        case GBR_OK: return "ok";
+        case GBR_EINVAL: return "invalid argument";
+        case GBR_ENOMEM: return "out of memory (device budget or host)";
+        case GBR_EDEVICE: return "CUDA error";
+        case GBR_ETIMEOUT: return "timed out";
+        case GBR_EAGAIN: return "not finished yet";
+        case GBR_EVERIFY: return "gcd verification failed with the maximum number of primes";
+        case GBR_ELIMIT: return "input beyond a size limit";
+        case GBR_ECANCELED: return "canceled";
+        case GBR_ENOTFOUND: return "unknown ticket";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char *gbr_last_error(gbr_ctx *ctx) {
+    if (!ctx) return "no context";
+    std::lock_guard<std::mutex> g(ctx->err_mu);
+    return ctx->err.c_str();
+}
+
+// ------------------------------------------------------------------ create / destroy
+
+extern "C" int gbr_create(gbr_ctx **out, int device, size_t budget, void *workspace, void *stream) {
+    if (!out || budget < ((size_t)1 << 20)) return GBR_EINVAL;
+    *out = nullptr;
+    gbr_ctx *c = new (std::nothrow) gbr_ctx();
+    if (!c) return GBR_ENOMEM;
+    num_primes();
+    c->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) {
+        delete c;
+        return GBR_EDEVICE;
+    }
+    c->stream = (cudaStream_t)stream;
+    c->budget = budget;
+    if (workspace) {
+        c->ws = workspace;
+        c->own_ws = false;
+    } else {
+        e = cudaMalloc(&c->ws, budget);
+        if (e != cudaSuccess) {
+            delete c;
+            return GBR_ENOMEM;
+        }
+        c->own_ws = true;
+    }
+    c->arena.init(c->ws, budget);
+    const int NP = num_primes();
+    c->d_mods = (ModP *)c->dalloc(sizeof(ModP) * NP);
+    c->d_err = (int32_t *)c->dalloc(64);
+    if (!c->d_mods || !c->d_err) {
+        gbr_destroy(c);
+        return GBR_ENOMEM;
+    }
+    e = cudaMemcpy(c->d_mods, host_mods(), sizeof(ModP) * NP, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, 64);
+    if (e != cudaSuccess) {
+        gbr_destroy(c);
+        return GBR_EDEVICE;
+    }
+    for (int i = 0; i < 4; ++i) cudaEventCreate(&c->ev[i]);
+    for (int i = 4; i < 8; ++i) cudaEventCreate(&c->ev[i]);
+    *out = c;
+    return GBR_OK;
+}
+
+extern "C" void gbr_destroy(gbr_ctx *c) {
+    if (!c) return;
+    gbr_serve_shutdown(c);
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    for (int i = 0; i < 8; ++i)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    for (int i = 0; i < 4; ++i)
+        if (c->h_pin[i]) cudaFreeHost(c->h_pin[i]);
+    if (c->own_ws && c->ws) cudaFree(c->ws);
+    delete c;
+}
+
+extern "C" int gbr_set_option(gbr_ctx *c, int opt, int64_t v) {
+    if (!c) return GBR_EINVAL;
+    switch (opt) {
+        case GBR_OPT_DROP_UNLUCKY: c->drop_unlucky = (int)(v != 0); return GBR_OK;
+        case GBR_OPT_STATS: c->stats_on = (int)(v != 0); return GBR_OK;
+        case GBR_OPT_GRAPH: c->graph_on = (int)(v != 0); return GBR_OK;
+        case GBR_OPT_EXTRA_PRIMES:
+            if (v < 0 || v > 64) return GBR_EINVAL;
+            c->extra_primes = (int)v;
+            return GBR_OK;
+        default: return GBR_EINVAL;
+    }
+}
+
+extern "C" int gbr_get_stats(gbr_ctx *c, gbr_stats *out) {
+    if (!c || !out) return GBR_EINVAL;
+    *out = c->stats;
+    return GBR_OK;
+}
+
+// ------------------------------------------------------------------ host-side info
+
+extern "C" int gbr_num_primes(void) { return num_primes(); }
+
+extern "C" int gbr_prime(int i, uint32_t *p) {
+    if (!p || i < 0 || i >= num_primes()) return GBR_EINVAL;
+    *p = host_mods()[i].p;
+    return GBR_OK;
+}
+
+extern "C" int gbr_primes_for_bits(double bits) { return primes_for_bits(bits); }
+
+// ------------------------------------------------------------------ input validation / packing
+
+static int check_bipoly(const gbr_bipoly *p) {
+    if (!p || !p->coef) return GBR_EINVAL;
+    if (p->deg_x < 0 || p->deg_y < 0 || p->words < 1 || p->words > GBR_MAX_WORDS) return GBR_EINVAL;
+    if ((int64_t)(p->deg_x + 1) * (p->deg_y + 1) > ((int64_t)1 << 28)) return GBR_ELIMIT;
+    return GBR_OK;
+}
+
+static int64_t bipoly_words(const gbr_bipoly *p) { return (int64_t)(p->deg_x + 1) * (p->deg_y + 1) * p->words; }
+
+static PolyDesc view_of(const gbr_bipoly *p, int var, int64_t off) {
+    PolyDesc d;
+    d.off = off;
+    d.words = p->words;
+    if (var == 1) {
+        d.rows = p->deg_y;
+        d.cols = p->deg_x;
+        d.rstride = p->deg_x + 1;
+        d.cstride = 1;
+    } else {
+        d.rows = p->deg_x;
+        d.cols = p->deg_y;
+        d.rstride = 1;
+        d.cstride = p->deg_x + 1;
+    }
+    d.rowdeg_off = 0;
+    return d;
+}
+
+// ------------------------------------------------------------------ resident batches
+
+extern "C" int gbr_upload_pairs(gbr_ctx *c, int n, const gbr_bipoly *f, const gbr_bipoly *g, int var, int disc,
+                                gbr_resident **out) {
+    if (!c || !out || n < 0 || (var != 0 && var != 1) || (n > 0 && !f) || (n > 0 && !disc && !g))
+        return GBR_EINVAL;
+    *out = nullptr;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    gbr_resident *r = new (std::nothrow) gbr_resident();
+    if (!r) return GBR_ENOMEM;
+    r->n = n;
+    r->var = var;
+    r->disc = disc ? 1 : 0;
+    int64_t words = 0;
+    int64_t rowdeg = 0;
+    try {
+        r->h_desc.resize(n);
+        for (int i = 0; i < n; ++i) {
+            int st = check_bipoly(&f[i]);
+            if (!st && !disc) st = check_bipoly(&g[i]);
+            if (st) {
+                delete r;
+                return c->fail(st, "bad polynomial descriptor");
+            }
+            PairDesc &D = r->h_desc[i];
+            D.disc = r->disc;
+            D.pad = 0;
+            D.f = view_of(&f[i], var, words);
+            words += bipoly_words(&f[i]);
+            D.f.rowdeg_off = (int32_t)rowdeg;
+            rowdeg += D.f.rows + 1;
+            if (disc) {
+                D.g = D.f;
+                D.g.rows = D.f.rows - 1;
+                D.g.rowdeg_off = (int32_t)rowdeg;
+                rowdeg += D.f.rows;
+            } else {
+                D.g = view_of(&g[i], var, words);
+                words += bipoly_words(&g[i]);
+                D.g.rowdeg_off = (int32_t)rowdeg;
+                rowdeg += D.g.rows + 1;
+            }
+            if (rowdeg > INT32_MAX / 2) {
+                delete r;
+                return c->fail(GBR_ELIMIT, "too many rows in one batch");
+            }
+        }
+    } catch (std::bad_alloc &) {
+        delete r;
+        return GBR_ENOMEM;
+    }
+    r->coef_words = words;
+    r->rowdeg_n = rowdeg;
+    size_t bytes = (size_t)words * 8;
+    r->d_coef = (uint64_t *)c->dalloc(bytes ? bytes : 8);
+    r->d_desc = (PairDesc *)c->dalloc(sizeof(PairDesc) * (n ? n : 1));
+    r->d_rowdeg = (int32_t *)c->dalloc(sizeof(int32_t) * (rowdeg ? rowdeg : 1));
+    r->d_bounds = (PairBound *)c->dalloc(sizeof(PairBound) * (n ? n : 1));
+    r->d_deg = (int32_t *)c->dalloc(sizeof(int32_t) * (n ? n : 1));
+    if (!r->d_coef || !r->d_desc || !r->d_rowdeg || !r->d_bounds || !r->d_deg) {
+        gbr_free_resident_locked(c, r);
+        return c->fail(GBR_ENOMEM, "device budget too small for the batch inputs");
+    }
+    // pack coefficients into pinned memory, then one copy
+    uint64_t *h = (uint64_t *)c->pinned(bytes + 8, 0);
+    if (!h) {
+        gbr_free_resident_locked(c, r);
+        return c->fail(GBR_ENOMEM, "pinned host staging");
+    }
+    int64_t pos = 0;
+    for (int i = 0; i < n; ++i) {
+        int64_t wf = bipoly_words(&f[i]);
+        std::memcpy(h + pos, f[i].coef, wf * 8);
+        pos += wf;
+        if (!disc) {
+            int64_t wg = bipoly_words(&g[i]);
+            std::memcpy(h + pos, g[i].coef, wg * 8);
+            pos += wg;
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    if (bytes) e = cudaMemcpyAsync(r->d_coef, h, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && n)
+        e = cudaMemcpyAsync(r->d_desc, r->h_desc.data(), sizeof(PairDesc) * n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        gbr_free_resident_locked(c, r);
+        return c->fail(GBR_EDEVICE, "upload pairs", e);
+    }
+    *out = r;
+    return GBR_OK;
+}
+
+void gbr_free_resident_locked(gbr_ctx *c, gbr_resident *r) {
+    if (!r) return;
+    for (void *p : {(void *)r->d_coef, (void *)r->d_desc, (void *)r->d_rowdeg, (void *)r->d_bounds, (void *)r->d_deg,
+                    (void *)r->d_planblk, (void *)r->d_res, (void *)r->d_val, (void *)r->d_out, (void *)r->d_sign})
+        c->dfree(p);
+    if (r->gexec) cudaGraphExecDestroy(r->gexec);
+    delete r;
+}
+
+extern "C" void gbr_free_resident(gbr_ctx *c, gbr_resident *r) {
+    if (!c || !r) return;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    gbr_free_resident_locked(c, r);
+}
+
+// grow-only device buffer held by a resident batch
+static int ensure_buf(gbr_ctx *c, void **p, size_t *cap, size_t bytes) {
+    if (bytes == 0) bytes = 8;
+    if (*p && *cap >= bytes) return GBR_OK;
+    c->dfree(*p);
+    *p = c->dalloc(bytes);
+    *cap = *p ? bytes : 0;
+    return *p ? GBR_OK : GBR_ENOMEM;
+}
+
+namespace {
+struct HostList {
+    std::vector<int32_t> pairs;
+    std::vector<int64_t> start;
+    // start[i] is the first item of pairs[i]
+    void add(int q, int64_t items) {
+        if (items <= 0) return;
+        pairs.push_back(q);
+        start.push_back(total);
+        total += items;
+    }
+    int64_t total = 0;
+};
+}  // namespace
+
+static void put_list(std::vector<char> &blk, const HostList &h, size_t &off_pairs, size_t &off_start) {
+    auto align = [&](size_t a) {
+        size_t s = (blk.size() + a - 1) / a * a;
+        blk.resize(s);
+    };
+    align(8);
+    off_start = blk.size();
+    size_t n = h.pairs.size();
+    blk.resize(blk.size() + (n + 1) * 8);
+    int64_t *st = (int64_t *)(blk.data() + off_start);
+    for (size_t i = 0; i < n; ++i) st[i] = h.start[i];
+    st[n] = h.total;
+    align(8);
+    off_pairs = blk.size();
+    blk.resize(blk.size() + (n ? n : 1) * 4);
+    if (n) std::memcpy(blk.data() + off_pairs, h.pairs.data(), n * 4);
+}
+
+int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
+    const int n = r->n;
+    cudaStream_t s = c->stream;
+    cudaError_t e;
+    gbr_stats st{};
+    if (n == 0) {
+        r->ran = true;
+        return GBR_OK;
+    }
+    if (c->stats_on) cudaEventRecord(c->ev[0], s);
+    // ---- A0 (device half): measure degrees and bounds
+    ResLaunch L{};
+    L.coef = r->d_coef;
+    L.desc = r->d_desc;
+    L.bounds = r->d_bounds;
+    L.rowdeg = r->d_rowdeg;
+    L.mods = c->d_mods;
+    L.npairs = n;
+    L.err = c->d_err;
+    L.deg = r->d_deg;
+    e = launch_bounds(L, s);
+    if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "bounds kernel", e);
+    PairBound *hb = (PairBound *)c->pinned(sizeof(PairBound) * n, 1);
+    if (!hb) return c->fail(GBR_ENOMEM, "pinned host staging");
+    e = cudaMemcpyAsync(hb, r->d_bounds, sizeof(PairBound) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "bounds readback", e);
+    // ---- A0 (host half): plan
+    std::vector<PairPlan> &plan = r->h_plan;
+    plan.assign(n, PairPlan{});
+    int64_t res_w = 0, val_w = 0, out_w = 0, sign_b = 0;
+    int Kmax = 1, Pmax = 1, Lmax = 1;
+    HostList red, interp, crt;
+    std::map<int, HostList> evb;
+    int64_t subproblems = 0;
+    for (int q = 0; q < n; ++q) {
+        const PairBound &b = hb[q];
+        PairPlan &p = plan[q];
+        p.disc = r->disc;
+        p.rowdeg_f = r->h_desc[q].f.rowdeg_off;
+        p.rowdeg_g = r->h_desc[q].g.rowdeg_off;
+        if (b.m < 0 || b.n < 0) {
+            p.flags = PLAN_ZERO;
+            p.m = b.m;
+            p.n = b.n;
+            p.res_off = res_w;
+            p.val_off = val_w;
+            p.out_off = out_w;
+            p.sign_off = sign_b;
+            continue;
+        }
+        if (b.m > GBR_MAX_YDEG || b.n > GBR_MAX_YDEG)
+            return c->fail(GBR_ELIMIT, "degree in the eliminated variable above GBR_MAX_YDEG");
+        p.m = b.m;
+        p.n = b.n;
+        p.dxf = std::max(b.dxf, 0);
+        p.dxg = std::max(b.dxg, 0);
+        int64_t D = degree_bound(b);
+        if (D + 1 > GBR_MAX_POINTS) return c->fail(GBR_ELIMIT, "x-degree bound above GBR_MAX_POINTS - 1");
+        p.P = (int32_t)(D + 1);
+        double bits = b.log2B * (1.0 + 1e-9) + 2.0;
+        int k = primes_for_bits(bits);
+        if (k < 0 || k + c->extra_primes > GBR_MAX_PRIMES)
+            return c->fail(GBR_ELIMIT, "coefficient bound needs more than GBR_MAX_PRIMES primes");
+        k += c->extra_primes;
+        p.k = k;
+        p.L = (31 * k + 31) / 32;
+        p.S = (p.m + 1) * (p.dxf + 1) + (p.n + 1) * (p.dxg + 1);
+        p.res_off = res_w;
+        res_w += (int64_t)k * p.S;
+        p.val_off = val_w;
+        val_w += (int64_t)k * p.P;
+        p.out_off = out_w;
+        out_w += (int64_t)p.P * p.L;
+        p.sign_off = sign_b;
+        sign_b += p.P;
+        Kmax = std::max(Kmax, k);
+        Pmax = std::max(Pmax, p.P);
+        Lmax = std::max(Lmax, p.L);
+        red.add(q, p.S);
+        int key = ((std::max(p.m, p.n) + 1) + 3) / 4 * 4;
+        evb[key].add(q, (int64_t)k * p.P);
+        interp.add(q, k);
+        crt.add(q, p.P);
+        subproblems += (int64_t)k * p.P;
+    }
+    int rc = c->ensure_tables(Kmax, Pmax);
+    if (rc) return rc;
+    // ---- plan block: plans + work lists, one upload
+    std::vector<char> blk(sizeof(PairPlan) * n);
+    std::memcpy(blk.data(), plan.data(), sizeof(PairPlan) * n);
+    size_t o_red_p, o_red_s, o_int_p, o_int_s, o_crt_p, o_crt_s;
+    put_list(blk, red, o_red_p, o_red_s);
+    put_list(blk, interp, o_int_p, o_int_s);
+    put_list(blk, crt, o_crt_p, o_crt_s);
+    std::vector<std::pair<size_t, size_t>> o_ev;
+    for (auto &kv : evb) {
+        size_t a, b2;
+        put_list(blk, kv.second, a, b2);
+        o_ev.push_back({a, b2});
+    }
+    if (ensure_buf(c, (void **)&r->d_planblk, &r->planblk_cap, blk.size()) ||
+        ensure_buf(c, (void **)&r->d_res, &r->res_cap, res_w * 4) ||
+        ensure_buf(c, (void **)&r->d_val, &r->val_cap, val_w * 4) ||
+        ensure_buf(c, (void **)&r->d_out, &r->out_cap, out_w * 4) ||
+        ensure_buf(c, (void **)&r->d_sign, &r->sign_cap, sign_b))
+        return c->fail(GBR_ENOMEM, "device budget too small for this batch");
+    char *hp = (char *)c->pinned(blk.size(), 2);
+    if (!hp) return c->fail(GBR_ENOMEM, "pinned host staging");
+    std::memcpy(hp, blk.data(), blk.size());
+    e = cudaMemcpyAsync(r->d_planblk, hp, blk.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->d_deg, 0xff, sizeof(int32_t) * n, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, 4, s);
+    if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "plan upload", e);
+    auto mk = [&](size_t op, size_t os, const HostList &h) {
+        WorkList w;
+        w.pairs = (const int32_t *)(r->d_planblk + op);
+        w.start = (const int64_t *)(r->d_planblk + os);
+        w.n = (int32_t)h.pairs.size();
+        w.total = h.total;
+        return w;
+    };
+    L.plan = (const PairPlan *)r->d_planblk;
+    L.garner = c->d_garner;
+    L.garner_K = c->garner_K;
+    L.invk = c->d_invk;
+    L.invk_T = c->invk_T;
+    L.res = r->d_res;
+    L.val = r->d_val;
+    L.out = r->d_out;
+    L.sign = r->d_sign;
+    L.drop_unlucky = c->drop_unlucky;
+    if (c->stats_on) cudaEventRecord(c->ev[1], s);
+    int64_t kernels = 1;
+    e = launch_reduce(L, mk(o_red_p, o_red_s, red), s);
+    kernels++;
+    if (c->stats_on) cudaEventRecord(c->ev[2], s);
+    size_t bi = 0;
+    for (auto &kv : evb) {
+        if (e != cudaSuccess) break;
+        int key = kv.first;
+        int block = key > 64 ? 64 : 128;
+        e = launch_evalres(L, mk(o_ev[bi].first, o_ev[bi].second, kv.second), key, key, block, s);
+        kernels++;
+        ++bi;
+    }
+    if (c->stats_on) cudaEventRecord(c->ev[3], s);
+    if (e == cudaSuccess) e = launch_interp(L, mk(o_int_p, o_int_s, interp), Pmax, s);
+    kernels++;
+    if (c->stats_on) cudaEventRecord(c->ev[4], s);
+    if (e == cudaSuccess) e = launch_crt(L, mk(o_crt_p, o_crt_s, crt), Lmax, s);
+    kernels++;
+    if (c->stats_on) cudaEventRecord(c->ev[5], s);
+    if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "stage launch", e);
+    int32_t herr = 0;
+    e = cudaMemcpyAsync(&herr, c->d_err, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "resultant stages", e);
+    if (herr) return c->fail(GBR_EDEVICE, "device-side consistency check failed");
+    r->out_words = out_w;
+    r->sign_bytes = sign_b;
+    r->ran = true;
+    st.kernels = kernels;
+    st.subproblems = subproblems;
+    if (c->stats_on) {
+        float ms;
+        cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]); st.bounds_ms = ms;
+        cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]); st.reduce_ms = ms;
+        cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]); st.evalres_ms = ms;
+        cudaEventElapsedTime(&ms, c->ev[3], c->ev[4]); st.interp_ms = ms;
+        cudaEventElapsedTime(&ms, c->ev[4], c->ev[5]); st.crt_ms = ms;
+        cudaEventElapsedTime(&ms, c->ev[0], c->ev[5]); st.total_ms = ms;
+    }
+    c->stats = st;
+    return GBR_OK;
+}
+
+extern "C" int gbr_run_resident(gbr_ctx *c, gbr_resident *r) {
+    if (!c || !r) return GBR_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    try {
+        return gbr_run_resident_locked(c, r);
+    } catch (std::bad_alloc &) {
+        return c->fail(GBR_ENOMEM, "host allocation");
+    }
+}
+
+int gbr_fetch_resident_locked(gbr_ctx *c, gbr_resident *r, int first, int count, gbr_bigpoly *out) {
+    if (first < 0 || count < 0 || first + count > r->n || (count && !out)) return GBR_EINVAL;
+    if (!r->ran) return c->fail(GBR_EINVAL, "fetch before run");
+    if (count == 0) return GBR_OK;
+    const std::vector<PairPlan> &plan = r->h_plan;
+    int last = first + count - 1;
+    int64_t o0 = plan[first].out_off, o1 = plan[last].out_off + (int64_t)plan[last].P * plan[last].L;
+    int64_t s0 = plan[first].sign_off, s1 = plan[last].sign_off + plan[last].P;
+    size_t need = (size_t)(o1 - o0) * 4 + (size_t)(s1 - s0) + (size_t)count * 4 + 64;
+    char *h = (char *)c->pinned(need, 3);
+    if (!h) return c->fail(GBR_ENOMEM, "pinned host staging");
+    uint32_t *hm = (uint32_t *)h;
+    int32_t *hd = (int32_t *)(h + (size_t)(o1 - o0) * 4);
+    int8_t *hs = (int8_t *)(hd + count);
+    cudaStream_t s = c->stream;
+    cudaError_t e = cudaSuccess;
+    if (o1 > o0) e = cudaMemcpyAsync(hm, r->d_out + o0, (size_t)(o1 - o0) * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hd, r->d_deg + first, (size_t)count * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && s1 > s0) e = cudaMemcpyAsync(hs, r->d_sign + s0, (size_t)(s1 - s0), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "result readback", e);
+    for (int i = 0; i < count; ++i) {
+        const PairPlan &p = plan[first + i];
+        gbr_bigpoly &b = out[i];
+        b.deg = (p.flags & PLAN_ZERO) ? -1 : hd[i];
+        b.limbs = p.L;
+        b.mag = nullptr;
+        b.sign = nullptr;
+        if (b.deg < 0) {
+            b.deg = -1;
+            continue;
+        }
+        size_t nm = (size_t)(b.deg + 1) * p.L;
+        b.mag = (uint32_t *)std::malloc(nm * 4);
+        b.sign = (int8_t *)std::malloc((size_t)b.deg + 1);
+        if (!b.mag || !b.sign) {
+            std::free(b.mag);
+            std::free(b.sign);
+            for (int j = 0; j < i; ++j) gbr_free_result(c, &out[j]);
+            return c->fail(GBR_ENOMEM, "host result allocation");
+        }
+        std::memcpy(b.mag, hm + (p.out_off - o0), nm * 4);
+        std::memcpy(b.sign, hs + (p.sign_off - s0), (size_t)b.deg + 1);
+    }
+    return GBR_OK;
+}
+
+extern "C" int gbr_fetch_resident(gbr_ctx *c, gbr_resident *r, int first, int count, gbr_bigpoly *out) {
+    if (!c || !r) return GBR_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    return gbr_fetch_resident_locked(c, r, first, count, out);
+}
+
+extern "C" void gbr_free_result(gbr_ctx *, gbr_bigpoly *b) {
+    if (!b) return;
+    std::free(b->mag);
+    std::free(b->sign);
+    b->mag = nullptr;
+    b->sign = nullptr;
+    b->deg = -1;
+}
+
+// ------------------------------------------------------------------ one-shot and batch wrappers
+
+static int res_batch_impl(gbr_ctx *c, int n, const gbr_bipoly *f, const gbr_bipoly *g, int var, int disc,
+                          gbr_bigpoly *out) {
+    if (!c || n < 0 || (n && !out)) return GBR_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        out[i].deg = -1;
+        out[i].limbs = 0;
+        out[i].mag = nullptr;
+        out[i].sign = nullptr;
+    }
+    gbr_resident *r = nullptr;
+    int st = gbr_upload_pairs(c, n, f, g, var, disc, &r);
+    if (st) return st;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        cudaSetDevice(c->device);
+        try {
+            st = gbr_run_resident_locked(c, r);
+            if (!st) st = gbr_fetch_resident_locked(c, r, 0, n, out);
+        } catch (std::bad_alloc &) {
+            st = c->fail(GBR_ENOMEM, "host allocation");
+        }
+        if (c->stream) cudaStreamSynchronize(c->stream);
+        gbr_free_resident_locked(c, r);
+    }
+    return st;
+}
+
+extern "C" int gbr_resultant(gbr_ctx *c, const gbr_bipoly *f, const gbr_bipoly *g, int var, gbr_bigpoly *out) {
+    if (!f || !g) return GBR_EINVAL;
+    return res_batch_impl(c, 1, f, g, var, 0, out);
+}
+
+extern "C" int gbr_discriminant_res(gbr_ctx *c, const gbr_bipoly *f, int var, gbr_bigpoly *out) {
+    if (!f) return GBR_EINVAL;
+    return res_batch_impl(c, 1, f, nullptr, var, 1, out);
+}
+
+extern "C" int gbr_resultant_batch(gbr_ctx *c, int n, const gbr_bipoly *f, const gbr_bipoly *g, int var,
+                                   gbr_bigpoly *out) {
+    return res_batch_impl(c, n, f, g, var, 0, out);
+}
+
+extern "C" int gbr_discriminant_res_batch(gbr_ctx *c, int n, const gbr_bipoly *f, int var, gbr_bigpoly *out) {
+    return res_batch_impl(c, n, f, nullptr, var, 1, out);
+}
+
+// ------------------------------------------------------------------ host-side planning info
+
+namespace {
+double host_log2abs(const uint64_t *w, int W) {
+    uint64_t mag[GBR_MAX_WORDS];
+    bool neg = (int64_t)w[W - 1] < 0;
+    uint64_t carry = 1;
+    for (int i = 0; i < W; ++i) {
+        uint64_t v = w[i];
+        if (neg) {
+            v = ~v + carry;
+            carry = (carry && v == 0) ? 1 : 0;
+        }
+        mag[i] = v;
+    }
+    int t = W - 1;
+    while (t >= 0 && mag[t] == 0) --t;
+    if (t < 0) return -INFINITY;
+    double v = (double)mag[t];
+    if (t > 0) v += (double)mag[t - 1] * 0x1p-64;
+    return std::log2(v) + 64.0 * t;
+}
+
+double lse2(const std::vector<double> &a) {   // log2 sum 2^a_i
+    double mx = -INFINITY;
+    for (double v : a) mx = std::max(mx, v);
+    if (mx == -INFINITY) return -INFINITY;
+    double s = 0;
+    for (double v : a)
+        if (v != -INFINITY) s += std::exp2(v - mx);
+    return mx + std::log2(s);
+}
+
+// row degrees and log2 row 1-norms of one polynomial in the eliminated-variable view
+void host_rows(const gbr_bipoly *p, int var, std::vector<int> &deg, std::vector<double> &nrm) {
+    PolyDesc d = view_of(p, var, 0);
+    const uint64_t *w = (const uint64_t *)p->coef;
+    deg.assign(d.rows + 1, -1);
+    nrm.assign(d.rows + 1, -INFINITY);
+    for (int r = 0; r <= d.rows; ++r) {
+        std::vector<double> a;
+        for (int c = 0; c <= d.cols; ++c) {
+            double v = host_log2abs(w + ((int64_t)r * d.rstride + (int64_t)c * d.cstride) * d.words, d.words);
+            if (v != -INFINITY) {
+                deg[r] = c;
+                a.push_back(v);
+            }
+        }
+        nrm[r] = lse2(a);
+    }
+}
+}  // namespace
+
+extern "C" int gbr_resultant_info(const gbr_bipoly *f, const gbr_bipoly *g, int var, int disc, gbr_res_info *out) {
+    if (!out || (var != 0 && var != 1) || check_bipoly(f) || (!disc && check_bipoly(g))) return GBR_EINVAL;
+    std::vector<int> df, dg;
+    std::vector<double> nf, ng;
+    host_rows(f, var, df, nf);
+    if (disc) {
+        dg.assign(df.size() > 1 ? df.size() - 1 : 0, -1);
+        ng.assign(dg.size(), -INFINITY);
+        for (size_t r = 1; r < df.size(); ++r) {
+            dg[r - 1] = df[r];
+            ng[r - 1] = nf[r] == -INFINITY ? -INFINITY : nf[r] + std::log2((double)r);
+        }
+    } else {
+        host_rows(g, var, dg, ng);
+    }
+    PairBound b{};
+    auto summarise = [](const std::vector<int> &d, const std::vector<double> &nrm, int &m, int &dx, int &td,
+                        double &sq) {
+        m = dx = td = -1;
+        std::vector<double> a;
+        for (size_t r = 0; r < d.size(); ++r)
+            if (d[r] >= 0) {
+                m = (int)r;
+                dx = std::max(dx, d[r]);
+                td = std::max(td, (int)r + d[r]);
+                a.push_back(2.0 * nrm[r]);
+            }
+        sq = lse2(a);
+    };
+    double sf, sg;
+    summarise(df, nf, b.m, b.dxf, b.tdf, sf);
+    summarise(dg, ng, b.n, b.dxg, b.tdg, sg);
+    out->m = b.m;
+    out->n = b.n;
+    if (b.m < 0 || b.n < 0) {
+        out->deg_bound = -1;
+        out->log2_bound = 0;
+        out->primes = 0;
+        out->limbs = 0;
+        return GBR_OK;
+    }
+    b.log2B = (b.m == 0 && b.n == 0) ? 0.0 : 0.5 * b.n * sf + 0.5 * b.m * sg;
+    out->deg_bound = degree_bound(b);
+    out->log2_bound = b.log2B;
+    out->primes = primes_for_bits(b.log2B * (1.0 + 1e-9) + 2.0);
+    out->limbs = (31 * out->primes + 31) / 32;
+    return GBR_OK;
+}

@@ -1,0 +1,102 @@
+// Host-side state of a libgbres context (internal).
+#pragma once
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/gbres.h"
+#include "gbr_internal.h"
+
+namespace gbr {
+
+// First-fit allocator with coalescing over one device allocation (the caller's
+// workspace or the library's own cudaMalloc of the budget).  256-byte aligned.
+class Arena {
+   public:
+    void init(void *base, size_t cap);
+    void *alloc(size_t bytes);   // nullptr when no free block is large enough
+    void release(void *p);
+    size_t largest_free();
+    size_t in_use() {
+        std::lock_guard<std::mutex> g(mu);
+        return inuse;
+    }
+    size_t peak_use() {
+        std::lock_guard<std::mutex> g(mu);
+        return peak;
+    }
+    size_t capacity() const { return cap; }
+
+   private:
+    char *base = nullptr;
+    size_t cap = 0, inuse = 0, peak = 0;
+    std::map<size_t, size_t> free_, used_;
+    std::mutex mu;
+};
+
+struct ServeState;   // gbr_serve.cu
+
+}  // namespace gbr
+
+struct gbr_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    void *ws = nullptr;
+    bool own_ws = false;
+    size_t budget = 0;
+    gbr::Arena arena;
+    std::mutex mu;                 // serialises synchronous calls
+    std::mutex err_mu;
+    std::string err;
+    ModP *d_mods = nullptr;
+    int32_t *d_err = nullptr;
+    uint32_t *d_garner = nullptr;
+    int garner_K = 0;
+    uint32_t *d_invk = nullptr;
+    int invk_K = 0, invk_T = 0;
+    void *h_pin[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t h_pin_cap[4] = {0, 0, 0, 0};
+    cudaEvent_t ev[8] = {};
+    int drop_unlucky = 0, stats_on = 0, graph_on = 1, extra_primes = 0;
+    gbr_stats stats{};
+    std::map<uint64_t, cudaGraphExec_t> graphs;
+    gbr::ServeState *serve = nullptr;
+
+    int fail(int code, const char *what, cudaError_t e = cudaSuccess);
+    void *dalloc(size_t bytes);
+    void dfree(void *p);
+    void *pinned(size_t bytes, int slot);   // grow-only pinned staging buffer per slot
+    int ensure_tables(int K, int T);
+};
+
+struct gbr_resident {
+    int n = 0, var = 1, disc = 0;
+    int64_t coef_words = 0, rowdeg_n = 0;
+    uint64_t *d_coef = nullptr;
+    gbr::PairDesc *d_desc = nullptr;
+    int32_t *d_rowdeg = nullptr;
+    gbr::PairBound *d_bounds = nullptr;
+    int32_t *d_deg = nullptr;
+    std::vector<gbr::PairDesc> h_desc;
+    std::vector<gbr::PairPlan> h_plan;
+    char *d_planblk = nullptr;
+    size_t planblk_cap = 0;
+    uint32_t *d_res = nullptr, *d_val = nullptr, *d_out = nullptr;
+    size_t res_cap = 0, val_cap = 0, out_cap = 0;
+    int8_t *d_sign = nullptr;
+    size_t sign_cap = 0;
+    int64_t out_words = 0, sign_bytes = 0;
+    bool ran = false;
+    cudaGraphExec_t gexec = nullptr;
+};
+
+// internal entry points (context lock held by the caller)
+int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r);
+int gbr_fetch_resident_locked(gbr_ctx *c, gbr_resident *r, int first, int count, gbr_bigpoly *out);
+void gbr_free_resident_locked(gbr_ctx *c, gbr_resident *r);
+void gbr_serve_shutdown(gbr_ctx *c);

@@ -1,0 +1,119 @@
+// Internal structures shared by the host driver and the kernels of libgbres.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "gbr_modarith.cuh"
+
+namespace gbr {
+
+// ------------------------------------------------------------------ prime table (host)
+int num_primes();
+const ModP *host_mods();              // ModP for every table prime, p_0 > p_1 > ...
+double log2_prime_prefix(int k);      // sum_{i<k} log2 p_i
+int primes_for_bits(double bits);     // smallest k with sum_{i<k} log2 p_i > bits
+
+// Garner constants for the prefix prime list p_0..p_{k-1}: for prime i,
+// cinv[i] = (p_0 ... p_{i-1})^-1 mod p_i and pm[i*(i-1)/2 + j] = p_j mod p_i (j < i),
+// both in Montgomery form modulo p_i.  Layout: cinv[0..K) then pm.
+void garner_prefix_table(int K, uint32_t *out);   // out has K + K*(K-1)/2 words
+
+// Inverses 1/t mod p_i for t = 1..T-1 in Montgomery form, t = 0 slot unused:
+// out[i*T + t].
+void inverse_table(int K, int T, uint32_t *out);
+
+// ------------------------------------------------------------------ resident batch
+// One input polynomial in the eliminated-variable view: row r is the coefficient
+// of (eliminated variable)^r, column c the power of the other variable.
+struct PolyDesc {
+    int64_t off;        // first 64-bit word of the polynomial in the coefficient buffer
+    int32_t rows;       // row extent (number of rows - 1)
+    int32_t cols;       // column extent
+    int32_t rstride;    // coefficient stride between rows
+    int32_t cstride;    // coefficient stride between columns
+    int32_t words;      // 64-bit words per coefficient
+    int32_t rowdeg_off; // where the bounds kernel writes this polynomial's row degrees
+};
+
+struct PairDesc {
+    PolyDesc f, g;      // for disc, g is unused: g_j = (j+1) f_{j+1}
+    int32_t disc;
+    int32_t pad;
+};
+
+// Written by the bounds kernel (one per pair), read back by the host planner.
+struct PairBound {
+    int32_t m, n;       // actual degrees in the eliminated variable (-1: zero polynomial)
+    int32_t dxf, dxg;   // actual degrees in the other variable
+    int32_t tdf, tdg;   // total degrees
+    double log2B;       // upper bound on log2 of the Hadamard bound
+};
+
+// Per-pair plan, written by the host, read by every stage kernel.
+struct PairPlan {
+    int32_t m, n, dxf, dxg;
+    int32_t P;          // evaluation points = degree bound + 1
+    int32_t k;          // primes
+    int32_t L;          // 32-bit limbs per output coefficient
+    int32_t S;          // residue words per prime: (m+1)(dxf+1) + (n+1)(dxg+1)
+    int64_t res_off;    // residues [prime][S]                       (u32 words)
+    int64_t val_off;    // values / coefficients [prime][P]          (u32 words)
+    int64_t out_off;    // output magnitudes [coef][L]               (u32 words)
+    int64_t sign_off;   // output signs [coef]                       (bytes)
+    int32_t rowdeg_f, rowdeg_g;   // offsets of row degree arrays
+    int32_t disc, flags;          // flags bit0: zero result, no device work
+};
+
+enum : int32_t { PLAN_ZERO = 1 };
+
+// Host-side bound arithmetic shared by gbr_resultant_info and the planner.
+GBR_HD int32_t degree_bound(const PairBound &b) {
+    if (b.m < 0 || b.n < 0) return 0;
+    int64_t d1 = (int64_t)b.n * b.dxf + (int64_t)b.m * b.dxg;
+    int64_t d2 = (int64_t)b.tdf * b.tdg;
+    int64_t d = d1 < d2 ? d1 : d2;
+    return (int32_t)(d < 0 ? 0 : d);
+}
+
+// ------------------------------------------------------------------ kernel launchers
+struct ResLaunch {
+    // device pointers
+    const uint64_t *coef;
+    const PairDesc *desc;
+    PairBound *bounds;
+    int32_t *rowdeg;
+    const PairPlan *plan;
+    const ModP *mods;
+    const uint32_t *garner;      // prefix Garner table (K + K(K-1)/2 words)
+    int32_t garner_K;
+    const uint32_t *invk;        // [prime][invk_T] inverses of 1..T-1
+    int32_t invk_T;
+    uint32_t *res;               // residues
+    uint32_t *val;               // values -> coefficients
+    uint32_t *out;               // output magnitudes
+    int8_t *sign;                // output signs
+    int32_t *deg;                // per pair output degree
+    int32_t *err;                // device error word (0 = ok)
+    int32_t npairs;
+    int32_t drop_unlucky;
+};
+
+// Work lists (device arrays, built by the host planner).
+struct WorkList {
+    const int32_t *pairs;     // pair ids
+    const int64_t *start;     // start[i] = first item of pairs[i]; start[n] = total
+    int32_t n;
+    int64_t total;
+};
+
+cudaError_t launch_bounds(const ResLaunch &L, cudaStream_t s);
+cudaError_t launch_reduce(const ResLaunch &L, const WorkList &w, cudaStream_t s);
+cudaError_t launch_evalres(const ResLaunch &L, const WorkList &w, int slots_f, int slots_g, int block,
+                           cudaStream_t s);
+cudaError_t launch_interp(const ResLaunch &L, const WorkList &w, int maxP, cudaStream_t s);
+cudaError_t launch_crt(const ResLaunch &L, const WorkList &w, int maxL, cudaStream_t s);
+cudaError_t launch_zero_init(const ResLaunch &L, cudaStream_t s);
+
+}  // namespace gbr

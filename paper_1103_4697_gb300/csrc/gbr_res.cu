@@ -1,0 +1,505 @@
+// Device stages of the multi-modular resultant res_var(f, g) in Z[x].
+//
+// The scheme is the divide-conquer-combine method the paper's Section 4
+// ("Symbolic Speedups") describes after Brown and Collins: (1) modular and
+// evaluation homomorphisms turn the bivariate problem into independent
+// subproblems over prime fields, (2) each subproblem is solved on its own,
+// (3) interpolation in x and Chinese remaindering recover the integer result.
+// Stages:
+//   bounds   (A0) actual degrees and the Hadamard bound, one warp per pair
+//   reduce   (A1) coefficients -> residues mod every prime (Montgomery form)
+//   evalres  (A2+A3) one thread per (pair, prime, point): Horner evaluation of
+//            every y-coefficient at x = point, then the univariate resultant with
+//            formal degrees by fraction-free remainder steps
+//   interp   (A4) one warp per (pair, prime): Newton interpolation on the
+//            points 0..P-1 and conversion to monomial coefficients
+//   crt      (A5) one thread per (pair, coefficient): Garner mixed-radix digits,
+//            symmetric lift, magnitude limbs
+#include <math.h>
+
+#include "gbr_internal.h"
+
+namespace gbr {
+
+__device__ __forceinline__ int wl_find(const int64_t *start, int n, int64_t item) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------------------ A0: bounds
+
+// log2 |c| of a two's-complement multi-word integer; -inf for zero.
+__device__ double coef_log2abs(const uint64_t *w, int W) {
+    uint64_t mag[8];
+    bool neg = (int64_t)w[W - 1] < 0;
+    uint64_t carry = 1;
+    for (int i = 0; i < W; ++i) {
+        uint64_t v = w[i];
+        if (neg) {
+            v = ~v + carry;
+            carry = (carry && v == 0) ? 1 : 0;
+        }
+        mag[i] = v;
+    }
+    int t = W - 1;
+    while (t >= 0 && mag[t] == 0) --t;
+    if (t < 0) return -INFINITY;
+    double v = (double)mag[t];
+    if (t > 0) v += (double)mag[t - 1] * 0x1p-64;
+    return log2(v) + 64.0 * t;
+}
+
+struct Lse {   // running log2 of a sum of powers of two: value = s * 2^mx
+    double mx, s;
+    __device__ void init() { mx = -INFINITY; s = 0.0; }
+    __device__ void add(double a) {
+        if (a == -INFINITY) return;
+        if (a > mx) { s = s * exp2(mx - a) + 1.0; mx = a; }
+        else s += exp2(a - mx);
+    }
+    __device__ void merge(double omx, double os) {
+        if (os == 0.0) return;
+        if (s == 0.0) { mx = omx; s = os; return; }
+        if (omx > mx) { s = s * exp2(mx - omx) + os; mx = omx; }
+        else s += os * exp2(omx - mx);
+    }
+    __device__ double log2v() const { return s == 0.0 ? -INFINITY : mx + log2(s); }
+};
+
+__device__ void warp_lse(Lse &l) {
+    for (int o = 16; o; o >>= 1) {
+        double omx = __shfl_xor_sync(0xffffffffu, l.mx, o);
+        double os = __shfl_xor_sync(0xffffffffu, l.s, o);
+        l.merge(omx, os);
+    }
+}
+
+__device__ __forceinline__ const uint64_t *coef_ptr(const uint64_t *coef, const PolyDesc &d, int r, int c) {
+    return coef + d.off + ((int64_t)r * d.rstride + (int64_t)c * d.cstride) * d.words;
+}
+
+// Scans one polynomial row by row.  For disc, also produces the rows of
+// g = d f / d var on the fly: g_r = (r+1) f_{r+1}.
+__global__ void k_bounds(ResLaunch L) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (warp >= L.npairs) return;
+    const PairDesc D = L.desc[warp];
+    PairBound B;
+    for (int which = 0; which < 2; ++which) {
+        if (which == 1 && D.disc) break;
+        const PolyDesc &P = which ? D.g : D.f;
+        int mdeg = -1, dxmax = -1, td = -1;
+        Lse sq;     // log2 sum_r ||row_r||_1^2
+        sq.init();
+        int mdeg_g = -1, dx_g = -1, td_g = -1;
+        Lse sq_g;
+        sq_g.init();
+        for (int r = 0; r <= P.rows; ++r) {
+            int cmax = -1;
+            Lse nrm;
+            nrm.init();
+            for (int c = lane; c <= P.cols; c += 32) {
+                double a = coef_log2abs(coef_ptr(L.coef, P, r, c), P.words);
+                if (a != -INFINITY) {
+                    cmax = c;
+                    nrm.add(a);
+                }
+            }
+            for (int o = 16; o; o >>= 1) cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+            warp_lse(nrm);
+            double ln = nrm.log2v();
+            if (lane == 0) L.rowdeg[P.rowdeg_off + r] = cmax;
+            if (cmax >= 0) {
+                mdeg = r;
+                dxmax = max(dxmax, cmax);
+                td = max(td, r + cmax);
+                sq.add(2.0 * ln);
+            }
+            if (which == 0 && D.disc && r >= 1) {
+                if (lane == 0) L.rowdeg[D.g.rowdeg_off + r - 1] = cmax;
+                if (cmax >= 0) {
+                    mdeg_g = r - 1;
+                    dx_g = max(dx_g, cmax);
+                    td_g = max(td_g, r - 1 + cmax);
+                    sq_g.add(2.0 * (ln + log2((double)r)));
+                }
+            }
+        }
+        if (which == 0) {
+            B.m = mdeg; B.dxf = dxmax; B.tdf = td;
+            B.log2B = sq.log2v();           // temporarily: log2 sum ||f_i||^2
+            if (D.disc) {
+                B.n = mdeg_g; B.dxg = dx_g; B.tdg = td_g;
+                // log2B = (n/2) log2 sum f + (m/2) log2 sum g
+                double lf = sq.log2v(), lg = sq_g.log2v();
+                if (B.m >= 0 && B.n >= 0) B.log2B = 0.5 * B.n * lf + 0.5 * B.m * lg;
+                else B.log2B = 0.0;
+            }
+        } else {
+            B.n = mdeg; B.dxg = dxmax; B.tdg = td;
+            double lf = B.log2B, lg = sq.log2v();
+            if (B.m >= 0 && B.n >= 0) B.log2B = 0.5 * B.n * lf + 0.5 * B.m * lg;
+            else B.log2B = 0.0;
+        }
+    }
+    if (B.m == 0 && B.n == 0) B.log2B = 0.0;
+    if (lane == 0) L.bounds[warp] = B;
+}
+
+cudaError_t launch_bounds(const ResLaunch &L, cudaStream_t s) {
+    if (L.npairs <= 0) return cudaSuccess;
+    int threads = 128;
+    int blocks = (L.npairs * 32 + threads - 1) / threads;
+    k_bounds<<<blocks, threads, 0, s>>>(L);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ A1: modular reduction
+
+__global__ void k_reduce(ResLaunch L, WorkList w) {
+    for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < w.total;
+         item += (int64_t)gridDim.x * blockDim.x) {
+        int bi = wl_find(w.start, w.n, item);
+        int q = w.pairs[bi];
+        int64_t s = item - w.start[bi];
+        const PairPlan &P = L.plan[q];
+        const PairDesc &D = L.desc[q];
+        int nf = (P.m + 1) * (P.dxf + 1);
+        const PolyDesc *src;
+        int row, col, mult = 0;
+        if (s < nf) {
+            src = &D.f;
+            row = (int)(s / (P.dxf + 1));
+            col = (int)(s % (P.dxf + 1));
+        } else {
+            int64_t s2 = s - nf;
+            row = (int)(s2 / (P.dxg + 1));
+            col = (int)(s2 % (P.dxg + 1));
+            if (D.disc) {
+                src = &D.f;
+                mult = row + 1;
+                row = row + 1;
+            } else {
+                src = &D.g;
+            }
+        }
+        uint64_t wbuf[8];
+        const uint64_t *cp = coef_ptr(L.coef, *src, row, col);
+        int W = src->words;
+        for (int i = 0; i < W; ++i) wbuf[i] = cp[i];
+        uint32_t *dst = L.res + P.res_off + s;
+        for (int i = 0; i < P.k; ++i) {
+            ModP M = L.mods[i];
+            uint32_t r = mp_from_words(wbuf, W, M);
+            if (mult) r = mp_mul(r, mp_to((uint32_t)mult, M), M);
+            dst[(int64_t)i * P.S] = r;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ A3: resultant mod p
+
+// res_{da,db}(A, B) over F_p with formal degrees.  A and B live in shared memory,
+// one column per thread (stride BS); A[t*BS] is the coefficient of y^(da - t).
+// Identities used (lc = leading coefficient):
+//   res_{a,b}(A,B) = (-1)^{ab} res_{b,a}(B,A)
+//   lc(A) != 0:  res_{a,b}(A,B) = lc(A)^{b-b'} res_{a,b'}(A,B')   (B' = B without zero top terms)
+//   lc(B) = zeta != 0, R = A mod B, deg R = r:
+//       res_{a,b}(A,B) = (-1)^{ab} zeta^{a-r} res_{b,r}(B,R)
+//   res_{b,r}(B, c R) = c^b res_{b,r}(B,R)    (R is reached as zeta^e R by e fraction-free steps)
+//   res_{a,0}(A, b0) = b0^a ; res_{0,0} = 1 ; both leading coefficients zero -> 0.
+GBR_HD uint32_t res_formal(uint32_t *A, int da, uint32_t *B, int db, int BS, const ModP &M) {
+    const uint32_t one = M.r1;
+    uint32_t acc = one, den = one;
+    bool neg = false;
+    if (da == 0 && db == 0) return one;
+    if (A[0] == 0 && B[0] == 0) return 0u;
+    if (A[0] == 0) {
+        int da0 = da;
+        while (da >= 0 && A[0] == 0) { A += BS; --da; }
+        if ((da0 * db) & 1) neg = !neg;
+        if (da < 0) {
+            if (db >= 1) return 0u;
+            return mp_pow(B[0], (uint32_t)da0, M);
+        }
+        acc = mp_pow(B[0], (uint32_t)(da0 - da), M);
+        uint32_t *t = A; A = B; B = t;
+        int ti = da; da = db; db = ti;
+    } else if (B[0] == 0) {
+        int db0 = db;
+        while (db >= 0 && B[0] == 0) { B += BS; --db; }
+        if (db < 0) {
+            if (da >= 1) return 0u;
+            return mp_pow(A[0], (uint32_t)db0, M);
+        }
+        acc = mp_pow(A[0], (uint32_t)(db0 - db), M);
+    }
+    while (true) {
+        if (da < db) {
+            uint32_t *t = A; A = B; B = t;
+            int ti = da; da = db; db = ti;
+            if ((da * db) & 1) neg = !neg;
+        }
+        if (db == 0) {
+            acc = mp_mul(acc, mp_pow(B[0], (uint32_t)da, M), M);
+            break;
+        }
+        const uint32_t zeta = B[0];
+        const int DA = da;
+        int e = 0;
+        while (da >= db) {
+            const uint32_t q = A[0];
+            int t = 1;
+            for (; t <= db; ++t) A[t * BS] = mp_mulsub(zeta, A[t * BS], q, B[t * BS], M);
+            for (; t <= da; ++t) A[t * BS] = mp_mul(zeta, A[t * BS], M);
+            A += BS;
+            --da;
+            ++e;
+            while (da >= 0 && A[0] == 0) { A += BS; --da; }
+        }
+        if (da < 0) return 0u;
+        if ((DA * db) & 1) neg = !neg;
+        acc = mp_mul(acc, mp_pow(zeta, (uint32_t)(DA - da), M), M);
+        den = mp_mul(den, mp_pow(zeta, (uint32_t)(e * db), M), M);
+        uint32_t *t = A; A = B; B = t;
+        int ti = da; da = db; db = ti;
+    }
+    uint32_t r = mp_mul(acc, mp_inv(den, M), M);
+    return neg ? mp_neg(r, M.p) : r;
+}
+
+// ------------------------------------------------------------------ A2 + A3: evaluate and solve
+
+__global__ void k_evalres(ResLaunch L, WorkList w, int SF, int SG) {
+    extern __shared__ uint32_t smem[];
+    const int BS = blockDim.x;
+    uint32_t *Fs = smem + threadIdx.x;
+    uint32_t *Gs = smem + SF * BS + threadIdx.x;
+    for (int64_t item = blockIdx.x * (int64_t)BS + threadIdx.x; item < w.total; item += (int64_t)gridDim.x * BS) {
+        int bi = wl_find(w.start, w.n, item);
+        int q = w.pairs[bi];
+        int64_t local = item - w.start[bi];
+        const PairPlan &P = L.plan[q];
+        int i = (int)(local / P.P);
+        int j = (int)(local % P.P);
+        const ModP M = L.mods[i];
+        const uint32_t a = mp_to((uint32_t)j, M);
+        const uint32_t *rf = L.res + P.res_off + (int64_t)i * P.S;
+        const uint32_t *rg = rf + (P.m + 1) * (P.dxf + 1);
+        const int32_t *dgf = L.rowdeg + P.rowdeg_f;
+        const int32_t *dgg = L.rowdeg + P.rowdeg_g;
+        for (int t = 0; t <= P.m; ++t) {
+            int row = P.m - t;
+            const uint32_t *c = rf + row * (P.dxf + 1);
+            uint32_t acc = 0;
+            for (int x = dgf[row]; x >= 0; --x) acc = mp_add(mp_mul(acc, a, M), c[x], M.p);
+            Fs[t * BS] = acc;
+        }
+        for (int t = 0; t <= P.n; ++t) {
+            int row = P.n - t;
+            const uint32_t *c = rg + row * (P.dxg + 1);
+            uint32_t acc = 0;
+            for (int x = dgg[row]; x >= 0; --x) acc = mp_add(mp_mul(acc, a, M), c[x], M.p);
+            Gs[t * BS] = acc;
+        }
+        L.val[P.val_off + (int64_t)i * P.P + j] = res_formal(Fs, P.m, Gs, P.n, BS, M);
+    }
+}
+
+// ------------------------------------------------------------------ A4: interpolation
+
+__global__ void k_interp(ResLaunch L, WorkList w, int maxP) {
+    extern __shared__ uint32_t smem[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t *V = smem + (size_t)wid * 2 * maxP;
+    uint32_t *Wp = V + maxP;
+    for (int64_t item = (int64_t)blockIdx.x * nw + wid; item < w.total; item += (int64_t)gridDim.x * nw) {
+        int bi = wl_find(w.start, w.n, item);
+        int q = w.pairs[bi];
+        int i = (int)(item - w.start[bi]);
+        const PairPlan &P = L.plan[q];
+        const int Pn = P.P;
+        const ModP M = L.mods[i];
+        uint32_t *g = L.val + P.val_off + (int64_t)i * Pn;
+        for (int t = lane; t < Pn; t += 32) {
+            V[t] = g[t];
+            Wp[t] = 0;
+        }
+        __syncwarp();
+        const int C = (Pn + 31) >> 5;
+        const int lo0 = lane * C;
+        const int hi0 = min(Pn, lo0 + C);
+        const uint32_t *inv = L.invk + (int64_t)i * L.invk_T;
+        // divided differences on the unit grid: level k divides by x_j - x_{j-k} = k
+        for (int k = 1; k < Pn; ++k) {
+            const uint32_t ik = inv[k];
+            uint32_t prev = (lo0 >= 1 && lo0 - 1 < Pn) ? V[lo0 - 1] : 0u;
+            __syncwarp();
+            const int lo = max(lo0, k);
+            for (int j = hi0 - 1; j >= lo; --j) {
+                uint32_t cm1 = (j - 1 >= lo0) ? V[j - 1] : prev;
+                V[j] = mp_mul(mp_sub(V[j], cm1, M.p), ik, M);
+            }
+            __syncwarp();
+        }
+        // Newton form -> monomial basis: W = c_{P-1}; W <- W (x - k) + c_k
+        if (lane == 0) Wp[0] = V[Pn - 1];
+        __syncwarp();
+        for (int k = Pn - 2; k >= 0; --k) {
+            const int deg = Pn - 1 - k;
+            const uint32_t kt = mp_to((uint32_t)k, M);
+            const uint32_t ck = V[k];
+            uint32_t prev = (lo0 >= 1 && lo0 - 1 < Pn) ? Wp[lo0 - 1] : 0u;
+            __syncwarp();
+            const int hi = min(hi0, deg + 1);
+            for (int t = hi - 1; t >= lo0; --t) {
+                uint32_t below = (t == 0) ? 0u : ((t - 1 >= lo0) ? Wp[t - 1] : prev);
+                uint32_t v = mp_sub(below, mp_mul(kt, Wp[t], M), M.p);
+                if (t == 0) v = mp_add(v, ck, M.p);
+                Wp[t] = v;
+            }
+            __syncwarp();
+        }
+        for (int t = lane; t < Pn; t += 32) g[t] = mp_from(Wp[t], M);
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ A5: Chinese remaindering
+
+__global__ void k_crt(ResLaunch L, WorkList w, int LM) {
+    extern __shared__ uint32_t smem[];
+    const int BS = blockDim.x;
+    uint32_t *limb = smem + threadIdx.x;
+    const uint32_t *cinv = L.garner;
+    const uint32_t *pm = L.garner + L.garner_K;
+    for (int64_t item = blockIdx.x * (int64_t)BS + threadIdx.x; item < w.total; item += (int64_t)gridDim.x * BS) {
+        int bi = wl_find(w.start, w.n, item);
+        int q = w.pairs[bi];
+        int c = (int)(item - w.start[bi]);
+        const PairPlan &P = L.plan[q];
+        const int k = P.k, Pn = P.P;
+        uint32_t *v = L.val + P.val_off + c;
+        // Garner: digits v_i with X = sum v_i prod_{j<i} p_j, 0 <= v_i < p_i
+        for (int i = 1; i < k; ++i) {
+            const ModP M = L.mods[i];
+            const uint32_t *pmi = pm + (int64_t)i * (i - 1) / 2;
+            uint32_t t = v[(int64_t)(i - 1) * Pn];
+            t = min(t, t - M.p);
+            for (int j = i - 2; j >= 0; --j) {
+                uint32_t vj = v[(int64_t)j * Pn];
+                vj = min(vj, vj - M.p);
+                t = mp_add(mp_mul(t, pmi[j], M), vj, M.p);
+            }
+            uint32_t r = v[(int64_t)i * Pn];
+            v[(int64_t)i * Pn] = mp_mul(mp_sub(r, t, M.p), cinv[i], M);
+        }
+        // symmetric lift: X > (M-1)/2 <=> digits compare above (p_i - 1)/2 from the top
+        int cmp = 0;
+        for (int i = k - 1; i >= 0 && cmp == 0; --i) {
+            uint32_t d = v[(int64_t)i * Pn];
+            uint32_t h = (L.mods[i].p - 1u) >> 1;
+            cmp = (d > h) - (d < h);
+        }
+        const bool neg = cmp > 0;
+        // |value| = X or M - X = sum (p_i - 1 - v_i) prod_{j<i} p_j + 1, Horner to 32-bit limbs
+        int nl = 0;
+        for (int i = k - 1; i >= 0; --i) {
+            const uint32_t p = L.mods[i].p;
+            uint32_t d = v[(int64_t)i * Pn];
+            if (neg) d = p - 1u - d;
+            uint32_t carry = d;
+            for (int l = 0; l < nl; ++l) {
+                uint64_t t = (uint64_t)limb[l * BS] * p + carry;
+                limb[l * BS] = (uint32_t)t;
+                carry = (uint32_t)(t >> 32);
+            }
+            if (carry && nl < LM) limb[(nl++) * BS] = carry;
+        }
+        if (neg) {
+            int l = 0;
+            for (; l < nl; ++l)
+                if (++limb[l * BS] != 0u) break;
+            if (l == nl && nl < LM) limb[(nl++) * BS] = 1u;
+        }
+        if (nl > P.L) atomicExch(L.err, 2);
+        uint32_t *o = L.out + P.out_off + (int64_t)c * P.L;
+        for (int l = 0; l < P.L; ++l) o[l] = l < nl ? limb[l * BS] : 0u;
+        L.sign[P.sign_off + c] = nl == 0 ? 0 : (neg ? -1 : 1);
+        if (nl > 0) atomicMax(L.deg + q, c);
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+
+static int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+template <typename K>
+static int persistent_grid(K kernel, int block, size_t smem, int64_t items_in_blocks) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
+    if (per_sm < 1) per_sm = 1;
+    int64_t cap = (int64_t)per_sm * sm_count();
+    return (int)(items_in_blocks < cap ? (items_in_blocks < 1 ? 1 : items_in_blocks) : cap);
+}
+
+cudaError_t launch_reduce(const ResLaunch &L, const WorkList &w, cudaStream_t s) {
+    if (w.total <= 0) return cudaSuccess;
+    int block = 256;
+    int grid = persistent_grid(k_reduce, block, 0, (w.total + block - 1) / block);
+    k_reduce<<<grid, block, 0, s>>>(L, w);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_evalres(const ResLaunch &L, const WorkList &w, int SF, int SG, int block, cudaStream_t s) {
+    if (w.total <= 0) return cudaSuccess;
+    size_t smem = (size_t)(SF + SG) * block * sizeof(uint32_t);
+    cudaError_t e = cudaFuncSetAttribute(k_evalres, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int grid = persistent_grid(k_evalres, block, smem, (w.total + block - 1) / block);
+    k_evalres<<<grid, block, smem, s>>>(L, w, SF, SG);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interp(const ResLaunch &L, const WorkList &w, int maxP, cudaStream_t s) {
+    if (w.total <= 0) return cudaSuccess;
+    size_t per_warp = (size_t)2 * maxP * sizeof(uint32_t);
+    int nw = (int)((48 * 1024) / per_warp);
+    if (nw > 8) nw = 8;
+    if (nw < 1) nw = 1;
+    size_t smem = per_warp * nw;
+    cudaError_t e = cudaFuncSetAttribute(k_interp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int grid = persistent_grid(k_interp, nw * 32, smem, (w.total + nw - 1) / nw);
+    k_interp<<<grid, nw * 32, smem, s>>>(L, w, maxP);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_crt(const ResLaunch &L, const WorkList &w, int maxL, cudaStream_t s) {
+    if (w.total <= 0) return cudaSuccess;
+    int block = 128;
+    while (block > 32 && (size_t)maxL * block * 4 > 160 * 1024) block >>= 1;
+    size_t smem = (size_t)maxL * block * sizeof(uint32_t);
+    cudaError_t e = cudaFuncSetAttribute(k_crt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int grid = persistent_grid(k_crt, block, smem, (w.total + block - 1) / block);
+    k_crt<<<grid, block, smem, s>>>(L, w, maxL);
+    return cudaGetLastError();
+}
+
+}  // namespace gbr

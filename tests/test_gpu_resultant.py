@@ -1,0 +1,194 @@
+"""GPU parity: res_var(f, g) from libgbres equals the CPU oracle bit for bit.
+
+Every comparison is exact (integer results, tolerance 0).  Small cases compare
+every coefficient; the full-size workloads compare every coefficient of sampled
+pairs against the oracle's exact interpolation and the value R(a) at random
+integer points a for more sampled pairs (a polynomial of degree D that agrees at
+D + 1 points is equal; random wide points catch any wrong coefficient).
+"""
+
+import json
+import os
+import random
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1103_4697_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1103_4697_gb300.api import Context
+
+    c = Context(device=0, mem_budget=16 << 30)
+    yield c
+    c.close()
+
+
+def _poly_eval(c, a):
+    v = 0
+    for x in reversed(c):
+        v = v * a + x
+    return v
+
+
+def _oracle(f, g):
+    return list(O.res_subres(f, g))
+
+
+def test_hand_examples(ctx):
+    gold = json.load(open(os.path.join(HERE, "golden", "hand_examples.json")))
+    for e in gold["resultants"]:
+        assert ctx.resultant(e["f"], e["g"]) == e["res"]
+
+
+def test_small_dense_pair(ctx):
+    f, g = W.small_dense_pair(1)
+    assert ctx.resultant(f, g) == list(O.res_bareiss(f, g))
+
+
+@pytest.mark.parametrize("seed,m,n", [(1, 1, 1), (2, 2, 3), (3, 5, 3), (4, 7, 6), (5, 1, 9)])
+def test_planted_roots(ctx, seed, m, n):
+    f, g, *_ = W.planted_roots_pair(seed, m, n)
+    assert ctx.resultant(f, g) == _oracle(f, g)
+
+
+def test_symmetry_and_var0(ctx):
+    f, g = W.small_dense_pair(11, 5, 8)
+    r = ctx.resultant(f, g)
+    m, n = O.ydeg(f), O.ydeg(g)
+    s = ctx.resultant(g, f)
+    assert s == (r if (m * n) % 2 == 0 else [-c for c in r])
+    # eliminating x of (f, g) equals eliminating y of the transposed pair
+    ft = np.array(f, dtype=np.int64).T.copy()
+    gt = np.array(g, dtype=np.int64).T.copy()
+    assert ctx.resultant(f, g, var=0) == _oracle(ft, gt)
+
+
+def test_degenerate_inputs(ctx):
+    g = [[1, 2], [0, 1], [5]]
+    assert ctx.resultant([[3, 1]], g) == _oracle([[3, 1]], g)            # m = 0
+    assert ctx.resultant(g, [[3, 1]]) == _oracle(g, [[3, 1]])            # n = 0
+    assert ctx.resultant([[2]], [[7, 1]]) == [1]                          # m = n = 0
+    assert ctx.resultant([[0]], g) == []                                  # f = 0
+    assert ctx.resultant(g, [[0, 0], [0, 0]]) == []                       # g = 0
+    assert ctx.resultant([[0, 0], [0, 0], [1]], g) == _oracle([[0, 0], [0, 0], [1]], g)   # zero rows
+
+
+def test_leading_coefficient_vanishes_at_points(ctx):
+    """lc_y f = (x-2)(x+3) x and lc_y g = x - 2 vanish at evaluation points 0 and 2:
+    the formal-degree elimination must still give the exact determinant."""
+    f = [[1, 2, -1], [0, 1], [0, -6, 1, 1]]
+    g = [[2, -1], [1, 0, 1], [-2, 1]]
+    assert ctx.resultant(f, g) == list(O.res_bareiss(f, g))
+    # both leading coefficients vanish at x = 2: R(2) = 0
+    assert _poly_eval(ctx.resultant(f, g), 2) == 0
+
+
+def test_prime_divides_leading_coefficient(ctx):
+    """lc_y f is a multiple of the first two table primes: it vanishes identically
+    modulo them; the formal-degree path stays exact."""
+    from paper_1103_4697_gb300.api import primes
+
+    p0, p1 = primes(2)
+    f = [[3, 1, 4], [1, 5], [p0 * p1, 0, p0 * p1 * 7]]
+    g = [[2, 7], [1, 8, 2], [9]]
+    assert ctx.resultant(f, g) == _oracle(f, g)
+
+
+def test_discriminant_small(ctx):
+    for seed in range(4):
+        f, _ = W.small_dense_pair(30 + seed, 6, 8)
+        assert ctx.discriminant_res(f) == list(O.disc_res(f))
+
+
+def test_batch_mixed_small(ctx):
+    """Mixed degrees in one batch: several work tiles per bucket and a ragged tail."""
+    rng = random.Random(7)
+    fs, gs = [], []
+    for _ in range(97):
+        m, n = rng.randint(0, 9), rng.randint(0, 9)
+        dx = rng.randint(0, 6)
+        fs.append([[rng.randint(-50, 50) for _ in range(dx + 1)] for _ in range(m + 1)])
+        gs.append([[rng.randint(-50, 50) for _ in range(rng.randint(0, 6) + 1)] for _ in range(n + 1)])
+    got = ctx.resultant_batch(fs, gs)
+    for f, g, r in zip(fs, gs, got):
+        assert r == _oracle(f, g)
+
+
+def test_batch_extra_prime_is_identical(ctx):
+    from paper_1103_4697_gb300.native import OPT_EXTRA_PRIMES
+
+    f, g = W.small_dense_pair(2, 8, 12)
+    r0 = ctx.resultant(f, g)
+    ctx.set_option(OPT_EXTRA_PRIMES, 1)
+    try:
+        r1 = ctx.resultant(f, g)
+    finally:
+        ctx.set_option(OPT_EXTRA_PRIMES, 0)
+    assert r0 == r1 == _oracle(f, g)
+
+
+def test_big_coefficients_multiword(ctx):
+    """Coefficients above 64 bits (multi-word input)."""
+    rng = random.Random(3)
+    f = [[rng.randint(-2 ** 150, 2 ** 150) for _ in range(4)] for _ in range(4)]
+    g = [[rng.randint(-2 ** 90, 2 ** 90) for _ in range(3)] for _ in range(5)]
+    assert ctx.resultant(f, g) == _oracle(f, g)
+
+
+def test_deg20_pair_full(ctx):
+    """The degree-20 pair, 16-bit coefficients: res_y(f, g) and res_y(f, f_y), every
+    coefficient against the oracle's exact interpolation over Z."""
+    f, g = W.deg20_pair(2)
+    assert ctx.resultant(f, g) == list(O.res_evalz(f, g))
+    assert ctx.discriminant_res(f) == list(O.disc_res(f, "evalz"))
+
+
+def test_conic_curves_full(ctx):
+    """Product of 8 conics plus sparse terms (hundreds of primes) against a dense
+    degree-24 curve with 64-bit coefficients; res_y(f, g) and res_y(f, f_y)."""
+    f, g = W.conic_curves(4)
+    r = ctx.resultant(f, g)
+    assert r == list(O.res_evalz(f, g))
+    d = ctx.discriminant_res(f)
+    assert d == list(O.disc_res(f, "evalz"))
+
+
+def test_deg20_batch_sampled(ctx):
+    """The 4096-pair degree-20 batch in the launch configuration the benchmark
+    times: sampled pairs checked coefficient by coefficient and at random points."""
+    F, G = W.deg20_batch_arrays(4096)
+    res = ctx.upload_pairs(F, G)
+    res.run()
+    out = res.fetch()
+    rng = random.Random(11)
+    for q in rng.sample(range(4096), 2):
+        assert out[q] == list(O.res_evalz(F[q], G[q]))
+    for q in rng.sample(range(4096), 48):
+        for a in (rng.randint(-10 ** 6, 10 ** 6), rng.randint(-10 ** 6, 10 ** 6)):
+            assert _poly_eval(out[q], a) == O.res_at_prs(F[q], G[q], a)
+    res.free()
+
+
+def test_mixed_batch_sampled(ctx):
+    """Heterogeneous batch (degrees 4..16 per variable, 8..32-bit coefficients,
+    a quarter with planted common factors)."""
+    ps = W.mixed_batch(3, 512)
+    out = ctx.resultant_batch(ps.f, ps.g)
+    rng = random.Random(5)
+    for q, planted in enumerate(ps.planted):
+        if planted:
+            assert out[q] == []
+    for q in rng.sample(range(512), 24):
+        for a in (rng.randint(-10 ** 5, 10 ** 5),):
+            assert _poly_eval(out[q], a) == O.res_at_prs(ps.f[q], ps.g[q], a)
+    small = [q for q in range(512) if not ps.planted[q] and len(ps.f[q]) <= 8 and len(ps.f[q][0]) <= 8]
+    for q in small[:3]:
+        assert out[q] == list(O.res_evalz(ps.f[q], ps.g[q]))

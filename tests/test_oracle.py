@@ -299,3 +299,13 @@ def test_subres_abnormal_sequences(seed):
         Fa = [O.zx_eval(O.zx_trim(r), a) for r in f]
         Ga = [O.zx_eval(O.zx_trim(r), a) for r in g]
         assert O.res_univariate(Fa, Ga, O.ZZ) == O.zx_eval(want, a)
+
+
+def test_res_at_prs_matches_determinant():
+    f, g = W.small_dense_pair(7, 4, 8)
+    for a in (-9, 0, 5, 123456):
+        assert O.res_at_prs(f, g, a) == O.res_at(f, g, a)
+    fl = [[1, 2, -1], [0, 1], [-6, 1, 1]]       # lc vanishes at 2 and -3
+    gl = [[2, -1], [1, 0, 1], [-2, 1]]
+    for a in (-3, 2, 4):
+        assert O.res_at_prs(fl, gl, a) == O.res_at(fl, gl, a)
