@@ -284,3 +284,51 @@ def primes(k: int) -> list[int]:
         N.check(L.gbr_prime(i, C.byref(p)))
         out.append(p.value)
     return out
+
+
+def _job(kind: int, a, b, var: int, keep: _Packed) -> N.Job:
+    j = N.Job()
+    j.kind, j.var = kind, var
+    if kind == N.JOB_GCD:
+        d = pack_upolys([a, b], keep)
+        j.p = N.UPoly(int(d[0]["deg"]), int(d[0]["words"]), int(d[0]["coef"]))
+        j.q = N.UPoly(int(d[1]["deg"]), int(d[1]["words"]), int(d[1]["coef"]))
+    else:
+        polys = [a, b] if kind == N.JOB_RESULTANT else [a, a]
+        d = pack_bipolys(polys, keep)
+        j.f = N.BiPoly(int(d[0]["deg_x"]), int(d[0]["deg_y"]), int(d[0]["words"]), int(d[0]["coef"]))
+        j.g = N.BiPoly(int(d[1]["deg_x"]), int(d[1]["deg_y"]), int(d[1]["words"]), int(d[1]["coef"]))
+    return j
+
+
+def _submit(self, kind: int, a, b=None, var: int = 1) -> int:
+    """gbr_submit: queue a resultant (kind JOB_RESULTANT), res(f, f') (JOB_DISC) or gcd
+    (JOB_GCD) job; returns its ticket.  The job's data is copied by the library."""
+    keep = _Packed()
+    j = _job(kind, a, b, var, keep)
+    t = C.c_uint64()
+    N.check(N.lib().gbr_submit(self.handle, C.byref(j), C.byref(t)), self.handle)
+    return t.value
+
+
+def _poll(self, ticket: int, timeout_ms: int = -1):
+    """gbr_poll: the job's result as a list of ints, or None if not finished in time."""
+    out = N.BigPoly()
+    st = N.lib().gbr_poll(self.handle, C.c_uint64(ticket), C.byref(out), int(timeout_ms))
+    if st in (N.EAGAIN, N.ETIMEOUT):
+        return None
+    N.check(st, self.handle)
+    r = bigpoly_to_ints(out)
+    N.lib().gbr_free_result(self.handle, C.byref(out))
+    return r
+
+
+def _serve_stats(self) -> dict:
+    s = N.ServeStats()
+    N.check(N.lib().gbr_get_serve_stats(self.handle, C.byref(s)), self.handle)
+    return {k: getattr(s, k) for k, _ in N.ServeStats._fields_}
+
+
+Context.submit = _submit
+Context.poll = _poll
+Context.serve_stats = _serve_stats

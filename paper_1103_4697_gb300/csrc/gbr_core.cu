@@ -215,8 +215,8 @@ int gbr_ctx::fail(int code, const char *what, cudaError_t e) {
     return code;
 }
 
-void *gbr_ctx::dalloc(size_t bytes) { return arena.alloc(bytes); }
-void gbr_ctx::dfree(void *p) { arena.release(p); }
+void *gbr_ctx::dalloc(size_t bytes) { return mem().alloc(bytes); }
+void gbr_ctx::dfree(void *p) { mem().release(p); }
 
 void *gbr_ctx::pinned(size_t bytes, int slot) {
     if (h_pin_cap[slot] < bytes) {
@@ -350,6 +350,45 @@ extern "C" void gbr_destroy(gbr_ctx *c) {
         if (c->h_pin[i]) cudaFreeHost(c->h_pin[i]);
     if (c->own_ws && c->ws) cudaFree(c->ws);
     delete c;
+}
+
+gbr_ctx *gbr_make_worker(gbr_ctx *parent) {
+    gbr_ctx *w = new (std::nothrow) gbr_ctx();
+    if (!w) return nullptr;
+    w->parent = parent;
+    w->device = parent->device;
+    w->budget = parent->budget;
+    w->drop_unlucky = parent->drop_unlucky;
+    w->extra_primes = parent->extra_primes;
+    cudaSetDevice(w->device);
+    if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete w;
+        return nullptr;
+    }
+    w->own_stream = true;
+    const int NP = num_primes();
+    w->d_mods = (ModP *)w->dalloc(sizeof(ModP) * NP);
+    w->d_err = (int32_t *)w->dalloc(64);
+    if (!w->d_mods || !w->d_err || cudaMemcpy(w->d_mods, host_mods(), sizeof(ModP) * NP, cudaMemcpyHostToDevice) ||
+        cudaMemset(w->d_err, 0, 64)) {
+        gbr_destroy_worker(w);
+        return nullptr;
+    }
+    for (int i = 0; i < 8; ++i) cudaEventCreate(&w->ev[i]);
+    return w;
+}
+
+void gbr_destroy_worker(gbr_ctx *w) {
+    if (!w) return;
+    cudaSetDevice(w->device);
+    if (w->stream) cudaStreamSynchronize(w->stream);
+    for (void *p : {(void *)w->d_mods, (void *)w->d_err, (void *)w->d_garner, (void *)w->d_invk}) w->dfree(p);
+    for (int i = 0; i < 8; ++i)
+        if (w->ev[i]) cudaEventDestroy(w->ev[i]);
+    for (int i = 0; i < 4; ++i)
+        if (w->h_pin[i]) cudaFreeHost(w->h_pin[i]);
+    if (w->own_stream && w->stream) cudaStreamDestroy(w->stream);
+    delete w;
 }
 
 extern "C" int gbr_set_option(gbr_ctx *c, int opt, int64_t v) {

@@ -66,10 +66,13 @@ struct gbr_ctx {
     gbr_stats stats{};
     std::map<uint64_t, cudaGraphExec_t> graphs;
     gbr::ServeState *serve = nullptr;
+    gbr_ctx *parent = nullptr;     // serving workers share the parent's arena
+    bool own_stream = false;
 
     int fail(int code, const char *what, cudaError_t e = cudaSuccess);
     void *dalloc(size_t bytes);
     void dfree(void *p);
+    gbr::Arena &mem() { return parent ? parent->arena : arena; }
     void *pinned(size_t bytes, int slot);   // grow-only pinned staging buffer per slot
     int ensure_tables(int K, int T);
 };
@@ -100,3 +103,5 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r);
 int gbr_fetch_resident_locked(gbr_ctx *c, gbr_resident *r, int first, int count, gbr_bigpoly *out);
 void gbr_free_resident_locked(gbr_ctx *c, gbr_resident *r);
 void gbr_serve_shutdown(gbr_ctx *c);
+gbr_ctx *gbr_make_worker(gbr_ctx *parent);    // own stream and tables, parent's arena
+void gbr_destroy_worker(gbr_ctx *w);

@@ -1,0 +1,81 @@
+"""Serving (continuous batching): each result is the same alone and in the mix."""
+
+import random
+import time
+
+import pytest
+
+import oracle as O
+from paper_1103_4697_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1103_4697_gb300.api import Context
+
+    c = Context(device=0, mem_budget=4 << 30)
+    yield c
+    c.close()
+
+
+def test_mixed_stream_matches_alone_and_oracle(ctx):
+    from paper_1103_4697_gb300.native import JOB_DISC, JOB_GCD, JOB_RESULTANT
+
+    reqs = W.serving_stream(5, 240, rate=1e9, dlo=3, dhi=9, blo=8, bhi=64)
+    tickets = []
+    for k, r in enumerate(reqs):
+        if r.kind == "res":
+            kind = JOB_DISC if k % 7 == 0 else JOB_RESULTANT
+            tickets.append((ctx.submit(kind, r.a, r.b), kind, r))
+        else:
+            tickets.append((ctx.submit(JOB_GCD, r.a, r.b), JOB_GCD, r))
+        if k % 40 == 0:
+            time.sleep(0.002)          # let some batches start while others arrive
+    results = [ctx.poll(t, -1) for t, _, _ in tickets]
+    rng = random.Random(1)
+    for (t, kind, r), got in zip(tickets, results):
+        if kind == JOB_GCD:
+            assert got == list(O.gcd_z(r.a, r.b))
+        elif kind == JOB_DISC:
+            assert got == list(O.disc_res(r.a))
+        else:
+            if r.planted:
+                assert got == []
+            assert got == list(O.res_subres(r.a, r.b))
+    # the same jobs alone, one call each, give identical results
+    for (t, kind, r), got in rng.sample(list(zip(tickets, results)), 20):
+        if kind == JOB_GCD:
+            assert ctx.gcd(r.a, r.b) == got
+        elif kind == JOB_DISC:
+            assert ctx.discriminant_res(r.a) == got
+        else:
+            assert ctx.resultant(r.a, r.b) == got
+    st = ctx.serve_stats()
+    assert st["completed"] == st["submitted"] == len(reqs)
+    assert st["batches"] >= 1
+
+
+def test_poll_unknown_ticket(ctx):
+    from paper_1103_4697_gb300.native import GbrError, ENOTFOUND
+
+    with pytest.raises(GbrError) as e:
+        ctx.poll(10 ** 12, 0)
+    assert e.value.status == ENOTFOUND
+
+
+def test_admission_refuses_oversized_job():
+    """A job that can never fit the budget fails with ENOMEM; jobs that fit still run."""
+    from paper_1103_4697_gb300.api import Context
+    from paper_1103_4697_gb300.native import GbrError, ENOMEM, JOB_RESULTANT
+
+    with Context(device=0, mem_budget=4 << 20) as c:
+        f, g = W.small_dense_pair(8, 40, 64)     # needs several MiB of residues
+        big = c.submit(JOB_RESULTANT, f, g)
+        fs, gs = W.small_dense_pair(3, 4, 8)
+        small = c.submit(JOB_RESULTANT, fs, gs)
+        assert c.poll(small, -1) == list(O.res_subres(fs, gs))
+        with pytest.raises(GbrError) as e:
+            c.poll(big, -1)
+        assert e.value.status == ENOMEM

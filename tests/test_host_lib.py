@@ -1,0 +1,136 @@
+"""Host-side tests of libgbres (no GPU): the library loads, exports every entry
+point include/gbres.h declares, and its host-only planning (prime table, prime
+counts, degree and coefficient bounds) is right."""
+
+import ctypes as C
+import math
+import os
+import random
+import re
+
+import pytest
+
+import oracle as O
+from paper_1103_4697_gb300 import native as N
+from paper_1103_4697_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(N.LIB_PATH):
+        from paper_1103_4697_gb300.build import build
+        build()
+    return N.lib()
+
+
+def _header_functions():
+    text = open(os.path.join(ROOT, "include", "gbres.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gbr_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _header_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(N.SIGNATURES) == names
+    assert N.missing_symbols() == []
+
+
+def _is_prime(n):
+    if n < 2:
+        return False
+    for p in (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37):
+        if n % p == 0:
+            return n == p
+    d, s = n - 1, 0
+    while d % 2 == 0:
+        d //= 2
+        s += 1
+    for a in (2, 3, 5, 7, 11, 13, 17):
+        x = pow(a, d, n)
+        if x in (1, n - 1):
+            continue
+        for _ in range(s - 1):
+            x = x * x % n
+            if x == n - 1:
+                break
+        else:
+            return False
+    return True
+
+
+def test_prime_table(lib):
+    from paper_1103_4697_gb300.api import primes
+
+    assert lib.gbr_num_primes() == 2048
+    ps = primes(300)
+    assert ps[0] == 2 ** 31 - 1
+    assert all(a > b for a, b in zip(ps, ps[1:]))
+    assert all(_is_prime(p) for p in ps)
+    # consecutive: no prime is skipped between table entries
+    for a, b in zip(ps[:40], ps[1:41]):
+        assert not any(_is_prime(c) for c in range(b + 2, a, 2))
+    p = C.c_uint32()
+    assert lib.gbr_prime(2048, C.byref(p)) == N.EINVAL
+    assert lib.gbr_prime(-1, C.byref(p)) == N.EINVAL
+
+
+@pytest.mark.parametrize("bits", [0.0, 1.0, 30.0, 31.0, 61.9, 100.0, 860.0, 9500.0])
+def test_primes_for_bits(lib, bits):
+    from paper_1103_4697_gb300.api import primes
+
+    k = lib.gbr_primes_for_bits(bits)
+    ps = primes(k)
+    assert sum(math.log2(p) for p in ps) > bits
+    assert k == 1 or sum(math.log2(p) for p in ps[:-1]) <= bits + 1e-5
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_resultant_info_bounds(lib, seed):
+    """Degrees match the oracle's, the x-degree bound holds, and every coefficient of
+    the exact resultant is below 2^log2_bound (Hadamard)."""
+    from paper_1103_4697_gb300.api import resultant_info
+
+    rng = random.Random(seed)
+    d = rng.randint(1, 6)
+    f, g = W.small_dense_pair(900 + seed, d, rng.randint(2, 20))
+    info = resultant_info(f, g)
+    assert (info["m"], info["n"]) == (O.ydeg(f), O.ydeg(g))
+    R = O.res_subres(f, g)
+    assert len(R) - 1 <= info["deg_bound"]
+    assert info["deg_bound"] <= d * d
+    for c in R:
+        assert abs(c) == 0 or math.log2(abs(c)) <= info["log2_bound"] + 1e-9
+    prod = 1
+    from paper_1103_4697_gb300.api import primes
+    for p in primes(info["primes"]):
+        prod *= p
+    assert all(prod > 2 * abs(c) + 1 for c in R)
+    di = resultant_info(f, None, disc=True)
+    Rd = O.disc_res(f)
+    assert di["n"] == O.ydeg(f) - 1
+    assert len(Rd) - 1 <= di["deg_bound"]
+    assert all(abs(c) == 0 or math.log2(abs(c)) <= di["log2_bound"] + 1e-9 for c in Rd)
+
+
+def test_resultant_info_var0_and_zero(lib):
+    from paper_1103_4697_gb300.api import resultant_info
+
+    f = [[1, 2, 3], [4, 5, 0]]        # deg_y 1, deg_x 2
+    g = [[1, 1], [0, 2], [3, 0]]      # deg_y 2, deg_x 1
+    i1 = resultant_info(f, g, var=0)
+    assert (i1["m"], i1["n"]) == (2, 1)
+    z = resultant_info([[0, 0]], g)
+    assert z["m"] == -1
+
+
+def test_status_strings_and_bad_create(lib):
+    assert lib.gbr_strerror(N.OK) == b"ok"
+    assert lib.gbr_strerror(N.ENOMEM).startswith(b"out of memory")
+    h = C.c_void_p()
+    assert lib.gbr_create(C.byref(h), 0, 1000, None, None) == N.EINVAL   # budget below 1 MiB
+    assert lib.gbr_create(None, 0, 1 << 30, None, None) == N.EINVAL
