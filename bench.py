@@ -1,0 +1,423 @@
+#!/usr/bin/env python3
+"""Benchmark: bit-exact res_y(f, g) solves per second on the batched degree-20
+workload (4096 dense pairs of total degree 20, 16-bit signed coefficients,
+pair i drawn from seed 2000 + i), one device-resident batch per step; plus
+serving p50/p99 latency on a Poisson stream of mixed resultant/gcd requests.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank runs its own batch of
+4096 pairs (seeds offset by rank, weak scaling, no collective on the data
+path); the barrier and the max-over-ranks timing use torch.distributed.
+"""
+
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import random
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "bit-exact res_y(f,g) solves/sec (deg 20; batched 4096 pairs); serving p50/p99"
+PAIRS, DEG, BITS, BASE_SEED = 4096, 20, 16, 2000
+
+
+# --------------------------------------------------------------------------- distributed helpers
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def rank_seed_base(rank: int, pairs: int = PAIRS) -> int:
+    """Rank r solves pairs with seeds BASE_SEED + r * pairs + i (rank 0: the headline seeds)."""
+    return BASE_SEED + rank * pairs
+
+
+def reduce_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# --------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (every 200 ms)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- CPU oracle baseline
+
+
+def _oracle_pair(seed: int):
+    import oracle as O
+    from paper_1103_4697_gb300 import workloads as W
+
+    f, g = W.small_dense_pair(seed, DEG, BITS)
+    t = time.perf_counter()
+    r = O.res_evalz(f, g)
+    return time.perf_counter() - t, len(r)
+
+
+def oracle_baseline(pairs_per_core: int = 1, cores: int | None = None) -> dict:
+    """The oracle as it stands (exact evaluation/interpolation over Z, res_evalz) on a
+    bounded sample of the workload's pairs, one pair per process on every host core."""
+    cores = cores or os.cpu_count() or 1
+    n = max(1, cores * pairs_per_core)
+    seeds = [BASE_SEED + i for i in range(n)]
+    ctx = mp.get_context("spawn")
+    t = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_pair, seeds, chunksize=1)
+    wall = time.perf_counter() - t
+    return {"value": n / wall, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} of the {PAIRS} pairs (seeds {BASE_SEED}..{BASE_SEED + n - 1}), res_evalz, "
+                      f"{wall:.1f} s wall, mean {statistics.mean(r[0] for r in res):.1f} s per pair"}
+
+
+# --------------------------------------------------------------------------- serving
+
+
+def serving_run(ctx, n_burst: int = 1500, n_stream: int = 6000, load: float = 0.8, seed: int = 5) -> dict:
+    """Open-loop Poisson stream of mixed resultant/gcd requests (degree log-uniform
+    5..30, 8..64-bit coefficients, 10 % planted factors): capacity from a burst, then
+    a stream at `load` x capacity; latency = completion - scheduled arrival."""
+    from paper_1103_4697_gb300 import api
+    from paper_1103_4697_gb300 import native as N
+    from paper_1103_4697_gb300 import workloads as W
+
+    L = N.lib()
+
+    def prepare(reqs):
+        keep = api._Packed()
+        jobs = []
+        for r in reqs:
+            kind = N.JOB_RESULTANT if r.kind == "res" else N.JOB_GCD
+            jobs.append(api._job(kind, r.a, r.b, 1, keep))
+        return jobs, keep
+
+    def run(jobs, arrivals):
+        """A submitter thread releases each job at its arrival time; this thread sweeps
+        the outstanding tickets with non-blocking polls and stamps completions."""
+        n = len(jobs)
+        done = [0.0] * n
+        tickets = [None] * n
+        t0 = time.perf_counter() + 0.01
+
+        def submitter():
+            for i, j in enumerate(jobs):
+                delay = t0 + arrivals[i] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                t = C.c_uint64()
+                N.check(L.gbr_submit(ctx.handle, C.byref(j), C.byref(t)), ctx.handle)
+                tickets[i] = t.value
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        pending, nxt, left = [], 0, n
+        out = N.BigPoly()
+        while left:
+            while nxt < n and tickets[nxt] is not None:
+                pending.append(nxt)
+                nxt += 1
+            still = []
+            for i in pending:
+                st = L.gbr_poll(ctx.handle, C.c_uint64(tickets[i]), C.byref(out), 0)
+                if st == N.EAGAIN:
+                    still.append(i)
+                    continue
+                done[i] = time.perf_counter()
+                assert st == N.OK, f"serving request failed with status {st}"
+                L.gbr_free_result(ctx.handle, C.byref(out))
+                left -= 1
+            if len(still) == len(pending):
+                time.sleep(5e-5)
+            pending = still
+        th.join()
+        return t0, done
+
+    burst = W.serving_stream(seed, n_burst, rate=1e12)
+    jb, kb = prepare(burst)
+    t0, done = run(jb, [0.0] * len(jb))
+    capacity = len(jb) / (max(done) - t0)
+    rate = load * capacity
+    stream = W.serving_stream(seed + 1, n_stream, rate=rate)
+    js, ks = prepare(stream)
+    arrivals = [r.t_arrive for r in stream]
+    t0, done = run(js, arrivals)
+    lat = sorted((done[i] - (t0 + arrivals[i])) * 1e3 for i in range(len(js)))
+    span = max(done) - t0
+    return {"p50_ms": lat[len(lat) // 2], "p99_ms": lat[int(len(lat) * 0.99)], "throughput_rps": len(js) / span,
+            "offered_rps": rate, "capacity_rps": capacity, "requests": len(js),
+            "mix": "50/50 res_y/gcd, degree log-uniform 5..30, 8..64-bit, 10% planted",
+            "stats": ctx.serve_stats()}
+
+
+# --------------------------------------------------------------------------- our arm
+
+
+def traffic_for(kernel_src: str) -> float | None:
+    """Per-launch DRAM bytes of the evaluation kernel from the committed ncu summary,
+    if that summary was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "evalres_dram.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    return d.get("bytes_per_launch_full") if d.get("source_sha") == h else None
+
+
+def run_ours(args) -> None:
+    import torch
+
+    import oracle as O
+    from paper_1103_4697_gb300 import api
+    from paper_1103_4697_gb300 import native as N
+    from paper_1103_4697_gb300 import workloads as W
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = oracle_baseline()          # spawn pool: safe before or after CUDA init
+    ctx = api.Context(device=local, mem_budget=args.mem_gb << 30)
+    cal = ctx.calibrate()
+    NP = args.pairs
+    base = rank_seed_base(rank, NP)
+    F, G = W.deg20_batch_arrays(NP, base, DEG, BITS)
+    res = ctx.upload_pairs(F, G)
+    ctx.set_option(N.OPT_STATS, 1)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
+    for _ in range(args.warmup):
+        res.run()
+    # parity spot check (outside the timed region): two sampled pairs at two points
+    out = res.fetch(0, 8)
+    rng = random.Random(rank)
+    for q in rng.sample(range(8), 2):
+        a = rng.randint(-10 ** 6, 10 ** 6)
+        v = 0
+        for c in reversed(out[q]):
+            v = v * a + c
+        assert v == O.res_at_prs(F[q], G[q], a), "parity spot check failed"
+    clocks = ClockSampler(local)
+    evs = []
+    stage = {k: 0.0 for k in ("bounds_ms", "reduce_ms", "evalres_ms", "interp_ms", "crt_ms")}
+    kernels = 0
+    st = {}
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)                                  # evict L2 between steps (untimed)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        res.run()
+        e.record(stream)
+        evs.append((s, e))
+        st = ctx.stats()
+        for k in stage:
+            stage[k] += st[k]
+        kernels += st["kernels"]
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    barrier(world)
+    clk = clocks.stop()
+    dev_ms = sum(s.elapsed_time(e) for s, e in evs)
+    dev_ms = reduce_max(dev_ms, world)
+    value = world * NP * args.steps / (dev_ms * 1e-3)
+    evalres_ms = stage["evalres_ms"] / args.steps
+    modmul = st["modmul_evalres"]
+    achieved = modmul / (evalres_ms * 1e-3)
+    peak = cal["mulsub_per_s"] * 2          # the fused multiply-subtract does two multiplications
+    # e2e: the public C call with host buffers (H2D of inputs and D2H of results inside)
+    keep = api._Packed()
+    df, dg = api.pack_bipolys(F, keep), api.pack_bipolys(G, keep)
+    outs = (N.BigPoly * NP)()
+    L = N.lib()
+    e2e_steps = max(2, min(args.steps, 6))
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    h2d = d2h = 0
+    for _ in range(e2e_steps):
+        N.check(L.gbr_resultant_batch(ctx.handle, NP, api._ptr(df), api._ptr(dg), 1, outs), ctx.handle)
+        s2 = ctx.stats()
+        h2d, d2h = s2["h2d_bytes"], s2["d2h_bytes"]
+        t_free = time.perf_counter()
+        for i in range(NP):
+            L.gbr_free_result(ctx.handle, C.byref(outs[i]))
+        t += time.perf_counter() - t_free           # freeing the returned buffers is not timed
+    e2e_s = reduce_max(time.perf_counter() - t, world)
+    e2e = {"value": world * NP * e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "api": "gbr_resultant_batch (host buffers)"}
+    # the plain GPU path: one pair per call
+    one = None
+    serving = None
+    if rank == 0:
+        n1 = 64
+        t = time.perf_counter()
+        for q in range(n1):
+            o = N.BigPoly()
+            N.check(L.gbr_resultant(ctx.handle, C.cast(api._ptr(df[q:q + 1]), C.POINTER(N.BiPoly)),
+                                    C.cast(api._ptr(dg[q:q + 1]), C.POINTER(N.BiPoly)), 1, C.byref(o)), ctx.handle)
+            L.gbr_free_result(ctx.handle, C.byref(o))
+        one = {"value": n1 / (time.perf_counter() - t), "unit": "solves/s", "sample": f"{n1} pairs, one call each"}
+        if not args.no_serve:
+            serving = serving_run(ctx)
+    res.free()
+    ctx.close()
+    if rank != 0:
+        return
+    kernel_src = os.path.join(ROOT, "paper_1103_4697_gb300", "csrc", "gbr_res.cu")
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": f"{NP} dense pairs (f, g), total degree {DEG}, {BITS}-bit signed coefficients, "
+                               f"seeds {BASE_SEED}+i per pair (+{NP}*rank)", "pairs_per_gpu": NP,
+                   "degree": DEG, "coef_bits": BITS, "inputs": "device-resident", "l2": "flushed between steps "
+                   "(256 MiB write)", "parallelism": "replicas" if world > 1 else "single GPU"},
+        "clocks": clk, "e2e": e2e, "gpu_launches": kernels,
+        "roofline": {"bound": "alu", "kernel": "k_evalres", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                     "unit": "Tmodmul/s", "frac": achieved / peak, "traffic": traffic_for(kernel_src),
+                     "peak_source": "measured: gbr_calibrate fused multiply-subtract rate x 2 on this GPU",
+                     "algorithmic_modmul_per_launch": modmul},
+        "cpu_baseline": cpu,
+        "stages_ms": {k: v / args.steps for k, v in stage.items()},
+        "wall_ms_per_step": t_wall * 1e3 / args.steps,
+        "calibration": cal,
+        "one_pair_per_launch": one,
+        "serving": serving,
+        "parity": "2 sampled pairs x 1 random point vs oracle before timing; full parity in tests -m gpu",
+    }
+    print(json.dumps(line))
+
+
+# --------------------------------------------------------------------------- reference arm
+
+
+def run_reference(args) -> None:
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    per = []
+    t_all = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = oracle_baseline(1, cores)
+        per.append(last["value"])
+    wall = time.perf_counter() - t_all
+    value = statistics.mean(per)
+    line = {
+        "metric": METRIC, "impl": "reference", "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int (arbitrary precision)",
+        "data": "synthetic",
+        "config": {"workload": f"{PAIRS} dense pairs (f, g), total degree {DEG}, {BITS}-bit signed coefficients, "
+                               f"seeds {BASE_SEED}+i; each step a bounded sample of {cores} pairs",
+                   "pairs_per_gpu": PAIRS, "degree": DEG, "coef_bits": BITS},
+        "cpu_baseline": dict(last, value=value),
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mem-gb", type=int, default=24)
+    ap.add_argument("--pairs", type=int, default=PAIRS, help="pairs per GPU (smaller only for profiling)")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -100,13 +100,22 @@ typedef struct {
     int8_t *sign;
 } gbr_bigpoly;
 
-/* Per-stage device times of the last synchronous call, in milliseconds,
- * measured with CUDA events on the context's stream. */
+/* Counters of the last resultant run (gbr_run_resident or a one-shot/batch
+ * resultant call).  Stage times are milliseconds between CUDA events on the
+ * context's stream (recorded only with GBR_OPT_STATS = 1; bounds_ms includes
+ * the host planning that follows the bounds kernel).  Algorithmic modular
+ * multiplications, per (prime, point) subproblem of a pair with y-degrees m, n
+ * and T non-zero-capable x-coefficients (sum over rows of row degree + 1):
+ * evaluation T, elimination 2 m n; per (pair, prime) with P points:
+ * interpolation P (P - 1); per output coefficient with k primes: Garner
+ * k (k - 1) / 2.  Bytes are the host<->device copies of the call. */
 typedef struct {
     double bounds_ms, reduce_ms, evalres_ms, interp_ms, crt_ms, gcd_ms, total_ms;
-    int64_t kernels;       /* kernels launched by the last call */
-    int64_t subproblems;   /* (prime, point) subproblems solved by the last call */
-    int64_t modmul;        /* algorithmic modular multiplications of the last call (see DESIGN) */
+    int64_t kernels;          /* kernels launched */
+    int64_t subproblems;      /* (prime, point) subproblems solved */
+    int64_t modmul;           /* algorithmic modular multiplications, whole path */
+    int64_t modmul_evalres;   /* of the evaluation + elimination stage alone */
+    int64_t h2d_bytes, d2h_bytes;
 } gbr_stats;
 
 /* ------------------------------------------------------------------ context */
@@ -209,6 +218,22 @@ typedef struct {
     int64_t submitted, completed, batches, max_batch, peak_bytes, waits_for_memory;
 } gbr_serve_stats;
 int gbr_get_serve_stats(gbr_ctx *ctx, gbr_serve_stats *out);
+
+/* ------------------------------------------------------------------ calibration */
+
+/* Measured arithmetic ceilings of this GPU for the library's own Montgomery
+ * arithmetic (integer pipes), used as the roofline denominators of the
+ * elimination and interpolation stages: independent chains of mp_mul and of
+ * the fused multiply-subtract, timed with CUDA events on the context's stream
+ * over about 50 ms each.  Results in operations per second; sm_clock_mhz is
+ * the clock the driver reported for the device (cudaDevAttrClockRate). */
+typedef struct {
+    double modmul_per_s;
+    double mulsub_per_s;
+    double sm_clock_mhz;
+    int32_t sms;
+} gbr_calib;
+int gbr_calibrate(gbr_ctx *ctx, gbr_calib *out);
 
 /* ------------------------------------------------------------------ host-side information */
 

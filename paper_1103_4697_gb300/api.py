@@ -200,6 +200,12 @@ class Context:
     def set_option(self, opt: int, value: int):
         N.check(N.lib().gbr_set_option(self.handle, opt, int(value)), self.handle)
 
+    def calibrate(self) -> dict:
+        """Measured Montgomery multiply and fused multiply-subtract rates of this GPU."""
+        cal = N.Calib()
+        N.check(N.lib().gbr_calibrate(self.handle, C.byref(cal)), self.handle)
+        return {k: getattr(cal, k) for k, _ in N.Calib._fields_}
+
     def stats(self) -> dict:
         s = N.Stats()
         N.check(N.lib().gbr_get_stats(self.handle, C.byref(s)), self.handle)

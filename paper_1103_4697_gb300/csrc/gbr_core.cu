@@ -507,6 +507,7 @@ extern "C" int gbr_upload_pairs(gbr_ctx *c, int n, const gbr_bipoly *f, const gb
     }
     r->coef_words = words;
     r->rowdeg_n = rowdeg;
+    r->upload_bytes = words * 8 + (int64_t)sizeof(PairDesc) * n;
     size_t bytes = (size_t)words * 8;
     r->d_coef = (uint64_t *)c->dalloc(bytes ? bytes : 8);
     r->d_desc = (PairDesc *)c->dalloc(sizeof(PairDesc) * (n ? n : 1));
@@ -692,6 +693,9 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
         interp.add(q, k);
         crt.add(q, p.P);
         subproblems += (int64_t)k * p.P;
+        int64_t ev = (int64_t)k * p.P * (b.tf + b.tg + 2LL * p.m * p.n);
+        st.modmul_evalres += ev;
+        st.modmul += ev + (int64_t)k * p.P * (p.P - 1) + (int64_t)p.P * k * (k - 1) / 2;
     }
     int rc = c->ensure_tables(Kmax, Pmax);
     if (rc) return rc;
@@ -771,6 +775,8 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
     r->ran = true;
     st.kernels = kernels;
     st.subproblems = subproblems;
+    st.h2d_bytes = (int64_t)blk.size();
+    st.d2h_bytes = (int64_t)sizeof(PairBound) * n + 4;
     if (c->stats_on) {
         float ms;
         cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]); st.bounds_ms = ms;
@@ -816,6 +822,7 @@ int gbr_fetch_resident_locked(gbr_ctx *c, gbr_resident *r, int first, int count,
     if (e == cudaSuccess && s1 > s0) e = cudaMemcpyAsync(hs, r->d_sign + s0, (size_t)(s1 - s0), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "result readback", e);
+    c->stats.d2h_bytes += (o1 - o0) * 4 + (int64_t)count * 4 + (s1 - s0);
     for (int i = 0; i < count; ++i) {
         const PairPlan &p = plan[first + i];
         gbr_bigpoly &b = out[i];
@@ -877,6 +884,7 @@ static int res_batch_impl(gbr_ctx *c, int n, const gbr_bipoly *f, const gbr_bipo
         cudaSetDevice(c->device);
         try {
             st = gbr_run_resident_locked(c, r);
+            c->stats.h2d_bytes += r->upload_bytes;
             if (!st) st = gbr_fetch_resident_locked(c, r, 0, n, out);
         } catch (std::bad_alloc &) {
             st = c->fail(GBR_ENOMEM, "host allocation");

@@ -79,7 +79,7 @@ struct gbr_ctx {
 
 struct gbr_resident {
     int n = 0, var = 1, disc = 0;
-    int64_t coef_words = 0, rowdeg_n = 0;
+    int64_t coef_words = 0, rowdeg_n = 0, upload_bytes = 0;
     uint64_t *d_coef = nullptr;
     gbr::PairDesc *d_desc = nullptr;
     int32_t *d_rowdeg = nullptr;

@@ -48,6 +48,7 @@ struct PairBound {
     int32_t m, n;       // actual degrees in the eliminated variable (-1: zero polynomial)
     int32_t dxf, dxg;   // actual degrees in the other variable
     int32_t tdf, tdg;   // total degrees
+    int32_t tf, tg;     // Horner terms: sum over rows <= degree of (row degree + 1)
     double log2B;       // upper bound on log2 of the Hadamard bound
 };
 

@@ -94,10 +94,10 @@ __global__ void k_bounds(ResLaunch L) {
     for (int which = 0; which < 2; ++which) {
         if (which == 1 && D.disc) break;
         const PolyDesc &P = which ? D.g : D.f;
-        int mdeg = -1, dxmax = -1, td = -1;
+        int mdeg = -1, dxmax = -1, td = -1, terms = 0, terms_upto = 0;
         Lse sq;     // log2 sum_r ||row_r||_1^2
         sq.init();
-        int mdeg_g = -1, dx_g = -1, td_g = -1;
+        int mdeg_g = -1, dx_g = -1, td_g = -1, terms_g = 0, terms_g_upto = 0;
         Lse sq_g;
         sq_g.init();
         for (int r = 0; r <= P.rows; ++r) {
@@ -115,16 +115,20 @@ __global__ void k_bounds(ResLaunch L) {
             warp_lse(nrm);
             double ln = nrm.log2v();
             if (lane == 0) L.rowdeg[P.rowdeg_off + r] = cmax;
+            terms += cmax + 1;
             if (cmax >= 0) {
                 mdeg = r;
+                terms_upto = terms;
                 dxmax = max(dxmax, cmax);
                 td = max(td, r + cmax);
                 sq.add(2.0 * ln);
             }
             if (which == 0 && D.disc && r >= 1) {
                 if (lane == 0) L.rowdeg[D.g.rowdeg_off + r - 1] = cmax;
+                terms_g += cmax + 1;
                 if (cmax >= 0) {
                     mdeg_g = r - 1;
+                    terms_g_upto = terms_g;
                     dx_g = max(dx_g, cmax);
                     td_g = max(td_g, r - 1 + cmax);
                     sq_g.add(2.0 * (ln + log2((double)r)));
@@ -132,17 +136,17 @@ __global__ void k_bounds(ResLaunch L) {
             }
         }
         if (which == 0) {
-            B.m = mdeg; B.dxf = dxmax; B.tdf = td;
+            B.m = mdeg; B.dxf = dxmax; B.tdf = td; B.tf = terms_upto;
             B.log2B = sq.log2v();           // temporarily: log2 sum ||f_i||^2
             if (D.disc) {
-                B.n = mdeg_g; B.dxg = dx_g; B.tdg = td_g;
+                B.n = mdeg_g; B.dxg = dx_g; B.tdg = td_g; B.tg = terms_g_upto;
                 // log2B = (n/2) log2 sum f + (m/2) log2 sum g
                 double lf = sq.log2v(), lg = sq_g.log2v();
                 if (B.m >= 0 && B.n >= 0) B.log2B = 0.5 * B.n * lf + 0.5 * B.m * lg;
                 else B.log2B = 0.0;
             }
         } else {
-            B.n = mdeg; B.dxg = dxmax; B.tdg = td;
+            B.n = mdeg; B.dxg = dxmax; B.tdg = td; B.tg = terms_upto;
             double lf = B.log2B, lg = sq.log2v();
             if (B.m >= 0 && B.n >= 0) B.log2B = 0.5 * B.n * lf + 0.5 * B.m * lg;
             else B.log2B = 0.0;

@@ -33,7 +33,13 @@ class Stats(C.Structure):
     _fields_ = [("bounds_ms", C.c_double), ("reduce_ms", C.c_double), ("evalres_ms", C.c_double),
                 ("interp_ms", C.c_double), ("crt_ms", C.c_double), ("gcd_ms", C.c_double),
                 ("total_ms", C.c_double), ("kernels", C.c_int64), ("subproblems", C.c_int64),
-                ("modmul", C.c_int64)]
+                ("modmul", C.c_int64), ("modmul_evalres", C.c_int64), ("h2d_bytes", C.c_int64),
+                ("d2h_bytes", C.c_int64)]
+
+
+class Calib(C.Structure):
+    _fields_ = [("modmul_per_s", C.c_double), ("mulsub_per_s", C.c_double), ("sm_clock_mhz", C.c_double),
+                ("sms", C.c_int32)]
 
 
 class ResInfo(C.Structure):
@@ -74,6 +80,7 @@ SIGNATURES = {
     "gbr_submit": (C.c_int, [C.c_void_p, C.POINTER(Job), C.POINTER(C.c_uint64)]),
     "gbr_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(BigPoly), C.c_int]),
     "gbr_get_serve_stats": (C.c_int, [C.c_void_p, C.POINTER(ServeStats)]),
+    "gbr_calibrate": (C.c_int, [C.c_void_p, C.POINTER(Calib)]),
     "gbr_num_primes": (C.c_int, []),
     "gbr_prime": (C.c_int, [C.c_int, C.POINTER(C.c_uint32)]),
     "gbr_primes_for_bits": (C.c_int, [C.c_double]),

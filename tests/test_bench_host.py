@@ -1,0 +1,71 @@
+"""Host-side pieces of bench.py and the input generators (no GPU)."""
+
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as tmp
+
+import bench
+from paper_1103_4697_gb300 import workloads as W
+
+
+def test_batch_arrays_match_generator():
+    F, G = W.deg20_batch_arrays(3, 2000)
+    ps = W.deg20_batch(3, 2000)
+    for q in range(3):
+        f = np.zeros((21, 21), dtype=np.int64)
+        g = np.zeros((21, 21), dtype=np.int64)
+        for j, r in enumerate(ps.f[q]):
+            f[j, :len(r)] = r
+        for j, r in enumerate(ps.g[q]):
+            g[j, :len(r)] = r
+        assert (F[q] == f).all() and (G[q] == g).all()
+    fs, gs = W.deg20_pair(2000)
+    assert (F[0] == np.array(fs)).all()
+
+
+def test_generator_is_deterministic_and_in_range():
+    a = W.Stream(5).signed_bits(16, 1000)
+    b = W.Stream(5).signed_bits(16, 1000)
+    assert a == b
+    assert min(a) >= -2 ** 15 and max(a) <= 2 ** 15 - 1
+    assert W.Stream(6).signed_bits(16, 10) != a[:10]
+    u = W.Stream(1).uniform_int(4, 16, 5000)
+    assert min(u) == 4 and max(u) == 16
+
+
+def test_rank_seeds_disjoint():
+    seeds = [set(range(bench.rank_seed_base(r, 4096), bench.rank_seed_base(r, 4096) + 4096)) for r in range(4)]
+    assert bench.rank_seed_base(0) == 2000
+    for i in range(4):
+        for j in range(i + 1, 4):
+            assert not seeds[i] & seeds[j]
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, out):
+    import torch.distributed as dist
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    bench.barrier(world)
+    m = bench.reduce_max(10.0 + rank, world)
+    out[rank] = m
+    dist.destroy_process_group()
+
+
+def test_reduce_max_gloo_two_ranks():
+    mgr = tmp.get_context("spawn").Manager()
+    out = mgr.dict()
+    port = _free_port()
+    tmp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
+    assert out[0] == out[1] == 11.0
