@@ -327,6 +327,8 @@ extern "C" int gbr_create(gbr_ctx **out, int device, size_t budget, void *worksp
     }
     e = cudaMemcpy(c->d_mods, host_mods(), sizeof(ModP) * NP, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, 64);
+    if (e == cudaSuccess) e = configure_res_kernels();
+    if (e == cudaSuccess) e = configure_gcd_kernels();
     if (e != cudaSuccess) {
         gbr_destroy(c);
         return GBR_EDEVICE;

@@ -427,6 +427,12 @@ __global__ void k_gcd_check(GcdLaunch L, const int32_t *jobs, int njobs) {
     }
 }
 
+cudaError_t configure_gcd_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(k_gcd_modp, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gcd_crt, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    return e;
+}
+
 }  // namespace gbr
 
 using namespace gbr;
@@ -639,8 +645,7 @@ static int gcd_batch_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upo
         size_t per_warp = (size_t)2 * maxreg * 4;
         int nw = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per_warp));
         size_t smem = per_warp * nw;
-        if (smem > 200 * 1024) return c->fail(GBR_ELIMIT, "gcd degree too large for shared memory");
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gcd_modp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (smem > (size_t)kMaxDynSmem) return c->fail(GBR_ELIMIT, "gcd degree too large for shared memory");
         if (e == cudaSuccess) {
             int grid = grid_for((const void *)k_gcd_modp, nw * 32, smem, (total + nw - 1) / nw);
             k_gcd_modp<<<grid, nw * 32, smem, s>>>(L, d_wls, d_wlj, (int)wl_jobs.size(), total, maxreg);
@@ -739,7 +744,7 @@ static int gcd_batch_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upo
                 int block = 128;
                 while (block > 32 && (size_t)maxL * block * 4 > 160 * 1024) block >>= 1;
                 size_t sm2 = (size_t)maxL * block * 4;
-                e = cudaFuncSetAttribute(k_gcd_crt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+                if (sm2 > (size_t)kMaxDynSmem) e = cudaErrorInvalidValue;
                 if (e == cudaSuccess) {
                     int grid = grid_for((const void *)k_gcd_crt, block, sm2, (ctotal + block - 1) / block);
                     k_gcd_crt<<<grid, block, sm2, s>>>(L, d_cs, d_cj, (int)cj.size(), ctotal, maxL);

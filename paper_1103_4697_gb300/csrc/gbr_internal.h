@@ -109,6 +109,11 @@ struct WorkList {
     int64_t total;
 };
 
+// dynamic shared memory ceiling set once for every kernel (bytes)
+constexpr int kMaxDynSmem = 200 * 1024;
+cudaError_t configure_res_kernels();
+cudaError_t configure_gcd_kernels();
+
 cudaError_t launch_bounds(const ResLaunch &L, cudaStream_t s);
 cudaError_t launch_reduce(const ResLaunch &L, const WorkList &w, cudaStream_t s);
 cudaError_t launch_evalres(const ResLaunch &L, const WorkList &w, int slots_f, int slots_g, int block,

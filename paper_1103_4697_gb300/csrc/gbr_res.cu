@@ -442,6 +442,16 @@ __global__ void k_crt(ResLaunch L, WorkList w, int LM) {
 
 // ------------------------------------------------------------------ launchers
 
+// The dynamic shared-memory ceiling of every kernel is raised once, to the same
+// value, when a context is created: changing it per launch would race between
+// host threads that launch concurrently (serving workers).
+cudaError_t configure_res_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(k_evalres, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_interp, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_crt, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    return e;
+}
+
 static int sm_count() {
     static int n = 0;
     if (!n) {
@@ -473,8 +483,7 @@ cudaError_t launch_reduce(const ResLaunch &L, const WorkList &w, cudaStream_t s)
 cudaError_t launch_evalres(const ResLaunch &L, const WorkList &w, int SF, int SG, int block, cudaStream_t s) {
     if (w.total <= 0) return cudaSuccess;
     size_t smem = (size_t)(SF + SG) * block * sizeof(uint32_t);
-    cudaError_t e = cudaFuncSetAttribute(k_evalres, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    if (smem > kMaxDynSmem) return cudaErrorInvalidValue;
     int grid = persistent_grid(k_evalres, block, smem, (w.total + block - 1) / block);
     k_evalres<<<grid, block, smem, s>>>(L, w, SF, SG);
     return cudaGetLastError();
@@ -487,8 +496,7 @@ cudaError_t launch_interp(const ResLaunch &L, const WorkList &w, int maxP, cudaS
     if (nw > 8) nw = 8;
     if (nw < 1) nw = 1;
     size_t smem = per_warp * nw;
-    cudaError_t e = cudaFuncSetAttribute(k_interp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    if (smem > kMaxDynSmem) return cudaErrorInvalidValue;
     int grid = persistent_grid(k_interp, nw * 32, smem, (w.total + nw - 1) / nw);
     k_interp<<<grid, nw * 32, smem, s>>>(L, w, maxP);
     return cudaGetLastError();
@@ -499,8 +507,7 @@ cudaError_t launch_crt(const ResLaunch &L, const WorkList &w, int maxL, cudaStre
     int block = 128;
     while (block > 32 && (size_t)maxL * block * 4 > 160 * 1024) block >>= 1;
     size_t smem = (size_t)maxL * block * sizeof(uint32_t);
-    cudaError_t e = cudaFuncSetAttribute(k_crt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    if (smem > kMaxDynSmem) return cudaErrorInvalidValue;
     int grid = persistent_grid(k_crt, block, smem, (w.total + block - 1) / block);
     k_crt<<<grid, block, smem, s>>>(L, w, maxL);
     return cudaGetLastError();

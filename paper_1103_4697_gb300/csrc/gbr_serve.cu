@@ -72,6 +72,17 @@ static void finish(ServeState *S, const std::shared_ptr<ServeJob> &j, int status
     S->stats.completed++;
 }
 
+// a failing job's detail text goes to the parent context, where gbr_last_error finds it
+static void parent_error(gbr_ctx *w, int st) {
+    if (!w->parent) return;
+    std::string msg;
+    {
+        std::lock_guard<std::mutex> g(w->err_mu);
+        msg = w->err;
+    }
+    w->parent->fail(st, ("serving job: " + msg).c_str());
+}
+
 static void run_group(gbr_ctx *w, ServeState *S, std::vector<std::shared_ptr<ServeJob>> &grp) {
     if (grp.empty()) return;
     const int n = (int)grp.size();
@@ -104,6 +115,7 @@ static void run_group(gbr_ctx *w, ServeState *S, std::vector<std::shared_ptr<Ser
         }
         return;
     } else {
+        parent_error(w, st);
         finish(S, grp[0], st, nullptr);
     }
     S->cv_done.notify_all();

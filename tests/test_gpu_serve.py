@@ -79,3 +79,27 @@ def test_admission_refuses_oversized_job():
         with pytest.raises(GbrError) as e:
             c.poll(big, -1)
         assert e.value.status == ENOMEM
+
+
+def test_full_mix_burst_sampled(ctx):
+    """Full request mix (degree 5..30, 8..64-bit): a burst of 1200 requests overlaps on
+    the workers' streams; sampled results are checked exactly (gcd) and at random
+    integer points (resultants)."""
+    from paper_1103_4697_gb300.native import JOB_GCD, JOB_RESULTANT
+
+    reqs = W.serving_stream(55, 1200, rate=1e12)
+    tickets = [ctx.submit(JOB_RESULTANT if r.kind == "res" else JOB_GCD, r.a, r.b) for r in reqs]
+    out = [ctx.poll(t, -1) for t in tickets]
+    rng = random.Random(2)
+    for i in rng.sample(range(len(reqs)), 60):
+        r, got = reqs[i], out[i]
+        if r.kind == "gcd":
+            assert got == list(O.gcd_z(r.a, r.b))
+        else:
+            a = rng.randint(-10 ** 4, 10 ** 4)
+            v = 0
+            for c in reversed(got):
+                v = v * a + c
+            assert v == O.res_at_prs(r.a, r.b, a)
+            if r.planted:
+                assert got == []
