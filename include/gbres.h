@@ -235,6 +235,45 @@ typedef struct {
 } gbr_calib;
 int gbr_calibrate(gbr_ctx *ctx, gbr_calib *out);
 
+/* ------------------------------------------------------------------ allocation-free reconstruction */
+
+/* gbr_crt_noalloc has no counterpart in the paper; it is here for callers that
+ * must not allocate device memory when they ask for a result - for example a
+ * host that reserves all of its GPU memory up front and forbids allocation
+ * afterwards, code running inside another framework's memory pool or
+ * allocator callback, or a latency-critical loop that cannot afford the
+ * device-wide synchronisation cudaMalloc/cudaFree may cause.  It takes no
+ * context, calls no cudaMalloc, cudaFree or other allocating routine, and
+ * uses only the buffers the caller passes plus a fixed array that the library
+ * declares in device memory (4 MiB, held on every GPU that loads the library
+ * until the process exits).
+ *
+ * What it computes: the signed integers X_c, |X_c| < M/2 with
+ * M = p_0 p_1 ... p_{k-1} the first k primes of the table (gbr_prime), whose
+ * residues X_c mod p_i are residues[i*stride + c] (normal form, in [0, p_i)),
+ * for c = 0..ncoef-1 - the Chinese-remaindering step of the resultant
+ * (Garner's mixed-radix digits, symmetric lift).  Output: magnitudes in
+ * mag[c*limbs + l] (32-bit limbs, least significant first) and signs in
+ * sign[c] in {-1, 0, +1}, the layout of gbr_bigpoly.  All four pointers are
+ * device memory owned by the caller.
+ *
+ * Limits: 1 <= k <= GBR_NOALLOC_MAX_PRIMES, ncoef * k <= 1048576 (the fixed
+ * array holds one digit per coefficient and prime); beyond them the call
+ * returns GBR_ELIMIT without launching anything.  limbs must be at least
+ * ceil(31 k / 32) (GBR_EINVAL otherwise); stride >= ncoef.
+ *
+ * Behaviour: asynchronous on `stream` (NULL: the legacy default stream);
+ * results are ready when the stream reaches that point.  The first call on a
+ * device, with that device current, looks up the device address of the fixed
+ * array (cudaGetSymbolAddress); make that first call before any stream
+ * capture begins.  Every call uses the same fixed array and leaves its last
+ * contents there; calls whose kernels overlap on the GPU (other streams, other
+ * host threads) overwrite each other's digits and give wrong results, so
+ * serialise them.  Returns GBR_EDEVICE if the lookup or the launch fails. */
+#define GBR_NOALLOC_MAX_PRIMES 64
+int gbr_crt_noalloc(const uint32_t *residues, int k, int ncoef, int64_t stride, uint32_t *mag, int limbs,
+                    int8_t *sign, void *stream);
+
 /* ------------------------------------------------------------------ host-side information */
 
 /* The fixed table of primes used by every context: p_0 > p_1 > ... are the

@@ -81,6 +81,8 @@ SIGNATURES = {
     "gbr_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(BigPoly), C.c_int]),
     "gbr_get_serve_stats": (C.c_int, [C.c_void_p, C.POINTER(ServeStats)]),
     "gbr_calibrate": (C.c_int, [C.c_void_p, C.POINTER(Calib)]),
+    "gbr_crt_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_int, C.c_void_p,
+                                  C.c_void_p]),
     "gbr_num_primes": (C.c_int, []),
     "gbr_prime": (C.c_int, [C.c_int, C.POINTER(C.c_uint32)]),
     "gbr_primes_for_bits": (C.c_int, [C.c_double]),
