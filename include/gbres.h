@@ -148,6 +148,9 @@ const char *gbr_last_error(gbr_ctx *ctx);
 #define GBR_OPT_GRAPH        3   /* 1 (default): replay the device stages of a resident batch from
                                     a captured CUDA graph when its plan repeats */
 #define GBR_OPT_EXTRA_PRIMES 4   /* add this many primes beyond the bound (tests: k+1 == k) */
+#define GBR_OPT_INTERP_GEMM  5   /* 1 (default): pairs of a batch that share their number of points
+                                    are interpolated by one inverse-Vandermonde contraction per
+                                    prime; 0: Newton interpolation for every (pair, prime) */
 int gbr_set_option(gbr_ctx *ctx, int option, int64_t value);
 int gbr_get_stats(gbr_ctx *ctx, gbr_stats *out);
 

@@ -266,6 +266,48 @@ int gbr_ctx::ensure_tables(int K, int T) {
     return GBR_OK;
 }
 
+// Inverse Vandermonde matrices are cached per point count P for the first K
+// primes; the cache is bounded (least recently used entries are dropped).
+static const size_t kVinvCacheBytes = (size_t)1 << 30;
+
+const uint32_t *gbr_ctx::get_vinv(int P, int K) {
+    auto it = vinv.find(P);
+    if (it != vinv.end() && it->second.K >= K) {
+        it->second.last_use = ++vinv_clock;
+        return it->second.d;
+    }
+    size_t bytes = (size_t)P * P * K * 4;
+    if (bytes > kVinvCacheBytes / 2) return nullptr;
+    auto total = [&]() {
+        size_t t = 0;
+        for (auto &kv : vinv) t += (size_t)kv.first * kv.first * kv.second.K * 4;
+        return t;
+    };
+    if (it != vinv.end()) {
+        dfree(it->second.d);
+        vinv.erase(it);
+    }
+    while (!vinv.empty() && total() + bytes > kVinvCacheBytes) {
+        auto lru = vinv.begin();
+        for (auto jt = vinv.begin(); jt != vinv.end(); ++jt)
+            if (jt->second.last_use < lru->second.last_use) lru = jt;
+        dfree(lru->second.d);
+        vinv.erase(lru);
+    }
+    uint32_t *d = (uint32_t *)dalloc(bytes);
+    if (!d) return nullptr;
+    if (launch_vinv(d_mods, P, K, d, stream) != cudaSuccess) {
+        dfree(d);
+        return nullptr;
+    }
+    Vinv v;
+    v.d = d;
+    v.K = K;
+    v.last_use = ++vinv_clock;
+    vinv[P] = v;
+    return d;
+}
+
 // ------------------------------------------------------------------ status strings
 
 extern "C" const char *gbr_strerror(int s) {
@@ -346,6 +388,7 @@ extern "C" void gbr_destroy(gbr_ctx *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto &kv : c->vinv) c->dfree(kv.second.d);
     for (int i = 0; i < 8; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     for (int i = 0; i < 4; ++i)
@@ -399,6 +442,7 @@ extern "C" int gbr_set_option(gbr_ctx *c, int opt, int64_t v) {
         case GBR_OPT_DROP_UNLUCKY: c->drop_unlucky = (int)(v != 0); return GBR_OK;
         case GBR_OPT_STATS: c->stats_on = (int)(v != 0); return GBR_OK;
         case GBR_OPT_GRAPH: c->graph_on = (int)(v != 0); return GBR_OK;
+        case GBR_OPT_INTERP_GEMM: c->gemm_on = (int)(v != 0); return GBR_OK;
         case GBR_OPT_EXTRA_PRIMES:
             if (v < 0 || v > 64) return GBR_EINVAL;
             c->extra_primes = (int)v;
@@ -553,7 +597,8 @@ extern "C" int gbr_upload_pairs(gbr_ctx *c, int n, const gbr_bipoly *f, const gb
 void gbr_free_resident_locked(gbr_ctx *c, gbr_resident *r) {
     if (!r) return;
     for (void *p : {(void *)r->d_coef, (void *)r->d_desc, (void *)r->d_rowdeg, (void *)r->d_bounds, (void *)r->d_deg,
-                    (void *)r->d_planblk, (void *)r->d_res, (void *)r->d_val, (void *)r->d_out, (void *)r->d_sign})
+                    (void *)r->d_planblk, (void *)r->d_res, (void *)r->d_val, (void *)r->d_cf, (void *)r->d_out,
+                    (void *)r->d_sign})
         c->dfree(p);
     if (r->gexec) cudaGraphExecDestroy(r->gexec);
     delete r;
@@ -644,6 +689,7 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
     int Kmax = 1, Pmax = 1, Lmax = 1;
     HostList red, interp, crt;
     std::map<int, HostList> evb;
+    std::map<int, std::vector<int32_t>> pgroups;   // pairs by point count
     int64_t subproblems = 0;
     for (int q = 0; q < n; ++q) {
         const PairBound &b = hb[q];
@@ -692,7 +738,7 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
         red.add(q, p.S);
         int key = ((std::max(p.m, p.n) + 1) + 3) / 4 * 4;
         evb[key].add(q, (int64_t)k * p.P);
-        interp.add(q, k);
+        pgroups[p.P].push_back(q);
         crt.add(q, p.P);
         subproblems += (int64_t)k * p.P;
         int64_t ev = (int64_t)k * p.P * (b.tf + b.tg + 2LL * p.m * p.n);
@@ -701,6 +747,30 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
     }
     int rc = c->ensure_tables(Kmax, Pmax);
     if (rc) return rc;
+    // interpolation: groups of pairs sharing P use the inverse-Vandermonde
+    // contraction; the rest (and groups whose matrices do not fit the cache)
+    // use Newton interpolation, one warp per (pair, prime)
+    struct Gemm {
+        int P, K;
+        const uint32_t *vinv;
+        size_t off;
+        int n;
+    };
+    std::vector<Gemm> gemms;
+    std::vector<int32_t> gemm_pairs;
+    for (auto &kv : pgroups) {
+        const std::vector<int32_t> &qs = kv.second;
+        int K = 0;
+        for (int q : qs) K = std::max(K, plan[q].k);
+        const uint32_t *vi = nullptr;
+        if ((int)qs.size() >= kGemmMinPairs && c->gemm_on) vi = c->get_vinv(kv.first, K);
+        if (vi) {
+            gemms.push_back({kv.first, K, vi, gemm_pairs.size(), (int)qs.size()});
+            gemm_pairs.insert(gemm_pairs.end(), qs.begin(), qs.end());
+        } else {
+            for (int q : qs) interp.add(q, plan[q].k);
+        }
+    }
     // ---- plan block: plans + work lists, one upload
     std::vector<char> blk(sizeof(PairPlan) * n);
     std::memcpy(blk.data(), plan.data(), sizeof(PairPlan) * n);
@@ -714,9 +784,13 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
         put_list(blk, kv.second, a, b2);
         o_ev.push_back({a, b2});
     }
+    size_t o_gemm = (blk.size() + 7) / 8 * 8;
+    blk.resize(o_gemm + gemm_pairs.size() * 4 + 4);
+    if (!gemm_pairs.empty()) std::memcpy(blk.data() + o_gemm, gemm_pairs.data(), gemm_pairs.size() * 4);
     if (ensure_buf(c, (void **)&r->d_planblk, &r->planblk_cap, blk.size()) ||
         ensure_buf(c, (void **)&r->d_res, &r->res_cap, res_w * 4) ||
         ensure_buf(c, (void **)&r->d_val, &r->val_cap, val_w * 4) ||
+        ensure_buf(c, (void **)&r->d_cf, &r->cf_cap, val_w * 4) ||
         ensure_buf(c, (void **)&r->d_out, &r->out_cap, out_w * 4) ||
         ensure_buf(c, (void **)&r->d_sign, &r->sign_cap, sign_b))
         return c->fail(GBR_ENOMEM, "device budget too small for this batch");
@@ -742,6 +816,7 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
     L.invk_T = c->invk_T;
     L.res = r->d_res;
     L.val = r->d_val;
+    L.cf = r->d_cf;
     L.out = r->d_out;
     L.sign = r->d_sign;
     L.drop_unlucky = c->drop_unlucky;
@@ -760,8 +835,15 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
         ++bi;
     }
     if (c->stats_on) cudaEventRecord(c->ev[3], s);
-    if (e == cudaSuccess) e = launch_interp(L, mk(o_int_p, o_int_s, interp), Pmax, s);
-    kernels++;
+    if (e == cudaSuccess && interp.total > 0) {
+        e = launch_interp(L, mk(o_int_p, o_int_s, interp), Pmax, s);
+        kernels++;
+    }
+    for (const Gemm &gm : gemms) {
+        if (e != cudaSuccess) break;
+        e = launch_interp_gemm(L, (const int32_t *)(r->d_planblk + o_gemm) + gm.off, gm.n, gm.P, gm.K, gm.vinv, s);
+        kernels++;
+    }
     if (c->stats_on) cudaEventRecord(c->ev[4], s);
     if (e == cudaSuccess) e = launch_crt(L, mk(o_crt_p, o_crt_s, crt), Lmax, s);
     kernels++;

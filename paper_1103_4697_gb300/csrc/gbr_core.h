@@ -62,9 +62,17 @@ struct gbr_ctx {
     void *h_pin[4] = {nullptr, nullptr, nullptr, nullptr};
     size_t h_pin_cap[4] = {0, 0, 0, 0};
     cudaEvent_t ev[8] = {};
-    int drop_unlucky = 0, stats_on = 0, graph_on = 1, extra_primes = 0;
+    int drop_unlucky = 0, stats_on = 0, graph_on = 1, extra_primes = 0, gemm_on = 1;
     gbr_stats stats{};
     std::map<uint64_t, cudaGraphExec_t> graphs;
+    struct Vinv {
+        uint32_t *d = nullptr;
+        int K = 0;
+        uint64_t last_use = 0;
+    };
+    std::map<int, Vinv> vinv;      // inverse Vandermonde matrices per point count P
+    uint64_t vinv_clock = 0;
+    const uint32_t *get_vinv(int P, int K);   // nullptr if it cannot be built
     gbr::ServeState *serve = nullptr;
     gbr_ctx *parent = nullptr;     // serving workers share the parent's arena
     bool own_stream = false;
@@ -89,8 +97,8 @@ struct gbr_resident {
     std::vector<gbr::PairPlan> h_plan;
     char *d_planblk = nullptr;
     size_t planblk_cap = 0;
-    uint32_t *d_res = nullptr, *d_val = nullptr, *d_out = nullptr;
-    size_t res_cap = 0, val_cap = 0, out_cap = 0;
+    uint32_t *d_res = nullptr, *d_val = nullptr, *d_cf = nullptr, *d_out = nullptr;
+    size_t res_cap = 0, val_cap = 0, cf_cap = 0, out_cap = 0;
     int8_t *d_sign = nullptr;
     size_t sign_cap = 0;
     int64_t out_words = 0, sign_bytes = 0;

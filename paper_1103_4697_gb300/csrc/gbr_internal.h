@@ -92,7 +92,8 @@ struct ResLaunch {
     const uint32_t *invk;        // [prime][invk_T] inverses of 1..T-1
     int32_t invk_T;
     uint32_t *res;               // residues
-    uint32_t *val;               // values -> coefficients
+    uint32_t *val;               // values R(a) mod p at the points (Montgomery form)
+    uint32_t *cf;                // coefficients of R mod p (normal form), same offsets as val
     uint32_t *out;               // output magnitudes
     int8_t *sign;                // output signs
     int32_t *deg;                // per pair output degree
@@ -109,6 +110,9 @@ struct WorkList {
     int64_t total;
 };
 
+// pairs sharing a point count needed before interpolation uses the contraction
+constexpr int kGemmMinPairs = 16;
+
 // dynamic shared memory ceiling set once for every kernel (bytes)
 constexpr int kMaxDynSmem = 200 * 1024;
 cudaError_t configure_res_kernels();
@@ -120,6 +124,9 @@ cudaError_t launch_evalres(const ResLaunch &L, const WorkList &w, int slots_f, i
                            cudaStream_t s);
 cudaError_t launch_interp(const ResLaunch &L, const WorkList &w, int maxP, cudaStream_t s);
 cudaError_t launch_crt(const ResLaunch &L, const WorkList &w, int maxL, cudaStream_t s);
+cudaError_t launch_vinv(const ModP *mods, int P, int K, uint32_t *out, cudaStream_t s);
+cudaError_t launch_interp_gemm(const ResLaunch &L, const int32_t *gpairs, int npairs, int P, int K,
+                               const uint32_t *vinv, cudaStream_t s);
 cudaError_t launch_zero_init(const ResLaunch &L, cudaStream_t s);
 
 }  // namespace gbr

@@ -370,8 +370,142 @@ __global__ void k_interp(ResLaunch L, WorkList w, int maxP) {
             }
             __syncwarp();
         }
-        for (int t = lane; t < Pn; t += 32) g[t] = mp_from(Wp[t], M);
+        uint32_t *o = L.cf + P.val_off + (int64_t)i * Pn;
+        for (int t = lane; t < Pn; t += 32) o[t] = mp_from(Wp[t], M);
         __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------ A4 as a contraction
+
+// Inverse Vandermonde matrix of the points 0..P-1 modulo prime i, normal form,
+// row-major: out[(i*P + c)*P + j] = coefficient of x^c in the Lagrange basis
+// polynomial L_j(x) = prod_{t != j} (x - t) / prod_{t != j} (j - t).
+// One block per prime: W(x) = prod_t (x - t) is built in shared memory, then
+// thread j divides W by (x - j) (synthetic division) and scales by
+// 1 / (j! (P-1-j)! (-1)^(P-1-j)).
+__global__ void k_vinv(const ModP *mods, int P, uint32_t *out) {
+    extern __shared__ uint32_t sh[];
+    uint32_t *W = sh;             // P + 1 words, Montgomery form
+    uint32_t *fact = sh + P + 1;  // P + 1 words: t! in Montgomery form
+    const int i = blockIdx.x;
+    const ModP M = mods[i];
+    for (int t = threadIdx.x; t <= P; t += blockDim.x) W[t] = t == 0 ? M.r1 : 0u;
+    __syncthreads();
+    for (int j = 0; j < P; ++j) {                 // W <- W (x - j), degree j -> j + 1
+        const uint32_t jm = mp_to((uint32_t)j, M);
+        uint32_t nv[4];
+        int cnt = 0;
+        for (int t = threadIdx.x; t <= j + 1 && cnt < 4; t += blockDim.x, ++cnt) {
+            uint32_t a = t ? W[t - 1] : 0u, b = t <= j ? W[t] : 0u;
+            nv[cnt] = mp_sub(a, mp_mul(jm, b, M), M.p);
+        }
+        __syncthreads();
+        cnt = 0;
+        for (int t = threadIdx.x; t <= j + 1 && cnt < 4; t += blockDim.x, ++cnt) W[t] = nv[cnt];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        fact[0] = M.r1;
+        for (int t = 1; t <= P; ++t) fact[t] = mp_mul(fact[t - 1], mp_to((uint32_t)t, M), M);
+    }
+    __syncthreads();
+    uint32_t *o = out + (int64_t)i * P * P;
+    for (int j = threadIdx.x; j < P; j += blockDim.x) {
+        uint32_t d = mp_mul(fact[j], fact[P - 1 - j], M);
+        if ((P - 1 - j) & 1) d = mp_neg(d, M.p);
+        const uint32_t id = mp_inv(d, M);
+        const uint32_t jm = mp_to((uint32_t)j, M);
+        uint32_t q = W[P];
+        o[(int64_t)(P - 1) * P + j] = mp_from(mp_mul(q, id, M), M);
+        for (int t = P - 1; t >= 1; --t) {
+            q = mp_add(W[t], mp_mul(jm, q, M), M.p);
+            o[(int64_t)(t - 1) * P + j] = mp_from(mp_mul(q, id, M), M);
+        }
+    }
+}
+
+// acc += x * y as a 96-bit sum in three words (two multiply-adds with carry and
+// one carry add): products are below 2^62, so up to 2^32 of them fit.
+__device__ __forceinline__ void mac96(uint32_t &a0, uint32_t &a1, uint32_t &a2, uint32_t x, uint32_t y) {
+    asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+        "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+        "addc.u32 %2, %2, 0;"
+        : "+r"(a0), "+r"(a1), "+r"(a2)
+        : "r"(x), "r"(y));
+}
+
+constexpr int GT_M = 64, GT_N = 64, GT_K = 32;
+
+// coefficients = Vinv_i * values for one prime i (blockIdx.z) and a group of
+// pairs that share P.  Tile: 64 coefficient rows x 64 pairs, K in chunks of 32
+// points; each of the 256 threads owns 4 x 4 outputs.  Values are in
+// Montgomery form and Vinv in normal form, so the exact sum X = sum Vinv * v~
+// is congruent to coef * 2^32; one reduction per output gives coef.
+__global__ void __launch_bounds__(256) k_interp_gemm(ResLaunch L, const int32_t *gpairs, int npairs, int P,
+                                                    const uint32_t *vinv) {
+    __shared__ uint32_t As[GT_K][GT_M + 1];
+    __shared__ __align__(16) uint32_t Bs[GT_K][GT_N + 4];
+    __shared__ uint32_t Cs[GT_N][GT_M + 1];
+    __shared__ int64_t colbase[GT_N];
+    const int i = blockIdx.z;
+    const int c0 = blockIdx.x * GT_M, q0 = blockIdx.y * GT_N;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    if (threadIdx.x < GT_N) {
+        int qi = q0 + threadIdx.x;
+        int64_t b = -1;
+        if (qi < npairs) {
+            const PairPlan &pp = L.plan[gpairs[qi]];
+            if (i < pp.k) b = pp.val_off + (int64_t)i * P;
+        }
+        colbase[threadIdx.x] = b;
+    }
+    __syncthreads();
+    const uint32_t *A = vinv + (int64_t)i * P * P;
+    uint32_t a0[16], a1[16], a2[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) a0[t] = a1[t] = a2[t] = 0u;
+    for (int j0 = 0; j0 < P; j0 += GT_K) {
+        for (int e = threadIdx.x; e < GT_M * GT_K; e += 256) {
+            int r = e / GT_K, kk = e % GT_K;
+            int c = c0 + r, j = j0 + kk;
+            As[kk][r] = (c < P && j < P) ? A[(int64_t)c * P + j] : 0u;
+        }
+        for (int e = threadIdx.x; e < GT_N * GT_K; e += 256) {
+            int qq = e / GT_K, kk = e % GT_K;
+            int64_t b = colbase[qq];
+            int j = j0 + kk;
+            Bs[kk][qq] = (b >= 0 && j < P) ? L.val[b + j] : 0u;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < GT_K; ++kk) {
+            const uint4 bv = *reinterpret_cast<const uint4 *>(&Bs[kk][tx * 4]);
+            const uint32_t av[4] = {As[kk][ty * 4], As[kk][ty * 4 + 1], As[kk][ty * 4 + 2], As[kk][ty * 4 + 3]};
+            const uint32_t bw[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) mac96(a0[r * 4 + cc], a1[r * 4 + cc], a2[r * 4 + cc], av[r], bw[cc]);
+        }
+        __syncthreads();
+    }
+    const ModP M = L.mods[i];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+            const int t = r * 4 + cc;
+            // X * 2^-32 = (a2 2^32 + a1) + a0 2^-32 (mod p); (a2:a1) < 2^41 < p 2^32
+            uint32_t hi = mp_mul(mp_redc(a1[t], a2[t], M.p, M.pinv), M.r2, M);
+            uint32_t lo = mp_redc(a0[t], 0u, M.p, M.pinv);
+            Cs[tx * 4 + cc][ty * 4 + r] = mp_add(hi, lo, M.p);
+        }
+    __syncthreads();
+    for (int e = threadIdx.x; e < GT_N * GT_M; e += 256) {
+        int qq = e / GT_M, r = e % GT_M;
+        int64_t b = colbase[qq];
+        if (b >= 0 && c0 + r < P) L.cf[b + c0 + r] = Cs[qq][r];
     }
 }
 
@@ -389,7 +523,7 @@ __global__ void k_crt(ResLaunch L, WorkList w, int LM) {
         int c = (int)(item - w.start[bi]);
         const PairPlan &P = L.plan[q];
         const int k = P.k, Pn = P.P;
-        uint32_t *v = L.val + P.val_off + c;
+        uint32_t *v = L.cf + P.val_off + c;
         // Garner: digits v_i with X = sum v_i prod_{j<i} p_j, 0 <= v_i < p_i
         for (int i = 1; i < k; ++i) {
             const ModP M = L.mods[i];
@@ -449,6 +583,7 @@ cudaError_t configure_res_kernels() {
     cudaError_t e = cudaFuncSetAttribute(k_evalres, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_interp, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_crt, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_vinv, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     return e;
 }
 
@@ -499,6 +634,23 @@ cudaError_t launch_interp(const ResLaunch &L, const WorkList &w, int maxP, cudaS
     if (smem > kMaxDynSmem) return cudaErrorInvalidValue;
     int grid = persistent_grid(k_interp, nw * 32, smem, (w.total + nw - 1) / nw);
     k_interp<<<grid, nw * 32, smem, s>>>(L, w, maxP);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vinv(const ModP *mods, int P, int K, uint32_t *out, cudaStream_t s) {
+    size_t smem = (size_t)2 * (P + 1) * sizeof(uint32_t);
+    int block = P + 2 <= 1024 ? ((P + 2 + 31) / 32) * 32 : 1024;
+    // each thread updates at most 4 coefficients of W per step
+    if (smem > kMaxDynSmem || P + 1 > 4 * block) return cudaErrorInvalidValue;
+    k_vinv<<<K, block, smem, s>>>(mods, P, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interp_gemm(const ResLaunch &L, const int32_t *gpairs, int npairs, int P, int K,
+                               const uint32_t *vinv, cudaStream_t s) {
+    if (npairs <= 0) return cudaSuccess;
+    dim3 grid((P + GT_M - 1) / GT_M, (npairs + GT_N - 1) / GT_N, K);
+    k_interp_gemm<<<grid, 256, 0, s>>>(L, gpairs, npairs, P, vinv);
     return cudaGetLastError();
 }
 

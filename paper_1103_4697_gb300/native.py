@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libgbres.so")
 
 OK, EINVAL, ENOMEM, EDEVICE, ETIMEOUT, EAGAIN, EVERIFY, ELIMIT, ECANCELED, ENOTFOUND = range(10)
-OPT_DROP_UNLUCKY, OPT_STATS, OPT_GRAPH, OPT_EXTRA_PRIMES = 1, 2, 3, 4
+OPT_DROP_UNLUCKY, OPT_STATS, OPT_GRAPH, OPT_EXTRA_PRIMES, OPT_INTERP_GEMM = 1, 2, 3, 4, 5
 JOB_RESULTANT, JOB_DISC, JOB_GCD = 0, 1, 2
 
 

@@ -192,3 +192,27 @@ def test_mixed_batch_sampled(ctx):
     small = [q for q in range(512) if not ps.planted[q] and len(ps.f[q]) <= 8 and len(ps.f[q][0]) <= 8]
     for q in small[:3]:
         assert out[q] == list(O.res_evalz(ps.f[q], ps.g[q]))
+
+
+def test_interpolation_contraction_matches_newton(ctx):
+    """Pairs sharing their point count are interpolated by the inverse-Vandermonde
+    contraction; with different coefficient sizes (so different prime counts) in one
+    group and a ragged number of pairs.  Newton interpolation must agree, and both
+    must equal the oracle."""
+    from paper_1103_4697_gb300.native import OPT_INTERP_GEMM
+
+    fs, gs = [], []
+    for i in range(37):
+        bits = 8 if i % 2 else 40
+        f, g = W.small_dense_pair(700 + i, 6, bits)
+        fs.append(f)
+        gs.append(g)
+    got = ctx.resultant_batch(fs, gs)
+    ctx.set_option(OPT_INTERP_GEMM, 0)
+    try:
+        newton = ctx.resultant_batch(fs, gs)
+    finally:
+        ctx.set_option(OPT_INTERP_GEMM, 1)
+    assert got == newton
+    for f, g, r in zip(fs, gs, got):
+        assert r == list(O.res_bareiss(f, g))
