@@ -64,7 +64,7 @@ extern "C" {
 #define GBR_MAX_WORDS   8     /* 64-bit words per input coefficient (512-bit inputs) */
 #define GBR_MAX_YDEG    127   /* degree in the eliminated variable, per polynomial */
 #define GBR_MAX_POINTS  16384 /* evaluation points per resultant = x-degree bound + 1 */
-#define GBR_MAX_PRIMES  2048  /* 31-bit primes per result (about 63 000-bit coefficients) */
+#define GBR_MAX_PRIMES  2048  /* primes per result (about 62 000-bit coefficients) */
 #define GBR_MAX_UDEG    8191  /* degree of a univariate gcd input */
 
 /* ------------------------------------------------------------------ types */
@@ -166,7 +166,7 @@ int gbr_resultant(gbr_ctx *ctx, const gbr_bipoly *f, const gbr_bipoly *g, int va
 int gbr_discriminant_res(gbr_ctx *ctx, const gbr_bipoly *f, int var, gbr_bigpoly *out);
 
 /* gcd(p, q) in Z[x] (Section 2: content removal; Section 2.1: square-free
- * factorisation).  Modular images over 31-bit primes, Chinese remaindering of
+ * factorisation).  Modular images over the table primes, Chinese remaindering of
  * the gcd and both cofactors, and an exact norm check that proves the result
  * (on failure more primes are added).  Input coefficients: words must be 1. */
 int gbr_gcd(gbr_ctx *ctx, const gbr_upoly *p, const gbr_upoly *q, gbr_bigpoly *out);
@@ -280,7 +280,8 @@ int gbr_crt_noalloc(const uint32_t *residues, int k, int ncoef, int64_t stride, 
 /* ------------------------------------------------------------------ host-side information */
 
 /* The fixed table of primes used by every context: p_0 > p_1 > ... are the
- * largest primes below 2^31.  Host only, needs no device. */
+ * largest primes below 2^32 / 3 (about 30.4 bits each, so that three
+ * products of residues fit one Montgomery reduction).  Host only. */
 int gbr_num_primes(void);
 int gbr_prime(int index, uint32_t *p);
 

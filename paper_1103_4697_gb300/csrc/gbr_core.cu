@@ -70,9 +70,13 @@ static ModP make_mod(uint32_t p) {
     return M;
 }
 
+// The table holds the largest primes below 2^32 / 3: three Montgomery products
+// then fit one reduction (see gbr_modarith.cuh).
 static void init_primes() {
     g_mods.reserve(GBR_MAX_PRIMES);
-    for (uint32_t c = 0x7fffffffu; (int)g_mods.size() < GBR_MAX_PRIMES; c -= 2)
+    uint32_t top = (uint32_t)(0xffffffffull / 3);
+    if (!(top & 1)) --top;
+    for (uint32_t c = top; (int)g_mods.size() < GBR_MAX_PRIMES; c -= 2)
         if (is_prime32(c)) g_mods.push_back(make_mod(c));
     g_log2pref.assign(g_mods.size() + 1, 0.0);
     for (size_t i = 0; i < g_mods.size(); ++i) g_log2pref[i + 1] = g_log2pref[i] + std::log2((double)g_mods[i].p);

@@ -1,9 +1,10 @@
-// Montgomery arithmetic modulo 31-bit primes (R = 2^32), integer pipes only.
+// Montgomery arithmetic modulo primes below 2^32 / 3 (R = 2^32), integer pipes only.
 //
 // Every residue on the device path is kept in Montgomery form x~ = x * 2^32 mod p.
-// redc(t) = t * 2^-32 mod p for 0 <= t < p * 2^32; with p < 2^31 a sum of two
-// products a*x + b*y of residues stays below 2 p^2 < p * 2^32, so one reduction
-// serves a fused multiply-subtract (the elimination step of the resultant).
+// redc(t) = t * 2^-32 mod p for 0 <= t < p * 2^32.  With p < 2^32 / 3 a sum of
+// up to three products of residues stays below 3 p^2 < p * 2^32, so one
+// reduction serves a fused multiply-subtract of two or three products (the
+// elimination steps of the resultant).
 #pragma once
 #include <stdint.h>
 
@@ -14,7 +15,7 @@
 #endif
 
 struct ModP {
-    uint32_t p;      // odd prime, 2^30 < p < 2^31
+    uint32_t p;      // odd prime, 2^30 < p < 2^32 / 3
     uint32_t pinv;   // -p^-1 mod 2^32
     uint32_t r1;     // 2^32 mod p   (Montgomery form of 1)
     uint32_t r2;     // 2^64 mod p   (to_mont multiplier)
@@ -63,6 +64,23 @@ GBR_HD uint32_t mp_mulsub(uint32_t a, uint32_t x, uint32_t b, uint32_t y, const 
     return mp_redc(lo, hi, M.p, M.pinv);
 #else
     uint64_t t = (uint64_t)a * x + (uint64_t)nb * y;
+    return mp_redc((uint32_t)t, (uint32_t)(t >> 32), M.p, M.pinv);
+#endif
+}
+
+// (a*x + b*y + c*z) * 2^-32 mod p for residues in [0, p] (sum < 3 p^2 < p 2^32).
+GBR_HD uint32_t mp_fma3(uint32_t a, uint32_t x, uint32_t b, uint32_t y, uint32_t c, uint32_t z, const ModP &M) {
+#if defined(__CUDA_ARCH__)
+    uint32_t lo = a * x, hi = __umulhi(a, x);
+    asm("mad.lo.cc.u32 %0, %2, %3, %0;\n\t"
+        "madc.hi.u32 %1, %2, %3, %1;\n\t"
+        "mad.lo.cc.u32 %0, %4, %5, %0;\n\t"
+        "madc.hi.u32 %1, %4, %5, %1;"
+        : "+r"(lo), "+r"(hi)
+        : "r"(b), "r"(y), "r"(c), "r"(z));
+    return mp_redc(lo, hi, M.p, M.pinv);
+#else
+    uint64_t t = (uint64_t)a * x + (uint64_t)b * y + (uint64_t)c * z;
     return mp_redc((uint32_t)t, (uint32_t)(t >> 32), M.p, M.pinv);
 #endif
 }

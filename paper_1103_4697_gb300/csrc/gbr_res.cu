@@ -218,9 +218,21 @@ __global__ void k_reduce(ResLaunch L, WorkList w) {
 //       res_{a,b}(A,B) = (-1)^{ab} zeta^{a-r} res_{b,r}(B,R)
 //   res_{b,r}(B, c R) = c^b res_{b,r}(B,R)    (R is reached as zeta^e R by e fraction-free steps)
 //   res_{a,0}(A, b0) = b0^a ; res_{0,0} = 1 ; both leading coefficients zero -> 0.
+//
+// Normal rounds (deg A = deg B + 1 = d + 1) are done in one pass:
+//   zeta^2 A - (zeta alpha x + q0) B,  q0 = zeta a_d - alpha b_{d-1},
+// three products per coefficient and one reduction (mp_fma3).  Such a round
+// contributes zeta^(2d) to the divisor and zeta^2 to the multiplier, i.e. a net
+// Z^(d-1) with Z = zeta^2 in the divisor.  These are collected without powers:
+// Q holds the product of the Z of all normal rounds so far, and whenever the
+// divisor degree drops by delta between rounds, D *= Q^delta (delta is 1 in the
+// normal case); after the last round D *= Q^(d_last - 1).  Each Z_r then appears
+// in D with exponent (d_r - d_last) + (d_last - 1) = d_r - 1.  Other rounds keep
+// explicit powers.
 GBR_HD uint32_t res_formal(uint32_t *A, int da, uint32_t *B, int db, int BS, const ModP &M) {
     const uint32_t one = M.r1;
-    uint32_t acc = one, den = one;
+    uint32_t acc = one, den = one, Q = one, D = one;
+    int prev_db = -1;
     bool neg = false;
     if (da == 0 && db == 0) return one;
     if (A[0] == 0 && B[0] == 0) return 0u;
@@ -254,28 +266,89 @@ GBR_HD uint32_t res_formal(uint32_t *A, int da, uint32_t *B, int db, int BS, con
             acc = mp_mul(acc, mp_pow(B[0], (uint32_t)da, M), M);
             break;
         }
+        if (prev_db >= 0) D = mp_mul(D, prev_db - db == 1 ? Q : mp_pow(Q, (uint32_t)(prev_db - db), M), M);
+        prev_db = db;
         const uint32_t zeta = B[0];
-        const int DA = da;
-        int e = 0;
-        while (da >= db) {
-            const uint32_t q = A[0];
-            int t = 1;
-            for (; t <= db; ++t) A[t * BS] = mp_mulsub(zeta, A[t * BS], q, B[t * BS], M);
-            for (; t <= da; ++t) A[t * BS] = mp_mul(zeta, A[t * BS], M);
-            A += BS;
-            --da;
-            ++e;
+        if (da == db + 1) {
+            const uint32_t alpha = A[0];
+            const uint32_t z2 = mp_mul(zeta, zeta, M);
+            const uint32_t nza = M.p - mp_mul(zeta, alpha, M);
+            const uint32_t nq0 = M.p - mp_mulsub(zeta, A[BS], alpha, B[BS], M);
+            // new A[s] = z2 A[s+2] - (zeta alpha) B[s+2] - q0 B[s+1], s = 0..db-1, B[db+1] = 0
+            int s = 0;
+            for (; s + 4 <= db; s += 4) {
+                uint32_t x0 = A[(s + 2) * BS], x1 = A[(s + 3) * BS], x2 = A[(s + 4) * BS], x3 = A[(s + 5) * BS];
+                uint32_t b1 = B[(s + 1) * BS], b2 = B[(s + 2) * BS], b3 = B[(s + 3) * BS], b4 = B[(s + 4) * BS];
+                uint32_t b5 = s + 5 <= db ? B[(s + 5) * BS] : 0u;
+                uint32_t r0 = mp_fma3(z2, x0, nza, b2, nq0, b1, M);
+                uint32_t r1 = mp_fma3(z2, x1, nza, b3, nq0, b2, M);
+                uint32_t r2 = mp_fma3(z2, x2, nza, b4, nq0, b3, M);
+                uint32_t r3 = mp_fma3(z2, x3, nza, b5, nq0, b4, M);
+                A[(s + 2) * BS] = r0;
+                A[(s + 3) * BS] = r1;
+                A[(s + 4) * BS] = r2;
+                A[(s + 5) * BS] = r3;
+            }
+            for (; s < db; ++s) {
+                uint32_t b2 = s + 2 <= db ? B[(s + 2) * BS] : 0u;
+                A[(s + 2) * BS] = mp_fma3(z2, A[(s + 2) * BS], nza, b2, nq0, B[(s + 1) * BS], M);
+            }
+            A += 2 * BS;
+            da = db - 1;
             while (da >= 0 && A[0] == 0) { A += BS; --da; }
+            if (da < 0) return 0u;
+            Q = mp_mul(Q, z2, M);
+            if (da < db - 1) acc = mp_mul(acc, mp_pow(zeta, (uint32_t)(db - 1 - da), M), M);
+        } else {
+            const int DA = da;
+            int e = 0;
+            while (da >= db) {
+                const uint32_t q = A[0];
+                int t = 1;
+                for (; t <= db; ++t) A[t * BS] = mp_mulsub(zeta, A[t * BS], q, B[t * BS], M);
+                for (; t <= da; ++t) A[t * BS] = mp_mul(zeta, A[t * BS], M);
+                A += BS;
+                --da;
+                ++e;
+                while (da >= 0 && A[0] == 0) { A += BS; --da; }
+            }
+            if (da < 0) return 0u;
+            if ((DA * db) & 1) neg = !neg;
+            acc = mp_mul(acc, mp_pow(zeta, (uint32_t)(DA - da), M), M);
+            den = mp_mul(den, mp_pow(zeta, (uint32_t)(e * db), M), M);
         }
-        if (da < 0) return 0u;
-        if ((DA * db) & 1) neg = !neg;
-        acc = mp_mul(acc, mp_pow(zeta, (uint32_t)(DA - da), M), M);
-        den = mp_mul(den, mp_pow(zeta, (uint32_t)(e * db), M), M);
         uint32_t *t = A; A = B; B = t;
         int ti = da; da = db; db = ti;
     }
+    if (prev_db >= 1) D = mp_mul(D, mp_pow(Q, (uint32_t)(prev_db - 1), M), M);
+    den = mp_mul(den, D, M);
     uint32_t r = mp_mul(acc, mp_inv(den, M), M);
     return neg ? mp_neg(r, M.p) : r;
+}
+
+// Horner evaluation of rows [r0 - 3, r0] (those >= 0) at x = a, four independent
+// chains; entries past a row's degree are zero, so every chain may start at the
+// group's largest degree.  Results go to slots t0.. of the column (top first).
+__device__ __forceinline__ void eval4(const uint32_t *rc, int ncol, const int32_t *rowdeg, int r0, uint32_t a,
+                                      const ModP &M, uint32_t *dst, int BS) {
+    const int nr = r0 + 1 < 4 ? r0 + 1 : 4;
+    int dmax = -1;
+    for (int i = 0; i < nr; ++i) dmax = max(dmax, rowdeg[r0 - i]);
+    const uint32_t *c0 = rc + (int64_t)r0 * ncol;
+    const uint32_t *c1 = nr > 1 ? c0 - ncol : c0;
+    const uint32_t *c2 = nr > 2 ? c0 - 2 * ncol : c0;
+    const uint32_t *c3 = nr > 3 ? c0 - 3 * ncol : c0;
+    uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    for (int x = dmax; x >= 0; --x) {
+        a0 = mp_add(mp_mul(a0, a, M), c0[x], M.p);
+        a1 = mp_add(mp_mul(a1, a, M), c1[x], M.p);
+        a2 = mp_add(mp_mul(a2, a, M), c2[x], M.p);
+        a3 = mp_add(mp_mul(a3, a, M), c3[x], M.p);
+    }
+    dst[0] = a0;
+    if (nr > 1) dst[BS] = a1;
+    if (nr > 2) dst[2 * BS] = a2;
+    if (nr > 3) dst[3 * BS] = a3;
 }
 
 // ------------------------------------------------------------------ A2 + A3: evaluate and solve
@@ -298,20 +371,8 @@ __global__ void k_evalres(ResLaunch L, WorkList w, int SF, int SG) {
         const uint32_t *rg = rf + (P.m + 1) * (P.dxf + 1);
         const int32_t *dgf = L.rowdeg + P.rowdeg_f;
         const int32_t *dgg = L.rowdeg + P.rowdeg_g;
-        for (int t = 0; t <= P.m; ++t) {
-            int row = P.m - t;
-            const uint32_t *c = rf + row * (P.dxf + 1);
-            uint32_t acc = 0;
-            for (int x = dgf[row]; x >= 0; --x) acc = mp_add(mp_mul(acc, a, M), c[x], M.p);
-            Fs[t * BS] = acc;
-        }
-        for (int t = 0; t <= P.n; ++t) {
-            int row = P.n - t;
-            const uint32_t *c = rg + row * (P.dxg + 1);
-            uint32_t acc = 0;
-            for (int x = dgg[row]; x >= 0; --x) acc = mp_add(mp_mul(acc, a, M), c[x], M.p);
-            Gs[t * BS] = acc;
-        }
+        for (int t = 0; t <= P.m; t += 4) eval4(rf, P.dxf + 1, dgf, P.m - t, a, M, Fs + t * BS, BS);
+        for (int t = 0; t <= P.n; t += 4) eval4(rg, P.dxg + 1, dgg, P.n - t, a, M, Gs + t * BS, BS);
         L.val[P.val_off + (int64_t)i * P.P + j] = res_formal(Fs, P.m, Gs, P.n, BS, M);
     }
 }
