@@ -727,7 +727,7 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
         k += c->extra_primes;
         p.k = k;
         p.L = (31 * k + 31) / 32;
-        p.S = (p.m + 1) * (p.dxf + 1) + (p.n + 1) * (p.dxg + 1);
+        p.S = (p.dxf + 1) * rows4(p.m) + (p.dxg + 1) * rows4(p.n);
         p.res_off = res_w;
         res_w += (int64_t)k * p.S;
         p.val_off = val_w;

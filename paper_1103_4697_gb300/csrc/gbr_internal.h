@@ -58,7 +58,7 @@ struct PairPlan {
     int32_t P;          // evaluation points = degree bound + 1
     int32_t k;          // primes
     int32_t L;          // 32-bit limbs per output coefficient
-    int32_t S;          // residue words per prime: (m+1)(dxf+1) + (n+1)(dxg+1)
+    int32_t S;          // residue words per prime: (dxf+1) rows4(m) + (dxg+1) rows4(n)
     int64_t res_off;    // residues [prime][S]                       (u32 words)
     int64_t val_off;    // values / coefficients [prime][P]          (u32 words)
     int64_t out_off;    // output magnitudes [coef][L]               (u32 words)
@@ -68,6 +68,10 @@ struct PairPlan {
 };
 
 enum : int32_t { PLAN_ZERO = 1 };
+
+// Residue rows of a polynomial of degree m in the eliminated variable, padded to
+// a multiple of 4 (the evaluation reads four rows per 16-byte load).
+GBR_HD int32_t rows4(int32_t m) { return (m + 1 + 3) & ~3; }
 
 // Host-side bound arithmetic shared by gbr_resultant_info and the planner.
 GBR_HD int32_t degree_bound(const PairBound &b) {

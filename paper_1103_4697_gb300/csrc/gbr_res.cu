@@ -174,35 +174,41 @@ __global__ void k_reduce(ResLaunch L, WorkList w) {
         int64_t s = item - w.start[bi];
         const PairPlan &P = L.plan[q];
         const PairDesc &D = L.desc[q];
-        int nf = (P.m + 1) * (P.dxf + 1);
+        const int rf4 = rows4(P.m), rg4 = rows4(P.n);
+        const int64_t nf = (int64_t)(P.dxf + 1) * rf4;
         const PolyDesc *src;
-        int row, col, mult = 0;
+        int row, col, mult = 0, nrows;
         if (s < nf) {
             src = &D.f;
-            row = (int)(s / (P.dxf + 1));
-            col = (int)(s % (P.dxf + 1));
+            col = (int)(s / rf4);
+            row = (int)(s % rf4);
+            nrows = P.m + 1;
         } else {
             int64_t s2 = s - nf;
-            row = (int)(s2 / (P.dxg + 1));
-            col = (int)(s2 % (P.dxg + 1));
+            col = (int)(s2 / rg4);
+            row = (int)(s2 % rg4);
+            nrows = P.n + 1;
             if (D.disc) {
                 src = &D.f;
                 mult = row + 1;
-                row = row + 1;
             } else {
                 src = &D.g;
             }
         }
+        uint32_t *dst = L.res + P.res_off + s;
+        if (row >= nrows) {                       // padding rows hold zeros
+            for (int i = 0; i < P.k; ++i) dst[(int64_t)i * P.S] = 0u;
+            continue;
+        }
         uint64_t wbuf[8];
-        const uint64_t *cp = coef_ptr(L.coef, *src, row, col);
+        const uint64_t *cp = coef_ptr(L.coef, *src, mult ? row + 1 : row, col);
         int W = src->words;
         for (int i = 0; i < W; ++i) wbuf[i] = cp[i];
-        uint32_t *dst = L.res + P.res_off + s;
         for (int i = 0; i < P.k; ++i) {
             ModP M = L.mods[i];
             uint32_t r = mp_from_words(wbuf, W, M);
             if (mult) r = mp_mul(r, mp_to((uint32_t)mult, M), M);
-            dst[(int64_t)i * P.S] = r;
+            dst[(int64_t)i * P.S] = mp_mul(r, M.r2, M);   // c R^2: one reduction per Horner step
         }
     }
 }
@@ -326,29 +332,43 @@ GBR_HD uint32_t res_formal(uint32_t *A, int da, uint32_t *B, int db, int BS, con
     return neg ? mp_neg(r, M.p) : r;
 }
 
-// Horner evaluation of rows [r0 - 3, r0] (those >= 0) at x = a, four independent
-// chains; entries past a row's degree are zero, so every chain may start at the
-// group's largest degree.  Results go to slots t0.. of the column (top first).
-__device__ __forceinline__ void eval4(const uint32_t *rc, int ncol, const int32_t *rowdeg, int r0, uint32_t a,
-                                      const ModP &M, uint32_t *dst, int BS) {
-    const int nr = r0 + 1 < 4 ? r0 + 1 : 4;
+// One Horner step acc <- acc a + c on Montgomery residues with c stored as
+// c R^2: acc~ a~ + c R^2 = (acc a + c) R^2 < p^2 + p, and one reduction leaves
+// (acc a + c) R.
+__device__ __forceinline__ uint32_t horner_step(uint32_t acc, uint32_t a, uint32_t c2, const ModP &M) {
+    uint32_t lo, hi;
+    asm("mad.lo.cc.u32 %0, %2, %3, %4;\n\t"
+        "madc.hi.u32 %1, %2, %3, %5;"
+        : "=r"(lo), "=r"(hi)
+        : "r"(acc), "r"(a), "r"(c2), "r"(0u));
+    return mp_redc(lo, hi, M.p, M.pinv);
+}
+
+// Evaluates rows r0..r0+3 (r0 a multiple of 4) at x = a with four independent
+// Horner chains; the residues are laid out [x][row, padded to 4 rows] so the
+// four coefficients of one power of x come in one 16-byte load.  Entries past
+// a row's degree (and padding rows) are zero, so every chain starts at the
+// group's largest degree.  Row r goes to slot (deg - r) of the column.
+__device__ __forceinline__ void eval4(const uint32_t *rc, int rows4n, const int32_t *rowdeg, int nrows, int r0,
+                                      uint32_t a, const ModP &M, uint32_t *col, int BS) {
+    const int nr = min(4, nrows - r0);
     int dmax = -1;
-    for (int i = 0; i < nr; ++i) dmax = max(dmax, rowdeg[r0 - i]);
-    const uint32_t *c0 = rc + (int64_t)r0 * ncol;
-    const uint32_t *c1 = nr > 1 ? c0 - ncol : c0;
-    const uint32_t *c2 = nr > 2 ? c0 - 2 * ncol : c0;
-    const uint32_t *c3 = nr > 3 ? c0 - 3 * ncol : c0;
+    for (int i = 0; i < nr; ++i) dmax = max(dmax, rowdeg[r0 + i]);
     uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    const uint4 *c = reinterpret_cast<const uint4 *>(rc + r0);
+    const int step = rows4n >> 2;
     for (int x = dmax; x >= 0; --x) {
-        a0 = mp_add(mp_mul(a0, a, M), c0[x], M.p);
-        a1 = mp_add(mp_mul(a1, a, M), c1[x], M.p);
-        a2 = mp_add(mp_mul(a2, a, M), c2[x], M.p);
-        a3 = mp_add(mp_mul(a3, a, M), c3[x], M.p);
+        const uint4 v = c[(int64_t)x * step];
+        a0 = horner_step(a0, a, v.x, M);
+        a1 = horner_step(a1, a, v.y, M);
+        a2 = horner_step(a2, a, v.z, M);
+        a3 = horner_step(a3, a, v.w, M);
     }
-    dst[0] = a0;
-    if (nr > 1) dst[BS] = a1;
-    if (nr > 2) dst[2 * BS] = a2;
-    if (nr > 3) dst[3 * BS] = a3;
+    const int top = nrows - 1;
+    col[(top - r0) * BS] = a0;
+    if (nr > 1) col[(top - r0 - 1) * BS] = a1;
+    if (nr > 2) col[(top - r0 - 2) * BS] = a2;
+    if (nr > 3) col[(top - r0 - 3) * BS] = a3;
 }
 
 // ------------------------------------------------------------------ A2 + A3: evaluate and solve
@@ -367,12 +387,13 @@ __global__ void k_evalres(ResLaunch L, WorkList w, int SF, int SG) {
         int j = (int)(local % P.P);
         const ModP M = L.mods[i];
         const uint32_t a = mp_to((uint32_t)j, M);
+        const int rf4 = rows4(P.m), rg4 = rows4(P.n);
         const uint32_t *rf = L.res + P.res_off + (int64_t)i * P.S;
-        const uint32_t *rg = rf + (P.m + 1) * (P.dxf + 1);
+        const uint32_t *rg = rf + (int64_t)(P.dxf + 1) * rf4;
         const int32_t *dgf = L.rowdeg + P.rowdeg_f;
         const int32_t *dgg = L.rowdeg + P.rowdeg_g;
-        for (int t = 0; t <= P.m; t += 4) eval4(rf, P.dxf + 1, dgf, P.m - t, a, M, Fs + t * BS, BS);
-        for (int t = 0; t <= P.n; t += 4) eval4(rg, P.dxg + 1, dgg, P.n - t, a, M, Gs + t * BS, BS);
+        for (int r0 = 0; r0 <= P.m; r0 += 4) eval4(rf, rf4, dgf, P.m + 1, r0, a, M, Fs, BS);
+        for (int r0 = 0; r0 <= P.n; r0 += 4) eval4(rg, rg4, dgg, P.n + 1, r0, a, M, Gs, BS);
         L.val[P.val_off + (int64_t)i * P.P + j] = res_formal(Fs, P.m, Gs, P.n, BS, M);
     }
 }
