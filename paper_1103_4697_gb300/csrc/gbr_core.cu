@@ -1071,22 +1071,17 @@ extern "C" int gbr_resultant_info(const gbr_bipoly *f, const gbr_bipoly *g, int 
         host_rows(g, var, dg, ng);
     }
     PairBound b{};
-    auto summarise = [](const std::vector<int> &d, const std::vector<double> &nrm, int &m, int &dx, int &td,
-                        double &sq) {
+    auto summarise = [](const std::vector<int> &d, int &m, int &dx, int &td) {
         m = dx = td = -1;
-        std::vector<double> a;
         for (size_t r = 0; r < d.size(); ++r)
             if (d[r] >= 0) {
                 m = (int)r;
                 dx = std::max(dx, d[r]);
                 td = std::max(td, (int)r + d[r]);
-                a.push_back(2.0 * nrm[r]);
             }
-        sq = lse2(a);
     };
-    double sf, sg;
-    summarise(df, nf, b.m, b.dxf, b.tdf, sf);
-    summarise(dg, ng, b.n, b.dxg, b.tdg, sg);
+    summarise(df, b.m, b.dxf, b.tdf);
+    summarise(dg, b.n, b.dxg, b.tdg);
     out->m = b.m;
     out->n = b.n;
     if (b.m < 0 || b.n < 0) {
@@ -1096,7 +1091,9 @@ extern "C" int gbr_resultant_info(const gbr_bipoly *f, const gbr_bipoly *g, int 
         out->limbs = 0;
         return GBR_OK;
     }
-    b.log2B = (b.m == 0 && b.n == 0) ? 0.0 : 0.5 * b.n * sf + 0.5 * b.m * sg;
+    if (b.m > GBR_MAX_YDEG || b.n > GBR_MAX_YDEG) return GBR_ELIMIT;
+    std::vector<double> ef(b.m + 2), eg(b.n + 2);
+    b.log2B = best_scaled_bound(nf.data(), b.m, ng.data(), b.n, ef.data(), eg.data());
     out->deg_bound = degree_bound(b);
     out->log2_bound = b.log2B;
     out->primes = primes_for_bits(b.log2B * (1.0 + 1e-9) + 2.0);

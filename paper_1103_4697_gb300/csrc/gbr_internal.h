@@ -1,10 +1,12 @@
 // Internal structures shared by the host driver and the kernels of libgbres.
 #pragma once
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <string>
 
+#include "../../include/gbres.h"
 #include "gbr_modarith.cuh"
 
 namespace gbr {
@@ -72,6 +74,74 @@ enum : int32_t { PLAN_ZERO = 1 };
 // Residue rows of a polynomial of degree m in the eliminated variable, padded to
 // a multiple of 4 (the evaluation reads four rows per 16-byte load).
 GBR_HD int32_t rows4(int32_t m) { return (m + 1 + 3) & ~3; }
+
+// Upper bound on log2 |coefficient| of res_y(f, g), from Hadamard's inequality on
+// the unit circle |x| = 1 (a coefficient of R is at most max |R(x)| there, and
+// |f_i(x)| <= ||f_i||_1).  lf[i] = log2 ||f_i||_1 (i = 0..m, -inf for zero
+// rows), lg likewise.  For any lambda > 0, res(f(x, lambda y), g(x, lambda y)) =
+// lambda^(mn) res(f, g), so the Hadamard bound of the scaled Sylvester matrix
+// (entries lambda^i f_i) minus mn log2 lambda is a bound too; both the product
+// of row norms and the product of column norms are used, and the smaller is
+// returned.  l2lam = log2 lambda.
+GBR_HD double scaled_hadamard_log2(const double *lf, int m, const double *lg, int n, double l2lam, double *ef,
+                                   double *eg) {
+    if (m <= 0 && n <= 0) return 0.0;
+    // scaled log2 norms, their maximum, and 2^(2 (F_i - M)) clamped below at
+    // 2^-1000 (enlarging a term only enlarges the bound; no sum underflows)
+    double M = -INFINITY;
+    for (int i = 0; i <= m; ++i)
+        if (lf[i] != -INFINITY && lf[i] + i * l2lam > M) M = lf[i] + i * l2lam;
+    for (int j = 0; j <= n; ++j)
+        if (lg[j] != -INFINITY && lg[j] + j * l2lam > M) M = lg[j] + j * l2lam;
+    double sf = 0.0, sg = 0.0;
+    for (int i = 0; i <= m; ++i) {
+        double t = lf[i] == -INFINITY ? 0.0 : exp2(fmax(2.0 * (lf[i] + i * l2lam - M), -1000.0));
+        ef[i] = t;
+        sf += t;
+    }
+    for (int j = 0; j <= n; ++j) {
+        double t = lg[j] == -INFINITY ? 0.0 : exp2(fmax(2.0 * (lg[j] + j * l2lam - M), -1000.0));
+        eg[j] = t;
+        sg += t;
+    }
+    double row = 0.0;
+    if (n > 0) row += 0.5 * n * (2.0 * M + log2(sf));
+    if (m > 0) row += 0.5 * m * (2.0 * M + log2(sg));
+    double col = 0.0;
+    for (int c = 0; c < m + n; ++c) {
+        double sc = 0.0;
+        // f rows r = 0..n-1 hold f_{m-(c-r)} in column c when 0 <= c - r <= m
+        int r0 = c - m > 0 ? c - m : 0, r1 = c < n - 1 ? c : n - 1;
+        for (int r = r0; r <= r1; ++r) sc += ef[m - (c - r)];
+        // g rows r = 0..m-1 hold g_{n-(c-r)} when 0 <= c - r <= n
+        r0 = c - n > 0 ? c - n : 0;
+        r1 = c < m - 1 ? c : m - 1;
+        for (int r = r0; r <= r1; ++r) sc += eg[n - (c - r)];
+        col += sc > 0.0 ? 0.5 * (2.0 * M + log2(sc)) : -INFINITY;
+    }
+    double b = row < col ? row : col;
+    // sums of k non-negative doubles carry a relative error below k 2^-53; the
+    // planner adds two bits and a relative margin on top of this value
+    return b - (double)m * n * l2lam;
+}
+
+// log2 lambda values the planner tries (the bound is valid for each; the
+// smallest is used)
+constexpr int kBoundLambdas = 13;
+GBR_HD double bound_lambda(int l) {
+    const double v[kBoundLambdas] = {0.0, 0.25, 0.5, 0.75, 1.0, 1.5, 2.0, 3.0, 4.0, 5.0, 6.0, -0.5, -1.0};
+    return v[l];
+}
+
+GBR_HD double best_scaled_bound(const double *lf, int m, const double *lg, int n, double *ef, double *eg) {
+    if (m <= 0 && n <= 0) return 0.0;
+    double best = INFINITY;
+    for (int l = 0; l < kBoundLambdas; ++l) {
+        double b = scaled_hadamard_log2(lf, m, lg, n, bound_lambda(l), ef, eg);
+        if (b < best) best = b;
+    }
+    return best;
+}
 
 // Host-side bound arithmetic shared by gbr_resultant_info and the planner.
 GBR_HD int32_t degree_bound(const PairBound &b) {

@@ -83,82 +83,163 @@ __device__ __forceinline__ const uint64_t *coef_ptr(const uint64_t *coef, const 
     return coef + d.off + ((int64_t)r * d.rstride + (int64_t)c * d.cstride) * d.words;
 }
 
-// Scans one polynomial row by row.  For disc, also produces the rows of
-// g = d f / d var on the fly: g_r = (r+1) f_{r+1}.
-__global__ void k_bounds(ResLaunch L) {
+// Scans one polynomial row by row (one warp per pair): row degrees, log2 of the
+// row 1-norms, degrees.  For disc, g = d f / d var is formed on the fly:
+// g_r = (r+1) f_{r+1}.  The row norms are kept in shared memory and every lane
+// evaluates the scaled Hadamard bound for one lambda; the minimum is kept.
+constexpr int kBoundsWarps = 4;
+
+// log2 of the 1-norm of a row: exact 128-bit sum for int64 coefficients, else
+// a log-sum-exp over the coefficients' log2 magnitudes.
+__device__ double row_log2_norm(const uint64_t *coef, const PolyDesc &P, int r, int lane, int &cmax) {
+    cmax = -1;
+    if (P.words == 1) {
+        uint64_t lo = 0, hi = 0;
+        for (int c = lane; c <= P.cols; c += 32) {
+            int64_t v = (int64_t)coef_ptr(coef, P, r, c)[0];
+            if (v) {
+                cmax = c;
+                uint64_t a = v < 0 ? 0ull - (uint64_t)v : (uint64_t)v;
+                lo += a;
+                hi += lo < a;
+            }
+        }
+        for (int o = 16; o; o >>= 1) {
+            uint64_t olo = __shfl_xor_sync(0xffffffffu, lo, o), ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+            lo += olo;
+            hi += ohi + (lo < olo);
+            cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+        }
+        if (!lo && !hi) return -INFINITY;
+        double v = (double)hi * 0x1p64 + (double)lo;
+        return log2(v) + 1e-12;
+    }
+    Lse nrm;
+    nrm.init();
+    for (int c = lane; c <= P.cols; c += 32) {
+        double a = coef_log2abs(coef_ptr(coef, P, r, c), P.words);
+        if (a != -INFINITY) {
+            cmax = c;
+            nrm.add(a);
+        }
+    }
+    for (int o = 16; o; o >>= 1) cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+    warp_lse(nrm);
+    return nrm.log2v();
+}
+
+// Warp-parallel evaluation of scaled_hadamard_log2: lanes split the rows for the
+// scaled squared norms and the columns for their logarithms.
+__device__ double scaled_hadamard_log2_warp(const double *lf, int m, const double *lg, int n, double l2lam,
+                                            double *ef, double *eg, int lane) {
+    double M = -INFINITY;
+    for (int i = lane; i <= m; i += 32)
+        if (lf[i] != -INFINITY) M = fmax(M, lf[i] + i * l2lam);
+    for (int j = lane; j <= n; j += 32)
+        if (lg[j] != -INFINITY) M = fmax(M, lg[j] + j * l2lam);
+    for (int o = 16; o; o >>= 1) M = fmax(M, __shfl_xor_sync(0xffffffffu, M, o));
+    double sf = 0.0, sg = 0.0;
+    for (int i = lane; i <= m; i += 32) {
+        double t = lf[i] == -INFINITY ? 0.0 : exp2(fmax(2.0 * (lf[i] + i * l2lam - M), -1000.0));
+        ef[i] = t;
+        sf += t;
+    }
+    for (int j = lane; j <= n; j += 32) {
+        double t = lg[j] == -INFINITY ? 0.0 : exp2(fmax(2.0 * (lg[j] + j * l2lam - M), -1000.0));
+        eg[j] = t;
+        sg += t;
+    }
+    for (int o = 16; o; o >>= 1) {
+        sf += __shfl_xor_sync(0xffffffffu, sf, o);
+        sg += __shfl_xor_sync(0xffffffffu, sg, o);
+    }
+    __syncwarp();
+    double row = 0.0;
+    if (n > 0) row += 0.5 * n * (2.0 * M + log2(sf));
+    if (m > 0) row += 0.5 * m * (2.0 * M + log2(sg));
+    double col = 0.0;
+    for (int c = lane; c < m + n; c += 32) {
+        double sc = 0.0;
+        int r0 = c - m > 0 ? c - m : 0, r1 = c < n - 1 ? c : n - 1;
+        for (int r = r0; r <= r1; ++r) sc += ef[m - (c - r)];
+        r0 = c - n > 0 ? c - n : 0;
+        r1 = c < m - 1 ? c : m - 1;
+        for (int r = r0; r <= r1; ++r) sc += eg[n - (c - r)];
+        col += sc > 0.0 ? 0.5 * (2.0 * M + log2(sc)) : -INFINITY;
+    }
+    for (int o = 16; o; o >>= 1) col += __shfl_xor_sync(0xffffffffu, col, o);
+    __syncwarp();
+    return fmin(row, col) - (double)m * n * l2lam;
+}
+
+__global__ void __launch_bounds__(kBoundsWarps * 32) k_bounds(ResLaunch L) {
+    __shared__ double lnf[kBoundsWarps][GBR_MAX_YDEG + 2], lng[kBoundsWarps][GBR_MAX_YDEG + 2];
+    __shared__ double ebuf[kBoundsWarps][2][GBR_MAX_YDEG + 2];
+    const int wib = threadIdx.x >> 5;
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (warp >= L.npairs) return;
     const PairDesc D = L.desc[warp];
     PairBound B;
+    B.tg = 0;
     for (int which = 0; which < 2; ++which) {
         if (which == 1 && D.disc) break;
         const PolyDesc &P = which ? D.g : D.f;
+        double *ln_out = which ? lng[wib] : lnf[wib];
         int mdeg = -1, dxmax = -1, td = -1, terms = 0, terms_upto = 0;
-        Lse sq;     // log2 sum_r ||row_r||_1^2
-        sq.init();
         int mdeg_g = -1, dx_g = -1, td_g = -1, terms_g = 0, terms_g_upto = 0;
-        Lse sq_g;
-        sq_g.init();
         for (int r = 0; r <= P.rows; ++r) {
-            int cmax = -1;
-            Lse nrm;
-            nrm.init();
-            for (int c = lane; c <= P.cols; c += 32) {
-                double a = coef_log2abs(coef_ptr(L.coef, P, r, c), P.words);
-                if (a != -INFINITY) {
-                    cmax = c;
-                    nrm.add(a);
-                }
+            int cmax;
+            const double ln = row_log2_norm(L.coef, P, r, lane, cmax);
+            if (lane == 0) {
+                L.rowdeg[P.rowdeg_off + r] = cmax;
+                if (r <= GBR_MAX_YDEG) ln_out[r] = ln;
             }
-            for (int o = 16; o; o >>= 1) cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
-            warp_lse(nrm);
-            double ln = nrm.log2v();
-            if (lane == 0) L.rowdeg[P.rowdeg_off + r] = cmax;
             terms += cmax + 1;
             if (cmax >= 0) {
                 mdeg = r;
                 terms_upto = terms;
                 dxmax = max(dxmax, cmax);
                 td = max(td, r + cmax);
-                sq.add(2.0 * ln);
             }
             if (which == 0 && D.disc && r >= 1) {
-                if (lane == 0) L.rowdeg[D.g.rowdeg_off + r - 1] = cmax;
+                if (lane == 0) {
+                    L.rowdeg[D.g.rowdeg_off + r - 1] = cmax;
+                    if (r - 1 <= GBR_MAX_YDEG) lng[wib][r - 1] = ln == -INFINITY ? ln : ln + log2((double)r);
+                }
                 terms_g += cmax + 1;
                 if (cmax >= 0) {
                     mdeg_g = r - 1;
                     terms_g_upto = terms_g;
                     dx_g = max(dx_g, cmax);
                     td_g = max(td_g, r - 1 + cmax);
-                    sq_g.add(2.0 * (ln + log2((double)r)));
                 }
             }
         }
         if (which == 0) {
             B.m = mdeg; B.dxf = dxmax; B.tdf = td; B.tf = terms_upto;
-            B.log2B = sq.log2v();           // temporarily: log2 sum ||f_i||^2
             if (D.disc) {
                 B.n = mdeg_g; B.dxg = dx_g; B.tdg = td_g; B.tg = terms_g_upto;
-                // log2B = (n/2) log2 sum f + (m/2) log2 sum g
-                double lf = sq.log2v(), lg = sq_g.log2v();
-                if (B.m >= 0 && B.n >= 0) B.log2B = 0.5 * B.n * lf + 0.5 * B.m * lg;
-                else B.log2B = 0.0;
             }
         } else {
             B.n = mdeg; B.dxg = dxmax; B.tdg = td; B.tg = terms_upto;
-            double lf = B.log2B, lg = sq.log2v();
-            if (B.m >= 0 && B.n >= 0) B.log2B = 0.5 * B.n * lf + 0.5 * B.m * lg;
-            else B.log2B = 0.0;
         }
     }
-    if (B.m == 0 && B.n == 0) B.log2B = 0.0;
+    __syncwarp();
+    double lb = 0.0;
+    if (B.m >= 0 && B.n >= 0 && B.m <= GBR_MAX_YDEG && B.n <= GBR_MAX_YDEG && (B.m > 0 || B.n > 0)) {
+        lb = INFINITY;
+        for (int l = 0; l < kBoundLambdas; ++l)
+            lb = fmin(lb, scaled_hadamard_log2_warp(lnf[wib], B.m, lng[wib], B.n, bound_lambda(l), ebuf[wib][0],
+                                                    ebuf[wib][1], lane));
+    }
+    B.log2B = lb;
     if (lane == 0) L.bounds[warp] = B;
 }
 
 cudaError_t launch_bounds(const ResLaunch &L, cudaStream_t s) {
     if (L.npairs <= 0) return cudaSuccess;
-    int threads = 128;
+    int threads = kBoundsWarps * 32;
     int blocks = (L.npairs * 32 + threads - 1) / threads;
     k_bounds<<<blocks, threads, 0, s>>>(L);
     return cudaGetLastError();

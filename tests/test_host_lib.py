@@ -134,3 +134,41 @@ def test_status_strings_and_bad_create(lib):
     h = C.c_void_p()
     assert lib.gbr_create(C.byref(h), 0, 1000, None, None) == N.EINVAL   # budget below 1 MiB
     assert lib.gbr_create(None, 0, 1 << 30, None, None) == N.EINVAL
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_scaled_bound_holds_on_varied_shapes(lib, seed):
+    """The planner's bound (minimum of row/column Hadamard bounds over scalings y ->
+    lambda y) is at least the true size of every coefficient, for dense boxes,
+    total-degree polynomials, sparse polynomials with large leading coefficients and
+    products with planted roots."""
+    from paper_1103_4697_gb300.api import resultant_info
+
+    rng = random.Random(1000 + seed)
+    kind = seed % 4
+    if kind == 0:
+        f, g = W.small_dense_pair(seed, rng.randint(1, 7), rng.randint(2, 30))
+    elif kind == 1:
+        f = W.dense_box(W.Stream(seed), rng.randint(0, 5), rng.randint(1, 6), rng.randint(2, 40))
+        g = W.dense_box(W.Stream(seed + 99), rng.randint(0, 5), rng.randint(1, 6), rng.randint(2, 40))
+    elif kind == 2:
+        m, n = rng.randint(1, 6), rng.randint(1, 6)
+        f = [[0] * 4 for _ in range(m + 1)]
+        g = [[0] * 4 for _ in range(n + 1)]
+        f[m][rng.randint(0, 3)] = rng.choice([-1, 1]) * rng.randint(1, 2 ** 40)
+        g[n][rng.randint(0, 3)] = rng.choice([-1, 1]) * rng.randint(1, 2 ** 40)
+        for _ in range(4):
+            f[rng.randint(0, m)][rng.randint(0, 3)] = rng.randint(-2 ** 20, 2 ** 20)
+            g[rng.randint(0, n)][rng.randint(0, 3)] = rng.randint(-2 ** 20, 2 ** 20)
+    else:
+        f, g, *_ = W.planted_roots_pair(seed, rng.randint(1, 5), rng.randint(1, 5), bits=rng.randint(2, 12))
+    if O.ydeg(f) < 0 or O.ydeg(g) < 0:
+        return
+    for disc in (False, True):
+        info = resultant_info(f, None if disc else g, disc=disc)
+        R = O.disc_res(f) if disc else O.res_subres(f, g)
+        if info["m"] < 0 or info["n"] < 0:
+            assert R == ()
+            continue
+        assert all(c == 0 or math.log2(abs(c)) <= info["log2_bound"] + 1e-9 for c in R), (info, disc)
+        assert len(R) - 1 <= info["deg_bound"]
