@@ -116,6 +116,8 @@ typedef struct {
     int64_t modmul;           /* algorithmic modular multiplications, whole path */
     int64_t modmul_evalres;   /* of the evaluation + elimination stage alone */
     int64_t h2d_bytes, d2h_bytes;
+    int64_t dropped_points;   /* GBR_OPT_DROP_UNLUCKY: evaluation points flagged unlucky and replaced */
+    int64_t dropped_primes;   /* GBR_OPT_DROP_UNLUCKY: primes skipped because a leading coefficient vanishes */
 } gbr_stats;
 
 /* ------------------------------------------------------------------ context */

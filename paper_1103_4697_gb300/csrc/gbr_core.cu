@@ -602,7 +602,7 @@ void gbr_free_resident_locked(gbr_ctx *c, gbr_resident *r) {
     if (!r) return;
     for (void *p : {(void *)r->d_coef, (void *)r->d_desc, (void *)r->d_rowdeg, (void *)r->d_bounds, (void *)r->d_deg,
                     (void *)r->d_planblk, (void *)r->d_res, (void *)r->d_val, (void *)r->d_cf, (void *)r->d_out,
-                    (void *)r->d_sign})
+                    (void *)r->d_sign, (void *)r->d_flags, (void *)r->d_gtab})
         c->dfree(p);
     if (r->gexec) cudaGraphExecDestroy(r->gexec);
     delete r;
@@ -686,35 +686,28 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
     e = cudaMemcpyAsync(hb, r->d_bounds, sizeof(PairBound) * n, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "bounds readback", e);
-    // ---- A0 (host half): plan
+    // ---- A0 (host half): degrees, point counts and prime counts
     std::vector<PairPlan> &plan = r->h_plan;
     plan.assign(n, PairPlan{});
-    int64_t res_w = 0, val_w = 0, out_w = 0, sign_b = 0;
-    int Kmax = 1, Pmax = 1, Lmax = 1;
-    HostList red, interp, crt;
-    std::map<int, HostList> evb;
-    std::map<int, std::vector<int32_t>> pgroups;   // pairs by point count
-    int64_t subproblems = 0;
+    const bool drop = c->drop_unlucky != 0;
+    int kc_max = 0;
     for (int q = 0; q < n; ++q) {
         const PairBound &b = hb[q];
         PairPlan &p = plan[q];
         p.disc = r->disc;
         p.rowdeg_f = r->h_desc[q].f.rowdeg_off;
         p.rowdeg_g = r->h_desc[q].g.rowdeg_off;
+        p.pmap_off = -1;
+        p.flag_off = -1;
+        p.gtab_off = -1;
+        p.m = b.m;
+        p.n = b.n;
         if (b.m < 0 || b.n < 0) {
             p.flags = PLAN_ZERO;
-            p.m = b.m;
-            p.n = b.n;
-            p.res_off = res_w;
-            p.val_off = val_w;
-            p.out_off = out_w;
-            p.sign_off = sign_b;
             continue;
         }
         if (b.m > GBR_MAX_YDEG || b.n > GBR_MAX_YDEG)
             return c->fail(GBR_ELIMIT, "degree in the eliminated variable above GBR_MAX_YDEG");
-        p.m = b.m;
-        p.n = b.n;
         p.dxf = std::max(b.dxf, 0);
         p.dxg = std::max(b.dxg, 0);
         int64_t D = degree_bound(b);
@@ -724,27 +717,93 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
         int k = primes_for_bits(bits);
         if (k < 0 || k + c->extra_primes > GBR_MAX_PRIMES)
             return c->fail(GBR_ELIMIT, "coefficient bound needs more than GBR_MAX_PRIMES primes");
-        k += c->extra_primes;
-        p.k = k;
+        p.k = k + c->extra_primes;
+        // drop mode: evaluate at spare points too; a leading coefficient of degree
+        // d vanishes at no more than d points modulo a prime that does not kill it
+        p.Pe = drop ? p.P + std::max(b.lcdf, 0) + std::max(b.lcdg, 0) : p.P;
+        if (p.Pe > GBR_MAX_POINTS + 2 * 4096) return c->fail(GBR_ELIMIT, "too many spare points");
+        kc_max = std::max(kc_max, p.k + 32);
+    }
+    // ---- A6 (drop mode): primes that kill a leading coefficient are skipped
+    std::vector<int32_t> pmap;
+    int64_t dropped_primes = 0;
+    if (drop && kc_max > 0) {
+        const int kc = std::min(kc_max, num_primes());
+        uint8_t *d_uf = (uint8_t *)c->dalloc((size_t)n * kc);
+        if (!d_uf) return c->fail(GBR_ENOMEM, "device budget too small for the unlucky-prime flags");
+        std::vector<uint8_t> uf((size_t)n * kc);
+        e = launch_unlucky_primes(L, kc, d_uf, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(uf.data(), d_uf, uf.size(), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        c->dfree(d_uf);
+        if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "unlucky-prime check", e);
+        for (int q = 0; q < n; ++q) {
+            PairPlan &p = plan[q];
+            if (p.flags & PLAN_ZERO) continue;
+            bool any = false;
+            for (int i = 0; i < p.k; ++i) any = any || uf[(size_t)q * kc + i];
+            if (!any) continue;
+            p.pmap_off = (int32_t)pmap.size();
+            int got = 0;
+            for (int i = 0; i < kc && got < p.k; ++i) {
+                if (uf[(size_t)q * kc + i]) {
+                    ++dropped_primes;
+                    continue;
+                }
+                pmap.push_back(i);
+                ++got;
+            }
+            if (got < p.k) return c->fail(GBR_ELIMIT, "too many primes kill a leading coefficient");
+        }
+    }
+    // ---- buffer offsets and work lists
+    int64_t res_w = 0, val_w = 0, cf_w = 0, flag_b = 0, gtab_w = 0, out_w = 0, sign_b = 0;
+    int Kmax = 1, Pmax = 1, Lmax = 1;
+    HostList red, interp, crt;
+    std::map<int, HostList> evb;
+    std::map<int, std::vector<int32_t>> pgroups;   // pairs by point count
+    std::vector<int32_t> mapped;                    // pairs with their own Garner table
+    int kmapped = 0;
+    int64_t subproblems = 0;
+    for (int q = 0; q < n; ++q) {
+        const PairBound &b = hb[q];
+        PairPlan &p = plan[q];
+        p.res_off = res_w;
+        p.val_off = val_w;
+        p.cf_off = cf_w;
+        p.out_off = out_w;
+        p.sign_off = sign_b;
+        if (p.flags & PLAN_ZERO) continue;
+        const int k = p.k;
         p.L = (31 * k + 31) / 32;
         p.S = (p.dxf + 1) * rows4(p.m) + (p.dxg + 1) * rows4(p.n);
-        p.res_off = res_w;
         res_w += (int64_t)k * p.S;
-        p.val_off = val_w;
-        val_w += (int64_t)k * p.P;
-        p.out_off = out_w;
+        val_w += (int64_t)k * p.Pe;
+        cf_w += (int64_t)k * p.P;
         out_w += (int64_t)p.P * p.L;
-        p.sign_off = sign_b;
         sign_b += p.P;
-        Kmax = std::max(Kmax, k);
-        Pmax = std::max(Pmax, p.P);
+        if (drop) {
+            p.flag_off = flag_b;
+            flag_b += (int64_t)k * p.Pe;
+        }
+        if (p.pmap_off >= 0) {
+            p.gtab_off = gtab_w;
+            gtab_w += k + (int64_t)k * (k - 1) / 2;
+            mapped.push_back(q);
+            kmapped = std::max(kmapped, k);
+        }
+        Kmax = std::max(Kmax, p.pmap_off >= 0 ? pmap[p.pmap_off + k - 1] + 1 : k);
+        Pmax = std::max(Pmax, p.Pe);
         Lmax = std::max(Lmax, p.L);
         red.add(q, p.S);
         int key = ((std::max(p.m, p.n) + 1) + 3) / 4 * 4;
-        evb[key].add(q, (int64_t)k * p.P);
-        pgroups[p.P].push_back(q);
+        evb[key].add(q, (int64_t)k * p.Pe);
+        // the contraction serves pairs whose points are exactly 0..P-1 and whose
+        // primes are the table prefix
+        if (p.pmap_off < 0 && p.Pe == p.P) pgroups[p.P].push_back(q);
+        else interp.add(q, k);
         crt.add(q, p.P);
-        subproblems += (int64_t)k * p.P;
+        subproblems += (int64_t)k * p.Pe;
         int64_t ev = (int64_t)k * p.P * (b.tf + b.tg + 2LL * p.m * p.n);
         st.modmul_evalres += ev;
         st.modmul += ev + (int64_t)k * p.P * (p.P - 1) + (int64_t)p.P * k * (k - 1) / 2;
@@ -791,10 +850,18 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
     size_t o_gemm = (blk.size() + 7) / 8 * 8;
     blk.resize(o_gemm + gemm_pairs.size() * 4 + 4);
     if (!gemm_pairs.empty()) std::memcpy(blk.data() + o_gemm, gemm_pairs.data(), gemm_pairs.size() * 4);
+    size_t o_pmap = (blk.size() + 7) / 8 * 8;
+    blk.resize(o_pmap + pmap.size() * 4 + 4);
+    if (!pmap.empty()) std::memcpy(blk.data() + o_pmap, pmap.data(), pmap.size() * 4);
+    size_t o_mapped = (blk.size() + 7) / 8 * 8;
+    blk.resize(o_mapped + mapped.size() * 4 + 4);
+    if (!mapped.empty()) std::memcpy(blk.data() + o_mapped, mapped.data(), mapped.size() * 4);
     if (ensure_buf(c, (void **)&r->d_planblk, &r->planblk_cap, blk.size()) ||
         ensure_buf(c, (void **)&r->d_res, &r->res_cap, res_w * 4) ||
         ensure_buf(c, (void **)&r->d_val, &r->val_cap, val_w * 4) ||
-        ensure_buf(c, (void **)&r->d_cf, &r->cf_cap, val_w * 4) ||
+        ensure_buf(c, (void **)&r->d_cf, &r->cf_cap, cf_w * 4) ||
+        ensure_buf(c, (void **)&r->d_flags, &r->flags_cap, flag_b) ||
+        ensure_buf(c, (void **)&r->d_gtab, &r->gtab_cap, gtab_w * 4) ||
         ensure_buf(c, (void **)&r->d_out, &r->out_cap, out_w * 4) ||
         ensure_buf(c, (void **)&r->d_sign, &r->sign_cap, sign_b))
         return c->fail(GBR_ENOMEM, "device budget too small for this batch");
@@ -803,7 +870,7 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
     std::memcpy(hp, blk.data(), blk.size());
     e = cudaMemcpyAsync(r->d_planblk, hp, blk.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->d_deg, 0xff, sizeof(int32_t) * n, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, 16, s);
     if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "plan upload", e);
     auto mk = [&](size_t op, size_t os, const HostList &h) {
         WorkList w;
@@ -824,8 +891,17 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
     L.out = r->d_out;
     L.sign = r->d_sign;
     L.drop_unlucky = c->drop_unlucky;
+    L.pmap = (const int32_t *)(r->d_planblk + o_pmap);
+    L.pflags = r->d_flags;
+    L.gtab = r->d_gtab;
+    L.dropped = (unsigned long long *)(c->d_err + 2);
     if (c->stats_on) cudaEventRecord(c->ev[1], s);
     int64_t kernels = 1;
+    if (!mapped.empty()) {
+        e = launch_pair_garner(L, (const int32_t *)(r->d_planblk + o_mapped), (int)mapped.size(), kmapped, r->d_gtab, s);
+        if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "pair Garner tables", e);
+        kernels++;
+    }
     e = launch_reduce(L, mk(o_red_p, o_red_s, red), s);
     kernels++;
     if (c->stats_on) cudaEventRecord(c->ev[2], s);
@@ -853,11 +929,13 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
     kernels++;
     if (c->stats_on) cudaEventRecord(c->ev[5], s);
     if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "stage launch", e);
-    int32_t herr = 0;
-    e = cudaMemcpyAsync(&herr, c->d_err, 4, cudaMemcpyDeviceToHost, s);
+    int32_t herr[4] = {0, 0, 0, 0};
+    e = cudaMemcpyAsync(herr, c->d_err, 16, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "resultant stages", e);
-    if (herr) return c->fail(GBR_EDEVICE, "device-side consistency check failed");
+    if (herr[0]) return c->fail(GBR_EDEVICE, "device-side consistency check failed");
+    st.dropped_points = (int64_t)((uint64_t)(uint32_t)herr[2] | ((uint64_t)(uint32_t)herr[3] << 32));
+    st.dropped_primes = dropped_primes;
     r->out_words = out_w;
     r->sign_bytes = sign_b;
     r->ran = true;

@@ -101,6 +101,10 @@ struct gbr_resident {
     size_t res_cap = 0, val_cap = 0, cf_cap = 0, out_cap = 0;
     int8_t *d_sign = nullptr;
     size_t sign_cap = 0;
+    uint8_t *d_flags = nullptr;
+    size_t flags_cap = 0;
+    uint32_t *d_gtab = nullptr;
+    size_t gtab_cap = 0;
     int64_t out_words = 0, sign_bytes = 0;
     bool ran = false;
     cudaGraphExec_t gexec = nullptr;

@@ -51,18 +51,25 @@ struct PairBound {
     int32_t dxf, dxg;   // actual degrees in the other variable
     int32_t tdf, tdg;   // total degrees
     int32_t tf, tg;     // Horner terms: sum over rows <= degree of (row degree + 1)
+    int32_t lcdf, lcdg; // degrees (in the other variable) of the leading coefficients
+    int32_t pad;
     double log2B;       // upper bound on log2 of the Hadamard bound
 };
 
 // Per-pair plan, written by the host, read by every stage kernel.
 struct PairPlan {
     int32_t m, n, dxf, dxg;
-    int32_t P;          // evaluation points = degree bound + 1
+    int32_t P;          // interpolation points = degree bound + 1
+    int32_t Pe;         // evaluated points: P, or P + spares when unlucky points are dropped
     int32_t k;          // primes
     int32_t L;          // 32-bit limbs per output coefficient
     int32_t S;          // residue words per prime: (dxf+1) rows4(m) + (dxg+1) rows4(n)
+    int32_t pmap_off;   // -1: primes are table entries 0..k-1; else their table indices at pmap[pmap_off..]
     int64_t res_off;    // residues [prime][S]                       (u32 words)
-    int64_t val_off;    // values / coefficients [prime][P]          (u32 words)
+    int64_t val_off;    // values [prime][Pe]                        (u32 words)
+    int64_t cf_off;     // coefficients mod p [prime][P]             (u32 words)
+    int64_t flag_off;   // -1, or unlucky-point flags [prime][Pe]    (bytes)
+    int64_t gtab_off;   // -1: prefix Garner table; else this pair's table (k + k(k-1)/2 words)
     int64_t out_off;    // output magnitudes [coef][L]               (u32 words)
     int64_t sign_off;   // output signs [coef]                       (bytes)
     int32_t rowdeg_f, rowdeg_g;   // offsets of row degree arrays
@@ -172,9 +179,17 @@ struct ResLaunch {
     int8_t *sign;                // output signs
     int32_t *deg;                // per pair output degree
     int32_t *err;                // device error word (0 = ok)
+    const int32_t *pmap;         // per-pair prime maps (drop mode)
+    uint8_t *pflags;             // unlucky-point flags (drop mode)
+    const uint32_t *gtab;        // per-pair Garner tables (drop mode)
+    unsigned long long *dropped; // count of flagged points
     int32_t npairs;
     int32_t drop_unlucky;
 };
+
+__host__ __device__ __forceinline__ int prime_of(const PairPlan &P, const int32_t *pmap, int i) {
+    return P.pmap_off < 0 ? i : pmap[P.pmap_off + i];
+}
 
 // Work lists (device arrays, built by the host planner).
 struct WorkList {
@@ -199,6 +214,9 @@ cudaError_t launch_evalres(const ResLaunch &L, const WorkList &w, int slots_f, i
 cudaError_t launch_interp(const ResLaunch &L, const WorkList &w, int maxP, cudaStream_t s);
 cudaError_t launch_crt(const ResLaunch &L, const WorkList &w, int maxL, cudaStream_t s);
 cudaError_t launch_vinv(const ModP *mods, int P, int K, uint32_t *out, cudaStream_t s);
+cudaError_t launch_unlucky_primes(const ResLaunch &L, int kc, uint8_t *out, cudaStream_t s);
+cudaError_t launch_pair_garner(const ResLaunch &L, const int32_t *pairs, int n, int kmax, uint32_t *gtab,
+                               cudaStream_t s);
 cudaError_t launch_interp_gemm(const ResLaunch &L, const int32_t *gpairs, int npairs, int P, int K,
                                const uint32_t *vinv, cudaStream_t s);
 cudaError_t launch_zero_init(const ResLaunch &L, cudaStream_t s);

@@ -17,6 +17,8 @@
 //            symmetric lift, magnitude limbs
 #include <math.h>
 
+#include <algorithm>
+
 #include "gbr_internal.h"
 
 namespace gbr {
@@ -182,12 +184,14 @@ __global__ void __launch_bounds__(kBoundsWarps * 32) k_bounds(ResLaunch L) {
     const PairDesc D = L.desc[warp];
     PairBound B;
     B.tg = 0;
+    B.lcdg = -1;
+    B.pad = 0;
     for (int which = 0; which < 2; ++which) {
         if (which == 1 && D.disc) break;
         const PolyDesc &P = which ? D.g : D.f;
         double *ln_out = which ? lng[wib] : lnf[wib];
-        int mdeg = -1, dxmax = -1, td = -1, terms = 0, terms_upto = 0;
-        int mdeg_g = -1, dx_g = -1, td_g = -1, terms_g = 0, terms_g_upto = 0;
+        int mdeg = -1, dxmax = -1, td = -1, terms = 0, terms_upto = 0, lcd = -1;
+        int mdeg_g = -1, dx_g = -1, td_g = -1, terms_g = 0, terms_g_upto = 0, lcd_g = -1;
         for (int r = 0; r <= P.rows; ++r) {
             int cmax;
             const double ln = row_log2_norm(L.coef, P, r, lane, cmax);
@@ -198,6 +202,7 @@ __global__ void __launch_bounds__(kBoundsWarps * 32) k_bounds(ResLaunch L) {
             terms += cmax + 1;
             if (cmax >= 0) {
                 mdeg = r;
+                lcd = cmax;
                 terms_upto = terms;
                 dxmax = max(dxmax, cmax);
                 td = max(td, r + cmax);
@@ -210,6 +215,7 @@ __global__ void __launch_bounds__(kBoundsWarps * 32) k_bounds(ResLaunch L) {
                 terms_g += cmax + 1;
                 if (cmax >= 0) {
                     mdeg_g = r - 1;
+                    lcd_g = cmax;
                     terms_g_upto = terms_g;
                     dx_g = max(dx_g, cmax);
                     td_g = max(td_g, r - 1 + cmax);
@@ -217,12 +223,12 @@ __global__ void __launch_bounds__(kBoundsWarps * 32) k_bounds(ResLaunch L) {
             }
         }
         if (which == 0) {
-            B.m = mdeg; B.dxf = dxmax; B.tdf = td; B.tf = terms_upto;
+            B.m = mdeg; B.dxf = dxmax; B.tdf = td; B.tf = terms_upto; B.lcdf = lcd;
             if (D.disc) {
-                B.n = mdeg_g; B.dxg = dx_g; B.tdg = td_g; B.tg = terms_g_upto;
+                B.n = mdeg_g; B.dxg = dx_g; B.tdg = td_g; B.tg = terms_g_upto; B.lcdg = lcd_g;
             }
         } else {
-            B.n = mdeg; B.dxg = dxmax; B.tdg = td; B.tg = terms_upto;
+            B.n = mdeg; B.dxg = dxmax; B.tdg = td; B.tg = terms_upto; B.lcdg = lcd;
         }
     }
     __syncwarp();
@@ -286,7 +292,7 @@ __global__ void k_reduce(ResLaunch L, WorkList w) {
         int W = src->words;
         for (int i = 0; i < W; ++i) wbuf[i] = cp[i];
         for (int i = 0; i < P.k; ++i) {
-            ModP M = L.mods[i];
+            ModP M = L.mods[prime_of(P, L.pmap, i)];
             uint32_t r = mp_from_words(wbuf, W, M);
             if (mult) r = mp_mul(r, mp_to((uint32_t)mult, M), M);
             dst[(int64_t)i * P.S] = mp_mul(r, M.r2, M);   // c R^2: one reduction per Horner step
@@ -464,9 +470,9 @@ __global__ void k_evalres(ResLaunch L, WorkList w, int SF, int SG) {
         int q = w.pairs[bi];
         int64_t local = item - w.start[bi];
         const PairPlan &P = L.plan[q];
-        int i = (int)(local / P.P);
-        int j = (int)(local % P.P);
-        const ModP M = L.mods[i];
+        int i = (int)(local / P.Pe);
+        int j = (int)(local % P.Pe);
+        const ModP M = L.mods[prime_of(P, L.pmap, i)];
         const uint32_t a = mp_to((uint32_t)j, M);
         const int rf4 = rows4(P.m), rg4 = rows4(P.n);
         const uint32_t *rf = L.res + P.res_off + (int64_t)i * P.S;
@@ -475,7 +481,15 @@ __global__ void k_evalres(ResLaunch L, WorkList w, int SF, int SG) {
         const int32_t *dgg = L.rowdeg + P.rowdeg_g;
         for (int r0 = 0; r0 <= P.m; r0 += 4) eval4(rf, rf4, dgf, P.m + 1, r0, a, M, Fs, BS);
         for (int r0 = 0; r0 <= P.n; r0 += 4) eval4(rg, rg4, dgg, P.n + 1, r0, a, M, Gs, BS);
-        L.val[P.val_off + (int64_t)i * P.P + j] = res_formal(Fs, P.m, Gs, P.n, BS, M);
+        if (P.flag_off >= 0) {
+            // a point where a leading coefficient vanishes is unlucky: flag it, so
+            // interpolation takes the spare points instead (its formal-degree value
+            // below is still exact)
+            const uint8_t unlucky = Fs[0] == 0u || Gs[0] == 0u;
+            L.pflags[P.flag_off + (int64_t)i * P.Pe + j] = unlucky;
+            if (unlucky) atomicAdd(L.dropped, 1ull);
+        }
+        L.val[P.val_off + (int64_t)i * P.Pe + j] = res_formal(Fs, P.m, Gs, P.n, BS, M);
     }
 }
 
@@ -484,43 +498,64 @@ __global__ void k_evalres(ResLaunch L, WorkList w, int SF, int SG) {
 __global__ void k_interp(ResLaunch L, WorkList w, int maxP) {
     extern __shared__ uint32_t smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    uint32_t *V = smem + (size_t)wid * 2 * maxP;
+    uint32_t *V = smem + (size_t)wid * 3 * maxP;
     uint32_t *Wp = V + maxP;
+    uint32_t *X = Wp + maxP;     // the integer points x_0 < x_1 < ... actually used
     for (int64_t item = (int64_t)blockIdx.x * nw + wid; item < w.total; item += (int64_t)gridDim.x * nw) {
         int bi = wl_find(w.start, w.n, item);
         int q = w.pairs[bi];
         int i = (int)(item - w.start[bi]);
         const PairPlan &P = L.plan[q];
         const int Pn = P.P;
-        const ModP M = L.mods[i];
-        uint32_t *g = L.val + P.val_off + (int64_t)i * Pn;
-        for (int t = lane; t < Pn; t += 32) {
-            V[t] = g[t];
-            Wp[t] = 0;
+        const int pt = prime_of(P, L.pmap, i);
+        const ModP M = L.mods[pt];
+        const uint32_t *g = L.val + P.val_off + (int64_t)i * P.Pe;
+        if (P.flag_off < 0) {
+            for (int t = lane; t < Pn; t += 32) {
+                V[t] = g[t];
+                X[t] = t;
+            }
+        } else {
+            // keep the first Pn points whose flag is clear
+            const uint8_t *fl = L.pflags + P.flag_off + (int64_t)i * P.Pe;
+            int cnt = 0;
+            for (int base = 0; base < P.Pe && cnt < Pn; base += 32) {
+                const int j = base + lane;
+                const bool good = j < P.Pe && !fl[j];
+                const unsigned bal = __ballot_sync(0xffffffffu, good);
+                const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+                if (good && pos < Pn) {
+                    X[pos] = j;
+                    V[pos] = g[j];
+                }
+                cnt += __popc(bal);
+            }
+            if (cnt < Pn && lane == 0) atomicExch(L.err, 5);
         }
+        for (int t = lane; t < Pn; t += 32) Wp[t] = 0;
         __syncwarp();
         const int C = (Pn + 31) >> 5;
         const int lo0 = lane * C;
         const int hi0 = min(Pn, lo0 + C);
-        const uint32_t *inv = L.invk + (int64_t)i * L.invk_T;
-        // divided differences on the unit grid: level k divides by x_j - x_{j-k} = k
+        const uint32_t *inv = L.invk + (int64_t)pt * L.invk_T;
+        // divided differences: level k divides by x_j - x_{j-k}, a small positive
+        // integer (k on the unit grid), whose inverse comes from the table
         for (int k = 1; k < Pn; ++k) {
-            const uint32_t ik = inv[k];
             uint32_t prev = (lo0 >= 1 && lo0 - 1 < Pn) ? V[lo0 - 1] : 0u;
             __syncwarp();
             const int lo = max(lo0, k);
             for (int j = hi0 - 1; j >= lo; --j) {
                 uint32_t cm1 = (j - 1 >= lo0) ? V[j - 1] : prev;
-                V[j] = mp_mul(mp_sub(V[j], cm1, M.p), ik, M);
+                V[j] = mp_mul(mp_sub(V[j], cm1, M.p), inv[X[j] - X[j - k]], M);
             }
             __syncwarp();
         }
-        // Newton form -> monomial basis: W = c_{P-1}; W <- W (x - k) + c_k
+        // Newton form -> monomial basis: W = c_{P-1}; W <- W (x - x_k) + c_k
         if (lane == 0) Wp[0] = V[Pn - 1];
         __syncwarp();
         for (int k = Pn - 2; k >= 0; --k) {
             const int deg = Pn - 1 - k;
-            const uint32_t kt = mp_to((uint32_t)k, M);
+            const uint32_t kt = mp_to(X[k], M);
             const uint32_t ck = V[k];
             uint32_t prev = (lo0 >= 1 && lo0 - 1 < Pn) ? Wp[lo0 - 1] : 0u;
             __syncwarp();
@@ -533,7 +568,7 @@ __global__ void k_interp(ResLaunch L, WorkList w, int maxP) {
             }
             __syncwarp();
         }
-        uint32_t *o = L.cf + P.val_off + (int64_t)i * Pn;
+        uint32_t *o = L.cf + P.cf_off + (int64_t)i * Pn;
         for (int t = lane; t < Pn; t += 32) o[t] = mp_from(Wp[t], M);
         __syncwarp();
     }
@@ -610,7 +645,7 @@ __global__ void __launch_bounds__(256) k_interp_gemm(ResLaunch L, const int32_t 
     __shared__ uint32_t As[GT_K][GT_M + 1];
     __shared__ __align__(16) uint32_t Bs[GT_K][GT_N + 4];
     __shared__ uint32_t Cs[GT_N][GT_M + 1];
-    __shared__ int64_t colbase[GT_N];
+    __shared__ int64_t colbase[GT_N], cfbase[GT_N];
     const int i = blockIdx.z;
     const int c0 = blockIdx.x * GT_M, q0 = blockIdx.y * GT_N;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -619,7 +654,10 @@ __global__ void __launch_bounds__(256) k_interp_gemm(ResLaunch L, const int32_t 
         int64_t b = -1;
         if (qi < npairs) {
             const PairPlan &pp = L.plan[gpairs[qi]];
-            if (i < pp.k) b = pp.val_off + (int64_t)i * P;
+            if (i < pp.k) {
+                b = pp.val_off + (int64_t)i * P;
+                cfbase[threadIdx.x] = pp.cf_off + (int64_t)i * P;
+            }
         }
         colbase[threadIdx.x] = b;
     }
@@ -668,7 +706,7 @@ __global__ void __launch_bounds__(256) k_interp_gemm(ResLaunch L, const int32_t 
     for (int e = threadIdx.x; e < GT_N * GT_M; e += 256) {
         int qq = e / GT_M, r = e % GT_M;
         int64_t b = colbase[qq];
-        if (b >= 0 && c0 + r < P) L.cf[b + c0 + r] = Cs[qq][r];
+        if (b >= 0 && c0 + r < P) L.cf[cfbase[qq] + c0 + r] = Cs[qq][r];
     }
 }
 
@@ -678,18 +716,18 @@ __global__ void k_crt(ResLaunch L, WorkList w, int LM) {
     extern __shared__ uint32_t smem[];
     const int BS = blockDim.x;
     uint32_t *limb = smem + threadIdx.x;
-    const uint32_t *cinv = L.garner;
-    const uint32_t *pm = L.garner + L.garner_K;
     for (int64_t item = blockIdx.x * (int64_t)BS + threadIdx.x; item < w.total; item += (int64_t)gridDim.x * BS) {
         int bi = wl_find(w.start, w.n, item);
         int q = w.pairs[bi];
         int c = (int)(item - w.start[bi]);
         const PairPlan &P = L.plan[q];
         const int k = P.k, Pn = P.P;
-        uint32_t *v = L.cf + P.val_off + c;
+        const uint32_t *cinv = P.gtab_off < 0 ? L.garner : L.gtab + P.gtab_off;
+        const uint32_t *pm = P.gtab_off < 0 ? L.garner + L.garner_K : L.gtab + P.gtab_off + k;
+        uint32_t *v = L.cf + P.cf_off + c;
         // Garner: digits v_i with X = sum v_i prod_{j<i} p_j, 0 <= v_i < p_i
         for (int i = 1; i < k; ++i) {
-            const ModP M = L.mods[i];
+            const ModP M = L.mods[prime_of(P, L.pmap, i)];
             const uint32_t *pmi = pm + (int64_t)i * (i - 1) / 2;
             uint32_t t = v[(int64_t)(i - 1) * Pn];
             t = min(t, t - M.p);
@@ -705,14 +743,14 @@ __global__ void k_crt(ResLaunch L, WorkList w, int LM) {
         int cmp = 0;
         for (int i = k - 1; i >= 0 && cmp == 0; --i) {
             uint32_t d = v[(int64_t)i * Pn];
-            uint32_t h = (L.mods[i].p - 1u) >> 1;
+            uint32_t h = (L.mods[prime_of(P, L.pmap, i)].p - 1u) >> 1;
             cmp = (d > h) - (d < h);
         }
         const bool neg = cmp > 0;
         // |value| = X or M - X = sum (p_i - 1 - v_i) prod_{j<i} p_j + 1, Horner to 32-bit limbs
         int nl = 0;
         for (int i = k - 1; i >= 0; --i) {
-            const uint32_t p = L.mods[i].p;
+            const uint32_t p = L.mods[prime_of(P, L.pmap, i)].p;
             uint32_t d = v[(int64_t)i * Pn];
             if (neg) d = p - 1u - d;
             uint32_t carry = d;
@@ -734,6 +772,57 @@ __global__ void k_crt(ResLaunch L, WorkList w, int LM) {
         for (int l = 0; l < P.L; ++l) o[l] = l < nl ? limb[l * BS] : 0u;
         L.sign[P.sign_off + c] = nl == 0 ? 0 : (neg ? -1 : 1);
         if (nl > 0) atomicMax(L.deg + q, c);
+    }
+}
+
+// ------------------------------------------------------------------ A6: unlucky primes
+
+// Flags prime c of pair q when the leading row of f or of g vanishes identically
+// modulo it (then every evaluation point of that prime is unlucky).  For disc,
+// lc(df/dy) = m lc(f) and the table primes exceed m, so f's row decides.
+__global__ void k_unlucky_primes(ResLaunch L, int kc, uint8_t *out) {
+    const int64_t total = (int64_t)L.npairs * kc;
+    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < total; it += (int64_t)gridDim.x * blockDim.x) {
+        const int q = (int)(it / kc), c = (int)(it % kc);
+        const PairBound &B = L.bounds[q];
+        const PairDesc &D = L.desc[q];
+        uint8_t bad = 0;
+        if (B.m >= 0 && B.n >= 0) {
+            const ModP M = L.mods[c];
+            for (int w = 0; w < 2 && !bad; ++w) {
+                if (w == 1 && D.disc) break;
+                const PolyDesc &Pd = w ? D.g : D.f;
+                const int row = w ? B.n : B.m;
+                bool allzero = true;
+                for (int col = 0; col <= Pd.cols && allzero; ++col)
+                    allzero = mp_from_words(coef_ptr(L.coef, Pd, row, col), Pd.words, M) == 0u;
+                bad = allzero;
+            }
+        }
+        out[it] = bad;
+    }
+}
+
+// Garner constants of a pair whose primes are not a prefix of the table
+// (same layout as the prefix table: k inverses, then the triangle).
+__global__ void k_pair_garner(ResLaunch L, const int32_t *pairs, int n, int kmax, uint32_t *gtab) {
+    const int64_t total = (int64_t)n * kmax;
+    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < total; it += (int64_t)gridDim.x * blockDim.x) {
+        const PairPlan &P = L.plan[pairs[it / kmax]];
+        const int i = (int)(it % kmax), k = P.k;
+        if (i >= k) continue;
+        const ModP M = L.mods[prime_of(P, L.pmap, i)];
+        uint32_t *tab = gtab + P.gtab_off;
+        uint32_t *pm = tab + k + (int64_t)i * (i - 1) / 2;
+        uint32_t prod = M.r1;
+        for (int j = 0; j < i; ++j) {
+            uint32_t pj = L.mods[prime_of(P, L.pmap, j)].p;
+            pj = pj >= M.p ? pj - M.p : pj;
+            uint32_t pjm = mp_to(pj, M);
+            pm[j] = pjm;
+            prod = mp_mul(prod, pjm, M);
+        }
+        tab[i] = mp_inv(prod, M);
     }
 }
 
@@ -789,7 +878,7 @@ cudaError_t launch_evalres(const ResLaunch &L, const WorkList &w, int SF, int SG
 
 cudaError_t launch_interp(const ResLaunch &L, const WorkList &w, int maxP, cudaStream_t s) {
     if (w.total <= 0) return cudaSuccess;
-    size_t per_warp = (size_t)2 * maxP * sizeof(uint32_t);
+    size_t per_warp = (size_t)3 * maxP * sizeof(uint32_t);
     int nw = (int)((48 * 1024) / per_warp);
     if (nw > 8) nw = 8;
     if (nw < 1) nw = 1;
@@ -814,6 +903,23 @@ cudaError_t launch_interp_gemm(const ResLaunch &L, const int32_t *gpairs, int np
     if (npairs <= 0) return cudaSuccess;
     dim3 grid((P + GT_M - 1) / GT_M, (npairs + GT_N - 1) / GT_N, K);
     k_interp_gemm<<<grid, 256, 0, s>>>(L, gpairs, npairs, P, vinv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unlucky_primes(const ResLaunch &L, int kc, uint8_t *out, cudaStream_t s) {
+    int64_t total = (int64_t)L.npairs * kc;
+    if (total <= 0) return cudaSuccess;
+    int grid = (int)std::min<int64_t>((total + 255) / 256, 4096);
+    k_unlucky_primes<<<grid, 256, 0, s>>>(L, kc, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_garner(const ResLaunch &L, const int32_t *pairs, int n, int kmax, uint32_t *gtab,
+                               cudaStream_t s) {
+    int64_t total = (int64_t)n * kmax;
+    if (total <= 0) return cudaSuccess;
+    int grid = (int)std::min<int64_t>((total + 255) / 256, 4096);
+    k_pair_garner<<<grid, 256, 0, s>>>(L, pairs, n, kmax, gtab);
     return cudaGetLastError();
 }
 

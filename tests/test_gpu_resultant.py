@@ -216,3 +216,34 @@ def test_interpolation_contraction_matches_newton(ctx):
     assert got == newton
     for f, g, r in zip(fs, gs, got):
         assert r == list(O.res_bareiss(f, g))
+
+
+def test_drop_unlucky_matches_formal_degrees(ctx):
+    """Dropping unlucky points (a leading coefficient vanishes there) for spare
+    points, and unlucky primes (a leading coefficient vanishes identically) for the
+    next table primes, gives the same resultants as keeping them with formal
+    degrees; the counters show that points and primes were actually dropped."""
+    from paper_1103_4697_gb300.api import primes
+    from paper_1103_4697_gb300.native import OPT_DROP_UNLUCKY
+
+    p0, p1 = primes(2)
+    pt_f = [[1, 2, -1], [0, 1], [0, -6, 1, 1]]                 # lc vanishes at x = 0, 2 (and -3)
+    pt_g = [[2, -1], [1, 0, 1], [-2, 1]]                       # lc vanishes at x = 2
+    pr_f = [[3, 1, 4], [1, 5], [p0 * p1, 0, p0 * p1 * 7]]      # lc = 0 mod p0 and mod p1
+    pr_g = [[2, 7], [1, 8, 2], [9]]
+    rng = random.Random(17)
+    fs = [pt_f, pr_f] + [[[rng.randint(-9, 9) for _ in range(4)] for _ in range(rng.randint(1, 6))] for _ in range(30)]
+    gs = [pt_g, pr_g] + [[[rng.randint(-9, 9) for _ in range(3)] for _ in range(rng.randint(1, 6))] for _ in range(30)]
+    formal = ctx.resultant_batch(fs, gs)
+    ctx.set_option(OPT_DROP_UNLUCKY, 1)
+    try:
+        dropped = ctx.resultant_batch(fs, gs)
+        st = ctx.stats()
+        d1 = ctx.discriminant_res(pt_f)
+    finally:
+        ctx.set_option(OPT_DROP_UNLUCKY, 0)
+    assert dropped == formal
+    assert st["dropped_points"] >= 2 and st["dropped_primes"] >= 2
+    for f, g, r in zip(fs, gs, formal):
+        assert r == _oracle(f, g)
+    assert d1 == ctx.discriminant_res(pt_f) == list(O.disc_res(pt_f))
