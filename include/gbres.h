@@ -228,15 +228,18 @@ int gbr_get_serve_stats(gbr_ctx *ctx, gbr_serve_stats *out);
 
 /* Measured arithmetic ceilings of this GPU for the library's own Montgomery
  * arithmetic (integer pipes), used as the roofline denominators of the
- * elimination and interpolation stages: independent chains of mp_mul and of
- * the fused multiply-subtract, timed with CUDA events on the context's stream
- * over about 50 ms each.  Results in operations per second; sm_clock_mhz is
- * the clock the driver reported for the device (cudaDevAttrClockRate). */
+ * evaluation, elimination and interpolation stages: independent chains of one
+ * Montgomery multiplication, of the fused two-product multiply-subtract and of
+ * the fused three-product reduction, timed with CUDA events on the context's
+ * stream.  Results in operations per second (an operation of the fused kinds
+ * does two or three modular products); sm_clock_mhz is the clock the driver
+ * reports for the device (cudaDevAttrClockRate). */
 typedef struct {
     double modmul_per_s;
     double mulsub_per_s;
     double sm_clock_mhz;
     int32_t sms;
+    double fma3_per_s;
 } gbr_calib;
 int gbr_calibrate(gbr_ctx *ctx, gbr_calib *out);
 

@@ -8,7 +8,7 @@
 
 namespace gbr {
 
-template <int CHAINS, bool FUSED>
+template <int CHAINS, int KIND>
 __global__ void k_calib(const ModP *mods, int iters, uint32_t *sink) {
     const ModP M = mods[threadIdx.x & 15];
     uint32_t x[CHAINS], y[CHAINS];
@@ -20,8 +20,13 @@ __global__ void k_calib(const ModP *mods, int iters, uint32_t *sink) {
     for (int it = 0; it < iters; ++it) {
 #pragma unroll
         for (int c = 0; c < CHAINS; ++c) {
-            if (FUSED) x[c] = mp_mulsub(x[c], y[c], y[(c + 1) % CHAINS], x[(c + 3) % CHAINS], M);
-            else x[c] = mp_mul(x[c], y[c], M);
+            if (KIND == 2)
+                x[c] = mp_fma3(x[c], y[c], y[(c + 1) % CHAINS], x[(c + 3) % CHAINS], y[(c + 5) % CHAINS],
+                               x[(c + 6) % CHAINS], M);
+            else if (KIND == 1)
+                x[c] = mp_mulsub(x[c], y[c], y[(c + 1) % CHAINS], x[(c + 3) % CHAINS], M);
+            else
+                x[c] = mp_mul(x[c], y[c], M);
         }
     }
     uint32_t acc = 0;
@@ -45,12 +50,13 @@ extern "C" int gbr_calibrate(gbr_ctx *c, gbr_calib *out) {
     if (!sink) return c->fail(GBR_ENOMEM, "calibration scratch");
     const int block = 256, grid = sms * 8, iters = 4096;
     const int CH = 8;
-    double rates[2];
+    double rates[3];
     cudaError_t e = cudaSuccess;
-    for (int fused = 0; fused < 2 && e == cudaSuccess; ++fused) {
+    for (int fused = 0; fused < 3 && e == cudaSuccess; ++fused) {
         auto launch = [&]() {
-            if (fused) k_calib<CH, true><<<grid, block, 0, c->stream>>>(c->d_mods, iters, sink);
-            else k_calib<CH, false><<<grid, block, 0, c->stream>>>(c->d_mods, iters, sink);
+            if (fused == 2) k_calib<CH, 2><<<grid, block, 0, c->stream>>>(c->d_mods, iters, sink);
+            else if (fused == 1) k_calib<CH, 1><<<grid, block, 0, c->stream>>>(c->d_mods, iters, sink);
+            else k_calib<CH, 0><<<grid, block, 0, c->stream>>>(c->d_mods, iters, sink);
         };
         launch();   // warm-up
         cudaEventRecord(c->ev[6], c->stream);
@@ -66,6 +72,7 @@ extern "C" int gbr_calibrate(gbr_ctx *c, gbr_calib *out) {
     if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "calibration", e);
     out->modmul_per_s = rates[0];
     out->mulsub_per_s = rates[1];
+    out->fma3_per_s = rates[2];
     out->sm_clock_mhz = clk / 1000.0;
     out->sms = sms;
     return GBR_OK;
