@@ -274,8 +274,9 @@ int gbr_ctx::ensure_tables(int K, int T) {
 // primes; the cache is bounded (least recently used entries are dropped).
 static const size_t kVinvCacheBytes = (size_t)1 << 30;
 
-const uint32_t *gbr_ctx::get_vinv(int P, int K) {
-    auto it = vinv.find(P);
+const uint32_t *gbr_ctx::get_vinv(int P, int K, int sym) {
+    const int key = 2 * P + (sym ? 1 : 0);
+    auto it = vinv.find(key);
     if (it != vinv.end() && it->second.K >= K) {
         it->second.last_use = ++vinv_clock;
         return it->second.d;
@@ -284,7 +285,7 @@ const uint32_t *gbr_ctx::get_vinv(int P, int K) {
     if (bytes > kVinvCacheBytes / 2) return nullptr;
     auto total = [&]() {
         size_t t = 0;
-        for (auto &kv : vinv) t += (size_t)kv.first * kv.first * kv.second.K * 4;
+        for (auto &kv : vinv) t += (size_t)(kv.first / 2) * (kv.first / 2) * kv.second.K * 4;
         return t;
     };
     if (it != vinv.end()) {
@@ -300,7 +301,7 @@ const uint32_t *gbr_ctx::get_vinv(int P, int K) {
     }
     uint32_t *d = (uint32_t *)dalloc(bytes);
     if (!d) return nullptr;
-    if (launch_vinv(d_mods, P, K, d, stream) != cudaSuccess) {
+    if (launch_vinv(d_mods, P, K, sym, d, stream) != cudaSuccess) {
         dfree(d);
         return nullptr;
     }
@@ -308,7 +309,7 @@ const uint32_t *gbr_ctx::get_vinv(int P, int K) {
     v.d = d;
     v.K = K;
     v.last_use = ++vinv_clock;
-    vinv[P] = v;
+    vinv[key] = v;
     return d;
 }
 
@@ -721,6 +722,10 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
         // drop mode: evaluate at spare points too; a leading coefficient of degree
         // d vanishes at no more than d points modulo a prime that does not kill it
         p.Pe = drop ? p.P + std::max(b.lcdf, 0) + std::max(b.lcdg, 0) : p.P;
+        // symmetric points 0, +-1, +-2, ... halve the evaluation work (lane pairs);
+        // the drop mode keeps the unit grid so that spare points are 0..Pe-1
+        p.sym = drop ? 0 : 1;
+        p.tiles = (p.P / 2 + 1 + 15) / 16;
         if (p.Pe > GBR_MAX_POINTS + 2 * 4096) return c->fail(GBR_ELIMIT, "too many spare points");
         kc_max = std::max(kc_max, p.k + 32);
     }
@@ -797,10 +802,10 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
         Lmax = std::max(Lmax, p.L);
         red.add(q, p.S);
         int key = ((std::max(p.m, p.n) + 1) + 3) / 4 * 4;
-        evb[key].add(q, (int64_t)k * p.Pe);
+        evb[key].add(q, p.sym ? (int64_t)k * p.tiles * 32 : (int64_t)k * p.Pe);
         // the contraction serves pairs whose points are exactly 0..P-1 and whose
         // primes are the table prefix
-        if (p.pmap_off < 0 && p.Pe == p.P) pgroups[p.P].push_back(q);
+        if (p.pmap_off < 0 && p.Pe == p.P) pgroups[2 * p.P + p.sym].push_back(q);
         else interp.add(q, k);
         crt.add(q, p.P);
         subproblems += (int64_t)k * p.Pe;
@@ -826,9 +831,10 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
         int K = 0;
         for (int q : qs) K = std::max(K, plan[q].k);
         const uint32_t *vi = nullptr;
-        if ((int)qs.size() >= kGemmMinPairs && c->gemm_on) vi = c->get_vinv(kv.first, K);
+        const int gP = kv.first / 2, gsym = kv.first & 1;
+        if ((int)qs.size() >= kGemmMinPairs && c->gemm_on) vi = c->get_vinv(gP, K, gsym);
         if (vi) {
-            gemms.push_back({kv.first, K, vi, gemm_pairs.size(), (int)qs.size()});
+            gemms.push_back({gP, K, vi, gemm_pairs.size(), (int)qs.size()});
             gemm_pairs.insert(gemm_pairs.end(), qs.begin(), qs.end());
         } else {
             for (int q : qs) interp.add(q, plan[q].k);

@@ -70,9 +70,9 @@ struct gbr_ctx {
         int K = 0;
         uint64_t last_use = 0;
     };
-    std::map<int, Vinv> vinv;      // inverse Vandermonde matrices per point count P
+    std::map<int, Vinv> vinv;      // inverse Vandermonde matrices, key 2 P + sym
     uint64_t vinv_clock = 0;
-    const uint32_t *get_vinv(int P, int K);   // nullptr if it cannot be built
+    const uint32_t *get_vinv(int P, int K, int sym);   // nullptr if it cannot be built
     gbr::ServeState *serve = nullptr;
     gbr_ctx *parent = nullptr;     // serving workers share the parent's arena
     bool own_stream = false;

@@ -65,6 +65,8 @@ struct PairPlan {
     int32_t L;          // 32-bit limbs per output coefficient
     int32_t S;          // residue words per prime: (dxf+1) rows4(m) + (dxg+1) rows4(n)
     int32_t pmap_off;   // -1: primes are table entries 0..k-1; else their table indices at pmap[pmap_off..]
+    int32_t sym;        // 1: points are point_of(j) (0, 1, -1, 2, -2, ...), evaluated in +-i lane pairs
+    int32_t tiles;      // symmetric points: warp tiles of 16 values of i per prime
     int64_t res_off;    // residues [prime][S]                       (u32 words)
     int64_t val_off;    // values [prime][Pe]                        (u32 words)
     int64_t cf_off;     // coefficients mod p [prime][P]             (u32 words)
@@ -187,6 +189,11 @@ struct ResLaunch {
     int32_t drop_unlucky;
 };
 
+// Evaluation point j: the unit grid j, or the symmetric order 0, 1, -1, 2, -2, ...
+__host__ __device__ __forceinline__ int point_of(int sym, int j) {
+    return !sym ? j : ((j & 1) ? (j + 1) >> 1 : -(j >> 1));
+}
+
 __host__ __device__ __forceinline__ int prime_of(const PairPlan &P, const int32_t *pmap, int i) {
     return P.pmap_off < 0 ? i : pmap[P.pmap_off + i];
 }
@@ -213,7 +220,7 @@ cudaError_t launch_evalres(const ResLaunch &L, const WorkList &w, int slots_f, i
                            cudaStream_t s);
 cudaError_t launch_interp(const ResLaunch &L, const WorkList &w, int maxP, cudaStream_t s);
 cudaError_t launch_crt(const ResLaunch &L, const WorkList &w, int maxL, cudaStream_t s);
-cudaError_t launch_vinv(const ModP *mods, int P, int K, uint32_t *out, cudaStream_t s);
+cudaError_t launch_vinv(const ModP *mods, int P, int K, int sym, uint32_t *out, cudaStream_t s);
 cudaError_t launch_unlucky_primes(const ResLaunch &L, int kc, uint8_t *out, cudaStream_t s);
 cudaError_t launch_pair_garner(const ResLaunch &L, const int32_t *pairs, int n, int kmax, uint32_t *gtab,
                                cudaStream_t s);

@@ -458,6 +458,54 @@ __device__ __forceinline__ void eval4(const uint32_t *rc, int rows4n, const int3
     if (nr > 3) col[(top - r0 - 3) * BS] = a3;
 }
 
+// Symmetric evaluation of rows r0..r0+3 at +ii and -ii: row(x) = E(x^2) + x O(x^2)
+// with E, O the even and odd parts, both evaluated at b = ii^2 (Horner on every
+// second coefficient).  The value at this lane's own point goes to its column,
+// the value at the partner's point (the opposite sign) to the partner's column.
+__device__ __forceinline__ void eval4_sym(const uint32_t *rc, int rows4n, const int32_t *rowdeg, int nrows, int r0,
+                                          uint32_t a, uint32_t b, bool negown, const ModP &M, uint32_t *own,
+                                          uint32_t *other, int BS) {
+    const int nr = min(4, nrows - r0);
+    int dmax = -1;
+    for (int i = 0; i < nr; ++i) dmax = max(dmax, rowdeg[r0 + i]);
+    uint32_t e0 = 0, e1 = 0, e2 = 0, e3 = 0, o0 = 0, o1 = 0, o2 = 0, o3 = 0;
+    const uint4 *c = reinterpret_cast<const uint4 *>(rc + r0);
+    const int step = rows4n >> 2;
+    int x = dmax;
+    if (x >= 0 && (x & 1) == 0) {     // top power even: starts E alone
+        const uint4 v = c[(int64_t)x * step];
+        e0 = horner_step(0u, b, v.x, M);
+        e1 = horner_step(0u, b, v.y, M);
+        e2 = horner_step(0u, b, v.z, M);
+        e3 = horner_step(0u, b, v.w, M);
+        --x;
+    }
+    for (; x >= 1; x -= 2) {          // x odd: O gets c_x, E gets c_{x-1}
+        const uint4 vo = c[(int64_t)x * step];
+        const uint4 ve = c[(int64_t)(x - 1) * step];
+        o0 = horner_step(o0, b, vo.x, M);
+        o1 = horner_step(o1, b, vo.y, M);
+        o2 = horner_step(o2, b, vo.z, M);
+        o3 = horner_step(o3, b, vo.w, M);
+        e0 = horner_step(e0, b, ve.x, M);
+        e1 = horner_step(e1, b, ve.y, M);
+        e2 = horner_step(e2, b, ve.z, M);
+        e3 = horner_step(e3, b, ve.w, M);
+    }
+    const uint32_t ev[4] = {e0, e1, e2, e3}, ov[4] = {o0, o1, o2, o3};
+    const int top = nrows - 1;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        if (t < nr) {
+            const uint32_t io = mp_mul(a, ov[t], M);
+            const uint32_t plus = mp_add(ev[t], io, M.p), minus = mp_sub(ev[t], io, M.p);
+            const int slot = (top - r0 - t) * BS;
+            own[slot] = negown ? minus : plus;
+            other[slot] = negown ? plus : minus;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ A2 + A3: evaluate and solve
 
 __global__ void k_evalres(ResLaunch L, WorkList w, int SF, int SG) {
@@ -470,15 +518,43 @@ __global__ void k_evalres(ResLaunch L, WorkList w, int SF, int SG) {
         int q = w.pairs[bi];
         int64_t local = item - w.start[bi];
         const PairPlan &P = L.plan[q];
+        const int rf4 = rows4(P.m), rg4 = rows4(P.n);
+        const int32_t *dgf = L.rowdeg + P.rowdeg_f;
+        const int32_t *dgg = L.rowdeg + P.rowdeg_g;
+        if (P.sym) {
+            // lanes 0-15 take points +ii, lanes 16-31 take -ii (same ii); a lane
+            // evaluates even and odd parts of one polynomial at ii^2 and hands the
+            // partner its value: f-lanes do f, g-lanes do g
+            const int per = P.tiles * 32;
+            const int i = (int)(local / per);
+            const int r = (int)(local % per);
+            const int lane = r & 31;
+            const int ii = (r >> 5) * 16 + (lane & 15);
+            const bool glane = lane >= 16;
+            const int j = ii == 0 ? (glane ? -1 : 0) : (glane ? 2 * ii : 2 * ii - 1);
+            const ModP M = L.mods[prime_of(P, L.pmap, i)];
+            const uint32_t a = mp_to((uint32_t)ii, M);
+            const uint32_t b = mp_mul(a, a, M);
+            const uint32_t *rbase = L.res + P.res_off + (int64_t)i * P.S;
+            const uint32_t *rc = glane ? rbase + (int64_t)(P.dxf + 1) * rf4 : rbase;
+            const int32_t *dg = glane ? dgg : dgf;
+            const int nrows = (glane ? P.n : P.m) + 1;
+            const int r4 = glane ? rg4 : rf4;
+            uint32_t *own = (glane ? Gs : Fs);
+            uint32_t *other = own + (glane ? -16 : 16);
+            for (int r0 = 0; r0 < nrows; r0 += 4) eval4_sym(rc, r4, dg, nrows, r0, a, b, glane, M, own, other, BS);
+            __syncwarp();
+            if (j >= 0 && j < P.P)
+                L.val[P.val_off + (int64_t)i * P.Pe + j] = res_formal(Fs, P.m, Gs, P.n, BS, M);
+            __syncwarp();
+            continue;
+        }
         int i = (int)(local / P.Pe);
         int j = (int)(local % P.Pe);
         const ModP M = L.mods[prime_of(P, L.pmap, i)];
         const uint32_t a = mp_to((uint32_t)j, M);
-        const int rf4 = rows4(P.m), rg4 = rows4(P.n);
         const uint32_t *rf = L.res + P.res_off + (int64_t)i * P.S;
         const uint32_t *rg = rf + (int64_t)(P.dxf + 1) * rf4;
-        const int32_t *dgf = L.rowdeg + P.rowdeg_f;
-        const int32_t *dgg = L.rowdeg + P.rowdeg_g;
         for (int r0 = 0; r0 <= P.m; r0 += 4) eval4(rf, rf4, dgf, P.m + 1, r0, a, M, Fs, BS);
         for (int r0 = 0; r0 <= P.n; r0 += 4) eval4(rg, rg4, dgg, P.n + 1, r0, a, M, Gs, BS);
         if (P.flag_off >= 0) {
@@ -513,7 +589,7 @@ __global__ void k_interp(ResLaunch L, WorkList w, int maxP) {
         if (P.flag_off < 0) {
             for (int t = lane; t < Pn; t += 32) {
                 V[t] = g[t];
-                X[t] = t;
+                X[t] = (uint32_t)point_of(P.sym, t);
             }
         } else {
             // keep the first Pn points whose flag is clear
@@ -546,7 +622,9 @@ __global__ void k_interp(ResLaunch L, WorkList w, int maxP) {
             const int lo = max(lo0, k);
             for (int j = hi0 - 1; j >= lo; --j) {
                 uint32_t cm1 = (j - 1 >= lo0) ? V[j - 1] : prev;
-                V[j] = mp_mul(mp_sub(V[j], cm1, M.p), inv[X[j] - X[j - k]], M);
+                const int d = (int)X[j] - (int)X[j - k];   // non-zero, |d| < P
+                const uint32_t id = d > 0 ? inv[d] : mp_neg(inv[-d], M.p);
+                V[j] = mp_mul(mp_sub(V[j], cm1, M.p), id, M);
             }
             __syncwarp();
         }
@@ -555,7 +633,8 @@ __global__ void k_interp(ResLaunch L, WorkList w, int maxP) {
         __syncwarp();
         for (int k = Pn - 2; k >= 0; --k) {
             const int deg = Pn - 1 - k;
-            const uint32_t kt = mp_to(X[k], M);
+            const int xk = (int)X[k];
+            const uint32_t kt = mp_to(xk >= 0 ? (uint32_t)xk : M.p - (uint32_t)(-xk), M);
             const uint32_t ck = V[k];
             uint32_t prev = (lo0 >= 1 && lo0 - 1 < Pn) ? Wp[lo0 - 1] : 0u;
             __syncwarp();
@@ -576,22 +655,25 @@ __global__ void k_interp(ResLaunch L, WorkList w, int maxP) {
 
 // ------------------------------------------------------------------ A4 as a contraction
 
-// Inverse Vandermonde matrix of the points 0..P-1 modulo prime i, normal form,
-// row-major: out[(i*P + c)*P + j] = coefficient of x^c in the Lagrange basis
-// polynomial L_j(x) = prod_{t != j} (x - t) / prod_{t != j} (j - t).
-// One block per prime: W(x) = prod_t (x - t) is built in shared memory, then
-// thread j divides W by (x - j) (synthetic division) and scales by
-// 1 / (j! (P-1-j)! (-1)^(P-1-j)).
-__global__ void k_vinv(const ModP *mods, int P, uint32_t *out) {
+// Inverse Vandermonde matrix of the points x_j = point_of(sym, j), j < P,
+// modulo prime i, normal form, row-major: out[(i*P + c)*P + j] = coefficient of
+// x^c in the Lagrange basis polynomial L_j(x) = prod_{t != j} (x - x_t) /
+// prod_{t != j} (x_j - x_t).  One block per prime: W(x) = prod_t (x - x_t) is
+// built in shared memory, then thread j divides W by (x - x_j) (synthetic
+// division) and scales by the inverse of its denominator.
+__device__ __forceinline__ uint32_t mont_of_int(int v, const ModP &M) {
+    return mp_to(v >= 0 ? (uint32_t)v : M.p - (uint32_t)(-v), M);
+}
+
+__global__ void k_vinv(const ModP *mods, int P, int sym, uint32_t *out) {
     extern __shared__ uint32_t sh[];
     uint32_t *W = sh;             // P + 1 words, Montgomery form
-    uint32_t *fact = sh + P + 1;  // P + 1 words: t! in Montgomery form
     const int i = blockIdx.x;
     const ModP M = mods[i];
     for (int t = threadIdx.x; t <= P; t += blockDim.x) W[t] = t == 0 ? M.r1 : 0u;
     __syncthreads();
-    for (int j = 0; j < P; ++j) {                 // W <- W (x - j), degree j -> j + 1
-        const uint32_t jm = mp_to((uint32_t)j, M);
+    for (int j = 0; j < P; ++j) {                 // W <- W (x - x_j), degree j -> j + 1
+        const uint32_t jm = mont_of_int(point_of(sym, j), M);
         uint32_t nv[4];
         int cnt = 0;
         for (int t = threadIdx.x; t <= j + 1 && cnt < 4; t += blockDim.x, ++cnt) {
@@ -603,17 +685,14 @@ __global__ void k_vinv(const ModP *mods, int P, uint32_t *out) {
         for (int t = threadIdx.x; t <= j + 1 && cnt < 4; t += blockDim.x, ++cnt) W[t] = nv[cnt];
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        fact[0] = M.r1;
-        for (int t = 1; t <= P; ++t) fact[t] = mp_mul(fact[t - 1], mp_to((uint32_t)t, M), M);
-    }
-    __syncthreads();
     uint32_t *o = out + (int64_t)i * P * P;
     for (int j = threadIdx.x; j < P; j += blockDim.x) {
-        uint32_t d = mp_mul(fact[j], fact[P - 1 - j], M);
-        if ((P - 1 - j) & 1) d = mp_neg(d, M.p);
+        const int xj = point_of(sym, j);
+        uint32_t d = M.r1;
+        for (int t = 0; t < P; ++t)
+            if (t != j) d = mp_mul(d, mont_of_int(xj - point_of(sym, t), M), M);
         const uint32_t id = mp_inv(d, M);
-        const uint32_t jm = mp_to((uint32_t)j, M);
+        const uint32_t jm = mont_of_int(xj, M);
         uint32_t q = W[P];
         o[(int64_t)(P - 1) * P + j] = mp_from(mp_mul(q, id, M), M);
         for (int t = P - 1; t >= 1; --t) {
@@ -889,12 +968,12 @@ cudaError_t launch_interp(const ResLaunch &L, const WorkList &w, int maxP, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_vinv(const ModP *mods, int P, int K, uint32_t *out, cudaStream_t s) {
-    size_t smem = (size_t)2 * (P + 1) * sizeof(uint32_t);
+cudaError_t launch_vinv(const ModP *mods, int P, int K, int sym, uint32_t *out, cudaStream_t s) {
+    size_t smem = (size_t)(P + 1) * sizeof(uint32_t);
     int block = P + 2 <= 1024 ? ((P + 2 + 31) / 32) * 32 : 1024;
     // each thread updates at most 4 coefficients of W per step
     if (smem > kMaxDynSmem || P + 1 > 4 * block) return cudaErrorInvalidValue;
-    k_vinv<<<K, block, smem, s>>>(mods, P, out);
+    k_vinv<<<K, block, smem, s>>>(mods, P, sym, out);
     return cudaGetLastError();
 }
 
