@@ -118,6 +118,7 @@ typedef struct {
     int64_t h2d_bytes, d2h_bytes;
     int64_t dropped_points;   /* GBR_OPT_DROP_UNLUCKY: evaluation points flagged unlucky and replaced */
     int64_t dropped_primes;   /* GBR_OPT_DROP_UNLUCKY: primes skipped because a leading coefficient vanishes */
+    int64_t graph_replayed;   /* 1 when the device stages ran as a CUDA graph (GBR_OPT_GRAPH) */
 } gbr_stats;
 
 /* ------------------------------------------------------------------ context */
@@ -147,8 +148,9 @@ const char *gbr_last_error(gbr_ctx *ctx);
                                     degrees; 1: they are detected, dropped and replaced by spare
                                     points / the next primes (same result, used to test both) */
 #define GBR_OPT_STATS        2   /* 1: record per-stage CUDA-event times (gbr_get_stats) */
-#define GBR_OPT_GRAPH        3   /* 1 (default): replay the device stages of a resident batch from
-                                    a captured CUDA graph when its plan repeats */
+#define GBR_OPT_GRAPH        3   /* 1 (default): when a resident batch runs again with an unchanged
+                                    plan, its device stages (after the bounds and the plan) are
+                                    captured into a CUDA graph once and replayed from then on */
 #define GBR_OPT_EXTRA_PRIMES 4   /* add this many primes beyond the bound (tests: k+1 == k) */
 #define GBR_OPT_INTERP_GEMM  5   /* 1 (default): pairs of a batch that share their number of points
                                     are interpolated by one inverse-Vandermonde contraction per

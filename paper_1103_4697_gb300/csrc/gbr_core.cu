@@ -313,6 +313,34 @@ const uint32_t *gbr_ctx::get_vinv(int P, int K, int sym) {
     return d;
 }
 
+cudaError_t gbr_ctx::capture_stream_ready() {
+    if (cap_stream) return cudaSuccess;
+    return cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking);
+}
+
+// Autotuning choices may be kept across processes in the file named by the
+// environment variable GBR_AUTOTUNE_FILE (lines "<kernel> <key> <value>").
+void gbr_ctx::autotune_load() {
+    const char *path = std::getenv("GBR_AUTOTUNE_FILE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    char name[64];
+    int key, val;
+    while (std::fscanf(f, "%63s %d %d", name, &key, &val) == 3)
+        if (!std::strcmp(name, "evalres") && (val == 64 || val == 128 || val == 256)) tuned_evalres[key] = val;
+    std::fclose(f);
+}
+
+void gbr_ctx::autotune_record(const char *kernel, int key, int value) {
+    const char *path = std::getenv("GBR_AUTOTUNE_FILE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d %d\n", kernel, key, value);
+    std::fclose(f);
+}
+
 // ------------------------------------------------------------------ status strings
 
 extern "C" const char *gbr_strerror(int s) {
@@ -380,8 +408,8 @@ extern "C" int gbr_create(gbr_ctx **out, int device, size_t budget, void *worksp
         gbr_destroy(c);
         return GBR_EDEVICE;
     }
-    for (int i = 0; i < 4; ++i) cudaEventCreate(&c->ev[i]);
-    for (int i = 4; i < 8; ++i) cudaEventCreate(&c->ev[i]);
+    for (int i = 0; i < 8; ++i) cudaEventCreate(&c->ev[i]);
+    c->autotune_load();
     *out = c;
     return GBR_OK;
 }
@@ -393,6 +421,7 @@ extern "C" void gbr_destroy(gbr_ctx *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (auto &kv : c->vinv) c->dfree(kv.second.d);
     for (int i = 0; i < 8; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -409,6 +438,8 @@ gbr_ctx *gbr_make_worker(gbr_ctx *parent) {
     w->device = parent->device;
     w->budget = parent->budget;
     w->drop_unlucky = parent->drop_unlucky;
+    w->tuned_evalres = parent->tuned_evalres;
+    w->graph_on = 0;   // serving batches differ every time; graphs would only add capture cost
     w->extra_primes = parent->extra_primes;
     cudaSetDevice(w->device);
     if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -875,8 +906,6 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
     if (!hp) return c->fail(GBR_ENOMEM, "pinned host staging");
     std::memcpy(hp, blk.data(), blk.size());
     e = cudaMemcpyAsync(r->d_planblk, hp, blk.size(), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(r->d_deg, 0xff, sizeof(int32_t) * n, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, 16, s);
     if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "plan upload", e);
     auto mk = [&](size_t op, size_t os, const HostList &h) {
         WorkList w;
@@ -901,39 +930,139 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
     L.pflags = r->d_flags;
     L.gtab = r->d_gtab;
     L.dropped = (unsigned long long *)(c->d_err + 2);
-    if (c->stats_on) cudaEventRecord(c->ev[1], s);
+    // ---- autotuning: the first run of an unseen degree bucket times the
+    // candidate block sizes of the evaluation kernel (results are identical)
+    std::vector<int> ev_block;
+    {
+        size_t bi = 0;
+        for (auto &kv : evb) {
+            const int key = kv.first;
+            auto it = c->tuned_evalres.find(key);
+            if (it != c->tuned_evalres.end()) {
+                ev_block.push_back(it->second);
+                ++bi;
+                continue;
+            }
+            WorkList w = mk(o_ev[bi].first, o_ev[bi].second, kv.second);
+            float best = 1e30f;
+            int best_block = 128;
+            for (int cand : {64, 128, 256}) {
+                if ((size_t)2 * key * cand * 4 > (size_t)kMaxDynSmem) continue;
+                cudaEventRecord(c->ev[6], s);
+                e = launch_evalres(L, w, key, key, cand, s);
+                cudaEventRecord(c->ev[7], s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(c->ev[7]);
+                if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "autotuning", e);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, c->ev[6], c->ev[7]);
+                if (ms < best) {
+                    best = ms;
+                    best_block = cand;
+                }
+            }
+            c->tuned_evalres[key] = best_block;
+            c->autotune_record("evalres", key, best_block);
+            ev_block.push_back(best_block);
+            ++bi;
+        }
+    }
+    // ---- the device stages; replayed from a captured CUDA graph when the plan repeats
     int64_t kernels = 1;
-    if (!mapped.empty()) {
-        e = launch_pair_garner(L, (const int32_t *)(r->d_planblk + o_mapped), (int)mapped.size(), kmapped, r->d_gtab, s);
-        if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "pair Garner tables", e);
+    auto record = [&](int idx, bool capturing, cudaStream_t q) {
+        if (!c->stats_on) return;
+        if (capturing) cudaEventRecordWithFlags(c->ev[idx], q, cudaEventRecordExternal);
+        else cudaEventRecord(c->ev[idx], q);
+    };
+    auto enqueue = [&](bool capturing, cudaStream_t q) -> cudaError_t {
+        kernels = 1;
+        cudaError_t x = cudaMemsetAsync(r->d_deg, 0xff, sizeof(int32_t) * n, q);
+        if (x == cudaSuccess) x = cudaMemsetAsync(c->d_err, 0, 16, q);
+        record(1, capturing, q);
+        if (x == cudaSuccess && !mapped.empty()) {
+            x = launch_pair_garner(L, (const int32_t *)(r->d_planblk + o_mapped), (int)mapped.size(), kmapped,
+                                   r->d_gtab, q);
+            kernels++;
+        }
+        if (x == cudaSuccess) x = launch_reduce(L, mk(o_red_p, o_red_s, red), q);
         kernels++;
-    }
-    e = launch_reduce(L, mk(o_red_p, o_red_s, red), s);
-    kernels++;
-    if (c->stats_on) cudaEventRecord(c->ev[2], s);
-    size_t bi = 0;
-    for (auto &kv : evb) {
-        if (e != cudaSuccess) break;
-        int key = kv.first;
-        int block = key > 64 ? 64 : 128;
-        e = launch_evalres(L, mk(o_ev[bi].first, o_ev[bi].second, kv.second), key, key, block, s);
+        record(2, capturing, q);
+        size_t bi = 0;
+        for (auto &kv : evb) {
+            if (x != cudaSuccess) break;
+            x = launch_evalres(L, mk(o_ev[bi].first, o_ev[bi].second, kv.second), kv.first, kv.first, ev_block[bi], q);
+            kernels++;
+            ++bi;
+        }
+        record(3, capturing, q);
+        if (x == cudaSuccess && interp.total > 0) {
+            x = launch_interp(L, mk(o_int_p, o_int_s, interp), Pmax, q);
+            kernels++;
+        }
+        for (const Gemm &gm : gemms) {
+            if (x != cudaSuccess) break;
+            x = launch_interp_gemm(L, (const int32_t *)(r->d_planblk + o_gemm) + gm.off, gm.n, gm.P, gm.K, gm.vinv, q);
+            kernels++;
+        }
+        record(4, capturing, q);
+        if (x == cudaSuccess) x = launch_crt(L, mk(o_crt_p, o_crt_s, crt), Lmax, q);
         kernels++;
-        ++bi;
+        record(5, capturing, q);
+        return x;
+    };
+    bool replayed = false;
+    if (c->graph_on && !r->oneshot) {
+        // the plan block, every buffer and table pointer and the launch shapes fix the graph
+        std::vector<uintptr_t> key = {(uintptr_t)r->d_planblk, (uintptr_t)r->d_res, (uintptr_t)r->d_val,
+                                      (uintptr_t)r->d_cf,      (uintptr_t)r->d_out, (uintptr_t)r->d_sign,
+                                      (uintptr_t)r->d_deg,     (uintptr_t)r->d_flags, (uintptr_t)r->d_gtab,
+                                      (uintptr_t)c->d_garner,  (uintptr_t)c->d_invk, (uintptr_t)c->d_err,
+                                      (uintptr_t)c->d_mods,    (uintptr_t)c->stats_on};
+        for (const Gemm &gm : gemms) key.push_back((uintptr_t)gm.vinv);
+        for (int b : ev_block) key.push_back((uintptr_t)b);
+        const bool same = r->gkey == key && r->gblk.size() == blk.size() &&
+                          std::memcmp(r->gblk.data(), blk.data(), blk.size()) == 0;
+        if (!same) {
+            // a new plan: run it plainly (this also warms every cache the launches
+            // consult) and capture it if it runs again
+            r->gkey = key;
+            r->gblk = blk;
+            r->gstate = 1;
+            e = enqueue(false, s);
+        } else if (r->gstate == 2) {
+            e = cudaGraphLaunch(r->gexec, s);
+            replayed = true;
+            kernels = r->graph_kernels;
+        } else {
+            // the context's stream may be the legacy default stream, which cannot
+            // be captured: capture on a private stream, launch on the context's
+            cudaGraph_t g = nullptr;
+            e = c->capture_stream_ready();
+            if (e == cudaSuccess) e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t x = enqueue(true, c->cap_stream);
+                e = cudaStreamEndCapture(c->cap_stream, &g);
+                if (x != cudaSuccess) e = x;
+            }
+            if (e == cudaSuccess) {
+                if (r->gexec) cudaGraphExecDestroy(r->gexec);
+                r->gexec = nullptr;
+                e = cudaGraphInstantiate(&r->gexec, g, 0);
+                r->graph_kernels = kernels;
+            }
+            if (g) cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                r->gexec = nullptr;
+                r->gstate = 0;
+                r->gkey.clear();
+                return c->fail(GBR_EDEVICE, "graph capture", e);
+            }
+            r->gstate = 2;
+            e = cudaGraphLaunch(r->gexec, s);
+            replayed = true;
+        }
+    } else {
+        e = enqueue(false, s);
     }
-    if (c->stats_on) cudaEventRecord(c->ev[3], s);
-    if (e == cudaSuccess && interp.total > 0) {
-        e = launch_interp(L, mk(o_int_p, o_int_s, interp), Pmax, s);
-        kernels++;
-    }
-    for (const Gemm &gm : gemms) {
-        if (e != cudaSuccess) break;
-        e = launch_interp_gemm(L, (const int32_t *)(r->d_planblk + o_gemm) + gm.off, gm.n, gm.P, gm.K, gm.vinv, s);
-        kernels++;
-    }
-    if (c->stats_on) cudaEventRecord(c->ev[4], s);
-    if (e == cudaSuccess) e = launch_crt(L, mk(o_crt_p, o_crt_s, crt), Lmax, s);
-    kernels++;
-    if (c->stats_on) cudaEventRecord(c->ev[5], s);
     if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "stage launch", e);
     int32_t herr[4] = {0, 0, 0, 0};
     e = cudaMemcpyAsync(herr, c->d_err, 16, cudaMemcpyDeviceToHost, s);
@@ -946,6 +1075,7 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
     r->sign_bytes = sign_b;
     r->ran = true;
     st.kernels = kernels;
+    st.graph_replayed = replayed ? 1 : 0;
     st.subproblems = subproblems;
     st.h2d_bytes = (int64_t)blk.size();
     st.d2h_bytes = (int64_t)sizeof(PairBound) * n + 4;
@@ -1051,6 +1181,7 @@ static int res_batch_impl(gbr_ctx *c, int n, const gbr_bipoly *f, const gbr_bipo
     gbr_resident *r = nullptr;
     int st = gbr_upload_pairs(c, n, f, g, var, disc, &r);
     if (st) return st;
+    r->oneshot = true;
     {
         std::lock_guard<std::mutex> lk(c->mu);
         cudaSetDevice(c->device);

@@ -74,6 +74,11 @@ struct gbr_ctx {
     uint64_t vinv_clock = 0;
     const uint32_t *get_vinv(int P, int K, int sym);   // nullptr if it cannot be built
     gbr::ServeState *serve = nullptr;
+    std::map<int, int> tuned_evalres;   // degree bucket -> block size chosen by the autotuner
+    cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+    cudaError_t capture_stream_ready();
+    void autotune_load();
+    void autotune_record(const char *kernel, int key, int value);
     gbr_ctx *parent = nullptr;     // serving workers share the parent's arena
     bool own_stream = false;
 
@@ -107,7 +112,12 @@ struct gbr_resident {
     size_t gtab_cap = 0;
     int64_t out_words = 0, sign_bytes = 0;
     bool ran = false;
-    cudaGraphExec_t gexec = nullptr;
+    bool oneshot = false;               // created by a one-shot call: never captured
+    cudaGraphExec_t gexec = nullptr;    // captured device stages of the last plan
+    int gstate = 0;                     // 0 no plan, 1 plan run once, 2 captured
+    int64_t graph_kernels = 0;
+    std::vector<uintptr_t> gkey;        // pointers and launch shapes of the captured plan
+    std::vector<char> gblk;             // plan block of the captured plan
 };
 
 // internal entry points (context lock held by the caller)

@@ -18,6 +18,9 @@
 #include <math.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "gbr_internal.h"
 
@@ -929,10 +932,25 @@ static int sm_count() {
     return n;
 }
 
+// Occupancy per (kernel, block size, shared memory), queried once: launches that
+// are being captured into a CUDA graph then make no query.
+static std::mutex g_occ_mu;
+static std::map<std::tuple<const void *, int, size_t>, int> g_occ;
+
 template <typename K>
 static int persistent_grid(K kernel, int block, size_t smem, int64_t items_in_blocks) {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
+    {
+        std::lock_guard<std::mutex> g(g_occ_mu);
+        auto key = std::make_tuple((const void *)kernel, block, smem);
+        auto it = g_occ.find(key);
+        if (it != g_occ.end()) {
+            per_sm = it->second;
+        } else {
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, smem);
+            g_occ[key] = per_sm;
+        }
+    }
     if (per_sm < 1) per_sm = 1;
     int64_t cap = (int64_t)per_sm * sm_count();
     return (int)(items_in_blocks < cap ? (items_in_blocks < 1 ? 1 : items_in_blocks) : cap);

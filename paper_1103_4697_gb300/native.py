@@ -34,7 +34,8 @@ class Stats(C.Structure):
                 ("interp_ms", C.c_double), ("crt_ms", C.c_double), ("gcd_ms", C.c_double),
                 ("total_ms", C.c_double), ("kernels", C.c_int64), ("subproblems", C.c_int64),
                 ("modmul", C.c_int64), ("modmul_evalres", C.c_int64), ("h2d_bytes", C.c_int64),
-                ("d2h_bytes", C.c_int64), ("dropped_points", C.c_int64), ("dropped_primes", C.c_int64)]
+                ("d2h_bytes", C.c_int64), ("dropped_points", C.c_int64), ("dropped_primes", C.c_int64),
+                ("graph_replayed", C.c_int64)]
 
 
 class Calib(C.Structure):

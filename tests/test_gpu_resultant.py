@@ -247,3 +247,33 @@ def test_drop_unlucky_matches_formal_degrees(ctx):
     for f, g, r in zip(fs, gs, formal):
         assert r == _oracle(f, g)
     assert d1 == ctx.discriminant_res(pt_f) == list(O.disc_res(pt_f))
+
+
+def test_graph_replay_and_autotuned_blocks(ctx):
+    """A resident batch run twice replays its captured CUDA graph the second time;
+    results are identical with graphs off, and the autotuner has picked a block
+    size for the batch's degree bucket."""
+    from paper_1103_4697_gb300.native import OPT_GRAPH, OPT_STATS
+
+    F, G = W.deg20_batch_arrays(96, 9000, d=7, bits=12)
+    ctx.set_option(OPT_STATS, 1)
+    res = ctx.upload_pairs(F, G)
+    res.run()                      # first sighting of the plan: plain launches
+    first = res.fetch()
+    res.run()                      # second: captured, then launched as a graph
+    res.run()                      # third: replayed
+    st = ctx.stats()
+    second = res.fetch()
+    ctx.set_option(OPT_GRAPH, 0)
+    try:
+        res.run()
+        plain = res.fetch()
+        st_plain = ctx.stats()
+    finally:
+        ctx.set_option(OPT_GRAPH, 1)
+        ctx.set_option(OPT_STATS, 0)
+    res.free()
+    assert st["graph_replayed"] == 1 and st_plain["graph_replayed"] == 0
+    assert first == second == plain
+    for q in (0, 37, 95):
+        assert first[q] == list(O.res_subres(F[q], G[q]))
