@@ -149,7 +149,8 @@ def oracle_baseline(pairs_per_core: int = 1, cores: int | None = None) -> dict:
 # --------------------------------------------------------------------------- serving
 
 
-def serving_run(ctx, n_burst: int = 1500, n_stream: int = 6000, load: float = 0.8, seed: int = 5) -> dict:
+def serving_run(ctx, n_burst: int = 1500, n_stream: int = 6000, load: float = 0.8, seed: int = 5,
+                capacity: float | None = None) -> dict:
     """Open-loop Poisson stream of mixed resultant/gcd requests (degree log-uniform
     5..30, 8..64-bit coefficients, 10 % planted factors): capacity from a burst, then
     a stream at `load` x capacity; latency = completion - scheduled arrival."""
@@ -208,10 +209,12 @@ def serving_run(ctx, n_burst: int = 1500, n_stream: int = 6000, load: float = 0.
         th.join()
         return t0, done
 
-    burst = W.serving_stream(seed, n_burst, rate=1e12)
-    jb, kb = prepare(burst)
-    t0, done = run(jb, [0.0] * len(jb))
-    capacity = len(jb) / (max(done) - t0)
+    if capacity is None:
+        burst = W.serving_stream(seed, n_burst, rate=1e12)
+        jb, kb = prepare(burst)
+        run(jb, [0.0] * len(jb))                   # warm-up: caches, tables, streams
+        t0, done = run(jb, [0.0] * len(jb))
+        capacity = len(jb) / (max(done) - t0)
     rate = load * capacity
     stream = W.serving_stream(seed + 1, n_stream, rate=rate)
     js, ks = prepare(stream)
@@ -403,6 +406,114 @@ def run_reference(args) -> None:
     print(json.dumps(line))
 
 
+# --------------------------------------------------------------------------- other workloads
+
+
+def _time_calls(fn, reps: int) -> float:
+    import torch
+
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(reps):
+        fn()
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t) / reps
+
+
+def _oracle_time(fn, *a) -> float:
+    t = time.perf_counter()
+    fn(*a)
+    return time.perf_counter() - t
+
+
+def run_config(args) -> None:
+    """Measurements for the other workloads (one JSON line each):
+    small   one dense degree-6 pair, res_y and gcd(f(x,0), g(x,0)), one call each;
+    deg20   one degree-20 pair, res_y(f, g) and res_y(f, f_y), one call each;
+    mixed   4096 mixed pairs (degrees 4..16, 8..32-bit, 25 % planted), resident batch,
+            and 4096 gcd jobs (degrees 30..200, planted degree-5 factor);
+    conic   product of 8 conics (+ sparse terms) against a dense degree-24 curve with
+            64-bit coefficients: res_y(f, g) and res_y(f, f_y), one call each;
+    serve   Poisson streams of mixed requests at 0.5, 0.8 and 0.95 of the measured capacity."""
+    import torch
+
+    import oracle as O
+    from paper_1103_4697_gb300 import api
+    from paper_1103_4697_gb300 import native as N
+    from paper_1103_4697_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    ctx = api.Context(device=0, mem_budget=args.mem_gb << 30)
+    out = {"config": args.config, "data": "synthetic", "n_gpus": 1}
+    if args.config == "small":
+        f, g = W.small_dense_pair(1)
+        p, q = list(f[0]), list(g[0])
+        ctx.resultant(f, g)
+        ctx.gcd(p, q)
+        out["res_ms"] = _time_calls(lambda: ctx.resultant(f, g), 20) * 1e3
+        out["gcd_ms"] = _time_calls(lambda: ctx.gcd(p, q), 20) * 1e3
+        out["oracle_res_ms"] = _oracle_time(O.res_bareiss, f, g) * 1e3
+        out["oracle_gcd_ms"] = _oracle_time(O.gcd_z, p, q) * 1e3
+        out["workload"] = "dense total degree 6, coefficients in [-128, 127] (seed 1)"
+    elif args.config == "deg20":
+        f, g = W.deg20_pair(2)
+        ctx.resultant(f, g)
+        out["res_ms"] = _time_calls(lambda: ctx.resultant(f, g), 10) * 1e3
+        out["disc_ms"] = _time_calls(lambda: ctx.discriminant_res(f), 10) * 1e3
+        out["oracle_res_ms"] = _oracle_time(O.res_evalz, f, g) * 1e3
+        out["oracle_disc_ms"] = _oracle_time(O.disc_res, f, "evalz") * 1e3
+        out["workload"] = "dense total degree 20, 16-bit (seed 2), one call per resultant"
+    elif args.config == "conic":
+        f, g = W.conic_curves(4)
+        info = api.resultant_info(f, g)
+        dinfo = api.resultant_info(f, None, disc=True)
+        ctx.resultant(f, g)
+        out["res_ms"] = _time_calls(lambda: ctx.resultant(f, g), 5) * 1e3
+        out["disc_ms"] = _time_calls(lambda: ctx.discriminant_res(f), 5) * 1e3
+        out["primes"] = {"res": info["primes"], "disc": dinfo["primes"]}
+        out["oracle_res_ms"] = _oracle_time(O.res_evalz, f, g) * 1e3
+        out["workload"] = "8 conics + 16 monomials (32-bit) vs dense degree 24, 64-bit (seed 4)"
+    elif args.config == "mixed":
+        ps = W.mixed_batch(3, PAIRS)
+        ctx.set_option(N.OPT_STATS, 1)
+        res = ctx.upload_pairs(ps.f, ps.g)
+        for _ in range(3):
+            res.run()
+        st0 = ctx.stats()
+        sec = _time_calls(res.run, 10)
+        outs = res.fetch()
+        assert all(outs[i] == [] for i in range(PAIRS) if ps.planted[i])
+        res.free()
+        out["res_solves_per_s"] = PAIRS / sec
+        out["res_stages_ms"] = {k: st0[k] for k in ("bounds_ms", "reduce_ms", "evalres_ms", "interp_ms", "crt_ms")}
+        P, Q, H = W.gcd_batch(3, PAIRS)
+        ctx.gcd_batch(P, Q)
+        gsec = _time_calls(lambda: ctx.gcd_batch(P, Q), 3)
+        out["gcd_jobs_per_s"] = PAIRS / gsec
+        t = time.perf_counter()
+        for i in range(4):
+            O.res_evalz(ps.f[i], ps.g[i])
+        out["oracle_res_solves_per_s_1core"] = 4 / (time.perf_counter() - t)
+        t = time.perf_counter()
+        for i in range(4):
+            O.gcd_z(P[i], Q[i])
+        out["oracle_gcd_jobs_per_s_1core"] = 4 / (time.perf_counter() - t)
+        out["workload"] = "4096 pairs deg_x, deg_y ~ U{4..16}, 8..32-bit, 25% planted (seed 3); 4096 gcds deg 30..200"
+    elif args.config == "serve":
+        res_all = {}
+        cap = None
+        for load in (0.5, 0.8, 0.95):
+            r = serving_run(ctx, n_burst=3000, n_stream=args.serve_requests, load=load, seed=5, capacity=cap)
+            cap = r["capacity_rps"]
+            res_all[str(load)] = {k: r[k] for k in ("p50_ms", "p99_ms", "throughput_rps", "offered_rps")}
+        out["capacity_rps"] = cap
+        out["loads"] = res_all
+        out["workload"] = (f"{args.serve_requests} Poisson-arrival requests per load, 50/50 res_y/gcd, degree "
+                           "log-uniform 5..30, 8..64-bit, 10% planted (seed 5)")
+    ctx.close()
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -411,6 +522,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mem-gb", type=int, default=24)
     ap.add_argument("--pairs", type=int, default=PAIRS, help="pairs per GPU (smaller only for profiling)")
+    ap.add_argument("--config", choices=["headline", "small", "deg20", "mixed", "conic", "serve"],
+                    default="headline", help="other workloads print their own JSON line")
+    ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
@@ -418,6 +532,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.config != "headline":
+        run_config(args)
     else:
         run_ours(args)
 

@@ -271,10 +271,10 @@ int gbr_ctx::ensure_tables(int K, int T) {
 }
 
 // Inverse Vandermonde matrices are cached per point count P for the first K
-// primes; the cache is bounded (least recently used entries are dropped).
-static const size_t kVinvCacheBytes = (size_t)1 << 30;
-
+// primes; the cache is bounded by a quarter of the context's budget (at least
+// 256 MiB), least recently used entries are dropped.
 const uint32_t *gbr_ctx::get_vinv(int P, int K, int sym) {
+    const size_t kVinvCacheBytes = std::max<size_t>((size_t)256 << 20, budget / 4);
     const int key = 2 * P + (sym ? 1 : 0);
     auto it = vinv.find(key);
     if (it != vinv.end() && it->second.K >= K) {
