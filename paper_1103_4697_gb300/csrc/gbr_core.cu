@@ -7,7 +7,10 @@
 // offsets and degree-bucketed work lists.  Everything after that runs in the
 // stage kernels of gbr_res.cu.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <functional>
+#include <thread>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -341,6 +344,157 @@ void gbr_ctx::autotune_record(const char *kernel, int key, int value) {
     std::fclose(f);
 }
 
+// ------------------------------------------------------------------ result storage
+
+// All results of one call live in one host block; a registry maps each block's
+// address range to its reference count (one per non-zero result).
+// gbr_free_result releases one reference; with the last one the block is
+// freed, or, if it is pinned memory, kept in a small pool so that the next
+// fetch can copy device results straight into it.
+namespace {
+struct ResBlock {
+    char *base;
+    size_t size;
+    int64_t refs;
+    bool pinned;
+};
+std::mutex g_res_mu;
+std::map<uintptr_t, ResBlock> g_res;          // by base address
+std::vector<std::pair<char *, size_t>> g_pool; // free pinned blocks
+size_t g_pool_bytes = 0;
+const size_t kPoolMaxBytes = (size_t)2 << 30;
+size_t round16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+void register_block(char *base, size_t size, int64_t refs, bool pinned) {
+    std::lock_guard<std::mutex> g(g_res_mu);
+    g_res[(uintptr_t)base] = ResBlock{base, size, refs, pinned};
+}
+}  // namespace
+
+// Pinned block of at least `bytes` from the pool (or a new one); nullptr if
+// pinned memory cannot be had.  The caller registers it once filled.
+char *gbr_pinned_result_block(size_t bytes, size_t *got) {
+    {
+        std::lock_guard<std::mutex> g(g_res_mu);
+        size_t best = SIZE_MAX, bi = 0;
+        for (size_t i = 0; i < g_pool.size(); ++i)
+            if (g_pool[i].second >= bytes && g_pool[i].second < best) {
+                best = g_pool[i].second;
+                bi = i;
+            }
+        if (best != SIZE_MAX) {
+            char *b = g_pool[bi].first;
+            *got = g_pool[bi].second;
+            g_pool_bytes -= g_pool[bi].second;
+            g_pool.erase(g_pool.begin() + bi);
+            return b;
+        }
+    }
+    void *p = nullptr;
+    size_t sz = std::max(bytes, (size_t)1 << 20);
+    if (cudaHostAlloc(&p, sz, cudaHostAllocPortable) != cudaSuccess) return nullptr;
+    *got = sz;
+    return (char *)p;
+}
+
+void gbr_register_result_block(char *base, size_t size, int64_t refs, bool pinned) {
+    if (refs > 0) {
+        register_block(base, size, refs, pinned);
+        return;
+    }
+    // nothing references it: give it back at once
+    if (pinned) {
+        std::lock_guard<std::mutex> g(g_res_mu);
+        g_pool.push_back({base, size});
+        g_pool_bytes += size;
+    } else {
+        std::free(base);
+    }
+}
+
+bool gbr_alloc_results(gbr_bigpoly *out, int count) {
+    size_t total = 0;
+    int64_t live = 0;
+    for (int i = 0; i < count; ++i)
+        if (out[i].deg >= 0) {
+            total += round16((size_t)(out[i].deg + 1) * out[i].limbs * 4) + round16((size_t)out[i].deg + 1);
+            ++live;
+        }
+    for (int i = 0; i < count; ++i) {
+        out[i].mag = nullptr;
+        out[i].sign = nullptr;
+    }
+    if (!live) return true;
+    char *base = (char *)std::malloc(total);
+    if (!base) return false;
+    size_t off = 0;
+    for (int i = 0; i < count; ++i) {
+        if (out[i].deg < 0) continue;
+        out[i].mag = (uint32_t *)(base + off);
+        off += round16((size_t)(out[i].deg + 1) * out[i].limbs * 4);
+        out[i].sign = (int8_t *)(base + off);
+        off += round16((size_t)out[i].deg + 1);
+    }
+    register_block(base, total, live, false);
+    return true;
+}
+
+extern "C" void gbr_free_result(gbr_ctx *, gbr_bigpoly *b) {
+    if (!b) return;
+    if (b->mag) {
+        char *release = nullptr;
+        bool pinned = false;
+        size_t size = 0;
+        {
+            std::lock_guard<std::mutex> g(g_res_mu);
+            auto it = g_res.upper_bound((uintptr_t)b->mag);
+            if (it != g_res.begin()) {
+                --it;
+                ResBlock &blk = it->second;
+                if ((uintptr_t)b->mag < (uintptr_t)blk.base + blk.size && --blk.refs == 0) {
+                    release = blk.base;
+                    pinned = blk.pinned;
+                    size = blk.size;
+                    g_res.erase(it);
+                    if (pinned && g_pool_bytes + size <= kPoolMaxBytes) {
+                        g_pool.push_back({release, size});
+                        g_pool_bytes += size;
+                        release = nullptr;
+                    }
+                }
+            }
+        }
+        if (release) {
+            if (pinned) cudaFreeHost(release);
+            else std::free(release);
+        }
+    }
+    b->mag = nullptr;
+    b->sign = nullptr;
+    b->deg = -1;
+}
+
+// Runs fn(lo, hi) over [0, n) on up to `threads` host threads.
+void gbr_parallel_for(int n, int threads, const std::function<void(int, int)> &fn) {
+    if (n <= 0) return;
+    threads = std::max(1, std::min(threads, n / 64 + 1));
+    if (threads == 1) {
+        fn(0, n);
+        return;
+    }
+    std::vector<std::thread> ts;
+    for (int t = 0; t < threads; ++t) {
+        int lo = (int)((int64_t)n * t / threads), hi = (int)((int64_t)n * (t + 1) / threads);
+        ts.emplace_back([&, lo, hi] { fn(lo, hi); });
+    }
+    for (auto &th : ts) th.join();
+}
+
+static int host_threads() {
+    unsigned h = std::thread::hardware_concurrency();
+    return (int)std::min<unsigned>(8, h ? h : 1);
+}
+
 // ------------------------------------------------------------------ status strings
 
 extern "C" const char *gbr_strerror(int s) {
@@ -606,17 +760,13 @@ extern "C" int gbr_upload_pairs(gbr_ctx *c, int n, const gbr_bipoly *f, const gb
         gbr_free_resident_locked(c, r);
         return c->fail(GBR_ENOMEM, "pinned host staging");
     }
-    int64_t pos = 0;
-    for (int i = 0; i < n; ++i) {
-        int64_t wf = bipoly_words(&f[i]);
-        std::memcpy(h + pos, f[i].coef, wf * 8);
-        pos += wf;
-        if (!disc) {
-            int64_t wg = bipoly_words(&g[i]);
-            std::memcpy(h + pos, g[i].coef, wg * 8);
-            pos += wg;
+    gbr_parallel_for(n, host_threads(), [&](int lo, int hi) {
+        for (int i = lo; i < hi; ++i) {
+            int64_t pos = r->h_desc[i].f.off;
+            std::memcpy(h + pos, f[i].coef, bipoly_words(&f[i]) * 8);
+            if (!disc) std::memcpy(h + r->h_desc[i].g.off, g[i].coef, bipoly_words(&g[i]) * 8);
         }
-    }
+    });
     cudaError_t e = cudaSuccess;
     if (bytes) e = cudaMemcpyAsync(r->d_coef, h, bytes, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && n)
@@ -1111,43 +1261,41 @@ int gbr_fetch_resident_locked(gbr_ctx *c, gbr_resident *r, int first, int count,
     int last = first + count - 1;
     int64_t o0 = plan[first].out_off, o1 = plan[last].out_off + (int64_t)plan[last].P * plan[last].L;
     int64_t s0 = plan[first].sign_off, s1 = plan[last].sign_off + plan[last].P;
-    size_t need = (size_t)(o1 - o0) * 4 + (size_t)(s1 - s0) + (size_t)count * 4 + 64;
-    char *h = (char *)c->pinned(need, 3);
-    if (!h) return c->fail(GBR_ENOMEM, "pinned host staging");
-    uint32_t *hm = (uint32_t *)h;
-    int32_t *hd = (int32_t *)(h + (size_t)(o1 - o0) * 4);
-    int8_t *hs = (int8_t *)(hd + count);
+    // the device layout is copied as is into one pinned block that becomes the
+    // results' storage: magnitudes, then signs, then the degrees
+    const size_t mag_b = round16((size_t)(o1 - o0) * 4), sign_b = round16((size_t)(s1 - s0));
+    const size_t need = mag_b + sign_b + (size_t)count * 4;
+    size_t got = 0;
+    char *blk = gbr_pinned_result_block(need, &got);
+    if (!blk) return c->fail(GBR_ENOMEM, "pinned host memory for the results");
+    uint32_t *hm = (uint32_t *)blk;
+    int8_t *hs = (int8_t *)(blk + mag_b);
+    int32_t *hd = (int32_t *)(blk + mag_b + sign_b);
     cudaStream_t s = c->stream;
     cudaError_t e = cudaSuccess;
     if (o1 > o0) e = cudaMemcpyAsync(hm, r->d_out + o0, (size_t)(o1 - o0) * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hd, r->d_deg + first, (size_t)count * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && s1 > s0) e = cudaMemcpyAsync(hs, r->d_sign + s0, (size_t)(s1 - s0), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "result readback", e);
+    if (e != cudaSuccess) {
+        gbr_register_result_block(blk, got, 0, true);
+        return c->fail(GBR_EDEVICE, "result readback", e);
+    }
     c->stats.d2h_bytes += (o1 - o0) * 4 + (int64_t)count * 4 + (s1 - s0);
+    int64_t live = 0;
     for (int i = 0; i < count; ++i) {
         const PairPlan &p = plan[first + i];
         gbr_bigpoly &b = out[i];
-        b.deg = (p.flags & PLAN_ZERO) ? -1 : hd[i];
+        b.deg = (p.flags & PLAN_ZERO) ? -1 : std::max(hd[i], -1);
         b.limbs = p.L;
         b.mag = nullptr;
         b.sign = nullptr;
-        if (b.deg < 0) {
-            b.deg = -1;
-            continue;
-        }
-        size_t nm = (size_t)(b.deg + 1) * p.L;
-        b.mag = (uint32_t *)std::malloc(nm * 4);
-        b.sign = (int8_t *)std::malloc((size_t)b.deg + 1);
-        if (!b.mag || !b.sign) {
-            std::free(b.mag);
-            std::free(b.sign);
-            for (int j = 0; j < i; ++j) gbr_free_result(c, &out[j]);
-            return c->fail(GBR_ENOMEM, "host result allocation");
-        }
-        std::memcpy(b.mag, hm + (p.out_off - o0), nm * 4);
-        std::memcpy(b.sign, hs + (p.sign_off - s0), (size_t)b.deg + 1);
+        if (b.deg < 0) continue;
+        b.mag = hm + (p.out_off - o0);
+        b.sign = hs + (p.sign_off - s0);
+        ++live;
     }
+    gbr_register_result_block(blk, got, live, true);
     return GBR_OK;
 }
 
@@ -1158,14 +1306,6 @@ extern "C" int gbr_fetch_resident(gbr_ctx *c, gbr_resident *r, int first, int co
     return gbr_fetch_resident_locked(c, r, first, count, out);
 }
 
-extern "C" void gbr_free_result(gbr_ctx *, gbr_bigpoly *b) {
-    if (!b) return;
-    std::free(b->mag);
-    std::free(b->sign);
-    b->mag = nullptr;
-    b->sign = nullptr;
-    b->deg = -1;
-}
 
 // ------------------------------------------------------------------ one-shot and batch wrappers
 

@@ -125,5 +125,8 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r);
 int gbr_fetch_resident_locked(gbr_ctx *c, gbr_resident *r, int first, int count, gbr_bigpoly *out);
 void gbr_free_resident_locked(gbr_ctx *c, gbr_resident *r);
 void gbr_serve_shutdown(gbr_ctx *c);
+bool gbr_alloc_results(gbr_bigpoly *out, int count);   // one refcounted host block for a call's results
+char *gbr_pinned_result_block(size_t bytes, size_t *got);
+void gbr_register_result_block(char *base, size_t size, int64_t refs, bool pinned);
 gbr_ctx *gbr_make_worker(gbr_ctx *parent);    // own stream and tables, parent's arena
 void gbr_destroy_worker(gbr_ctx *w);

@@ -465,9 +465,7 @@ void set_big_int(gbr_bigpoly &b, const std::vector<std::pair<uint64_t, int>> &co
     b.mag = nullptr;
     b.sign = nullptr;
     if (b.deg < 0) return;
-    b.mag = (uint32_t *)std::malloc(sizeof(uint32_t) * 2 * coef.size());
-    b.sign = (int8_t *)std::malloc(coef.size());
-    if (!b.mag || !b.sign) return;
+    if (!gbr_alloc_results(&b, 1)) return;
     for (size_t i = 0; i < coef.size(); ++i) {
         b.mag[2 * i] = (uint32_t)coef[i].first;
         b.mag[2 * i + 1] = (uint32_t)(coef[i].first >> 32);
@@ -776,9 +774,7 @@ static int gcd_batch_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upo
                 gbr_bigpoly &b = out[i];
                 b.deg = od[i];
                 b.limbs = G.Lout;
-                b.mag = (uint32_t *)std::malloc((size_t)(b.deg + 1) * G.Lout * 4);
-                b.sign = (int8_t *)std::malloc((size_t)b.deg + 1);
-                if (!b.mag || !b.sign) return c->fail(GBR_ENOMEM, "host result allocation");
+                if (!gbr_alloc_results(&b, 1)) return c->fail(GBR_ENOMEM, "host result allocation");
                 std::memcpy(b.mag, hout.data() + G.out_off, (size_t)(b.deg + 1) * G.Lout * 4);
                 std::memcpy(b.sign, hos.data() + G.osign_off, (size_t)b.deg + 1);
             }
