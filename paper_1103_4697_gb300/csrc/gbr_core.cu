@@ -292,13 +292,18 @@ const uint32_t *gbr_ctx::get_vinv(int P, int K, int sym) {
         return t;
     };
     if (it != vinv.end()) {
+        if (it->second.last_use > vinv_run_mark) return nullptr;   // held by this run with a smaller K
         dfree(it->second.d);
         vinv.erase(it);
     }
-    while (!vinv.empty() && total() + bytes > kVinvCacheBytes) {
-        auto lru = vinv.begin();
+    // evict least recently used entries, never one that the current run already
+    // holds (used after vinv_run_mark)
+    while (total() + bytes > kVinvCacheBytes) {
+        auto lru = vinv.end();
         for (auto jt = vinv.begin(); jt != vinv.end(); ++jt)
-            if (jt->second.last_use < lru->second.last_use) lru = jt;
+            if (jt->second.last_use <= vinv_run_mark && (lru == vinv.end() || jt->second.last_use < lru->second.last_use))
+                lru = jt;
+        if (lru == vinv.end()) return nullptr;
         dfree(lru->second.d);
         vinv.erase(lru);
     }
@@ -1007,6 +1012,7 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
     };
     std::vector<Gemm> gemms;
     std::vector<int32_t> gemm_pairs;
+    c->vinv_run_mark = c->vinv_clock;
     for (auto &kv : pgroups) {
         const std::vector<int32_t> &qs = kv.second;
         int K = 0;
@@ -1037,6 +1043,28 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
     size_t o_gemm = (blk.size() + 7) / 8 * 8;
     blk.resize(o_gemm + gemm_pairs.size() * 4 + 4);
     if (!gemm_pairs.empty()) std::memcpy(blk.data() + o_gemm, gemm_pairs.data(), gemm_pairs.size() * 4);
+    // one contraction launch for all groups: group table and tile list (tiles of
+    // one group and prime are adjacent so its V^-1 rows stay in L2)
+    std::vector<GemmGroup> ggroups;
+    std::vector<GemmTile> gtiles;
+    for (size_t gi = 0; gi < gemms.size(); ++gi) {
+        const Gemm &gm = gemms[gi];
+        GemmGroup gg;
+        gg.vinv = gm.vinv;
+        gg.pairs_off = (int64_t)(o_gemm + gm.off * sizeof(int32_t));   // the block is (re)allocated later
+        gg.P = gm.P;
+        gg.npairs = gm.n;
+        ggroups.push_back(gg);
+        for (int i = 0; i < gm.K; ++i)
+            for (int c0 = 0; c0 < gm.P; c0 += kGemmTileM)
+                for (int q0 = 0; q0 < gm.n; q0 += kGemmTileN) gtiles.push_back({(int32_t)gi, c0, q0, i});
+    }
+    size_t o_ggroups = (blk.size() + 15) / 16 * 16;
+    blk.resize(o_ggroups + ggroups.size() * sizeof(GemmGroup) + 16);
+    if (!ggroups.empty()) std::memcpy(blk.data() + o_ggroups, ggroups.data(), ggroups.size() * sizeof(GemmGroup));
+    size_t o_gtiles = (blk.size() + 15) / 16 * 16;
+    blk.resize(o_gtiles + gtiles.size() * sizeof(GemmTile) + 16);
+    if (!gtiles.empty()) std::memcpy(blk.data() + o_gtiles, gtiles.data(), gtiles.size() * sizeof(GemmTile));
     size_t o_pmap = (blk.size() + 7) / 8 * 8;
     blk.resize(o_pmap + pmap.size() * 4 + 4);
     if (!pmap.empty()) std::memcpy(blk.data() + o_pmap, pmap.data(), pmap.size() * 4);
@@ -1080,42 +1108,33 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
     L.pflags = r->d_flags;
     L.gtab = r->d_gtab;
     L.dropped = (unsigned long long *)(c->d_err + 2);
-    // ---- autotuning: the first run of an unseen degree bucket times the
-    // candidate block sizes of the evaluation kernel (results are identical)
-    std::vector<int> ev_block;
-    {
-        size_t bi = 0;
-        for (auto &kv : evb) {
-            const int key = kv.first;
-            auto it = c->tuned_evalres.find(key);
-            if (it != c->tuned_evalres.end()) {
-                ev_block.push_back(it->second);
-                ++bi;
-                continue;
+    // ---- autotuning: a plain run that meets an unseen degree bucket times the
+    // candidate block sizes of the evaluation kernel on the real work (after the
+    // reduction; every candidate writes the same values, so the last one stands)
+    auto evalres_bucket = [&](int key, const WorkList &w, cudaStream_t q, bool capturing) -> cudaError_t {
+        auto it = c->tuned_evalres.find(key);
+        if (it != c->tuned_evalres.end()) return launch_evalres(L, w, key, key, it->second, q);
+        if (capturing) return launch_evalres(L, w, key, key, 128, q);
+        float best = 1e30f;
+        int best_block = 128;
+        for (int cand : {64, 128, 256}) {
+            if ((size_t)2 * key * cand * 4 > (size_t)kMaxDynSmem) continue;
+            cudaEventRecord(c->ev[6], q);
+            cudaError_t x = launch_evalres(L, w, key, key, cand, q);
+            cudaEventRecord(c->ev[7], q);
+            if (x == cudaSuccess) x = cudaEventSynchronize(c->ev[7]);
+            if (x != cudaSuccess) return x;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, c->ev[6], c->ev[7]);
+            if (ms < best) {
+                best = ms;
+                best_block = cand;
             }
-            WorkList w = mk(o_ev[bi].first, o_ev[bi].second, kv.second);
-            float best = 1e30f;
-            int best_block = 128;
-            for (int cand : {64, 128, 256}) {
-                if ((size_t)2 * key * cand * 4 > (size_t)kMaxDynSmem) continue;
-                cudaEventRecord(c->ev[6], s);
-                e = launch_evalres(L, w, key, key, cand, s);
-                cudaEventRecord(c->ev[7], s);
-                if (e == cudaSuccess) e = cudaEventSynchronize(c->ev[7]);
-                if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "autotuning", e);
-                float ms = 0;
-                cudaEventElapsedTime(&ms, c->ev[6], c->ev[7]);
-                if (ms < best) {
-                    best = ms;
-                    best_block = cand;
-                }
-            }
-            c->tuned_evalres[key] = best_block;
-            c->autotune_record("evalres", key, best_block);
-            ev_block.push_back(best_block);
-            ++bi;
         }
-    }
+        c->tuned_evalres[key] = best_block;
+        c->autotune_record("evalres", key, best_block);
+        return cudaSuccess;
+    };
     // ---- the device stages; replayed from a captured CUDA graph when the plan repeats
     int64_t kernels = 1;
     auto record = [&](int idx, bool capturing, cudaStream_t q) {
@@ -1139,7 +1158,7 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
         size_t bi = 0;
         for (auto &kv : evb) {
             if (x != cudaSuccess) break;
-            x = launch_evalres(L, mk(o_ev[bi].first, o_ev[bi].second, kv.second), kv.first, kv.first, ev_block[bi], q);
+            x = evalres_bucket(kv.first, mk(o_ev[bi].first, o_ev[bi].second, kv.second), q, capturing);
             kernels++;
             ++bi;
         }
@@ -1148,9 +1167,9 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
             x = launch_interp(L, mk(o_int_p, o_int_s, interp), Pmax, q);
             kernels++;
         }
-        for (const Gemm &gm : gemms) {
-            if (x != cudaSuccess) break;
-            x = launch_interp_gemm(L, (const int32_t *)(r->d_planblk + o_gemm) + gm.off, gm.n, gm.P, gm.K, gm.vinv, q);
+        if (x == cudaSuccess && !gtiles.empty()) {
+            x = launch_interp_gemm(L, r->d_planblk, (const GemmGroup *)(r->d_planblk + o_ggroups),
+                                   (const GemmTile *)(r->d_planblk + o_gtiles), (int)gtiles.size(), q);
             kernels++;
         }
         record(4, capturing, q);
@@ -1168,7 +1187,6 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
                                       (uintptr_t)c->d_garner,  (uintptr_t)c->d_invk, (uintptr_t)c->d_err,
                                       (uintptr_t)c->d_mods,    (uintptr_t)c->stats_on};
         for (const Gemm &gm : gemms) key.push_back((uintptr_t)gm.vinv);
-        for (int b : ev_block) key.push_back((uintptr_t)b);
         const bool same = r->gkey == key && r->gblk.size() == blk.size() &&
                           std::memcmp(r->gblk.data(), blk.data(), blk.size()) == 0;
         if (!same) {

@@ -71,7 +71,7 @@ struct gbr_ctx {
         uint64_t last_use = 0;
     };
     std::map<int, Vinv> vinv;      // inverse Vandermonde matrices, key 2 P + sym
-    uint64_t vinv_clock = 0;
+    uint64_t vinv_clock = 0, vinv_run_mark = 0;
     const uint32_t *get_vinv(int P, int K, int sym);   // nullptr if it cannot be built
     gbr::ServeState *serve = nullptr;
     std::map<int, int> tuned_evalres;   // degree bucket -> block size chosen by the autotuner

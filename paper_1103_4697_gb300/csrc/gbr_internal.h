@@ -207,11 +207,14 @@ struct WorkList {
 };
 
 // pairs sharing a point count needed before interpolation uses the contraction
-constexpr int kGemmMinPairs = 16;
+// (its inverse Vandermonde matrix is cached per point count; Newton is the
+// fallback when the matrix cannot be cached)
+constexpr int kGemmMinPairs = 1;
 
 // dynamic shared memory ceiling set once for every kernel (bytes)
 constexpr int kMaxDynSmem = 200 * 1024;
 cudaError_t configure_res_kernels();
+cudaError_t configure_evalres_kernel();
 cudaError_t configure_gcd_kernels();
 
 cudaError_t launch_bounds(const ResLaunch &L, cudaStream_t s);
@@ -224,8 +227,19 @@ cudaError_t launch_vinv(const ModP *mods, int P, int K, int sym, uint32_t *out, 
 cudaError_t launch_unlucky_primes(const ResLaunch &L, int kc, uint8_t *out, cudaStream_t s);
 cudaError_t launch_pair_garner(const ResLaunch &L, const int32_t *pairs, int n, int kmax, uint32_t *gtab,
                                cudaStream_t s);
-cudaError_t launch_interp_gemm(const ResLaunch &L, const int32_t *gpairs, int npairs, int P, int K,
-                               const uint32_t *vinv, cudaStream_t s);
+// Interpolation as a contraction: pairs sharing a point count form a group;
+// the launch covers tiles of 64 coefficients x 64 pairs x one prime.
+struct GemmGroup {
+    const uint32_t *vinv;   // [prime][P][P] inverse Vandermonde matrices
+    int64_t pairs_off;      // the group's pair ids: int32 entries at this byte offset of the plan block
+    int32_t P, npairs;
+};
+struct GemmTile {
+    int32_t group, c0, q0, prime;
+};
+constexpr int kGemmTileM = 64, kGemmTileN = 64;
+cudaError_t launch_interp_gemm(const ResLaunch &L, const char *planblk, const GemmGroup *groups,
+                               const GemmTile *tiles, int ntiles, cudaStream_t s);
 cudaError_t launch_zero_init(const ResLaunch &L, cudaStream_t s);
 
 }  // namespace gbr
