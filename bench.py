@@ -350,7 +350,7 @@ def run_ours(args) -> None:
     ctx.close()
     if rank != 0:
         return
-    kernel_src = os.path.join(ROOT, "paper_1103_4697_gb300", "csrc", "gbr_res.cu")
+    kernel_src = os.path.join(ROOT, "paper_1103_4697_gb300", "csrc", "gbr_evalres.cu")
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True, "scaling": "weak",
