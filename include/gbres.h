@@ -299,7 +299,10 @@ int gbr_primes_for_bits(double bits);
 /* Resultant planning for a pair given on the host: actual degrees m, n, the
  * x-degree bound D (min of n deg_x f + m deg_x g and the total-degree Bezout
  * bound), log2 of the Hadamard bound B on |coefficients| and the number of
- * primes k with prod p > 2B + 1.  Host only.  disc = 1 uses g = df/dvar. */
+ * primes k with prod p > 2B + 1.  Host only.  disc = 1 uses g = df/dvar.
+ * B is the smallest scaled bound over all lambda values; the device planner
+ * picks its lambda with a single-precision search, so in a near tie it may
+ * use a slightly larger (equally valid) B and one prime more. */
 typedef struct {
     int32_t m, n, deg_bound, primes, limbs;
     double log2_bound;

@@ -137,9 +137,10 @@ GBR_HD double scaled_hadamard_log2(const double *lf, int m, const double *lg, in
 // log2 lambda values the planner tries (the bound is valid for each; the
 // smallest is used)
 constexpr int kBoundLambdas = 13;
+// (0, 0.25, 0.5, 0.75, 1, 1.5, 2, 3, 4, 5, 6, -0.5, -1), computed rather than
+// indexed so that no table lands in a kernel's local memory
 GBR_HD double bound_lambda(int l) {
-    const double v[kBoundLambdas] = {0.0, 0.25, 0.5, 0.75, 1.0, 1.5, 2.0, 3.0, 4.0, 5.0, 6.0, -0.5, -1.0};
-    return v[l];
+    return l < 5 ? 0.25 * l : l < 7 ? 1.0 + 0.5 * (l - 4) : l < 11 ? (double)(l - 4) : -0.5 * (l - 10);
 }
 
 GBR_HD double best_scaled_bound(const double *lf, int m, const double *lg, int n, double *ef, double *eg) {

@@ -80,8 +80,11 @@ __device__ __forceinline__ const uint64_t *coef_ptr(const uint64_t *coef, const 
 
 // Scans one polynomial row by row (one warp per pair): row degrees, log2 of the
 // row 1-norms, degrees.  For disc, g = d f / d var is formed on the fly:
-// g_r = (r+1) f_{r+1}.  The row norms are kept in shared memory and every lane
-// evaluates the scaled Hadamard bound for one lambda; the minimum is kept.
+// g_r = (r+1) f_{r+1}.  The row norms are kept in shared memory; the warp
+// ranks the lambda values by a single-precision evaluation of the scaled
+// Hadamard bound and evaluates the best one again in double precision, which
+// is the value the plan uses (FP64 transcendentals are slow on this part, and
+// any lambda gives a valid bound).
 constexpr int kBoundsWarps = 4;
 
 // log2 of the 1-norm of a row: exact 128-bit sum for int64 coefficients, else
@@ -124,23 +127,29 @@ __device__ double row_log2_norm(const uint64_t *coef, const PolyDesc &P, int r, 
 }
 
 // Warp-parallel evaluation of scaled_hadamard_log2: lanes split the rows for the
-// scaled squared norms and the columns for their logarithms.
-__device__ double scaled_hadamard_log2_warp(const double *lf, int m, const double *lg, int n, double l2lam,
-                                            double *ef, double *eg, int lane) {
-    double M = -INFINITY;
+// scaled squared norms and the columns for their logarithms.  T = double gives
+// the rigorous value; T = float is only used to choose lambda (every lambda
+// gives a valid bound, and the chosen one is evaluated again in double).
+template <typename T>
+__device__ T scaled_hadamard_log2_warp(const double *lf, int m, const double *lg, int n, T l2lam, T *ef, T *eg,
+                                       int lane) {
+    // terms are clamped from below so that every column sum stays positive
+    // (an upward rounding); the float floor stays a normal number
+    const T kFloor = sizeof(T) == 4 ? (T)-120 : (T)-1000;
+    T M = -INFINITY;
     for (int i = lane; i <= m; i += 32)
-        if (lf[i] != -INFINITY) M = fmax(M, lf[i] + i * l2lam);
+        if (lf[i] != -INFINITY) M = fmax(M, (T)lf[i] + i * l2lam);
     for (int j = lane; j <= n; j += 32)
-        if (lg[j] != -INFINITY) M = fmax(M, lg[j] + j * l2lam);
+        if (lg[j] != -INFINITY) M = fmax(M, (T)lg[j] + j * l2lam);
     for (int o = 16; o; o >>= 1) M = fmax(M, __shfl_xor_sync(0xffffffffu, M, o));
-    double sf = 0.0, sg = 0.0;
+    T sf = 0, sg = 0;
     for (int i = lane; i <= m; i += 32) {
-        double t = lf[i] == -INFINITY ? 0.0 : exp2(fmax(2.0 * (lf[i] + i * l2lam - M), -1000.0));
+        T t = lf[i] == -INFINITY ? (T)0 : exp2(fmax((T)2 * ((T)lf[i] + i * l2lam - M), kFloor));
         ef[i] = t;
         sf += t;
     }
     for (int j = lane; j <= n; j += 32) {
-        double t = lg[j] == -INFINITY ? 0.0 : exp2(fmax(2.0 * (lg[j] + j * l2lam - M), -1000.0));
+        T t = lg[j] == -INFINITY ? (T)0 : exp2(fmax((T)2 * ((T)lg[j] + j * l2lam - M), kFloor));
         eg[j] = t;
         sg += t;
     }
@@ -149,27 +158,28 @@ __device__ double scaled_hadamard_log2_warp(const double *lf, int m, const doubl
         sg += __shfl_xor_sync(0xffffffffu, sg, o);
     }
     __syncwarp();
-    double row = 0.0;
-    if (n > 0) row += 0.5 * n * (2.0 * M + log2(sf));
-    if (m > 0) row += 0.5 * m * (2.0 * M + log2(sg));
-    double col = 0.0;
+    T row = 0;
+    if (n > 0) row += (T)0.5 * n * ((T)2 * M + log2(sf));
+    if (m > 0) row += (T)0.5 * m * ((T)2 * M + log2(sg));
+    T col = 0;
     for (int c = lane; c < m + n; c += 32) {
-        double sc = 0.0;
+        T sc = 0;
         int r0 = c - m > 0 ? c - m : 0, r1 = c < n - 1 ? c : n - 1;
         for (int r = r0; r <= r1; ++r) sc += ef[m - (c - r)];
         r0 = c - n > 0 ? c - n : 0;
         r1 = c < m - 1 ? c : m - 1;
         for (int r = r0; r <= r1; ++r) sc += eg[n - (c - r)];
-        col += sc > 0.0 ? 0.5 * (2.0 * M + log2(sc)) : -INFINITY;
+        col += sc > 0 ? (T)0.5 * ((T)2 * M + log2(sc)) : (T)-INFINITY;
     }
     for (int o = 16; o; o >>= 1) col += __shfl_xor_sync(0xffffffffu, col, o);
     __syncwarp();
-    return fmin(row, col) - (double)m * n * l2lam;
+    return fmin(row, col) - (T)m * n * l2lam;
 }
 
 __global__ void __launch_bounds__(kBoundsWarps * 32) k_bounds(ResLaunch L) {
     __shared__ double lnf[kBoundsWarps][GBR_MAX_YDEG + 2], lng[kBoundsWarps][GBR_MAX_YDEG + 2];
     __shared__ double ebuf[kBoundsWarps][2][GBR_MAX_YDEG + 2];
+    __shared__ float fbuf[kBoundsWarps][2][GBR_MAX_YDEG + 2];
     const int wib = threadIdx.x >> 5;
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
@@ -227,10 +237,18 @@ __global__ void __launch_bounds__(kBoundsWarps * 32) k_bounds(ResLaunch L) {
     __syncwarp();
     double lb = 0.0;
     if (B.m >= 0 && B.n >= 0 && B.m <= GBR_MAX_YDEG && B.n <= GBR_MAX_YDEG && (B.m > 0 || B.n > 0)) {
-        lb = INFINITY;
-        for (int l = 0; l < kBoundLambdas; ++l)
-            lb = fmin(lb, scaled_hadamard_log2_warp(lnf[wib], B.m, lng[wib], B.n, bound_lambda(l), ebuf[wib][0],
-                                                    ebuf[wib][1], lane));
+        float bestf = INFINITY;
+        int bestl = 0;
+        for (int l = 0; l < kBoundLambdas; ++l) {
+            float b = scaled_hadamard_log2_warp<float>(lnf[wib], B.m, lng[wib], B.n, (float)bound_lambda(l),
+                                                       fbuf[wib][0], fbuf[wib][1], lane);
+            if (b < bestf) {
+                bestf = b;
+                bestl = l;
+            }
+        }
+        lb = scaled_hadamard_log2_warp<double>(lnf[wib], B.m, lng[wib], B.n, bound_lambda(bestl), ebuf[wib][0],
+                                               ebuf[wib][1], lane);
     }
     B.log2B = lb;
     if (lane == 0) L.bounds[warp] = B;
@@ -437,6 +455,7 @@ __device__ __forceinline__ void mac96(uint32_t &a0, uint32_t &a1, uint32_t &a2, 
 }
 
 constexpr int GT_M = 64, GT_N = 64, GT_K = 32;
+static_assert(GT_M == GT_N && GT_M * GT_K % 256 == 0, "one load layout serves both operands");
 
 // coefficients = Vinv_i * values for one prime i (blockIdx.z) and a group of
 // pairs that share P.  Tile: 64 coefficient rows x 64 pairs, K in chunks of 32
@@ -445,7 +464,7 @@ constexpr int GT_M = 64, GT_N = 64, GT_K = 32;
 // is congruent to coef * 2^32; one reduction per output gives coef.
 // One block per tile of the flattened list of every point-count group's tiles,
 // so all groups share one launch.
-__global__ void __launch_bounds__(256) k_interp_gemm(ResLaunch L, const char *planblk, const GemmGroup *groups,
+__global__ void __launch_bounds__(256, 2) k_interp_gemm(ResLaunch L, const char *planblk, const GemmGroup *groups,
                                                     const GemmTile *tiles) {
     __shared__ uint32_t As[GT_K][GT_M + 1];
     __shared__ __align__(16) uint32_t Bs[GT_K][GT_N + 4];
@@ -476,19 +495,31 @@ __global__ void __launch_bounds__(256) k_interp_gemm(ResLaunch L, const char *pl
     uint32_t a0[16], a1[16], a2[16];
 #pragma unroll
     for (int t = 0; t < 16; ++t) a0[t] = a1[t] = a2[t] = 0u;
-    for (int j0 = 0; j0 < P; j0 += GT_K) {
-        for (int e = threadIdx.x; e < GT_M * GT_K; e += 256) {
-            int r = e / GT_K, kk = e % GT_K;
-            int c = c0 + r, j = j0 + kk;
-            As[kk][r] = (c < P && j < P) ? A[(int64_t)c * P + j] : 0u;
+    // the next chunk's operands are loaded into registers while the current
+    // chunk is multiplied from shared memory (one chunk of loads in flight)
+    constexpr int kLoads = GT_M * GT_K / 256;   // per thread, for A and for B
+    uint32_t ra[kLoads], rb[kLoads];
+    auto load_chunk = [&](int j0) {
+#pragma unroll
+        for (int u = 0; u < kLoads; ++u) {
+            const int e = threadIdx.x + u * 256;
+            const int r = e / GT_K, kk = e % GT_K;
+            const int c = c0 + r, j = j0 + kk;
+            ra[u] = (c < P && j < P) ? A[(int64_t)c * P + j] : 0u;
+            const int64_t b = colbase[r];
+            rb[u] = (b >= 0 && j < P) ? L.val[b + j] : 0u;
         }
-        for (int e = threadIdx.x; e < GT_N * GT_K; e += 256) {
-            int qq = e / GT_K, kk = e % GT_K;
-            int64_t b = colbase[qq];
-            int j = j0 + kk;
-            Bs[kk][qq] = (b >= 0 && j < P) ? L.val[b + j] : 0u;
+    };
+    load_chunk(0);
+    for (int j0 = 0; j0 < P; j0 += GT_K) {
+#pragma unroll
+        for (int u = 0; u < kLoads; ++u) {
+            const int e = threadIdx.x + u * 256;
+            As[e % GT_K][e / GT_K] = ra[u];
+            Bs[e % GT_K][e / GT_K] = rb[u];
         }
         __syncthreads();
+        if (j0 + GT_K < P) load_chunk(j0 + GT_K);
 #pragma unroll 8
         for (int kk = 0; kk < GT_K; ++kk) {
             const uint4 bv = *reinterpret_cast<const uint4 *>(&Bs[kk][tx * 4]);
