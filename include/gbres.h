@@ -119,6 +119,8 @@ typedef struct {
     int64_t dropped_points;   /* GBR_OPT_DROP_UNLUCKY: evaluation points flagged unlucky and replaced */
     int64_t dropped_primes;   /* GBR_OPT_DROP_UNLUCKY: primes skipped because a leading coefficient vanishes */
     int64_t graph_replayed;   /* 1 when the device stages ran as a CUDA graph (GBR_OPT_GRAPH) */
+    int64_t redo_warps;       /* GBR_OPT_REGISTER_FORM: warps of 32 subproblems solved again on
+                                 shared memory */
 } gbr_stats;
 
 /* ------------------------------------------------------------------ context */
@@ -155,6 +157,11 @@ const char *gbr_last_error(gbr_ctx *ctx);
 #define GBR_OPT_INTERP_GEMM  5   /* 1 (default): pairs of a batch that share their number of points
                                     are interpolated by one inverse-Vandermonde contraction per
                                     prime; 0: Newton interpolation for every (pair, prime) */
+#define GBR_OPT_REGISTER_FORM 6  /* 1 (default): pairs of shape (N, N), (N, N-1) or (N-1, N) in the
+                                    eliminated variable, 2 <= N <= 32, are solved with the
+                                    polynomials in registers (warps that meet a vanishing leading
+                                    coefficient or a non-normal remainder sequence are solved again
+                                    on shared memory); 0: every subproblem on shared memory */
 int gbr_set_option(gbr_ctx *ctx, int option, int64_t value);
 int gbr_get_stats(gbr_ctx *ctx, gbr_stats *out);
 

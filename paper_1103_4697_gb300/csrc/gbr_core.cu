@@ -598,6 +598,8 @@ gbr_ctx *gbr_make_worker(gbr_ctx *parent) {
     w->budget = parent->budget;
     w->drop_unlucky = parent->drop_unlucky;
     w->tuned_evalres = parent->tuned_evalres;
+    w->gemm_on = parent->gemm_on;
+    w->reg_on = parent->reg_on;
     w->graph_on = 0;   // serving batches differ every time; graphs would only add capture cost
     w->extra_primes = parent->extra_primes;
     cudaSetDevice(w->device);
@@ -638,6 +640,7 @@ extern "C" int gbr_set_option(gbr_ctx *c, int opt, int64_t v) {
         case GBR_OPT_STATS: c->stats_on = (int)(v != 0); return GBR_OK;
         case GBR_OPT_GRAPH: c->graph_on = (int)(v != 0); return GBR_OK;
         case GBR_OPT_INTERP_GEMM: c->gemm_on = (int)(v != 0); return GBR_OK;
+        case GBR_OPT_REGISTER_FORM: c->reg_on = (int)(v != 0); return GBR_OK;
         case GBR_OPT_EXTRA_PRIMES:
             if (v < 0 || v > 64) return GBR_EINVAL;
             c->extra_primes = (int)v;
@@ -789,7 +792,7 @@ void gbr_free_resident_locked(gbr_ctx *c, gbr_resident *r) {
     if (!r) return;
     for (void *p : {(void *)r->d_coef, (void *)r->d_desc, (void *)r->d_rowdeg, (void *)r->d_bounds, (void *)r->d_deg,
                     (void *)r->d_planblk, (void *)r->d_res, (void *)r->d_val, (void *)r->d_cf, (void *)r->d_out,
-                    (void *)r->d_sign, (void *)r->d_flags, (void *)r->d_gtab})
+                    (void *)r->d_sign, (void *)r->d_flags, (void *)r->d_gtab, (void *)r->d_redo})
         c->dfree(p);
     if (r->gexec) cudaGraphExecDestroy(r->gexec);
     delete r;
@@ -952,6 +955,7 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
     int Kmax = 1, Pmax = 1, Lmax = 1;
     HostList red, interp, crt;
     std::map<int, HostList> evb;
+    std::map<int, HostList> evr;                    // register form, by N
     std::map<int, std::vector<int32_t>> pgroups;   // pairs by point count
     std::vector<int32_t> mapped;                    // pairs with their own Garner table
     int kmapped = 0;
@@ -988,7 +992,9 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
         Lmax = std::max(Lmax, p.L);
         red.add(q, p.S);
         int key = ((std::max(p.m, p.n) + 1) + 3) / 4 * 4;
-        evb[key].add(q, p.sym ? (int64_t)k * p.tiles * 32 : (int64_t)k * p.Pe);
+        const int rN = p.sym && c->reg_on ? reg_shape(p.m, p.n) : 0;
+        if (rN) evr[rN].add(q, (int64_t)k * p.tiles * 32);
+        else evb[key].add(q, p.sym ? (int64_t)k * p.tiles * 32 : (int64_t)k * p.Pe);
         // the contraction serves pairs whose points are exactly 0..P-1 and whose
         // primes are the table prefix
         if (p.pmap_off < 0 && p.Pe == p.P) pgroups[2 * p.P + p.sym].push_back(q);
@@ -1040,6 +1046,17 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
         put_list(blk, kv.second, a, b2);
         o_ev.push_back({a, b2});
     }
+    std::vector<std::pair<size_t, size_t>> o_evr;
+    int64_t redo_entries = 0;
+    for (auto &kv : evr) {
+        size_t a, b2;
+        put_list(blk, kv.second, a, b2);
+        o_evr.push_back({a, b2});
+        redo_entries += kv.second.total / 32;
+    }
+    // redo area: one counter per register bucket (16-byte aligned), then the lists
+    const size_t redo_head = (evr.size() * 8 + 15) / 16 * 16;
+    const size_t redo_bytes = evr.empty() ? 0 : redo_head + (size_t)redo_entries * 8;
     size_t o_gemm = (blk.size() + 7) / 8 * 8;
     blk.resize(o_gemm + gemm_pairs.size() * 4 + 4);
     if (!gemm_pairs.empty()) std::memcpy(blk.data() + o_gemm, gemm_pairs.data(), gemm_pairs.size() * 4);
@@ -1077,6 +1094,7 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
         ensure_buf(c, (void **)&r->d_cf, &r->cf_cap, cf_w * 4) ||
         ensure_buf(c, (void **)&r->d_flags, &r->flags_cap, flag_b) ||
         ensure_buf(c, (void **)&r->d_gtab, &r->gtab_cap, gtab_w * 4) ||
+        ensure_buf(c, (void **)&r->d_redo, &r->redo_cap, redo_bytes) ||
         ensure_buf(c, (void **)&r->d_out, &r->out_cap, out_w * 4) ||
         ensure_buf(c, (void **)&r->d_sign, &r->sign_cap, sign_b))
         return c->fail(GBR_ENOMEM, "device budget too small for this batch");
@@ -1135,6 +1153,33 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
         c->autotune_record("evalres", key, best_block);
         return cudaSuccess;
     };
+    auto evalres_reg_bucket = [&](int N, const WorkList &w, unsigned long long *cnt, int64_t *list,
+                                  cudaStream_t q, bool capturing) -> cudaError_t {
+        const int key = 1000 + N;
+        auto it = c->tuned_evalres.find(key);
+        if (it != c->tuned_evalres.end()) return launch_evalres_reg(L, w, N, it->second, cnt, list, q);
+        if (capturing) return launch_evalres_reg(L, w, N, 128, cnt, list, q);
+        float best = 1e30f;
+        int best_block = 128;
+        for (int cand : {64, 128, 256}) {
+            // each trial starts from an empty redo list
+            cudaError_t x = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), q);
+            if (x == cudaSuccess) x = cudaEventRecord(c->ev[6], q);
+            if (x == cudaSuccess) x = launch_evalres_reg(L, w, N, cand, cnt, list, q);
+            if (x == cudaSuccess) x = cudaEventRecord(c->ev[7], q);
+            if (x == cudaSuccess) x = cudaEventSynchronize(c->ev[7]);
+            if (x != cudaSuccess) return x;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, c->ev[6], c->ev[7]);
+            if (ms < best) {
+                best = ms;
+                best_block = cand;
+            }
+        }
+        c->tuned_evalres[key] = best_block;
+        c->autotune_record("evalres", key, best_block);
+        return cudaSuccess;
+    };
     // ---- the device stages; replayed from a captured CUDA graph when the plan repeats
     int64_t kernels = 1;
     auto record = [&](int idx, bool capturing, cudaStream_t q) {
@@ -1162,6 +1207,19 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
             kernels++;
             ++bi;
         }
+        if (x == cudaSuccess && !evr.empty()) x = cudaMemsetAsync(r->d_redo, 0, redo_head, q);
+        size_t ri = 0;
+        int64_t roff = 0;
+        for (auto &kv : evr) {
+            if (x != cudaSuccess) break;
+            unsigned long long *cnt = (unsigned long long *)(r->d_redo + 8 * ri);
+            int64_t *list = (int64_t *)(r->d_redo + redo_head) + roff;
+            x = evalres_reg_bucket(kv.first, mk(o_evr[ri].first, o_evr[ri].second, kv.second), cnt, list, q,
+                                   capturing);
+            kernels += 2;
+            roff += kv.second.total / 32;
+            ++ri;
+        }
         record(3, capturing, q);
         if (x == cudaSuccess && interp.total > 0) {
             x = launch_interp(L, mk(o_int_p, o_int_s, interp), Pmax, q);
@@ -1184,6 +1242,7 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
         std::vector<uintptr_t> key = {(uintptr_t)r->d_planblk, (uintptr_t)r->d_res, (uintptr_t)r->d_val,
                                       (uintptr_t)r->d_cf,      (uintptr_t)r->d_out, (uintptr_t)r->d_sign,
                                       (uintptr_t)r->d_deg,     (uintptr_t)r->d_flags, (uintptr_t)r->d_gtab,
+                                      (uintptr_t)r->d_redo,
                                       (uintptr_t)c->d_garner,  (uintptr_t)c->d_invk, (uintptr_t)c->d_err,
                                       (uintptr_t)c->d_mods,    (uintptr_t)c->stats_on};
         for (const Gemm &gm : gemms) key.push_back((uintptr_t)gm.vinv);
@@ -1233,12 +1292,17 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
     }
     if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "stage launch", e);
     int32_t herr[4] = {0, 0, 0, 0};
+    std::vector<unsigned long long> hredo(evr.size());
     e = cudaMemcpyAsync(herr, c->d_err, 16, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && !evr.empty())
+        e = cudaMemcpyAsync(hredo.data(), r->d_redo, 8 * evr.size(), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "resultant stages", e);
     if (herr[0]) return c->fail(GBR_EDEVICE, "device-side consistency check failed");
     st.dropped_points = (int64_t)((uint64_t)(uint32_t)herr[2] | ((uint64_t)(uint32_t)herr[3] << 32));
     st.dropped_primes = dropped_primes;
+    st.redo_warps = 0;
+    for (unsigned long long v : hredo) st.redo_warps += (int64_t)v;
     r->out_words = out_w;
     r->sign_bytes = sign_b;
     r->ran = true;

@@ -62,7 +62,7 @@ struct gbr_ctx {
     void *h_pin[4] = {nullptr, nullptr, nullptr, nullptr};
     size_t h_pin_cap[4] = {0, 0, 0, 0};
     cudaEvent_t ev[8] = {};
-    int drop_unlucky = 0, stats_on = 0, graph_on = 1, extra_primes = 0, gemm_on = 1;
+    int drop_unlucky = 0, stats_on = 0, graph_on = 1, extra_primes = 0, gemm_on = 1, reg_on = 1;
     gbr_stats stats{};
     std::map<uint64_t, cudaGraphExec_t> graphs;
     struct Vinv {
@@ -110,6 +110,8 @@ struct gbr_resident {
     size_t flags_cap = 0;
     uint32_t *d_gtab = nullptr;
     size_t gtab_cap = 0;
+    char *d_redo = nullptr;   // register-form redo counters and warp lists
+    size_t redo_cap = 0;
     int64_t out_words = 0, sign_bytes = 0;
     bool ran = false;
     bool oneshot = false;               // created by a one-shot call: never captured

@@ -128,6 +128,89 @@ GBR_HD uint32_t res_formal(uint32_t *A, int da, uint32_t *B, int db, int BS, con
     return neg ? mp_neg(r, M.p) : r;
 }
 
+// Register form of res_formal for the shapes (N, N), (N, N-1) and (N-1, N) when
+// the remainder sequence is normal at this point (every remainder has degree
+// one less than its divisor) -- the generic case.  F[k], G[k] hold the
+// coefficients of y^k.  Degrees are compile-time constants in every round, so
+// the polynomials stay in registers.  Returns with ok = false when a leading
+// coefficient vanishes at the point or the sequence is not normal (the caller
+// then solves the subproblem with res_formal); a remainder that vanishes
+// identically proves a common factor of positive degree and gives 0.
+//   (N-1, N): res_{N-1,N}(F,G) = res_{N,N-1}(G,F), since (N-1) N is even.
+//   (N, N):   with alpha = lc A, zeta = lc B and B' = alpha B - zeta A,
+//             res_{N,N}(A,B) = alpha^(1-N) res_{N,N-1}(A,B') (the remainder
+//             identity applied to res(B, A), whose sign cancels the swap's).
+//   Normal rounds are the fused three-product rounds of res_formal with the
+//   same telescoped divisor D = Q_0 Q_1 ... (Q_t = Z_0 ... Z_t, Z = zeta^2).
+template <int N>
+GBR_HD void chain_round(uint32_t (&U)[N + 1], const uint32_t (&V)[N + 1], const int d, const bool first,
+                        uint32_t &Dq, uint32_t &Q, bool &done, bool &ok, const ModP &M) {
+    // U has degree d + 1, V degree d; U <- zeta^2 U - (zeta alpha y + q0) V
+    if (done) return;
+    const uint32_t zeta = V[d], alpha = U[d + 1];
+    if (!first) Dq = mp_mul(Dq, Q, M);
+    const uint32_t z2 = mp_mul(zeta, zeta, M);
+    const uint32_t nza = M.p - mp_mul(zeta, alpha, M);
+    const uint32_t nq0 = M.p - mp_mulsub(zeta, U[d], alpha, V[d - 1], M);
+    U[0] = mp_fma2(z2, U[0], nq0, V[0], M);
+#pragma unroll
+    for (int k = 1; k < d; ++k) U[k] = mp_fma3(z2, U[k], nza, V[k - 1], nq0, V[k], M);
+    Q = mp_mul(Q, z2, M);
+    if (U[d - 1] == 0u) {
+        uint32_t any = 0u;
+#pragma unroll
+        for (int k = 0; k < d - 1; ++k) any |= U[k];
+        done = true;
+        ok = any == 0u;   // identically zero: the resultant is 0 (Dq is then ignored)
+        Dq = 0u;
+    }
+}
+
+template <int N>
+GBR_HD uint32_t res_chain(const uint32_t (&F)[N + 1], const uint32_t (&G)[N + 1], int m, int n, const ModP &M,
+                          bool &ok) {
+    static_assert(N >= 2, "the register form starts at degree 2");
+    const bool sw = m != N;   // (N-1, N): solve res(G, F)
+    const int nb = sw ? m : n;
+    uint32_t A[N + 1], B[N + 1];
+#pragma unroll
+    for (int k = 0; k <= N; ++k) {
+        A[k] = sw ? G[k] : F[k];
+        B[k] = sw ? F[k] : G[k];
+    }
+    ok = false;
+    // (a constant index keeps B in registers)
+    if (A[N] == 0u || (nb == N ? B[N] : B[N - 1]) == 0u) return 0u;   // a leading coefficient vanishes here
+    uint32_t acc = M.r1, den = M.r1, Dq = M.r1, Q = M.r1;
+    if (nb == N) {
+        const uint32_t alpha = A[N], zeta = B[N];
+        uint32_t any = 0u;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            B[k] = mp_mulsub(alpha, B[k], zeta, A[k], M);
+            any |= B[k];
+        }
+        if (B[N - 1] == 0u) {
+            ok = any == 0u;
+            return 0u;
+        }
+        acc = alpha;
+        den = mp_pow(alpha, (uint32_t)N, M);
+    }
+    bool done = false;
+    ok = true;
+#pragma unroll
+    for (int t = 0; t < N - 1; t += 2) {
+        chain_round<N>(A, B, N - 1 - t, t == 0, Dq, Q, done, ok, M);
+        if (t + 1 < N - 1) chain_round<N>(B, A, N - 2 - t, false, Dq, Q, done, ok, M);
+    }
+    if (done) return 0u;   // ok tells a zero resultant from a sequence that is not normal
+    const uint32_t c = ((N - 2) % 2 == 0) ? A[0] : B[0];   // the last remainder, a constant
+    acc = mp_mul(acc, c, M);
+    den = mp_mul(den, Dq, M);
+    return mp_mul(acc, mp_inv(den, M), M);
+}
+
 // One Horner step acc <- acc a + c on Montgomery residues with c stored as
 // c R^2: acc~ a~ + c R^2 = (acc a + c) R^2 < p^2 + p, and one reduction leaves
 // (acc a + c) R.
@@ -217,67 +300,176 @@ __device__ __forceinline__ void eval4_sym(const uint32_t *rc, int rows4n, const 
 
 // ------------------------------------------------------------------ A2 + A3: evaluate and solve
 
+// One (pair, prime, point) item of a work list on shared-memory columns Fs, Gs
+// (stride BS).  Symmetric pairs need the whole warp: lane l and lane l ^ 16
+// hand each other values.
+__device__ __forceinline__ void evalres_item(const ResLaunch &L, const WorkList &w, int64_t item, uint32_t *Fs,
+                                             uint32_t *Gs, int BS) {
+    int bi = wl_find(w.start, w.n, item);
+    int q = w.pairs[bi];
+    int64_t local = item - w.start[bi];
+    const PairPlan &P = L.plan[q];
+    const int rf4 = rows4(P.m), rg4 = rows4(P.n);
+    const int32_t *dgf = L.rowdeg + P.rowdeg_f;
+    const int32_t *dgg = L.rowdeg + P.rowdeg_g;
+    if (P.sym) {
+        // lanes 0-15 take points +ii, lanes 16-31 take -ii (same ii); a lane
+        // evaluates even and odd parts of one polynomial at ii^2 and hands the
+        // partner its value: f-lanes do f, g-lanes do g
+        const int per = P.tiles * 32;
+        const int i = (int)(local / per);
+        const int r = (int)(local % per);
+        const int lane = r & 31;
+        const int ii = (r >> 5) * 16 + (lane & 15);
+        const bool glane = lane >= 16;
+        const int j = ii == 0 ? (glane ? -1 : 0) : (glane ? 2 * ii : 2 * ii - 1);
+        const ModP M = L.mods[prime_of(P, L.pmap, i)];
+        const uint32_t a = mp_to((uint32_t)ii, M);
+        const uint32_t b = mp_mul(a, a, M);
+        const uint32_t *rbase = L.res + P.res_off + (int64_t)i * P.S;
+        const uint32_t *rc = glane ? rbase + (int64_t)(P.dxf + 1) * rf4 : rbase;
+        const int32_t *dg = glane ? dgg : dgf;
+        const int nrows = (glane ? P.n : P.m) + 1;
+        const int r4 = glane ? rg4 : rf4;
+        uint32_t *own = (glane ? Gs : Fs);
+        uint32_t *other = own + (glane ? -16 : 16);
+        for (int r0 = 0; r0 < nrows; r0 += 4) eval4_sym(rc, r4, dg, nrows, r0, a, b, glane, M, own, other, BS);
+        __syncwarp();
+        if (j >= 0 && j < P.P) L.val[P.val_off + (int64_t)i * P.Pe + j] = res_formal(Fs, P.m, Gs, P.n, BS, M);
+        __syncwarp();
+        return;
+    }
+    int i = (int)(local / P.Pe);
+    int j = (int)(local % P.Pe);
+    const ModP M = L.mods[prime_of(P, L.pmap, i)];
+    const uint32_t a = mp_to((uint32_t)j, M);
+    const uint32_t *rf = L.res + P.res_off + (int64_t)i * P.S;
+    const uint32_t *rg = rf + (int64_t)(P.dxf + 1) * rf4;
+    for (int r0 = 0; r0 <= P.m; r0 += 4) eval4(rf, rf4, dgf, P.m + 1, r0, a, M, Fs, BS);
+    for (int r0 = 0; r0 <= P.n; r0 += 4) eval4(rg, rg4, dgg, P.n + 1, r0, a, M, Gs, BS);
+    if (P.flag_off >= 0) {
+        // a point where a leading coefficient vanishes is unlucky: flag it, so
+        // interpolation takes the spare points instead (its formal-degree value
+        // below is still exact)
+        const uint8_t unlucky = Fs[0] == 0u || Gs[0] == 0u;
+        L.pflags[P.flag_off + (int64_t)i * P.Pe + j] = unlucky;
+        if (unlucky) atomicAdd(L.dropped, 1ull);
+    }
+    L.val[P.val_off + (int64_t)i * P.Pe + j] = res_formal(Fs, P.m, Gs, P.n, BS, M);
+}
+
 __global__ void k_evalres(ResLaunch L, WorkList w, int SF, int SG) {
     extern __shared__ uint32_t smem[];
     const int BS = blockDim.x;
     uint32_t *Fs = smem + threadIdx.x;
     uint32_t *Gs = smem + SF * BS + threadIdx.x;
-    for (int64_t item = blockIdx.x * (int64_t)BS + threadIdx.x; item < w.total; item += (int64_t)gridDim.x * BS) {
-        int bi = wl_find(w.start, w.n, item);
-        int q = w.pairs[bi];
-        int64_t local = item - w.start[bi];
+    for (int64_t item = blockIdx.x * (int64_t)BS + threadIdx.x; item < w.total; item += (int64_t)gridDim.x * BS)
+        evalres_item(L, w, item, Fs, Gs, BS);
+}
+
+// Symmetric pairs of shape (N, N), (N, N-1) or (N-1, N): the same lane pairs
+// as k_evalres, but the evaluated columns stay in registers (handed across by
+// shuffles) and res_chain solves in registers.  A warp with a lane whose
+// subproblem needs the general solver is appended to `redo` and written by
+// k_evalres_redo instead (whole warps, since lane pairs share evaluations).
+template <int N>
+__global__ void __launch_bounds__(256) k_evalres_reg(ResLaunch L, WorkList w, unsigned long long *redo_n,
+                                                     int64_t *redo) {
+    for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < w.total;
+         item += (int64_t)gridDim.x * blockDim.x) {
+        const int bi = wl_find(w.start, w.n, item);
+        const int q = w.pairs[bi];
+        const int64_t local = item - w.start[bi];
         const PairPlan &P = L.plan[q];
-        const int rf4 = rows4(P.m), rg4 = rows4(P.n);
-        const int32_t *dgf = L.rowdeg + P.rowdeg_f;
-        const int32_t *dgg = L.rowdeg + P.rowdeg_g;
-        if (P.sym) {
-            // lanes 0-15 take points +ii, lanes 16-31 take -ii (same ii); a lane
-            // evaluates even and odd parts of one polynomial at ii^2 and hands the
-            // partner its value: f-lanes do f, g-lanes do g
-            const int per = P.tiles * 32;
-            const int i = (int)(local / per);
-            const int r = (int)(local % per);
-            const int lane = r & 31;
-            const int ii = (r >> 5) * 16 + (lane & 15);
-            const bool glane = lane >= 16;
-            const int j = ii == 0 ? (glane ? -1 : 0) : (glane ? 2 * ii : 2 * ii - 1);
-            const ModP M = L.mods[prime_of(P, L.pmap, i)];
-            const uint32_t a = mp_to((uint32_t)ii, M);
-            const uint32_t b = mp_mul(a, a, M);
-            const uint32_t *rbase = L.res + P.res_off + (int64_t)i * P.S;
-            const uint32_t *rc = glane ? rbase + (int64_t)(P.dxf + 1) * rf4 : rbase;
-            const int32_t *dg = glane ? dgg : dgf;
-            const int nrows = (glane ? P.n : P.m) + 1;
-            const int r4 = glane ? rg4 : rf4;
-            uint32_t *own = (glane ? Gs : Fs);
-            uint32_t *other = own + (glane ? -16 : 16);
-            for (int r0 = 0; r0 < nrows; r0 += 4) eval4_sym(rc, r4, dg, nrows, r0, a, b, glane, M, own, other, BS);
-            __syncwarp();
-            if (j >= 0 && j < P.P)
-                L.val[P.val_off + (int64_t)i * P.Pe + j] = res_formal(Fs, P.m, Gs, P.n, BS, M);
-            __syncwarp();
-            continue;
-        }
-        int i = (int)(local / P.Pe);
-        int j = (int)(local % P.Pe);
+        const int per = P.tiles * 32;
+        const int i = (int)(local / per);
+        const int r = (int)(local % per);
+        const int lane = r & 31;
+        const int ii = (r >> 5) * 16 + (lane & 15);
+        const bool glane = lane >= 16;
+        const int j = ii == 0 ? (glane ? -1 : 0) : (glane ? 2 * ii : 2 * ii - 1);
         const ModP M = L.mods[prime_of(P, L.pmap, i)];
-        const uint32_t a = mp_to((uint32_t)j, M);
-        const uint32_t *rf = L.res + P.res_off + (int64_t)i * P.S;
-        const uint32_t *rg = rf + (int64_t)(P.dxf + 1) * rf4;
-        for (int r0 = 0; r0 <= P.m; r0 += 4) eval4(rf, rf4, dgf, P.m + 1, r0, a, M, Fs, BS);
-        for (int r0 = 0; r0 <= P.n; r0 += 4) eval4(rg, rg4, dgg, P.n + 1, r0, a, M, Gs, BS);
-        if (P.flag_off >= 0) {
-            // a point where a leading coefficient vanishes is unlucky: flag it, so
-            // interpolation takes the spare points instead (its formal-degree value
-            // below is still exact)
-            const uint8_t unlucky = Fs[0] == 0u || Gs[0] == 0u;
-            L.pflags[P.flag_off + (int64_t)i * P.Pe + j] = unlucky;
-            if (unlucky) atomicAdd(L.dropped, 1ull);
+        const uint32_t a = mp_to((uint32_t)ii, M);
+        const uint32_t b = mp_mul(a, a, M);
+        const int rf4 = rows4(P.m);
+        const uint32_t *rbase = L.res + P.res_off + (int64_t)i * P.S;
+        const uint32_t *rc = glane ? rbase + (int64_t)(P.dxf + 1) * rf4 : rbase;
+        const int32_t *dg = L.rowdeg + (glane ? P.rowdeg_g : P.rowdeg_f);
+        const int nrows = (glane ? P.n : P.m) + 1;
+        const int step = (glane ? rows4(P.n) : rf4) >> 2;
+        // own[k]: this lane's polynomial at its own point; oth[k]: at the partner's
+        uint32_t own[N + 1], oth[N + 1];
+#pragma unroll
+        for (int r0 = 0; r0 <= N; r0 += 4) {
+            uint32_t e[4] = {0u, 0u, 0u, 0u}, o[4] = {0u, 0u, 0u, 0u};
+            if (r0 < nrows) {
+                int dmax = -1;
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (r0 + t < nrows) dmax = max(dmax, dg[r0 + t]);
+                const uint4 *c = reinterpret_cast<const uint4 *>(rc + r0);
+                int x = dmax;
+                if (x >= 0 && (x & 1) == 0) {
+                    const uint4 v = c[(int64_t)x * step];
+                    e[0] = horner_step(0u, b, v.x, M);
+                    e[1] = horner_step(0u, b, v.y, M);
+                    e[2] = horner_step(0u, b, v.z, M);
+                    e[3] = horner_step(0u, b, v.w, M);
+                    --x;
+                }
+                for (; x >= 1; x -= 2) {
+                    const uint4 vo = c[(int64_t)x * step];
+                    const uint4 ve = c[(int64_t)(x - 1) * step];
+                    o[0] = horner_step(o[0], b, vo.x, M);
+                    o[1] = horner_step(o[1], b, vo.y, M);
+                    o[2] = horner_step(o[2], b, vo.z, M);
+                    o[3] = horner_step(o[3], b, vo.w, M);
+                    e[0] = horner_step(e[0], b, ve.x, M);
+                    e[1] = horner_step(e[1], b, ve.y, M);
+                    e[2] = horner_step(e[2], b, ve.z, M);
+                    e[3] = horner_step(e[3], b, ve.w, M);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (r0 + t <= N) {
+                    const uint32_t io = mp_mul(a, o[t], M);
+                    const uint32_t plus = mp_add(e[t], io, M.p), minus = mp_sub(e[t], io, M.p);
+                    own[r0 + t] = glane ? minus : plus;
+                    oth[r0 + t] = glane ? plus : minus;
+                }
+            }
         }
-        L.val[P.val_off + (int64_t)i * P.Pe + j] = res_formal(Fs, P.m, Gs, P.n, BS, M);
+        uint32_t F[N + 1], G[N + 1];
+#pragma unroll
+        for (int k = 0; k <= N; ++k) {
+            const uint32_t got = __shfl_xor_sync(0xffffffffu, oth[k], 16);
+            F[k] = glane ? got : own[k];
+            G[k] = glane ? own[k] : got;
+        }
+        bool ok;
+        const uint32_t v = res_chain<N>(F, G, P.m, P.n, M, ok);
+        const bool valid = j >= 0 && j < P.P;
+        if (__ballot_sync(0xffffffffu, valid && !ok)) {
+            if (lane == 0) redo[atomicAdd(redo_n, 1ull)] = item;
+        } else if (valid) {
+            L.val[P.val_off + (int64_t)i * P.Pe + j] = v;
+        }
     }
 }
 
+// The warps listed by k_evalres_reg, solved on shared-memory columns.
+__global__ void k_evalres_redo(ResLaunch L, WorkList w, int SF, const unsigned long long *redo_n,
+                               const int64_t *redo) {
+    extern __shared__ uint32_t smem[];
+    const int BS = blockDim.x;
+    uint32_t *Fs = smem + threadIdx.x;
+    uint32_t *Gs = smem + SF * BS + threadIdx.x;
+    const int64_t nw = (int64_t)*redo_n;
+    const int lane = threadIdx.x & 31;
+    for (int64_t e = (blockIdx.x * (int64_t)BS + threadIdx.x) >> 5; e < nw; e += ((int64_t)gridDim.x * BS) >> 5)
+        evalres_item(L, w, redo[e] + lane, Fs, Gs, BS);
+}
 
 cudaError_t launch_evalres(const ResLaunch &L, const WorkList &w, int SF, int SG, int block, cudaStream_t s) {
     if (w.total <= 0) return cudaSuccess;
@@ -289,7 +481,46 @@ cudaError_t launch_evalres(const ResLaunch &L, const WorkList &w, int SF, int SG
 }
 
 
+using RegKernel = void (*)(ResLaunch, WorkList, unsigned long long *, int64_t *);
+
+static RegKernel reg_kernel(int N) {
+    switch (N) {
+#define GBR_REG_CASE(n) \
+    case n:             \
+        return k_evalres_reg<n>;
+        GBR_REG_CASE(2) GBR_REG_CASE(3) GBR_REG_CASE(4) GBR_REG_CASE(5) GBR_REG_CASE(6) GBR_REG_CASE(7)
+        GBR_REG_CASE(8) GBR_REG_CASE(9) GBR_REG_CASE(10) GBR_REG_CASE(11) GBR_REG_CASE(12) GBR_REG_CASE(13)
+        GBR_REG_CASE(14) GBR_REG_CASE(15) GBR_REG_CASE(16) GBR_REG_CASE(17) GBR_REG_CASE(18) GBR_REG_CASE(19)
+        GBR_REG_CASE(20) GBR_REG_CASE(21) GBR_REG_CASE(22) GBR_REG_CASE(23) GBR_REG_CASE(24) GBR_REG_CASE(25)
+        GBR_REG_CASE(26) GBR_REG_CASE(27) GBR_REG_CASE(28) GBR_REG_CASE(29) GBR_REG_CASE(30) GBR_REG_CASE(31)
+        GBR_REG_CASE(32)
+#undef GBR_REG_CASE
+    }
+    return nullptr;
+}
+static_assert(kRegMinN == 2 && kRegMaxN == 32, "reg_kernel covers kRegMinN..kRegMaxN");
+
+cudaError_t launch_evalres_reg(const ResLaunch &L, const WorkList &w, int N, int block, unsigned long long *redo_n,
+                               int64_t *redo, cudaStream_t s) {
+    if (w.total <= 0) return cudaSuccess;
+    RegKernel k = reg_kernel(N);
+    if (!k || w.total % 32 != 0 || block % 32 != 0) return cudaErrorInvalidValue;
+    int grid = persistent_grid(k, block, 0, (w.total + block - 1) / block);
+    k<<<grid, block, 0, s>>>(L, w, redo_n, redo);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the redo pass reads its count on the device; with nothing listed its
+    // blocks return at once
+    const int rb = 128, SF = (N + 1 + 3) / 4 * 4;
+    const size_t smem = (size_t)2 * SF * rb * sizeof(uint32_t);
+    grid = persistent_grid(k_evalres_redo, rb, smem, (w.total / 32 + rb / 32 - 1) / (rb / 32));
+    k_evalres_redo<<<grid, rb, smem, s>>>(L, w, SF, redo_n, redo);
+    return cudaGetLastError();
+}
+
 cudaError_t configure_evalres_kernel() {
+    cudaError_t e = cudaFuncSetAttribute(k_evalres_redo, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_evalres, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
 }
 

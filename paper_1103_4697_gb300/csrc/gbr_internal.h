@@ -222,6 +222,18 @@ cudaError_t launch_bounds(const ResLaunch &L, cudaStream_t s);
 cudaError_t launch_reduce(const ResLaunch &L, const WorkList &w, cudaStream_t s);
 cudaError_t launch_evalres(const ResLaunch &L, const WorkList &w, int slots_f, int slots_g, int block,
                            cudaStream_t s);
+// register form for symmetric pairs of shape (N, N), (N, N-1), (N-1, N) with
+// kRegMinN <= N <= kRegMaxN; warps it cannot finish are listed in `redo`
+// (capacity total / 32, count in *redo_n, zeroed before) and solved by a
+// second launch on shared memory
+constexpr int kRegMinN = 2, kRegMaxN = 32;
+GBR_HD int reg_shape(int m, int n) {
+    const int N = m > n ? m : n;
+    if (N < kRegMinN || N > kRegMaxN || m < N - 1 || n < N - 1) return 0;
+    return N;
+}
+cudaError_t launch_evalres_reg(const ResLaunch &L, const WorkList &w, int N, int block, unsigned long long *redo_n,
+                               int64_t *redo, cudaStream_t s);
 cudaError_t launch_interp(const ResLaunch &L, const WorkList &w, int maxP, cudaStream_t s);
 cudaError_t launch_crt(const ResLaunch &L, const WorkList &w, int maxL, cudaStream_t s);
 cudaError_t launch_vinv(const ModP *mods, int P, int K, int sym, uint32_t *out, cudaStream_t s);

@@ -68,6 +68,21 @@ GBR_HD uint32_t mp_mulsub(uint32_t a, uint32_t x, uint32_t b, uint32_t y, const 
 #endif
 }
 
+// (a*x + b*y) * 2^-32 mod p for residues in [0, p].
+GBR_HD uint32_t mp_fma2(uint32_t a, uint32_t x, uint32_t b, uint32_t y, const ModP &M) {
+#if defined(__CUDA_ARCH__)
+    uint32_t lo = a * x, hi = __umulhi(a, x);
+    asm("mad.lo.cc.u32 %0, %2, %3, %0;\n\t"
+        "madc.hi.u32 %1, %2, %3, %1;"
+        : "+r"(lo), "+r"(hi)
+        : "r"(b), "r"(y));
+    return mp_redc(lo, hi, M.p, M.pinv);
+#else
+    uint64_t t = (uint64_t)a * x + (uint64_t)b * y;
+    return mp_redc((uint32_t)t, (uint32_t)(t >> 32), M.p, M.pinv);
+#endif
+}
+
 // (a*x + b*y + c*z) * 2^-32 mod p for residues in [0, p] (sum < 3 p^2 < p 2^32).
 GBR_HD uint32_t mp_fma3(uint32_t a, uint32_t x, uint32_t b, uint32_t y, uint32_t c, uint32_t z, const ModP &M) {
 #if defined(__CUDA_ARCH__)

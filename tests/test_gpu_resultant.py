@@ -218,6 +218,80 @@ def test_interpolation_contraction_matches_newton(ctx):
         assert r == list(O.res_bareiss(f, g))
 
 
+def _bimul(a, b):
+    """Product of two bivariate polynomials given as rows (row j = x-coefficients of y^j)."""
+    nx = len(a[0]) + len(b[0]) - 1
+    out = [[0] * nx for _ in range(len(a) + len(b) - 1)]
+    for i, ra in enumerate(a):
+        for j, rb in enumerate(b):
+            for u, ca in enumerate(ra):
+                for v, cb in enumerate(rb):
+                    out[i + j][u + v] += ca * cb
+    return out
+
+
+def test_register_form_matches_shared_memory_form(ctx):
+    """Pairs of shape (N, N), (N, N-1), (N-1, N) for every N of the register form
+    (2..32) are solved with the polynomials in registers; pairs even in y (the
+    remainder sequence is not normal at any point), pairs whose leading coefficient
+    vanishes at integer points, pairs with a planted common factor and a shape
+    outside the register form ride along.  With the register form off every
+    subproblem runs on shared memory: both must agree with each other and with the
+    oracle, and the register run must have sent warps to the shared-memory redo."""
+    from paper_1103_4697_gb300.native import OPT_REGISTER_FORM, OPT_STATS
+
+    rng = random.Random(23)
+
+    def rnd(ny, nx, even=False):
+        rows = [[rng.randint(-40, 40) for _ in range(nx + 1)] for _ in range(ny + 1)]
+        if even:
+            rows = [r if j % 2 == 0 else [0] * (nx + 1) for j, r in enumerate(rows)]
+        if not any(rows[-1]):
+            rows[-1][0] = 1
+        return rows
+
+    fs, gs = [], []
+    for N in range(2, 33):
+        for m, n in ((N, N), (N, N - 1), (N - 1, N)):
+            fs.append(rnd(m, 1))
+            gs.append(rnd(n, 1))
+    for N in (4, 6, 10, 20):
+        fs.append(rnd(N, 1, even=True))
+        gs.append(rnd(N, 1, even=True))
+    for N in (5, 12, 20):
+        h = rnd(2, 1)
+        fs.append(_bimul(h, rnd(N - 2, 1)))
+        gs.append(_bimul(h, rnd(N - 2, 1)))
+    for N in (3, 9, 16):
+        f, g = rnd(N, 1), rnd(N, 1)
+        f[-1] = [-3, 1]        # lc_y f = x - 3 vanishes at x = 3 for every prime
+        fs.append(f)
+        gs.append(g)
+    fs.append(rnd(7, 2))
+    gs.append(rnd(3, 2))
+    ctx.set_option(OPT_STATS, 1)
+    try:
+        got = ctx.resultant_batch(fs, gs)
+        st = ctx.stats()
+        ctx.set_option(OPT_REGISTER_FORM, 0)
+        shared = ctx.resultant_batch(fs, gs)
+        st0 = ctx.stats()
+    finally:
+        ctx.set_option(OPT_REGISTER_FORM, 1)
+        ctx.set_option(OPT_STATS, 0)
+    assert got == shared
+    assert st["redo_warps"] > 0 and st0["redo_warps"] == 0
+    prng = random.Random(5)
+    for f, g, r in zip(fs, gs, got):
+        if max(len(f), len(g)) <= 11:
+            assert r == _oracle(f, g)
+        else:
+            for a in (prng.randint(-10 ** 6, 10 ** 6), prng.randint(-10 ** 6, 10 ** 6)):
+                assert _poly_eval(r, a) == O.res_at_prs(f, g, a)
+    planted = got[3 * 31 + 4: 3 * 31 + 7]
+    assert all(r == [] or all(c == 0 for c in r) for r in planted)
+
+
 def test_drop_unlucky_matches_formal_degrees(ctx):
     """Dropping unlucky points (a leading coefficient vanishes there) for spare
     points, and unlucky primes (a leading coefficient vanishes identically) for the
