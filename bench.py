@@ -360,7 +360,7 @@ def run_ours(args) -> None:
                    "degree": DEG, "coef_bits": BITS, "inputs": "device-resident", "l2": "flushed between steps "
                    "(256 MiB write)", "parallelism": "replicas" if world > 1 else "single GPU"},
         "clocks": clk, "e2e": e2e, "gpu_launches": kernels,
-        "roofline": {"bound": "alu", "kernel": "k_evalres", "achieved": achieved / 1e12, "peak": peak / 1e12,
+        "roofline": {"bound": "alu", "kernel": "k_evalres_reg<20> (+ k_evalres_redo)", "achieved": achieved / 1e12, "peak": peak / 1e12,
                      "unit": "Tmodmul/s", "frac": achieved / peak, "traffic": traffic_for(kernel_src),
                      "peak_source": "measured on this GPU by gbr_calibrate: best of modmul, 2 x fused mulsub, "
                                     "3 x fused 3-product rate (modular products per second)",

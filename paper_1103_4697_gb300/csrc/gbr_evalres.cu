@@ -223,6 +223,15 @@ __device__ __forceinline__ uint32_t horner_step(uint32_t acc, uint32_t a, uint32
     return mp_redc(lo, hi, M.p, M.pinv);
 }
 
+// One Horner step with a fixed multiplier b < p in Shoup's form (bp = floor(b
+// 2^32 / p) precomputed): acc b - floor(acc bp / 2^32) p lies in [0, 2p) for any
+// 32-bit acc, so with c < p the new accumulator stays below 3p < 2^32 and needs
+// no correction inside the loop (three multiply-adds instead of five).  The
+// accumulator is congruent to acc b + c modulo p; it is not reduced.
+__device__ __forceinline__ uint32_t shoup_step(uint32_t acc, uint32_t b, uint32_t bp, uint32_t c, uint32_t np) {
+    return __umulhi(acc, bp) * np + (acc * b + c);
+}
+
 // Evaluates rows r0..r0+3 (r0 a multiple of 4) at x = a with four independent
 // Horner chains; the residues are laid out [x][row, padded to 4 rows] so the
 // four coefficients of one power of x come in one 16-byte load.  Entries past
@@ -389,8 +398,11 @@ __global__ void __launch_bounds__(256) k_evalres_reg(ResLaunch L, WorkList w, un
         const bool glane = lane >= 16;
         const int j = ii == 0 ? (glane ? -1 : 0) : (glane ? 2 * ii : 2 * ii - 1);
         const ModP M = L.mods[prime_of(P, L.pmap, i)];
-        const uint32_t a = mp_to((uint32_t)ii, M);
-        const uint32_t b = mp_mul(a, a, M);
+        // even and odd parts at b = ii^2 (an exact integer below p) by Shoup steps on
+        // the stored c R^2 residues, so the parts come out as R^2 E and R^2 O
+        const uint32_t b = (uint32_t)ii * (uint32_t)ii;
+        const uint32_t bp = (uint32_t)(((uint64_t)b << 32) / M.p);
+        const uint32_t np = 0u - M.p;
         const int rf4 = rows4(P.m);
         const uint32_t *rbase = L.res + P.res_off + (int64_t)i * P.S;
         const uint32_t *rc = glane ? rbase + (int64_t)(P.dxf + 1) * rf4 : rbase;
@@ -411,30 +423,33 @@ __global__ void __launch_bounds__(256) k_evalres_reg(ResLaunch L, WorkList w, un
                 int x = dmax;
                 if (x >= 0 && (x & 1) == 0) {
                     const uint4 v = c[(int64_t)x * step];
-                    e[0] = horner_step(0u, b, v.x, M);
-                    e[1] = horner_step(0u, b, v.y, M);
-                    e[2] = horner_step(0u, b, v.z, M);
-                    e[3] = horner_step(0u, b, v.w, M);
+                    e[0] = v.x;
+                    e[1] = v.y;
+                    e[2] = v.z;
+                    e[3] = v.w;
                     --x;
                 }
                 for (; x >= 1; x -= 2) {
                     const uint4 vo = c[(int64_t)x * step];
                     const uint4 ve = c[(int64_t)(x - 1) * step];
-                    o[0] = horner_step(o[0], b, vo.x, M);
-                    o[1] = horner_step(o[1], b, vo.y, M);
-                    o[2] = horner_step(o[2], b, vo.z, M);
-                    o[3] = horner_step(o[3], b, vo.w, M);
-                    e[0] = horner_step(e[0], b, ve.x, M);
-                    e[1] = horner_step(e[1], b, ve.y, M);
-                    e[2] = horner_step(e[2], b, ve.z, M);
-                    e[3] = horner_step(e[3], b, ve.w, M);
+                    o[0] = shoup_step(o[0], b, bp, vo.x, np);
+                    o[1] = shoup_step(o[1], b, bp, vo.y, np);
+                    o[2] = shoup_step(o[2], b, bp, vo.z, np);
+                    o[3] = shoup_step(o[3], b, bp, vo.w, np);
+                    e[0] = shoup_step(e[0], b, bp, ve.x, np);
+                    e[1] = shoup_step(e[1], b, bp, ve.y, np);
+                    e[2] = shoup_step(e[2], b, bp, ve.z, np);
+                    e[3] = shoup_step(e[3], b, bp, ve.w, np);
                 }
             }
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 if (r0 + t <= N) {
-                    const uint32_t io = mp_mul(a, o[t], M);
-                    const uint32_t plus = mp_add(e[t], io, M.p), minus = mp_sub(e[t], io, M.p);
+                    // R E = redc(R^2 E); R ii O = redc(R^2 O ii) (R^2 O < 3p, so
+                    // both inputs stay below p 2^32)
+                    const uint32_t ev = mp_redc(e[t], 0u, M.p, M.pinv);
+                    const uint32_t io = mp_mul(o[t], (uint32_t)ii, M);
+                    const uint32_t plus = mp_add(ev, io, M.p), minus = mp_sub(ev, io, M.p);
                     own[r0 + t] = glane ? minus : plus;
                     oth[r0 + t] = glane ? plus : minus;
                 }
