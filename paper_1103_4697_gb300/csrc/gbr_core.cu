@@ -273,22 +273,22 @@ int gbr_ctx::ensure_tables(int K, int T) {
     return GBR_OK;
 }
 
-// Inverse Vandermonde matrices are cached per point count P for the first K
-// primes; the cache is bounded by a quarter of the context's budget (at least
+// Inverse Vandermonde matrices are cached per (size n, point set) for the first
+// K primes; the cache is bounded by a quarter of the context's budget (at least
 // 256 MiB), least recently used entries are dropped.
-const uint32_t *gbr_ctx::get_vinv(int P, int K, int sym) {
+const uint32_t *gbr_ctx::get_vinv(int n, int K, int mode) {
     const size_t kVinvCacheBytes = std::max<size_t>((size_t)256 << 20, budget / 4);
-    const int key = 2 * P + (sym ? 1 : 0);
+    const int64_t key = 4 * (int64_t)n + mode;
     auto it = vinv.find(key);
     if (it != vinv.end() && it->second.K >= K) {
         it->second.last_use = ++vinv_clock;
         return it->second.d;
     }
-    size_t bytes = (size_t)P * P * K * 4;
+    size_t bytes = (size_t)n * n * K * 4;
     if (bytes > kVinvCacheBytes / 2) return nullptr;
     auto total = [&]() {
         size_t t = 0;
-        for (auto &kv : vinv) t += (size_t)(kv.first / 2) * (kv.first / 2) * kv.second.K * 4;
+        for (auto &kv : vinv) t += kv.second.bytes;
         return t;
     };
     if (it != vinv.end()) {
@@ -309,13 +309,14 @@ const uint32_t *gbr_ctx::get_vinv(int P, int K, int sym) {
     }
     uint32_t *d = (uint32_t *)dalloc(bytes);
     if (!d) return nullptr;
-    if (launch_vinv(d_mods, P, K, sym, d, stream) != cudaSuccess) {
+    if (launch_vinv(d_mods, n, K, mode, d, stream) != cudaSuccess) {
         dfree(d);
         return nullptr;
     }
     Vinv v;
     v.d = d;
     v.K = K;
+    v.bytes = bytes;
     v.last_use = ++vinv_clock;
     vinv[key] = v;
     return d;
@@ -915,6 +916,9 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
         // the drop mode keeps the unit grid so that spare points are 0..Pe-1
         p.sym = drop ? 0 : 1;
         p.tiles = (p.P / 2 + 1 + 15) / 16;
+        // a complete symmetric set 0, +-1, ..., +-h (h = P/2, one point more when P
+        // is even) lets interpolation split into even and odd parts
+        if (p.sym) p.Pe = 2 * (p.P / 2) + 1;
         if (p.Pe > GBR_MAX_POINTS + 2 * 4096) return c->fail(GBR_ELIMIT, "too many spare points");
         kc_max = std::max(kc_max, p.k + 32);
     }
@@ -997,7 +1001,7 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
         else evb[key].add(q, p.sym ? (int64_t)k * p.tiles * 32 : (int64_t)k * p.Pe);
         // the contraction serves pairs whose points are exactly 0..P-1 and whose
         // primes are the table prefix
-        if (p.pmap_off < 0 && p.Pe == p.P) pgroups[2 * p.P + p.sym].push_back(q);
+        if (p.pmap_off < 0 && (p.sym || p.Pe == p.P)) pgroups[2 * p.P + p.sym].push_back(q);
         else interp.add(q, k);
         crt.add(q, p.P);
         subproblems += (int64_t)k * p.Pe;
@@ -1011,10 +1015,10 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
     // contraction; the rest (and groups whose matrices do not fit the cache)
     // use Newton interpolation, one warp per (pair, prime)
     struct Gemm {
-        int P, K;
+        int n, rows, mode, K;
         const uint32_t *vinv;
         size_t off;
-        int n;
+        int npairs;
     };
     std::vector<Gemm> gemms;
     std::vector<int32_t> gemm_pairs;
@@ -1023,15 +1027,33 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
         const std::vector<int32_t> &qs = kv.second;
         int K = 0;
         for (int q : qs) K = std::max(K, plan[q].k);
-        const uint32_t *vi = nullptr;
         const int gP = kv.first / 2, gsym = kv.first & 1;
-        if ((int)qs.size() >= kGemmMinPairs && c->gemm_on) vi = c->get_vinv(gP, K, gsym);
-        if (vi) {
-            gemms.push_back({gP, K, vi, gemm_pairs.size(), (int)qs.size()});
-            gemm_pairs.insert(gemm_pairs.end(), qs.begin(), qs.end());
-        } else {
-            for (int q : qs) interp.add(q, plan[q].k);
+        const size_t off = gemm_pairs.size();
+        bool done = false;
+        if ((int)qs.size() >= kGemmMinPairs && c->gemm_on) {
+            if (gsym) {
+                // R(x) = E(x^2) + x O(x^2): E has D/2 + 1 coefficients from h + 1 sums,
+                // O has (D + 1)/2 from h differences (D = P - 1, h = P/2)
+                const int h = gP / 2, ne = (gP - 1) / 2 + 1, no = gP / 2;
+                const uint32_t *ve = c->get_vinv(h + 1, K, VINV_EVEN);
+                const uint32_t *vo = no > 0 && ve ? c->get_vinv(h, K, VINV_ODD) : nullptr;
+                if (ve && (no == 0 || vo)) {
+                    gemms.push_back({h + 1, ne, GEMM_EVEN, K, ve, off, (int)qs.size()});
+                    if (no > 0) gemms.push_back({h, no, GEMM_ODD, K, vo, off, (int)qs.size()});
+                    done = true;
+                }
+            }
+            if (!done) {
+                const uint32_t *vi = c->get_vinv(gP, K, gsym ? VINV_SYM : VINV_GRID);
+                if (vi) {
+                    gemms.push_back({gP, gP, GEMM_PLAIN, K, vi, off, (int)qs.size()});
+                    done = true;
+                }
+            }
         }
+        if (done) gemm_pairs.insert(gemm_pairs.end(), qs.begin(), qs.end());
+        else
+            for (int q : qs) interp.add(q, plan[q].k);
     }
     // ---- plan block: plans + work lists, one upload
     std::vector<char> blk(sizeof(PairPlan) * n);
@@ -1069,12 +1091,14 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
         GemmGroup gg;
         gg.vinv = gm.vinv;
         gg.pairs_off = (int64_t)(o_gemm + gm.off * sizeof(int32_t));   // the block is (re)allocated later
-        gg.P = gm.P;
-        gg.npairs = gm.n;
+        gg.n = gm.n;
+        gg.rows = gm.rows;
+        gg.npairs = gm.npairs;
+        gg.mode = gm.mode;
         ggroups.push_back(gg);
         for (int i = 0; i < gm.K; ++i)
-            for (int c0 = 0; c0 < gm.P; c0 += kGemmTileM)
-                for (int q0 = 0; q0 < gm.n; q0 += kGemmTileN) gtiles.push_back({(int32_t)gi, c0, q0, i});
+            for (int c0 = 0; c0 < gm.rows; c0 += kGemmTileM)
+                for (int q0 = 0; q0 < gm.npairs; q0 += kGemmTileN) gtiles.push_back({(int32_t)gi, c0, q0, i});
     }
     size_t o_ggroups = (blk.size() + 15) / 16 * 16;
     blk.resize(o_ggroups + ggroups.size() * sizeof(GemmGroup) + 16);

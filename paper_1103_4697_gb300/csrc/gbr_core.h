@@ -68,11 +68,12 @@ struct gbr_ctx {
     struct Vinv {
         uint32_t *d = nullptr;
         int K = 0;
+        size_t bytes = 0;
         uint64_t last_use = 0;
     };
-    std::map<int, Vinv> vinv;      // inverse Vandermonde matrices, key 2 P + sym
+    std::map<int64_t, Vinv> vinv;  // inverse Vandermonde matrices, key 4 n + point-set mode
     uint64_t vinv_clock = 0, vinv_run_mark = 0;
-    const uint32_t *get_vinv(int P, int K, int sym);   // nullptr if it cannot be built
+    const uint32_t *get_vinv(int n, int K, int mode);   // nullptr if it cannot be built
     gbr::ServeState *serve = nullptr;
     std::map<int, int> tuned_evalres;   // degree bucket -> block size chosen by the autotuner
     cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs

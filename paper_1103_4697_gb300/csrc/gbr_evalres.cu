@@ -344,7 +344,7 @@ __device__ __forceinline__ void evalres_item(const ResLaunch &L, const WorkList 
         uint32_t *other = own + (glane ? -16 : 16);
         for (int r0 = 0; r0 < nrows; r0 += 4) eval4_sym(rc, r4, dg, nrows, r0, a, b, glane, M, own, other, BS);
         __syncwarp();
-        if (j >= 0 && j < P.P) L.val[P.val_off + (int64_t)i * P.Pe + j] = res_formal(Fs, P.m, Gs, P.n, BS, M);
+        if (j >= 0 && j < P.Pe) L.val[P.val_off + (int64_t)i * P.Pe + j] = res_formal(Fs, P.m, Gs, P.n, BS, M);
         __syncwarp();
         return;
     }
@@ -381,8 +381,14 @@ __global__ void k_evalres(ResLaunch L, WorkList w, int SF, int SG) {
 // shuffles) and res_chain solves in registers.  A warp with a lane whose
 // subproblem needs the general solver is appended to `redo` and written by
 // k_evalres_redo instead (whole warps, since lane pairs share evaluations).
+// blocks of 256 per SM the register allocation must allow: three (80 registers,
+// a few spills to L1)
+// measured fastest at N = 20 (12.0 against 12.5 ms with 128 registers on the
+// 4096-pair degree-20 batch); larger N need more registers than that
+constexpr int reg_min_blocks(int N) { return N <= 20 ? 3 : N <= 27 ? 2 : 1; }
+
 template <int N>
-__global__ void __launch_bounds__(256) k_evalres_reg(ResLaunch L, WorkList w, unsigned long long *redo_n,
+__global__ void __launch_bounds__(256, reg_min_blocks(N)) k_evalres_reg(ResLaunch L, WorkList w, unsigned long long *redo_n,
                                                      int64_t *redo) {
     for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < w.total;
          item += (int64_t)gridDim.x * blockDim.x) {
@@ -464,7 +470,7 @@ __global__ void __launch_bounds__(256) k_evalres_reg(ResLaunch L, WorkList w, un
         }
         bool ok;
         const uint32_t v = res_chain<N>(F, G, P.m, P.n, M, ok);
-        const bool valid = j >= 0 && j < P.P;
+        const bool valid = j >= 0 && j < P.Pe;
         if (__ballot_sync(0xffffffffu, valid && !ok)) {
             if (lane == 0) redo[atomicAdd(redo_n, 1ull)] = item;
         } else if (valid) {

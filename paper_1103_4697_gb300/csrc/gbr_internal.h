@@ -236,16 +236,34 @@ cudaError_t launch_evalres_reg(const ResLaunch &L, const WorkList &w, int N, int
                                int64_t *redo, cudaStream_t s);
 cudaError_t launch_interp(const ResLaunch &L, const WorkList &w, int maxP, cudaStream_t s);
 cudaError_t launch_crt(const ResLaunch &L, const WorkList &w, int maxL, cudaStream_t s);
-cudaError_t launch_vinv(const ModP *mods, int P, int K, int sym, uint32_t *out, cudaStream_t s);
+cudaError_t launch_vinv(const ModP *mods, int n, int K, int mode, uint32_t *out, cudaStream_t s);
 cudaError_t launch_unlucky_primes(const ResLaunch &L, int kc, uint8_t *out, cudaStream_t s);
 cudaError_t launch_pair_garner(const ResLaunch &L, const int32_t *pairs, int n, int kmax, uint32_t *gtab,
                                cudaStream_t s);
 // Interpolation as a contraction: pairs sharing a point count form a group;
 // the launch covers tiles of 64 coefficients x 64 pairs x one prime.
+// Point sets of the inverse Vandermonde matrices (k_vinv):
+//   VINV_GRID  x_j = j                       (values at the unit grid)
+//   VINV_SYM   x_j = point_of(1, j)          (values at 0, +-1, +-2, ...)
+//   VINV_EVEN  x_j = j^2, columns j >= 1 scaled by 1/2
+//   VINV_ODD   x_j = (j+1)^2, column j scaled by 1/(2 (j+1))
+// With values v(+-i) at a complete symmetric point set, R(x) = E(x^2) + x O(x^2)
+// where E(i^2) = (v(i) + v(-i)) / 2 and O(i^2) = (v(i) - v(-i)) / (2 i): the
+// EVEN and ODD matrices applied to the sums and differences give E and O.
+enum { VINV_GRID = 0, VINV_SYM = 1, VINV_EVEN = 2, VINV_ODD = 3 };
+GBR_HD int vinv_point(int mode, int j) {
+    return mode == VINV_EVEN ? j * j : mode == VINV_ODD ? (j + 1) * (j + 1) : point_of(mode, j);
+}
+
+// one contraction: coefficients (rows of the matrix) x operand (n entries per
+// pair and prime, formed from the values according to mode)
+enum { GEMM_PLAIN = 0, GEMM_EVEN = 1, GEMM_ODD = 2 };
 struct GemmGroup {
-    const uint32_t *vinv;   // [prime][P][P] inverse Vandermonde matrices
+    const uint32_t *vinv;   // [prime][n][n] inverse Vandermonde matrices
     int64_t pairs_off;      // the group's pair ids: int32 entries at this byte offset of the plan block
-    int32_t P, npairs;
+    int32_t n;              // contraction length = matrix size
+    int32_t rows;           // coefficients produced (<= n): PLAIN c -> c, EVEN c -> 2c, ODD c -> 2c + 1
+    int32_t npairs, mode;
 };
 struct GemmTile {
     int32_t group, c0, q0, prime;

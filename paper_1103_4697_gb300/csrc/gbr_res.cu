@@ -397,25 +397,26 @@ __global__ void k_interp(ResLaunch L, WorkList w, int maxP) {
 
 // ------------------------------------------------------------------ A4 as a contraction
 
-// Inverse Vandermonde matrix of the points x_j = point_of(sym, j), j < P,
-// modulo prime i, normal form, row-major: out[(i*P + c)*P + j] = coefficient of
+// Inverse Vandermonde matrix of the points x_j = vinv_point(mode, j), j < n,
+// modulo prime i, normal form, row-major: out[(i*n + c)*n + j] = coefficient of
 // x^c in the Lagrange basis polynomial L_j(x) = prod_{t != j} (x - x_t) /
-// prod_{t != j} (x_j - x_t).  One block per prime: W(x) = prod_t (x - x_t) is
-// built in shared memory, then thread j divides W by (x - x_j) (synthetic
-// division) and scales by the inverse of its denominator.
+// prod_{t != j} (x_j - x_t), times the column scale of the mode.  One block per
+// prime: W(x) = prod_t (x - x_t) is built in shared memory, then thread j
+// divides W by (x - x_j) (synthetic division) and scales by the inverse of its
+// denominator.
 __device__ __forceinline__ uint32_t mont_of_int(int v, const ModP &M) {
     return mp_to(v >= 0 ? (uint32_t)v : M.p - (uint32_t)(-v), M);
 }
 
-__global__ void k_vinv(const ModP *mods, int P, int sym, uint32_t *out) {
+__global__ void k_vinv(const ModP *mods, int n, int mode, uint32_t *out) {
     extern __shared__ uint32_t sh[];
-    uint32_t *W = sh;             // P + 1 words, Montgomery form
+    uint32_t *W = sh;             // n + 1 words, Montgomery form
     const int i = blockIdx.x;
     const ModP M = mods[i];
-    for (int t = threadIdx.x; t <= P; t += blockDim.x) W[t] = t == 0 ? M.r1 : 0u;
+    for (int t = threadIdx.x; t <= n; t += blockDim.x) W[t] = t == 0 ? M.r1 : 0u;
     __syncthreads();
-    for (int j = 0; j < P; ++j) {                 // W <- W (x - x_j), degree j -> j + 1
-        const uint32_t jm = mont_of_int(point_of(sym, j), M);
+    for (int j = 0; j < n; ++j) {                 // W <- W (x - x_j), degree j -> j + 1
+        const uint32_t jm = mont_of_int(vinv_point(mode, j), M);
         uint32_t nv[4];
         int cnt = 0;
         for (int t = threadIdx.x; t <= j + 1 && cnt < 4; t += blockDim.x, ++cnt) {
@@ -427,19 +428,22 @@ __global__ void k_vinv(const ModP *mods, int P, int sym, uint32_t *out) {
         for (int t = threadIdx.x; t <= j + 1 && cnt < 4; t += blockDim.x, ++cnt) W[t] = nv[cnt];
         __syncthreads();
     }
-    uint32_t *o = out + (int64_t)i * P * P;
-    for (int j = threadIdx.x; j < P; j += blockDim.x) {
-        const int xj = point_of(sym, j);
+    uint32_t *o = out + (int64_t)i * n * n;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int xj = vinv_point(mode, j);
         uint32_t d = M.r1;
-        for (int t = 0; t < P; ++t)
-            if (t != j) d = mp_mul(d, mont_of_int(xj - point_of(sym, t), M), M);
+        for (int t = 0; t < n; ++t)
+            if (t != j) d = mp_mul(d, mont_of_int(xj - vinv_point(mode, t), M), M);
+        // column scale 1/2 (EVEN, j >= 1) or 1/(2 (j+1)) (ODD) joins the denominator
+        const int den = mode == VINV_EVEN ? (j ? 2 : 1) : mode == VINV_ODD ? 2 * (j + 1) : 1;
+        if (den != 1) d = mp_mul(d, mont_of_int(den, M), M);
         const uint32_t id = mp_inv(d, M);
         const uint32_t jm = mont_of_int(xj, M);
-        uint32_t q = W[P];
-        o[(int64_t)(P - 1) * P + j] = mp_from(mp_mul(q, id, M), M);
-        for (int t = P - 1; t >= 1; --t) {
+        uint32_t q = W[n];
+        o[(int64_t)(n - 1) * n + j] = mp_from(mp_mul(q, id, M), M);
+        for (int t = n - 1; t >= 1; --t) {
             q = mp_add(W[t], mp_mul(jm, q, M), M.p);
-            o[(int64_t)(t - 1) * P + j] = mp_from(mp_mul(q, id, M), M);
+            o[(int64_t)(t - 1) * n + j] = mp_from(mp_mul(q, id, M), M);
         }
     }
 }
@@ -457,41 +461,45 @@ __device__ __forceinline__ void mac96(uint32_t &a0, uint32_t &a1, uint32_t &a2, 
 constexpr int GT_M = 64, GT_N = 64, GT_K = 32;
 static_assert(GT_M == GT_N && GT_M * GT_K % 256 == 0, "one load layout serves both operands");
 
-// coefficients = Vinv_i * values for one prime i (blockIdx.z) and a group of
-// pairs that share P.  Tile: 64 coefficient rows x 64 pairs, K in chunks of 32
-// points; each of the 256 threads owns 4 x 4 outputs.  Values are in
-// Montgomery form and Vinv in normal form, so the exact sum X = sum Vinv * v~
-// is congruent to coef * 2^32; one reduction per output gives coef.
-// One block per tile of the flattened list of every point-count group's tiles,
-// so all groups share one launch.
+// coefficients = Vinv_i * operand for one prime i and a group of pairs that
+// share the point set.  Tile: 64 coefficient rows x 64 pairs, K in chunks of 32;
+// each of the 256 threads owns 4 x 4 outputs.  The operand is the values
+// themselves (PLAIN) or, for a complete symmetric point set (value of +i at
+// 2i - 1, of -i at 2i), their sums v(i) + v(-i) (EVEN, v(0) for i = 0) or
+// differences v(i) - v(-i) (ODD, i = j + 1); sums and differences are formed
+// while loading and stay below 2p.  Values are in Montgomery form and Vinv in
+// normal form, so the exact sum X = sum Vinv * v~ is congruent to coef * 2^32;
+// one reduction per output gives coef.  One block per tile of the flattened
+// list of every group's tiles, so all groups share one launch.
 __global__ void __launch_bounds__(256, 2) k_interp_gemm(ResLaunch L, const char *planblk, const GemmGroup *groups,
-                                                    const GemmTile *tiles) {
+                                                       const GemmTile *tiles) {
     __shared__ uint32_t As[GT_K][GT_M + 1];
     __shared__ __align__(16) uint32_t Bs[GT_K][GT_N + 4];
     __shared__ uint32_t Cs[GT_N][GT_M + 1];
     __shared__ int64_t colbase[GT_N], cfbase[GT_N];
     const GemmTile T = tiles[blockIdx.x];
     const GemmGroup Gr = groups[T.group];
-    const int P = Gr.P, npairs = Gr.npairs;
+    const int n = Gr.n, rows = Gr.rows, npairs = Gr.npairs, mode = Gr.mode;
     const int32_t *gpairs = (const int32_t *)(planblk + Gr.pairs_off);
     const uint32_t *vinv = Gr.vinv;
     const int i = T.prime;
     const int c0 = T.c0, q0 = T.q0;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const ModP M = L.mods[i];
     if (threadIdx.x < GT_N) {
         int qi = q0 + threadIdx.x;
         int64_t b = -1;
         if (qi < npairs) {
             const PairPlan &pp = L.plan[gpairs[qi]];
             if (i < pp.k) {
-                b = pp.val_off + (int64_t)i * P;
-                cfbase[threadIdx.x] = pp.cf_off + (int64_t)i * P;
+                b = pp.val_off + (int64_t)i * pp.Pe;
+                cfbase[threadIdx.x] = pp.cf_off + (int64_t)i * pp.P;
             }
         }
         colbase[threadIdx.x] = b;
     }
     __syncthreads();
-    const uint32_t *A = vinv + (int64_t)i * P * P;
+    const uint32_t *A = vinv + (int64_t)i * n * n;
     uint32_t a0[16], a1[16], a2[16];
 #pragma unroll
     for (int t = 0; t < 16; ++t) a0[t] = a1[t] = a2[t] = 0u;
@@ -505,13 +513,19 @@ __global__ void __launch_bounds__(256, 2) k_interp_gemm(ResLaunch L, const char 
             const int e = threadIdx.x + u * 256;
             const int r = e / GT_K, kk = e % GT_K;
             const int c = c0 + r, j = j0 + kk;
-            ra[u] = (c < P && j < P) ? A[(int64_t)c * P + j] : 0u;
+            ra[u] = (c < rows && j < n) ? A[(int64_t)c * n + j] : 0u;
             const int64_t b = colbase[r];
-            rb[u] = (b >= 0 && j < P) ? L.val[b + j] : 0u;
+            uint32_t v = 0u;
+            if (b >= 0 && j < n) {
+                if (mode == GEMM_PLAIN) v = L.val[b + j];
+                else if (mode == GEMM_EVEN) v = j == 0 ? L.val[b] : L.val[b + 2 * j - 1] + L.val[b + 2 * j];
+                else v = L.val[b + 2 * j + 1] + (M.p - L.val[b + 2 * j + 2]);
+            }
+            rb[u] = v;
         }
     };
     load_chunk(0);
-    for (int j0 = 0; j0 < P; j0 += GT_K) {
+    for (int j0 = 0; j0 < n; j0 += GT_K) {
 #pragma unroll
         for (int u = 0; u < kLoads; ++u) {
             const int e = threadIdx.x + u * 256;
@@ -519,7 +533,7 @@ __global__ void __launch_bounds__(256, 2) k_interp_gemm(ResLaunch L, const char 
             Bs[e % GT_K][e / GT_K] = rb[u];
         }
         __syncthreads();
-        if (j0 + GT_K < P) load_chunk(j0 + GT_K);
+        if (j0 + GT_K < n) load_chunk(j0 + GT_K);
 #pragma unroll 8
         for (int kk = 0; kk < GT_K; ++kk) {
             const uint4 bv = *reinterpret_cast<const uint4 *>(&Bs[kk][tx * 4]);
@@ -532,22 +546,23 @@ __global__ void __launch_bounds__(256, 2) k_interp_gemm(ResLaunch L, const char 
         }
         __syncthreads();
     }
-    const ModP M = L.mods[i];
 #pragma unroll
     for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
             const int t = r * 4 + cc;
-            // X * 2^-32 = (a2 2^32 + a1) + a0 2^-32 (mod p); (a2:a1) < 2^41 < p 2^32
+            // X * 2^-32 = (a2 2^32 + a1) + a0 2^-32 (mod p); operands below 2p and
+            // n <= 8192 terms give (a2:a1) < 2^43 < p 2^32
             uint32_t hi = mp_mul(mp_redc(a1[t], a2[t], M.p, M.pinv), M.r2, M);
             uint32_t lo = mp_redc(a0[t], 0u, M.p, M.pinv);
             Cs[tx * 4 + cc][ty * 4 + r] = mp_add(hi, lo, M.p);
         }
     __syncthreads();
+    const int ostride = mode == GEMM_PLAIN ? 1 : 2, ooff = mode == GEMM_ODD ? 1 : 0;
     for (int e = threadIdx.x; e < GT_N * GT_M; e += 256) {
         int qq = e / GT_M, r = e % GT_M;
         int64_t b = colbase[qq];
-        if (b >= 0 && c0 + r < P) L.cf[cfbase[qq] + c0 + r] = Cs[qq][r];
+        if (b >= 0 && c0 + r < rows) L.cf[cfbase[qq] + (int64_t)(c0 + r) * ostride + ooff] = Cs[qq][r];
     }
 }
 
@@ -701,12 +716,13 @@ cudaError_t launch_interp(const ResLaunch &L, const WorkList &w, int maxP, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_vinv(const ModP *mods, int P, int K, int sym, uint32_t *out, cudaStream_t s) {
-    size_t smem = (size_t)(P + 1) * sizeof(uint32_t);
-    int block = P + 2 <= 1024 ? ((P + 2 + 31) / 32) * 32 : 1024;
+cudaError_t launch_vinv(const ModP *mods, int n, int K, int mode, uint32_t *out, cudaStream_t s) {
+    if (n < 1) return cudaErrorInvalidValue;
+    size_t smem = (size_t)(n + 1) * sizeof(uint32_t);
+    int block = n + 2 <= 1024 ? ((n + 2 + 31) / 32) * 32 : 1024;
     // each thread updates at most 4 coefficients of W per step
-    if (smem > kMaxDynSmem || P + 1 > 4 * block) return cudaErrorInvalidValue;
-    k_vinv<<<K, block, smem, s>>>(mods, P, sym, out);
+    if (smem > kMaxDynSmem || n + 1 > 4 * block) return cudaErrorInvalidValue;
+    k_vinv<<<K, block, smem, s>>>(mods, n, mode, out);
     return cudaGetLastError();
 }
 
