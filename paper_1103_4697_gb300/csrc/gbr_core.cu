@@ -273,6 +273,60 @@ int gbr_ctx::ensure_tables(int K, int T) {
     return GBR_OK;
 }
 
+// Device prime table: the ModP entries of every table prime, followed by
+// (R^3 mod p, R^4 mod p) per prime for the one-reduction residue conversion.
+size_t gbr::prime_table_bytes() {
+    return (size_t)num_primes() * (sizeof(ModP) + sizeof(uint2)) + (size_t)kCrtTabWords * 4;
+}
+
+cudaError_t gbr::upload_prime_table(ModP *d) {
+    const int NP = num_primes();
+    const ModP *hm = host_mods();
+    std::vector<char> buf(prime_table_bytes());
+    std::memcpy(buf.data(), hm, sizeof(ModP) * NP);
+    uint2 *r34 = (uint2 *)(buf.data() + sizeof(ModP) * NP);
+    for (int i = 0; i < NP; ++i) {
+        const uint64_t p = hm[i].p, r1 = hm[i].r1, r2 = hm[i].r2;
+        r34[i].x = (uint32_t)(r2 * r1 % p);
+        r34[i].y = (uint32_t)(r2 * r2 % p);
+    }
+    // CRT tables of the first kCrtFastK primes
+    uint32_t *tab = (uint32_t *)(r34 + NP);
+    std::memset(tab, 0, (size_t)kCrtTabWords * 4);
+    const int KF = std::min(kCrtFastK, NP);
+    for (int i = 1; i < KF; ++i) {
+        const uint64_t pi = hm[i].p;
+        uint64_t C = 1;   // prod_{l<j} p_l mod p_i
+        for (int j = 0; j < i; ++j) {
+            tab[crt_gd_off(i) + j] = to_mont_host((uint32_t)((pi - C) % pi), (uint32_t)pi);
+            C = C * (hm[j].p % pi) % pi;
+        }
+    }
+    uint32_t *T = tab + kCrtGdWords;
+    std::vector<uint32_t> P(kCrtFastL + 2, 0u);   // prod_{j<i} p_j in 32-bit limbs
+    P[0] = 1;
+    for (int i = 0; i <= KF; ++i) {
+        for (int l = 0; l < kCrtFastL; ++l) T[(size_t)l * kCrtFastRow + i] = P[l];
+        if (i == KF) break;
+        uint64_t carry = 0;
+        for (int l = 0; l < kCrtFastL + 2; ++l) {
+            const uint64_t t = (uint64_t)P[l] * hm[i].p + carry;
+            P[l] = (uint32_t)t;
+            carry = t >> 32;
+        }
+    }
+    uint32_t *I0 = T + (size_t)kCrtFastL * kCrtFastRow;
+    for (int l = 0; l < kCrtFastL; ++l) {
+        int i = 0;
+        while (i <= KF && T[(size_t)l * kCrtFastRow + i] == 0u) ++i;
+        I0[l] = (uint32_t)(i & ~3);
+    }
+    return cudaMemcpy(d, buf.data(), buf.size(), cudaMemcpyHostToDevice);
+}
+
+const uint2 *gbr::prime_r34(const ModP *d) { return (const uint2 *)(d + num_primes()); }
+const uint32_t *gbr::prime_crt_tables(const ModP *d) { return (const uint32_t *)(prime_r34(d) + num_primes()); }
+
 // Inverse Vandermonde matrices are cached per (size n, point set) for the first
 // K primes; the cache is bounded by a quarter of the context's budget (at least
 // 256 MiB), least recently used entries are dropped.
@@ -554,13 +608,13 @@ extern "C" int gbr_create(gbr_ctx **out, int device, size_t budget, void *worksp
     }
     c->arena.init(c->ws, budget);
     const int NP = num_primes();
-    c->d_mods = (ModP *)c->dalloc(sizeof(ModP) * NP);
+    c->d_mods = (ModP *)c->dalloc(prime_table_bytes());
     c->d_err = (int32_t *)c->dalloc(64);
     if (!c->d_mods || !c->d_err) {
         gbr_destroy(c);
         return GBR_ENOMEM;
     }
-    e = cudaMemcpy(c->d_mods, host_mods(), sizeof(ModP) * NP, cudaMemcpyHostToDevice);
+    e = upload_prime_table(c->d_mods);
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, 64);
     if (e == cudaSuccess) e = configure_res_kernels();
     if (e == cudaSuccess) e = configure_gcd_kernels();
@@ -609,10 +663,9 @@ gbr_ctx *gbr_make_worker(gbr_ctx *parent) {
         return nullptr;
     }
     w->own_stream = true;
-    const int NP = num_primes();
-    w->d_mods = (ModP *)w->dalloc(sizeof(ModP) * NP);
+    w->d_mods = (ModP *)w->dalloc(prime_table_bytes());
     w->d_err = (int32_t *)w->dalloc(64);
-    if (!w->d_mods || !w->d_err || cudaMemcpy(w->d_mods, host_mods(), sizeof(ModP) * NP, cudaMemcpyHostToDevice) ||
+    if (!w->d_mods || !w->d_err || upload_prime_table(w->d_mods) ||
         cudaMemset(w->d_err, 0, 64)) {
         gbr_destroy_worker(w);
         return nullptr;
@@ -867,6 +920,8 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
     L.bounds = r->d_bounds;
     L.rowdeg = r->d_rowdeg;
     L.mods = c->d_mods;
+    L.r34 = prime_r34(c->d_mods);
+    L.crtfast = prime_crt_tables(c->d_mods);
     L.npairs = n;
     L.err = c->d_err;
     L.deg = r->d_deg;
@@ -956,8 +1011,9 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
     }
     // ---- buffer offsets and work lists
     int64_t res_w = 0, val_w = 0, cf_w = 0, flag_b = 0, gtab_w = 0, out_w = 0, sign_b = 0;
-    int Kmax = 1, Pmax = 1, Lmax = 1;
-    HostList red, interp, crt;
+    int Kmax = 1, Pmax = 1, Lmax = 1, Kdig = 1;   // Kdig: most primes of one pair
+    HostList red, interp, crt, crtf;
+    int Kdig_f = 1, Lmax_f = 1;
     std::map<int, HostList> evb;
     std::map<int, HostList> evr;                    // register form, by N
     std::map<int, std::vector<int32_t>> pgroups;   // pairs by point count
@@ -992,6 +1048,7 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
             kmapped = std::max(kmapped, k);
         }
         Kmax = std::max(Kmax, p.pmap_off >= 0 ? pmap[p.pmap_off + k - 1] + 1 : k);
+        Kdig = std::max(Kdig, k);
         Pmax = std::max(Pmax, p.Pe);
         Lmax = std::max(Lmax, p.L);
         red.add(q, p.S);
@@ -1003,7 +1060,13 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
         // primes are the table prefix
         if (p.pmap_off < 0 && (p.sym || p.Pe == p.P)) pgroups[2 * p.P + p.sym].push_back(q);
         else interp.add(q, k);
-        crt.add(q, p.P);
+        if (p.pmap_off < 0 && k <= kCrtFastK) {
+            crtf.add(q, p.P);
+            Kdig_f = std::max(Kdig_f, k);
+            Lmax_f = std::max(Lmax_f, p.L);
+        } else {
+            crt.add(q, p.P);
+        }
         subproblems += (int64_t)k * p.Pe;
         int64_t ev = (int64_t)k * p.P * (b.tf + b.tg + 2LL * p.m * p.n);
         st.modmul_evalres += ev;
@@ -1062,6 +1125,8 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
     put_list(blk, red, o_red_p, o_red_s);
     put_list(blk, interp, o_int_p, o_int_s);
     put_list(blk, crt, o_crt_p, o_crt_s);
+    size_t o_crtf_p, o_crtf_s;
+    put_list(blk, crtf, o_crtf_p, o_crtf_s);
     std::vector<std::pair<size_t, size_t>> o_ev;
     for (auto &kv : evb) {
         size_t a, b2;
@@ -1255,8 +1320,14 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
             kernels++;
         }
         record(4, capturing, q);
-        if (x == cudaSuccess) x = launch_crt(L, mk(o_crt_p, o_crt_s, crt), Lmax, q);
-        kernels++;
+        if (x == cudaSuccess && crtf.total > 0) {
+            x = launch_crt_fast(L, mk(o_crtf_p, o_crtf_s, crtf), Kdig_f, Lmax_f, q);
+            kernels++;
+        }
+        if (x == cudaSuccess && crt.total > 0) {
+            x = launch_crt(L, mk(o_crt_p, o_crt_s, crt), Kdig, Lmax, q);
+            kernels++;
+        }
         record(5, capturing, q);
         return x;
     };

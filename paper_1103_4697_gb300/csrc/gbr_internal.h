@@ -14,6 +14,25 @@ namespace gbr {
 // ------------------------------------------------------------------ prime table (host)
 int num_primes();
 const ModP *host_mods();              // ModP for every table prime, p_0 > p_1 > ...
+size_t prime_table_bytes();             // device prime table: ModP[num_primes()], uint2 (R^3, R^4)[num_primes()],
+cudaError_t upload_prime_table(ModP *d);  // then the CRT tables of the first kCrtFastK primes
+const uint2 *prime_r34(const ModP *d);
+const uint32_t *prime_crt_tables(const ModP *d);
+
+// Chinese remaindering tables for pairs on the first kCrtFastK table primes:
+//   Garner rows: row i (at crt_gd_off(i), padded with zeros to a multiple of 4)
+//     holds (-prod_{l<j} p_l mod p_i) R mod p_i for j < i, so that
+//     r_i R + sum_j v_j row_i[j] = R (r_i - sum_{j<i} v_j prod_{l<j} p_l) (mod p_i);
+//   limb table T[l][i] (rows of kCrtFastRow words): limb l of prod_{j<i} p_j, i <= kCrtFastK;
+//   I0[l]: the first i (a multiple of 4) with T[l][i] != 0.
+constexpr int kCrtFastK = 64, kCrtFastRow = 68, kCrtFastL = 62;
+GBR_HD int crt_gd_off(int i) {
+    if (i <= 0) return 0;
+    const int q = (i - 1) / 4, r = (i - 1) % 4;
+    return 8 * q * (q + 1) + 4 * r * (q + 1);
+}
+constexpr int kCrtGdWords = 8 * 15 * 16 + 4 * 3 * 16;   // crt_gd_off(kCrtFastK)
+constexpr int kCrtTabWords = kCrtGdWords + kCrtFastL * kCrtFastRow + kCrtFastL;
 double log2_prime_prefix(int k);      // sum_{i<k} log2 p_i
 int primes_for_bits(double bits);     // smallest k with sum_{i<k} log2 p_i > bits
 
@@ -171,6 +190,8 @@ struct ResLaunch {
     int32_t *rowdeg;
     const PairPlan *plan;
     const ModP *mods;
+    const uint2 *r34;            // per prime (R^3 mod p, R^4 mod p), R = 2^32
+    const uint32_t *crtfast;     // CRT tables of the first kCrtFastK primes (Garner rows, T, I0)
     const uint32_t *garner;      // prefix Garner table (K + K(K-1)/2 words)
     int32_t garner_K;
     const uint32_t *invk;        // [prime][invk_T] inverses of 1..T-1
@@ -235,7 +256,9 @@ GBR_HD int reg_shape(int m, int n) {
 cudaError_t launch_evalres_reg(const ResLaunch &L, const WorkList &w, int N, int block, unsigned long long *redo_n,
                                int64_t *redo, cudaStream_t s);
 cudaError_t launch_interp(const ResLaunch &L, const WorkList &w, int maxP, cudaStream_t s);
-cudaError_t launch_crt(const ResLaunch &L, const WorkList &w, int maxL, cudaStream_t s);
+cudaError_t launch_crt(const ResLaunch &L, const WorkList &w, int maxK, int maxL, cudaStream_t s);
+// pairs on the prime-table prefix with k <= kCrtFastK
+cudaError_t launch_crt_fast(const ResLaunch &L, const WorkList &w, int maxK, int maxL, cudaStream_t s);
 cudaError_t launch_vinv(const ModP *mods, int n, int K, int mode, uint32_t *out, cudaStream_t s);
 cudaError_t launch_unlucky_primes(const ResLaunch &L, int kc, uint8_t *out, cudaStream_t s);
 cudaError_t launch_pair_garner(const ResLaunch &L, const int32_t *pairs, int n, int kmax, uint32_t *gtab,

@@ -87,9 +87,11 @@ __device__ __forceinline__ const uint64_t *coef_ptr(const uint64_t *coef, const 
 // any lambda gives a valid bound).
 constexpr int kBoundsWarps = 4;
 
-// log2 of the 1-norm of a row: exact 128-bit sum for int64 coefficients, else
-// a log-sum-exp over the coefficients' log2 magnitudes.
-__device__ double row_log2_norm(const uint64_t *coef, const PolyDesc &P, int r, int lane, int &cmax) {
+// 1-norm of a row.  int64 coefficients: the exact 128-bit sum, returned as a
+// double (the caller takes log2 of it later, one row per lane, +1e-12 for the
+// rounding of the conversion and of log2); wider coefficients: log2 of the norm
+// by a log-sum-exp over the coefficients' log2 magnitudes.
+__device__ double row_norm(const uint64_t *coef, const PolyDesc &P, int r, int lane, int &cmax) {
     cmax = -1;
     if (P.words == 1) {
         uint64_t lo = 0, hi = 0;
@@ -108,9 +110,7 @@ __device__ double row_log2_norm(const uint64_t *coef, const PolyDesc &P, int r, 
             hi += ohi + (lo < olo);
             cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
         }
-        if (!lo && !hi) return -INFINITY;
-        double v = (double)hi * 0x1p64 + (double)lo;
-        return log2(v) + 1e-12;
+        return (double)hi * 0x1p64 + (double)lo;
     }
     Lse nrm;
     nrm.init();
@@ -193,11 +193,12 @@ __global__ void __launch_bounds__(kBoundsWarps * 32) k_bounds(ResLaunch L) {
         if (which == 1 && D.disc) break;
         const PolyDesc &P = which ? D.g : D.f;
         double *ln_out = which ? lng[wib] : lnf[wib];
+        const bool linear = P.words == 1;   // row_norm returns the norm itself
         int mdeg = -1, dxmax = -1, td = -1, terms = 0, terms_upto = 0, lcd = -1;
         int mdeg_g = -1, dx_g = -1, td_g = -1, terms_g = 0, terms_g_upto = 0, lcd_g = -1;
         for (int r = 0; r <= P.rows; ++r) {
             int cmax;
-            const double ln = row_log2_norm(L.coef, P, r, lane, cmax);
+            const double ln = row_norm(L.coef, P, r, lane, cmax);
             if (lane == 0) {
                 L.rowdeg[P.rowdeg_off + r] = cmax;
                 if (r <= GBR_MAX_YDEG) ln_out[r] = ln;
@@ -213,7 +214,8 @@ __global__ void __launch_bounds__(kBoundsWarps * 32) k_bounds(ResLaunch L) {
             if (which == 0 && D.disc && r >= 1) {
                 if (lane == 0) {
                     L.rowdeg[D.g.rowdeg_off + r - 1] = cmax;
-                    if (r - 1 <= GBR_MAX_YDEG) lng[wib][r - 1] = ln == -INFINITY ? ln : ln + log2((double)r);
+                    if (r - 1 <= GBR_MAX_YDEG)
+                        lng[wib][r - 1] = linear ? ln * r : (ln == -INFINITY ? ln : ln + log2((double)r));
                 }
                 terms_g += cmax + 1;
                 if (cmax >= 0) {
@@ -225,6 +227,17 @@ __global__ void __launch_bounds__(kBoundsWarps * 32) k_bounds(ResLaunch L) {
                 }
             }
         }
+        // log2 of the norms, one row per lane
+        __syncwarp();
+        if (linear) {
+            const int nr = min(P.rows, GBR_MAX_YDEG + 1);
+            for (int r = lane; r <= nr; r += 32) {
+                if (r <= GBR_MAX_YDEG) ln_out[r] = ln_out[r] > 0.0 ? log2(ln_out[r]) + 1e-12 : -INFINITY;
+                if (which == 0 && D.disc && r >= 1)
+                    lng[wib][r - 1] = lng[wib][r - 1] > 0.0 ? log2(lng[wib][r - 1]) + 1e-12 : -INFINITY;
+            }
+        }
+        __syncwarp();
         if (which == 0) {
             B.m = mdeg; B.dxf = dxmax; B.tdf = td; B.tf = terms_upto; B.lcdf = lcd;
             if (D.disc) {
@@ -298,9 +311,30 @@ __global__ void k_reduce(ResLaunch L, WorkList w) {
             for (int i = 0; i < P.k; ++i) dst[(int64_t)i * P.S] = 0u;
             continue;
         }
-        uint64_t wbuf[8];
         const uint64_t *cp = coef_ptr(L.coef, *src, mult ? row + 1 : row, col);
         int W = src->words;
+        if (W == 1) {
+            // |c| = hi 2^32 + lo: c R^2 = redc(hi R^4 + lo R^3); the sum is below
+            // 2p 2^32, so the reduction leaves a value below 3p
+            const int64_t v = (int64_t)cp[0];
+            const bool neg = v < 0;
+            const uint64_t av = neg ? 0ull - (uint64_t)v : (uint64_t)v;
+            const uint32_t hi = (uint32_t)(av >> 32), lo = (uint32_t)av;
+            for (int i = 0; i < P.k; ++i) {
+                const int pi = prime_of(P, L.pmap, i);
+                const ModP M = L.mods[pi];
+                const uint2 r34 = L.r34[pi];
+                const uint64_t t = (uint64_t)hi * r34.y + (uint64_t)lo * r34.x;
+                const uint32_t m = (uint32_t)t * M.pinv;
+                uint32_t r = (uint32_t)((t + (uint64_t)m * M.p) >> 32);
+                r = min(r, r - M.p);
+                r = min(r, r - M.p);
+                if (mult) r = mp_mul(r, mp_to((uint32_t)mult, M), M);
+                dst[(int64_t)i * P.S] = neg ? mp_neg(r, M.p) : r;
+            }
+            continue;
+        }
+        uint64_t wbuf[8];
         for (int i = 0; i < W; ++i) wbuf[i] = cp[i];
         for (int i = 0; i < P.k; ++i) {
             ModP M = L.mods[prime_of(P, L.pmap, i)];
@@ -471,7 +505,7 @@ static_assert(GT_M == GT_N && GT_M * GT_K % 256 == 0, "one load layout serves bo
 // normal form, so the exact sum X = sum Vinv * v~ is congruent to coef * 2^32;
 // one reduction per output gives coef.  One block per tile of the flattened
 // list of every group's tiles, so all groups share one launch.
-__global__ void __launch_bounds__(256, 2) k_interp_gemm(ResLaunch L, const char *planblk, const GemmGroup *groups,
+__global__ void __launch_bounds__(256, 3) k_interp_gemm(ResLaunch L, const char *planblk, const GemmGroup *groups,
                                                        const GemmTile *tiles) {
     __shared__ uint32_t As[GT_K][GT_M + 1];
     __shared__ __align__(16) uint32_t Bs[GT_K][GT_N + 4];
@@ -568,10 +602,14 @@ __global__ void __launch_bounds__(256, 2) k_interp_gemm(ResLaunch L, const char 
 
 // ------------------------------------------------------------------ A5: Chinese remaindering
 
-__global__ void k_crt(ResLaunch L, WorkList w, int LM) {
+// One thread per output coefficient.  The k residues are read once into this
+// thread's column of shared memory (stride BS) and turned into Garner digits
+// there; the limbs of the magnitude follow in the same column.  KM = 0 (too
+// many primes for shared memory): the digits overwrite the residues in place.
+__global__ void k_crt(ResLaunch L, WorkList w, int KM, int LM) {
     extern __shared__ uint32_t smem[];
     const int BS = blockDim.x;
-    uint32_t *limb = smem + threadIdx.x;
+    uint32_t *limb = smem + (size_t)KM * BS + threadIdx.x;
     for (int64_t item = blockIdx.x * (int64_t)BS + threadIdx.x; item < w.total; item += (int64_t)gridDim.x * BS) {
         int bi = wl_find(w.start, w.n, item);
         int q = w.pairs[bi];
@@ -580,25 +618,28 @@ __global__ void k_crt(ResLaunch L, WorkList w, int LM) {
         const int k = P.k, Pn = P.P;
         const uint32_t *cinv = P.gtab_off < 0 ? L.garner : L.gtab + P.gtab_off;
         const uint32_t *pm = P.gtab_off < 0 ? L.garner + L.garner_K : L.gtab + P.gtab_off + k;
-        uint32_t *v = L.cf + P.cf_off + c;
+        uint32_t *src = L.cf + P.cf_off + c;
+        uint32_t *v = KM ? smem + threadIdx.x : src;
+        const int64_t vs = KM ? BS : Pn;
+        if (KM)
+            for (int i = 0; i < k; ++i) v[i * vs] = src[(int64_t)i * Pn];
         // Garner: digits v_i with X = sum v_i prod_{j<i} p_j, 0 <= v_i < p_i
         for (int i = 1; i < k; ++i) {
             const ModP M = L.mods[prime_of(P, L.pmap, i)];
             const uint32_t *pmi = pm + (int64_t)i * (i - 1) / 2;
-            uint32_t t = v[(int64_t)(i - 1) * Pn];
+            uint32_t t = v[(i - 1) * vs];
             t = min(t, t - M.p);
             for (int j = i - 2; j >= 0; --j) {
-                uint32_t vj = v[(int64_t)j * Pn];
+                uint32_t vj = v[j * vs];
                 vj = min(vj, vj - M.p);
                 t = mp_add(mp_mul(t, pmi[j], M), vj, M.p);
             }
-            uint32_t r = v[(int64_t)i * Pn];
-            v[(int64_t)i * Pn] = mp_mul(mp_sub(r, t, M.p), cinv[i], M);
+            v[i * vs] = mp_mul(mp_sub(v[i * vs], t, M.p), cinv[i], M);
         }
         // symmetric lift: X > (M-1)/2 <=> digits compare above (p_i - 1)/2 from the top
         int cmp = 0;
         for (int i = k - 1; i >= 0 && cmp == 0; --i) {
-            uint32_t d = v[(int64_t)i * Pn];
+            uint32_t d = v[i * vs];
             uint32_t h = (L.mods[prime_of(P, L.pmap, i)].p - 1u) >> 1;
             cmp = (d > h) - (d < h);
         }
@@ -607,7 +648,7 @@ __global__ void k_crt(ResLaunch L, WorkList w, int LM) {
         int nl = 0;
         for (int i = k - 1; i >= 0; --i) {
             const uint32_t p = L.mods[prime_of(P, L.pmap, i)].p;
-            uint32_t d = v[(int64_t)i * Pn];
+            uint32_t d = v[i * vs];
             if (neg) d = p - 1u - d;
             uint32_t carry = d;
             for (int l = 0; l < nl; ++l) {
@@ -626,6 +667,94 @@ __global__ void k_crt(ResLaunch L, WorkList w, int LM) {
         if (nl > P.L) atomicExch(L.err, 2);
         uint32_t *o = L.out + P.out_off + (int64_t)c * P.L;
         for (int l = 0; l < P.L; ++l) o[l] = l < nl ? limb[l * BS] : 0u;
+        L.sign[P.sign_off + c] = nl == 0 ? 0 : (neg ? -1 : 1);
+        if (nl > 0) atomicMax(L.deg + q, c);
+    }
+}
+
+// Chinese remaindering for pairs on the first kCrtFastK table primes, one
+// thread per output coefficient.  Garner digits as dot products:
+//   v_i = (r_i - sum_{j<i} v_j prod_{l<j} p_l) (prod_{l<i} p_l)^-1 mod p_i,
+// each row summed exactly in 96 bits from the residue r_i R and the table row
+// of (-prod_{l<j} p_l) R (one reduction per digit instead of one per term).
+// The magnitude X = sum_i v_i prod_{j<i} p_j is built limb by limb from the
+// limb table T (limb l = sum_i v_i T[l][i] + carry, exact in 96 bits); a
+// negative value has magnitude prod_{i<k} p_i - X, subtracted limb by limb.
+// Digits live in shared memory as uint4 groups [i/4][thread], the tables are
+// staged in shared memory once per block.
+__global__ void k_crt_fast(ResLaunch L, WorkList w, int KD, int LD) {
+    extern __shared__ uint4 smem4[];
+    uint32_t *sw = reinterpret_cast<uint32_t *>(smem4);
+    const int BS = blockDim.x;
+    const int gdw = (crt_gd_off(KD) + 3) & ~3;
+    uint32_t *Gd = sw;                                   // gdw words
+    uint32_t *T = Gd + gdw;                              // LD rows of kCrtFastRow words
+    uint32_t *I0 = T + (size_t)LD * kCrtFastRow;         // LD words (padded to 4)
+    uint4 *dig = reinterpret_cast<uint4 *>(I0 + ((LD + 3) & ~3));
+    for (int t = threadIdx.x; t < gdw; t += BS) Gd[t] = t < kCrtGdWords ? L.crtfast[t] : 0u;
+    for (int t = threadIdx.x; t < LD * kCrtFastRow; t += BS) T[t] = L.crtfast[kCrtGdWords + t];
+    for (int t = threadIdx.x; t < LD; t += BS) I0[t] = L.crtfast[kCrtGdWords + kCrtFastL * kCrtFastRow + t];
+    __syncthreads();
+    uint32_t *dw = reinterpret_cast<uint32_t *>(dig);
+    auto dslot = [&](int i) -> uint32_t & { return dw[((size_t)(i >> 2) * BS + threadIdx.x) * 4 + (i & 3)]; };
+    for (int64_t item = blockIdx.x * (int64_t)BS + threadIdx.x; item < w.total; item += (int64_t)gridDim.x * BS) {
+        const int bi = wl_find(w.start, w.n, item);
+        const int q = w.pairs[bi];
+        const int c = (int)(item - w.start[bi]);
+        const PairPlan &P = L.plan[q];
+        const int k = P.k, Pn = P.P, k4 = (k + 3) >> 2;
+        const uint32_t *src = L.cf + P.cf_off + c;
+        dslot(0) = src[0];
+        for (int i = k; i < 4 * k4; ++i) dslot(i) = 0u;   // the last group's unused digits
+        for (int i = 1; i < k; ++i) {
+            const ModP M = L.mods[i];
+            uint32_t a0 = 0u, a1 = src[(int64_t)i * Pn], a2 = 0u;
+            const uint4 *row = reinterpret_cast<const uint4 *>(Gd + crt_gd_off(i));
+            for (int g = 0; g < ((i + 3) >> 2); ++g) {
+                const uint4 d = dig[(size_t)g * BS + threadIdx.x], e = row[g];
+                mac96(a0, a1, a2, d.x, e.x);
+                mac96(a0, a1, a2, d.y, e.y);
+                mac96(a0, a1, a2, d.z, e.z);
+                mac96(a0, a1, a2, d.w, e.w);
+            }
+            // (a2 2^32 + a1) + a0 2^-32 = R (r_i - S) 2^-32 = r_i - S (mod p_i)
+            const uint32_t hi = mp_mul(mp_redc(a1, a2, M.p, M.pinv), M.r2, M);
+            const uint32_t y = mp_add(hi, mp_redc(a0, 0u, M.p, M.pinv), M.p);
+            dslot(i) = mp_mul(y, L.garner[i], M);
+        }
+        // symmetric lift: X > (M-1)/2 <=> digits compare above (p_i - 1)/2 from the top
+        int cmp = 0;
+        for (int i = k - 1; i >= 0 && cmp == 0; --i) {
+            const uint32_t d = dslot(i), h = (L.mods[i].p - 1u) >> 1;
+            cmp = (d > h) - (d < h);
+        }
+        const bool neg = cmp > 0;
+        uint32_t *o = L.out + P.out_off + (int64_t)c * P.L;
+        uint32_t c0 = 0u, c1 = 0u, borrow = 0u;
+        int nl = 0;
+        for (int l = 0; l < P.L; ++l) {
+            uint32_t a0 = c0, a1 = c1, a2 = 0u;
+            const uint32_t *Tl = T + (size_t)l * kCrtFastRow;
+            for (int g = (int)(I0[l] >> 2); g < k4; ++g) {
+                const uint4 d = dig[(size_t)g * BS + threadIdx.x];
+                const uint4 e = *reinterpret_cast<const uint4 *>(Tl + 4 * g);
+                mac96(a0, a1, a2, d.x, e.x);
+                mac96(a0, a1, a2, d.y, e.y);
+                mac96(a0, a1, a2, d.z, e.z);
+                mac96(a0, a1, a2, d.w, e.w);
+            }
+            c0 = a1;
+            c1 = a2;
+            uint32_t x = a0;
+            if (neg) {
+                const uint32_t m = Tl[k];
+                const uint64_t t = (uint64_t)m - x - borrow;
+                x = (uint32_t)t;
+                borrow = (uint32_t)(t >> 63);
+            }
+            o[l] = x;
+            if (x) nl = l + 1;
+        }
         L.sign[P.sign_off + c] = nl == 0 ? 0 : (neg ? -1 : 1);
         if (nl > 0) atomicMax(L.deg + q, c);
     }
@@ -691,6 +820,7 @@ cudaError_t configure_res_kernels() {
     cudaError_t e = configure_evalres_kernel();
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_interp, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_crt, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_crt_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_vinv, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     return e;
 }
@@ -733,6 +863,18 @@ cudaError_t launch_interp_gemm(const ResLaunch &L, const char *planblk, const Ge
     return cudaGetLastError();
 }
 
+cudaError_t launch_crt_fast(const ResLaunch &L, const WorkList &w, int maxK, int maxL, cudaStream_t s) {
+    if (w.total <= 0) return cudaSuccess;
+    if (maxK > kCrtFastK || maxL > kCrtFastL) return cudaErrorInvalidValue;
+    const int block = 128, k4 = (maxK + 3) / 4;
+    const size_t tab = (size_t)((crt_gd_off(maxK) + 3) & ~3) + (size_t)maxL * kCrtFastRow + ((maxL + 3) & ~3);
+    const size_t smem = tab * 4 + (size_t)k4 * block * 16;
+    if (smem > kMaxDynSmem) return cudaErrorInvalidValue;
+    int grid = persistent_grid(k_crt_fast, block, smem, (w.total + block - 1) / block);
+    k_crt_fast<<<grid, block, smem, s>>>(L, w, maxK, maxL);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_unlucky_primes(const ResLaunch &L, int kc, uint8_t *out, cudaStream_t s) {
     int64_t total = (int64_t)L.npairs * kc;
     if (total <= 0) return cudaSuccess;
@@ -750,14 +892,15 @@ cudaError_t launch_pair_garner(const ResLaunch &L, const int32_t *pairs, int n, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_crt(const ResLaunch &L, const WorkList &w, int maxL, cudaStream_t s) {
+cudaError_t launch_crt(const ResLaunch &L, const WorkList &w, int maxK, int maxL, cudaStream_t s) {
     if (w.total <= 0) return cudaSuccess;
     int block = 128;
-    while (block > 32 && (size_t)maxL * block * 4 > 160 * 1024) block >>= 1;
-    size_t smem = (size_t)maxL * block * sizeof(uint32_t);
+    while (block > 32 && (size_t)(maxK + maxL) * block * 4 > 160 * 1024) block >>= 1;
+    if ((size_t)(maxK + maxL) * block * 4 > 160 * 1024) maxK = 0;   // digits stay in global memory
+    size_t smem = (size_t)(maxK + maxL) * block * sizeof(uint32_t);
     if (smem > kMaxDynSmem) return cudaErrorInvalidValue;
     int grid = persistent_grid(k_crt, block, smem, (w.total + block - 1) / block);
-    k_crt<<<grid, block, smem, s>>>(L, w, maxL);
+    k_crt<<<grid, block, smem, s>>>(L, w, maxK, maxL);
     return cudaGetLastError();
 }
 
