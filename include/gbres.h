@@ -157,6 +157,9 @@ const char *gbr_last_error(gbr_ctx *ctx);
 #define GBR_OPT_INTERP_GEMM  5   /* 1 (default): pairs of a batch that share their number of points
                                     are interpolated by one inverse-Vandermonde contraction per
                                     prime; 0: Newton interpolation for every (pair, prime) */
+#define GBR_OPT_INTERP_TC    7   /* 1 (default): the inverse-Vandermonde contractions of up to 256
+                                    points run on the tensor cores (bf16 digits, exact fp32 sums);
+                                    0: on the integer pipes */
 #define GBR_OPT_REGISTER_FORM 6  /* 1 (default): pairs of shape (N, N), (N, N-1) or (N-1, N) in the
                                     eliminated variable, 2 <= N <= 32, are solved with the
                                     polynomials in registers (warps that meet a vanishing leading

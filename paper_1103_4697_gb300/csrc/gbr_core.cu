@@ -348,6 +348,7 @@ const uint32_t *gbr_ctx::get_vinv(int n, int K, int mode) {
     if (it != vinv.end()) {
         if (it->second.last_use > vinv_run_mark) return nullptr;   // held by this run with a smaller K
         dfree(it->second.d);
+        dfree(it->second.tc);
         vinv.erase(it);
     }
     // evict least recently used entries, never one that the current run already
@@ -359,6 +360,7 @@ const uint32_t *gbr_ctx::get_vinv(int n, int K, int mode) {
                 lru = jt;
         if (lru == vinv.end()) return nullptr;
         dfree(lru->second.d);
+        dfree(lru->second.tc);
         vinv.erase(lru);
     }
     uint32_t *d = (uint32_t *)dalloc(bytes);
@@ -373,6 +375,27 @@ const uint32_t *gbr_ctx::get_vinv(int n, int K, int mode) {
     v.bytes = bytes;
     v.last_use = ++vinv_clock;
     vinv[key] = v;
+    return d;
+}
+
+// bf16 digit tiles of a cached matrix (all n rows), built on first use and
+// counted against the cache; nullptr when the matrix is too large for the
+// tensor-core path or the memory is not there
+const uint16_t *gbr_ctx::get_vinv_tc(int n, int K, int mode) {
+    if (n > kTcMaxN) return nullptr;
+    auto it = vinv.find(4 * (int64_t)n + mode);
+    if (it == vinv.end() || it->second.K < K) return nullptr;
+    Vinv &v = it->second;
+    if (v.tc) return v.tc;
+    const size_t bytes = vinv_tc_bytes(n, n, v.K);
+    uint16_t *d = (uint16_t *)dalloc(bytes);
+    if (!d) return nullptr;
+    if (launch_vinv_tc(v.d, n, n, v.K, d, stream) != cudaSuccess) {
+        dfree(d);
+        return nullptr;
+    }
+    v.tc = d;
+    v.bytes += bytes;
     return d;
 }
 
@@ -618,6 +641,7 @@ extern "C" int gbr_create(gbr_ctx **out, int device, size_t budget, void *worksp
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, 64);
     if (e == cudaSuccess) e = configure_res_kernels();
     if (e == cudaSuccess) e = configure_gcd_kernels();
+    if (e == cudaSuccess) e = configure_interp_tc_kernel();
     if (e != cudaSuccess) {
         gbr_destroy(c);
         return GBR_EDEVICE;
@@ -636,7 +660,10 @@ extern "C" void gbr_destroy(gbr_ctx *c) {
     else cudaDeviceSynchronize();
     for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-    for (auto &kv : c->vinv) c->dfree(kv.second.d);
+    for (auto &kv : c->vinv) {
+        c->dfree(kv.second.d);
+        c->dfree(kv.second.tc);
+    }
     for (int i = 0; i < 8; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     for (int i = 0; i < 4; ++i)
@@ -655,6 +682,7 @@ gbr_ctx *gbr_make_worker(gbr_ctx *parent) {
     w->tuned_evalres = parent->tuned_evalres;
     w->gemm_on = parent->gemm_on;
     w->reg_on = parent->reg_on;
+    w->tc_on = parent->tc_on;
     w->graph_on = 0;   // serving batches differ every time; graphs would only add capture cost
     w->extra_primes = parent->extra_primes;
     cudaSetDevice(w->device);
@@ -695,6 +723,7 @@ extern "C" int gbr_set_option(gbr_ctx *c, int opt, int64_t v) {
         case GBR_OPT_GRAPH: c->graph_on = (int)(v != 0); return GBR_OK;
         case GBR_OPT_INTERP_GEMM: c->gemm_on = (int)(v != 0); return GBR_OK;
         case GBR_OPT_REGISTER_FORM: c->reg_on = (int)(v != 0); return GBR_OK;
+        case GBR_OPT_INTERP_TC: c->tc_on = (int)(v != 0); return GBR_OK;
         case GBR_OPT_EXTRA_PRIMES:
             if (v < 0 || v > 64) return GBR_EINVAL;
             c->extra_primes = (int)v;
@@ -1082,6 +1111,7 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
         const uint32_t *vinv;
         size_t off;
         int npairs;
+        const uint16_t *vtc;
     };
     std::vector<Gemm> gemms;
     std::vector<int32_t> gemm_pairs;
@@ -1101,20 +1131,34 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
                 const uint32_t *ve = c->get_vinv(h + 1, K, VINV_EVEN);
                 const uint32_t *vo = no > 0 && ve ? c->get_vinv(h, K, VINV_ODD) : nullptr;
                 if (ve && (no == 0 || vo)) {
-                    gemms.push_back({h + 1, ne, GEMM_EVEN, K, ve, off, (int)qs.size()});
-                    if (no > 0) gemms.push_back({h, no, GEMM_ODD, K, vo, off, (int)qs.size()});
+                    gemms.push_back({h + 1, ne, GEMM_EVEN, K, ve, off, (int)qs.size(), nullptr});
+                    if (no > 0) gemms.push_back({h, no, GEMM_ODD, K, vo, off, (int)qs.size(), nullptr});
                     done = true;
                 }
             }
             if (!done) {
                 const uint32_t *vi = c->get_vinv(gP, K, gsym ? VINV_SYM : VINV_GRID);
                 if (vi) {
-                    gemms.push_back({gP, gP, GEMM_PLAIN, K, vi, off, (int)qs.size()});
+                    gemms.push_back({gP, gP, GEMM_PLAIN, K, vi, off, (int)qs.size(), nullptr});
                     done = true;
                 }
             }
         }
         if (done) gemm_pairs.insert(gemm_pairs.end(), qs.begin(), qs.end());
+        if (done && c->tc_on) {
+            // digit tiles for the tensor cores (each matrix of the group, or none)
+            const size_t g0 = gemms.size() - (gsym && gemms.back().mode == GEMM_ODD ? 2 : 1);
+            bool all = true;
+            for (size_t gi = g0; gi < gemms.size(); ++gi) {
+                const int vmode = gemms[gi].mode == GEMM_EVEN ? VINV_EVEN : gemms[gi].mode == GEMM_ODD ? VINV_ODD
+                                  : gsym                     ? VINV_SYM
+                                                             : VINV_GRID;
+                gemms[gi].vtc = c->get_vinv_tc(gemms[gi].n, K, vmode);
+                all = all && gemms[gi].vtc;
+            }
+            if (!all)
+                for (size_t gi = g0; gi < gemms.size(); ++gi) gemms[gi].vtc = nullptr;
+        }
         else
             for (int q : qs) interp.add(q, plan[q].k);
     }
@@ -1150,20 +1194,27 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
     // one contraction launch for all groups: group table and tile list (tiles of
     // one group and prime are adjacent so its V^-1 rows stay in L2)
     std::vector<GemmGroup> ggroups;
-    std::vector<GemmTile> gtiles;
+    std::vector<GemmTile> gtiles, ttiles;   // integer-pipe and tensor-core contraction tiles
     for (size_t gi = 0; gi < gemms.size(); ++gi) {
         const Gemm &gm = gemms[gi];
         GemmGroup gg;
         gg.vinv = gm.vinv;
+        gg.vtc = gm.vtc;
         gg.pairs_off = (int64_t)(o_gemm + gm.off * sizeof(int32_t));   // the block is (re)allocated later
         gg.n = gm.n;
         gg.rows = gm.rows;
         gg.npairs = gm.npairs;
         gg.mode = gm.mode;
         ggroups.push_back(gg);
-        for (int i = 0; i < gm.K; ++i)
-            for (int c0 = 0; c0 < gm.rows; c0 += kGemmTileM)
-                for (int q0 = 0; q0 < gm.npairs; q0 += kGemmTileN) gtiles.push_back({(int32_t)gi, c0, q0, i});
+        if (gm.vtc) {
+            for (int i = 0; i < gm.K; ++i)
+                for (int c0 = 0; c0 < gm.rows; c0 += kTcTileM)
+                    for (int q0 = 0; q0 < gm.npairs; q0 += kTcTileN) ttiles.push_back({(int32_t)gi, c0, q0, i});
+        } else {
+            for (int i = 0; i < gm.K; ++i)
+                for (int c0 = 0; c0 < gm.rows; c0 += kGemmTileM)
+                    for (int q0 = 0; q0 < gm.npairs; q0 += kGemmTileN) gtiles.push_back({(int32_t)gi, c0, q0, i});
+        }
     }
     size_t o_ggroups = (blk.size() + 15) / 16 * 16;
     blk.resize(o_ggroups + ggroups.size() * sizeof(GemmGroup) + 16);
@@ -1171,6 +1222,9 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
     size_t o_gtiles = (blk.size() + 15) / 16 * 16;
     blk.resize(o_gtiles + gtiles.size() * sizeof(GemmTile) + 16);
     if (!gtiles.empty()) std::memcpy(blk.data() + o_gtiles, gtiles.data(), gtiles.size() * sizeof(GemmTile));
+    size_t o_ttiles = (blk.size() + 15) / 16 * 16;
+    blk.resize(o_ttiles + ttiles.size() * sizeof(GemmTile) + 16);
+    if (!ttiles.empty()) std::memcpy(blk.data() + o_ttiles, ttiles.data(), ttiles.size() * sizeof(GemmTile));
     size_t o_pmap = (blk.size() + 7) / 8 * 8;
     blk.resize(o_pmap + pmap.size() * 4 + 4);
     if (!pmap.empty()) std::memcpy(blk.data() + o_pmap, pmap.data(), pmap.size() * 4);
@@ -1319,6 +1373,11 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
                                    (const GemmTile *)(r->d_planblk + o_gtiles), (int)gtiles.size(), q);
             kernels++;
         }
+        if (x == cudaSuccess && !ttiles.empty()) {
+            x = launch_interp_tc(L, r->d_planblk, (const GemmGroup *)(r->d_planblk + o_ggroups),
+                                 (const GemmTile *)(r->d_planblk + o_ttiles), (int)ttiles.size(), q);
+            kernels++;
+        }
         record(4, capturing, q);
         if (x == cudaSuccess && crtf.total > 0) {
             x = launch_crt_fast(L, mk(o_crtf_p, o_crtf_s, crtf), Kdig_f, Lmax_f, q);
@@ -1340,7 +1399,10 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
                                       (uintptr_t)r->d_redo,
                                       (uintptr_t)c->d_garner,  (uintptr_t)c->d_invk, (uintptr_t)c->d_err,
                                       (uintptr_t)c->d_mods,    (uintptr_t)c->stats_on};
-        for (const Gemm &gm : gemms) key.push_back((uintptr_t)gm.vinv);
+        for (const Gemm &gm : gemms) {
+            key.push_back((uintptr_t)gm.vinv);
+            key.push_back((uintptr_t)gm.vtc);
+        }
         const bool same = r->gkey == key && r->gblk.size() == blk.size() &&
                           std::memcmp(r->gblk.data(), blk.data(), blk.size()) == 0;
         if (!same) {

@@ -62,11 +62,12 @@ struct gbr_ctx {
     void *h_pin[4] = {nullptr, nullptr, nullptr, nullptr};
     size_t h_pin_cap[4] = {0, 0, 0, 0};
     cudaEvent_t ev[8] = {};
-    int drop_unlucky = 0, stats_on = 0, graph_on = 1, extra_primes = 0, gemm_on = 1, reg_on = 1;
+    int drop_unlucky = 0, stats_on = 0, graph_on = 1, extra_primes = 0, gemm_on = 1, reg_on = 1, tc_on = 1;
     gbr_stats stats{};
     std::map<uint64_t, cudaGraphExec_t> graphs;
     struct Vinv {
         uint32_t *d = nullptr;
+        uint16_t *tc = nullptr;   // bf16 digit tiles for the tensor-core path (built on first use)
         int K = 0;
         size_t bytes = 0;
         uint64_t last_use = 0;
@@ -74,6 +75,7 @@ struct gbr_ctx {
     std::map<int64_t, Vinv> vinv;  // inverse Vandermonde matrices, key 4 n + point-set mode
     uint64_t vinv_clock = 0, vinv_run_mark = 0;
     const uint32_t *get_vinv(int n, int K, int mode);   // nullptr if it cannot be built
+    const uint16_t *get_vinv_tc(int n, int K, int mode);   // digit tiles of a matrix get_vinv returned
     gbr::ServeState *serve = nullptr;
     std::map<int, int> tuned_evalres;   // degree bucket -> block size chosen by the autotuner
     cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs

@@ -283,6 +283,7 @@ GBR_HD int vinv_point(int mode, int j) {
 enum { GEMM_PLAIN = 0, GEMM_EVEN = 1, GEMM_ODD = 2 };
 struct GemmGroup {
     const uint32_t *vinv;   // [prime][n][n] inverse Vandermonde matrices
+    const uint16_t *vtc;    // the same matrices as bf16 digit tiles (tensor-core path), or null
     int64_t pairs_off;      // the group's pair ids: int32 entries at this byte offset of the plan block
     int32_t n;              // contraction length = matrix size
     int32_t rows;           // coefficients produced (<= n): PLAIN c -> c, EVEN c -> 2c, ODD c -> 2c + 1
@@ -292,6 +293,13 @@ struct GemmTile {
     int32_t group, c0, q0, prime;
 };
 constexpr int kGemmTileM = 64, kGemmTileN = 64;
+// tensor-core contraction (gbr_interp_tc.cu): tiles of 64 coefficients x 128 pairs
+constexpr int kTcTileM = 64, kTcTileN = 128, kTcMaxN = 256;
+size_t vinv_tc_bytes(int n, int rows, int K);
+cudaError_t launch_vinv_tc(const uint32_t *vinv, int n, int rows, int K, uint16_t *out, cudaStream_t s);
+cudaError_t launch_interp_tc(const ResLaunch &L, const char *planblk, const GemmGroup *groups, const GemmTile *tiles,
+                             int ntiles, cudaStream_t s);
+cudaError_t configure_interp_tc_kernel();
 cudaError_t launch_interp_gemm(const ResLaunch &L, const char *planblk, const GemmGroup *groups,
                                const GemmTile *tiles, int ntiles, cudaStream_t s);
 cudaError_t launch_zero_init(const ResLaunch &L, cudaStream_t s);

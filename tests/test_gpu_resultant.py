@@ -218,6 +218,38 @@ def test_interpolation_contraction_matches_newton(ctx):
         assert r == list(O.res_bareiss(f, g))
 
 
+def test_tensor_core_contraction_matches_integer_pipes(ctx):
+    """The interpolation contractions of up to 256 points run on the tensor cores
+    (bf16 digits, exact fp32 sums); larger ones on the integer pipes.  Point counts
+    odd and even (a symmetric set one point larger), 150 pairs sharing one count
+    (two pair tiles), and a count above the tensor-core limit in the same batch:
+    the results equal those of the integer-pipe contraction and the oracle."""
+    from paper_1103_4697_gb300.native import OPT_INTERP_TC
+
+    fs, gs = [], []
+    for i in range(150):                              # P = 17: two tiles of 128 pairs
+        f, g = W.small_dense_pair(900 + i, 4, 12)
+        fs.append(f)
+        gs.append(g)
+    for d, bits in ((3, 30), (7, 20), (10, 16), (15, 8), (16, 8), (23, 6)):   # P = 10, 50, 101, 226, 257, 530
+        f, g = W.small_dense_pair(950 + d, d, bits)
+        fs.append(f)
+        gs.append(g)
+    got = ctx.resultant_batch(fs, gs)
+    ctx.set_option(OPT_INTERP_TC, 0)
+    try:
+        ref = ctx.resultant_batch(fs, gs)
+    finally:
+        ctx.set_option(OPT_INTERP_TC, 1)
+    assert got == ref
+    for q in (0, 77, 149, 150, 151):
+        assert got[q] == list(O.res_bareiss(fs[q], gs[q]))
+    rng = random.Random(11)
+    for q in range(152, len(fs)):
+        for a in (rng.randint(-10 ** 6, 10 ** 6), rng.randint(-10 ** 6, 10 ** 6)):
+            assert _poly_eval(got[q], a) == O.res_at_prs(fs[q], gs[q], a)
+
+
 def _bimul(a, b):
     """Product of two bivariate polynomials given as rows (row j = x-coefficients of y^j)."""
     nx = len(a[0]) + len(b[0]) - 1
