@@ -1645,6 +1645,23 @@ void host_rows(const gbr_bipoly *p, int var, std::vector<int> &deg, std::vector<
             }
         }
         nrm[r] = lse2(a);
+        if (d.words == 1 && deg[r] >= 0) {
+            // the autocorrelation bound of the device planner (k_bounds): |f_r(x)|^2 <= A_0 + 2 sum |A_k|
+            const int L = deg[r] + 1;
+            const double gam = 2.0 * (L + 1) * 0x1p-53;
+            double G = 0.0;
+            for (int k = 0; k < L; ++k) {
+                double sk = 0.0, tk = 0.0;
+                for (int a2 = 0; a2 + k < L; ++a2) {
+                    const double x = (double)(int64_t)w[(int64_t)r * d.rstride + (int64_t)a2 * d.cstride];
+                    const double y = (double)(int64_t)w[(int64_t)r * d.rstride + (int64_t)(a2 + k) * d.cstride];
+                    sk = std::fma(x, y, sk);
+                    tk = std::fma(std::fabs(x), std::fabs(y), tk);
+                }
+                G += (k ? 2.0 : 1.0) * (std::fabs(sk) + gam * tk);
+            }
+            nrm[r] = 0.5 * std::log2(G * (1.0 + 0x1p-40)) + 1e-12;
+        }
     }
 }
 }  // namespace

@@ -87,30 +87,58 @@ __device__ __forceinline__ const uint64_t *coef_ptr(const uint64_t *coef, const 
 // any lambda gives a valid bound).
 constexpr int kBoundsWarps = 4;
 
-// 1-norm of a row.  int64 coefficients: the exact 128-bit sum, returned as a
-// double (the caller takes log2 of it later, one row per lane, +1e-12 for the
-// rounding of the conversion and of log2); wider coefficients: log2 of the norm
-// by a log-sum-exp over the coefficients' log2 magnitudes.
-__device__ double row_norm(const uint64_t *coef, const PolyDesc &P, int r, int lane, int &cmax) {
+// Row quantity of the Hadamard bound.  For a row f_r(x) = sum_a c_a x^a with
+// int64 coefficients: G = A_0 + 2 sum_{k>0} |A_k|, A_k = sum_a c_a c_{a+k} (the
+// autocorrelation), which bounds |f_r(x)|^2 on |x| = 1 because
+// |f_r(x)|^2 = A_0 + 2 sum_k A_k cos(k theta); it never exceeds the squared
+// 1-norm and is far smaller when the signs cancel.  The row is staged in
+// shared memory; with every |c| < 2^27 each A_k is summed exactly in int64
+// (products below 2^54, at most 128 of them), otherwise in double with the
+// error term gamma sum |c_a c_{a+k}|, gamma = 2 (L+1) 2^-53 (covering the
+// conversions, products and the sum of L terms), so G is an upper bound; it is
+// returned linear (the caller takes half its log2 later, one row per lane).  Wider coefficients: log2 of the 1-norm by a log-sum-exp over the
+// coefficients' log2 magnitudes.
+constexpr int kRowBuf = 128;   // coefficients of one row staged per warp
+__device__ double row_norm(const uint64_t *coef, const PolyDesc &P, int r, int lane, int &cmax, int64_t *rb) {
     cmax = -1;
     if (P.words == 1) {
-        uint64_t lo = 0, hi = 0;
+        uint64_t big = 0;   // OR of the |c|
         for (int c = lane; c <= P.cols; c += 32) {
-            int64_t v = (int64_t)coef_ptr(coef, P, r, c)[0];
-            if (v) {
-                cmax = c;
-                uint64_t a = v < 0 ? 0ull - (uint64_t)v : (uint64_t)v;
-                lo += a;
-                hi += lo < a;
-            }
+            const int64_t v = (int64_t)coef_ptr(coef, P, r, c)[0];
+            if (c < kRowBuf) rb[c] = v;
+            if (v) cmax = c;
+            big |= v < 0 ? 0ull - (uint64_t)v : (uint64_t)v;
         }
         for (int o = 16; o; o >>= 1) {
-            uint64_t olo = __shfl_xor_sync(0xffffffffu, lo, o), ohi = __shfl_xor_sync(0xffffffffu, hi, o);
-            lo += olo;
-            hi += ohi + (lo < olo);
             cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+            big |= __shfl_xor_sync(0xffffffffu, big, o);
         }
-        return (double)hi * 0x1p64 + (double)lo;
+        __syncwarp();
+        if (cmax < 0) return 0.0;
+        const int L = cmax + 1;
+        double G = 0.0;
+        if (L <= kRowBuf && big < (1ull << 27)) {
+            for (int k = lane; k < L; k += 32) {
+                int64_t sk = 0;
+                for (int a = 0; a + k < L; ++a) sk += rb[a] * rb[a + k];
+                G += (k ? 2.0 : 1.0) * (double)(sk < 0 ? -sk : sk);
+            }
+        } else {
+            const double gam = 2.0 * (L + 1) * 0x1p-53;
+            for (int k = lane; k < L; k += 32) {
+                double sk = 0.0, tk = 0.0;
+                for (int a = 0; a + k < L; ++a) {
+                    const double x = (double)(L <= kRowBuf ? rb[a] : (int64_t)coef_ptr(coef, P, r, a)[0]);
+                    const double y = (double)(L <= kRowBuf ? rb[a + k] : (int64_t)coef_ptr(coef, P, r, a + k)[0]);
+                    sk = fma(x, y, sk);
+                    tk = fma(fabs(x), fabs(y), tk);
+                }
+                G += (k ? 2.0 : 1.0) * (fabs(sk) + gam * tk);
+            }
+        }
+        for (int o = 16; o; o >>= 1) G += __shfl_xor_sync(0xffffffffu, G, o);
+        __syncwarp();
+        return G * (1.0 + 0x1p-40);   // the double sums of at most 160 non-negative terms
     }
     Lse nrm;
     nrm.init();
@@ -180,6 +208,7 @@ __global__ void __launch_bounds__(kBoundsWarps * 32) k_bounds(ResLaunch L) {
     __shared__ double lnf[kBoundsWarps][GBR_MAX_YDEG + 2], lng[kBoundsWarps][GBR_MAX_YDEG + 2];
     __shared__ double ebuf[kBoundsWarps][2][GBR_MAX_YDEG + 2];
     __shared__ float fbuf[kBoundsWarps][2][GBR_MAX_YDEG + 2];
+    __shared__ int64_t rbuf[kBoundsWarps][kRowBuf];
     const int wib = threadIdx.x >> 5;
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
@@ -193,12 +222,12 @@ __global__ void __launch_bounds__(kBoundsWarps * 32) k_bounds(ResLaunch L) {
         if (which == 1 && D.disc) break;
         const PolyDesc &P = which ? D.g : D.f;
         double *ln_out = which ? lng[wib] : lnf[wib];
-        const bool linear = P.words == 1;   // row_norm returns the norm itself
+        const bool linear = P.words == 1;   // row_norm returns G (the squared row quantity) itself
         int mdeg = -1, dxmax = -1, td = -1, terms = 0, terms_upto = 0, lcd = -1;
         int mdeg_g = -1, dx_g = -1, td_g = -1, terms_g = 0, terms_g_upto = 0, lcd_g = -1;
         for (int r = 0; r <= P.rows; ++r) {
             int cmax;
-            const double ln = row_norm(L.coef, P, r, lane, cmax);
+            const double ln = row_norm(L.coef, P, r, lane, cmax, rbuf[wib]);
             if (lane == 0) {
                 L.rowdeg[P.rowdeg_off + r] = cmax;
                 if (r <= GBR_MAX_YDEG) ln_out[r] = ln;
@@ -215,7 +244,7 @@ __global__ void __launch_bounds__(kBoundsWarps * 32) k_bounds(ResLaunch L) {
                 if (lane == 0) {
                     L.rowdeg[D.g.rowdeg_off + r - 1] = cmax;
                     if (r - 1 <= GBR_MAX_YDEG)
-                        lng[wib][r - 1] = linear ? ln * r : (ln == -INFINITY ? ln : ln + log2((double)r));
+                        lng[wib][r - 1] = linear ? ln * ((double)r * r) : (ln == -INFINITY ? ln : ln + log2((double)r));
                 }
                 terms_g += cmax + 1;
                 if (cmax >= 0) {
@@ -227,14 +256,14 @@ __global__ void __launch_bounds__(kBoundsWarps * 32) k_bounds(ResLaunch L) {
                 }
             }
         }
-        // log2 of the norms, one row per lane
+        // half the log2 of the row quantities, one row per lane
         __syncwarp();
         if (linear) {
             const int nr = min(P.rows, GBR_MAX_YDEG + 1);
             for (int r = lane; r <= nr; r += 32) {
-                if (r <= GBR_MAX_YDEG) ln_out[r] = ln_out[r] > 0.0 ? log2(ln_out[r]) + 1e-12 : -INFINITY;
+                if (r <= GBR_MAX_YDEG) ln_out[r] = ln_out[r] > 0.0 ? 0.5 * log2(ln_out[r]) + 1e-12 : -INFINITY;
                 if (which == 0 && D.disc && r >= 1)
-                    lng[wib][r - 1] = lng[wib][r - 1] > 0.0 ? log2(lng[wib][r - 1]) + 1e-12 : -INFINITY;
+                    lng[wib][r - 1] = lng[wib][r - 1] > 0.0 ? 0.5 * log2(lng[wib][r - 1]) + 1e-12 : -INFINITY;
             }
         }
         __syncwarp();
