@@ -160,6 +160,9 @@ const char *gbr_last_error(gbr_ctx *ctx);
 #define GBR_OPT_INTERP_TC    7   /* 1 (default): the inverse-Vandermonde contractions of up to 256
                                     points run on the tensor cores (bf16 digits, exact fp32 sums);
                                     0: on the integer pipes */
+#define GBR_OPT_PIPELINE     8   /* 1 (default): one-shot batches of at least 2048 pairs run in
+                                    chunks of 1024 on two internal streams, so that copies and
+                                    host work overlap the kernels; 0: one piece */
 #define GBR_OPT_REGISTER_FORM 6  /* 1 (default): pairs of shape (N, N), (N, N-1) or (N-1, N) in the
                                     eliminated variable, 2 <= N <= 32, are solved with the
                                     polynomials in registers (warps that meet a vanishing leading

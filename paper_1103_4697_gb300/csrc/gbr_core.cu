@@ -655,6 +655,7 @@ extern "C" int gbr_create(gbr_ctx **out, int device, size_t budget, void *worksp
 extern "C" void gbr_destroy(gbr_ctx *c) {
     if (!c) return;
     gbr_serve_shutdown(c);
+    for (int w = 0; w < 2; ++w) gbr_destroy_worker(c->pipe[w]);
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
@@ -706,6 +707,10 @@ void gbr_destroy_worker(gbr_ctx *w) {
     if (!w) return;
     cudaSetDevice(w->device);
     if (w->stream) cudaStreamSynchronize(w->stream);
+    for (auto &kv : w->vinv) {
+        w->dfree(kv.second.d);
+        w->dfree(kv.second.tc);
+    }
     for (void *p : {(void *)w->d_mods, (void *)w->d_err, (void *)w->d_garner, (void *)w->d_invk}) w->dfree(p);
     for (int i = 0; i < 8; ++i)
         if (w->ev[i]) cudaEventDestroy(w->ev[i]);
@@ -724,6 +729,7 @@ extern "C" int gbr_set_option(gbr_ctx *c, int opt, int64_t v) {
         case GBR_OPT_INTERP_GEMM: c->gemm_on = (int)(v != 0); return GBR_OK;
         case GBR_OPT_REGISTER_FORM: c->reg_on = (int)(v != 0); return GBR_OK;
         case GBR_OPT_INTERP_TC: c->tc_on = (int)(v != 0); return GBR_OK;
+        case GBR_OPT_PIPELINE: c->pipe_on = (int)(v != 0); return GBR_OK;
         case GBR_OPT_EXTRA_PRIMES:
             if (v < 0 || v > 64) return GBR_EINVAL;
             c->extra_primes = (int)v;
@@ -932,7 +938,7 @@ static void put_list(std::vector<char> &blk, const HostList &h, size_t &off_pair
     if (n) std::memcpy(blk.data() + off_pairs, h.pairs.data(), n * 4);
 }
 
-int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
+int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     const int n = r->n;
     cudaStream_t s = c->stream;
     cudaError_t e;
@@ -1448,26 +1454,39 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
         e = enqueue(false, s);
     }
     if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "stage launch", e);
-    int32_t herr[4] = {0, 0, 0, 0};
-    std::vector<unsigned long long> hredo(evr.size());
-    e = cudaMemcpyAsync(herr, c->d_err, 16, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && !evr.empty())
-        e = cudaMemcpyAsync(hredo.data(), r->d_redo, 8 * evr.size(), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "resultant stages", e);
-    if (herr[0]) return c->fail(GBR_EDEVICE, "device-side consistency check failed");
-    st.dropped_points = (int64_t)((uint64_t)(uint32_t)herr[2] | ((uint64_t)(uint32_t)herr[3] << 32));
     st.dropped_primes = dropped_primes;
-    st.redo_warps = 0;
-    for (unsigned long long v : hredo) st.redo_warps += (int64_t)v;
-    r->out_words = out_w;
-    r->sign_bytes = sign_b;
-    r->ran = true;
     st.kernels = kernels;
     st.graph_replayed = replayed ? 1 : 0;
     st.subproblems = subproblems;
     st.h2d_bytes = (int64_t)blk.size();
     st.d2h_bytes = (int64_t)sizeof(PairBound) * n + 4;
+    r->pend_st = st;
+    r->pend_nredo = (int)evr.size();
+    r->pend_out_w = out_w;
+    r->pend_sign_b = sign_b;
+    r->pending = true;
+    return GBR_OK;
+}
+
+int gbr_run_resident_finish(gbr_ctx *c, gbr_resident *r) {
+    if (!r->pending) return GBR_OK;
+    r->pending = false;
+    cudaStream_t s = c->stream;
+    gbr_stats st = r->pend_st;
+    int32_t herr[4] = {0, 0, 0, 0};
+    std::vector<unsigned long long> hredo(r->pend_nredo);
+    cudaError_t e = cudaMemcpyAsync(herr, c->d_err, 16, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && r->pend_nredo)
+        e = cudaMemcpyAsync(hredo.data(), r->d_redo, 8 * (size_t)r->pend_nredo, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "resultant stages", e);
+    if (herr[0]) return c->fail(GBR_EDEVICE, "device-side consistency check failed");
+    st.dropped_points = (int64_t)((uint64_t)(uint32_t)herr[2] | ((uint64_t)(uint32_t)herr[3] << 32));
+    st.redo_warps = 0;
+    for (unsigned long long v : hredo) st.redo_warps += (int64_t)v;
+    r->out_words = r->pend_out_w;
+    r->sign_bytes = r->pend_sign_b;
+    r->ran = true;
     if (c->stats_on) {
         float ms;
         cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]); st.bounds_ms = ms;
@@ -1479,6 +1498,15 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
     }
     c->stats = st;
     return GBR_OK;
+}
+
+int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
+    int st = gbr_run_resident_launch(c, r);
+    if (st) {
+        r->pending = false;
+        return st;
+    }
+    return gbr_run_resident_finish(c, r);
 }
 
 extern "C" int gbr_run_resident(gbr_ctx *c, gbr_resident *r) {
@@ -1548,6 +1576,101 @@ extern "C" int gbr_fetch_resident(gbr_ctx *c, gbr_resident *r, int first, int co
 
 // ------------------------------------------------------------------ one-shot and batch wrappers
 
+// Large one-shot batches run in chunks on two private worker contexts (own
+// stream and error word, the parent's arena): while one chunk's stages run on
+// the GPU, the other chunk is fetched, the next one uploaded and planned, so
+// host<->device copies and host work overlap the kernels.  Results are the
+// same as one resident batch (each pair is independent).
+constexpr int kPipeChunk = 1024, kPipeMinPairs = 2 * kPipeChunk;
+
+static int res_batch_pipelined(gbr_ctx *c, int n, const gbr_bipoly *f, const gbr_bipoly *g, int var, int disc,
+                               gbr_bigpoly *out) {
+    for (int w = 0; w < 2; ++w) {
+        if (!c->pipe[w]) c->pipe[w] = gbr_make_worker(c);
+        if (!c->pipe[w]) return -1;   // no worker: the caller runs the batch in one piece
+        gbr_ctx *x = c->pipe[w];
+        x->drop_unlucky = c->drop_unlucky;
+        x->gemm_on = c->gemm_on;
+        x->reg_on = c->reg_on;
+        x->tc_on = c->tc_on;
+        x->extra_primes = c->extra_primes;
+        x->stats_on = 0;
+        for (auto &kv : c->tuned_evalres) x->tuned_evalres.insert(kv);
+    }
+    const int nc = (n + kPipeChunk - 1) / kPipeChunk;
+    gbr_resident *rs[2] = {nullptr, nullptr};
+    int lo_of[2] = {0, 0}, cnt_of[2] = {0, 0};
+    gbr_stats total{};
+    int st = GBR_OK;
+    const char *where = nullptr;
+    auto start = [&](int ci) -> int {
+        gbr_ctx *w = c->pipe[ci & 1];
+        const int lo = ci * kPipeChunk, cnt = std::min(kPipeChunk, n - lo);
+        gbr_resident *r = nullptr;
+        int x = gbr_upload_pairs(w, cnt, f + lo, disc ? nullptr : g + lo, var, disc, &r);
+        if (x) return x;
+        r->oneshot = true;
+        rs[ci & 1] = r;
+        lo_of[ci & 1] = lo;
+        cnt_of[ci & 1] = cnt;
+        std::lock_guard<std::mutex> lk(w->mu);
+        return gbr_run_resident_launch(w, r);
+    };
+    auto complete = [&](int ci) -> int {
+        gbr_ctx *w = c->pipe[ci & 1];
+        gbr_resident *r = rs[ci & 1];
+        if (!r) return GBR_OK;
+        std::lock_guard<std::mutex> lk(w->mu);
+        int x = gbr_run_resident_finish(w, r);
+        if (!x) x = gbr_fetch_resident_locked(w, r, 0, cnt_of[ci & 1], out + lo_of[ci & 1]);
+        cudaStreamSynchronize(w->stream);
+        if (!x) {
+            total.kernels += w->stats.kernels;
+            total.subproblems += w->stats.subproblems;
+            total.modmul += w->stats.modmul;
+            total.modmul_evalres += w->stats.modmul_evalres;
+            total.h2d_bytes += w->stats.h2d_bytes + r->upload_bytes;
+            total.d2h_bytes += w->stats.d2h_bytes;
+            total.dropped_points += w->stats.dropped_points;
+            total.dropped_primes += w->stats.dropped_primes;
+            total.redo_warps += w->stats.redo_warps;
+        }
+        gbr_free_resident_locked(w, r);
+        rs[ci & 1] = nullptr;
+        return x;
+    };
+    try {
+        st = start(0);
+        if (!st && nc > 1) st = start(1);
+        for (int ci = 0; ci < nc && !st; ++ci) {
+            st = complete(ci);
+            if (!st && ci + 2 < nc) st = start(ci + 2);
+        }
+    } catch (std::bad_alloc &) {
+        st = GBR_ENOMEM;
+        where = "host allocation";
+    }
+    for (int w = 0; w < 2; ++w)
+        if (rs[w]) {
+            std::lock_guard<std::mutex> lk(c->pipe[w]->mu);
+            cudaStreamSynchronize(c->pipe[w]->stream);
+            rs[w]->pending = false;
+            gbr_free_resident_locked(c->pipe[w], rs[w]);
+            rs[w] = nullptr;
+        }
+    if (st) {
+        for (int i = 0; i < n; ++i) gbr_free_result(c, &out[i]);
+        std::string msg = where ? where : "";
+        for (int w = 0; w < 2 && msg.empty(); ++w) {
+            std::lock_guard<std::mutex> g2(c->pipe[w]->err_mu);
+            msg = c->pipe[w]->err;
+        }
+        return c->fail(st, msg.empty() ? "pipelined batch" : msg.c_str());
+    }
+    c->stats = total;
+    return GBR_OK;
+}
+
 static int res_batch_impl(gbr_ctx *c, int n, const gbr_bipoly *f, const gbr_bipoly *g, int var, int disc,
                           gbr_bigpoly *out) {
     if (!c || n < 0 || (n && !out)) return GBR_EINVAL;
@@ -1556,6 +1679,12 @@ static int res_batch_impl(gbr_ctx *c, int n, const gbr_bipoly *f, const gbr_bipo
         out[i].limbs = 0;
         out[i].mag = nullptr;
         out[i].sign = nullptr;
+    }
+    if (n >= kPipeMinPairs && c->pipe_on && !c->parent) {
+        std::lock_guard<std::mutex> lk(c->mu);
+        cudaSetDevice(c->device);
+        const int st = res_batch_pipelined(c, n, f, g, var, disc, out);
+        if (st >= 0) return st;
     }
     gbr_resident *r = nullptr;
     int st = gbr_upload_pairs(c, n, f, g, var, disc, &r);

@@ -77,6 +77,8 @@ struct gbr_ctx {
     const uint32_t *get_vinv(int n, int K, int mode);   // nullptr if it cannot be built
     const uint16_t *get_vinv_tc(int n, int K, int mode);   // digit tiles of a matrix get_vinv returned
     gbr::ServeState *serve = nullptr;
+    gbr_ctx *pipe[2] = {nullptr, nullptr};   // private workers that pipeline large one-shot batches
+    int pipe_on = 1;
     std::map<int, int> tuned_evalres;   // degree bucket -> block size chosen by the autotuner
     cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
     cudaError_t capture_stream_ready();
@@ -123,10 +125,17 @@ struct gbr_resident {
     int64_t graph_kernels = 0;
     std::vector<uintptr_t> gkey;        // pointers and launch shapes of the captured plan
     std::vector<char> gblk;             // plan block of the captured plan
+    // launched but not yet finished (gbr_run_resident_launch / _finish)
+    bool pending = false;
+    gbr_stats pend_st{};
+    int pend_nredo = 0;
+    int64_t pend_out_w = 0, pend_sign_b = 0;
 };
 
 // internal entry points (context lock held by the caller)
 int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r);
+int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r);   // bounds, plan, stages enqueued
+int gbr_run_resident_finish(gbr_ctx *c, gbr_resident *r);   // wait, check, statistics
 int gbr_fetch_resident_locked(gbr_ctx *c, gbr_resident *r, int first, int count, gbr_bigpoly *out);
 void gbr_free_resident_locked(gbr_ctx *c, gbr_resident *r);
 void gbr_serve_shutdown(gbr_ctx *c);

@@ -12,8 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libgbres.so")
 
 OK, EINVAL, ENOMEM, EDEVICE, ETIMEOUT, EAGAIN, EVERIFY, ELIMIT, ECANCELED, ENOTFOUND = range(10)
-OPT_DROP_UNLUCKY, OPT_STATS, OPT_GRAPH, OPT_EXTRA_PRIMES, OPT_INTERP_GEMM, OPT_REGISTER_FORM, OPT_INTERP_TC = (
-    1, 2, 3, 4, 5, 6, 7)
+OPT_DROP_UNLUCKY, OPT_STATS, OPT_GRAPH, OPT_EXTRA_PRIMES, OPT_INTERP_GEMM, OPT_REGISTER_FORM, OPT_INTERP_TC, \
+    OPT_PIPELINE = (1, 2, 3, 4, 5, 6, 7, 8)
 JOB_RESULTANT, JOB_DISC, JOB_GCD = 0, 1, 2
 
 

@@ -250,6 +250,31 @@ def test_tensor_core_contraction_matches_integer_pipes(ctx):
             assert _poly_eval(got[q], a) == O.res_at_prs(fs[q], gs[q], a)
 
 
+def test_pipelined_batch_matches_one_piece(ctx):
+    """A one-shot batch of 2048 pairs or more runs in chunks of 1024 on two internal
+    streams (copies and host work overlap the kernels); the results equal those of
+    the same batch run in one piece, for resultants and for res(f, f_y)."""
+    from paper_1103_4697_gb300.native import OPT_PIPELINE
+
+    fs, gs = [], []
+    for i in range(2600):
+        f, g = W.small_dense_pair(3000 + i, 3 + i % 3, 10 + i % 7)
+        fs.append(f)
+        gs.append(g)
+    got = ctx.resultant_batch(fs, gs)
+    got_d = ctx.discriminant_res_batch(fs)
+    ctx.set_option(OPT_PIPELINE, 0)
+    try:
+        ref = ctx.resultant_batch(fs, gs)
+        ref_d = ctx.discriminant_res_batch(fs)
+    finally:
+        ctx.set_option(OPT_PIPELINE, 1)
+    assert got == ref and got_d == ref_d
+    for q in (0, 1023, 1024, 2047, 2048, 2599):
+        assert got[q] == list(O.res_subres(fs[q], gs[q]))
+    assert got_d[2599] == list(O.disc_res(fs[2599]))
+
+
 def _bimul(a, b):
     """Product of two bivariate polynomials given as rows (row j = x-coefficients of y^j)."""
     nx = len(a[0]) + len(b[0]) - 1
