@@ -434,7 +434,8 @@ def run_config(args) -> None:
             and 4096 gcd jobs (degrees 30..200, planted degree-5 factor);
     conic   product of 8 conics (+ sparse terms) against a dense degree-24 curve with
             64-bit coefficients: res_y(f, g) and res_y(f, f_y), one call each;
-    serve   Poisson streams of mixed requests at 0.5, 0.8 and 0.95 of the measured capacity."""
+    serve   Poisson streams of mixed requests at 0.5, 0.8 and 0.95 of the measured capacity;
+    gcd     the 4096 gcd jobs alone, through the C ABI with packed host buffers."""
     import torch
 
     import oracle as O
@@ -487,9 +488,27 @@ def run_config(args) -> None:
         out["res_solves_per_s"] = PAIRS / sec
         out["res_stages_ms"] = {k: st0[k] for k in ("bounds_ms", "reduce_ms", "evalres_ms", "interp_ms", "crt_ms")}
         P, Q, H = W.gcd_batch(3, PAIRS)
-        ctx.gcd_batch(P, Q)
+        got = ctx.gcd_batch(P, Q)
         gsec = _time_calls(lambda: ctx.gcd_batch(P, Q), 3)
-        out["gcd_jobs_per_s"] = PAIRS / gsec
+        out["gcd_jobs_per_s_python_lists"] = PAIRS / gsec
+        # through the C ABI with packed host buffers (what a native caller pays):
+        # copies, kernels and the certificate; freeing the results is not timed
+        keep = api._Packed()
+        dp, dq = api.pack_upolys(P, keep), api.pack_upolys(Q, keep)
+        L = N.lib()
+        gouts = (N.BigPoly * PAIRS)()
+        t_gcd = 0.0
+        for _ in range(5):
+            t0 = time.perf_counter()
+            N.check(L.gbr_gcd_batch(ctx.handle, PAIRS, api._ptr(dp), api._ptr(dq), gouts), ctx.handle)
+            t_gcd += time.perf_counter() - t0
+            gst = ctx.stats()
+            for i in range(PAIRS):
+                L.gbr_free_result(ctx.handle, C.byref(gouts[i]))
+        out["gcd_jobs_per_s"] = 5 * PAIRS / t_gcd
+        out["gcd_stats"] = {k: gst[k] for k in ("gcd_ms", "total_ms", "kernels", "subproblems", "h2d_bytes",
+                                                "d2h_bytes")}
+        assert all(len(got[i]) - 1 >= 5 for i in range(0, PAIRS, 97))   # the planted degree-5 factor divides
         t = time.perf_counter()
         for i in range(4):
             O.res_evalz(ps.f[i], ps.g[i])
@@ -499,6 +518,27 @@ def run_config(args) -> None:
             O.gcd_z(P[i], Q[i])
         out["oracle_gcd_jobs_per_s_1core"] = 4 / (time.perf_counter() - t)
         out["workload"] = "4096 pairs deg_x, deg_y ~ U{4..16}, 8..32-bit, 25% planted (seed 3); 4096 gcds deg 30..200"
+    elif args.config == "gcd":
+        # the gcd batch alone, through the C ABI with packed host buffers
+        P, Q, H = W.gcd_batch(3, PAIRS)
+        keep = api._Packed()
+        dp, dq = api.pack_upolys(P, keep), api.pack_upolys(Q, keep)
+        ctx.set_option(N.OPT_STATS, 1)
+        L = N.lib()
+        gouts = (N.BigPoly * PAIRS)()
+        times = []
+        for it in range(6):
+            t0 = time.perf_counter()
+            N.check(L.gbr_gcd_batch(ctx.handle, PAIRS, api._ptr(dp), api._ptr(dq), gouts), ctx.handle)
+            times.append(time.perf_counter() - t0)
+            gst = ctx.stats()
+            for i in range(PAIRS):
+                L.gbr_free_result(ctx.handle, C.byref(gouts[i]))
+        sec = statistics.median(times[1:])
+        out["gcd_jobs_per_s"] = PAIRS / sec
+        out["gcd_stats"] = {k: gst[k] for k in ("gcd_ms", "total_ms", "kernels", "subproblems", "h2d_bytes",
+                                                "d2h_bytes")}
+        out["workload"] = "4096 gcds deg 30..200, planted degree-5 factor, 8..32-bit cofactors (seed 3)"
     elif args.config == "serve":
         res_all = {}
         cap = None
@@ -522,7 +562,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mem-gb", type=int, default=24)
     ap.add_argument("--pairs", type=int, default=PAIRS, help="pairs per GPU (smaller only for profiling)")
-    ap.add_argument("--config", choices=["headline", "small", "deg20", "mixed", "conic", "serve"],
+    ap.add_argument("--config", choices=["headline", "small", "deg20", "mixed", "conic", "serve", "gcd"],
                     default="headline", help="other workloads print their own JSON line")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--no-serve", action="store_true")

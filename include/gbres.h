@@ -108,7 +108,11 @@ typedef struct {
  * and T non-zero-capable x-coefficients (sum over rows of row degree + 1):
  * evaluation T, elimination 2 m n; per (pair, prime) with P points:
  * interpolation P (P - 1); per output coefficient with k primes: Garner
- * k (k - 1) / 2.  Bytes are the host<->device copies of the call. */
+ * k (k - 1) / 2.  Bytes are the host<->device copies of the call.  A gcd call
+ * (gbr_gcd, gbr_gcd_batch) records gcd_ms (CUDA events around the whole call on
+ * the context's stream, including the host work between its stages), total_ms
+ * (host wall time), kernels, subproblems ((job, prime) pairs of the modular
+ * gcds) and the bytes copied. */
 typedef struct {
     double bounds_ms, reduce_ms, evalres_ms, interp_ms, crt_ms, gcd_ms, total_ms;
     int64_t kernels;          /* kernels launched */

@@ -95,6 +95,24 @@ def pack_bipolys(polys, keep: _Packed):
 
 def pack_upolys(polys, keep: _Packed):
     desc = np.zeros(len(polys), dtype=_UPOLY_DT)
+    # int64 coefficients: one contiguous buffer, filled by numpy
+    try:
+        lens = np.array([max(len(p), 1) for p in polys], dtype=np.int64)
+        offs = np.zeros(len(polys), dtype=np.int64)
+        if len(polys):
+            offs[1:] = np.cumsum(lens)[:-1]
+        flat = np.zeros(int(lens.sum()) if len(polys) else 1, dtype=np.int64)
+        for p, o in zip(polys, offs):
+            if len(p):
+                flat[o:o + len(p)] = p
+        keep.bufs.append(flat)
+        desc["deg"] = lens - 1
+        desc["words"] = 1
+        desc["coef"] = flat.ctypes.data + 8 * offs
+        keep.bufs.append(desc)
+        return desc
+    except OverflowError:
+        pass
     for k, p in enumerate(polys):
         vals = [int(c) for c in p] or [0]
         W = _words_for(vals)

@@ -28,6 +28,8 @@
 #include <cstring>
 #include <vector>
 
+#include <chrono>
+
 #include "gbr_core.h"
 
 namespace gbr {
@@ -475,9 +477,18 @@ void set_big_int(gbr_bigpoly &b, const std::vector<std::pair<uint64_t, int>> &co
 
 }  // namespace
 
+// copies of the gcd path, counted for gbr_stats
+static cudaError_t gcd_copy(gbr_ctx *c, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind,
+                            cudaStream_t s) {
+    if (kind == cudaMemcpyHostToDevice) c->gcd_h2d += (int64_t)bytes;
+    else c->gcd_d2h += (int64_t)bytes;
+    return cudaMemcpyAsync(dst, src, bytes, kind, s);
+}
+
 static int gcd_batch_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upoly *q, gbr_bigpoly *out) {
     cudaStream_t s = c->stream;
     cudaError_t e;
+    c->gcd_kernels = c->gcd_subproblems = c->gcd_h2d = c->gcd_d2h = 0;
     // ---- validate and pack
     std::vector<int64_t> in_off(n);
     std::vector<int32_t> in_deg(2 * (size_t)n);
@@ -517,9 +528,9 @@ static int gcd_batch_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upo
     int32_t *d_deg = (int32_t *)bufs.get((size_t)n * 8);
     GcdInfo *d_info = (GcdInfo *)bufs.get(sizeof(GcdInfo) * n);
     if (!d_in || !d_off || !d_deg || !d_info) return c->fail(GBR_ENOMEM, "device budget too small for the gcd batch");
-    e = cudaMemcpyAsync(d_in, hin, (size_t)words * 8, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, in_off.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_deg, in_deg.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s);
+    e = gcd_copy(c, d_in, hin, (size_t)words * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = gcd_copy(c, d_off, in_off.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = gcd_copy(c, d_deg, in_deg.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s);
     GcdLaunch L{};
     L.in = d_in;
     L.in_off = d_off;
@@ -531,10 +542,11 @@ static int gcd_batch_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upo
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, 4, s);
     if (e == cudaSuccess) {
         k_gcd_prep<<<(n * 32 + 127) / 128, 128, 0, s>>>(L);
+        c->gcd_kernels++;
         e = cudaGetLastError();
     }
     std::vector<GcdInfo> info(n);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(info.data(), d_info, sizeof(GcdInfo) * n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = gcd_copy(c, info.data(), d_info, sizeof(GcdInfo) * n, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "gcd prep", e);
     // ---- trivial jobs on the host (zero inputs, constants)
@@ -632,10 +644,10 @@ static int gcd_batch_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upo
         int32_t *d_wlj = (int32_t *)ab.get(wl_jobs.size() * 4);
         if (!d_plan || !d_slotlist || !d_sdeg || !d_slots || !d_wls || !d_wlj)
             return c->fail(GBR_ENOMEM, "device budget too small for the gcd batch");
-        e = cudaMemcpyAsync(d_plan, plan.data(), sizeof(GcdPlan) * n, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d_slotlist, slotlist.data(), slotlist.size() * 4, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d_wls, wl_start.data(), wl_start.size() * 8, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(d_wlj, wl_jobs.data(), wl_jobs.size() * 4, cudaMemcpyHostToDevice, s);
+        e = gcd_copy(c, d_plan, plan.data(), sizeof(GcdPlan) * n, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = gcd_copy(c, d_slotlist, slotlist.data(), slotlist.size() * 4, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = gcd_copy(c, d_wls, wl_start.data(), wl_start.size() * 8, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = gcd_copy(c, d_wlj, wl_jobs.data(), wl_jobs.size() * 4, cudaMemcpyHostToDevice, s);
         L.plan = d_plan;
         L.slots = d_slots;
         L.slotlist = d_slotlist;
@@ -647,10 +659,12 @@ static int gcd_batch_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upo
         if (e == cudaSuccess) {
             int grid = grid_for((const void *)k_gcd_modp, nw * 32, smem, (total + nw - 1) / nw);
             k_gcd_modp<<<grid, nw * 32, smem, s>>>(L, d_wls, d_wlj, (int)wl_jobs.size(), total, maxreg);
+            c->gcd_kernels++;
+            c->gcd_subproblems += total;
             e = cudaGetLastError();
         }
         std::vector<int32_t> sdeg(slotlist.size());
-        if (e == cudaSuccess) e = cudaMemcpyAsync(sdeg.data(), d_sdeg, sdeg.size() * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = gcd_copy(c, sdeg.data(), d_sdeg, sdeg.size() * 4, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "gcd modular stage", e);
         // ---- keep the primes of minimal gcd degree
@@ -717,11 +731,11 @@ static int gcd_batch_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upo
             if (!d_crtlist || !d_garner || !d_lift || !d_lsign || !d_out || !d_osign || !d_odeg || !d_status ||
                 !d_ready || !d_cs || !d_cj)
                 return c->fail(GBR_ENOMEM, "device budget too small for the gcd lift");
-            e = cudaMemcpyAsync(d_plan, plan.data(), sizeof(GcdPlan) * n, cudaMemcpyHostToDevice, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(d_crtlist, crtlist.data(), crtlist.size() * 4, cudaMemcpyHostToDevice, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(d_ready, ready.data(), ready.size() * 4, cudaMemcpyHostToDevice, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(d_cs, cs.data(), cs.size() * 8, cudaMemcpyHostToDevice, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(d_cj, cj.data(), cj.size() * 4, cudaMemcpyHostToDevice, s);
+            e = gcd_copy(c, d_plan, plan.data(), sizeof(GcdPlan) * n, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = gcd_copy(c, d_crtlist, crtlist.data(), crtlist.size() * 4, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = gcd_copy(c, d_ready, ready.data(), ready.size() * 4, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = gcd_copy(c, d_cs, cs.data(), cs.size() * 8, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = gcd_copy(c, d_cj, cj.data(), cj.size() * 4, cudaMemcpyHostToDevice, s);
             if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, (size_t)n * 4, s);
             L.crtlist = d_crtlist;
             L.garner = d_garner;
@@ -736,6 +750,7 @@ static int gcd_batch_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upo
                 int64_t it = (int64_t)nr * GBR_MAX_PRIMES;
                 int grid = (int)std::min<int64_t>((it + 255) / 256, 4096);
                 k_gcd_garner<<<grid, 256, 0, s>>>(L, d_ready, nr);
+                c->gcd_kernels++;
                 e = cudaGetLastError();
             }
             if (e == cudaSuccess) {
@@ -746,37 +761,47 @@ static int gcd_batch_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upo
                 if (e == cudaSuccess) {
                     int grid = grid_for((const void *)k_gcd_crt, block, sm2, (ctotal + block - 1) / block);
                     k_gcd_crt<<<grid, block, sm2, s>>>(L, d_cs, d_cj, (int)cj.size(), ctotal, maxL);
+                    c->gcd_kernels++;
                     e = cudaGetLastError();
                 }
             }
             if (e == cudaSuccess) {
                 k_gcd_check<<<(nr * 32 + 127) / 128, 128, 0, s>>>(L, d_ready, nr);
+                c->gcd_kernels++;
                 e = cudaGetLastError();
             }
             std::vector<int32_t> st(n), od(n);
             std::vector<uint32_t> hout((size_t)out_w);
             std::vector<int8_t> hos((size_t)osign_b);
             int32_t herr = 0;
-            if (e == cudaSuccess) e = cudaMemcpyAsync(st.data(), d_status, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(od.data(), d_odeg, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess && out_w) e = cudaMemcpyAsync(hout.data(), d_out, (size_t)out_w * 4, cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess && osign_b) e = cudaMemcpyAsync(hos.data(), d_osign, (size_t)osign_b, cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, c->d_err, 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = gcd_copy(c, st.data(), d_status, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = gcd_copy(c, od.data(), d_odeg, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess && out_w) e = gcd_copy(c, hout.data(), d_out, (size_t)out_w * 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess && osign_b) e = gcd_copy(c, hos.data(), d_osign, (size_t)osign_b, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = gcd_copy(c, &herr, c->d_err, 4, cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "gcd lift and check", e);
             if (herr) return c->fail(GBR_EDEVICE, "gcd device-side consistency check failed");
+            // the results verified in this attempt share one host block
+            std::vector<int> done;
             for (int i : ready) {
+                if (st[i] != 1) retry.push_back(i);
+                else done.push_back(i);
+            }
+            std::vector<gbr_bigpoly> tmp(done.size());
+            for (size_t t = 0; t < done.size(); ++t) {
+                tmp[t].deg = od[done[t]];
+                tmp[t].limbs = plan[done[t]].Lout;
+            }
+            if (!tmp.empty() && !gbr_alloc_results(tmp.data(), (int)tmp.size()))
+                return c->fail(GBR_ENOMEM, "host result allocation");
+            for (size_t t = 0; t < done.size(); ++t) {
+                const int i = done[t];
                 const GcdPlan &G = plan[i];
-                if (st[i] != 1) {
-                    retry.push_back(i);
-                    continue;
-                }
-                gbr_bigpoly &b = out[i];
-                b.deg = od[i];
-                b.limbs = G.Lout;
-                if (!gbr_alloc_results(&b, 1)) return c->fail(GBR_ENOMEM, "host result allocation");
-                std::memcpy(b.mag, hout.data() + G.out_off, (size_t)(b.deg + 1) * G.Lout * 4);
-                std::memcpy(b.sign, hos.data() + G.osign_off, (size_t)b.deg + 1);
+                out[i] = tmp[t];
+                if (out[i].deg < 0) continue;
+                std::memcpy(out[i].mag, hout.data() + G.out_off, (size_t)(out[i].deg + 1) * G.Lout * 4);
+                std::memcpy(out[i].sign, hos.data() + G.osign_off, (size_t)out[i].deg + 1);
             }
         }
         pending = retry;
@@ -794,8 +819,26 @@ extern "C" int gbr_gcd_batch(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_up
     std::lock_guard<std::mutex> lk(c->mu);
     cudaSetDevice(c->device);
     int st;
+    const auto t0 = std::chrono::steady_clock::now();
+    if (c->stats_on) cudaEventRecord(c->ev[0], c->stream);
     try {
         st = gcd_batch_locked(c, n, p, q, out);
+        if (c->stats_on) {
+            // the whole call on the context's stream: copies, kernels and the host
+            // planning between them (the gcd path synchronises after each stage)
+            cudaEventRecord(c->ev[1], c->stream);
+            cudaEventSynchronize(c->ev[1]);
+            gbr_stats g{};
+            float ms = 0;
+            cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+            g.gcd_ms = ms;
+            g.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            g.kernels = c->gcd_kernels;
+            g.subproblems = c->gcd_subproblems;
+            g.h2d_bytes = c->gcd_h2d;
+            g.d2h_bytes = c->gcd_d2h;
+            c->stats = g;
+        }
     } catch (std::bad_alloc &) {
         st = c->fail(GBR_ENOMEM, "host allocation");
     }
