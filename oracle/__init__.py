@@ -31,6 +31,8 @@ Functions
 ``res_at``        exact R(a) for one integer a (Sylvester determinant at x = a).
 ``disc_res``      res_y(f, df/dy).
 ``gcd_z``         primitive polynomial remainder sequence over Z.
+``sqf_yun``       square-free factorisation R = u prod r_i^i (Section 2.1) by Yun's
+                  algorithm over Z with primitive gcds.
 
 Every function is pinned by ``tests/test_oracle.py`` against closed forms
 (planted roots), invariants (symmetry, multiplicativity, planted common factor),
@@ -42,10 +44,11 @@ from .zpoly import (ZZ, ZX, zx_add, zx_sub, zx_mul, zx_neg, zx_trim, zx_eval, zx
 from .resultant import (sylvester, det_bareiss, res_bareiss, res_leibniz, res_subres, res_evalz, res_at_prs,
                         res_at, disc_res, deriv_y, ydeg, xdeg, res_univariate, degree_bound)
 from .gcd import gcd_z, divides_z
+from .sqf import sqf_yun
 
 __all__ = [
     "ZZ", "ZX", "zx_add", "zx_sub", "zx_mul", "zx_neg", "zx_trim", "zx_eval", "zx_divexact",
     "zx_deg", "content", "primitive_part", "sylvester", "det_bareiss", "res_bareiss", "res_leibniz",
     "res_subres", "res_evalz", "res_at", "res_at_prs", "disc_res", "deriv_y", "ydeg", "xdeg", "res_univariate",
-    "degree_bound", "gcd_z", "divides_z",
+    "degree_bound", "gcd_z", "divides_z", "sqf_yun",
 ]

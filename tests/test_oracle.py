@@ -309,3 +309,99 @@ def test_res_at_prs_matches_determinant():
     gl = [[2, -1], [1, 0, 1], [-2, 1]]
     for a in (-3, 2, 4):
         assert O.res_at_prs(fl, gl, a) == O.res_at(fl, gl, a)
+
+
+# --------------------------------------------------------------------------- square-free factorisation
+
+
+def _planted_sqf(rng, mults, nroots=3, lc_choices=(1, 2, 3, 5)):
+    """u * prod r_i^i with every r_i a product of distinct primitive linear factors
+    (b x - a), gcd(a, b) = 1, all ratios a / b distinct: square-free, pairwise coprime
+    and primitive by construction."""
+    used = set()
+    factors = []
+    for _ in range(mults):
+        r = (1,)
+        for _ in range(rng.randint(0, nroots)):
+            while True:
+                b = rng.choice(lc_choices)
+                a = rng.randint(-9, 9)
+                if math.gcd(a, b) == 1 and (a, b) not in used and all(a * bb != aa * b for aa, bb in used):
+                    break
+            used.add((a, b))
+            r = O.zx_mul(r, (-a, b))
+        factors.append(r)
+    while factors and len(factors[-1]) == 1:
+        factors.pop()
+    u = rng.choice([1, -1, 6, -10, 35])
+    R = (u,)
+    for i, r in enumerate(factors, start=1):
+        R = O.zx_mul(R, _zx_pow(r, i))
+    return u, factors, R
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_sqf_planted_factorisation(seed):
+    rng = random.Random(900 + seed)
+    u, factors, R = _planted_sqf(rng, rng.randint(1, 4))
+    assert O.sqf_yun(R) == (u, factors)
+
+
+def test_sqf_hand_cases():
+    assert O.sqf_yun([]) == (0, [])
+    assert O.sqf_yun([-6]) == (-6, [])
+    assert O.sqf_yun([-3, 6, -3]) == (-3, [(1,), (-1, 1)])           # -3 (x - 1)^2
+    assert O.sqf_yun([0, 0, 0, 4]) == (4, [(1,), (1,), (0, 1)])      # 4 x^3
+    assert O.sqf_yun([-2, 0, 2]) == (2, [(-1, 0, 1)])                 # 2 (x^2 - 1)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_sqf_against_sympy(seed):
+    sympy = pytest.importorskip("sympy")
+    x = sympy.symbols("x")
+    rng = random.Random(950 + seed)
+    R = (rng.choice([1, -2, 3]),)
+    for _ in range(rng.randint(1, 4)):
+        p = tuple(rng.randint(-5, 5) for _ in range(rng.randint(2, 4)))
+        R = O.zx_mul(R, _zx_pow(O.zx_trim(p) or (1,), rng.randint(1, 3)))
+    u, facs = O.sqf_yun(R)
+    coeff, lst = sympy.sqf_list(sympy.Poly(list(reversed(R)), x))
+    mult = {}
+    for fac, e in lst:
+        c = fac.all_coeffs()
+        if c[0] < 0:
+            c = [-v for v in c]
+            coeff = -coeff
+        mult[e] = tuple(int(v) for v in reversed(c))
+    want = [mult.get(i, (1,)) for i in range(1, (max(mult) if mult else 0) + 1)]
+    assert facs == want and u == int(coeff)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_sqf_invariants_on_discriminant_resultant(seed):
+    """R = res_y(f, f_y) of a union of two circles (singular where they meet): u prod r_i^i equals R,
+    every r_i is primitive with positive leading coefficient and the r_i are pairwise
+    coprime (checked with sympy's gcd where available, by trial division otherwise)."""
+    rng = random.Random(970 + seed)
+
+    def circle(a, b, r):   # (x - a)^2 + (y - b)^2 - r^2, rows = powers of y
+        return [[a * a + b * b - r * r, -2 * a, 1], [-2 * b], [1]]
+
+    # two circles: a square-free curve, singular where they meet (repeated roots of R)
+    f = W._mul2(circle(rng.randint(-3, 3), rng.randint(-3, 3), rng.randint(2, 4)),
+                circle(rng.randint(-3, 3), rng.randint(-3, 3), rng.randint(2, 4)))
+    R = O.disc_res(f)
+    assert O.zx_trim(R)
+    u, facs = O.sqf_yun(R)
+    prod = (u,)
+    for i, r in enumerate(facs, start=1):
+        assert r[-1] > 0 and O.content(r) == 1
+        prod = O.zx_mul(prod, _zx_pow(r, i))
+    assert prod == O.zx_trim(R)
+    sympy = pytest.importorskip("sympy")
+    x = sympy.symbols("x")
+    polys = [sympy.Poly(list(reversed(r)), x) for r in facs]
+    for i in range(len(polys)):
+        assert sympy.degree(sympy.gcd(polys[i], polys[i].diff(x)), x) <= 0
+        for j in range(i):
+            assert sympy.degree(sympy.gcd(polys[i], polys[j]), x) <= 0
