@@ -55,7 +55,7 @@ extern "C" {
 #define GBR_EDEVICE   3   /* a CUDA call failed (text in gbr_last_error) */
 #define GBR_ETIMEOUT  4   /* gbr_poll: not finished within timeout_ms */
 #define GBR_EAGAIN    5   /* gbr_poll with timeout 0: not finished yet */
-#define GBR_EVERIFY   6   /* gcd: the exact check still failed after GBR_MAX_PRIMES primes */
+#define GBR_EVERIFY   6   /* gcd, square-free: the exact check still failed with every allowed prime */
 #define GBR_ELIMIT    7   /* input beyond a documented size limit (see GBR_MAX_*) */
 #define GBR_ECANCELED 8   /* serving: the context was shut down before the job ran */
 #define GBR_ENOTFOUND 9   /* serving: unknown ticket */
@@ -200,6 +200,36 @@ int gbr_resultant_batch(gbr_ctx *ctx, int n, const gbr_bipoly *f, const gbr_bipo
                         gbr_bigpoly *out);
 int gbr_discriminant_res_batch(gbr_ctx *ctx, int n, const gbr_bipoly *f, int var, gbr_bigpoly *out);
 int gbr_gcd_batch(gbr_ctx *ctx, int n, const gbr_upoly *p, const gbr_upoly *q, gbr_bigpoly *out);
+
+/* ------------------------------------------------------------------ square-free factorisation */
+
+/* R = unit * prod_{i=1..count} factors[i-1]^i (Section 2.1, Projection Phase:
+ * the square-free, pairwise coprime factors r_i of R, from Yun's algorithm).
+ * Every factor is primitive with a positive leading coefficient; a multiplicity
+ * that does not occur has the factor 1 (degree 0); factors[count-1] has positive
+ * degree.  unit is a degree-0 polynomial (the content of R with the sign of its
+ * leading coefficient), or deg = -1 when R = 0 (count 0).  A constant R gives
+ * unit = R, count 0.  Library-owned: release with gbr_free_sqf. */
+typedef struct {
+    gbr_bigpoly unit;
+    int32_t count;
+    gbr_bigpoly *factors;
+} gbr_sqf;
+
+/* Square-free factorisation of integer polynomials given in the gbr_bigpoly
+ * layout (caller-owned host memory; deg <= GBR_MAX_UDEG; leading zero
+ * coefficients are ignored).  Device stages: the coefficients modulo a run of
+ * table primes, Yun's algorithm over F_p with one warp per (polynomial, prime),
+ * the Garner lift of lc(R) times each monic modular factor over primes that
+ * share the degree pattern of largest square-free degree (primes whose product
+ * exceeds 2^(deg r_i + 3) ||R||_2), and the exact check R = u prod r_i^i modulo
+ * primes whose product exceeds both sides' coefficient bounds.  The host takes
+ * the primitive parts (big-integer gcds of the lifted coefficients) and u.  A
+ * failed check retries with twice the primes; GBR_EVERIFY once the table is
+ * exhausted.  On error every out[i] is left empty (count 0, NULL pointers). */
+int gbr_squarefree(gbr_ctx *ctx, const gbr_bigpoly *r, gbr_sqf *out);
+int gbr_squarefree_batch(gbr_ctx *ctx, int n, const gbr_bigpoly *r, gbr_sqf *out);
+void gbr_free_sqf(gbr_ctx *ctx, gbr_sqf *x);
 
 /* Device-resident batches: gbr_upload_pairs copies the inputs into device
  * memory once; gbr_run_resident then runs the whole path (bounds included) on

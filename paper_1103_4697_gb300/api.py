@@ -139,6 +139,29 @@ def bigpoly_to_ints(b: N.BigPoly) -> list[int]:
     return out
 
 
+def pack_bigpolys(polys, keep: _Packed):
+    """Integer polynomials (ascending coefficients) in the gbr_bigpoly layout:
+    little-endian 32-bit limbs of |c| and a sign byte per coefficient."""
+    arr = (N.BigPoly * max(len(polys), 1))()
+    for k, p in enumerate(polys):
+        vals = [int(c) for c in p]
+        while vals and vals[-1] == 0:
+            vals.pop()
+        if not vals:
+            arr[k].deg, arr[k].limbs = -1, 1
+            continue
+        L = max(1, max((abs(v).bit_length() + 31) // 32 for v in vals))
+        raw = b"".join(abs(v).to_bytes(4 * L, "little") for v in vals)
+        mag = np.frombuffer(raw, dtype="<u4").copy()
+        sgn = np.array([(v > 0) - (v < 0) for v in vals], dtype=np.int8)
+        keep.bufs += [mag, sgn]
+        arr[k].deg, arr[k].limbs = len(vals) - 1, L
+        arr[k].mag = mag.ctypes.data_as(C.POINTER(C.c_uint32))
+        arr[k].sign = sgn.ctypes.data_as(C.POINTER(C.c_int8))
+    keep.bufs.append(arr)
+    return arr
+
+
 def _ptr(desc) -> C.c_void_p:
     return C.c_void_p(desc.ctypes.data)
 
@@ -286,6 +309,28 @@ class Context:
 
     def gcd(self, p, q) -> list[int]:
         return self.gcd_batch([p], [q])[0]
+
+    # ------------------------------------------------------------- square-free factorisation
+    def squarefree_batch(self, rs) -> list[tuple[int, list[list[int]]]]:
+        """gbr_squarefree_batch: for each R, (u, [r_1, ..., r_m]) with
+        R = u * prod r_i^i (Section 2.1), every r_i primitive with a positive
+        leading coefficient; R = 0 gives (0, [])."""
+        keep = _Packed()
+        arr = pack_bigpolys(rs, keep)
+        n = len(rs)
+        outs = (N.Sqf * max(n, 1))()
+        L = N.lib()
+        N.check(L.gbr_squarefree_batch(self.handle, n, arr, outs), self.handle)
+        res = []
+        for i in range(n):
+            u = bigpoly_to_ints(outs[i].unit)
+            facs = [bigpoly_to_ints(outs[i].factors[k]) for k in range(outs[i].count)]
+            L.gbr_free_sqf(self.handle, C.byref(outs[i]))
+            res.append((u[0] if u else 0, [f if f else [0] for f in facs]))
+        return res
+
+    def squarefree(self, r) -> tuple[int, list[list[int]]]:
+        return self.squarefree_batch([r])[0]
 
 
 def resultant_info(f, g=None, var: int = 1, disc: bool = False) -> dict:

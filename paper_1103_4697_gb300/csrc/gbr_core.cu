@@ -641,6 +641,7 @@ extern "C" int gbr_create(gbr_ctx **out, int device, size_t budget, void *worksp
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, 64);
     if (e == cudaSuccess) e = configure_res_kernels();
     if (e == cudaSuccess) e = configure_gcd_kernels();
+    if (e == cudaSuccess) e = configure_sqf_kernels();
     if (e == cudaSuccess) e = configure_interp_tc_kernel();
     if (e != cudaSuccess) {
         gbr_destroy(c);

@@ -238,6 +238,7 @@ constexpr int kMaxDynSmem = 200 * 1024;
 cudaError_t configure_res_kernels();
 cudaError_t configure_evalres_kernel();
 cudaError_t configure_gcd_kernels();
+cudaError_t configure_sqf_kernels();
 
 cudaError_t launch_bounds(const ResLaunch &L, cudaStream_t s);
 cudaError_t launch_reduce(const ResLaunch &L, const WorkList &w, cudaStream_t s);

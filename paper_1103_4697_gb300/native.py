@@ -30,6 +30,10 @@ class BigPoly(C.Structure):
                 ("sign", C.POINTER(C.c_int8))]
 
 
+class Sqf(C.Structure):
+    _fields_ = [("unit", BigPoly), ("count", C.c_int32), ("factors", C.POINTER(BigPoly))]
+
+
 class Stats(C.Structure):
     _fields_ = [("bounds_ms", C.c_double), ("reduce_ms", C.c_double), ("evalres_ms", C.c_double),
                 ("interp_ms", C.c_double), ("crt_ms", C.c_double), ("gcd_ms", C.c_double),
@@ -73,6 +77,9 @@ SIGNATURES = {
     "gbr_resultant_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(BigPoly)]),
     "gbr_discriminant_res_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(BigPoly)]),
     "gbr_gcd_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(BigPoly)]),
+    "gbr_squarefree": (C.c_int, [C.c_void_p, C.POINTER(BigPoly), C.POINTER(Sqf)]),
+    "gbr_squarefree_batch": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(BigPoly), C.POINTER(Sqf)]),
+    "gbr_free_sqf": (None, [C.c_void_p, C.POINTER(Sqf)]),
     "gbr_upload_pairs": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
                                    C.POINTER(C.c_void_p)]),
     "gbr_run_resident": (C.c_int, [C.c_void_p, C.c_void_p]),

@@ -247,6 +247,33 @@ def gcd_batch(seed: int = 3, n: int = 4096, lo: int = 30, hi: int = 200, hdeg: i
     return P, Q, H
 
 
+def sqf_batch(seed: int = 6, n: int = 2048, degs=((20, 60), (4, 16), (0, 4)), bits: int = 16,
+              unit_bits: int = 8):
+    """Square-free factorisation inputs R = u * r_1 * r_2^2 * r_3^3 ... shaped like the
+    projection resultants res(f, f_y) of curves with nodes and cusps: a large
+    square-free part, squared factors from the singular points, a few higher powers.
+    deg r_i ~ U{degs[i-1]}, coefficients signed `bits`-bit (non-zero leading term),
+    u a signed `unit_bits`-bit constant.  Returns (R list, planted list of (u, [r_i]))."""
+    st = Stream(seed, 2)
+    R, planted = [], []
+    for _ in range(n):
+        u = _nonzero(st, unit_bits)
+        facs = []
+        for lo, hi in degs:
+            d = st.uniform_int(lo, hi, 1)[0]
+            r = st.signed_bits(bits, d + 1)
+            if r[-1] == 0:
+                r[-1] = _nonzero(st, bits)
+            facs.append(r)
+        out = [u]
+        for i, r in enumerate(facs, start=1):
+            for _ in range(i):
+                out = _mul1(out, r)
+        R.append(out)
+        planted.append((u, facs))
+    return R, planted
+
+
 def conic_curves(seed: int = 4, ncon: int = 8, rbits: int = 10, nterms: int = 16,
                  tdeg: int = 16, tbits: int = 32, gdeg: int = 24, gbits: int = 64):
     """Large structured curves: f = product of `ncon` circles/axis-parallel ellipses with
