@@ -435,7 +435,10 @@ def run_config(args) -> None:
     conic   product of 8 conics (+ sparse terms) against a dense degree-24 curve with
             64-bit coefficients: res_y(f, g) and res_y(f, f_y), one call each;
     serve   Poisson streams of mixed requests at 0.5, 0.8 and 0.95 of the measured capacity;
-    gcd     the 4096 gcd jobs alone, through the C ABI with packed host buffers."""
+    gcd     the 4096 gcd jobs alone, through the C ABI with packed host buffers;
+    sqf     square-free factorisation R = u prod r_i^i (Section 2.1) of 2048 planted
+            projection-resultant-shaped polynomials, through the C ABI, and of
+            R = res_y(f, f_y) of the conic-product curve (the path's own output)."""
     import torch
 
     import oracle as O
@@ -539,6 +542,42 @@ def run_config(args) -> None:
         out["gcd_stats"] = {k: gst[k] for k in ("gcd_ms", "total_ms", "kernels", "subproblems", "h2d_bytes",
                                                 "d2h_bytes")}
         out["workload"] = "4096 gcds deg 30..200, planted degree-5 factor, 8..32-bit cofactors (seed 3)"
+    elif args.config == "sqf":
+        NS = 2048
+        R, _ = W.sqf_batch(6, NS)
+        keep = api._Packed()
+        arr = api.pack_bigpolys(R, keep)
+        ctx.set_option(N.OPT_STATS, 1)
+        L = N.lib()
+        souts = (N.Sqf * NS)()
+        times = []
+        for it in range(6):
+            t0 = time.perf_counter()
+            N.check(L.gbr_squarefree_batch(ctx.handle, NS, arr, souts), ctx.handle)
+            times.append(time.perf_counter() - t0)
+            sst = ctx.stats()
+            for i in range(NS):
+                L.gbr_free_sqf(ctx.handle, C.byref(souts[i]))
+        sec = statistics.median(times[1:])
+        out["sqf_jobs_per_s"] = NS / sec
+        out["sqf_ms_per_call"] = sec * 1e3
+        out["sqf_stats"] = {k: sst[k] for k in ("gcd_ms", "total_ms", "kernels", "subproblems", "h2d_bytes",
+                                                "d2h_bytes")}
+        t = time.perf_counter()
+        for i in range(4):
+            O.sqf_yun(R[i])
+        out["oracle_sqf_jobs_per_s_1core"] = 4 / (time.perf_counter() - t)
+        # the paper's chain: R = res_y(f, f_y) of a product of 8 circles/ellipses
+        # (singular at their intersections, so R has squared factors), then Yun on R
+        f, _g = W.conic_curves(4, nterms=0)
+        Rc = ctx.discriminant_res(f)
+        ctx.squarefree(Rc)
+        tc = _time_calls(lambda: ctx.squarefree(Rc), 5)
+        u, facs = ctx.squarefree(Rc)
+        out["conic_R"] = {"deg": len(Rc) - 1, "max_bits": max(abs(c).bit_length() for c in Rc),
+                          "factor_degrees": [len(x) - 1 for x in facs], "sqf_ms": tc * 1e3}
+        out["workload"] = ("2048 R = u r1 r2^2 r3^3, deg r_i ~ U{20..60}, U{4..16}, U{0..4}, 16-bit "
+                           "(deg R 28..104, about 100-bit coefficients; seed 6); R = res_y(f, f_y) of 8 conics (seed 4)")
     elif args.config == "serve":
         res_all = {}
         cap = None
@@ -562,7 +601,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mem-gb", type=int, default=24)
     ap.add_argument("--pairs", type=int, default=PAIRS, help="pairs per GPU (smaller only for profiling)")
-    ap.add_argument("--config", choices=["headline", "small", "deg20", "mixed", "conic", "serve", "gcd"],
+    ap.add_argument("--config", choices=["headline", "small", "deg20", "mixed", "conic", "serve", "gcd", "sqf"],
                     default="headline", help="other workloads print their own JSON line")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--no-serve", action="store_true")

@@ -112,7 +112,9 @@ typedef struct {
  * (gbr_gcd, gbr_gcd_batch) records gcd_ms (CUDA events around the whole call on
  * the context's stream, including the host work between its stages), total_ms
  * (host wall time), kernels, subproblems ((job, prime) pairs of the modular
- * gcds) and the bytes copied. */
+ * gcds) and the bytes copied; a square-free call (gbr_squarefree,
+ * gbr_squarefree_batch) records the same fields, its subproblems being the
+ * (polynomial, prime) pairs of the modular Yun runs and of the exact check. */
 typedef struct {
     double bounds_ms, reduce_ms, evalres_ms, interp_ms, crt_ms, gcd_ms, total_ms;
     int64_t kernels;          /* kernels launched */

@@ -1,6 +1,8 @@
 // Host big integers for the square-free factorisation (internal): sign and
 // magnitude in little-endian 32-bit limbs.  Only what the lift needs: products,
-// exact and Euclidean division (Knuth's long division), gcd, comparison.
+// exact and Euclidean division (Knuth's long division), gcd, comparison.  The
+// division and gcd work on limb slices with caller-provided scratch vectors, so
+// a loop over many coefficients allocates nothing once the scratch has grown.
 #pragma once
 #include <stdint.h>
 
@@ -11,20 +13,32 @@
 namespace gbr {
 namespace bn {
 
+using Limbs = std::vector<uint32_t>;
+
 struct Big {
-    std::vector<uint32_t> m;   // magnitude, no leading zero limbs; empty = 0
-    int s = 0;                 // -1, 0, +1
+    Limbs m;     // magnitude, no leading zero limbs; empty = 0
+    int s = 0;   // -1, 0, +1
 };
 
+// reusable buffers of one thread
+struct Scratch {
+    Limbs u, v, q, r, a, b, g, x;
+};
+
+inline size_t top(const uint32_t *x, size_t n) {
+    while (n && x[n - 1] == 0u) --n;
+    return n;
+}
+
 inline void trim(Big &a) {
-    while (!a.m.empty() && a.m.back() == 0u) a.m.pop_back();
+    a.m.resize(top(a.m.data(), a.m.size()));
     if (a.m.empty()) a.s = 0;
     else if (a.s == 0) a.s = 1;
 }
 
 inline Big from_limbs(const uint32_t *x, int n, int sign) {
     Big a;
-    a.m.assign(x, x + n);
+    a.m.assign(x, x + top(x, (size_t)n));
     a.s = sign < 0 ? -1 : 1;
     trim(a);
     return a;
@@ -38,16 +52,16 @@ inline Big from_u64(uint64_t v, int sign = 1) {
     return a;
 }
 
-inline int cmp_mag(const std::vector<uint32_t> &a, const std::vector<uint32_t> &b) {
-    if (a.size() != b.size()) return a.size() < b.size() ? -1 : 1;
-    for (size_t i = a.size(); i-- > 0;)
+inline int cmp_mag(const uint32_t *a, size_t na, const uint32_t *b, size_t nb) {
+    if (na != nb) return na < nb ? -1 : 1;
+    for (size_t i = na; i-- > 0;)
         if (a[i] != b[i]) return a[i] < b[i] ? -1 : 1;
     return 0;
 }
 
-inline std::vector<uint32_t> mul_mag(const std::vector<uint32_t> &a, const std::vector<uint32_t> &b) {
+inline Limbs mul_mag(const Limbs &a, const Limbs &b) {
     if (a.empty() || b.empty()) return {};
-    std::vector<uint32_t> r(a.size() + b.size(), 0u);
+    Limbs r(a.size() + b.size(), 0u);
     for (size_t i = 0; i < a.size(); ++i) {
         uint64_t carry = 0;
         for (size_t j = 0; j < b.size(); ++j) {
@@ -57,7 +71,7 @@ inline std::vector<uint32_t> mul_mag(const std::vector<uint32_t> &a, const std::
         }
         r[i + b.size()] = (uint32_t)carry;
     }
-    while (!r.empty() && r.back() == 0u) r.pop_back();
+    r.resize(top(r.data(), r.size()));
     return r;
 }
 
@@ -69,34 +83,36 @@ inline Big mul(const Big &a, const Big &b) {
     return r;
 }
 
-// q = a / b, r = a mod b for magnitudes (b non-zero): Knuth's algorithm D with
-// 32-bit digits, normalised so that the divisor's top digit has its high bit set
-inline void divmod_mag(const std::vector<uint32_t> &a, const std::vector<uint32_t> &b, std::vector<uint32_t> &q,
-                       std::vector<uint32_t> &r) {
+// q = a / b, r = a mod b for trimmed magnitudes (nb > 0): Knuth's algorithm D
+// with 32-bit digits, normalised so that the divisor's top digit has its high
+// bit set.  q and r must not alias a, b or the scratch's u and v.
+inline void divmod_mag(const uint32_t *a, size_t na, const uint32_t *b, size_t n, Limbs &q, Limbs &r, Scratch &S) {
     q.clear();
     r.clear();
-    if (cmp_mag(a, b) < 0) {
-        r = a;
+    if (cmp_mag(a, na, b, n) < 0) {
+        r.assign(a, a + na);
         return;
     }
-    const size_t n = b.size(), m = a.size() - n;
+    const size_t m = na - n;
     if (n == 1) {
-        q.assign(a.size(), 0u);
+        q.assign(na, 0u);
         uint64_t rem = 0;
-        for (size_t i = a.size(); i-- > 0;) {
+        for (size_t i = na; i-- > 0;) {
             const uint64_t cur = (rem << 32) | a[i];
             q[i] = (uint32_t)(cur / b[0]);
             rem = cur % b[0];
         }
-        while (!q.empty() && q.back() == 0u) q.pop_back();
-        if (rem) r = {(uint32_t)rem};
+        q.resize(top(q.data(), q.size()));
+        if (rem) r.assign(1, (uint32_t)rem);
         return;
     }
     int sh = 0;
     while (!(b[n - 1] & (0x80000000u >> sh))) ++sh;
-    std::vector<uint32_t> v(n), u(a.size() + 1, 0u);
+    Limbs &v = S.v, &u = S.u;
+    v.assign(n, 0u);
+    u.assign(na + 1, 0u);
     for (size_t i = n; i-- > 0;) v[i] = (b[i] << sh) | (sh && i ? b[i - 1] >> (32 - sh) : 0u);
-    for (size_t i = a.size(); i-- > 0;) {
+    for (size_t i = na; i-- > 0;) {
         u[i + 1] |= sh ? a[i] >> (32 - sh) : 0u;
         u[i] = a[i] << sh;
     }
@@ -135,38 +151,83 @@ inline void divmod_mag(const std::vector<uint32_t> &a, const std::vector<uint32_
         }
         q[j] = (uint32_t)qh;
     }
-    while (!q.empty() && q.back() == 0u) q.pop_back();
+    q.resize(top(q.data(), q.size()));
     r.assign(n, 0u);
     for (size_t i = 0; i < n; ++i) r[i] = (u[i] >> sh) | (sh ? (uint32_t)((uint64_t)u[i + 1] << (32 - sh)) : 0u);
-    while (!r.empty() && r.back() == 0u) r.pop_back();
+    r.resize(top(r.data(), r.size()));
 }
 
-// a / b when b divides a exactly; false otherwise (b non-zero)
-inline bool divexact(const Big &a, const Big &b, Big &q) {
-    std::vector<uint32_t> r;
-    divmod_mag(a.m, b.m, q.m, r);
+inline void divmod_mag(const Limbs &a, const Limbs &b, Limbs &q, Limbs &r, Scratch &S) {
+    divmod_mag(a.data(), a.size(), b.data(), b.size(), q, r, S);
+}
+
+// a / b when b (non-zero) divides a exactly; false otherwise
+inline bool divexact(const Big &a, const Big &b, Big &q, Scratch &S) {
+    divmod_mag(a.m, b.m, q.m, S.r, S);
     q.s = a.s * b.s;
     trim(q);
-    return r.empty();
+    return S.r.empty();
 }
 
-inline std::vector<uint32_t> gcd_mag(std::vector<uint32_t> a, std::vector<uint32_t> b) {
-    std::vector<uint32_t> q, r;
-    while (!b.empty()) {
-        divmod_mag(a, b, q, r);
-        a.swap(b);
-        b.swap(r);
+inline uint64_t gcd64(uint64_t a, uint64_t b) {
+    while (b) {
+        const uint64_t t = a % b;
+        a = b;
+        b = t;
     }
     return a;
 }
 
-inline double log2_mag(const std::vector<uint32_t> &a) {
-    if (a.empty()) return -1e300;
-    const size_t t = a.size() - 1;
+// g <- gcd(g, x) for a trimmed g and the limb slice x (n limbs, maybe with
+// leading zeros); g = 0 (empty) is the identity
+inline void gcd_into(Limbs &g, const uint32_t *x, size_t n, Scratch &S) {
+    n = top(x, n);
+    if (!n) return;
+    if (g.empty()) {
+        g.assign(x, x + n);
+        return;
+    }
+    if (g.size() == 1 && g[0] == 1u) return;
+    if (g.size() <= 2) {   // reduce x modulo the small g, then word gcd
+        const uint64_t gv = (uint64_t)g[0] | (g.size() > 1 ? (uint64_t)g[1] << 32 : 0ull);
+        uint64_t rem = 0;
+        for (size_t i = n; i-- > 0;) {
+            const unsigned __int128 cur = ((unsigned __int128)rem << 32) | x[i];
+            rem = (uint64_t)(cur % gv);
+        }
+        const uint64_t d = gcd64(gv, rem);
+        g.assign({(uint32_t)d, (uint32_t)(d >> 32)});
+        g.resize(top(g.data(), g.size()));
+        return;
+    }
+    S.a = g;
+    S.b.assign(x, x + n);
+    while (!S.b.empty()) {
+        divmod_mag(S.a, S.b, S.q, S.r, S);
+        S.a.swap(S.b);
+        S.b.swap(S.r);
+    }
+    g = S.a;
+}
+
+inline double log2_mag(const uint32_t *a, size_t n) {
+    n = top(a, n);
+    if (!n) return -1e300;
+    const size_t t = n - 1;
     double v = (double)a[t];
     if (t >= 1) v += (double)a[t - 1] * 0x1p-32;
     if (t >= 2) v += 0x1p-64 * 2.0;   // the truncated tail, rounded up
     return std::log2(v) + 32.0 * (double)t;
+}
+
+inline double log2_mag(const Limbs &a) { return log2_mag(a.data(), a.size()); }
+
+// an upper bound of |x| / 2^(32 (ref - 1)) from the top two limbs of the
+// trimmed magnitude x (n limbs, n <= ref), as a double
+inline double scaled_mag(const uint32_t *x, size_t n, size_t ref) {
+    if (!n) return 0.0;
+    double v = (double)x[n - 1] + (n >= 2 ? ((double)x[n - 2] + 1.0) * 0x1p-32 : 0.0);
+    return std::ldexp(v * (1.0 + 0x1p-50), 32 * ((int)n - (int)ref));
 }
 
 }  // namespace bn

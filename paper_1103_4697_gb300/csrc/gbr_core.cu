@@ -8,6 +8,7 @@
 // stage kernels of gbr_res.cu.
 #include <algorithm>
 #include <atomic>
+#include <condition_variable>
 #include <cmath>
 #include <functional>
 #include <thread>
@@ -19,6 +20,8 @@
 #include <new>
 #include <string>
 #include <vector>
+
+#include <unistd.h>
 
 #include "../../include/gbres.h"
 #include "gbr_core.h"
@@ -557,20 +560,88 @@ extern "C" void gbr_free_result(gbr_ctx *, gbr_bigpoly *b) {
     b->deg = -1;
 }
 
-// Runs fn(lo, hi) over [0, n) on up to `threads` host threads.
+// Host worker pool behind gbr_parallel_for: created on first use and kept for
+// the life of the process (detached threads waiting on a condition variable),
+// so a call costs a wake-up instead of thread creation.  One parallel loop runs
+// at a time; a loop started from inside a worker, or in a child process forked
+// after the pool started, runs on the calling thread.
+namespace {
+thread_local bool t_in_pool = false;
+
+struct HostPool {
+    std::mutex call_mu, mu;
+    std::condition_variable cv, done;
+    const std::function<void(int, int)> *fn = nullptr;
+    int n = 0, chunks = 0, busy = 0, workers = 0;
+    uint64_t gen = 0;
+    std::atomic<int> next{0};
+    pid_t owner = 0;
+
+    void run() {
+        for (;;) {
+            const int c = next.fetch_add(1);
+            if (c >= chunks) return;
+            (*fn)((int)((int64_t)n * c / chunks), (int)((int64_t)n * (c + 1) / chunks));
+        }
+    }
+    void loop() {
+        t_in_pool = true;
+        uint64_t seen = 0;
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+            cv.wait(lk, [&] { return gen != seen; });
+            seen = gen;
+            lk.unlock();
+            run();
+            lk.lock();
+            if (--busy == 0) done.notify_one();
+        }
+    }
+};
+
+HostPool &host_pool() {
+    static HostPool *P = [] {
+        HostPool *p = new HostPool();
+        p->owner = getpid();
+        const unsigned h = std::thread::hardware_concurrency();
+        p->workers = (int)std::min<unsigned>(16, h ? h : 1) - 1;
+        for (int i = 0; i < p->workers; ++i) std::thread([p] { p->loop(); }).detach();
+        return p;
+    }();
+    return *P;
+}
+}  // namespace
+
+// Runs fn(lo, hi) over [0, n) in chunks on up to `threads` x 4 pieces, shared by
+// the pool's workers and the calling thread.
 void gbr_parallel_for(int n, int threads, const std::function<void(int, int)> &fn) {
     if (n <= 0) return;
-    threads = std::max(1, std::min(threads, n / 64 + 1));
-    if (threads == 1) {
+    threads = std::max(1, std::min(threads, n / 16 + 1));
+    if (threads == 1 || t_in_pool) {
         fn(0, n);
         return;
     }
-    std::vector<std::thread> ts;
-    for (int t = 0; t < threads; ++t) {
-        int lo = (int)((int64_t)n * t / threads), hi = (int)((int64_t)n * (t + 1) / threads);
-        ts.emplace_back([&, lo, hi] { fn(lo, hi); });
+    HostPool &P = host_pool();
+    if (P.workers < 1 || P.owner != getpid()) {
+        fn(0, n);
+        return;
     }
-    for (auto &th : ts) th.join();
+    std::lock_guard<std::mutex> call(P.call_mu);
+    {
+        std::lock_guard<std::mutex> lk(P.mu);
+        P.fn = &fn;
+        P.n = n;
+        P.chunks = std::min(n, threads * 4);
+        P.next = 0;
+        P.busy = P.workers;
+        ++P.gen;
+    }
+    P.cv.notify_all();
+    t_in_pool = true;
+    P.run();
+    t_in_pool = false;
+    std::unique_lock<std::mutex> lk(P.mu);
+    P.done.wait(lk, [&] { return P.busy == 0; });
 }
 
 static int host_threads() {

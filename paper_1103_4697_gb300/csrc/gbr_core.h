@@ -2,6 +2,7 @@
 #pragma once
 #include <condition_variable>
 #include <deque>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <string>
@@ -140,6 +141,7 @@ int gbr_run_resident_finish(gbr_ctx *c, gbr_resident *r);   // wait, check, stat
 int gbr_fetch_resident_locked(gbr_ctx *c, gbr_resident *r, int first, int count, gbr_bigpoly *out);
 void gbr_free_resident_locked(gbr_ctx *c, gbr_resident *r);
 void gbr_serve_shutdown(gbr_ctx *c);
+void gbr_parallel_for(int n, int threads, const std::function<void(int, int)> &fn);   // fn(lo, hi) on threads
 bool gbr_alloc_results(gbr_bigpoly *out, int count);   // one refcounted host block for a call's results
 char *gbr_pinned_result_block(size_t bytes, size_t *got);
 void gbr_register_result_block(char *base, size_t size, int64_t refs, bool pinned);

@@ -14,9 +14,10 @@
 //   verify   R = u prod r_i^i modulo primes whose product exceeds twice both
 //            sides' coefficient bounds, so the identity holds over Z (device).
 // A failed check (too few lucky primes among those tried) doubles the primes.
+#include <chrono>
 #include <cstdlib>
 #include <cstring>
-#include <map>
+#include <thread>
 
 #include "gbr_bigint.h"
 #include "gbr_core.h"
@@ -406,6 +407,13 @@ using namespace gbr;
 
 namespace {
 
+// one factor r_i: deg + 1 coefficients of L limbs each, and their signs
+struct FlatPoly {
+    int deg = -1, L = 1;
+    std::vector<uint32_t> mag;
+    std::vector<int8_t> sign;
+};
+
 struct SqfHost {
     int n = -1;                        // degree of R (-1: zero)
     bn::Big lc;                        // leading coefficient of R
@@ -414,7 +422,7 @@ struct SqfHost {
     std::vector<int> pat;              // chosen degree pattern
     std::vector<int> lucky;            // slots with that pattern
     bn::Big u;
-    std::vector<std::vector<bn::Big>> fac;   // r_1..r_m
+    std::vector<FlatPoly> fac;         // r_1..r_m
 };
 
 struct DevBufs {
@@ -447,75 +455,159 @@ int sqf_warps(int bufs, int stride) {
     return std::max(w, 0);
 }
 
-bool big_results(const std::vector<const std::vector<bn::Big> *> &polys, std::vector<gbr_bigpoly> &out) {
-    // one host block for all polynomials of one factorisation (unit first)
-    out.resize(polys.size());
-    for (size_t i = 0; i < polys.size(); ++i) {
-        const auto &P = *polys[i];
-        int d = (int)P.size() - 1;
-        while (d >= 0 && P[d].s == 0) --d;
-        size_t L = 1;
-        for (int t = 0; t <= d; ++t) L = std::max(L, P[t].m.size());
-        out[i].deg = d;
-        out[i].limbs = (int)L;
+// log2 of the 1-, 2- and max-norms of `count` coefficients, rounded up; get(t,
+// x, n) gives coefficient t's trimmed magnitude (n = 0 for zero).  Each
+// magnitude is bounded from its top two limbs relative to the longest one, so
+// the sums need no logarithm per coefficient; -1e300 for the zero polynomial.
+struct Norms {
+    double l1 = -1e300, l2 = -1e300, linf = -1e300;
+};
+template <class Get>
+Norms log2_norms(int count, Get get) {
+    size_t ref = 0;
+    for (int t = 0; t < count; ++t) {
+        const uint32_t *x;
+        size_t n;
+        get(t, x, n);
+        ref = std::max(ref, n);
     }
-    if (!gbr_alloc_results(out.data(), (int)out.size())) return false;
-    for (size_t i = 0; i < polys.size(); ++i) {
-        const auto &P = *polys[i];
-        for (int t = 0; t <= out[i].deg; ++t) {
-            for (int l = 0; l < out[i].limbs; ++l)
-                out[i].mag[(size_t)t * out[i].limbs + l] = l < (int)P[t].m.size() ? P[t].m[l] : 0u;
-            out[i].sign[t] = (int8_t)P[t].s;
+    Norms r;
+    if (!ref) return r;
+    double s1 = 0.0, s2 = 0.0, mx = 0.0;
+    for (int t = 0; t < count; ++t) {
+        const uint32_t *x;
+        size_t n;
+        get(t, x, n);
+        const double v = bn::scaled_mag(x, n, ref);
+        s1 += v;
+        s2 += v * v;
+        mx = std::max(mx, v);
+    }
+    const double e = 32.0 * (double)(ref - 1), pad = 1e-9 + 1e-12 * count;
+    r.l1 = std::log2(s1) + e + pad;
+    r.l2 = 0.5 * std::log2(s2) + e + pad;
+    r.linf = std::log2(mx) + e + pad;
+    return r;
+}
+
+// primitive part with a positive leading coefficient of the lifted factor whose
+// d + 1 coefficients (LL limbs each) start at x, signs at sg; false when the
+// lift cannot be a multiple of a factor of R (zero leading coefficient).  The
+// content g starts as the leading coefficient; every coefficient is divided by
+// the current g and a non-zero remainder r replaces g by gcd(g, r) (= gcd(g, c)),
+// after which the coefficients already divided are divided again.
+bool primitive_part(const uint32_t *x, const int8_t *sg, int d, int LL, FlatPoly &f, bn::Scratch &S) {
+    if (sg[d] == 0) return false;
+    bn::Limbs &g = S.g;
+    g.assign(x + (size_t)d * LL, x + (size_t)d * LL + bn::top(x + (size_t)d * LL, LL));
+    const int flip = sg[d] < 0 ? -1 : 1;
+    f.deg = d;
+    f.sign.resize(d + 1);
+    f.mag.assign((size_t)(d + 1) * LL, 0u);
+    int redo_to = -1;   // coefficients d .. redo_to were divided by an older g
+    for (int t = d; t >= 0; --t) {
+        f.sign[t] = (int8_t)(sg[t] * flip);
+        if (!sg[t] || (g.size() == 1 && g[0] == 1u)) continue;
+        const uint32_t *c = x + (size_t)t * LL;
+        bn::divmod_mag(c, bn::top(c, LL), g.data(), g.size(), S.q, S.r, S);
+        if (!S.r.empty()) {
+            S.x = S.r;
+            bn::gcd_into(g, S.x.data(), S.x.size(), S);
+            redo_to = t;
+            continue;
         }
+        std::fill(f.mag.begin() + (size_t)t * LL, f.mag.begin() + (size_t)(t + 1) * LL, 0u);
+        std::copy(S.q.begin(), S.q.end(), f.mag.begin() + (size_t)t * LL);
     }
+    const bool unit = g.size() == 1 && g[0] == 1u;
+    int L = 1;
+    for (int t = d; t >= 0; --t) {
+        if (!sg[t]) continue;
+        const uint32_t *c = x + (size_t)t * LL;
+        uint32_t *o = f.mag.data() + (size_t)t * LL;
+        if (unit) {
+            const size_t nl = bn::top(c, LL);
+            std::copy(c, c + nl, o);
+            std::fill(o + nl, o + LL, 0u);
+            L = std::max(L, (int)nl);
+            continue;
+        }
+        if (redo_to >= 0 && t >= redo_to) {
+            bn::divmod_mag(c, bn::top(c, LL), g.data(), g.size(), S.q, S.r, S);
+            if (!S.r.empty()) return false;
+            std::fill(o, o + LL, 0u);
+            std::copy(S.q.begin(), S.q.end(), o);
+        }
+        L = std::max(L, (int)bn::top(o, LL));
+    }
+    if (L < LL) {   // compact to L limbs per coefficient
+        for (int t = 1; t <= d; ++t)
+            std::copy(f.mag.begin() + (size_t)t * LL, f.mag.begin() + (size_t)t * LL + L, f.mag.begin() + (size_t)t * L);
+        f.mag.resize((size_t)(d + 1) * L);
+    }
+    f.L = L;
     return true;
+}
+
+bn::Big lead(const FlatPoly &f) {
+    return bn::from_limbs(f.mag.data() + (size_t)f.deg * f.L, f.L, f.sign[f.deg]);
 }
 
 }  // namespace
 
+// copies of the square-free path, counted for gbr_stats like the gcd path's
+static cudaError_t sqf_copy(gbr_ctx *c, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind,
+                            cudaStream_t s) {
+    if (kind == cudaMemcpyHostToDevice) c->gcd_h2d += (int64_t)bytes;
+    else c->gcd_d2h += (int64_t)bytes;
+    return cudaMemcpyAsync(dst, src, bytes, kind, s);
+}
+
 static int sqf_batch_locked(gbr_ctx *c, int n, const gbr_bigpoly *in, gbr_sqf *out) {
     cudaStream_t s = c->stream;
     const int NP = num_primes();
+    const int threads = (int)std::min(16u, std::max(1u, std::thread::hardware_concurrency()));
+    c->gcd_kernels = c->gcd_subproblems = c->gcd_h2d = c->gcd_d2h = 0;
     std::vector<SqfHost> H(n);
     // ---- host view of every input; constants and zero are finished here
-    int64_t words = 0, signs = 0;
-    std::vector<int64_t> mag_off(n, 0), sign_off(n, 0);
     for (int j = 0; j < n; ++j) {
         const gbr_bigpoly &P = in[j];
         if (P.deg >= 0 && (!P.mag || !P.sign || P.limbs < 1)) return c->fail(GBR_EINVAL, "bad input polynomial");
         int d = P.deg;
-        while (d >= 0 && P.sign[d] == 0) --d;
-        H[j].n = d;
+        while (d > GBR_MAX_UDEG && P.sign[d] == 0) --d;
         if (d > GBR_MAX_UDEG) return c->fail(GBR_ELIMIT, "square-free input degree above GBR_MAX_UDEG");
-        if (d < 1) {
-            H[j].status = 1;
-            if (d == 0) H[j].u = bn::from_limbs(P.mag, P.limbs, P.sign[0]);
-            continue;
-        }
-        H[j].lc = bn::from_limbs(P.mag + (size_t)d * P.limbs, P.limbs, P.sign[d]);
-        double mx = -1e300, s2 = 0.0;
-        for (int t = 0; t <= d; ++t) {
-            if (!P.sign[t]) continue;
-            std::vector<uint32_t> mm(P.mag + (size_t)t * P.limbs, P.mag + (size_t)(t + 1) * P.limbs);
-            while (!mm.empty() && !mm.back()) mm.pop_back();
-            const double l = bn::log2_mag(mm);
-            if (l > mx) {
-                s2 = s2 * std::exp2(2.0 * (mx - l)) + 1.0;
-                mx = l;
-            } else {
-                s2 += std::exp2(2.0 * (l - mx));
+    }
+    gbr_parallel_for(n, threads, [&](int lo, int hi) {
+        for (int j = lo; j < hi; ++j) {
+            const gbr_bigpoly &P = in[j];
+            int d = P.deg;
+            while (d >= 0 && P.sign[d] == 0) --d;
+            H[j].n = d;
+            if (d < 1) {
+                H[j].status = 1;
+                if (d == 0) H[j].u = bn::from_limbs(P.mag, P.limbs, P.sign[0]);
+                continue;
             }
+            H[j].lc = bn::from_limbs(P.mag + (size_t)d * P.limbs, P.limbs, P.sign[d]);
+            const Norms nr = log2_norms(d + 1, [&](int t, const uint32_t *&x, size_t &nl) {
+                x = P.mag + (size_t)t * P.limbs;
+                nl = P.sign[t] ? bn::top(x, (size_t)P.limbs) : 0;
+            });
+            H[j].l2norm2 = nr.l2;
+            H[j].l2inf = nr.linf;
         }
-        H[j].l2inf = mx;
-        H[j].l2norm2 = mx + 0.5 * std::log2(s2) + 1e-9;
+    });
+    int64_t words = 0, signs = 0;
+    std::vector<int64_t> mag_off(n, 0), sign_off(n, 0);
+    std::vector<int> pend;
+    for (int j = 0; j < n; ++j) {
+        if (H[j].status) continue;
+        pend.push_back(j);
         mag_off[j] = words;
         sign_off[j] = signs;
-        words += (int64_t)(d + 1) * P.limbs;
-        signs += d + 1;
+        words += (int64_t)(H[j].n + 1) * in[j].limbs;
+        signs += H[j].n + 1;
     }
-    std::vector<int> pend;
-    for (int j = 0; j < n; ++j)
-        if (!H[j].status) pend.push_back(j);
     DevBufs B{c, {}};
     uint32_t *d_limbs = nullptr;
     int8_t *d_signs = nullptr;
@@ -523,22 +615,26 @@ static int sqf_batch_locked(gbr_ctx *c, int n, const gbr_bigpoly *in, gbr_sqf *o
         uint32_t *hl = (uint32_t *)c->pinned((size_t)words * 4 + (size_t)signs + 64, 0);
         if (!hl) return c->fail(GBR_ENOMEM, "pinned host staging");
         int8_t *hs = (int8_t *)(hl + words);
-        for (int j : pend) {
-            std::memcpy(hl + mag_off[j], in[j].mag, (size_t)(H[j].n + 1) * in[j].limbs * 4);
-            std::memcpy(hs + sign_off[j], in[j].sign, (size_t)H[j].n + 1);
-        }
+        gbr_parallel_for((int)pend.size(), threads, [&](int lo, int hi) {
+            for (int q = lo; q < hi; ++q) {
+                const int j = pend[q];
+                std::memcpy(hl + mag_off[j], in[j].mag, (size_t)(H[j].n + 1) * in[j].limbs * 4);
+                std::memcpy(hs + sign_off[j], in[j].sign, (size_t)H[j].n + 1);
+            }
+        });
         d_limbs = (uint32_t *)B.get((size_t)words * 4 + (size_t)signs + 64);
         if (!d_limbs) return c->fail(GBR_ENOMEM, "device budget too small for the square-free inputs");
         d_signs = (int8_t *)(d_limbs + words);
-        cudaError_t e = cudaMemcpyAsync(d_limbs, hl, (size_t)words * 4 + (size_t)signs, cudaMemcpyHostToDevice, s);
+        cudaError_t e = sqf_copy(c, d_limbs, hl, (size_t)words * 4 + (size_t)signs, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "square-free upload", e);
     }
     // ---- attempts: K primes from the start of the table, doubled on failure
     int K = 0;
     for (int j : pend) K = std::max(K, primes_for_bits(H[j].n + H[j].l2norm2 + 3.0) + 4);
-    for (int attempt = 0; !pend.empty(); ++attempt) {
-        if (K > NP || K > GBR_MAX_PRIMES) return c->fail(GBR_EVERIFY, "square-free check failed with every table prime");
+    if (K > NP) return c->fail(GBR_ELIMIT, "square-free input needs more than the table's primes");
+    while (!pend.empty()) {
+        if (K > NP) return c->fail(GBR_EVERIFY, "square-free check failed with every table prime");
         const int nj = (int)pend.size();
         std::vector<SqfJob> J(nj);
         int64_t res_w = 0, out_w = 0, pat_w = 0, red = 0;
@@ -581,87 +677,118 @@ static int sqf_batch_locked(gbr_ctx *c, int n, const gbr_bigpoly *in, gbr_sqf *o
         L.out = d_out;
         L.pat = d_pat;
         L.err = c->d_err;
-        cudaError_t e = cudaMemcpyAsync(d_jobs, J.data(), sizeof(SqfJob) * nj, cudaMemcpyHostToDevice, s);
+        cudaError_t e = sqf_copy(c, d_jobs, J.data(), sizeof(SqfJob) * nj, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, 4, s);
         if (e == cudaSuccess) {
             k_sqf_reduce<<<sqf_blocks((const void *)k_sqf_reduce, 256, 0, (red + 255) / 256), 256, 0, s>>>(L, red);
             e = cudaGetLastError();
+            ++c->gcd_kernels;
         }
         if (e == cudaSuccess) {
             const size_t smem = (size_t)nwy * 6 * stride * 4;
             k_sqf_yun<<<sqf_blocks((const void *)k_sqf_yun, nwy * 32, smem, ((int64_t)nj * K + nwy - 1) / nwy),
                         nwy * 32, smem, s>>>(L, stride);
             e = cudaGetLastError();
+            ++c->gcd_kernels;
+            c->gcd_subproblems += (int64_t)nj * K;
         }
         std::vector<int32_t> pat(pat_w);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(pat.data(), d_pat, (size_t)pat_w * 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = sqf_copy(c, pat.data(), d_pat, (size_t)pat_w * 4, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "square-free modular stage", e);
         // ---- lucky primes: largest square-free degree, then the most common pattern
-        std::vector<int> retry;
+        gbr_parallel_for(nj, threads, [&](int lo, int hi) {
+            std::vector<std::pair<uint64_t, int>> cand_slots;
+            for (int q = lo; q < hi; ++q) {
+                const int j = pend[q];
+                SqfJob &x = J[q];
+                const int32_t *pq = pat.data() + x.pat_off;
+                // slots of the largest square-free degree, grouped by their degree pattern
+                int best = -1;
+                for (int sl = 0; sl < K; ++sl) {
+                    const int32_t *ps = pq + (int64_t)sl * (x.n + 2);
+                    if (ps[0] < 1) continue;
+                    int sd = 0;
+                    for (int i = 0; i < ps[0]; ++i) sd += ps[1 + i];
+                    best = std::max(best, sd);
+                }
+                cand_slots.clear();
+                for (int sl = 0; sl < K && best >= 0; ++sl) {
+                    const int32_t *ps = pq + (int64_t)sl * (x.n + 2);
+                    if (ps[0] < 1) continue;
+                    int sd = 0;
+                    uint64_t hsh = 1469598103934665603ull;
+                    for (int i = 0; i <= ps[0]; ++i) {
+                        if (i) sd += ps[i];
+                        hsh = (hsh ^ (uint32_t)ps[i]) * 1099511628211ull;
+                    }
+                    if (sd == best) cand_slots.push_back({hsh, sl});
+                }
+                std::sort(cand_slots.begin(), cand_slots.end());
+                // the longest run of one hash; slots whose pattern differs from the
+                // run's first (a hash collision) are left out
+                size_t rb = 0, rl = 0;
+                for (size_t i = 0; i < cand_slots.size();) {
+                    size_t k2 = i;
+                    while (k2 < cand_slots.size() && cand_slots[k2].first == cand_slots[i].first) ++k2;
+                    if (k2 - i > rl) {
+                        rb = i;
+                        rl = k2 - i;
+                    }
+                    i = k2;
+                }
+                const int32_t *rep = rl ? pq + (int64_t)cand_slots[rb].second * (x.n + 2) : nullptr;
+                std::vector<int> &lucky = H[j].lucky;
+                lucky.clear();
+                for (size_t i = rb; i < rb + rl; ++i) {
+                    const int32_t *ps = pq + (int64_t)cand_slots[i].second * (x.n + 2);
+                    if (std::equal(ps, ps + 1 + ps[0], rep)) lucky.push_back(cand_slots[i].second);
+                }
+                std::sort(lucky.begin(), lucky.end());
+                const std::vector<int> gpat = rep ? std::vector<int>(rep + 1, rep + 1 + rep[0]) : std::vector<int>();
+                const std::vector<int> *gp = rep ? &gpat : nullptr;
+                int dmax = 0, nfac = 0;
+                if (gp)
+                    for (int d : *gp) {
+                        dmax = std::max(dmax, d);
+                        nfac += d + 1;
+                    }
+                const int kneed = primes_for_bits(dmax + H[j].l2norm2 + 3.0);
+                if (!gp || (int)lucky.size() < kneed) {
+                    x.status = 2;
+                    continue;
+                }
+                H[j].pat = *gp;
+                lucky.resize(kneed);
+                x.status = 0;
+                x.lift_k = kneed;
+                x.lift_L = (31 * kneed + 31) / 32 + 1;
+                x.nfac = nfac;
+            }
+        });
+        std::vector<int> retry, lifted;
         int64_t lsel_w = 0, gtab_w = 0, lift_w = 0, lsign_w = 0, lift_items = 0;
         int KMx = 1, LMx = 1;
         for (int q = 0; q < nj; ++q) {
-            const int j = pend[q];
             SqfJob &x = J[q];
-            const int32_t *pq = pat.data() + x.pat_off;
             x.lift0 = lift_items;   // jobs that are not lifted keep an empty range here
-            int best = -1;
-            for (int sl = 0; sl < K; ++sl) {
-                const int32_t *ps = pq + (int64_t)sl * (x.n + 2);
-                if (ps[0] < 1) continue;
-                int sd = 0;
-                for (int i = 0; i < ps[0]; ++i) sd += ps[1 + i];
-                best = std::max(best, sd);
-            }
-            std::map<std::vector<int>, std::vector<int>> groups;
-            for (int sl = 0; sl < K && best >= 0; ++sl) {
-                const int32_t *ps = pq + (int64_t)sl * (x.n + 2);
-                if (ps[0] < 1) continue;
-                int sd = 0;
-                for (int i = 0; i < ps[0]; ++i) sd += ps[1 + i];
-                if (sd != best) continue;
-                groups[std::vector<int>(ps + 1, ps + 1 + ps[0])].push_back(sl);
-            }
-            const std::vector<int> *gp = nullptr, *gs = nullptr;
-            for (auto &kv : groups)
-                if (!gs || kv.second.size() > gs->size()) {
-                    gp = &kv.first;
-                    gs = &kv.second;
-                }
-            int dmax = 0, nfac = 0;
-            if (gp)
-                for (int d : *gp) {
-                    dmax = std::max(dmax, d);
-                    nfac += d + 1;
-                }
-            const int kneed = primes_for_bits(dmax + H[j].l2norm2 + 3.0);
-            if (!gs || (int)gs->size() < kneed) {
-                retry.push_back(j);
-                x.status = 2;
+            if (x.status != 0) {
+                retry.push_back(pend[q]);
                 continue;
             }
-            H[j].pat = *gp;
-            H[j].lucky.assign(gs->begin(), gs->begin() + kneed);
-            x.status = 0;
-            x.lift_k = kneed;
-            x.lift_L = (31 * kneed + 31) / 32 + 1;
-            x.nfac = nfac;
+            lifted.push_back(q);
             x.lsel_off = lsel_w;
             x.gtab_off = gtab_w;
             x.lift_off = lift_w;
             x.lsign_off = lsign_w;
-            lsel_w += kneed;
-            gtab_w += kneed + (int64_t)kneed * (kneed - 1) / 2;
-            lift_w += (int64_t)nfac * x.lift_L;
-            lsign_w += nfac;
-            lift_items += nfac;
-            KMx = std::max(KMx, kneed);
+            lsel_w += x.lift_k;
+            gtab_w += x.lift_k + (int64_t)x.lift_k * (x.lift_k - 1) / 2;
+            lift_w += (int64_t)x.nfac * x.lift_L;
+            lsign_w += x.nfac;
+            lift_items += x.nfac;
+            KMx = std::max(KMx, x.lift_k);
             LMx = std::max(LMx, x.lift_L);
         }
-        std::vector<int> lifted;
-        for (int q = 0; q < nj; ++q)
-            if (J[q].status == 0) lifted.push_back(q);
         if (!lifted.empty()) {
             std::vector<int32_t> lsel(lsel_w);
             for (int q : lifted)
@@ -676,11 +803,12 @@ static int sqf_batch_locked(gbr_ctx *c, int n, const gbr_bigpoly *in, gbr_sqf *o
             L.gtab = d_gtab;
             L.lift = d_lift;
             L.lsign = d_lsign;
-            e = cudaMemcpyAsync(d_jobs, J.data(), sizeof(SqfJob) * nj, cudaMemcpyHostToDevice, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(d_lsel, lsel.data(), (size_t)lsel_w * 4, cudaMemcpyHostToDevice, s);
+            e = sqf_copy(c, d_jobs, J.data(), sizeof(SqfJob) * nj, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) e = sqf_copy(c, d_lsel, lsel.data(), (size_t)lsel_w * 4, cudaMemcpyHostToDevice, s);
             if (e == cudaSuccess) {
                 k_sqf_garner<<<std::min(nj, 1024), 128, 0, s>>>(L);
                 e = cudaGetLastError();
+                ++c->gcd_kernels;
             }
             int block = 128;
             while (block > 32 && (size_t)(KMx + LMx) * block * 4 > 160 * 1024) block >>= 1;
@@ -690,120 +818,117 @@ static int sqf_batch_locked(gbr_ctx *c, int n, const gbr_bigpoly *in, gbr_sqf *o
                 k_sqf_lift<<<sqf_blocks((const void *)k_sqf_lift, block, lsm, (lift_items + block - 1) / block), block,
                              lsm, s>>>(L, KMx, LMx, lift_items);
                 e = cudaGetLastError();
+                ++c->gcd_kernels;
             }
             std::vector<uint32_t> hlift(lift_w);
             std::vector<int8_t> hlsign(lsign_w);
             int32_t herr = 0;
-            if (e == cudaSuccess) e = cudaMemcpyAsync(hlift.data(), d_lift, (size_t)lift_w * 4, cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(hlsign.data(), d_lsign, (size_t)lsign_w, cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, c->d_err, 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = sqf_copy(c, hlift.data(), d_lift, (size_t)lift_w * 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = sqf_copy(c, hlsign.data(), d_lsign, (size_t)lsign_w, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = sqf_copy(c, &herr, c->d_err, 4, cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "square-free lift", e);
             if (herr) return c->fail(GBR_EDEVICE, "square-free device-side consistency check failed");
-            // ---- primitive parts, unit; candidates for the exact check
+            // ---- primitive parts, unit, the check's coefficient bound (per job, in parallel)
+            const int nl = (int)lifted.size();
+            std::vector<char> okv(nl, 0);
+            std::vector<double> bitsv(nl, 0.0);
+            gbr_parallel_for(nl, threads, [&](int lo, int hi) {
+                bn::Scratch S;
+                for (int t = lo; t < hi; ++t) {
+                    const int q = lifted[t];
+                    SqfHost &h = H[pend[q]];
+                    h.fac.assign(h.pat.size(), FlatPoly());
+                    bool ok = true;
+                    int off = 0;
+                    bn::Big lcprod = bn::from_u64(1);
+                    for (size_t i = 0; i < h.pat.size() && ok; ++i) {
+                        const int d = h.pat[i];
+                        ok = primitive_part(hlift.data() + J[q].lift_off + (int64_t)off * J[q].lift_L,
+                                            hlsign.data() + J[q].lsign_off + off, d, J[q].lift_L, h.fac[i], S);
+                        off += d + 1;
+                        if (!ok) break;
+                        const bn::Big l = lead(h.fac[i]);
+                        for (size_t e3 = 0; e3 <= i; ++e3) lcprod = bn::mul(lcprod, l);
+                    }
+                    if (ok) ok = bn::divexact(h.lc, lcprod, h.u, S);
+                    okv[t] = ok;
+                    if (!ok) continue;
+                    // coefficient bound of u prod r_i^i: |u| prod ||r_i||_1^i
+                    double bits = bn::log2_mag(h.u.m);
+                    for (size_t i = 0; i < h.fac.size(); ++i) {
+                        const FlatPoly &f = h.fac[i];
+                        bits += (double)(i + 1) * log2_norms(f.deg + 1, [&](int k, const uint32_t *&x, size_t &n2) {
+                                    x = f.mag.data() + (size_t)k * f.L;
+                                    n2 = f.sign[k] ? bn::top(x, (size_t)f.L) : 0;
+                                }).l1;
+                    }
+                    bitsv[t] = std::max(bits, h.l2inf) + 2.0;
+                }
+            });
             std::vector<int> cand;
             double maxbits_v = 0.0;
-            for (int q : lifted) {
-                const int j = pend[q];
-                SqfHost &h = H[j];
-                h.fac.clear();
-                int off = 0;
-                bool ok = true;
-                bn::Big lcprod = bn::from_u64(1);
-                for (size_t i = 0; i < h.pat.size() && ok; ++i) {
-                    const int d = h.pat[i];
-                    std::vector<bn::Big> f(d + 1);
-                    std::vector<uint32_t> g;
-                    for (int t = 0; t <= d; ++t) {
-                        const int e2 = off + t;
-                        f[t] = bn::from_limbs(hlift.data() + J[q].lift_off + (int64_t)e2 * J[q].lift_L, J[q].lift_L,
-                                              hlsign[J[q].lsign_off + e2]);
-                        if (hlsign[J[q].lsign_off + e2] == 0) f[t] = bn::Big();
-                        g = bn::gcd_mag(g, f[t].m);
-                    }
-                    off += d + 1;
-                    if (g.empty() || f[d].s == 0) {
-                        ok = false;
-                        break;
-                    }
-                    bn::Big gb;
-                    gb.m = g;
-                    gb.s = f[d].s;   // also makes the leading coefficient positive
-                    for (int t = 0; t <= d; ++t) {
-                        bn::Big qt;
-                        if (f[t].s != 0 && !bn::divexact(f[t], gb, qt)) ok = false;
-                        f[t] = f[t].s == 0 ? bn::Big() : qt;
-                    }
-                    for (size_t e3 = 0; e3 <= i; ++e3) lcprod = bn::mul(lcprod, f[d]);
-                    h.fac.push_back(std::move(f));
-                }
-                if (ok) ok = bn::divexact(h.lc, lcprod, h.u);
-                if (!ok) {
-                    retry.push_back(j);
+            for (int t = 0; t < nl; ++t) {
+                if (!okv[t]) {
+                    retry.push_back(pend[lifted[t]]);
                     continue;
                 }
-                // coefficient bound of u prod r_i^i: |u| prod ||r_i||_1^i
-                double bits = bn::log2_mag(h.u.m);
-                for (size_t i = 0; i < h.fac.size(); ++i) {
-                    double mx = -1e300, s1 = 0.0;
-                    for (const auto &b : h.fac[i]) {
-                        if (b.s == 0) continue;
-                        const double l = bn::log2_mag(b.m);
-                        if (l > mx) {
-                            s1 = s1 * std::exp2(mx - l) + 1.0;
-                            mx = l;
-                        } else {
-                            s1 += std::exp2(l - mx);
-                        }
-                    }
-                    bits += (double)(i + 1) * (mx + std::log2(s1) + 1e-9);
-                }
-                maxbits_v = std::max(maxbits_v, std::max(bits, h.l2inf) + 2.0);
-                cand.push_back(q);
+                cand.push_back(lifted[t]);
+                maxbits_v = std::max(maxbits_v, bitsv[t]);
             }
             // ---- exact check: R = u prod r_i^i modulo enough primes
             if (!cand.empty()) {
                 const int Kv = primes_for_bits(maxbits_v);
                 if (Kv > NP) return c->fail(GBR_ELIMIT, "square-free check needs more than the table's primes");
+                const int nv = (int)cand.size();
                 int VL = 1, maxfac = 1;
-                for (int q : cand) {
-                    const SqfHost &h = H[pend[q]];
+                std::vector<int64_t> voff(nv + 1, 0);
+                for (int t = 0; t < nv; ++t) {
+                    const SqfHost &h = H[pend[cand[t]]];
                     VL = std::max(VL, (int)h.u.m.size());
-                    for (const auto &f : h.fac)
-                        for (const auto &b : f) VL = std::max(VL, (int)b.m.size());
+                    for (const auto &f : h.fac) VL = std::max(VL, f.L);
                     maxfac = std::max(maxfac, (int)h.fac.size());
                 }
-                std::vector<SqfJob> JV;
-                std::vector<uint32_t> hv;
-                std::vector<int32_t> hdeg;
-                int64_t vres = 0, vred = 0;
-                for (int q : cand) {
-                    const SqfHost &h = H[pend[q]];
-                    SqfJob x = J[q];
+                std::vector<SqfJob> JV(nv);
+                int64_t vres = 0;
+                for (int t = 0; t < nv; ++t) {
+                    const SqfHost &h = H[pend[cand[t]]];
+                    int ncoef = 1;
+                    for (const auto &f : h.fac) ncoef += f.deg + 1;
+                    SqfJob x = J[cand[t]];
                     x.status = 0;
                     x.res_off = vres;
-                    x.red0 = vred;
+                    x.red0 = vres;
                     x.ver_L = VL;
                     x.nfac = (int)h.fac.size();
-                    x.ver_off = (int64_t)hv.size();
+                    x.ver_off = voff[t];
                     vres += (int64_t)Kv * (x.n + 1);
-                    vred += (int64_t)Kv * (x.n + 1);
-                    std::vector<const bn::Big *> all = {&h.u};
-                    for (const auto &f : h.fac)
-                        for (const auto &b : f) all.push_back(&b);
-                    for (const bn::Big *b : all)
-                        for (int l = 0; l < VL; ++l) hv.push_back(l < (int)b->m.size() ? b->m[l] : 0u);
-                    const size_t sw = (all.size() + 3) / 4;
-                    const size_t base = hv.size();
-                    hv.resize(base + sw, 0u);
-                    int8_t *sg = reinterpret_cast<int8_t *>(hv.data() + base);
-                    for (size_t t = 0; t < all.size(); ++t) sg[t] = (int8_t)all[t]->s;
-                    std::vector<int32_t> dg(maxfac + 1, 0);
-                    for (size_t i = 0; i < h.fac.size(); ++i) dg[i] = (int)h.fac[i].size() - 1;
-                    hdeg.insert(hdeg.end(), dg.begin(), dg.end());
-                    JV.push_back(x);
+                    voff[t + 1] = voff[t] + (int64_t)ncoef * VL + (ncoef + 3) / 4;
+                    JV[t] = x;
                 }
-                const int nv = (int)JV.size();
+                std::vector<uint32_t> hv(voff[nv], 0u);
+                std::vector<int32_t> hdeg((size_t)nv * (maxfac + 1), 0);
+                gbr_parallel_for(nv, threads, [&](int lo, int hi) {
+                    for (int t = lo; t < hi; ++t) {
+                        const SqfHost &h = H[pend[cand[t]]];
+                        uint32_t *w = hv.data() + voff[t];
+                        int ncoef = 1;
+                        for (const auto &f : h.fac) ncoef += f.deg + 1;
+                        int8_t *sg = reinterpret_cast<int8_t *>(w + (int64_t)ncoef * VL);
+                        std::copy(h.u.m.begin(), h.u.m.end(), w);
+                        sg[0] = (int8_t)h.u.s;
+                        int k = 1;
+                        for (size_t i = 0; i < h.fac.size(); ++i) {
+                            const FlatPoly &f = h.fac[i];
+                            hdeg[(size_t)t * (maxfac + 1) + i] = f.deg;
+                            for (int e2 = 0; e2 <= f.deg; ++e2, ++k) {
+                                std::copy(f.mag.begin() + (size_t)e2 * f.L, f.mag.begin() + (size_t)(e2 + 1) * f.L,
+                                          w + (int64_t)k * VL);
+                                sg[k] = f.sign[e2];
+                            }
+                        }
+                    }
+                });
                 SqfJob *d_jv = (SqfJob *)B.get(sizeof(SqfJob) * nv);
                 uint32_t *d_vres = (uint32_t *)B.get((size_t)vres * 4);
                 uint32_t *d_ver = (uint32_t *)B.get(hv.size() * 4);
@@ -821,13 +946,14 @@ static int sqf_batch_locked(gbr_ctx *c, int n, const gbr_bigpoly *in, gbr_sqf *o
                 V.ver_deg = d_vdeg;
                 V.ver_fail = d_fail;
                 V.max_fac = maxfac;
-                e = cudaMemcpyAsync(d_jv, JV.data(), sizeof(SqfJob) * nv, cudaMemcpyHostToDevice, s);
-                if (e == cudaSuccess) e = cudaMemcpyAsync(d_ver, hv.data(), hv.size() * 4, cudaMemcpyHostToDevice, s);
-                if (e == cudaSuccess) e = cudaMemcpyAsync(d_vdeg, hdeg.data(), hdeg.size() * 4, cudaMemcpyHostToDevice, s);
+                e = sqf_copy(c, d_jv, JV.data(), sizeof(SqfJob) * nv, cudaMemcpyHostToDevice, s);
+                if (e == cudaSuccess) e = sqf_copy(c, d_ver, hv.data(), hv.size() * 4, cudaMemcpyHostToDevice, s);
+                if (e == cudaSuccess) e = sqf_copy(c, d_vdeg, hdeg.data(), hdeg.size() * 4, cudaMemcpyHostToDevice, s);
                 if (e == cudaSuccess) e = cudaMemsetAsync(d_fail, 0, (size_t)nv * 4, s);
                 if (e == cudaSuccess) {
-                    k_sqf_reduce<<<sqf_blocks((const void *)k_sqf_reduce, 256, 0, (vred + 255) / 256), 256, 0, s>>>(V, vred);
+                    k_sqf_reduce<<<sqf_blocks((const void *)k_sqf_reduce, 256, 0, (vres + 255) / 256), 256, 0, s>>>(V, vres);
                     e = cudaGetLastError();
+                    ++c->gcd_kernels;
                 }
                 const int nwv = sqf_warps(3, stride);
                 if (nwv < 1) return c->fail(GBR_ELIMIT, "square-free input degree too large for shared memory");
@@ -837,9 +963,11 @@ static int sqf_batch_locked(gbr_ctx *c, int n, const gbr_bigpoly *in, gbr_sqf *o
                                               ((int64_t)nv * Kv + nwv - 1) / nwv),
                                    nwv * 32, smem, s>>>(V, stride);
                     e = cudaGetLastError();
+                    ++c->gcd_kernels;
+                    c->gcd_subproblems += (int64_t)nv * Kv;
                 }
                 std::vector<int32_t> fail(nv);
-                if (e == cudaSuccess) e = cudaMemcpyAsync(fail.data(), d_fail, (size_t)nv * 4, cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = sqf_copy(c, fail.data(), d_fail, (size_t)nv * 4, cudaMemcpyDeviceToHost, s);
                 if (e == cudaSuccess) e = cudaStreamSynchronize(s);
                 if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "square-free check", e);
                 for (int t = 0; t < nv; ++t) {
@@ -854,23 +982,44 @@ static int sqf_batch_locked(gbr_ctx *c, int n, const gbr_bigpoly *in, gbr_sqf *o
         pend.erase(std::unique(pend.begin(), pend.end()), pend.end());
         K *= 2;
     }
-    // ---- results: unit and factors of every input share one host block
+    // ---- results: the units and factors of all inputs share one refcounted host block
+    std::vector<int64_t> roff(n + 1, 0);
+    for (int j = 0; j < n; ++j) roff[j + 1] = roff[j] + 1 + (int64_t)H[j].fac.size();
+    std::vector<gbr_bigpoly> res(roff[n]);
     for (int j = 0; j < n; ++j) {
-        SqfHost &h = H[j];
-        std::vector<bn::Big> uv = {h.u};
-        std::vector<const std::vector<bn::Big> *> polys = {&uv};
-        for (const auto &f : h.fac) polys.push_back(&f);
-        std::vector<gbr_bigpoly> res;
-        if (!big_results(polys, res)) return c->fail(GBR_ENOMEM, "host result allocation");
-        out[j].unit = res[0];
-        out[j].count = (int32_t)h.fac.size();
-        out[j].factors = nullptr;
-        if (out[j].count) {
-            out[j].factors = (gbr_bigpoly *)std::malloc(sizeof(gbr_bigpoly) * out[j].count);
-            if (!out[j].factors) return c->fail(GBR_ENOMEM, "host result allocation");
-            for (int i = 0; i < out[j].count; ++i) out[j].factors[i] = res[1 + i];
+        const SqfHost &h = H[j];
+        gbr_bigpoly *r = res.data() + roff[j];
+        r[0].deg = h.u.s ? 0 : -1;
+        r[0].limbs = std::max<int>(1, (int)h.u.m.size());
+        for (size_t i = 0; i < h.fac.size(); ++i) {
+            r[1 + i].deg = h.fac[i].deg;
+            r[1 + i].limbs = h.fac[i].L;
         }
     }
+    for (int j = 0; j < n; ++j)
+        if (!H[j].fac.empty()) {
+            out[j].factors = (gbr_bigpoly *)std::malloc(sizeof(gbr_bigpoly) * H[j].fac.size());
+            if (!out[j].factors) return c->fail(GBR_ENOMEM, "host result allocation");
+            out[j].count = (int32_t)H[j].fac.size();
+            for (int i = 0; i < out[j].count; ++i) out[j].factors[i] = gbr_bigpoly{-1, 0, nullptr, nullptr};
+        }
+    if (!gbr_alloc_results(res.data(), (int)res.size())) return c->fail(GBR_ENOMEM, "host result allocation");
+    gbr_parallel_for(n, threads, [&](int lo, int hi) {
+        for (int j = lo; j < hi; ++j) {
+            const SqfHost &h = H[j];
+            gbr_bigpoly *r = res.data() + roff[j];
+            if (h.u.s) {
+                for (int l = 0; l < r[0].limbs; ++l) r[0].mag[l] = l < (int)h.u.m.size() ? h.u.m[l] : 0u;
+                r[0].sign[0] = (int8_t)h.u.s;
+            }
+            for (size_t i = 0; i < h.fac.size(); ++i) {
+                std::copy(h.fac[i].mag.begin(), h.fac[i].mag.end(), r[1 + i].mag);
+                std::copy(h.fac[i].sign.begin(), h.fac[i].sign.end(), r[1 + i].sign);
+                out[j].factors[i] = r[1 + i];
+            }
+            out[j].unit = r[0];
+        }
+    });
     return GBR_OK;
 }
 
@@ -888,8 +1037,25 @@ extern "C" int gbr_squarefree_batch(gbr_ctx *c, int n, const gbr_bigpoly *in, gb
     std::lock_guard<std::mutex> lk(c->mu);
     cudaSetDevice(c->device);
     int st;
+    const auto t0 = std::chrono::steady_clock::now();
+    if (c->stats_on) cudaEventRecord(c->ev[0], c->stream);
     try {
         st = sqf_batch_locked(c, n, in, out);
+        if (c->stats_on) {
+            // the whole call on the context's stream, as for a gcd call
+            cudaEventRecord(c->ev[1], c->stream);
+            cudaEventSynchronize(c->ev[1]);
+            gbr_stats g{};
+            float ms = 0;
+            cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+            g.gcd_ms = ms;
+            g.total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            g.kernels = c->gcd_kernels;
+            g.subproblems = c->gcd_subproblems;
+            g.h2d_bytes = c->gcd_h2d;
+            g.d2h_bytes = c->gcd_d2h;
+            c->stats = g;
+        }
     } catch (std::bad_alloc &) {
         st = c->fail(GBR_ENOMEM, "host allocation");
     }

@@ -133,6 +133,15 @@ def test_projection_resultant_two_circles(ctx):
     assert len(got[1]) >= 2 and len(got[1][1]) > 1     # a squared factor is present
 
 
+def test_projection_resultant_three_conics(ctx):
+    # a product of three circles/ellipses from the curve generator: R has a
+    # squared factor for the intersection points and the x-extreme points
+    f, _ = W.conic_curves(8, ncon=3, rbits=4, nterms=0)
+    fy = [[(j + 1) * c for c in f[j + 1]] for j in range(len(f) - 1)]
+    R = _trim(O.res_subres(f, fy))
+    assert ctx.squarefree(R) == _oracle(R)
+
+
 def test_batch_mixed(ctx):
     R, _ = W.sqf_batch(11, 24, degs=((0, 12), (0, 6), (0, 3)), bits=12)
     R = R + [[], [5], [0, 0, 3], [-1, 0, 1]]
