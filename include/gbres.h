@@ -242,6 +242,19 @@ typedef struct gbr_resident gbr_resident;
 int gbr_upload_pairs(gbr_ctx *ctx, int n, const gbr_bipoly *f, const gbr_bipoly *g, int var, int disc,
                      gbr_resident **out);
 int gbr_run_resident(gbr_ctx *ctx, gbr_resident *r);
+
+/* The resultants of an arrangement of n curves (Section 3, curve-pair analysis:
+ * every pair of curves C, D needs R_C = res(f_C, d f_C / dy), R_D and R_CD =
+ * res(f_C, f_D); an arrangement of n curves needs n(n + 1)/2 of them).  Each
+ * curve is uploaded once; the jobs are
+ *   q = i                       res_var(f[i], d f[i] / dvar),   0 <= i < n
+ *   q = n + pair(i, j)          res_var(f[i], f[j]),            0 <= i < j < n
+ * with pair(i, j) = i (2n - i - 1) / 2 + (j - i - 1) (pairs in row-major order).
+ * gbr_upload_arrangement makes a resident batch of those n(n + 1)/2 jobs (run
+ * and fetch it as above); gbr_arrangement_resultants runs it once and writes
+ * out[0 .. n(n + 1)/2).  GBR_ELIMIT when n(n + 1)/2 exceeds 2^29. */
+int gbr_upload_arrangement(gbr_ctx *ctx, int n, const gbr_bipoly *f, int var, gbr_resident **out);
+int gbr_arrangement_resultants(gbr_ctx *ctx, int n, const gbr_bipoly *f, int var, gbr_bigpoly *out);
 int gbr_fetch_resident(gbr_ctx *ctx, gbr_resident *r, int first, int count, gbr_bigpoly *out);
 void gbr_free_resident(gbr_ctx *ctx, gbr_resident *r);
 

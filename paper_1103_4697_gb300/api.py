@@ -298,6 +298,34 @@ class Context:
                                          var, int(disc), C.byref(h)), self.handle)
         return Resident(self, h, len(df))
 
+    # ------------------------------------------------------------- arrangements
+    def arrangement_resultants(self, fs, var: int = 1) -> tuple[list[list[int]], dict]:
+        """gbr_arrangement_resultants: ([res(f_i, d f_i/dvar) for i], {(i, j): res(f_i, f_j)
+        for i < j}) for the curves fs (Section 3, curve-pair analysis)."""
+        keep = _Packed()
+        df = pack_bipolys(fs, keep)
+        n = len(df)
+        nj = n * (n + 1) // 2
+        outs = (N.BigPoly * max(nj, 1))()
+        N.check(N.lib().gbr_arrangement_resultants(self.handle, n, _ptr(df), var, outs), self.handle)
+        res = self._collect(outs, nj)
+        pairs, q = {}, n
+        for i in range(n):
+            for j in range(i + 1, n):
+                pairs[(i, j)] = res[q]
+                q += 1
+        return res[:n], pairs
+
+    def upload_arrangement(self, fs, var: int = 1) -> Resident:
+        """gbr_upload_arrangement: a resident batch of the n(n + 1)/2 arrangement jobs
+        (the n discriminant-type resultants first, then the pairs in row-major order)."""
+        keep = _Packed()
+        df = pack_bipolys(fs, keep)
+        h = C.c_void_p()
+        N.check(N.lib().gbr_upload_arrangement(self.handle, len(df), _ptr(df), var, C.byref(h)), self.handle)
+        n = len(df)
+        return Resident(self, h, n * (n + 1) // 2)
+
     # ------------------------------------------------------------- gcd
     def gcd_batch(self, ps, qs) -> list[list[int]]:
         keep = _Packed()

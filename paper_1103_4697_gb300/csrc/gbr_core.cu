@@ -860,34 +860,52 @@ static PolyDesc view_of(const gbr_bipoly *p, int var, int64_t off) {
 
 // ------------------------------------------------------------------ resident batches
 
-extern "C" int gbr_upload_pairs(gbr_ctx *c, int n, const gbr_bipoly *f, const gbr_bipoly *g, int var, int disc,
-                                gbr_resident **out) {
-    if (!c || !out || n < 0 || (var != 0 && var != 1) || (n > 0 && !f) || (n > 0 && !disc && !g))
-        return GBR_EINVAL;
+// One resident batch over `ncurve` distinct polynomials, each uploaded once, and
+// `njob` jobs: job q is res_var(curve[jf[q]], curve[jg[q]]), or, when jg[q] < 0,
+// res_var(curve[jf[q]], d curve[jf[q]] / d var) (the derivative is taken by the
+// kernels from f's coefficients).  Jobs of both kinds mix freely in one batch.
+static int upload_jobs_locked(gbr_ctx *c, int ncurve, const gbr_bipoly *const *curves, int njob, const int32_t *jf,
+                              const int32_t *jg, int var, gbr_resident **out) {
     *out = nullptr;
-    std::lock_guard<std::mutex> lk(c->mu);
-    cudaSetDevice(c->device);
     gbr_resident *r = new (std::nothrow) gbr_resident();
     if (!r) return GBR_ENOMEM;
+    const int n = njob;
     r->n = n;
     r->var = var;
-    r->disc = disc ? 1 : 0;
+    int ndisc = 0;
     int64_t words = 0;
     int64_t rowdeg = 0;
+    std::vector<PolyDesc> cv;
+    std::vector<char> used;
     try {
-        r->h_desc.resize(n);
-        for (int i = 0; i < n; ++i) {
-            int st = check_bipoly(&f[i]);
-            if (!st && !disc) st = check_bipoly(&g[i]);
+        cv.resize(ncurve);
+        used.assign(ncurve, 0);
+        for (int q = 0; q < n; ++q) {
+            if (jf[q] < 0 || jf[q] >= ncurve || jg[q] >= ncurve) {
+                delete r;
+                return c->fail(GBR_EINVAL, "job refers to a polynomial outside the batch");
+            }
+            used[jf[q]] = 1;
+            if (jg[q] >= 0) used[jg[q]] = 1;
+        }
+        for (int i = 0; i < ncurve; ++i) {
+            if (!used[i]) continue;
+            const int st = check_bipoly(curves[i]);
             if (st) {
                 delete r;
                 return c->fail(st, "bad polynomial descriptor");
             }
-            PairDesc &D = r->h_desc[i];
-            D.disc = r->disc;
+            cv[i] = view_of(curves[i], var, words);
+            words += bipoly_words(curves[i]);
+        }
+        r->h_desc.resize(n);
+        for (int q = 0; q < n; ++q) {
+            PairDesc &D = r->h_desc[q];
+            const bool disc = jg[q] < 0;
+            ndisc += disc;
+            D.disc = disc ? 1 : 0;
             D.pad = 0;
-            D.f = view_of(&f[i], var, words);
-            words += bipoly_words(&f[i]);
+            D.f = cv[jf[q]];
             D.f.rowdeg_off = (int32_t)rowdeg;
             rowdeg += D.f.rows + 1;
             if (disc) {
@@ -896,8 +914,7 @@ extern "C" int gbr_upload_pairs(gbr_ctx *c, int n, const gbr_bipoly *f, const gb
                 D.g.rowdeg_off = (int32_t)rowdeg;
                 rowdeg += D.f.rows;
             } else {
-                D.g = view_of(&g[i], var, words);
-                words += bipoly_words(&g[i]);
+                D.g = cv[jg[q]];
                 D.g.rowdeg_off = (int32_t)rowdeg;
                 rowdeg += D.g.rows + 1;
             }
@@ -910,6 +927,7 @@ extern "C" int gbr_upload_pairs(gbr_ctx *c, int n, const gbr_bipoly *f, const gb
         delete r;
         return GBR_ENOMEM;
     }
+    r->disc = n > 0 && ndisc == n ? 1 : 0;
     r->coef_words = words;
     r->rowdeg_n = rowdeg;
     r->upload_bytes = words * 8 + (int64_t)sizeof(PairDesc) * n;
@@ -929,12 +947,10 @@ extern "C" int gbr_upload_pairs(gbr_ctx *c, int n, const gbr_bipoly *f, const gb
         gbr_free_resident_locked(c, r);
         return c->fail(GBR_ENOMEM, "pinned host staging");
     }
-    gbr_parallel_for(n, host_threads(), [&](int lo, int hi) {
-        for (int i = lo; i < hi; ++i) {
-            int64_t pos = r->h_desc[i].f.off;
-            std::memcpy(h + pos, f[i].coef, bipoly_words(&f[i]) * 8);
-            if (!disc) std::memcpy(h + r->h_desc[i].g.off, g[i].coef, bipoly_words(&g[i]) * 8);
-        }
+    gbr_parallel_for(ncurve, host_threads(), [&](int lo, int hi) {
+        for (int i = lo; i < hi; ++i)
+            if (used[i])
+                std::memcpy(h + cv[i].off, curves[i]->coef, bipoly_words(curves[i]) * 8);
     });
     cudaError_t e = cudaSuccess;
     if (bytes) e = cudaMemcpyAsync(r->d_coef, h, bytes, cudaMemcpyHostToDevice, c->stream);
@@ -947,6 +963,58 @@ extern "C" int gbr_upload_pairs(gbr_ctx *c, int n, const gbr_bipoly *f, const gb
     }
     *out = r;
     return GBR_OK;
+}
+
+extern "C" int gbr_upload_pairs(gbr_ctx *c, int n, const gbr_bipoly *f, const gbr_bipoly *g, int var, int disc,
+                                gbr_resident **out) {
+    if (!c || !out || n < 0 || (var != 0 && var != 1) || (n > 0 && !f) || (n > 0 && !disc && !g))
+        return GBR_EINVAL;
+    *out = nullptr;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    try {
+        // polynomials: f[0..n), then g[0..n) unless disc
+        const int nc = disc ? n : 2 * n;
+        std::vector<const gbr_bipoly *> curves(nc);
+        std::vector<int32_t> jf(n), jg(n);
+        for (int i = 0; i < n; ++i) {
+            curves[i] = &f[i];
+            if (!disc) curves[n + i] = &g[i];
+            jf[i] = i;
+            jg[i] = disc ? -1 : n + i;
+        }
+        return upload_jobs_locked(c, nc, curves.data(), n, jf.data(), jg.data(), var, out);
+    } catch (std::bad_alloc &) {
+        return GBR_ENOMEM;
+    }
+}
+
+extern "C" int gbr_upload_arrangement(gbr_ctx *c, int n, const gbr_bipoly *f, int var, gbr_resident **out) {
+    if (!c || !out || n < 0 || (var != 0 && var != 1) || (n > 0 && !f)) return GBR_EINVAL;
+    if ((int64_t)n * (n + 1) / 2 > INT32_MAX / 4) return GBR_ELIMIT;
+    *out = nullptr;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    try {
+        const int nj = n * (n + 1) / 2;
+        std::vector<const gbr_bipoly *> curves(n);
+        std::vector<int32_t> jf(nj), jg(nj);
+        for (int i = 0; i < n; ++i) {
+            curves[i] = &f[i];
+            jf[i] = i;
+            jg[i] = -1;
+        }
+        int q = n;
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) {
+                jf[q] = i;
+                jg[q] = j;
+                ++q;
+            }
+        return upload_jobs_locked(c, n, curves.data(), nj, jf.data(), jg.data(), var, out);
+    } catch (std::bad_alloc &) {
+        return GBR_ENOMEM;
+    }
 }
 
 void gbr_free_resident_locked(gbr_ctx *c, gbr_resident *r) {
@@ -1047,7 +1115,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     for (int q = 0; q < n; ++q) {
         const PairBound &b = hb[q];
         PairPlan &p = plan[q];
-        p.disc = r->disc;
+        p.disc = r->h_desc[q].disc;
         p.rowdeg_f = r->h_desc[q].f.rowdeg_off;
         p.rowdeg_g = r->h_desc[q].g.rowdeg_off;
         p.pmap_off = -1;
@@ -1775,6 +1843,29 @@ static int res_batch_impl(gbr_ctx *c, int n, const gbr_bipoly *f, const gbr_bipo
         if (c->stream) cudaStreamSynchronize(c->stream);
         gbr_free_resident_locked(c, r);
     }
+    return st;
+}
+
+extern "C" int gbr_arrangement_resultants(gbr_ctx *c, int n, const gbr_bipoly *f, int var, gbr_bigpoly *out) {
+    if (!c || n < 0 || (n && (!out || !f))) return GBR_EINVAL;
+    if ((int64_t)n * (n + 1) / 2 > INT32_MAX / 4) return GBR_ELIMIT;
+    const int nj = n * (n + 1) / 2;
+    for (int i = 0; i < nj; ++i) out[i] = gbr_bigpoly{-1, 0, nullptr, nullptr};
+    gbr_resident *r = nullptr;
+    int st = gbr_upload_arrangement(c, n, f, var, &r);
+    if (st) return st;
+    r->oneshot = true;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    try {
+        st = gbr_run_resident_locked(c, r);
+        c->stats.h2d_bytes += r->upload_bytes;
+        if (!st) st = gbr_fetch_resident_locked(c, r, 0, nj, out);
+    } catch (std::bad_alloc &) {
+        st = c->fail(GBR_ENOMEM, "host allocation");
+    }
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    gbr_free_resident_locked(c, r);
     return st;
 }
 

@@ -83,6 +83,8 @@ SIGNATURES = {
     "gbr_upload_pairs": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
                                    C.POINTER(C.c_void_p)]),
     "gbr_run_resident": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "gbr_upload_arrangement": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
+    "gbr_arrangement_resultants": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(BigPoly)]),
     "gbr_fetch_resident": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.POINTER(BigPoly)]),
     "gbr_free_resident": (None, [C.c_void_p, C.c_void_p]),
     "gbr_free_result": (None, [C.c_void_p, C.POINTER(BigPoly)]),

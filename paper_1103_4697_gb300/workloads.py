@@ -310,6 +310,27 @@ def conic_curves(seed: int = 4, ncon: int = 8, rbits: int = 10, nterms: int = 16
     return f, g
 
 
+def arrangement_curves(seed: int = 7, n: int = 90, d: int = 8, bits: int = 12, conic_frac: float = 0.25,
+                       rbits: int = 6):
+    """An arrangement of n curves for the curve-pair analysis (Section 3): a fraction
+    `conic_frac` are products of d/2 circles/axis-parallel ellipses with integer centres
+    and radii in [-2^rbits, 2^rbits] (singular where the conics meet, like the paper's
+    circle families), the others dense random curves of total degree d with `bits`-bit
+    coefficients (non-zero y^d term, so the y-degree is d)."""
+    st = Stream(seed, 3)
+    curves = []
+    for _ in range(n):
+        if st.uniform01(1)[0] < conic_frac:
+            f, _g = conic_curves(int(st.u64(1)[0] >> np.uint64(33)), ncon=max(1, d // 2), rbits=rbits, nterms=0,
+                                 gdeg=1, gbits=2)
+        else:
+            f = dense_total_degree(st, d, bits)
+            if f[d][0] == 0:
+                f[d][0] = _nonzero(st, bits)
+        curves.append(f)
+    return curves
+
+
 @dataclass
 class Request:
     t_arrive: float
