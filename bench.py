@@ -436,6 +436,9 @@ def run_config(args) -> None:
             64-bit coefficients: res_y(f, g) and res_y(f, f_y), one call each;
     serve   Poisson streams of mixed requests at 0.5, 0.8 and 0.95 of the measured capacity;
     gcd     the 4096 gcd jobs alone, through the C ABI with packed host buffers;
+    arrangement  the n(n+1)/2 resultants of an arrangement of 90 curves (Section 3:
+            res(f, f_y) per curve, res(f, g) per pair; 4095 jobs) in one pass, then the
+            square-free factorisation of all of them (Section 2.1);
     sqf     square-free factorisation R = u prod r_i^i (Section 2.1) of 2048 planted
             projection-resultant-shaped polynomials, through the C ABI, and of
             R = res_y(f, f_y) of the conic-product curve (the path's own output)."""
@@ -542,6 +545,65 @@ def run_config(args) -> None:
         out["gcd_stats"] = {k: gst[k] for k in ("gcd_ms", "total_ms", "kernels", "subproblems", "h2d_bytes",
                                                 "d2h_bytes")}
         out["workload"] = "4096 gcds deg 30..200, planted degree-5 factor, 8..32-bit cofactors (seed 3)"
+    elif args.config == "arrangement":
+        NC = 90
+        curves = W.arrangement_curves(7, n=NC, d=8, bits=12, conic_frac=0.25, rbits=6)
+        NJ = NC * (NC + 1) // 2
+        keep = api._Packed()
+        df = api.pack_bipolys(curves, keep)
+        ctx.set_option(N.OPT_STATS, 1)
+        L = N.lib()
+        outs = (N.BigPoly * NJ)()
+        times = []
+        for it in range(6):
+            t0 = time.perf_counter()
+            N.check(L.gbr_arrangement_resultants(ctx.handle, NC, api._ptr(df), 1, outs), ctx.handle)
+            times.append(time.perf_counter() - t0)
+            if it < 5:
+                for i in range(NJ):
+                    L.gbr_free_result(ctx.handle, C.byref(outs[i]))
+        sec = statistics.median(times[1:])
+        allres = ctx._collect(outs, NJ)
+        out["arrangement_jobs_per_s_e2e"] = NJ / sec
+        out["arrangement_ms_per_call"] = sec * 1e3
+        res = ctx.upload_arrangement(curves)
+        for _ in range(3):
+            res.run()
+        rt = []
+        for _ in range(10):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res.run()
+            rt.append(time.perf_counter() - t0)
+        st = ctx.stats()
+        res.free()
+        out["arrangement_jobs_per_s_resident"] = NJ / statistics.median(rt)
+        out["resident_stages_ms"] = {k: st[k] for k in ("bounds_ms", "reduce_ms", "evalres_ms", "interp_ms", "crt_ms")}
+        # projection phase: square-free factorisation of every resultant of the arrangement
+        sk = api._Packed()
+        arr = api.pack_bigpolys(allres, sk)
+        souts = (N.Sqf * NJ)()
+        stimes = []
+        for it in range(4):
+            t0 = time.perf_counter()
+            N.check(L.gbr_squarefree_batch(ctx.handle, NJ, arr, souts), ctx.handle)
+            stimes.append(time.perf_counter() - t0)
+            counts = [souts[i].count for i in range(NJ)]
+            for i in range(NJ):
+                L.gbr_free_sqf(ctx.handle, C.byref(souts[i]))
+        out["sqf_of_all_ms"] = statistics.median(stimes[1:]) * 1e3
+        out["resultants_with_repeated_factors"] = sum(1 for k in counts if k >= 2)
+        degs = [len(r) - 1 for r in allres]
+        bits = [max(abs(c) for c in r).bit_length() if r else 0 for r in allres]
+        out["result_degree_max"] = max(degs)
+        out["result_bits_max"] = max(bits)
+        t = time.perf_counter()
+        O.res_subres(curves[0], curves[1])
+        O.disc_res(curves[2])
+        out["oracle_jobs_per_s_1core"] = 2 / (time.perf_counter() - t)
+        out["workload"] = ("arrangement of 90 curves (seed 7): 25% products of 4 circles/ellipses (radii/centres "
+                           "in [-64, 64]), 75% dense total degree 8 with 12-bit coefficients; 90 res(f, f_y) + "
+                           "4005 res(f, g) per pass")
     elif args.config == "sqf":
         NS = 2048
         R, _ = W.sqf_batch(6, NS)
@@ -601,7 +663,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mem-gb", type=int, default=24)
     ap.add_argument("--pairs", type=int, default=PAIRS, help="pairs per GPU (smaller only for profiling)")
-    ap.add_argument("--config", choices=["headline", "small", "deg20", "mixed", "conic", "serve", "gcd", "sqf"],
+    ap.add_argument("--config", choices=["headline", "small", "deg20", "mixed", "conic", "serve", "gcd", "sqf",
+                                                 "arrangement"],
                     default="headline", help="other workloads print their own JSON line")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--no-serve", action="store_true")

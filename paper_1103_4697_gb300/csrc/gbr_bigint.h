@@ -178,6 +178,77 @@ inline uint64_t gcd64(uint64_t a, uint64_t b) {
     return a;
 }
 
+// the 62 bits of x starting at bit `shift` (bits beyond the top read as 0)
+inline uint64_t bits62(const Limbs &x, size_t shift) {
+    const size_t w = shift >> 5, o = shift & 31;
+    unsigned __int128 t = 0;
+    for (int k = 2; k >= 0; --k) {
+        const size_t i = w + (size_t)k;
+        t = (t << 32) | (i < x.size() ? x[i] : 0u);
+    }
+    return (uint64_t)(t >> o) & ((1ull << 62) - 1);
+}
+
+// r = A x + B y for the non-negative result of a Lehmer step (A, B of opposite
+// signs or zero, |A|, |B| < 2^62)
+inline void lin_comb(const Limbs &x, int64_t A, const Limbs &y, int64_t B, Limbs &r) {
+    const size_t n = std::max(x.size(), y.size());
+    r.assign(n + 2, 0u);
+    __int128 acc = 0;
+    for (size_t i = 0; i < n + 2; ++i) {
+        if (i < x.size()) acc += (__int128)A * x[i];
+        if (i < y.size()) acc += (__int128)B * y[i];
+        r[i] = (uint32_t)(uint64_t)acc;
+        acc >>= 32;   // arithmetic shift: floor division by 2^32
+    }
+    r.resize(top(r.data(), r.size()));
+}
+
+// a <- gcd(a, b) of trimmed magnitudes (b is destroyed) by Lehmer's algorithm
+// (Knuth, TAOCP vol. 2, 4.5.2, Algorithm L) on 62-bit leading parts: single-word
+// quotient steps collected in a 2x2 cofactor matrix, applied to the full numbers
+// once the word quotients become uncertain; word Euclid at the end
+inline void gcd_lehmer(Limbs &a, Limbs &b, Scratch &S) {
+    if (cmp_mag(a.data(), a.size(), b.data(), b.size()) < 0) a.swap(b);
+    while (b.size() > 2) {
+        const size_t abits = 32 * a.size() - (size_t)__builtin_clz(a.back());
+        const size_t shift = abits - 62;
+        int64_t ah = (int64_t)bits62(a, shift), bh = (int64_t)bits62(b, shift);
+        int64_t A = 1, B = 0, C = 0, D = 1;
+        for (;;) {
+            if (bh + C == 0 || bh + D == 0) break;
+            const int64_t q = (ah + A) / (bh + C);
+            if (q != (ah + B) / (bh + D)) break;
+            int64_t t = A - q * C;
+            A = C;
+            C = t;
+            t = B - q * D;
+            B = D;
+            D = t;
+            t = ah - q * bh;
+            ah = bh;
+            bh = t;
+        }
+        if (B == 0) {   // no single-word step was certain: one full division
+            divmod_mag(a, b, S.q, S.r, S);
+            a.swap(b);
+            b.swap(S.r);
+        } else {
+            lin_comb(a, A, b, B, S.q);
+            lin_comb(a, C, b, D, S.r);
+            a.swap(S.q);
+            b.swap(S.r);
+        }
+    }
+    if (b.empty()) return;
+    const uint64_t bv = (uint64_t)b[0] | (b.size() > 1 ? (uint64_t)b[1] << 32 : 0ull);
+    uint64_t rem = 0;
+    for (size_t i = a.size(); i-- > 0;) rem = (uint64_t)((((unsigned __int128)rem << 32) | a[i]) % bv);
+    const uint64_t d = gcd64(bv, rem);
+    a.assign({(uint32_t)d, (uint32_t)(d >> 32)});
+    a.resize(top(a.data(), a.size()));
+}
+
 // g <- gcd(g, x) for a trimmed g and the limb slice x (n limbs, maybe with
 // leading zeros); g = 0 (empty) is the identity
 inline void gcd_into(Limbs &g, const uint32_t *x, size_t n, Scratch &S) {
@@ -202,11 +273,7 @@ inline void gcd_into(Limbs &g, const uint32_t *x, size_t n, Scratch &S) {
     }
     S.a = g;
     S.b.assign(x, x + n);
-    while (!S.b.empty()) {
-        divmod_mag(S.a, S.b, S.q, S.r, S);
-        S.a.swap(S.b);
-        S.b.swap(S.r);
-    }
+    gcd_lehmer(S.a, S.b, S);
     g = S.a;
 }
 

@@ -555,12 +555,100 @@ bn::Big lead(const FlatPoly &f) {
 
 }  // namespace
 
+// inputs whose lift would take at least this many primes get the two-prime
+// square-free test first
+constexpr int kSqfTestMinPrimes = 12;
+
 // copies of the square-free path, counted for gbr_stats like the gcd path's
 static cudaError_t sqf_copy(gbr_ctx *c, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind,
                             cudaStream_t s) {
     if (kind == cudaMemcpyHostToDevice) c->gcd_h2d += (int64_t)bytes;
     else c->gcd_d2h += (int64_t)bytes;
     return cudaMemcpyAsync(dst, src, bytes, kind, s);
+}
+
+// The modular stage: R modulo the first K table primes and Yun's algorithm over
+// each, for the jobs `pend`; fills the job table, the launch parameters (residues
+// and monic factors stay on the device) and the degree patterns on the host.
+struct SqfStage {
+    std::vector<SqfJob> J;
+    std::vector<int32_t> pat;
+    SqfLaunch L{};
+    SqfJob *d_jobs = nullptr;
+    int stride = 0;
+};
+
+static int sqf_modular_stage(gbr_ctx *c, DevBufs &B, const std::vector<int> &pend, const std::vector<SqfHost> &H,
+                             const gbr_bigpoly *in, const std::vector<int64_t> &mag_off,
+                             const std::vector<int64_t> &sign_off, const uint32_t *d_limbs, const int8_t *d_signs,
+                             int K, SqfStage &st) {
+    cudaStream_t s = c->stream;
+    const int nj = (int)pend.size();
+    std::vector<SqfJob> &J = st.J;
+    J.assign(nj, SqfJob{});
+    int64_t res_w = 0, out_w = 0, pat_w = 0, red = 0;
+    int maxn = 0;
+    for (int q = 0; q < nj; ++q) {
+        const int j = pend[q];
+        SqfJob &x = J[q];
+        std::memset(&x, 0, sizeof(x));
+        x.n = H[j].n;
+        x.limbs = in[j].limbs;
+        x.mag_off = mag_off[j];
+        x.sign_off = sign_off[j];
+        x.res_off = res_w;
+        x.out_off = out_w;
+        x.pat_off = pat_w;
+        x.red0 = red;
+        res_w += (int64_t)K * (x.n + 1);
+        out_w += (int64_t)K * (2 * x.n + 2);
+        pat_w += (int64_t)K * (x.n + 2);
+        red += (int64_t)K * (x.n + 1);
+        maxn = std::max(maxn, x.n);
+    }
+    const int stride = maxn + 2;
+    const int nwy = sqf_warps(6, stride);
+    if (nwy < 1) return c->fail(GBR_ELIMIT, "square-free input degree too large for shared memory");
+    SqfJob *d_jobs = (SqfJob *)B.get(sizeof(SqfJob) * nj);
+    uint32_t *d_res = (uint32_t *)B.get((size_t)res_w * 4);
+    uint32_t *d_out = (uint32_t *)B.get((size_t)out_w * 4);
+    int32_t *d_pat = (int32_t *)B.get((size_t)pat_w * 4);
+    if (!d_jobs || !d_res || !d_out || !d_pat) return c->fail(GBR_ENOMEM, "device budget too small for the square-free stage");
+    SqfLaunch &L = st.L;
+    L = SqfLaunch{};
+    L.jobs = d_jobs;
+    L.njobs = nj;
+    L.p0 = 0;
+    L.nprimes = K;
+    L.mods = c->d_mods;
+    L.limbs = d_limbs;
+    L.signs = d_signs;
+    L.res = d_res;
+    L.out = d_out;
+    L.pat = d_pat;
+    L.err = c->d_err;
+    cudaError_t e = sqf_copy(c, d_jobs, J.data(), sizeof(SqfJob) * nj, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, 4, s);
+    if (e == cudaSuccess) {
+        k_sqf_reduce<<<sqf_blocks((const void *)k_sqf_reduce, 256, 0, (red + 255) / 256), 256, 0, s>>>(L, red);
+        e = cudaGetLastError();
+        ++c->gcd_kernels;
+    }
+    if (e == cudaSuccess) {
+        const size_t smem = (size_t)nwy * 6 * stride * 4;
+        k_sqf_yun<<<sqf_blocks((const void *)k_sqf_yun, nwy * 32, smem, ((int64_t)nj * K + nwy - 1) / nwy), nwy * 32,
+                    smem, s>>>(L, stride);
+        e = cudaGetLastError();
+        ++c->gcd_kernels;
+        c->gcd_subproblems += (int64_t)nj * K;
+    }
+    st.pat.resize(pat_w);
+    if (e == cudaSuccess) e = sqf_copy(c, st.pat.data(), d_pat, (size_t)pat_w * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "square-free modular stage", e);
+    st.d_jobs = d_jobs;
+    st.stride = stride;
+    return GBR_OK;
 }
 
 static int sqf_batch_locked(gbr_ctx *c, int n, const gbr_bigpoly *in, gbr_sqf *out) {
@@ -629,6 +717,51 @@ static int sqf_batch_locked(gbr_ctx *c, int n, const gbr_bigpoly *in, gbr_sqf *o
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "square-free upload", e);
     }
+    // ---- square-free test: Yun modulo two primes.  A prime not dividing lc(R) whose
+    // modular square-free part has degree n proves R square-free over Z (a repeated
+    // factor g^2 of R would stay one modulo p, with deg(g mod p) = deg g); then
+    // R = u * pp(R) and nothing needs lifting.  Most projection resultants are
+    // square-free, so this settles them with two primes instead of the lift's count;
+    // it pays for itself once that count is large (kSqfTestMinPrimes and above).
+    std::vector<int> tpend, rest;
+    for (int j : pend)
+        (primes_for_bits(H[j].n + H[j].l2norm2 + 3.0) + 4 >= kSqfTestMinPrimes ? tpend : rest).push_back(j);
+    if (!tpend.empty()) {
+        SqfStage ST;
+        const int KA = 2;
+        int rc = sqf_modular_stage(c, B, tpend, H, in, mag_off, sign_off, d_limbs, d_signs, KA, ST);
+        if (rc) return rc;
+        std::vector<char> done(tpend.size(), 0), fail(tpend.size(), 0);
+        gbr_parallel_for((int)tpend.size(), threads, [&](int lo, int hi) {
+            bn::Scratch S;
+            for (int q = lo; q < hi; ++q) {
+                const int j = tpend[q];
+                SqfHost &h = H[j];
+                const int32_t *pq = ST.pat.data() + ST.J[q].pat_off;
+                bool sf = false;
+                for (int sl = 0; sl < KA && !sf; ++sl) {
+                    const int32_t *ps = pq + (int64_t)sl * (h.n + 2);
+                    sf = ps[0] == 1 && ps[1] == h.n;
+                }
+                if (!sf) continue;
+                h.fac.assign(1, FlatPoly());
+                if (!primitive_part(in[j].mag, in[j].sign, h.n, in[j].limbs, h.fac[0], S) ||
+                    !bn::divexact(h.lc, lead(h.fac[0]), h.u, S)) {
+                    fail[q] = 1;
+                    continue;
+                }
+                h.pat.assign(1, h.n);
+                done[q] = 1;
+            }
+        });
+        for (size_t q = 0; q < tpend.size(); ++q) {
+            if (fail[q]) return c->fail(GBR_EDEVICE, "square-free: primitive part of a square-free input failed");
+            if (done[q]) H[tpend[q]].status = 1;
+            else rest.push_back(tpend[q]);
+        }
+        std::sort(rest.begin(), rest.end());
+    }
+    pend.swap(rest);
     // ---- attempts: K primes from the start of the table, doubled on failure
     int K = 0;
     for (int j : pend) K = std::max(K, primes_for_bits(H[j].n + H[j].l2norm2 + 3.0) + 4);
@@ -636,66 +769,15 @@ static int sqf_batch_locked(gbr_ctx *c, int n, const gbr_bigpoly *in, gbr_sqf *o
     while (!pend.empty()) {
         if (K > NP) return c->fail(GBR_EVERIFY, "square-free check failed with every table prime");
         const int nj = (int)pend.size();
-        std::vector<SqfJob> J(nj);
-        int64_t res_w = 0, out_w = 0, pat_w = 0, red = 0;
-        int maxn = 0;
-        for (int q = 0; q < nj; ++q) {
-            const int j = pend[q];
-            SqfJob &x = J[q];
-            std::memset(&x, 0, sizeof(x));
-            x.n = H[j].n;
-            x.limbs = in[j].limbs;
-            x.mag_off = mag_off[j];
-            x.sign_off = sign_off[j];
-            x.res_off = res_w;
-            x.out_off = out_w;
-            x.pat_off = pat_w;
-            x.red0 = red;
-            res_w += (int64_t)K * (x.n + 1);
-            out_w += (int64_t)K * (2 * x.n + 2);
-            pat_w += (int64_t)K * (x.n + 2);
-            red += (int64_t)K * (x.n + 1);
-            maxn = std::max(maxn, x.n);
-        }
-        const int stride = maxn + 2;
-        const int nwy = sqf_warps(6, stride);
-        if (nwy < 1) return c->fail(GBR_ELIMIT, "square-free input degree too large for shared memory");
-        SqfJob *d_jobs = (SqfJob *)B.get(sizeof(SqfJob) * nj);
-        uint32_t *d_res = (uint32_t *)B.get((size_t)res_w * 4);
-        uint32_t *d_out = (uint32_t *)B.get((size_t)out_w * 4);
-        int32_t *d_pat = (int32_t *)B.get((size_t)pat_w * 4);
-        if (!d_jobs || !d_res || !d_out || !d_pat) return c->fail(GBR_ENOMEM, "device budget too small for the square-free stage");
-        SqfLaunch L{};
-        L.jobs = d_jobs;
-        L.njobs = nj;
-        L.p0 = 0;
-        L.nprimes = K;
-        L.mods = c->d_mods;
-        L.limbs = d_limbs;
-        L.signs = d_signs;
-        L.res = d_res;
-        L.out = d_out;
-        L.pat = d_pat;
-        L.err = c->d_err;
-        cudaError_t e = sqf_copy(c, d_jobs, J.data(), sizeof(SqfJob) * nj, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, 4, s);
-        if (e == cudaSuccess) {
-            k_sqf_reduce<<<sqf_blocks((const void *)k_sqf_reduce, 256, 0, (red + 255) / 256), 256, 0, s>>>(L, red);
-            e = cudaGetLastError();
-            ++c->gcd_kernels;
-        }
-        if (e == cudaSuccess) {
-            const size_t smem = (size_t)nwy * 6 * stride * 4;
-            k_sqf_yun<<<sqf_blocks((const void *)k_sqf_yun, nwy * 32, smem, ((int64_t)nj * K + nwy - 1) / nwy),
-                        nwy * 32, smem, s>>>(L, stride);
-            e = cudaGetLastError();
-            ++c->gcd_kernels;
-            c->gcd_subproblems += (int64_t)nj * K;
-        }
-        std::vector<int32_t> pat(pat_w);
-        if (e == cudaSuccess) e = sqf_copy(c, pat.data(), d_pat, (size_t)pat_w * 4, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "square-free modular stage", e);
+        SqfStage ST;
+        int rc = sqf_modular_stage(c, B, pend, H, in, mag_off, sign_off, d_limbs, d_signs, K, ST);
+        if (rc) return rc;
+        std::vector<SqfJob> &J = ST.J;
+        std::vector<int32_t> &pat = ST.pat;
+        SqfLaunch &L = ST.L;
+        SqfJob *d_jobs = ST.d_jobs;
+        const int stride = ST.stride;
+        cudaError_t e = cudaSuccess;
         // ---- lucky primes: largest square-free degree, then the most common pattern
         gbr_parallel_for(nj, threads, [&](int lo, int hi) {
             std::vector<std::pair<uint64_t, int>> cand_slots;

@@ -110,6 +110,25 @@ def test_wide_coefficients(ctx):
     assert ctx.squarefree(R2) == _oracle(R2)
 
 
+def test_square_free_test_path(ctx):
+    # lifts of 12 or more primes first get the two-prime square-free test: wide
+    # square-free inputs (with and without a content) finish there, wide inputs with
+    # repeated factors fall through to the full lift
+    rng = random.Random(31)
+    cases = []
+    for d in (1, 7, 40):
+        r = [rng.randint(-2**400, 2**400) for _ in range(d + 1)]
+        r[-1] = r[-1] or 1
+        cases.append(r)
+        cases.append([-(3**50) * c for c in r])                     # content 3^50, negative lc
+    a = [rng.randint(-2**150, 2**150) for _ in range(6)]
+    b = [rng.randint(-2**120, 2**120) for _ in range(4)]
+    cases.append(_mul(_mul(a, a), b))                                 # a^2 b, about 420-bit coefficients
+    cases.append(_mul(_mul(_mul(b, b), b), [0, 1]))                   # x b^3
+    got = ctx.squarefree_batch(cases)
+    assert got == [_oracle(r) for r in cases]
+
+
 def test_high_multiplicity(ctx):
     for k in (5, 9, 17):
         R = [1]
@@ -176,3 +195,14 @@ def test_full_batch_properties_and_samples(ctx):
 def test_batch_determinism(ctx):
     R, _ = W.sqf_batch(12, 64, degs=((5, 20), (1, 6), (0, 2)), bits=24)
     assert ctx.squarefree_batch(R) == ctx.squarefree_batch(R)
+
+
+def test_arrangement_resultants_chain(ctx):
+    # the projection phase on an arrangement: square-free factorisation of every
+    # res(f, f_y) and res(f, g) of five curves (the resultants are the oracle's)
+    curves = W.arrangement_curves(8, n=5, d=4, bits=10, conic_frac=0.5, rbits=4)
+    rs = [_trim(O.disc_res(f)) for f in curves]
+    rs += [_trim(O.res_subres(curves[i], curves[j])) for i in range(5) for j in range(i + 1, 5)]
+    rs = [r for r in rs if r]
+    got = ctx.squarefree_batch(rs)
+    assert got == [_oracle(r) for r in rs]
