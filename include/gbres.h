@@ -362,14 +362,24 @@ int gbr_primes_for_bits(double bits);
  * x-degree bound D (min of n deg_x f + m deg_x g and the total-degree Bezout
  * bound), log2 of the Hadamard bound B on |coefficients| and the number of
  * primes k with prod p > 2B + 1.  Host only.  disc = 1 uses g = df/dvar.
- * B is the smallest scaled bound over all lambda values; the device planner
- * picks its lambda with a single-precision search, so in a near tie it may
- * use a slightly larger (equally valid) B and one prime more. */
+ * B is the smallest scaled bound over all lambda values; the device evaluates
+ * the same bounds in single precision rounded upward, so its B can be slightly
+ * larger (at most a few thousandths of a bit) and, in a near tie, take one
+ * prime more. */
 typedef struct {
     int32_t m, n, deg_bound, primes, limbs;
     double log2_bound;
 } gbr_res_info;
 int gbr_resultant_info(const gbr_bipoly *f, const gbr_bipoly *g, int var, int disc, gbr_res_info *out);
+
+/* The plan the device made for jobs [first, first + count) of a resident batch
+ * in its last gbr_run_resident: actual degrees, x-degree bound (deg_bound =
+ * points - 1), primes used (including GBR_OPT_EXTRA_PRIMES), output limbs, and
+ * the log2 of the coefficient bound computed on the device (an upper bound of
+ * the same scaled Hadamard bound gbr_resultant_info evaluates, in single
+ * precision with directed rounding).  A zero result has deg_bound = -1 and
+ * primes = 0.  GBR_EINVAL before the first run. */
+int gbr_resident_plan(gbr_ctx *ctx, gbr_resident *r, int first, int count, gbr_res_info *out);
 
 #ifdef __cplusplus
 }

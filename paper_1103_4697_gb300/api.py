@@ -181,6 +181,14 @@ class Resident:
         N.check(N.lib().gbr_fetch_resident(self.ctx.handle, self.handle, first, count, outs), self.ctx.handle)
         return self.ctx._collect(outs, count)
 
+    def plan(self, first: int = 0, count: int | None = None) -> list[dict]:
+        """gbr_resident_plan: the device's plan per job after a run (degrees, points - 1,
+        primes, limbs, log2 of the coefficient bound)."""
+        count = self.n - first if count is None else count
+        outs = (N.ResInfo * max(count, 1))()
+        N.check(N.lib().gbr_resident_plan(self.ctx.handle, self.handle, first, count, outs), self.ctx.handle)
+        return [{k: getattr(outs[i], k) for k, _ in N.ResInfo._fields_} for i in range(count)]
+
     def free(self):
         if self.handle:
             N.lib().gbr_free_resident(self.ctx.handle, self.handle)

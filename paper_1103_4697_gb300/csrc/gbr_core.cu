@@ -1110,6 +1110,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     // ---- A0 (host half): degrees, point counts and prime counts
     std::vector<PairPlan> &plan = r->h_plan;
     plan.assign(n, PairPlan{});
+    r->h_log2B.assign(n, 0.0);
     const bool drop = c->drop_unlucky != 0;
     int kc_max = 0;
     for (int q = 0; q < n; ++q) {
@@ -1134,6 +1135,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
         int64_t D = degree_bound(b);
         if (D + 1 > GBR_MAX_POINTS) return c->fail(GBR_ELIMIT, "x-degree bound above GBR_MAX_POINTS - 1");
         p.P = (int32_t)(D + 1);
+        r->h_log2B[q] = b.log2B;
         double bits = b.log2B * (1.0 + 1e-9) + 2.0;
         int k = primes_for_bits(bits);
         if (k < 0 || k + c->extra_primes > GBR_MAX_PRIMES)
@@ -1844,6 +1846,24 @@ static int res_batch_impl(gbr_ctx *c, int n, const gbr_bipoly *f, const gbr_bipo
         gbr_free_resident_locked(c, r);
     }
     return st;
+}
+
+extern "C" int gbr_resident_plan(gbr_ctx *c, gbr_resident *r, int first, int count, gbr_res_info *out) {
+    if (!c || !r || first < 0 || count < 0 || (int64_t)first + count > r->n || (count && !out)) return GBR_EINVAL;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (!r->ran || (int)r->h_plan.size() != r->n) return c->fail(GBR_EINVAL, "the resident batch has not run yet");
+    for (int i = 0; i < count; ++i) {
+        const PairPlan &p = r->h_plan[first + i];
+        gbr_res_info &o = out[i];
+        o.m = p.m;
+        o.n = p.n;
+        const bool zero = (p.flags & PLAN_ZERO) != 0;
+        o.deg_bound = zero ? -1 : p.P - 1;
+        o.primes = zero ? 0 : p.k;
+        o.limbs = zero ? 0 : p.L;
+        o.log2_bound = zero ? 0.0 : r->h_log2B[first + i];
+    }
+    return GBR_OK;
 }
 
 extern "C" int gbr_arrangement_resultants(gbr_ctx *c, int n, const gbr_bipoly *f, int var, gbr_bigpoly *out) {

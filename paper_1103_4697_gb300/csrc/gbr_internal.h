@@ -162,6 +162,11 @@ GBR_HD double bound_lambda(int l) {
     return l < 5 ? 0.25 * l : l < 7 ? 1.0 + 0.5 * (l - 4) : l < 11 ? (double)(l - 4) : -0.5 * (l - 10);
 }
 
+// the same values in single precision (all exact), for device code
+GBR_HD float bound_lambda_f(int l) {
+    return l < 5 ? 0.25f * l : l < 7 ? 1.0f + 0.5f * (l - 4) : l < 11 ? (float)(l - 4) : -0.5f * (l - 10);
+}
+
 GBR_HD double best_scaled_bound(const double *lf, int m, const double *lg, int n, double *ef, double *eg) {
     if (m <= 0 && n <= 0) return 0.0;
     double best = INFINITY;

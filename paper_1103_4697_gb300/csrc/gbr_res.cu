@@ -15,6 +15,7 @@
 //            points 0..P-1 and conversion to monomial coefficients
 //   crt      (A5) one thread per (pair, coefficient): Garner mixed-radix digits,
 //            symmetric lift, magnitude limbs
+#include <limits.h>
 #include <math.h>
 
 #include <algorithm>
@@ -27,6 +28,47 @@
 namespace gbr {
 
 // ------------------------------------------------------------------ A0: bounds
+
+// Top bit e and the top 32 bits of |c| (plus one when any lower bit is set; at
+// most 2^32 - 1 + 1, kept as 2^31 with e + 1 then) of a two's-complement
+// multi-word integer, so that |c| <= m32 2^(e - 31); false for zero.
+__device__ bool coef_top_bits(const uint64_t *w, int W, int &e, uint32_t &m32) {
+    uint64_t mag[8];
+    const bool neg = (int64_t)w[W - 1] < 0;
+    uint64_t carry = 1;
+    for (int i = 0; i < W; ++i) {
+        uint64_t v = w[i];
+        if (neg) {
+            v = ~v + carry;
+            carry = (carry && v == 0) ? 1 : 0;
+        }
+        mag[i] = v;
+    }
+    int t = W - 1;
+    while (t >= 0 && mag[t] == 0) --t;
+    if (t < 0) return false;
+    const int lz = __clzll((long long)mag[t]);
+    e = 64 * t + 63 - lz;
+    // the 64 bits from the top bit down, and whether anything below them is set
+    uint64_t top = mag[t] << lz;
+    bool rest = false;
+    if (t > 0) {
+        if (lz) top |= mag[t - 1] >> (64 - lz);
+        rest = (mag[t - 1] << lz) != 0;
+        for (int i = t - 2; i >= 0 && !rest; --i) rest = mag[i] != 0;
+    }
+    m32 = (uint32_t)(top >> 32);
+    rest = rest || (uint32_t)top != 0;
+    if (rest) {
+        if (m32 == 0xFFFFFFFFu) {
+            m32 = 0x80000000u;
+            ++e;
+        } else {
+            ++m32;
+        }
+    }
+    return true;
+}
 
 // log2 |c| of a two's-complement multi-word integer; -inf for zero.
 __device__ double coef_log2abs(const uint64_t *w, int W) {
@@ -81,25 +123,54 @@ __device__ __forceinline__ const uint64_t *coef_ptr(const uint64_t *coef, const 
 // Scans one polynomial row by row (one warp per pair): row degrees, log2 of the
 // row 1-norms, degrees.  For disc, g = d f / d var is formed on the fly:
 // g_r = (r+1) f_{r+1}.  The row norms are kept in shared memory; the warp
-// ranks the lambda values by a single-precision evaluation of the scaled
-// Hadamard bound and evaluates the best one again in double precision, which
-// is the value the plan uses (FP64 transcendentals are slow on this part, and
-// any lambda gives a valid bound).
+// evaluates the scaled Hadamard bound for every lambda in single precision with
+// directed rounding and explicit error margins (each value is an upper bound)
+// and keeps the smallest (the FP64 pipe of this part is slow).
 constexpr int kBoundsWarps = 4;
 
 // Row quantity of the Hadamard bound.  For a row f_r(x) = sum_a c_a x^a with
 // int64 coefficients: G = A_0 + 2 sum_{k>0} |A_k|, A_k = sum_a c_a c_{a+k} (the
 // autocorrelation), which bounds |f_r(x)|^2 on |x| = 1 because
 // |f_r(x)|^2 = A_0 + 2 sum_k A_k cos(k theta); it never exceeds the squared
-// 1-norm and is far smaller when the signs cancel.  The row is staged in
-// shared memory; with every |c| < 2^27 each A_k is summed exactly in int64
-// (products below 2^54, at most 128 of them), otherwise in double with the
-// error term gamma sum |c_a c_{a+k}|, gamma = 2 (L+1) 2^-53 (covering the
-// conversions, products and the sum of L terms), so G is an upper bound; it is
-// returned linear (the caller takes half its log2 later, one row per lane).  Wider coefficients: log2 of the 1-norm by a log-sum-exp over the
-// coefficients' log2 magnitudes.
+// 1-norm and is far smaller when the signs cancel.  The row is staged in shared
+// memory.  Coefficients of 2^56 and more: double sums with the error term
+// gamma sum |c_a c_{a+k}|, gamma = 2 (L+1) 2^-53 (covering the conversions,
+// products and the sum of L terms), so G stays an upper bound.  Wider
+// coefficients: log2 of the 1-norm by a log-sum-exp over the coefficients'
+// log2 magnitudes.
 constexpr int kRowBuf = 128;   // coefficients of one row staged per warp
-__device__ double row_norm(const uint64_t *coef, const PolyDesc &P, int r, int lane, int &cmax, int64_t *rb) {
+
+// log2 of a positive 128-bit integer hi 2^64 + lo, rounded up to a float: the
+// top 32 bits (plus one when lower bits are set) as a float rounded up, log2f of
+// it (in [31, 32], within 1 ulp < 2^-19, covered by adding 2^-18), plus the shift
+__device__ __forceinline__ float log2_up_u128(uint64_t hi, uint64_t lo) {
+    const unsigned __int128 G = ((unsigned __int128)hi << 64) | lo;
+    const int e = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+    uint32_t m32;
+    bool rest = false;
+    int s = 0;
+    if (e >= 31) {
+        s = e - 31;
+        m32 = (uint32_t)(G >> s);
+        rest = s > 0 && (G << (128 - s)) != 0;
+    } else {
+        m32 = (uint32_t)(lo << (31 - e));
+        s = e - 31;
+    }
+    float mf = __uint2float_ru(m32);
+    if (rest) mf = __fadd_ru(mf, 1.0f);
+    return __fadd_ru((float)s, __fadd_ru(log2f(mf), 0x1p-18f));
+}
+
+__device__ __forceinline__ float log2_up(double x);
+
+// An upper bound of log2 of the row norm used by the Hadamard bound, as a float
+// (-inf for a zero row).  Single-word rows: half the log2 of the autocorrelation
+// quantity G; with every |c| < 2^56, G is summed exactly (int64 terms below 2^27,
+// else 128-bit products; G < 2^127) and its log2 taken from its leading bits;
+// wider single-word coefficients use the double sum with its error term.
+// Multi-word rows: the log2 of the 1-norm by a log-sum-exp, rounded up.
+__device__ float row_log2_up(const uint64_t *coef, const PolyDesc &P, int r, int lane, int &cmax, int64_t *rb) {
     cmax = -1;
     if (P.words == 1) {
         uint64_t big = 0;   // OR of the |c|
@@ -114,100 +185,174 @@ __device__ double row_norm(const uint64_t *coef, const PolyDesc &P, int r, int l
             big |= __shfl_xor_sync(0xffffffffu, big, o);
         }
         __syncwarp();
-        if (cmax < 0) return 0.0;
+        if (cmax < 0) return -INFINITY;
         const int L = cmax + 1;
-        double G = 0.0;
-        if (L <= kRowBuf && big < (1ull << 27)) {
+        if (L <= kRowBuf && big < (1ull << 56)) {
+            // exact: |A_k| < 128 * 2^112, G < 2^127
+            unsigned __int128 acc = 0;
             for (int k = lane; k < L; k += 32) {
-                int64_t sk = 0;
-                for (int a = 0; a + k < L; ++a) sk += rb[a] * rb[a + k];
-                G += (k ? 2.0 : 1.0) * (double)(sk < 0 ? -sk : sk);
-            }
-        } else {
-            const double gam = 2.0 * (L + 1) * 0x1p-53;
-            for (int k = lane; k < L; k += 32) {
-                double sk = 0.0, tk = 0.0;
-                for (int a = 0; a + k < L; ++a) {
-                    const double x = (double)(L <= kRowBuf ? rb[a] : (int64_t)coef_ptr(coef, P, r, a)[0]);
-                    const double y = (double)(L <= kRowBuf ? rb[a + k] : (int64_t)coef_ptr(coef, P, r, a + k)[0]);
-                    sk = fma(x, y, sk);
-                    tk = fma(fabs(x), fabs(y), tk);
+                unsigned __int128 ak;
+                if (big < (1ull << 27)) {
+                    int64_t sk = 0;
+                    for (int a = 0; a + k < L; ++a) sk += rb[a] * rb[a + k];
+                    ak = (unsigned __int128)(uint64_t)(sk < 0 ? -sk : sk);
+                } else {
+                    __int128 sk = 0;
+                    for (int a = 0; a + k < L; ++a) sk += (__int128)rb[a] * rb[a + k];
+                    ak = (unsigned __int128)(sk < 0 ? -sk : sk);
                 }
-                G += (k ? 2.0 : 1.0) * (fabs(sk) + gam * tk);
+                acc += ak << (k ? 1 : 0);
             }
+            uint64_t lo = (uint64_t)acc, hi = (uint64_t)(acc >> 64);
+            for (int o = 16; o; o >>= 1) {
+                const uint64_t olo = __shfl_xor_sync(0xffffffffu, lo, o), ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+                lo += olo;
+                hi += ohi + (lo < olo ? 1u : 0u);
+            }
+            __syncwarp();
+            return 0.5f * log2_up_u128(hi, lo);
+        }
+        double G = 0.0;
+        const double gam = 2.0 * (L + 1) * 0x1p-53;
+        for (int k = lane; k < L; k += 32) {
+            double sk = 0.0, tk = 0.0;
+            for (int a = 0; a + k < L; ++a) {
+                const double x = (double)(L <= kRowBuf ? rb[a] : (int64_t)coef_ptr(coef, P, r, a)[0]);
+                const double y = (double)(L <= kRowBuf ? rb[a + k] : (int64_t)coef_ptr(coef, P, r, a + k)[0]);
+                sk = fma(x, y, sk);
+                tk = fma(fabs(x), fabs(y), tk);
+            }
+            G += (k ? 2.0 : 1.0) * (fabs(sk) + gam * tk);
         }
         for (int o = 16; o; o >>= 1) G += __shfl_xor_sync(0xffffffffu, G, o);
         __syncwarp();
-        return G * (1.0 + 0x1p-40);   // the double sums of at most 160 non-negative terms
+        return 0.5f * log2_up(G * (1.0 + 0x1p-40));   // the double sums of at most 160 non-negative terms
     }
-    Lse nrm;
-    nrm.init();
+    // multi-word: the 1-norm.  Each |c| <= m32 2^(e - 31) with m32 its top 32 bits
+    // (plus one when lower bits are set) and e its top bit; the terms are summed
+    // in float relative to the row's largest e, rounded up (terms below 2^-100 of
+    // it are raised to 2^-100, which only enlarges the sum)
+    int emax = -1;
     for (int c = lane; c <= P.cols; c += 32) {
-        double a = coef_log2abs(coef_ptr(coef, P, r, c), P.words);
-        if (a != -INFINITY) {
+        int e;
+        uint32_t m32;
+        if (coef_top_bits(coef_ptr(coef, P, r, c), P.words, e, m32)) {
             cmax = c;
-            nrm.add(a);
+            emax = max(emax, e);
         }
     }
-    for (int o = 16; o; o >>= 1) cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
-    warp_lse(nrm);
-    return nrm.log2v();
+    for (int o = 16; o; o >>= 1) {
+        cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+        emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    }
+    if (cmax < 0) return -INFINITY;
+    float sum = 0.0f;
+    for (int c = lane; c <= P.cols; c += 32) {
+        int e;
+        uint32_t m32;
+        if (coef_top_bits(coef_ptr(coef, P, r, c), P.words, e, m32)) {
+            const float t = __uint2float_ru(m32) * 0x1p-31f;   // in [1, 2], exact scaling
+            sum = __fadd_ru(sum, e - emax < -100 ? 0x1p-100f : ldexpf(t, e - emax));
+        }
+    }
+    for (int o = 16; o; o >>= 1) sum = __fadd_ru(sum, __shfl_xor_sync(0xffffffffu, sum, o));
+    // sum in [1, 2^12): log2f within 1 ulp (below 2^-20), covered by 2^-19
+    return __fadd_ru((float)emax, __fadd_ru(log2f(sum), 0x1p-19f));
 }
 
-// Warp-parallel evaluation of scaled_hadamard_log2: lanes split the rows for the
-// scaled squared norms and the columns for their logarithms.  T = double gives
-// the rigorous value; T = float is only used to choose lambda (every lambda
-// gives a valid bound, and the chosen one is evaluated again in double).
-template <typename T>
-__device__ T scaled_hadamard_log2_warp(const double *lf, int m, const double *lg, int n, T l2lam, T *ef, T *eg,
-                                       int lane) {
-    // terms are clamped from below so that every column sum stays positive
-    // (an upward rounding); the float floor stays a normal number
-    const T kFloor = sizeof(T) == 4 ? (T)-120 : (T)-1000;
-    T M = -INFINITY;
-    for (int i = lane; i <= m; i += 32)
-        if (lf[i] != -INFINITY) M = fmax(M, (T)lf[i] + i * l2lam);
-    for (int j = lane; j <= n; j += 32)
-        if (lg[j] != -INFINITY) M = fmax(M, (T)lg[j] + j * l2lam);
-    for (int o = 16; o; o >>= 1) M = fmax(M, __shfl_xor_sync(0xffffffffu, M, o));
-    T sf = 0, sg = 0;
+// log2 x rounded up to a float, for a positive finite double x: the exponent
+// from the bits, log2f of the mantissa in [1, 2) (converted upward; log2f is
+// within 1 ulp, below 2^-23 there, covered by the 2^-20 added), the sum rounded up
+__device__ __forceinline__ float log2_up(double x) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    const double mant = __longlong_as_double((b & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
+    return __fadd_ru((float)e, __fadd_ru(log2f(__double2float_ru(mant)), 0x1p-20f));
+}
+
+// ceil(x 2^16) for a finite |x| < 2^15 (the scaling is exact)
+__device__ __forceinline__ long long fx16_up(float x) { return (long long)__float2int_ru(x * 65536.0f); }
+
+// 2 tm + log2 s, in units of 2^-16 and rounded up, for the sum s of the terms
+// exp2f(max(2 (t_k - tm) rounded up, -120)) of a set of exponents t_k with the
+// finite maximum tm: an upper bound of log2 sum_k 2^(2 t_k).  exp2f (within 2
+// ulp) and the round-up sums of at most 256 terms are covered by the factor
+// 1 + 2^-20, log2f of s in [1, 2^9) (within 1 ulp, below 2^-15) by adding 2^-14;
+// terms below 2^-120 of the largest are raised to it (that only enlarges it).
+__device__ __forceinline__ long long log2_sum_fx(float tm, float s) {
+    return 2 * fx16_up(tm) + fx16_up(__fadd_ru(log2f(__fmul_ru(s, 1.0f + 0x1p-20f)), 0x1p-14f));
+}
+
+__device__ __forceinline__ float exp2_term(float t, float tm) { return exp2f(fmaxf(2.0f * __fsub_ru(t, tm), -120.0f)); }
+
+// Twice (the log2 of the scaled Hadamard bound's smaller form minus m n l2lam),
+// in units of 2^-16 and rounded up, evaluated warp-parallel: lanes split the rows
+// for the scaled squared norms and the columns for their logarithms.  lf, lg are
+// float upper bounds of the log2 row norms (-inf for zero rows); the scaled
+// exponents t = lf_i + i l2lam are rounded up; every sum of powers is shifted by
+// its own largest term (the rows of f, the rows of g, each column); the outer
+// sums are exact integer sums.  LLONG_MIN when a column of the Sylvester matrix
+// is zero (the resultant vanishes).  l2lam is a multiple of 1/4 in [-2^2, 2^3].
+__device__ long long scaled_hadamard_fx(const float *lf, int m, const float *lg, int n, float l2lam, float *tf,
+                                        float *tg, int lane) {
+    float Mf = -INFINITY, Mg = -INFINITY;
     for (int i = lane; i <= m; i += 32) {
-        T t = lf[i] == -INFINITY ? (T)0 : exp2(fmax((T)2 * ((T)lf[i] + i * l2lam - M), kFloor));
-        ef[i] = t;
-        sf += t;
+        const float t = lf[i] == -INFINITY ? -INFINITY : __fmaf_ru((float)i, l2lam, lf[i]);
+        tf[i] = t;
+        Mf = fmaxf(Mf, t);
     }
     for (int j = lane; j <= n; j += 32) {
-        T t = lg[j] == -INFINITY ? (T)0 : exp2(fmax((T)2 * ((T)lg[j] + j * l2lam - M), kFloor));
-        eg[j] = t;
-        sg += t;
+        const float t = lg[j] == -INFINITY ? -INFINITY : __fmaf_ru((float)j, l2lam, lg[j]);
+        tg[j] = t;
+        Mg = fmaxf(Mg, t);
     }
     for (int o = 16; o; o >>= 1) {
-        sf += __shfl_xor_sync(0xffffffffu, sf, o);
-        sg += __shfl_xor_sync(0xffffffffu, sg, o);
+        Mf = fmaxf(Mf, __shfl_xor_sync(0xffffffffu, Mf, o));
+        Mg = fmaxf(Mg, __shfl_xor_sync(0xffffffffu, Mg, o));
     }
     __syncwarp();
-    T row = 0;
-    if (n > 0) row += (T)0.5 * n * ((T)2 * M + log2(sf));
-    if (m > 0) row += (T)0.5 * m * ((T)2 * M + log2(sg));
-    T col = 0;
+    float sf = 0.0f, sg = 0.0f;
+    for (int i = lane; i <= m; i += 32)
+        if (tf[i] != -INFINITY) sf = __fadd_ru(sf, exp2_term(tf[i], Mf));
+    for (int j = lane; j <= n; j += 32)
+        if (tg[j] != -INFINITY) sg = __fadd_ru(sg, exp2_term(tg[j], Mg));
+    for (int o = 16; o; o >>= 1) {
+        sf = __fadd_ru(sf, __shfl_xor_sync(0xffffffffu, sf, o));
+        sg = __fadd_ru(sg, __shfl_xor_sync(0xffffffffu, sg, o));
+    }
+    long long row = 0;
+    if (n > 0) row += (long long)n * log2_sum_fx(Mf, sf);
+    if (m > 0) row += (long long)m * log2_sum_fx(Mg, sg);
+    long long col = 0;
+    int zero = 0;
     for (int c = lane; c < m + n; c += 32) {
-        T sc = 0;
-        int r0 = c - m > 0 ? c - m : 0, r1 = c < n - 1 ? c : n - 1;
-        for (int r = r0; r <= r1; ++r) sc += ef[m - (c - r)];
-        r0 = c - n > 0 ? c - n : 0;
-        r1 = c < m - 1 ? c : m - 1;
-        for (int r = r0; r <= r1; ++r) sc += eg[n - (c - r)];
-        col += sc > 0 ? (T)0.5 * ((T)2 * M + log2(sc)) : (T)-INFINITY;
+        // f rows r = 0..n-1 hold f_{m-(c-r)} in column c; g rows r = 0..m-1 hold g_{n-(c-r)}
+        const int fr0 = c - m > 0 ? c - m : 0, fr1 = c < n - 1 ? c : n - 1;
+        const int gr0 = c - n > 0 ? c - n : 0, gr1 = c < m - 1 ? c : m - 1;
+        float mc = -INFINITY;
+        for (int r = fr0; r <= fr1; ++r) mc = fmaxf(mc, tf[m - (c - r)]);
+        for (int r = gr0; r <= gr1; ++r) mc = fmaxf(mc, tg[n - (c - r)]);
+        if (mc == -INFINITY) {
+            zero = 1;
+            continue;
+        }
+        float sc = 0.0f;
+        for (int r = fr0; r <= fr1; ++r)
+            if (tf[m - (c - r)] != -INFINITY) sc = __fadd_ru(sc, exp2_term(tf[m - (c - r)], mc));
+        for (int r = gr0; r <= gr1; ++r)
+            if (tg[n - (c - r)] != -INFINITY) sc = __fadd_ru(sc, exp2_term(tg[n - (c - r)], mc));
+        col += log2_sum_fx(mc, sc);
     }
     for (int o = 16; o; o >>= 1) col += __shfl_xor_sync(0xffffffffu, col, o);
-    __syncwarp();
-    return fmin(row, col) - (T)m * n * l2lam;
+    zero = __any_sync(0xffffffffu, zero);
+    if (zero) return LLONG_MIN;
+    const long long lam = (long long)m * n * (long long)__float2int_rn(l2lam * 131072.0f);   // 2 m n l2lam 2^16
+    return (row < col ? row : col) - lam;
 }
 
 __global__ void __launch_bounds__(kBoundsWarps * 32) k_bounds(ResLaunch L) {
-    __shared__ double lnf[kBoundsWarps][GBR_MAX_YDEG + 2], lng[kBoundsWarps][GBR_MAX_YDEG + 2];
-    __shared__ double ebuf[kBoundsWarps][2][GBR_MAX_YDEG + 2];
-    __shared__ float fbuf[kBoundsWarps][2][GBR_MAX_YDEG + 2];
+    __shared__ float lff[kBoundsWarps][GBR_MAX_YDEG + 2], lgf[kBoundsWarps][GBR_MAX_YDEG + 2];
+    __shared__ float tbuf[kBoundsWarps][2][GBR_MAX_YDEG + 2];
     __shared__ int64_t rbuf[kBoundsWarps][kRowBuf];
     const int wib = threadIdx.x >> 5;
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -221,13 +366,12 @@ __global__ void __launch_bounds__(kBoundsWarps * 32) k_bounds(ResLaunch L) {
     for (int which = 0; which < 2; ++which) {
         if (which == 1 && D.disc) break;
         const PolyDesc &P = which ? D.g : D.f;
-        double *ln_out = which ? lng[wib] : lnf[wib];
-        const bool linear = P.words == 1;   // row_norm returns G (the squared row quantity) itself
+        float *ln_out = which ? lgf[wib] : lff[wib];
         int mdeg = -1, dxmax = -1, td = -1, terms = 0, terms_upto = 0, lcd = -1;
         int mdeg_g = -1, dx_g = -1, td_g = -1, terms_g = 0, terms_g_upto = 0, lcd_g = -1;
         for (int r = 0; r <= P.rows; ++r) {
             int cmax;
-            const double ln = row_norm(L.coef, P, r, lane, cmax, rbuf[wib]);
+            const float ln = row_log2_up(L.coef, P, r, lane, cmax, rbuf[wib]);
             if (lane == 0) {
                 L.rowdeg[P.rowdeg_off + r] = cmax;
                 if (r <= GBR_MAX_YDEG) ln_out[r] = ln;
@@ -241,10 +385,12 @@ __global__ void __launch_bounds__(kBoundsWarps * 32) k_bounds(ResLaunch L) {
                 td = max(td, r + cmax);
             }
             if (which == 0 && D.disc && r >= 1) {
+                // row r - 1 of d f / d var is r f_r: its norm is r times f_r's
                 if (lane == 0) {
                     L.rowdeg[D.g.rowdeg_off + r - 1] = cmax;
                     if (r - 1 <= GBR_MAX_YDEG)
-                        lng[wib][r - 1] = linear ? ln * ((double)r * r) : (ln == -INFINITY ? ln : ln + log2((double)r));
+                        lgf[wib][r - 1] =
+                            ln == -INFINITY ? -INFINITY : __fadd_ru(ln, __fadd_ru(log2f((float)r), 0x1p-19f));
                 }
                 terms_g += cmax + 1;
                 if (cmax >= 0) {
@@ -254,16 +400,6 @@ __global__ void __launch_bounds__(kBoundsWarps * 32) k_bounds(ResLaunch L) {
                     dx_g = max(dx_g, cmax);
                     td_g = max(td_g, r - 1 + cmax);
                 }
-            }
-        }
-        // half the log2 of the row quantities, one row per lane
-        __syncwarp();
-        if (linear) {
-            const int nr = min(P.rows, GBR_MAX_YDEG + 1);
-            for (int r = lane; r <= nr; r += 32) {
-                if (r <= GBR_MAX_YDEG) ln_out[r] = ln_out[r] > 0.0 ? 0.5 * log2(ln_out[r]) + 1e-12 : -INFINITY;
-                if (which == 0 && D.disc && r >= 1)
-                    lng[wib][r - 1] = lng[wib][r - 1] > 0.0 ? 0.5 * log2(lng[wib][r - 1]) + 1e-12 : -INFINITY;
             }
         }
         __syncwarp();
@@ -279,18 +415,14 @@ __global__ void __launch_bounds__(kBoundsWarps * 32) k_bounds(ResLaunch L) {
     __syncwarp();
     double lb = 0.0;
     if (B.m >= 0 && B.n >= 0 && B.m <= GBR_MAX_YDEG && B.n <= GBR_MAX_YDEG && (B.m > 0 || B.n > 0)) {
-        float bestf = INFINITY;
-        int bestl = 0;
+        // every lambda gives a valid bound; each evaluation is itself an upper bound
+        long long best = LLONG_MAX;
         for (int l = 0; l < kBoundLambdas; ++l) {
-            float b = scaled_hadamard_log2_warp<float>(lnf[wib], B.m, lng[wib], B.n, (float)bound_lambda(l),
-                                                       fbuf[wib][0], fbuf[wib][1], lane);
-            if (b < bestf) {
-                bestf = b;
-                bestl = l;
-            }
+            const long long v = scaled_hadamard_fx(lff[wib], B.m, lgf[wib], B.n, bound_lambda_f(l), tbuf[wib][0],
+                                                   tbuf[wib][1], lane);
+            best = v < best ? v : best;
         }
-        lb = scaled_hadamard_log2_warp<double>(lnf[wib], B.m, lng[wib], B.n, bound_lambda(bestl), ebuf[wib][0],
-                                               ebuf[wib][1], lane);
+        lb = best == LLONG_MIN ? -INFINITY : (double)best * 0x1p-17 + 0x1p-10;
     }
     B.log2B = lb;
     if (lane == 0) L.bounds[warp] = B;

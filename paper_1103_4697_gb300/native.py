@@ -97,6 +97,7 @@ SIGNATURES = {
     "gbr_num_primes": (C.c_int, []),
     "gbr_prime": (C.c_int, [C.c_int, C.POINTER(C.c_uint32)]),
     "gbr_primes_for_bits": (C.c_int, [C.c_double]),
+    "gbr_resident_plan": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.POINTER(ResInfo)]),
     "gbr_resultant_info": (C.c_int, [C.POINTER(BiPoly), C.POINTER(BiPoly), C.c_int, C.c_int, C.POINTER(ResInfo)]),
 }
 

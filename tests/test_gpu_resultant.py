@@ -408,3 +408,36 @@ def test_graph_replay_and_autotuned_blocks(ctx):
     assert first == second == plain
     for q in (0, 37, 95):
         assert first[q] == list(O.res_subres(F[q], G[q]))
+
+
+def test_device_bound_is_rigorous_and_tight(ctx):
+    """The device evaluates the scaled Hadamard bound in single precision with
+    upward rounding and error margins; it must never fall below the host's
+    double-precision value of the same bound (that would leave too few primes) and
+    stays within a small margin above it."""
+    from paper_1103_4697_gb300.api import resultant_info
+
+    ps = W.mixed_batch(3, 96)
+    d20 = W.deg20_batch(8)
+    fc, gc = W.conic_curves(4)
+    cases = [(f, g, 0) for f, g in zip(ps.f, ps.g)] + [(f, g, 0) for f, g in zip(d20.f, d20.g)]
+    cases += [(fc, gc, 0), (fc, None, 1), (d20.f[0], None, 1)]
+    for var in (1, 0):
+        res = ctx.upload_pairs([c[0] for c in cases[:-2]], [c[1] for c in cases[:-2]], var=var)
+        disc = ctx.upload_pairs([c[0] for c in cases[-2:]], var=var, disc=True)
+        try:
+            res.run()
+            disc.run()
+            dev = res.plan() + disc.plan()
+        finally:
+            res.free()
+            disc.free()
+        for (f, g, dflag), d in zip(cases, dev):
+            h = resultant_info(f, g, var=var, disc=bool(dflag))
+            assert (d["m"], d["n"]) == (h["m"], h["n"])
+            if h["deg_bound"] < 0:
+                assert d["primes"] == 0
+                continue
+            assert d["log2_bound"] >= h["log2_bound"] - 1e-9 * max(1.0, abs(h["log2_bound"]))
+            assert d["log2_bound"] <= h["log2_bound"] + 0.01 + 0.002 * (h["m"] + h["n"])
+            assert h["primes"] <= d["primes"] <= h["primes"] + 1
