@@ -1112,48 +1112,72 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     plan.assign(n, PairPlan{});
     r->h_log2B.assign(n, 0.0);
     const bool drop = c->drop_unlucky != 0;
-    int kc_max = 0;
-    for (int q = 0; q < n; ++q) {
-        const PairBound &b = hb[q];
-        PairPlan &p = plan[q];
-        p.disc = r->h_desc[q].disc;
-        p.rowdeg_f = r->h_desc[q].f.rowdeg_off;
-        p.rowdeg_g = r->h_desc[q].g.rowdeg_off;
-        p.pmap_off = -1;
-        p.flag_off = -1;
-        p.gtab_off = -1;
-        p.m = b.m;
-        p.n = b.n;
-        if (b.m < 0 || b.n < 0) {
-            p.flags = PLAN_ZERO;
-            continue;
+    // per pair: degrees, points, primes; the first failing pair decides the error
+    // (a serial loop: waking the host workers costs more than this work)
+    std::vector<int8_t> perr(n, 0);
+    int kcl = 0;
+    {
+        for (int q = 0; q < n; ++q) {
+            const PairBound &b = hb[q];
+            PairPlan &p = plan[q];
+            p.disc = r->h_desc[q].disc;
+            p.rowdeg_f = r->h_desc[q].f.rowdeg_off;
+            p.rowdeg_g = r->h_desc[q].g.rowdeg_off;
+            p.pmap_off = -1;
+            p.flag_off = -1;
+            p.gtab_off = -1;
+            p.m = b.m;
+            p.n = b.n;
+            if (b.m < 0 || b.n < 0) {
+                p.flags = PLAN_ZERO;
+                continue;
+            }
+            if (b.m > GBR_MAX_YDEG || b.n > GBR_MAX_YDEG) {
+                perr[q] = 1;
+                continue;
+            }
+            p.dxf = std::max(b.dxf, 0);
+            p.dxg = std::max(b.dxg, 0);
+            int64_t D = degree_bound(b);
+            if (D + 1 > GBR_MAX_POINTS) {
+                perr[q] = 2;
+                continue;
+            }
+            p.P = (int32_t)(D + 1);
+            r->h_log2B[q] = b.log2B;
+            double bits = b.log2B * (1.0 + 1e-9) + 2.0;
+            int k = primes_for_bits(bits);
+            if (k < 0 || k + c->extra_primes > GBR_MAX_PRIMES) {
+                perr[q] = 3;
+                continue;
+            }
+            p.k = k + c->extra_primes;
+            // drop mode: evaluate at spare points too; a leading coefficient of degree
+            // d vanishes at no more than d points modulo a prime that does not kill it
+            p.Pe = drop ? p.P + std::max(b.lcdf, 0) + std::max(b.lcdg, 0) : p.P;
+            // symmetric points 0, +-1, +-2, ... halve the evaluation work (lane pairs);
+            // the drop mode keeps the unit grid so that spare points are 0..Pe-1
+            p.sym = drop ? 0 : 1;
+            p.tiles = (p.P / 2 + 1 + 15) / 16;
+            // a complete symmetric set 0, +-1, ..., +-h (h = P/2, one point more when P
+            // is even) lets interpolation split into even and odd parts
+            if (p.sym) p.Pe = 2 * (p.P / 2) + 1;
+            if (p.Pe > GBR_MAX_POINTS + 2 * 4096) {
+                perr[q] = 4;
+                continue;
+            }
+            kcl = std::max(kcl, p.k + 32);
         }
-        if (b.m > GBR_MAX_YDEG || b.n > GBR_MAX_YDEG)
-            return c->fail(GBR_ELIMIT, "degree in the eliminated variable above GBR_MAX_YDEG");
-        p.dxf = std::max(b.dxf, 0);
-        p.dxg = std::max(b.dxg, 0);
-        int64_t D = degree_bound(b);
-        if (D + 1 > GBR_MAX_POINTS) return c->fail(GBR_ELIMIT, "x-degree bound above GBR_MAX_POINTS - 1");
-        p.P = (int32_t)(D + 1);
-        r->h_log2B[q] = b.log2B;
-        double bits = b.log2B * (1.0 + 1e-9) + 2.0;
-        int k = primes_for_bits(bits);
-        if (k < 0 || k + c->extra_primes > GBR_MAX_PRIMES)
-            return c->fail(GBR_ELIMIT, "coefficient bound needs more than GBR_MAX_PRIMES primes");
-        p.k = k + c->extra_primes;
-        // drop mode: evaluate at spare points too; a leading coefficient of degree
-        // d vanishes at no more than d points modulo a prime that does not kill it
-        p.Pe = drop ? p.P + std::max(b.lcdf, 0) + std::max(b.lcdg, 0) : p.P;
-        // symmetric points 0, +-1, +-2, ... halve the evaluation work (lane pairs);
-        // the drop mode keeps the unit grid so that spare points are 0..Pe-1
-        p.sym = drop ? 0 : 1;
-        p.tiles = (p.P / 2 + 1 + 15) / 16;
-        // a complete symmetric set 0, +-1, ..., +-h (h = P/2, one point more when P
-        // is even) lets interpolation split into even and odd parts
-        if (p.sym) p.Pe = 2 * (p.P / 2) + 1;
-        if (p.Pe > GBR_MAX_POINTS + 2 * 4096) return c->fail(GBR_ELIMIT, "too many spare points");
-        kc_max = std::max(kc_max, p.k + 32);
     }
+    for (int q = 0; q < n; ++q)
+        switch (perr[q]) {
+            case 0: break;
+            case 1: return c->fail(GBR_ELIMIT, "degree in the eliminated variable above GBR_MAX_YDEG");
+            case 2: return c->fail(GBR_ELIMIT, "x-degree bound above GBR_MAX_POINTS - 1");
+            case 3: return c->fail(GBR_ELIMIT, "coefficient bound needs more than GBR_MAX_PRIMES primes");
+            default: return c->fail(GBR_ELIMIT, "too many spare points");
+        }
+    const int kc_max = kcl;
     // ---- A6 (drop mode): primes that kill a leading coefficient are skipped
     std::vector<int32_t> pmap;
     int64_t dropped_primes = 0;
@@ -1191,9 +1215,16 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     int Kmax = 1, Pmax = 1, Lmax = 1, Kdig = 1;   // Kdig: most primes of one pair
     HostList red, interp, crt, crtf;
     int Kdig_f = 1, Lmax_f = 1;
-    std::map<int, HostList> evb;
-    std::map<int, HostList> evr;                    // register form, by N
-    std::map<int, std::vector<int32_t>> pgroups;   // pairs by point count
+    // evaluation buckets by y-degree (key / 4), register-form buckets by N, and
+    // contraction groups by (points, symmetric): flat tables in ascending key order
+    std::vector<HostList> evb_t((GBR_MAX_YDEG + 5) / 4 + 1);
+    std::vector<HostList> evr_t(kRegMaxN + 1);
+    std::vector<std::pair<int, int32_t>> pg_items;   // (2 P + sym, pair)
+    pg_items.reserve(n);
+    red.pairs.reserve(n);
+    red.start.reserve(n);
+    crtf.pairs.reserve(n);
+    crtf.start.reserve(n);
     std::vector<int32_t> mapped;                    // pairs with their own Garner table
     int kmapped = 0;
     int64_t subproblems = 0;
@@ -1231,11 +1262,11 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
         red.add(q, p.S);
         int key = ((std::max(p.m, p.n) + 1) + 3) / 4 * 4;
         const int rN = p.sym && c->reg_on ? reg_shape(p.m, p.n) : 0;
-        if (rN) evr[rN].add(q, (int64_t)k * p.tiles * 32);
-        else evb[key].add(q, p.sym ? (int64_t)k * p.tiles * 32 : (int64_t)k * p.Pe);
+        if (rN) evr_t[rN].add(q, (int64_t)k * p.tiles * 32);
+        else evb_t[key / 4].add(q, p.sym ? (int64_t)k * p.tiles * 32 : (int64_t)k * p.Pe);
         // the contraction serves pairs whose points are exactly 0..P-1 and whose
         // primes are the table prefix
-        if (p.pmap_off < 0 && (p.sym || p.Pe == p.P)) pgroups[2 * p.P + p.sym].push_back(q);
+        if (p.pmap_off < 0 && (p.sym || p.Pe == p.P)) pg_items.push_back({2 * p.P + p.sym, q});
         else interp.add(q, k);
         if (p.pmap_off < 0 && k <= kCrtFastK) {
             crtf.add(q, p.P);
@@ -1248,6 +1279,23 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
         int64_t ev = (int64_t)k * p.P * (b.tf + b.tg + 2LL * p.m * p.n);
         st.modmul_evalres += ev;
         st.modmul += ev + (int64_t)k * p.P * (p.P - 1) + (int64_t)p.P * k * (k - 1) / 2;
+    }
+    // the buckets as ordered maps of non-empty entries (same order as by key)
+    std::map<int, HostList> evb, evr;
+    for (size_t i = 0; i < evb_t.size(); ++i)
+        if (!evb_t[i].pairs.empty()) evb[(int)i * 4] = std::move(evb_t[i]);
+    for (size_t i = 0; i < evr_t.size(); ++i)
+        if (!evr_t[i].pairs.empty()) evr[(int)i] = std::move(evr_t[i]);
+    std::stable_sort(pg_items.begin(), pg_items.end(),
+                     [](const std::pair<int, int32_t> &x, const std::pair<int, int32_t> &y) { return x.first < y.first; });
+    std::map<int, std::vector<int32_t>> pgroups;   // pairs by point count
+    for (size_t i = 0; i < pg_items.size();) {
+        size_t j = i;
+        while (j < pg_items.size() && pg_items[j].first == pg_items[i].first) ++j;
+        std::vector<int32_t> &v = pgroups[pg_items[i].first];
+        v.reserve(j - i);
+        for (size_t t = i; t < j; ++t) v.push_back(pg_items[t].second);
+        i = j;
     }
     int rc = c->ensure_tables(Kmax, Pmax);
     if (rc) return rc;
