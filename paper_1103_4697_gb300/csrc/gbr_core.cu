@@ -103,10 +103,9 @@ double log2_prime_prefix(int k) {
 int primes_for_bits(double bits) {
     std::call_once(g_once, init_primes);
     // smallest k >= 1 with sum_{i<k} log2 p_i > bits; the sums are rounded to
-    // double, so demand a margin of 1e-6 bit
-    for (size_t k = 1; k < g_log2pref.size(); ++k)
-        if (g_log2pref[k] > bits + 1e-6) return (int)k;
-    return -1;
+    // double, so demand a margin of 1e-6 bit (the prefix sums increase)
+    const auto it = std::upper_bound(g_log2pref.begin() + 1, g_log2pref.end(), bits + 1e-6);
+    return it == g_log2pref.end() ? -1 : (int)(it - g_log2pref.begin());
 }
 
 static uint32_t to_mont_host(uint32_t x, uint32_t p) { return (uint32_t)(((uint64_t)x << 32) % p); }
@@ -1359,7 +1358,9 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
             for (int q : qs) interp.add(q, plan[q].k);
     }
     // ---- plan block: plans + work lists, one upload
-    std::vector<char> blk(sizeof(PairPlan) * n);
+    // (the resident batch keeps the block's storage, so later runs do not reallocate)
+    std::vector<char> &blk = r->h_blk;
+    blk.resize(sizeof(PairPlan) * n);
     std::memcpy(blk.data(), plan.data(), sizeof(PairPlan) * n);
     size_t o_red_p, o_red_s, o_int_p, o_int_s, o_crt_p, o_crt_s;
     put_list(blk, red, o_red_p, o_red_s);
@@ -1391,6 +1392,13 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     // one group and prime are adjacent so its V^-1 rows stay in L2)
     std::vector<GemmGroup> ggroups;
     std::vector<GemmTile> gtiles, ttiles;   // integer-pipe and tensor-core contraction tiles
+    {
+        size_t nt = 0;
+        for (const Gemm &gm : gemms)
+            nt += (size_t)gm.K * ((gm.rows + kTcTileM - 1) / kTcTileM) * ((gm.npairs + kGemmTileN - 1) / kGemmTileN);
+        ttiles.reserve(nt);
+        gtiles.reserve(nt);
+    }
     for (size_t gi = 0; gi < gemms.size(); ++gi) {
         const Gemm &gm = gemms[gi];
         GemmGroup gg;

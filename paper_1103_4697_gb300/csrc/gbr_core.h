@@ -108,6 +108,7 @@ struct gbr_resident {
     std::vector<gbr::PairDesc> h_desc;
     std::vector<gbr::PairPlan> h_plan;
     std::vector<double> h_log2B;        // the device's coefficient bound per job (log2)
+    std::vector<char> h_blk;            // host copy of the last plan block (storage reused)
     char *d_planblk = nullptr;
     size_t planblk_cap = 0;
     uint32_t *d_res = nullptr, *d_val = nullptr, *d_cf = nullptr, *d_out = nullptr;

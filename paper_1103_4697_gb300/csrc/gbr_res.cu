@@ -70,52 +70,6 @@ __device__ bool coef_top_bits(const uint64_t *w, int W, int &e, uint32_t &m32) {
     return true;
 }
 
-// log2 |c| of a two's-complement multi-word integer; -inf for zero.
-__device__ double coef_log2abs(const uint64_t *w, int W) {
-    uint64_t mag[8];
-    bool neg = (int64_t)w[W - 1] < 0;
-    uint64_t carry = 1;
-    for (int i = 0; i < W; ++i) {
-        uint64_t v = w[i];
-        if (neg) {
-            v = ~v + carry;
-            carry = (carry && v == 0) ? 1 : 0;
-        }
-        mag[i] = v;
-    }
-    int t = W - 1;
-    while (t >= 0 && mag[t] == 0) --t;
-    if (t < 0) return -INFINITY;
-    double v = (double)mag[t];
-    if (t > 0) v += (double)mag[t - 1] * 0x1p-64;
-    return log2(v) + 64.0 * t;
-}
-
-struct Lse {   // running log2 of a sum of powers of two: value = s * 2^mx
-    double mx, s;
-    __device__ void init() { mx = -INFINITY; s = 0.0; }
-    __device__ void add(double a) {
-        if (a == -INFINITY) return;
-        if (a > mx) { s = s * exp2(mx - a) + 1.0; mx = a; }
-        else s += exp2(a - mx);
-    }
-    __device__ void merge(double omx, double os) {
-        if (os == 0.0) return;
-        if (s == 0.0) { mx = omx; s = os; return; }
-        if (omx > mx) { s = s * exp2(mx - omx) + os; mx = omx; }
-        else s += os * exp2(omx - mx);
-    }
-    __device__ double log2v() const { return s == 0.0 ? -INFINITY : mx + log2(s); }
-};
-
-__device__ void warp_lse(Lse &l) {
-    for (int o = 16; o; o >>= 1) {
-        double omx = __shfl_xor_sync(0xffffffffu, l.mx, o);
-        double os = __shfl_xor_sync(0xffffffffu, l.s, o);
-        l.merge(omx, os);
-    }
-}
-
 __device__ __forceinline__ const uint64_t *coef_ptr(const uint64_t *coef, const PolyDesc &d, int r, int c) {
     return coef + d.off + ((int64_t)r * d.rstride + (int64_t)c * d.cstride) * d.words;
 }
@@ -162,7 +116,15 @@ __device__ __forceinline__ float log2_up_u128(uint64_t hi, uint64_t lo) {
     return __fadd_ru((float)s, __fadd_ru(log2f(mf), 0x1p-18f));
 }
 
-__device__ __forceinline__ float log2_up(double x);
+// log2 x rounded up to a float, for a positive finite double x: the exponent
+// from the bits, log2f of the mantissa in [1, 2) (converted upward; log2f is
+// within 1 ulp, below 2^-23 there, covered by the 2^-20 added), the sum rounded up
+__device__ __forceinline__ float log2_up(double x) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff) - 1023;
+    const double mant = __longlong_as_double((b & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
+    return __fadd_ru((float)e, __fadd_ru(log2f(__double2float_ru(mant)), 0x1p-20f));
+}
 
 // An upper bound of log2 of the row norm used by the Hadamard bound, as a float
 // (-inf for a zero row).  Single-word rows: half the log2 of the autocorrelation
@@ -260,24 +222,16 @@ __device__ float row_log2_up(const uint64_t *coef, const PolyDesc &P, int r, int
     return __fadd_ru((float)emax, __fadd_ru(log2f(sum), 0x1p-19f));
 }
 
-// log2 x rounded up to a float, for a positive finite double x: the exponent
-// from the bits, log2f of the mantissa in [1, 2) (converted upward; log2f is
-// within 1 ulp, below 2^-23 there, covered by the 2^-20 added), the sum rounded up
-__device__ __forceinline__ float log2_up(double x) {
-    const long long b = __double_as_longlong(x);
-    const int e = (int)((b >> 52) & 0x7ff) - 1023;
-    const double mant = __longlong_as_double((b & 0x000FFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
-    return __fadd_ru((float)e, __fadd_ru(log2f(__double2float_ru(mant)), 0x1p-20f));
-}
-
 // ceil(x 2^16) for a finite |x| < 2^15 (the scaling is exact)
 __device__ __forceinline__ long long fx16_up(float x) { return (long long)__float2int_ru(x * 65536.0f); }
 
 // 2 tm + log2 s, in units of 2^-16 and rounded up, for the sum s of the terms
 // exp2f(max(2 (t_k - tm) rounded up, -120)) of a set of exponents t_k with the
-// finite maximum tm: an upper bound of log2 sum_k 2^(2 t_k).  exp2f (within 2
+// finite maximum tm (or any tm at least as large whose largest term is at least
+// 2^-100): an upper bound of log2 sum_k 2^(2 t_k).  exp2f (within 2
 // ulp) and the round-up sums of at most 256 terms are covered by the factor
-// 1 + 2^-20, log2f of s in [1, 2^9) (within 1 ulp, below 2^-15) by adding 2^-14;
+// 1 + 2^-20, log2f of s in [2^-100, 2^9) (within 1 ulp, at most 2^-17 there) by
+// adding 2^-14;
 // terms below 2^-120 of the largest are raised to it (that only enlarges it).
 __device__ __forceinline__ long long log2_sum_fx(float tm, float s) {
     return 2 * fx16_up(tm) + fx16_up(__fadd_ru(log2f(__fmul_ru(s, 1.0f + 0x1p-20f)), 0x1p-14f));
@@ -289,12 +243,13 @@ __device__ __forceinline__ float exp2_term(float t, float tm) { return exp2f(fma
 // in units of 2^-16 and rounded up, evaluated warp-parallel: lanes split the rows
 // for the scaled squared norms and the columns for their logarithms.  lf, lg are
 // float upper bounds of the log2 row norms (-inf for zero rows); the scaled
-// exponents t = lf_i + i l2lam are rounded up; every sum of powers is shifted by
-// its own largest term (the rows of f, the rows of g, each column); the outer
+// exponents t = lf_i + i l2lam are rounded up; the row sums are shifted by their
+// own largest term (the rows of f, the rows of g), a column by the overall
+// largest term M unless its own is more than 50 below M (then by its own); the outer
 // sums are exact integer sums.  LLONG_MIN when a column of the Sylvester matrix
 // is zero (the resultant vanishes).  l2lam is a multiple of 1/4 in [-2^2, 2^3].
 __device__ long long scaled_hadamard_fx(const float *lf, int m, const float *lg, int n, float l2lam, float *tf,
-                                        float *tg, int lane) {
+                                        float *tg, float *ef, float *eg, int lane) {
     float Mf = -INFINITY, Mg = -INFINITY;
     for (int i = lane; i <= m; i += 32) {
         const float t = lf[i] == -INFINITY ? -INFINITY : __fmaf_ru((float)i, l2lam, lf[i]);
@@ -311,11 +266,19 @@ __device__ long long scaled_hadamard_fx(const float *lf, int m, const float *lg,
         Mg = fmaxf(Mg, __shfl_xor_sync(0xffffffffu, Mg, o));
     }
     __syncwarp();
+    // the terms once more against the overall maximum M, for the columns
+    const float M = fmaxf(Mf, Mg);
     float sf = 0.0f, sg = 0.0f;
-    for (int i = lane; i <= m; i += 32)
-        if (tf[i] != -INFINITY) sf = __fadd_ru(sf, exp2_term(tf[i], Mf));
-    for (int j = lane; j <= n; j += 32)
-        if (tg[j] != -INFINITY) sg = __fadd_ru(sg, exp2_term(tg[j], Mg));
+    for (int i = lane; i <= m; i += 32) {
+        const bool z = tf[i] == -INFINITY;
+        if (!z) sf = __fadd_ru(sf, exp2_term(tf[i], Mf));
+        ef[i] = z ? 0.0f : exp2_term(tf[i], M);
+    }
+    for (int j = lane; j <= n; j += 32) {
+        const bool z = tg[j] == -INFINITY;
+        if (!z) sg = __fadd_ru(sg, exp2_term(tg[j], Mg));
+        eg[j] = z ? 0.0f : exp2_term(tg[j], M);
+    }
     for (int o = 16; o; o >>= 1) {
         sf = __fadd_ru(sf, __shfl_xor_sync(0xffffffffu, sf, o));
         sg = __fadd_ru(sg, __shfl_xor_sync(0xffffffffu, sg, o));
@@ -337,11 +300,19 @@ __device__ long long scaled_hadamard_fx(const float *lf, int m, const float *lg,
             continue;
         }
         float sc = 0.0f;
-        for (int r = fr0; r <= fr1; ++r)
-            if (tf[m - (c - r)] != -INFINITY) sc = __fadd_ru(sc, exp2_term(tf[m - (c - r)], mc));
-        for (int r = gr0; r <= gr1; ++r)
-            if (tg[n - (c - r)] != -INFINITY) sc = __fadd_ru(sc, exp2_term(tg[n - (c - r)], mc));
-        col += log2_sum_fx(mc, sc);
+        if (mc >= M - 50.0f) {
+            // the terms against M: the largest is at least 2^-100, so raising the
+            // others to 2^-120 enlarges the sum by at most 256 2^-20 of it
+            for (int r = fr0; r <= fr1; ++r) sc = __fadd_ru(sc, ef[m - (c - r)]);
+            for (int r = gr0; r <= gr1; ++r) sc = __fadd_ru(sc, eg[n - (c - r)]);
+            col += log2_sum_fx(M, sc);
+        } else {
+            for (int r = fr0; r <= fr1; ++r)
+                if (tf[m - (c - r)] != -INFINITY) sc = __fadd_ru(sc, exp2_term(tf[m - (c - r)], mc));
+            for (int r = gr0; r <= gr1; ++r)
+                if (tg[n - (c - r)] != -INFINITY) sc = __fadd_ru(sc, exp2_term(tg[n - (c - r)], mc));
+            col += log2_sum_fx(mc, sc);
+        }
     }
     for (int o = 16; o; o >>= 1) col += __shfl_xor_sync(0xffffffffu, col, o);
     zero = __any_sync(0xffffffffu, zero);
@@ -350,9 +321,12 @@ __device__ long long scaled_hadamard_fx(const float *lf, int m, const float *lg,
     return (row < col ? row : col) - lam;
 }
 
-__global__ void __launch_bounds__(kBoundsWarps * 32) k_bounds(ResLaunch L) {
+// (at most 72 registers: seven 4-warp blocks per SM, so a batch of 4096 pairs
+// runs in one wave on 152 SMs)
+__global__ void __launch_bounds__(kBoundsWarps * 32, 7) k_bounds(ResLaunch L) {
     __shared__ float lff[kBoundsWarps][GBR_MAX_YDEG + 2], lgf[kBoundsWarps][GBR_MAX_YDEG + 2];
     __shared__ float tbuf[kBoundsWarps][2][GBR_MAX_YDEG + 2];
+    __shared__ float xbuf[kBoundsWarps][2][GBR_MAX_YDEG + 2];
     __shared__ int64_t rbuf[kBoundsWarps][kRowBuf];
     const int wib = threadIdx.x >> 5;
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -419,7 +393,7 @@ __global__ void __launch_bounds__(kBoundsWarps * 32) k_bounds(ResLaunch L) {
         long long best = LLONG_MAX;
         for (int l = 0; l < kBoundLambdas; ++l) {
             const long long v = scaled_hadamard_fx(lff[wib], B.m, lgf[wib], B.n, bound_lambda_f(l), tbuf[wib][0],
-                                                   tbuf[wib][1], lane);
+                                                   tbuf[wib][1], xbuf[wib][0], xbuf[wib][1], lane);
             best = v < best ? v : best;
         }
         lb = best == LLONG_MIN ? -INFINITY : (double)best * 0x1p-17 + 0x1p-10;
