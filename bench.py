@@ -169,11 +169,14 @@ def serving_run(ctx, n_burst: int = 1500, n_stream: int = 6000, load: float = 0.
         return jobs, keep
 
     def run(jobs, arrivals):
-        """A submitter thread releases each job at its arrival time; this thread sweeps
-        the outstanding tickets with non-blocking polls and stamps completions."""
+        """A submitter thread releases each job at its arrival time; this thread takes
+        finished jobs with gbr_wait_any (blocking in the library, without the GIL) and
+        keeps the library's completion time of each, on perf_counter's clock."""
         n = len(jobs)
         done = [0.0] * n
-        tickets = [None] * n
+        index = {}
+        # both clocks are CLOCK_MONOTONIC on Linux; the offset removes any difference
+        off = time.perf_counter() - L.gbr_clock()
         t0 = time.perf_counter() + 0.01
 
         def submitter():
@@ -183,29 +186,26 @@ def serving_run(ctx, n_burst: int = 1500, n_stream: int = 6000, load: float = 0.
                     time.sleep(delay)
                 t = C.c_uint64()
                 N.check(L.gbr_submit(ctx.handle, C.byref(j), C.byref(t)), ctx.handle)
-                tickets[i] = t.value
+                index[t.value] = i
 
         th = threading.Thread(target=submitter)
         th.start()
-        pending, nxt, left = [], 0, n
         out = N.BigPoly()
+        tk = C.c_uint64()
+        td = C.c_double()
+        left = n
         while left:
-            while nxt < n and tickets[nxt] is not None:
-                pending.append(nxt)
-                nxt += 1
-            still = []
-            for i in pending:
-                st = L.gbr_poll(ctx.handle, C.c_uint64(tickets[i]), C.byref(out), 0)
-                if st == N.EAGAIN:
-                    still.append(i)
-                    continue
-                done[i] = time.perf_counter()
-                assert st == N.OK, f"serving request failed with status {st}"
-                L.gbr_free_result(ctx.handle, C.byref(out))
-                left -= 1
-            if len(still) == len(pending):
-                time.sleep(5e-5)
-            pending = still
+            st = L.gbr_wait_any(ctx.handle, 100, C.byref(tk), C.byref(out), C.byref(td))
+            if st in (N.ETIMEOUT, N.EAGAIN, N.ENOTFOUND):
+                if st == N.ENOTFOUND:
+                    time.sleep(1e-4)                    # nothing submitted yet
+                continue
+            assert st == N.OK, f"serving request failed with status {st}"
+            while tk.value not in index:                # the submitter records the ticket
+                time.sleep(1e-6)
+            done[index[tk.value]] = td.value + off
+            L.gbr_free_result(ctx.handle, C.byref(out))
+            left -= 1
         th.join()
         return t0, done
 

@@ -282,6 +282,19 @@ typedef struct {
 int gbr_submit(gbr_ctx *ctx, const gbr_job *job, uint64_t *ticket);
 int gbr_poll(gbr_ctx *ctx, uint64_t ticket, gbr_bigpoly *out, int timeout_ms);
 
+/* The next finished job in completion order, whichever it is: waits up to
+ * timeout_ms (0 = do not wait, <0 = until one finishes) and returns its status
+ * (GBR_OK with the result in *out, or the job's own error), its ticket, and in
+ * *t_done (may be NULL) the time it finished in seconds on gbr_clock.  The
+ * ticket is consumed; tickets already consumed by gbr_poll are skipped.
+ * GBR_EAGAIN/GBR_ETIMEOUT when none finished in time, GBR_ENOTFOUND when no job
+ * is outstanding. */
+int gbr_wait_any(gbr_ctx *ctx, int timeout_ms, uint64_t *ticket, gbr_bigpoly *out, double *t_done);
+
+/* Seconds on the library's monotonic clock (the steady clock of the C++
+ * runtime: CLOCK_MONOTONIC on Linux). */
+double gbr_clock(void);
+
 /* Serving counters: jobs admitted, batches launched, peak bytes in flight. */
 typedef struct {
     int64_t submitted, completed, batches, max_batch, peak_bytes, waits_for_memory;

@@ -428,6 +428,22 @@ def _poll(self, ticket: int, timeout_ms: int = -1):
     return r
 
 
+def _wait_any(self, timeout_ms: int = -1):
+    """gbr_wait_any: (ticket, result as a list of ints, completion time in seconds on
+    gbr_clock) of the next finished job, or None when none finished in time or no
+    job is outstanding."""
+    out = N.BigPoly()
+    t = C.c_uint64()
+    td = C.c_double()
+    st = N.lib().gbr_wait_any(self.handle, int(timeout_ms), C.byref(t), C.byref(out), C.byref(td))
+    if st in (N.EAGAIN, N.ETIMEOUT, N.ENOTFOUND):
+        return None
+    N.check(st, self.handle)
+    r = bigpoly_to_ints(out)
+    N.lib().gbr_free_result(self.handle, C.byref(out))
+    return t.value, r, td.value
+
+
 def _serve_stats(self) -> dict:
     s = N.ServeStats()
     N.check(N.lib().gbr_get_serve_stats(self.handle, C.byref(s)), self.handle)
@@ -436,4 +452,5 @@ def _serve_stats(self) -> dict:
 
 Context.submit = _submit
 Context.poll = _poll
+Context.wait_any = _wait_any
 Context.serve_stats = _serve_stats

@@ -2,8 +2,10 @@
 //
 // gbr_submit deep-copies a job into the queue and returns a ticket.  Worker
 // threads (one CUDA stream and one child context each, all sharing the parent
-// context's device arena) repeatedly take every queued job that fits the
-// device-memory budget, group them by kind, and run them as device batches.
+// context's device arena) repeatedly take their share of the queued jobs (a
+// third of the queue, at least 32) as far as the device-memory budget allows,
+// group them by kind, and run them as device batches; gbr_wait_any hands out
+// finished jobs in completion order.
 // Because several workers run at once on separate streams, a batch that
 // arrives while another is on the GPU is admitted as soon as memory allows and
 // overlaps with it.  Residues stay in device memory for the whole life of a
@@ -27,14 +29,20 @@ struct ServeJob {
     size_t est = 0;                  // device bytes reserved while in flight
     int status = GBR_EAGAIN;
     bool done = false;
+    double t_done = 0.0;             // completion time, seconds on the steady clock
     gbr_bigpoly result{-1, 0, nullptr, nullptr};
 };
+
+static double steady_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
 
 struct ServeState {
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<std::shared_ptr<ServeJob>> queue;
     std::unordered_map<uint64_t, std::shared_ptr<ServeJob>> jobs;
+    std::deque<uint64_t> completions;   // tickets in completion order (gbr_wait_any)
     std::vector<std::thread> threads;
     std::vector<gbr_ctx *> workers;
     bool stop = false;
@@ -45,6 +53,7 @@ struct ServeState {
 
 static const int kWorkers = 3;
 static const int kMaxBatch = 8192;
+static const size_t kMinShare = 32;   // a worker takes at least this many queued jobs
 
 static size_t estimate_bytes(const ServeJob &j) {
     if (j.kind == GBR_JOB_GCD) {
@@ -63,13 +72,20 @@ static size_t estimate_bytes(const ServeJob &j) {
     return (size_t)(k * S * 4 + k * P * 4 + P * L * 4 + P + in + 8192);
 }
 
+// marks j finished (caller holds S->mu) and queues its ticket for gbr_wait_any
+static void mark_done(ServeState *S, ServeJob &j, int status) {
+    j.status = status;
+    j.done = true;
+    j.t_done = steady_s();
+    S->completions.push_back(j.ticket);
+    S->stats.completed++;
+}
+
 static void finish(ServeState *S, const std::shared_ptr<ServeJob> &j, int status, const gbr_bigpoly *r) {
     std::lock_guard<std::mutex> g(S->mu);
-    j->status = status;
     if (r) j->result = *r;
-    j->done = true;
     S->inflight -= j->est;
-    S->stats.completed++;
+    mark_done(S, *j, status);
 }
 
 // a failing job's detail text goes to the parent context, where gbr_last_error finds it
@@ -130,13 +146,14 @@ static void worker_loop(gbr_ctx *parent, int wi) {
             std::unique_lock<std::mutex> lk(S->mu);
             S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty(); });
             if (S->stop) return;
-            // admission by memory: take queued jobs while they fit the budget
-            while (!S->queue.empty() && (int)batch.size() < kMaxBatch) {
+            // admission by memory: take queued jobs while they fit the budget, at most
+            // a worker's share of the queue (so a burst spreads over the workers'
+            // streams and overlaps on the device instead of waiting in one batch)
+            const size_t share = std::max<size_t>(kMinShare, (S->queue.size() + kWorkers - 1) / kWorkers);
+            while (!S->queue.empty() && (int)batch.size() < kMaxBatch && batch.size() < share) {
                 auto &j = S->queue.front();
                 if (j->est > S->cap) {   // can never fit: fail it now
-                    j->status = GBR_ENOMEM;
-                    j->done = true;
-                    S->stats.completed++;
+                    mark_done(S, *j, GBR_ENOMEM);
                     S->queue.pop_front();
                     S->cv_done.notify_all();
                     continue;
@@ -203,10 +220,7 @@ void gbr_serve_shutdown(gbr_ctx *c) {
     {
         std::lock_guard<std::mutex> g(S->mu);
         S->stop = true;
-        for (auto &j : S->queue) {
-            j->status = GBR_ECANCELED;
-            j->done = true;
-        }
+        for (auto &j : S->queue) mark_done(S, *j, GBR_ECANCELED);
         S->queue.clear();
     }
     S->cv_work.notify_all();
@@ -294,6 +308,39 @@ extern "C" int gbr_poll(gbr_ctx *c, uint64_t ticket, gbr_bigpoly *out, int timeo
     S->jobs.erase(ticket);
     return st;
 }
+
+extern "C" int gbr_wait_any(gbr_ctx *c, int timeout_ms, uint64_t *ticket, gbr_bigpoly *out, double *t_done) {
+    if (!c || !ticket || !out) return GBR_EINVAL;
+    if (!c->serve) return GBR_ENOTFOUND;
+    ServeState *S = c->serve;
+    std::unique_lock<std::mutex> lk(S->mu);
+    // tickets already consumed by gbr_poll are skipped
+    auto ready = [&] {
+        while (!S->completions.empty() && !S->jobs.count(S->completions.front())) S->completions.pop_front();
+        return !S->completions.empty() || S->jobs.empty();
+    };
+    if (!ready()) {
+        if (timeout_ms == 0) return GBR_EAGAIN;
+        if (timeout_ms < 0) S->cv_done.wait(lk, ready);
+        else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) return GBR_ETIMEOUT;
+    }
+    if (S->completions.empty()) return GBR_ENOTFOUND;   // nothing outstanding
+    const uint64_t t = S->completions.front();
+    S->completions.pop_front();
+    auto it = S->jobs.find(t);
+    std::shared_ptr<ServeJob> j = it->second;
+    *ticket = t;
+    if (t_done) *t_done = j->t_done;
+    const int st = j->status;
+    if (st == GBR_OK) {
+        *out = j->result;
+        j->result = gbr_bigpoly{-1, 0, nullptr, nullptr};
+    }
+    S->jobs.erase(it);
+    return st;
+}
+
+extern "C" double gbr_clock(void) { return steady_s(); }
 
 extern "C" int gbr_get_serve_stats(gbr_ctx *c, gbr_serve_stats *out) {
     if (!c || !out) return GBR_EINVAL;

@@ -90,6 +90,9 @@ SIGNATURES = {
     "gbr_free_result": (None, [C.c_void_p, C.POINTER(BigPoly)]),
     "gbr_submit": (C.c_int, [C.c_void_p, C.POINTER(Job), C.POINTER(C.c_uint64)]),
     "gbr_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(BigPoly), C.c_int]),
+    "gbr_wait_any": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_uint64), C.POINTER(BigPoly),
+                               C.POINTER(C.c_double)]),
+    "gbr_clock": (C.c_double, []),
     "gbr_get_serve_stats": (C.c_int, [C.c_void_p, C.POINTER(ServeStats)]),
     "gbr_calibrate": (C.c_int, [C.c_void_p, C.POINTER(Calib)]),
     "gbr_crt_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_int, C.c_void_p,

@@ -103,3 +103,39 @@ def test_full_mix_burst_sampled(ctx):
             assert v == O.res_at_prs(r.a, r.b, a)
             if r.planted:
                 assert got == []
+
+
+def test_wait_any_returns_every_job_once(ctx):
+    """gbr_wait_any hands out finished jobs in completion order: every ticket once,
+    with the result gbr_poll would give, mixed with tickets consumed by polls."""
+    from paper_1103_4697_gb300 import native as N
+    from paper_1103_4697_gb300.native import JOB_GCD, JOB_RESULTANT
+
+    reqs = W.serving_stream(9, 120, rate=1e9, dlo=3, dhi=8, blo=8, bhi=40)
+    t0 = N.lib().gbr_clock()
+    tickets = {}
+    for r in reqs:
+        kind = JOB_RESULTANT if r.kind == "res" else JOB_GCD
+        tickets[ctx.submit(kind, r.a, r.b)] = (kind, r)
+    # a few tickets are taken by polls first; wait_any must skip them
+    polled = {}
+    for t in list(tickets)[:5]:
+        polled[t] = ctx.poll(t, -1)
+    got, times = {}, []
+    while True:
+        x = ctx.wait_any(2000)
+        if x is None:
+            break
+        t, res, td = x
+        assert t in tickets and t not in got and t not in polled
+        got[t] = res
+        times.append(td)
+    assert len(got) + len(polled) == len(tickets)
+    assert times == sorted(times) and times[0] >= t0
+    for t, res in list(got.items())[:40] + list(polled.items()):
+        kind, r = tickets[t]
+        if kind == JOB_GCD:
+            assert res == list(O.gcd_z(r.a, r.b))
+        else:
+            assert res == list(O.res_subres(r.a, r.b))
+    assert ctx.wait_any(0) is None                 # nothing outstanding
