@@ -33,6 +33,9 @@ Functions
 ``gcd_z``         primitive polynomial remainder sequence over Z.
 ``sqf_yun``       square-free factorisation R = u prod r_i^i (Section 2.1) by Yun's
                   algorithm over Z with primitive gcds.
+``gcd_zxy``       gcd in Z[x][y] by the primitive remainder sequence over Z[x];
+                  ``content_y`` (content removal, Section 2), ``teissier_q``
+                  (Q = res(f_x/h, f_y/h, y), h = gcd(f_x, f_y), Section 2.1).
 
 Every function is pinned by ``tests/test_oracle.py`` against closed forms
 (planted roots), invariants (symmetry, multiplicativity, planted common factor),
@@ -45,10 +48,13 @@ from .resultant import (sylvester, det_bareiss, res_bareiss, res_leibniz, res_su
                         res_at, disc_res, deriv_y, ydeg, xdeg, res_univariate, degree_bound)
 from .gcd import gcd_z, divides_z
 from .sqf import sqf_yun
+from . import bigcd
+from .bigcd import content_y, divexact_zxy, gcd_zxy, teissier_parts, teissier_q
 
 __all__ = [
     "ZZ", "ZX", "zx_add", "zx_sub", "zx_mul", "zx_neg", "zx_trim", "zx_eval", "zx_divexact",
     "zx_deg", "content", "primitive_part", "sylvester", "det_bareiss", "res_bareiss", "res_leibniz",
     "res_subres", "res_evalz", "res_at", "res_at_prs", "disc_res", "deriv_y", "ydeg", "xdeg", "res_univariate",
-    "degree_bound", "gcd_z", "divides_z", "sqf_yun",
+    "degree_bound", "gcd_z", "divides_z", "sqf_yun", "bigcd", "content_y", "divexact_zxy", "gcd_zxy",
+    "teissier_parts", "teissier_q",
 ]

@@ -405,3 +405,141 @@ def test_sqf_invariants_on_discriminant_resultant(seed):
         assert sympy.degree(sympy.gcd(polys[i], polys[i].diff(x)), x) <= 0
         for j in range(i):
             assert sympy.degree(sympy.gcd(polys[i], polys[j]), x) <= 0
+
+
+# --------------------------------------------------------------------------- bivariate gcd, Teissier Q
+
+def _rows_mul(a, b):
+    out = [[0] * (max(len(r) for r in a) + max(len(r) for r in b) - 1) for _ in range(len(a) + len(b) - 1)]
+    for j1, r1 in enumerate(a):
+        for i1, c1 in enumerate(r1):
+            if c1:
+                for j2, r2 in enumerate(b):
+                    for i2, c2 in enumerate(r2):
+                        out[j1 + j2][i1 + i2] += c1 * c2
+    return out
+
+
+def _rand_bipoly(rng, dy, dx, amp):
+    f = [[rng.randint(-amp, amp) for _ in range(dx + 1)] for _ in range(dy + 1)]
+    f[dy][rng.randint(0, dx)] = rng.choice([1, -1, 2, 3])
+    return f
+
+
+def test_bigcd_hand_cases():
+    from oracle.bigcd import content_y, gcd_zxy, teissier_parts, teissier_q
+
+    xpy, xmy = [[0, 1], [1]], [[0, 1], [-1]]
+    assert gcd_zxy([[0, 0], [0, 1]], [[0, 0, 1]]) == [(0, 1)]                 # gcd(x y, x^2) = x
+    assert gcd_zxy(_rows_mul(xpy, xpy), _rows_mul(xpy, xmy)) == [(0, 1), (1,)]   # x + y
+    assert gcd_zxy([[0]], [[0]]) == []
+    assert gcd_zxy([[0, 0], [0, -3]], [[0]]) == [(), (0, 3)]                 # gcd(-3 x y, 0) = 3 x y
+    assert content_y([[4, 2], [0, 2]]) == (2,)                               # 2 x y + 2 x + 4
+    assert content_y([[0, 2], [0, 4]]) == (0, 2)                             # 4 x y + 2 x
+    f = _rows_mul(xpy, xpy)
+    f[0][0] += 1                                                             # (x + y)^2 + 1
+    h, fxs, fys = teissier_parts(f)
+    assert h == [(0, 2), (2,)] and fxs == [(1,)] and fys == [(1,)] and teissier_q(f) == (1,)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_bigcd_planted_factor(seed):
+    """A planted common factor h divides the gcd, the gcd divides both inputs, and
+    the cofactors are coprime: their contents have gcd 1 (gcd_z) and at some
+    integer x = a with non-vanishing leading coefficients their univariate gcd in y
+    is constant."""
+    from oracle.bigcd import content_y, divexact_zxy, gcd_zxy
+
+    rng = random.Random(4100 + seed)
+    h = _rand_bipoly(rng, rng.randint(1, 2), rng.randint(0, 2), 3)
+    u = _rand_bipoly(rng, rng.randint(0, 2), rng.randint(0, 2), 5)
+    v = _rand_bipoly(rng, rng.randint(0, 2), rng.randint(0, 2), 5)
+    if seed % 3 == 0:                       # a shared factor in x alone as well
+        u = _rows_mul(u, [[seed + 1, 1]])
+        v = _rows_mul(v, [[seed + 1, 1]])
+    f, g = _rows_mul(h, u), _rows_mul(h, v)
+    G = gcd_zxy(f, g)
+    assert divexact_zxy(G, [tuple(r) for r in O.bigcd.as_zxy(h)]) is not None      # h | G
+    a, b = divexact_zxy(f, G), divexact_zxy(g, G)                            # G | f, G | g
+    assert O.gcd_z(content_y(a), content_y(b)) == (1,)
+    ok = False
+    for x0 in range(-6, 7):
+        ra = [O.zx_eval(r, x0) for r in a]
+        rb = [O.zx_eval(r, x0) for r in b]
+        if ra[-1] == 0 or rb[-1] == 0:
+            continue
+        if len(O.gcd_z(ra, rb)) == 1:
+            ok = True
+            break
+    assert ok
+    assert G[-1][-1] > 0
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_bigcd_against_sympy(seed):
+    sympy = pytest.importorskip("sympy")
+    from oracle.bigcd import gcd_zxy
+
+    x, y = sympy.symbols("x y")
+    rng = random.Random(4200 + seed)
+    h = _rand_bipoly(rng, rng.randint(0, 2), rng.randint(0, 2), 4)
+    u = _rand_bipoly(rng, rng.randint(0, 2), rng.randint(0, 3), 6)
+    v = _rand_bipoly(rng, rng.randint(0, 2), rng.randint(0, 3), 6)
+    f, g = _rows_mul(h, u), _rows_mul(h, v)
+
+    def expr(rows):
+        return sum(c * x**i * y**j for j, r in enumerate(rows) for i, c in enumerate(r))
+
+    want = sympy.Poly(sympy.gcd(expr(f), expr(g)), y, x)
+    got = sympy.Poly(expr([list(r) for r in gcd_zxy(f, g)]), y, x)
+    assert got == want or got == -want
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_teissier_q_against_sympy(seed):
+    sympy = pytest.importorskip("sympy")
+    from oracle.bigcd import teissier_q
+
+    x, y = sympy.symbols("x y")
+    rng = random.Random(4300 + seed)
+    if seed % 2 == 0:                       # f = g(x + 2y) + (small perturbation in x only)
+        L = [[0, 1], [2]]
+        f, p = [[rng.randint(-4, 4)]], [[1]]
+        for k in range(1, 4):
+            p = _rows_mul(p, L)
+            c = rng.randint(-3, 3) or 1
+            f = [[(f[j][i] if j < len(f) and i < len(f[j]) else 0) + c * (p[j][i] if j < len(p) and i < len(p[j]) else 0)
+                  for i in range(max(len(r) for r in f + p))] for j in range(max(len(f), len(p)))]
+    else:                                   # a generic curve: gcd(f_x, f_y) = 1
+        f = _rand_bipoly(rng, 3, 3, 5)
+
+    def expr(rows):
+        return sum(c * x**i * y**j for j, r in enumerate(rows) for i, c in enumerate(r))
+
+    F = expr(f)
+    fx, fy = sympy.diff(F, x), sympy.diff(F, y)
+    h = sympy.gcd(fx, fy)
+    Q = sympy.resultant(sympy.quo(fx, h), sympy.quo(fy, h), y)
+    want = sympy.Poly(Q, x).all_coeffs()[::-1] if Q != 0 else []
+    got = list(teissier_q(f))
+    while want and want[-1] == 0:
+        want.pop()
+    assert got == [int(c) for c in want] or got == [-int(c) for c in want]
+
+
+def test_teissier_q_generic_curve_is_the_plain_resultant():
+    """gcd(f_x, f_y) = 1 for a generic curve, so Q = res(f_x, f_y) itself (with the
+    x-derivative taken row by row)."""
+    from oracle.bigcd import deriv_x, teissier_parts, teissier_q
+
+    rng = random.Random(4400)
+    f = _rand_bipoly(rng, 4, 4, 9)
+    h, _, _ = teissier_parts(f)
+    assert len(h) == 1 and len(h[0]) == 1                        # a constant
+    fx = [list(r) or [0] for r in deriv_x(f)]
+    fy = [list(r) or [0] for r in O.deriv_y(f)]
+    want = O.res_subres(fx, fy)
+    c = h[0][0]
+    # res(f_x / c, f_y / c) = c^-(deg f_x + deg f_y) res(f_x, f_y) in y
+    m, n = O.ydeg(fx), O.ydeg(fy)
+    assert tuple(v * c ** (m + n) for v in teissier_q(f)) == tuple(want)
