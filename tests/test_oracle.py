@@ -420,7 +420,7 @@ def _rows_mul(a, b):
     return out
 
 
-def _rand_bipoly(rng, dy, dx, amp):
+def _rand_bivariate(rng, dy, dx, amp):
     f = [[rng.randint(-amp, amp) for _ in range(dx + 1)] for _ in range(dy + 1)]
     f[dy][rng.randint(0, dx)] = rng.choice([1, -1, 2, 3])
     return f
@@ -451,9 +451,9 @@ def test_bigcd_planted_factor(seed):
     from oracle.bigcd import content_y, divexact_zxy, gcd_zxy
 
     rng = random.Random(4100 + seed)
-    h = _rand_bipoly(rng, rng.randint(1, 2), rng.randint(0, 2), 3)
-    u = _rand_bipoly(rng, rng.randint(0, 2), rng.randint(0, 2), 5)
-    v = _rand_bipoly(rng, rng.randint(0, 2), rng.randint(0, 2), 5)
+    h = _rand_bivariate(rng, rng.randint(1, 2), rng.randint(0, 2), 3)
+    u = _rand_bivariate(rng, rng.randint(0, 2), rng.randint(0, 2), 5)
+    v = _rand_bivariate(rng, rng.randint(0, 2), rng.randint(0, 2), 5)
     if seed % 3 == 0:                       # a shared factor in x alone as well
         u = _rows_mul(u, [[seed + 1, 1]])
         v = _rows_mul(v, [[seed + 1, 1]])
@@ -482,9 +482,9 @@ def test_bigcd_against_sympy(seed):
 
     x, y = sympy.symbols("x y")
     rng = random.Random(4200 + seed)
-    h = _rand_bipoly(rng, rng.randint(0, 2), rng.randint(0, 2), 4)
-    u = _rand_bipoly(rng, rng.randint(0, 2), rng.randint(0, 3), 6)
-    v = _rand_bipoly(rng, rng.randint(0, 2), rng.randint(0, 3), 6)
+    h = _rand_bivariate(rng, rng.randint(0, 2), rng.randint(0, 2), 4)
+    u = _rand_bivariate(rng, rng.randint(0, 2), rng.randint(0, 3), 6)
+    v = _rand_bivariate(rng, rng.randint(0, 2), rng.randint(0, 3), 6)
     f, g = _rows_mul(h, u), _rows_mul(h, v)
 
     def expr(rows):
@@ -511,7 +511,7 @@ def test_teissier_q_against_sympy(seed):
             f = [[(f[j][i] if j < len(f) and i < len(f[j]) else 0) + c * (p[j][i] if j < len(p) and i < len(p[j]) else 0)
                   for i in range(max(len(r) for r in f + p))] for j in range(max(len(f), len(p)))]
     else:                                   # a generic curve: gcd(f_x, f_y) = 1
-        f = _rand_bipoly(rng, 3, 3, 5)
+        f = _rand_bivariate(rng, 3, 3, 5)
 
     def expr(rows):
         return sum(c * x**i * y**j for j, r in enumerate(rows) for i, c in enumerate(r))
@@ -533,7 +533,7 @@ def test_teissier_q_generic_curve_is_the_plain_resultant():
     from oracle.bigcd import deriv_x, teissier_parts, teissier_q
 
     rng = random.Random(4400)
-    f = _rand_bipoly(rng, 4, 4, 9)
+    f = _rand_bivariate(rng, 4, 4, 9)
     h, _, _ = teissier_parts(f)
     assert len(h) == 1 and len(h[0]) == 1                        # a constant
     fx = [list(r) or [0] for r in deriv_x(f)]
