@@ -203,6 +203,44 @@ int gbr_resultant_batch(gbr_ctx *ctx, int n, const gbr_bipoly *f, const gbr_bipo
 int gbr_discriminant_res_batch(gbr_ctx *ctx, int n, const gbr_bipoly *f, int var, gbr_bigpoly *out);
 int gbr_gcd_batch(gbr_ctx *ctx, int n, const gbr_upoly *p, const gbr_upoly *q, gbr_bigpoly *out);
 
+/* gcd with cofactors: g[i] = gcd(p[i], q[i]) as gbr_gcd_batch computes it, and
+ * p_over_g[i] = p[i] / g[i], q_over_g[i] = q[i] / g[i] exactly (from the same
+ * certified lift: the cofactors satisfy p = g * p_over_g and q = g * q_over_g).
+ * gcd(0, 0) = 0 has zero cofactors.  All three outputs are library-owned. */
+int gbr_gcd_cofactors_batch(gbr_ctx *ctx, int n, const gbr_upoly *p, const gbr_upoly *q, gbr_bigpoly *g,
+                            gbr_bigpoly *p_over_g, gbr_bigpoly *q_over_g);
+
+/* ------------------------------------------------------------------ bivariate gcd, Teissier resultant */
+
+/* An exact polynomial in Z[x, y]: coefficient of x^i y^j at index j (deg_x + 1) + i
+ * of c (sign-magnitude limbs as gbr_bigpoly; c.deg + 1 = (deg_x + 1)(deg_y + 1)).
+ * deg_y = -1 for the zero polynomial.  Library-owned: gbr_free_bigbipoly. */
+typedef struct {
+    int32_t deg_x, deg_y;
+    gbr_bigpoly c;
+} gbr_bigbipoly;
+void gbr_free_bigbipoly(gbr_ctx *ctx, gbr_bigbipoly *x);
+
+/* h[i] = gcd(a[i], b[i]) in Z[x, y] (normalised so that the leading coefficient in
+ * x of its leading coefficient in y is positive; it includes the gcd of the
+ * contents) and the cofactors a[i] / h[i], b[i] / h[i] (Section 2.1 needs
+ * h = gcd(f_x, f_y) for the Teissier bound).  Inputs: int64 bipolys (words = 1).
+ * Method: Kronecker substitution x^i y^j -> z^(i + j D), D above every x-degree,
+ * the certified univariate gcd with cofactors on the device, and the map back;
+ * the map-back is exact when deg_x h + deg_x (a / h) < D and likewise for b, which
+ * is checked, else D is doubled.  GBR_ELIMIT when an image would exceed
+ * GBR_MAX_UDEG. */
+int gbr_gcd2_batch(gbr_ctx *ctx, int n, const gbr_bipoly *a, const gbr_bipoly *b, gbr_bigbipoly *h,
+                   gbr_bigbipoly *a_over_h, gbr_bigbipoly *b_over_h);
+
+/* q[i] = Q = res(f_x*, f_y*, y) with h = gcd(f_x, f_y), f_x* = f_x / h, f_y* = f_y / h
+ * (Section 2.1, the Teissier bound on the number of distinct roots of f(alpha, y):
+ * deg_y f - mult(R, alpha) + mult(Q, alpha)).  Derivatives of the int64 input on the
+ * host (GBR_ELIMIT on int64 overflow), h and the cofactors by gbr_gcd2_batch, Q by
+ * the resultant path (cofactors of up to GBR_MAX_WORDS words).  Q = 0 when f_x or
+ * f_y vanishes. */
+int gbr_teissier_res_batch(gbr_ctx *ctx, int n, const gbr_bipoly *f, gbr_bigpoly *q);
+
 /* ------------------------------------------------------------------ square-free factorisation */
 
 /* R = unit * prod_{i=1..count} factors[i-1]^i (Section 2.1, Projection Phase:

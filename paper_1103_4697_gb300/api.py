@@ -346,6 +346,47 @@ class Context:
     def gcd(self, p, q) -> list[int]:
         return self.gcd_batch([p], [q])[0]
 
+    # ------------------------------------------------------------- gcd with cofactors, bivariate gcd
+    def gcd_cofactors_batch(self, ps, qs) -> list[tuple[list[int], list[int], list[int]]]:
+        """gbr_gcd_cofactors_batch: (gcd, p / gcd, q / gcd) per pair."""
+        keep = _Packed()
+        dp, dq = pack_upolys(ps, keep), pack_upolys(qs, keep)
+        n = len(dp)
+        g, a, b = ((N.BigPoly * max(n, 1))() for _ in range(3))
+        N.check(N.lib().gbr_gcd_cofactors_batch(self.handle, n, _ptr(dp), _ptr(dq), g, a, b), self.handle)
+        return list(zip(self._collect(g, n), self._collect(a, n), self._collect(b, n)))
+
+    def _bigbipoly_rows(self, x) -> list[list[int]]:
+        if x.deg_y < 0:
+            out = []
+        else:
+            flat = bigpoly_to_ints(N.BigPoly(x.c.deg, x.c.limbs, x.c.mag, x.c.sign))
+            w = x.deg_x + 1
+            flat = flat + [0] * ((x.deg_y + 1) * w - len(flat))
+            out = [flat[j * w:(j + 1) * w] for j in range(x.deg_y + 1)]
+        N.lib().gbr_free_bigbipoly(self.handle, C.byref(x))
+        return out
+
+    def gcd2_batch(self, fs, gs):
+        """gbr_gcd2_batch: (h, f / h, g / h) per pair, each as rows (row j = coefficients
+        of y^j, lowest power of x first; [] for zero)."""
+        keep = _Packed()
+        df, dg = pack_bipolys(fs, keep), pack_bipolys(gs, keep)
+        n = len(df)
+        h, a, b = ((N.BigBiPoly * max(n, 1))() for _ in range(3))
+        N.check(N.lib().gbr_gcd2_batch(self.handle, n, _ptr(df), _ptr(dg), h, a, b), self.handle)
+        return [(self._bigbipoly_rows(h[i]), self._bigbipoly_rows(a[i]), self._bigbipoly_rows(b[i])) for i in range(n)]
+
+    def teissier_res_batch(self, fs) -> list[list[int]]:
+        """gbr_teissier_res_batch: Q = res(f_x / h, f_y / h, y), h = gcd(f_x, f_y)
+        (Section 2.1)."""
+        keep = _Packed()
+        df = pack_bipolys(fs, keep)
+        n = len(df)
+        outs = (N.BigPoly * max(n, 1))()
+        N.check(N.lib().gbr_teissier_res_batch(self.handle, n, _ptr(df), outs), self.handle)
+        return self._collect(outs, n)
+
     # ------------------------------------------------------------- square-free factorisation
     def squarefree_batch(self, rs) -> list[tuple[int, list[list[int]]]]:
         """gbr_squarefree_batch: for each R, (u, [r_1, ..., r_m]) with

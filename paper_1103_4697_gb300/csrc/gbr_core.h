@@ -144,7 +144,11 @@ int gbr_fetch_resident_locked(gbr_ctx *c, gbr_resident *r, int first, int count,
 void gbr_free_resident_locked(gbr_ctx *c, gbr_resident *r);
 void gbr_serve_shutdown(gbr_ctx *c);
 void gbr_parallel_for(int n, int threads, const std::function<void(int, int)> &fn);   // fn(lo, hi) on threads
-bool gbr_alloc_results(gbr_bigpoly *out, int count);   // one refcounted host block for a call's results
+bool gbr_alloc_results(gbr_bigpoly *out, int count);
+// gcd batch with optional cofactors (out_a = p / gcd, out_b = q / gcd; both or
+// neither), with the context lock held
+int gbr_gcd_cof_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upoly *q, gbr_bigpoly *out,
+                       gbr_bigpoly *out_a, gbr_bigpoly *out_b);   // one refcounted host block for a call's results
 char *gbr_pinned_result_block(size_t bytes, size_t *got);
 void gbr_register_result_block(char *base, size_t size, int64_t refs, bool pinned);
 gbr_ctx *gbr_make_worker(gbr_ctx *parent);    // own stream and tables, parent's arena

@@ -51,7 +51,8 @@ struct GcdPlan {
     int64_t garner_off;                 // kcrt + kcrt(kcrt-1)/2 words
     int64_t lift_off, lsign_off;        // lifted w|f|g limbs and signs
     int64_t out_off, osign_off;         // final result limbs and signs
-    int32_t dstar, pad;
+    int64_t cof_off, cofsign_off;       // cofactors P/G then Q/G (Lcof limbs each), when asked for
+    int32_t dstar, Lcof;
     uint64_t cP, cQ, c, b;
     double log2M;
 };
@@ -73,6 +74,8 @@ struct GcdLaunch {
     uint32_t *out;
     int8_t *osign;
     int32_t *odeg;
+    uint32_t *cof;           // optional cofactor outputs (null: gcd only)
+    int8_t *cofsign;
     int32_t *status;
     int32_t *err;
     int32_t njobs;
@@ -423,6 +426,35 @@ __global__ void k_gcd_check(GcdLaunch L, const int32_t *jobs, int njobs) {
         if (carry) atomicExch(L.err, 4);
         L.osign[G.osign_off + i] = L.lsign[G.lsign_off + i];
     }
+    // cofactors P / G = (cP / c) f* / (b / g) and Q / G = (cQ / c) g* / (b / g): from
+    // f* w = b P' with w = g pp(w) and G = c pp(w); the divisions are exact
+    if (L.cof) {
+        const uint64_t lpw = G.b / g;
+        for (int part = 0; part < 2; ++part) {
+            const int first = part ? nw + nf : nw, cnt = part ? ng : nf, ob = part ? nf : 0;
+            const uint64_t cs = (part ? G.cQ : G.cP) / G.c;
+            for (int i = lane; i < cnt; i += 32) {
+                const uint32_t *x = lift + (int64_t)(first + i) * G.Lcrt;
+                uint32_t *o = L.cof + G.cof_off + (int64_t)(ob + i) * G.Lcof;
+                unsigned __int128 r = 0;
+                for (int l = G.Lcrt - 1; l >= 0; --l) {
+                    r = (r << 32) | x[l];
+                    o[l] = (uint32_t)(r / lpw);
+                    r %= lpw;
+                }
+                if (r) atomicExch(L.err, 5);
+                for (int l = G.Lcrt; l < G.Lcof; ++l) o[l] = 0u;
+                unsigned __int128 carry = 0;
+                for (int l = 0; l < G.Lcof; ++l) {
+                    const unsigned __int128 t = (unsigned __int128)o[l] * cs + carry;
+                    o[l] = (uint32_t)t;
+                    carry = t >> 32;
+                }
+                if (carry) atomicExch(L.err, 4);
+                L.cofsign[G.cofsign_off + ob + i] = L.lsign[G.lsign_off + first + i];
+            }
+        }
+    }
     if (lane == 0) {
         L.odeg[job] = d;
         L.status[job] = 1;
@@ -485,7 +517,10 @@ static cudaError_t gcd_copy(gbr_ctx *c, void *dst, const void *src, size_t bytes
     return cudaMemcpyAsync(dst, src, bytes, kind, s);
 }
 
-static int gcd_batch_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upoly *q, gbr_bigpoly *out) {
+// out_a, out_b (both or neither): the cofactors p / gcd and q / gcd
+static int gcd_batch_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upoly *q, gbr_bigpoly *out,
+                            gbr_bigpoly *out_a = nullptr, gbr_bigpoly *out_b = nullptr) {
+    const bool cof = out_a && out_b;
     cudaStream_t s = c->stream;
     cudaError_t e;
     c->gcd_kernels = c->gcd_subproblems = c->gcd_h2d = c->gcd_d2h = 0;
@@ -557,6 +592,7 @@ static int gcd_batch_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upo
         out[i].limbs = 0;
         out[i].mag = nullptr;
         out[i].sign = nullptr;
+        if (cof) out_a[i] = out_b[i] = gbr_bigpoly{-1, 0, nullptr, nullptr};
         if (I.dP < 0 && I.dQ < 0) continue;
         if (I.dP < 0 || I.dQ < 0) {   // gcd(X, 0) = X / sign(lc X)
             const int64_t *X = I.dP < 0 ? hin + in_off[i] + p[i].deg + 1 : hin + in_off[i];
@@ -570,11 +606,31 @@ static int gcd_batch_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upo
             }
             set_big_int(out[i], co);
             if (!out[i].mag) return c->fail(GBR_ENOMEM, "host result allocation");
+            if (cof) {   // X / gcd = sign(lc X), 0 / gcd = 0
+                gbr_bigpoly &cx = I.dP < 0 ? out_b[i] : out_a[i];
+                set_big_int(cx, {{1u, sg}});
+                if (!cx.mag) return c->fail(GBR_ENOMEM, "host result allocation");
+            }
             continue;
         }
         if (I.dP == 0 || I.dQ == 0) {   // a non-zero constant: gcd of the contents
             set_big_int(out[i], {{I.c, 1}});
             if (!out[i].mag) return c->fail(GBR_ENOMEM, "host result allocation");
+            if (cof) {   // each input divided by the integer gcd of the contents
+                for (int w = 0; w < 2; ++w) {
+                    const int64_t *X = hin + in_off[i] + (w ? p[i].deg + 1 : 0);
+                    const int dx = w ? I.dQ : I.dP;
+                    std::vector<std::pair<uint64_t, int>> co(dx + 1);
+                    for (int t = 0; t <= dx; ++t) {
+                        const int64_t v = X[t];
+                        const uint64_t mag = v < 0 ? 0ull - (uint64_t)v : (uint64_t)v;
+                        co[t] = {mag / I.c, v == 0 ? 0 : (v < 0 ? -1 : 1)};
+                    }
+                    gbr_bigpoly &cx = w ? out_b[i] : out_a[i];
+                    set_big_int(cx, co);
+                    if (!cx.mag) return c->fail(GBR_ENOMEM, "host result allocation");
+                }
+            }
             continue;
         }
         pending.push_back(i);
@@ -670,7 +726,7 @@ static int gcd_batch_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upo
         // ---- keep the primes of minimal gcd degree
         std::vector<int32_t> crtlist;
         std::vector<int> ready, retry;
-        int64_t garner_w = 0, lift_w = 0, lsign_b = 0, out_w = 0, osign_b = 0;
+        int64_t garner_w = 0, lift_w = 0, lsign_b = 0, out_w = 0, osign_b = 0, cof_w = 0, cofsign_b = 0;
         int maxL = 1;
         std::vector<int32_t> cj;
         std::vector<int64_t> cs;
@@ -699,6 +755,13 @@ static int gcd_batch_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upo
             garner_w += G.kcrt + (int64_t)G.kcrt * (G.kcrt - 1) / 2;
             G.Lcrt = (31 * G.kcrt + 31) / 32;
             G.Lout = G.Lcrt + 2;
+            G.Lcof = G.Lcrt + 2;
+            G.cof_off = cof_w;
+            G.cofsign_off = cofsign_b;
+            if (cof) {
+                cof_w += (int64_t)((G.dP - dmin + 1) + (G.dQ - dmin + 1)) * G.Lcof;
+                cofsign_b += (G.dP - dmin + 1) + (G.dQ - dmin + 1);
+            }
             int ncoef = (dmin + 1) + (G.dP - dmin + 1) + (G.dQ - dmin + 1);
             G.lift_off = lift_w;
             lift_w += (int64_t)ncoef * G.Lcrt;
@@ -725,6 +788,9 @@ static int gcd_batch_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upo
             int8_t *d_osign = (int8_t *)cb.get((size_t)osign_b);
             int32_t *d_odeg = (int32_t *)cb.get((size_t)n * 4);
             int32_t *d_status = (int32_t *)cb.get((size_t)n * 4);
+            uint32_t *d_cof = cof ? (uint32_t *)cb.get((size_t)cof_w * 4) : nullptr;
+            int8_t *d_cofsign = cof ? (int8_t *)cb.get((size_t)cofsign_b) : nullptr;
+            if (cof && (!d_cof || !d_cofsign)) return c->fail(GBR_ENOMEM, "device budget too small for the gcd cofactors");
             int32_t *d_ready = (int32_t *)cb.get(ready.size() * 4);
             int64_t *d_cs = (int64_t *)cb.get(cs.size() * 8);
             int32_t *d_cj = (int32_t *)cb.get(cj.size() * 4);
@@ -744,6 +810,8 @@ static int gcd_batch_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upo
             L.out = d_out;
             L.osign = d_osign;
             L.odeg = d_odeg;
+            L.cof = d_cof;
+            L.cofsign = d_cofsign;
             L.status = d_status;
             const int nr = (int)ready.size();
             if (e == cudaSuccess) {
@@ -778,6 +846,10 @@ static int gcd_batch_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upo
             if (e == cudaSuccess) e = gcd_copy(c, od.data(), d_odeg, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess && out_w) e = gcd_copy(c, hout.data(), d_out, (size_t)out_w * 4, cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess && osign_b) e = gcd_copy(c, hos.data(), d_osign, (size_t)osign_b, cudaMemcpyDeviceToHost, s);
+            std::vector<uint32_t> hcof(cof ? (size_t)cof_w : 0);
+            std::vector<int8_t> hcs(cof ? (size_t)cofsign_b : 0);
+            if (e == cudaSuccess && cof && cof_w) e = gcd_copy(c, hcof.data(), d_cof, (size_t)cof_w * 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess && cof && cofsign_b) e = gcd_copy(c, hcs.data(), d_cofsign, (size_t)cofsign_b, cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = gcd_copy(c, &herr, c->d_err, 4, cudaMemcpyDeviceToHost, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "gcd lift and check", e);
@@ -788,20 +860,39 @@ static int gcd_batch_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upo
                 if (st[i] != 1) retry.push_back(i);
                 else done.push_back(i);
             }
-            std::vector<gbr_bigpoly> tmp(done.size());
+            // per done job: the gcd, then (when asked for) the two cofactors
+            const int per = cof ? 3 : 1;
+            std::vector<gbr_bigpoly> tmp(done.size() * per);
             for (size_t t = 0; t < done.size(); ++t) {
-                tmp[t].deg = od[done[t]];
-                tmp[t].limbs = plan[done[t]].Lout;
+                const GcdPlan &G = plan[done[t]];
+                tmp[t * per].deg = od[done[t]];
+                tmp[t * per].limbs = G.Lout;
+                if (cof) {
+                    tmp[t * per + 1].deg = G.dP - od[done[t]];
+                    tmp[t * per + 1].limbs = G.Lcof;
+                    tmp[t * per + 2].deg = G.dQ - od[done[t]];
+                    tmp[t * per + 2].limbs = G.Lcof;
+                }
             }
             if (!tmp.empty() && !gbr_alloc_results(tmp.data(), (int)tmp.size()))
                 return c->fail(GBR_ENOMEM, "host result allocation");
             for (size_t t = 0; t < done.size(); ++t) {
                 const int i = done[t];
                 const GcdPlan &G = plan[i];
-                out[i] = tmp[t];
-                if (out[i].deg < 0) continue;
-                std::memcpy(out[i].mag, hout.data() + G.out_off, (size_t)(out[i].deg + 1) * G.Lout * 4);
-                std::memcpy(out[i].sign, hos.data() + G.osign_off, (size_t)out[i].deg + 1);
+                out[i] = tmp[t * per];
+                if (out[i].deg >= 0) {
+                    std::memcpy(out[i].mag, hout.data() + G.out_off, (size_t)(out[i].deg + 1) * G.Lout * 4);
+                    std::memcpy(out[i].sign, hos.data() + G.osign_off, (size_t)out[i].deg + 1);
+                }
+                if (cof) {
+                    out_a[i] = tmp[t * per + 1];
+                    out_b[i] = tmp[t * per + 2];
+                    const int na = out_a[i].deg + 1, nb = out_b[i].deg + 1;
+                    std::memcpy(out_a[i].mag, hcof.data() + G.cof_off, (size_t)na * G.Lcof * 4);
+                    std::memcpy(out_a[i].sign, hcs.data() + G.cofsign_off, (size_t)na);
+                    std::memcpy(out_b[i].mag, hcof.data() + G.cof_off + (int64_t)na * G.Lcof, (size_t)nb * G.Lcof * 4);
+                    std::memcpy(out_b[i].sign, hcs.data() + G.cofsign_off + na, (size_t)nb);
+                }
             }
         }
         pending = retry;
@@ -813,16 +904,13 @@ static int gcd_batch_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upo
     return GBR_OK;
 }
 
-extern "C" int gbr_gcd_batch(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upoly *q, gbr_bigpoly *out) {
-    if (!c || n < 0 || (n && (!p || !q || !out))) return GBR_EINVAL;
-    if (n == 0) return GBR_OK;
-    std::lock_guard<std::mutex> lk(c->mu);
-    cudaSetDevice(c->device);
+int gbr_gcd_cof_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upoly *q, gbr_bigpoly *out,
+                       gbr_bigpoly *out_a, gbr_bigpoly *out_b) {
     int st;
     const auto t0 = std::chrono::steady_clock::now();
     if (c->stats_on) cudaEventRecord(c->ev[0], c->stream);
     try {
-        st = gcd_batch_locked(c, n, p, q, out);
+        st = gcd_batch_locked(c, n, p, q, out, out_a, out_b);
         if (c->stats_on) {
             // the whole call on the context's stream: copies, kernels and the host
             // planning between them (the gcd path synchronises after each stage)
@@ -843,8 +931,29 @@ extern "C" int gbr_gcd_batch(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_up
         st = c->fail(GBR_ENOMEM, "host allocation");
     }
     if (st != GBR_OK)
-        for (int i = 0; i < n; ++i) gbr_free_result(c, &out[i]);
+        for (int i = 0; i < n; ++i) {
+            gbr_free_result(c, &out[i]);
+            if (out_a) gbr_free_result(c, &out_a[i]);
+            if (out_b) gbr_free_result(c, &out_b[i]);
+        }
     return st;
+}
+
+extern "C" int gbr_gcd_batch(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upoly *q, gbr_bigpoly *out) {
+    if (!c || n < 0 || (n && (!p || !q || !out))) return GBR_EINVAL;
+    if (n == 0) return GBR_OK;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    return gbr_gcd_cof_locked(c, n, p, q, out, nullptr, nullptr);
+}
+
+extern "C" int gbr_gcd_cofactors_batch(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upoly *q, gbr_bigpoly *g,
+                                       gbr_bigpoly *p_over_g, gbr_bigpoly *q_over_g) {
+    if (!c || n < 0 || (n && (!p || !q || !g || !p_over_g || !q_over_g))) return GBR_EINVAL;
+    if (n == 0) return GBR_OK;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    return gbr_gcd_cof_locked(c, n, p, q, g, p_over_g, q_over_g);
 }
 
 extern "C" int gbr_gcd(gbr_ctx *c, const gbr_upoly *p, const gbr_upoly *q, gbr_bigpoly *out) {

@@ -30,6 +30,10 @@ class BigPoly(C.Structure):
                 ("sign", C.POINTER(C.c_int8))]
 
 
+class BigBiPoly(C.Structure):
+    _fields_ = [("deg_x", C.c_int32), ("deg_y", C.c_int32), ("c", BigPoly)]
+
+
 class Sqf(C.Structure):
     _fields_ = [("unit", BigPoly), ("count", C.c_int32), ("factors", C.POINTER(BigPoly))]
 
@@ -77,6 +81,12 @@ SIGNATURES = {
     "gbr_resultant_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(BigPoly)]),
     "gbr_discriminant_res_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(BigPoly)]),
     "gbr_gcd_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(BigPoly)]),
+    "gbr_gcd_cofactors_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(BigPoly),
+                                          C.POINTER(BigPoly), C.POINTER(BigPoly)]),
+    "gbr_gcd2_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(BigBiPoly),
+                                 C.POINTER(BigBiPoly), C.POINTER(BigBiPoly)]),
+    "gbr_free_bigbipoly": (None, [C.c_void_p, C.POINTER(BigBiPoly)]),
+    "gbr_teissier_res_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(BigPoly)]),
     "gbr_squarefree": (C.c_int, [C.c_void_p, C.POINTER(BigPoly), C.POINTER(Sqf)]),
     "gbr_squarefree_batch": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(BigPoly), C.POINTER(Sqf)]),
     "gbr_free_sqf": (None, [C.c_void_p, C.POINTER(Sqf)]),
