@@ -439,6 +439,8 @@ def run_config(args) -> None:
     arrangement  the n(n+1)/2 resultants of an arrangement of 90 curves (Section 3:
             res(f, f_y) per curve, res(f, g) per pair; 4095 jobs) in one pass, then the
             square-free factorisation of all of them (Section 2.1);
+    teissier  the Teissier resultant Q = res(f_x/h, f_y/h, y), h = gcd(f_x, f_y)
+            (Section 2.1), for 1024 curves shaped like the arrangement's (degree 8);
     sqf     square-free factorisation R = u prod r_i^i (Section 2.1) of 2048 planted
             projection-resultant-shaped polynomials, through the C ABI, and of
             R = res_y(f, f_y) of the conic-product curve (the path's own output)."""
@@ -604,6 +606,31 @@ def run_config(args) -> None:
         out["workload"] = ("arrangement of 90 curves (seed 7): 25% products of 4 circles/ellipses (radii/centres "
                            "in [-64, 64]), 75% dense total degree 8 with 12-bit coefficients; 90 res(f, f_y) + "
                            "4005 res(f, g) per pass")
+    elif args.config == "teissier":
+        NT = 1024
+        curves = W.arrangement_curves(11, n=NT, d=8, bits=12, conic_frac=0.25, rbits=4)
+        keep = api._Packed()
+        df = api.pack_bipolys(curves, keep)
+        L = N.lib()
+        outs = (N.BigPoly * NT)()
+        times = []
+        for it in range(5):
+            t0 = time.perf_counter()
+            N.check(L.gbr_teissier_res_batch(ctx.handle, NT, api._ptr(df), outs), ctx.handle)
+            times.append(time.perf_counter() - t0)
+            got = ctx._collect(outs, NT)
+        sec = statistics.median(times[1:])
+        out["teissier_jobs_per_s"] = NT / sec
+        out["teissier_ms_per_call"] = sec * 1e3
+        out["q_degree_max"] = max(len(q) - 1 for q in got)
+        for k in random.Random(3).sample(range(NT), 2):      # parity spot check before reporting
+            assert got[k] == list(O.teissier_q(curves[k])), k
+        t = time.perf_counter()
+        for k in range(2):
+            O.teissier_q(curves[k])
+        out["oracle_teissier_jobs_per_s_1core"] = 2 / (time.perf_counter() - t)
+        out["workload"] = ("Q = res(f_x/h, f_y/h, y) for 1024 curves (seed 11): 25% products of 4 circles/ellipses "
+                           "(centres and radii in [-16, 16]), 75% dense total degree 8, 12-bit")
     elif args.config == "sqf":
         NS = 2048
         R, _ = W.sqf_batch(6, NS)
@@ -664,7 +691,7 @@ def main():
     ap.add_argument("--mem-gb", type=int, default=24)
     ap.add_argument("--pairs", type=int, default=PAIRS, help="pairs per GPU (smaller only for profiling)")
     ap.add_argument("--config", choices=["headline", "small", "deg20", "mixed", "conic", "serve", "gcd", "sqf",
-                                                 "arrangement"],
+                                                 "arrangement", "teissier"],
                     default="headline", help="other workloads print their own JSON line")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--no-serve", action="store_true")
