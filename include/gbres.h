@@ -241,6 +241,14 @@ int gbr_gcd2_batch(gbr_ctx *ctx, int n, const gbr_bipoly *a, const gbr_bipoly *b
  * f_y vanishes. */
 int gbr_teissier_res_batch(gbr_ctx *ctx, int n, const gbr_bipoly *f, gbr_bigpoly *q);
 
+/* out[i] = the content of f[i] with respect to var (Section 2, content removal:
+ * h = gcd(f_0, f_1, ...) in Z[other variable] of the coefficients f_j of var^j; a
+ * non-trivial h marks vertical (var = 1) components), with a positive leading
+ * coefficient; zero for f = 0.  Inputs: int64 bipolys (words = 1).  A tree of
+ * batched gcds on the device, all curves of a level in one batch; GBR_ELIMIT
+ * when a partial gcd does not fit int64. */
+int gbr_content_batch(gbr_ctx *ctx, int n, const gbr_bipoly *f, int var, gbr_bigpoly *out);
+
 /* ------------------------------------------------------------------ square-free factorisation */
 
 /* R = unit * prod_{i=1..count} factors[i-1]^i (Section 2.1, Projection Phase:

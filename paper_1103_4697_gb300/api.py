@@ -377,6 +377,16 @@ class Context:
         N.check(N.lib().gbr_gcd2_batch(self.handle, n, _ptr(df), _ptr(dg), h, a, b), self.handle)
         return [(self._bigbipoly_rows(h[i]), self._bigbipoly_rows(a[i]), self._bigbipoly_rows(b[i])) for i in range(n)]
 
+    def content_batch(self, fs, var: int = 1) -> list[list[int]]:
+        """gbr_content_batch: the content of each curve with respect to var (Section 2,
+        content removal), a polynomial in the other variable."""
+        keep = _Packed()
+        df = pack_bipolys(fs, keep)
+        n = len(df)
+        outs = (N.BigPoly * max(n, 1))()
+        N.check(N.lib().gbr_content_batch(self.handle, n, _ptr(df), var, outs), self.handle)
+        return self._collect(outs, n)
+
     def teissier_res_batch(self, fs) -> list[list[int]]:
         """gbr_teissier_res_batch: Q = res(f_x / h, f_y / h, y), h = gcd(f_x, f_y)
         (Section 2.1)."""

@@ -258,3 +258,112 @@ extern "C" int gbr_teissier_res_batch(gbr_ctx *c, int n, const gbr_bipoly *f, gb
     }
     return st;
 }
+
+// ------------------------------------------------------------------ content removal
+
+// content of f with respect to `var` (Section 2, content removal: h = gcd(f_0, f_1,
+// ...) of the coefficients of the powers of var, polynomials in the other
+// variable): a tree of batched gcds, all inputs of a level in one device batch.
+// The gcd of int64 polynomials is read back into int64 for the next level;
+// GBR_ELIMIT when a partial gcd does not fit.
+static int content_locked(gbr_ctx *c, int n, const gbr_bipoly *f, int var, gbr_bigpoly *out) {
+    std::vector<std::vector<std::vector<int64_t>>> level(n);   // per job: its polynomials
+    for (int i = 0; i < n; ++i) {
+        const gbr_bipoly &p = f[i];
+        if (!p.coef || p.deg_x < 0 || p.deg_y < 0 || p.words != 1)
+            return c->fail(GBR_EINVAL, "content inputs must be int64 bipolys (words = 1)");
+        const int64_t *cf = (const int64_t *)p.coef;
+        const int nr = var ? p.deg_y + 1 : p.deg_x + 1, nc = var ? p.deg_x + 1 : p.deg_y + 1;
+        for (int r = 0; r < nr; ++r) {
+            std::vector<int64_t> row(nc);
+            bool any = false;
+            for (int k = 0; k < nc; ++k) {
+                row[k] = var ? cf[(size_t)r * (p.deg_x + 1) + k] : cf[(size_t)k * (p.deg_x + 1) + r];
+                any = any || row[k];
+            }
+            if (any) level[i].push_back(std::move(row));
+        }
+        if (level[i].size() == 1) level[i].push_back(level[i][0]);   // gcd(p, p) normalises p
+    }
+    while (true) {
+        std::vector<gbr_upoly> P, Q;
+        std::vector<std::pair<int, int>> who;   // (job, slot of the result)
+        std::vector<std::vector<std::vector<int64_t>>> next(n);
+        for (int i = 0; i < n; ++i) {
+            const size_t m = level[i].size();
+            if (m < 2) {   // finished (or zero): carried to the next level as it is
+                next[i] = level[i];
+                continue;
+            }
+            for (size_t k = 0; k + 1 < m; k += 2) {
+                P.push_back(gbr_upoly{(int32_t)level[i][k].size() - 1, 1, level[i][k].data()});
+                Q.push_back(gbr_upoly{(int32_t)level[i][k + 1].size() - 1, 1, level[i][k + 1].data()});
+                who.push_back({i, (int)next[i].size()});
+                next[i].emplace_back();
+            }
+            if (m % 2) next[i].push_back(level[i][m - 1]);
+        }
+        if (P.empty()) break;
+        std::vector<gbr_bigpoly> g(P.size());
+        int st = gbr_gcd_cof_locked(c, (int)P.size(), P.data(), Q.data(), g.data(), nullptr, nullptr);
+        if (st) return st;
+        int rc = GBR_OK;
+        for (size_t t = 0; t < g.size(); ++t) {
+            std::vector<int64_t> &dst = next[who[t].first][who[t].second];
+            const gbr_bigpoly &b = g[t];
+            dst.assign((size_t)std::max(b.deg, 0) + 1, 0);
+            for (int k = 0; k <= b.deg && rc == GBR_OK; ++k) {
+                uint64_t mag = 0;
+                for (int l = 0; l < b.limbs; ++l) {
+                    const uint32_t v = b.mag[(size_t)k * b.limbs + l];
+                    if (l >= 2 && v) rc = GBR_ELIMIT;
+                    if (l < 2) mag |= (uint64_t)v << (32 * l);
+                }
+                if (mag > (uint64_t)INT64_MAX) rc = GBR_ELIMIT;
+                dst[k] = b.sign[k] < 0 ? -(int64_t)mag : (int64_t)mag;
+            }
+            gbr_free_result(c, &g[t]);
+        }
+        if (rc) return c->fail(rc, "content: a partial gcd does not fit int64");
+        level.swap(next);
+    }
+    // the remaining polynomial of each job is its content (positive leading coefficient)
+    std::vector<gbr_bigpoly> res(n);
+    for (int i = 0; i < n; ++i) {
+        res[i] = gbr_bigpoly{-1, 2, nullptr, nullptr};
+        if (!level[i].empty()) {
+            int d = (int)level[i][0].size() - 1;
+            while (d >= 0 && !level[i][0][d]) --d;
+            res[i].deg = d;
+        }
+    }
+    if (!gbr_alloc_results(res.data(), n)) return c->fail(GBR_ENOMEM, "host result allocation");
+    for (int i = 0; i < n; ++i) {
+        out[i] = res[i];
+        for (int k = 0; k <= res[i].deg; ++k) {
+            const int64_t v = level[i][0][k];
+            const uint64_t mag = v < 0 ? 0ull - (uint64_t)v : (uint64_t)v;
+            out[i].mag[2 * k] = (uint32_t)mag;
+            out[i].mag[2 * k + 1] = (uint32_t)(mag >> 32);
+            out[i].sign[k] = (int8_t)((v > 0) - (v < 0));
+        }
+    }
+    return GBR_OK;
+}
+
+extern "C" int gbr_content_batch(gbr_ctx *c, int n, const gbr_bipoly *f, int var, gbr_bigpoly *out) {
+    if (!c || n < 0 || (n && (!f || !out)) || (var != 0 && var != 1)) return GBR_EINVAL;
+    for (int i = 0; i < n; ++i) out[i] = gbr_bigpoly{-1, 0, nullptr, nullptr};
+    if (n == 0) return GBR_OK;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    int st;
+    try {
+        st = content_locked(c, n, f, var, out);
+    } catch (std::bad_alloc &) {
+        st = c->fail(GBR_ENOMEM, "host allocation");
+    }
+    if (st)
+        for (int i = 0; i < n; ++i) gbr_free_result(c, &out[i]);
+    return st;
+}

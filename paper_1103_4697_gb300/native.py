@@ -86,6 +86,7 @@ SIGNATURES = {
     "gbr_gcd2_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(BigBiPoly),
                                  C.POINTER(BigBiPoly), C.POINTER(BigBiPoly)]),
     "gbr_free_bigbipoly": (None, [C.c_void_p, C.POINTER(BigBiPoly)]),
+    "gbr_content_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(BigPoly)]),
     "gbr_teissier_res_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(BigPoly)]),
     "gbr_squarefree": (C.c_int, [C.c_void_p, C.POINTER(BigPoly), C.POINTER(Sqf)]),
     "gbr_squarefree_batch": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(BigPoly), C.POINTER(Sqf)]),

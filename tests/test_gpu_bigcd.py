@@ -131,3 +131,28 @@ def test_teissier_q(ctx):
     got = ctx.teissier_res_batch(curves)
     for f, q in zip(curves, got):
         assert q == list(O.teissier_q(f)), f
+
+
+def _transpose(f):
+    w = max(len(r) for r in f)
+    rows = [list(r) + [0] * (w - len(r)) for r in f]
+    return [[rows[j][i] for j in range(len(rows))] for i in range(w)]
+
+
+def test_content(ctx):
+    """Content removal (Section 2): gcd of the coefficients of the powers of y (and of
+    x, on the transposed curve), against the oracle's content_y."""
+    rng = random.Random(53)
+    curves = []
+    for _ in range(20):
+        h = [[rng.randint(-4, 4) for _ in range(rng.randint(1, 3))]]   # a factor in x alone
+        if not any(h[0]):
+            h[0][0] = 3
+        curves.append(_mul2(h, _rand2(rng, rng.randint(0, 3), rng.randint(0, 3), 9)))
+    curves += [[[0, 0], [0, 0]], [[5, 0, 10]], [[0, 3], [0, 6], [0, 9]], [[-4, 0, 2]], _rand2(rng, 2, 2, 5)]
+    got = ctx.content_batch(curves)
+    for f, g in zip(curves, got):
+        assert g == list(O.content_y(f)), f
+    got0 = ctx.content_batch(curves, var=0)
+    for f, g in zip(curves, got0):
+        assert g == list(O.content_y(_transpose(f))), f
