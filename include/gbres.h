@@ -228,8 +228,11 @@ void gbr_free_bigbipoly(gbr_ctx *ctx, gbr_bigbipoly *x);
  * Method: Kronecker substitution x^i y^j -> z^(i + j D), D above every x-degree,
  * the certified univariate gcd with cofactors on the device, and the map back;
  * the map-back is exact when deg_x h + deg_x (a / h) < D and likewise for b, which
- * is checked, else D is doubled.  GBR_ELIMIT when an image would exceed
- * GBR_MAX_UDEG. */
+ * is checked, else D grows by one; after four values of D the inputs are shifted
+ * by y -> y + s (s = 1, 2, 3; this moves common zeros such as (1, 1), which every
+ * monomial substitution sends to z = 1) and the results shifted back exactly.
+ * GBR_EVERIFY when every shift fails (or its int64 inputs would overflow);
+ * GBR_ELIMIT when an image would exceed GBR_MAX_UDEG. */
 int gbr_gcd2_batch(gbr_ctx *ctx, int n, const gbr_bipoly *a, const gbr_bipoly *b, gbr_bigbipoly *h,
                    gbr_bigbipoly *a_over_h, gbr_bigbipoly *b_over_h);
 

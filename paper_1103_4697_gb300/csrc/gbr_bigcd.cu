@@ -18,31 +18,27 @@
 // t = v, v - 1, ..., 0 (the cofactors multiplied by z^(v - t)) and the first that
 // maps back exactly is taken: the largest such t is at least w, so phi(H) divides
 // that candidate and it is H.  When no t passes (G holds another common factor of
-// the images that is not an image of one), the job runs again with D doubled.
+// the images that is not an image of one), the job runs again with D + 1: such a
+// factor comes from common zeros (x0, x0^D) of the inputs with x0 a root of unity
+// (both inputs vanishing at (-1, 1) put 1 + z into every image with D even), so
+// consecutive D leave it behind unless the common zeros cover every residue of D.
+// A common zero at (1, 1) defeats every monomial substitution (z - 1 divides
+// every image), so after kTriesPerShift values of D the inputs are replaced by
+// A(x, y + s), B(x, y + s) for s = 1, 2, 3 (int64 Taylor shifts, moving the common
+// zeros), and the results are shifted back by y -> y - s in exact big integers;
+// leading coefficients in y and contents are unchanged by the shift.  After the
+// last shift the call gives up with GBR_EVERIFY.
 #include <cstring>
 #include <vector>
 
+#include "gbr_bigint.h"
 #include "gbr_core.h"
+#include "gbr_kron.h"
 
 using namespace gbr;
+using namespace gbr::kron;
 
 namespace {
-
-// x-degree of the map-back of z^off times a Kronecker image with D columns (-1
-// for zero); every non-zero coefficient of g sits at an exponent k with k + off >= 0
-int back_degx(const gbr_bigpoly &g, int D, int off) {
-    int dx = -1;
-    for (int k = 0; k <= g.deg; ++k)
-        if (g.sign[k]) dx = std::max(dx, (k + off) % D);
-    return dx;
-}
-
-// lowest exponent with a non-zero coefficient (-1 for zero)
-int valuation(const gbr_bigpoly &g) {
-    for (int k = 0; k <= g.deg; ++k)
-        if (g.sign[k]) return k;
-    return -1;
-}
 
 // the map-back of z^off g into [deg_y][deg_x] layout
 bool map_back(const gbr_bigpoly &g, int D, int off, gbr_bigbipoly &out) {
@@ -71,7 +67,54 @@ void clear(gbr_bigbipoly &x) {
     x.c = gbr_bigpoly{-1, 0, nullptr, nullptr};
 }
 
+// in[j][i] (deg_x + 1 columns) -> in(x, y + s), column by column (Taylor shift in
+// y by repeated synthetic division); false on int64 overflow
+bool shift_y_i64(const int64_t *in, int dx, int dy, int s, std::vector<int64_t> &out) {
+    out.assign(in, in + (size_t)(dx + 1) * (dy + 1));
+    for (int i = 0; i <= dx; ++i)
+        for (int k = 0; k < dy; ++k)
+            for (int j = dy - 1; j >= k; --j) {
+                int64_t t;
+                if (__builtin_mul_overflow(out[(size_t)(j + 1) * (dx + 1) + i], (int64_t)s, &t) ||
+                    __builtin_add_overflow(out[(size_t)j * (dx + 1) + i], t, &out[(size_t)j * (dx + 1) + i]))
+                    return false;
+            }
+    return true;
+}
+
+// x <- x(x, y - s) in exact big integers (the inverse of the input shift)
+bool unshift_y(gbr_ctx *c, gbr_bigbipoly &x, int s) {
+    if (x.deg_y < 1) return true;   // constants in y are unchanged
+    const int dx = x.deg_x, dy = x.deg_y, L = x.c.limbs;
+    std::vector<bn::Big> g((size_t)(dx + 1) * (dy + 1));
+    for (size_t t = 0; t < g.size(); ++t)
+        if (x.c.sign[t]) g[t] = bn::from_limbs(x.c.mag + t * L, L, x.c.sign[t]);
+    const bn::Big ms = bn::from_i64(-(int64_t)s);
+    for (int i = 0; i <= dx; ++i)
+        for (int k = 0; k < dy; ++k)
+            for (int j = dy - 1; j >= k; --j) {
+                bn::Big &cj = g[(size_t)j * (dx + 1) + i];
+                cj = bn::add(cj, bn::mul(g[(size_t)(j + 1) * (dx + 1) + i], ms));
+            }
+    size_t nl = 1;
+    for (const bn::Big &b : g) nl = std::max(nl, b.m.size());
+    gbr_bigbipoly y;
+    y.deg_x = dx;
+    y.deg_y = dy;
+    y.c = gbr_bigpoly{x.c.deg, (int32_t)nl, nullptr, nullptr};
+    if (!gbr_alloc_results(&y.c, 1)) return false;
+    for (size_t t = 0; t < g.size(); ++t) {
+        for (size_t l = 0; l < nl; ++l) y.c.mag[t * nl + l] = l < g[t].m.size() ? g[t].m[l] : 0u;
+        y.c.sign[t] = (int8_t)g[t].s;
+    }
+    gbr_free_result(c, &x.c);
+    x = y;
+    return true;
+}
+
 }  // namespace
+
+static const int kTriesPerShift = 4, kMaxShift = 3;
 
 static int gcd2_locked(gbr_ctx *c, int n, const gbr_bipoly *a, const gbr_bipoly *b, gbr_bigbipoly *h,
                        gbr_bigbipoly *ah, gbr_bigbipoly *bh) {
@@ -83,9 +126,10 @@ static int gcd2_locked(gbr_ctx *c, int n, const gbr_bipoly *a, const gbr_bipoly 
         clear(ah[i]);
         clear(bh[i]);
     }
-    std::vector<int> D(n), pend(n);
+    std::vector<int> D(n), pend(n), D0(n), sh(n, 0), tries(n, 0);
+    std::vector<std::vector<int64_t>> sa(n), sb(n);   // shifted inputs (when sh > 0)
     for (int i = 0; i < n; ++i) {
-        D[i] = std::max(a[i].deg_x, b[i].deg_x) + 1;
+        D[i] = D0[i] = std::max(a[i].deg_x, b[i].deg_x) + 1;
         pend[i] = i;
     }
     while (!pend.empty()) {
@@ -101,7 +145,7 @@ static int gcd2_locked(gbr_ctx *c, int n, const gbr_bipoly *a, const gbr_bipoly 
                 if (deg > GBR_MAX_UDEG)
                     return c->fail(GBR_ELIMIT, "bivariate gcd: Kronecker image above GBR_MAX_UDEG");
                 z.assign((size_t)deg + 1, 0);
-                const int64_t *cf = (const int64_t *)x.coef;
+                const int64_t *cf = sh[i] ? (w ? sb[i] : sa[i]).data() : (const int64_t *)x.coef;
                 for (int j = 0; j <= x.deg_y; ++j)
                     for (int k = 0; k <= x.deg_x; ++k) z[(size_t)j * D[i] + k] = cf[(size_t)j * (x.deg_x + 1) + k];
                 gbr_upoly &u = w ? uq[t] : up[t];
@@ -117,21 +161,13 @@ static int gcd2_locked(gbr_ctx *c, int n, const gbr_bipoly *a, const gbr_bipoly 
         int rc = GBR_OK;
         for (int t = 0; t < m && rc == GBR_OK; ++t) {
             const int i = pend[t];
-            int shift = -1;   // the candidate z^(v - shift) G / z^v that maps back exactly
-            if (g[t].deg < 0) {
-                shift = 0;
-            } else {
-                const int v = valuation(g[t]);
-                for (int sh = 0; sh <= v && shift < 0; ++sh) {
-                    const int dh = back_degx(g[t], D[i], -sh), da = back_degx(ga[t], D[i], sh),
-                              db = back_degx(gb[t], D[i], sh);
-                    if (dh + std::max(da, 0) < D[i] && dh + std::max(db, 0) < D[i]) shift = sh;
-                }
-            }
+            const int shift = kron_shift(g[t], ga[t], gb[t], D[i]);
             if (shift < 0) {
                 retry.push_back(i);
             } else if (!map_back(g[t], D[i], -shift, h[i]) || !map_back(ga[t], D[i], shift, ah[i]) ||
-                       !map_back(gb[t], D[i], shift, bh[i])) {
+                       !map_back(gb[t], D[i], shift, bh[i]) ||
+                       (sh[i] && (!unshift_y(c, h[i], sh[i]) || !unshift_y(c, ah[i], sh[i]) ||
+                                  !unshift_y(c, bh[i], sh[i])))) {
                 rc = c->fail(GBR_ENOMEM, "host result allocation");
             }
         }
@@ -141,7 +177,20 @@ static int gcd2_locked(gbr_ctx *c, int n, const gbr_bipoly *a, const gbr_bipoly 
             gbr_free_result(c, &gb[t]);
         }
         if (rc) return rc;
-        for (int i : retry) D[i] *= 2;
+        for (int i : retry) {
+            ++D[i];
+            if (++tries[i] < kTriesPerShift) continue;
+            // move the common zeros: the next shift y -> y + s of both inputs
+            bool ok = false;
+            while (!ok && sh[i] < kMaxShift) {
+                ++sh[i];
+                ok = shift_y_i64((const int64_t *)a[i].coef, a[i].deg_x, a[i].deg_y, sh[i], sa[i]) &&
+                     shift_y_i64((const int64_t *)b[i].coef, b[i].deg_x, b[i].deg_y, sh[i], sb[i]);
+            }
+            if (!ok) return c->fail(GBR_EVERIFY, "bivariate gcd: the Kronecker images keep a spurious common factor");
+            D[i] = D0[i];
+            tries[i] = 0;
+        }
         pend.swap(retry);
     }
     return GBR_OK;

@@ -75,6 +75,55 @@ inline Limbs mul_mag(const Limbs &a, const Limbs &b) {
     return r;
 }
 
+// |a| + |b| and |a| - |b| (|a| >= |b|) for trimmed magnitudes
+inline Limbs add_mag(const Limbs &a, const Limbs &b) {
+    const Limbs &x = a.size() >= b.size() ? a : b, &y = a.size() >= b.size() ? b : a;
+    Limbs r(x.size() + 1, 0u);
+    uint64_t carry = 0;
+    for (size_t i = 0; i < x.size(); ++i) {
+        const uint64_t t = (uint64_t)x[i] + (i < y.size() ? y[i] : 0u) + carry;
+        r[i] = (uint32_t)t;
+        carry = t >> 32;
+    }
+    r[x.size()] = (uint32_t)carry;
+    r.resize(top(r.data(), r.size()));
+    return r;
+}
+
+inline Limbs sub_mag(const Limbs &a, const Limbs &b) {
+    Limbs r(a.size(), 0u);
+    int64_t borrow = 0;
+    for (size_t i = 0; i < a.size(); ++i) {
+        const int64_t t = (int64_t)a[i] - (i < b.size() ? (int64_t)b[i] : 0) + borrow;
+        r[i] = (uint32_t)t;
+        borrow = t >> 32;
+    }
+    r.resize(top(r.data(), r.size()));
+    return r;
+}
+
+// a + b, signed
+inline Big add(const Big &a, const Big &b) {
+    if (!b.s) return a;
+    if (!a.s) return b;
+    Big r;
+    if (a.s == b.s) {
+        r.m = add_mag(a.m, b.m);
+        r.s = a.s;
+    } else {
+        const int c = cmp_mag(a.m.data(), a.m.size(), b.m.data(), b.m.size());
+        if (c == 0) return Big();
+        r.m = c > 0 ? sub_mag(a.m, b.m) : sub_mag(b.m, a.m);
+        r.s = c > 0 ? a.s : b.s;
+    }
+    trim(r);
+    return r;
+}
+
+inline Big from_i64(int64_t v) {
+    return from_u64(v < 0 ? 0ull - (uint64_t)v : (uint64_t)v, v < 0 ? -1 : 1);
+}
+
 inline Big mul(const Big &a, const Big &b) {
     Big r;
     r.m = mul_mag(a.m, b.m);

@@ -80,6 +80,10 @@ def test_gcd2_hand_cases(ctx):
         (_mul2(_mul2(xpy, [[0, 1]]), [[0], [1]]), _mul2(xmy, [[0, 1], [0, 1]])),   # monomial factors
         ([[0]], [[0, 0], [0, 3]]),                       # gcd(0, 3 x y)
         ([[6, 4], [2]], [[9, 6], [3]]),                  # contents 2 and 3, common part
+        # both vanish at (1, 1) outside their gcd: every monomial substitution keeps
+        # z - 1 in the images, so the library shifts y -> y + s
+        ([[0, -3], [-3, 0], [0, 4], [4, -1], [-1, 0]],
+         [[0, 9, 12, -9], [-9, -6, 9, -12], [-6, 6, 2, 0], [-6, 23, 10, 1], [-13, -14, -3, 0], [4, 2, 0, 0]]),
     ]
     got = ctx.gcd2_batch([c[0] for c in cases], [c[1] for c in cases])
     for (f, g), (h, a, b) in zip(cases, got):

@@ -104,3 +104,132 @@ def test_sqf_primitive_parts_and_norms(tmp_path):
         if not (e1 <= l1 <= e1 + 1e-6 and e2 <= l2 <= e2 + 1e-6 and ei <= li <= ei + 1e-6):
             loose.append(case)
     assert n == 1000 and not bad and not loose, (bad[:5], loose[:5])
+
+
+def _kron(rows, D):
+    z = {}
+    for j, r in enumerate(rows):
+        for i, c in enumerate(r):
+            if c:
+                z[i + j * D] = c
+    n = max(z) + 1 if z else 0
+    return [z.get(k, 0) for k in range(n)]
+
+
+def _unkron(coefs, D, off):
+    rows = {}
+    for k, c in enumerate(coefs):
+        if c:
+            i, j = (k + off) % D, (k + off) // D
+            rows.setdefault(j, {})[i] = c
+    if not rows:
+        return []
+    out = []
+    for j in range(max(rows) + 1):
+        r = rows.get(j, {})
+        out.append(tuple(r.get(i, 0) for i in range(max(r) + 1)) if r else ())
+    return out
+
+
+def _shift_rows(rows, s):
+    """rows (row j = Z[x] coefficients of y^j) -> the same polynomial at y + s."""
+    if not rows:
+        return []
+    dy, w = len(rows) - 1, max(len(r) for r in rows)
+    c = [list(r) + [0] * (w - len(r)) for r in rows]
+    for i in range(w):
+        for k in range(dy):
+            for j in range(dy - 1, k - 1, -1):
+                c[j][i] += s * c[j + 1][i]
+    out = [tuple(r) for r in c]
+    out = [tuple(_trim_t(r)) for r in out]
+    while out and not out[-1]:
+        out.pop()
+    return out
+
+
+def _trim_t(r):
+    r = list(r)
+    while r and r[-1] == 0:
+        r.pop()
+    return r
+
+
+def test_kronecker_shift_choice(tmp_path):
+    """The bivariate gcd's candidate choice on the CPU: for random pairs (and pairs
+    whose images share a power of z, or a common zero at (1, 1), that is not a common
+    factor), the Kronecker images' gcd and cofactors come from the oracle; with the
+    candidate the harness picks, D + 1 while none passes and, after four values of D,
+    the inputs shifted by y -> y + s (as the library does), the map-back shifted back
+    equals the oracle's gcd_zxy and exact quotients."""
+    import random
+
+    import oracle as O
+
+    exe = _build(tmp_path, "kron_harness.cpp")
+    rng = random.Random(61)
+
+    def rand2(dy, dx, amp):
+        f = [[rng.randint(-amp, amp) for _ in range(dx + 1)] for _ in range(dy + 1)]
+        f[dy][rng.randint(0, dx)] = rng.choice([1, -1, 2])
+        return f
+
+    def mul2(a, b):
+        out = [[0] * (max(len(r) for r in a) + max(len(r) for r in b) - 1) for _ in range(len(a) + len(b) - 1)]
+        for j1, r1 in enumerate(a):
+            for i1, c1 in enumerate(r1):
+                for j2, r2 in enumerate(b):
+                    for i2, c2 in enumerate(r2):
+                        out[j1 + j2][i1 + i2] += c1 * c2
+        return out
+
+    pairs = [([[0, 1], [1]], [[0, 1], [-1]]), ([[0, 0], [0, 1]], [[0, 0, 1]])]
+    for _ in range(150):
+        h = rand2(rng.randint(0, 2), rng.randint(0, 2), 3)
+        u, v = rand2(rng.randint(0, 2), rng.randint(0, 2), 4), rand2(rng.randint(0, 2), rng.randint(0, 2), 4)
+        if rng.random() < 0.3:                      # no constant terms: images share powers of z
+            u, v = mul2(u, [[0, 1], [rng.choice([1, -1, 2])]]), mul2(v, [[0, 1], [rng.choice([1, -1, 3])]])
+        pairs.append((mul2(h, u), mul2(h, v)))
+    n = len(pairs)
+    D0 = [max(max(len(r) for r in a), max(len(r) for r in b)) for a, b in pairs]
+    D, ys, tries = list(D0), [0] * n, [0] * n
+    pend, done, shifted = list(range(n)), 0, 0
+    for _ in range(40):
+        if not pend:
+            break
+        lines, data = [str(len(pend))], []
+        for k in pend:
+            a, b = pairs[k]
+            if ys[k]:
+                a, b = _shift_rows(a, ys[k]), _shift_rows(b, ys[k])
+            za, zb = _kron(a, D[k]), _kron(b, D[k])
+            G = list(O.gcd_z(za, zb))
+            Ga = list(O.zx_divexact(O.zx_trim(za), tuple(G))) if G else []
+            Gb = list(O.zx_divexact(O.zx_trim(zb), tuple(G))) if G else []
+            data.append((G, Ga, Gb))
+            lines.append(str(D[k]))
+            for p in (G, Ga, Gb):
+                lines.append(" ".join([str(len(p) - 1)] + [str((c > 0) - (c < 0)) for c in p]))
+        res = subprocess.run([exe], input="\n".join(lines) + "\n", check=True, capture_output=True, text=True)
+        cand = [int(t) for t in res.stdout.split()]
+        retry = []
+        for k, t, (G, Ga, Gb) in zip(pend, cand, data):
+            if t < 0:
+                D[k] += 1
+                tries[k] += 1
+                if tries[k] == 4:
+                    ys[k] += 1
+                    assert ys[k] <= 3, k
+                    D[k], tries[k] = D0[k], 0
+                retry.append(k)
+                continue
+            a, b = pairs[k]
+            H = O.gcd_zxy(a, b)
+            assert _shift_rows(_unkron(G, D[k], -t), -ys[k]) == H, k
+            assert _shift_rows(_unkron(Ga, D[k], t), -ys[k]) == O.divexact_zxy(a, H), k
+            assert _shift_rows(_unkron(Gb, D[k], t), -ys[k]) == O.divexact_zxy(b, H), k
+            done += 1
+            shifted += ys[k] > 0
+        pend = retry
+    assert not pend and done == n
+    assert shifted >= 1                     # the (1, 1) case took the shifted path
