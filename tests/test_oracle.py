@@ -69,6 +69,19 @@ def test_hand_gcds(k):
     assert O.gcd_z(e["p"], e["q"]) == tuple(e["gcd"])
 
 
+@pytest.mark.parametrize("k", range(len(GOLD["teissier"])))
+def test_hand_teissier(k):
+    """Hand-derived h, f_x/h, f_y/h and Q (Section 2.1); the first two have
+    deg_y(f_x/h) = deg_y(f_y/h) = 1, so swapped operands would flip the sign of Q."""
+    from oracle.bigcd import teissier_parts, teissier_q
+
+    e = GOLD["teissier"][k]
+    h, fxs, fys = teissier_parts(e["f"])
+    assert h == [tuple(r) for r in e["h"]]
+    assert fxs == [tuple(r) for r in e["fx_star"]] and fys == [tuple(r) for r in e["fy_star"]]
+    assert teissier_q(e["f"]) == tuple(e["q"])
+
+
 # --------------------------------------------------------------------------- closed forms
 
 
