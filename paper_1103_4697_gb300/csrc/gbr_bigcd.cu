@@ -67,21 +67,6 @@ void clear(gbr_bigbipoly &x) {
     x.c = gbr_bigpoly{-1, 0, nullptr, nullptr};
 }
 
-// in[j][i] (deg_x + 1 columns) -> in(x, y + s), column by column (Taylor shift in
-// y by repeated synthetic division); false on int64 overflow
-bool shift_y_i64(const int64_t *in, int dx, int dy, int s, std::vector<int64_t> &out) {
-    out.assign(in, in + (size_t)(dx + 1) * (dy + 1));
-    for (int i = 0; i <= dx; ++i)
-        for (int k = 0; k < dy; ++k)
-            for (int j = dy - 1; j >= k; --j) {
-                int64_t t;
-                if (__builtin_mul_overflow(out[(size_t)(j + 1) * (dx + 1) + i], (int64_t)s, &t) ||
-                    __builtin_add_overflow(out[(size_t)j * (dx + 1) + i], t, &out[(size_t)j * (dx + 1) + i]))
-                    return false;
-            }
-    return true;
-}
-
 // x <- x(x, y - s) in exact big integers (the inverse of the input shift)
 bool unshift_y(gbr_ctx *c, gbr_bigbipoly &x, int s) {
     if (x.deg_y < 1) return true;   // constants in y are unchanged
@@ -89,13 +74,7 @@ bool unshift_y(gbr_ctx *c, gbr_bigbipoly &x, int s) {
     std::vector<bn::Big> g((size_t)(dx + 1) * (dy + 1));
     for (size_t t = 0; t < g.size(); ++t)
         if (x.c.sign[t]) g[t] = bn::from_limbs(x.c.mag + t * L, L, x.c.sign[t]);
-    const bn::Big ms = bn::from_i64(-(int64_t)s);
-    for (int i = 0; i <= dx; ++i)
-        for (int k = 0; k < dy; ++k)
-            for (int j = dy - 1; j >= k; --j) {
-                bn::Big &cj = g[(size_t)j * (dx + 1) + i];
-                cj = bn::add(cj, bn::mul(g[(size_t)(j + 1) * (dx + 1) + i], ms));
-            }
+    unshift_y_big(g, dx, dy, s);
     size_t nl = 1;
     for (const bn::Big &b : g) nl = std::max(nl, b.m.size());
     gbr_bigbipoly y;
@@ -224,63 +203,6 @@ extern "C" void gbr_free_bigbipoly(gbr_ctx *c, gbr_bigbipoly *x) {
 }
 
 // ------------------------------------------------------------------ Teissier resultant
-
-namespace {
-
-// derivative of an int64 bipoly in x (wx = true) or y, into `buf`; false on overflow
-bool derive(const gbr_bipoly &f, bool wx, std::vector<int64_t> &buf, gbr_bipoly &out) {
-    const int dx = f.deg_x, dy = f.deg_y;
-    const int ox = wx ? std::max(dx - 1, 0) : dx, oy = wx ? dy : std::max(dy - 1, 0);
-    buf.assign((size_t)(ox + 1) * (oy + 1), 0);
-    const int64_t *cf = (const int64_t *)f.coef;
-    for (int j = 0; j <= oy; ++j)
-        for (int i = 0; i <= ox; ++i) {
-            const int si = wx ? i + 1 : i, sj = wx ? j : j + 1;
-            if (si > dx || sj > dy) continue;
-            const int64_t v = cf[(size_t)sj * (dx + 1) + si], k = wx ? si : sj;
-            int64_t r;
-            if (__builtin_mul_overflow(v, k, &r)) return false;
-            buf[(size_t)j * (ox + 1) + i] = r;
-        }
-    out.deg_x = ox;
-    out.deg_y = oy;
-    out.words = 1;
-    out.coef = buf.data();
-    return true;
-}
-
-// a sign-magnitude bigbipoly as an array of two's-complement 64-bit words
-bool to_words(const gbr_bigbipoly &x, std::vector<uint64_t> &buf, gbr_bipoly &out) {
-    if (x.deg_y < 0) {   // zero: one coefficient 0
-        buf.assign(1, 0);
-        out.deg_x = out.deg_y = 0;
-        out.words = 1;
-        out.coef = buf.data();
-        return true;
-    }
-    const int L = x.c.limbs, W = (L * 32 + 1 + 63) / 64;
-    if (W > GBR_MAX_WORDS) return false;
-    const int nco = (x.deg_x + 1) * (x.deg_y + 1);
-    buf.assign((size_t)nco * W, 0);
-    for (int t = 0; t < nco; ++t) {
-        uint64_t *w = buf.data() + (size_t)t * W;
-        for (int l = 0; l < L; ++l) w[l / 2] |= (uint64_t)x.c.mag[(size_t)t * L + l] << (32 * (l % 2));
-        if (x.c.sign[t] < 0) {   // negate in two's complement
-            uint64_t carry = 1;
-            for (int k = 0; k < W; ++k) {
-                w[k] = ~w[k] + carry;
-                carry = (carry && w[k] == 0) ? 1 : 0;
-            }
-        }
-    }
-    out.deg_x = x.deg_x;
-    out.deg_y = x.deg_y;
-    out.words = W;
-    out.coef = buf.data();
-    return true;
-}
-
-}  // namespace
 
 extern "C" int gbr_teissier_res_batch(gbr_ctx *c, int n, const gbr_bipoly *f, gbr_bigpoly *q) {
     if (!c || n < 0 || (n && (!f || !q))) return GBR_EINVAL;

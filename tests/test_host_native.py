@@ -233,3 +233,132 @@ def test_kronecker_shift_choice(tmp_path):
         pend = retry
     assert not pend and done == n
     assert shifted >= 1                     # the (1, 1) case took the shifted path
+
+
+def _limbs(v):
+    m, out = abs(v), []
+    while m:
+        out.append(m & 0xFFFFFFFF)
+        m >>= 32
+    return out
+
+
+def _taylor(rows, s):
+    """rows[j][i] of f(x, y) -> rows of f(x, y + s) by the binomial theorem."""
+    dy, w = len(rows) - 1, len(rows[0])
+    out = [[0] * w for _ in range(dy + 1)]
+    for j in range(dy + 1):
+        for k in range(j + 1):
+            c = math.comb(j, k) * s ** (j - k)
+            for i in range(w):
+                out[k][i] += c * rows[j][i]
+    return out
+
+
+def test_kronecker_host_helpers(tmp_path):
+    """The bivariate gcd's int64 shift y -> y + s (exact, or refused on int64
+    overflow), the big-integer shift back, the partial derivatives of an int64 curve
+    and the two's-complement packing of big cofactors, against Python integers
+    (binomial expansions, plain products, two's-complement decoding)."""
+    import random
+
+    exe = _build(tmp_path, "kron_ops_harness.cpp")
+    rng = random.Random(62)
+    I64 = (-(1 << 63), (1 << 63) - 1)
+    cmds, checks = [], []
+
+    def flat(rows):
+        return [c for r in rows for c in r]
+
+    def unflat(v, dx, dy):
+        return [v[j * (dx + 1):(j + 1) * (dx + 1)] for j in range(dy + 1)]
+
+    for _ in range(300):                                     # S: y -> y + s in int64
+        dx, dy, s = rng.randint(0, 4), rng.randint(0, 6), rng.randint(1, 3)
+        big = rng.random() < 0.3
+        amp = (1 << rng.randint(50, 62)) if big else 1000
+        rows = [[rng.randint(-amp, amp) for _ in range(dx + 1)] for _ in range(dy + 1)]
+        cmds.append(" ".join(map(str, ["S", dx, dy, s] + flat(rows))))
+        checks.append(("S", rows, s, dx, dy))
+    for _ in range(200):                                     # U: y -> y - s in big integers
+        dx, dy, s = rng.randint(0, 3), rng.randint(0, 6), rng.randint(1, 3)
+        rows = [[rng.choice([0, rng.randint(-(1 << 300), 1 << 300)]) for _ in range(dx + 1)] for _ in range(dy + 1)]
+        words = ["U", dx, dy, s]
+        for c in flat(rows):
+            l = _limbs(c)
+            words += [(c > 0) - (c < 0), len(l)] + l
+        cmds.append(" ".join(map(str, words)))
+        checks.append(("U", rows, s, dx, dy))
+    for _ in range(200):                                     # D: derivatives in x and y
+        dx, dy, wx = rng.randint(0, 5), rng.randint(0, 5), rng.randint(0, 1)
+        amp = (1 << 61) if rng.random() < 0.3 else 1 << 20
+        rows = [[rng.randint(-amp, amp) for _ in range(dx + 1)] for _ in range(dy + 1)]
+        cmds.append(" ".join(map(str, ["D", wx, dx, dy] + flat(rows))))
+        checks.append(("D", rows, wx, dx, dy))
+    for _ in range(200):                                     # W: two's-complement words
+        dx, dy, L = rng.randint(0, 3), rng.randint(-1, 3), rng.randint(1, 17)
+        nco = (dx + 1) * (dy + 1) if dy >= 0 else 0
+        vals = [rng.choice([0, rng.randint(-(1 << (32 * L)) + 1, (1 << (32 * L)) - 1)]) for _ in range(nco)]
+        words = ["W", dx, dy, L]
+        for c in vals:
+            l = _limbs(c) + [0] * L
+            words += [(c > 0) - (c < 0)] + l[:L]
+        cmds.append(" ".join(map(str, words)))
+        checks.append(("W", vals, L, dx, dy))
+
+    res = subprocess.run([exe], input="\n".join(cmds) + "\n", check=True, capture_output=True, text=True)
+    lines = res.stdout.splitlines()
+    assert len(lines) == len(checks)
+    seen = {"OVF": 0, "LIMIT": 0}
+    for line, (op, a, b, dx, dy) in zip(lines, checks):
+        t = line.split()
+        if op == "S":
+            want = flat(_taylor(a, b))
+            fits = all(I64[0] <= v <= I64[1] for v in want)
+            small = all(abs(c) <= 1000 for c in flat(a))
+            if t[0] == "OVF":
+                assert not small, line                       # small inputs never overflow
+                seen["OVF"] += 1
+            else:
+                assert [int(v) for v in t[1:]] == want
+            if not fits:
+                assert t[0] == "OVF"
+        elif op == "U":
+            want, got, k = flat(_taylor(a, -b)), [], 0
+            while k < len(t):
+                sg, nl = int(t[k]), int(t[k + 1])
+                got.append(sg * sum(int(v) << (32 * q) for q, v in enumerate(t[k + 2:k + 2 + nl])))
+                k += 2 + nl
+            assert got == want
+            assert flat(_taylor(unflat(got, dx, dy), b)) == flat(a)        # the shift back inverts the shift
+        elif op == "D":
+            if b:   # d/dx
+                ox, oy = max(dx - 1, 0), dy
+                want = [[(i + 1) * a[j][i + 1] if i + 1 <= dx else 0 for i in range(ox + 1)] for j in range(oy + 1)]
+            else:
+                ox, oy = dx, max(dy - 1, 0)
+                want = [[(j + 1) * a[j + 1][i] if j + 1 <= dy else 0 for i in range(ox + 1)] for j in range(oy + 1)]
+            fits = all(I64[0] <= v <= I64[1] for v in flat(want))
+            if fits:
+                assert t[:3] == ["OK", str(ox), str(oy)] and [int(v) for v in t[3:]] == flat(want), line
+            else:
+                assert t == ["OVF"]
+                seen["OVF"] += 1
+        else:
+            L, W = b, (32 * b + 1 + 63) // 64
+            if dy < 0:                                   # zero: one coefficient 0, whatever L
+                assert t == ["OK", "0", "0", "1", "0"]
+                continue
+            if W > 8:
+                assert t == ["LIMIT"]
+                seen["LIMIT"] += 1
+                continue
+            assert t[0] == "OK"
+            assert t[1:4] == [str(dx), str(dy), str(W)]
+            w = [int(v) for v in t[4:]]
+            got = []
+            for c in range(len(a)):
+                u = sum(w[c * W + q] << (64 * q) for q in range(W))
+                got.append(u - (1 << (64 * W)) if u >> (64 * W - 1) else u)
+            assert got == a
+    assert seen["OVF"] > 0 and seen["LIMIT"] > 0
