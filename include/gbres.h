@@ -417,13 +417,17 @@ int gbr_num_primes(void);
 int gbr_prime(int index, uint32_t *p);
 
 /* Number of primes from the table whose product exceeds 2^bits (the count a
- * resultant whose coefficients satisfy |c| < 2^(bits-1) needs). */
+ * resultant whose coefficients satisfy |c| < 2^(bits-1) needs); -1 when the
+ * product of all GBR_MAX_PRIMES primes does not. */
 int gbr_primes_for_bits(double bits);
 
 /* Resultant planning for a pair given on the host: actual degrees m, n, the
  * x-degree bound D (min of n deg_x f + m deg_x g and the total-degree Bezout
  * bound), log2 of the Hadamard bound B on |coefficients| and the number of
- * primes k with prod p > 2B + 1.  Host only.  disc = 1 uses g = df/dvar.
+ * primes k with prod p > 2B + 1 (-1 when more than GBR_MAX_PRIMES would be
+ * needed: a resultant call then returns GBR_ELIMIT).  Host only.  disc = 1 uses
+ * g = df/dvar.  GBR_ELIMIT when m or n exceeds GBR_MAX_YDEG, GBR_EINVAL for an
+ * input of more than GBR_MAX_WORDS words per coefficient.
  * B is the smallest scaled bound over all lambda values; the device evaluates
  * the same bounds in single precision rounded upward, so its B can be slightly
  * larger (at most a few thousandths of a bit) and, in a near tie, take one

@@ -1212,6 +1212,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     // ---- buffer offsets and work lists
     int64_t res_w = 0, val_w = 0, cf_w = 0, flag_b = 0, gtab_w = 0, out_w = 0, sign_b = 0;
     int Kmax = 1, Pmax = 1, Lmax = 1, Kdig = 1;   // Kdig: most primes of one pair
+    int Puse = 1;   // most points one interpolation uses (Pmax also counts the spare points)
     HostList red, interp, crt, crtf;
     int Kdig_f = 1, Lmax_f = 1;
     // evaluation buckets by y-degree (key / 4), register-form buckets by N, and
@@ -1257,6 +1258,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
         Kmax = std::max(Kmax, p.pmap_off >= 0 ? pmap[p.pmap_off + k - 1] + 1 : k);
         Kdig = std::max(Kdig, k);
         Pmax = std::max(Pmax, p.Pe);
+        Puse = std::max(Puse, p.P);
         Lmax = std::max(Lmax, p.L);
         red.add(q, p.S);
         int key = ((std::max(p.m, p.n) + 1) + 3) / 4 * 4;
@@ -1569,7 +1571,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
         }
         record(3, capturing, q);
         if (x == cudaSuccess && interp.total > 0) {
-            x = launch_interp(L, mk(o_int_p, o_int_s, interp), Pmax, q);
+            x = launch_interp(L, mk(o_int_p, o_int_s, interp), Puse, q);
             kernels++;
         }
         if (x == cudaSuccess && !gtiles.empty()) {

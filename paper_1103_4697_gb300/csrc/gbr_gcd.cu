@@ -822,8 +822,10 @@ static int gcd_batch_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upo
                 e = cudaGetLastError();
             }
             if (e == cudaSuccess) {
+                // one thread per coefficient, no warp-wide operation: blocks below a
+                // warp are fine for very wide lifts
                 int block = 128;
-                while (block > 32 && (size_t)maxL * block * 4 > 160 * 1024) block >>= 1;
+                while (block > 1 && (size_t)maxL * block * 4 > 160 * 1024) block >>= 1;
                 size_t sm2 = (size_t)maxL * block * 4;
                 if (sm2 > (size_t)kMaxDynSmem) e = cudaErrorInvalidValue;
                 if (e == cudaSuccess) {

@@ -188,7 +188,10 @@ __device__ float row_log2_up(const uint64_t *coef, const PolyDesc &P, int r, int
         }
         for (int o = 16; o; o >>= 1) G += __shfl_xor_sync(0xffffffffu, G, o);
         __syncwarp();
-        return 0.5f * log2_up(G * (1.0 + 0x1p-40));   // the double sums of at most 160 non-negative terms
+        // G: a lane's sum of about L / 32 non-negative terms plus five shuffle
+        // additions; a row whose norm enters the bound (m, n >= 1) has L <= 16384
+        // under the point limit, so the relative error stays below 2^-43
+        return 0.5f * log2_up(G * (1.0 + 0x1p-40));
     }
     // multi-word: the 1-norm.  Each |c| <= m32 2^(e - 31) with m32 its top 32 bits
     // (plus one when lower bits are set) and e its top bit; the terms are summed
@@ -1032,6 +1035,9 @@ cudaError_t launch_crt(const ResLaunch &L, const WorkList &w, int maxK, int maxL
     int block = 128;
     while (block > 32 && (size_t)(maxK + maxL) * block * 4 > 160 * 1024) block >>= 1;
     if ((size_t)(maxK + maxL) * block * 4 > 160 * 1024) maxK = 0;   // digits stay in global memory
+    // results of more than 1280 limbs (about 1320 primes): fewer threads per block,
+    // below a warp if need be (every thread works alone, no warp-wide operation)
+    while (block > 1 && (size_t)maxL * block * 4 > 160 * 1024) block >>= 1;
     size_t smem = (size_t)(maxK + maxL) * block * sizeof(uint32_t);
     if (smem > kMaxDynSmem) return cudaErrorInvalidValue;
     int grid = persistent_grid(k_crt, block, smem, (w.total + block - 1) / block);

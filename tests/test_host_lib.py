@@ -172,3 +172,42 @@ def test_scaled_bound_holds_on_varied_shapes(lib, seed):
             continue
         assert all(c == 0 or math.log2(abs(c)) <= info["log2_bound"] + 1e-9 for c in R), (info, disc)
         assert len(R) - 1 <= info["deg_bound"]
+
+
+def _rand_rows(rng, dy, dx, amp):
+    rows = [[rng.randint(-amp, amp) for _ in range(dx + 1)] for _ in range(dy + 1)]
+    rows[dy][dx] = amp                                   # full degree in both variables
+    return rows
+
+
+def test_resultant_info_at_the_size_limits(lib):
+    """The documented limits of include/gbres.h on the host-side plan: y-degree
+    GBR_MAX_YDEG (127) and 8-word (511-bit) coefficients are planned, y-degree 128
+    and a 512-bit coefficient (9 words) are refused with GBR_ELIMIT and GBR_EINVAL.
+    The 8-word pair of y-degree 56 needs between 1321 and 2048 primes, so its
+    result is wider than 1280 limbs (the Chinese remaindering's narrow-block case);
+    y-degree 64 needs more than GBR_MAX_PRIMES (primes = -1)."""
+    from paper_1103_4697_gb300.api import resultant_info
+
+    rng = random.Random(71)
+    f, g = _rand_rows(rng, 127, 1, 3), _rand_rows(rng, 127, 1, 3)
+    i = resultant_info(f, g)
+    assert (i["m"], i["n"]) == (127, 127) and 0 < i["deg_bound"] <= 254
+    d = resultant_info(f, None, disc=True)
+    assert (d["m"], d["n"]) == (127, 126)
+    with pytest.raises(N.GbrError) as e:
+        resultant_info(_rand_rows(rng, 128, 1, 3), g)
+    assert e.value.status == N.ELIMIT
+
+    big = (1 << 511) - 1                                  # the widest 8-word two's-complement magnitude
+    f8, g8 = _rand_rows(rng, 56, 1, big), _rand_rows(rng, 56, 1, big)
+    i8 = resultant_info(f8, g8)
+    assert 1321 < i8["primes"] <= 2048 and i8["limbs"] > 1280
+    assert i8["deg_bound"] == 112
+    f9 = [list(r) for r in f8]
+    f9[0][0] = 1 << 511                                   # 512 bits and a sign bit: 9 words
+    with pytest.raises(N.GbrError) as e:
+        resultant_info(f9, g8)
+    assert e.value.status == N.EINVAL
+    i64 = resultant_info(_rand_rows(rng, 64, 1, big), _rand_rows(rng, 64, 1, big))
+    assert i64["primes"] == -1                            # more than the table's GBR_MAX_PRIMES primes
