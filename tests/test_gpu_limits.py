@@ -16,6 +16,7 @@ import random
 import pytest
 
 import oracle as O
+from oracle.resultant import as_zxy
 from paper_1103_4697_gb300 import native as N
 
 pytestmark = pytest.mark.gpu
@@ -46,7 +47,7 @@ def _ev(r, a):
 def _points(f, g, cands):
     """The candidate points where lc_y f and lc_y g do not vanish (the oracle's
     integer subresultant sequence applies there)."""
-    lf, lg = O.as_zxy(f)[-1], O.as_zxy(g)[-1]
+    lf, lg = as_zxy(f)[-1], as_zxy(g)[-1]
     return [a for a in cands if O.zx_eval(lf, a) != 0 and O.zx_eval(lg, a) != 0]
 
 
