@@ -540,6 +540,24 @@ def test_teissier_q_against_sympy(seed):
     assert got == [int(c) for c in want] or got == [-int(c) for c in want]
 
 
+def test_teissier_q_degenerate_curves():
+    """Q = res(f_x/h, f_y/h, y) is the zero polynomial () when f_x or f_y vanishes
+    (Section 2.1 with the determinant convention res(0, g) = 0): a curve in y
+    alone (f_x = 0, h = f_y up to its sign), in x alone (f_y = 0) and a constant
+    (h = gcd(0, 0) = 0)."""
+    from oracle.bigcd import teissier_parts, teissier_q
+
+    fy_only = [[1], [0], [1]]                                   # y^2 + 1
+    h, fxs, fys = teissier_parts(fy_only)
+    assert h == [(), (2,)] and fxs == [] and fys == [(1,)]      # h = 2y, f_x / h = 0, f_y / h = 1
+    assert teissier_q(fy_only) == ()
+    fx_only = [[5, -1, 0, 1]]                                   # x^3 - x + 5
+    h, fxs, fys = teissier_parts(fx_only)
+    assert h == [(-1, 0, 3)] and fxs == [(1,)] and fys == []
+    assert teissier_q(fx_only) == ()
+    assert teissier_parts([[7]]) == ([], [], []) and teissier_q([[7]]) == ()
+
+
 def test_teissier_q_generic_curve_is_the_plain_resultant():
     """gcd(f_x, f_y) = 1 for a generic curve, so Q = res(f_x, f_y) itself (with the
     x-derivative taken row by row)."""

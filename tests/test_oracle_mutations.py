@@ -73,6 +73,28 @@ MUTATIONS = [
     ("teissier_operands_swapped", "bigcd.py",
      "return res_subres([list(r) or [0] for r in fxs], [list(r) or [0] for r in fys])",
      "return res_subres([list(r) or [0] for r in fys], [list(r) or [0] for r in fxs])"),
+    ("teissier_zero_not_trimmed", "bigcd.py", "    if not fxs or not fys:\n        return ()\n",
+     "    if not fxs or not fys:\n        return (0,)\n"),
+    ("pp_y_no_division", "bigcd.py", "return [zx_divexact(r, c) if r else () for r in F] if c else []", "return F"),
+    ("content_y_skips_first_row", "bigcd.py", "    for row in as_zxy(f):\n        g = gcd_z(g, row)",
+     "    for row in as_zxy(f)[1:]:\n        g = gcd_z(g, row)"),
+    # more of the resultant's definition and evaluation
+    ("evalz_window_ignores_g", "resultant.py", "zx_eval(lf, a) * zx_eval(lg, a) == 0", "zx_eval(lf, a) == 0"),
+    ("bareiss_pivot_search_skips_a_row", "resultant.py", "for i in range(k + 1, n) if not ring.is_zero(A[i][k])",
+     "for i in range(k + 2, n) if not ring.is_zero(A[i][k])"),
+    ("res_at_operands_swapped", "resultant.py", "return det_bareiss(sylvester(Fa, Ga, ZZ), ZZ)",
+     "return det_bareiss(sylvester(Ga, Fa, ZZ), ZZ)"),
+    ("subres_constant_power", "resultant.py",
+     "        v = _pow(B[0], da, ring)\n        return v if s > 0 else ring.neg(v)\n    g = ring.one",
+     "        v = _pow(B[0], max(da - 1, 0), ring)\n        return v if s > 0 else ring.neg(v)\n    g = ring.one"),
+    ("leibniz_sign_dropped", "resultant.py",
+     "total = ring.add(total, term) if _perm_sign(p) > 0 else ring.sub(total, term)", "total = ring.add(total, term)"),
+    ("degree_bound_transposed", "resultant.py", "return max(0, n * dxf + m * dxg)", "return max(0, m * dxf + n * dxg)"),
+    ("deriv_y_drops_top_row", "resultant.py", "for j in range(len(F) - 1)]", "for j in range(len(F) - 2)]"),
+    ("zx_eval_sign", "zpoly.py", "v = v * x + c", "v = v * x - c"),
+    ("primitive_part_keeps_content", "zpoly.py", "    g = content(a)\n    if a[-1] < 0:", "    g = 1\n    if a[-1] < 0:"),
+    ("gcd_content_of_one_argument", "gcd.py", "c = math.gcd(content(p), content(q))", "c = content(p)"),
+    ("yun_quotient_not_divided", "sqf.py", "        c = zx_divexact(c, ri)\n", "        c = c[1:] or c\n"),
 ]
 
 
