@@ -181,7 +181,11 @@ int gbr_get_stats(gbr_ctx *ctx, gbr_stats *out);
 
 /* res_var(f, g): var = 1 eliminates y (res_y, the paper's R_CD), var = 0
  * eliminates x.  Bounds, modular reduction, evaluation, per-(prime, point)
- * resultants, interpolation and Chinese remaindering all run on the device. */
+ * resultants, interpolation and Chinese remaindering all run on the device.
+ * GBR_EINVAL for more than GBR_MAX_WORDS words per coefficient; GBR_ELIMIT when
+ * a degree in var exceeds GBR_MAX_YDEG, the degree bound of the result exceeds
+ * GBR_MAX_POINTS - 1, or the coefficient bound needs more than GBR_MAX_PRIMES
+ * primes (gbr_resultant_info answers these on the host). */
 int gbr_resultant(gbr_ctx *ctx, const gbr_bipoly *f, const gbr_bipoly *g, int var, gbr_bigpoly *out);
 
 /* res_var(f, df/dvar), the projection resultant R of Section 2.1, not divided
@@ -191,7 +195,9 @@ int gbr_discriminant_res(gbr_ctx *ctx, const gbr_bipoly *f, int var, gbr_bigpoly
 /* gcd(p, q) in Z[x] (Section 2: content removal; Section 2.1: square-free
  * factorisation).  Modular images over the table primes, Chinese remaindering of
  * the gcd and both cofactors, and an exact norm check that proves the result
- * (on failure more primes are added).  Input coefficients: words must be 1. */
+ * (on failure more primes are added).  Input coefficients: words must be 1;
+ * GBR_ELIMIT for a degree above GBR_MAX_UDEG or a bound that needs more than
+ * GBR_MAX_PRIMES primes. */
 int gbr_gcd(gbr_ctx *ctx, const gbr_upoly *p, const gbr_upoly *q, gbr_bigpoly *out);
 
 /* ------------------------------------------------------------------ batches */
@@ -277,7 +283,10 @@ typedef struct {
  * primes whose product exceeds both sides' coefficient bounds.  The host takes
  * the primitive parts (big-integer gcds of the lifted coefficients) and u.  A
  * failed check retries with twice the primes; GBR_EVERIFY once the table is
- * exhausted.  On error every out[i] is left empty (count 0, NULL pointers). */
+ * exhausted.  GBR_ELIMIT when a lift needs more primes than the lift kernel
+ * holds in shared memory (primes + limbs above 1600: about 810 primes, a
+ * factor bound above about 24 000 bits).  On error every out[i] is left empty
+ * (count 0, NULL pointers). */
 int gbr_squarefree(gbr_ctx *ctx, const gbr_bigpoly *r, gbr_sqf *out);
 int gbr_squarefree_batch(gbr_ctx *ctx, int n, const gbr_bigpoly *r, gbr_sqf *out);
 void gbr_free_sqf(gbr_ctx *ctx, gbr_sqf *x);
