@@ -211,3 +211,44 @@ def test_resultant_info_at_the_size_limits(lib):
     assert e.value.status == N.EINVAL
     i64 = resultant_info(_rand_rows(rng, 64, 1, big), _rand_rows(rng, 64, 1, big))
     assert i64["primes"] == -1                            # more than the table's GBR_MAX_PRIMES primes
+
+
+def _is_prime(v):
+    if v < 2 or v % 2 == 0:
+        return v == 2
+    d = 3
+    while d * d <= v:
+        if v % d == 0:
+            return False
+        d += 2
+    return True
+
+
+def test_header_is_plain_c_and_links_from_c(lib, tmp_path):
+    """include/gbres.h compiles as C99 (-Wall -Wextra -pedantic -Werror) and a C
+    program linked against libgbres.so gets the host-only answers: the table's
+    two largest primes below 2^32 / 3, prime counts (-1 beyond the table), the
+    plan of res_y(x^2 + y^2 - 25, y + x - 1) and of its projection resultant,
+    GBR_EINVAL for var = 2, and a status string."""
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if not gcc:
+        pytest.skip("gcc not available")
+    exe = str(tmp_path / "c_abi_example")
+    libdir = os.path.dirname(N.LIB_PATH)
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                    "-o", exe, os.path.join(ROOT, "tests", "native", "c_abi_example.c"), "-L", libdir, "-lgbres",
+                    "-Wl,-rpath," + libdir], check=True, capture_output=True, text=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
+    top = (2 ** 32 - 1) // 3
+    want_p = [v for v in range(top, top - 200, -1) if _is_prime(v)][:2]
+    assert out[0] == "num_primes 2048"
+    assert out[1] == f"primes 0 {want_p[0]} {want_p[1]}"
+    assert out[2] == "primes_for_bits 4 -1"            # 3 primes give about 91 bits, 4 about 121
+    # m = 2, n = 1; D = min(n deg_x f + m deg_x g, Bezout 2 * 1) = min(4, 2) = 2; one prime
+    assert out[3] == "info 0 2 1 2 1"
+    assert out[4] == "disc 0 2 1 2"                    # f_y = 2y: D = min(1 * 2 + 2 * 0, 2 * 1) = 2
+    assert out[5] == f"bad_var {N.EINVAL}"
+    assert out[6] == "strerror " + lib.gbr_strerror(N.ELIMIT).decode()
