@@ -179,6 +179,7 @@ extern "C" int gbr_gcd2_batch(gbr_ctx *c, int n, const gbr_bipoly *a, const gbr_
                               gbr_bigbipoly *a_over_h, gbr_bigbipoly *b_over_h) {
     if (!c || n < 0 || (n && (!a || !b || !h || !a_over_h || !b_over_h))) return GBR_EINVAL;
     if (n == 0) return GBR_OK;
+    NvtxScope call("gbr_gcd2_batch");
     std::lock_guard<std::mutex> lk(c->mu);
     cudaSetDevice(c->device);
     int st;
@@ -208,6 +209,7 @@ extern "C" int gbr_teissier_res_batch(gbr_ctx *c, int n, const gbr_bipoly *f, gb
     if (!c || n < 0 || (n && (!f || !q))) return GBR_EINVAL;
     for (int i = 0; i < n; ++i) q[i] = gbr_bigpoly{-1, 0, nullptr, nullptr};
     if (n == 0) return GBR_OK;
+    NvtxScope call("gbr_teissier_res_batch");
     std::vector<std::vector<int64_t>> bx(n), by(n);
     std::vector<gbr_bipoly> fx(n), fy(n);
     for (int i = 0; i < n; ++i) {
@@ -326,6 +328,7 @@ extern "C" int gbr_content_batch(gbr_ctx *c, int n, const gbr_bipoly *f, int var
     if (!c || n < 0 || (n && (!f || !out)) || (var != 0 && var != 1)) return GBR_EINVAL;
     for (int i = 0; i < n; ++i) out[i] = gbr_bigpoly{-1, 0, nullptr, nullptr};
     if (n == 0) return GBR_OK;
+    NvtxScope call("gbr_content_batch");
     std::lock_guard<std::mutex> lk(c->mu);
     cudaSetDevice(c->device);
     int st;

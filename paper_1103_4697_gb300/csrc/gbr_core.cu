@@ -1088,6 +1088,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     }
     if (c->stats_on) cudaEventRecord(c->ev[0], s);
     // ---- A0 (device half): measure degrees and bounds
+    NvtxScope phase("gbr: bounds (A0, device)");
     ResLaunch L{};
     L.coef = r->d_coef;
     L.desc = r->d_desc;
@@ -1107,6 +1108,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "bounds readback", e);
     // ---- A0 (host half): degrees, point counts and prime counts
+    phase.next("gbr: plan (A0, host)");
     std::vector<PairPlan> &plan = r->h_plan;
     plan.assign(n, PairPlan{});
     r->h_log2B.assign(n, 0.0);
@@ -1530,6 +1532,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
         return cudaSuccess;
     };
     // ---- the device stages; replayed from a captured CUDA graph when the plan repeats
+    phase.next("gbr: device stages (A1-A5)");
     int64_t kernels = 1;
     auto record = [&](int idx, bool capturing, cudaStream_t q) {
         if (!c->stats_on) return;
@@ -1670,6 +1673,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
 
 int gbr_run_resident_finish(gbr_ctx *c, gbr_resident *r) {
     if (!r->pending) return GBR_OK;
+    NvtxScope phase("gbr: finish (wait for the stages, check)");
     r->pending = false;
     cudaStream_t s = c->stream;
     gbr_stats st = r->pend_st;
@@ -1711,6 +1715,7 @@ int gbr_run_resident_locked(gbr_ctx *c, gbr_resident *r) {
 
 extern "C" int gbr_run_resident(gbr_ctx *c, gbr_resident *r) {
     if (!c || !r) return GBR_EINVAL;
+    NvtxScope call("gbr_run_resident");
     std::lock_guard<std::mutex> lk(c->mu);
     cudaSetDevice(c->device);
     try {
@@ -1724,6 +1729,7 @@ int gbr_fetch_resident_locked(gbr_ctx *c, gbr_resident *r, int first, int count,
     if (first < 0 || count < 0 || first + count > r->n || (count && !out)) return GBR_EINVAL;
     if (!r->ran) return c->fail(GBR_EINVAL, "fetch before run");
     if (count == 0) return GBR_OK;
+    NvtxScope phase("gbr: fetch results");
     const std::vector<PairPlan> &plan = r->h_plan;
     int last = first + count - 1;
     int64_t o0 = plan[first].out_off, o1 = plan[last].out_off + (int64_t)plan[last].P * plan[last].L;
@@ -1880,6 +1886,7 @@ static int res_batch_impl(gbr_ctx *c, int n, const gbr_bipoly *f, const gbr_bipo
         out[i].mag = nullptr;
         out[i].sign = nullptr;
     }
+    NvtxScope call(disc ? "gbr_discriminant_res_batch" : "gbr_resultant_batch");
     if (n >= kPipeMinPairs && c->pipe_on && !c->parent) {
         std::lock_guard<std::mutex> lk(c->mu);
         cudaSetDevice(c->device);
@@ -1929,6 +1936,7 @@ extern "C" int gbr_arrangement_resultants(gbr_ctx *c, int n, const gbr_bipoly *f
     if ((int64_t)n * (n + 1) / 2 > INT32_MAX / 4) return GBR_ELIMIT;
     const int nj = n * (n + 1) / 2;
     for (int i = 0; i < nj; ++i) out[i] = gbr_bigpoly{-1, 0, nullptr, nullptr};
+    NvtxScope call("gbr_arrangement_resultants");
     gbr_resident *r = nullptr;
     int st = gbr_upload_arrangement(c, n, f, var, &r);
     if (st) return st;

@@ -10,10 +10,28 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/gbres.h"
 #include "gbr_internal.h"
 
 namespace gbr {
+
+// A host-side NVTX range for the duration of a scope (a profiler shows it on the
+// calling thread's timeline beside the kernels; without one attached each push
+// and pop costs a few nanoseconds).  next() closes the current range and opens
+// the following phase's, so early returns always leave the ranges balanced.
+class NvtxScope {
+  public:
+    explicit NvtxScope(const char *name) { nvtxRangePushA(name); }
+    void next(const char *name) {
+        nvtxRangePop();
+        nvtxRangePushA(name);
+    }
+    ~NvtxScope() { nvtxRangePop(); }
+    NvtxScope(const NvtxScope &) = delete;
+    NvtxScope &operator=(const NvtxScope &) = delete;
+};
 
 // First-fit allocator with coalescing over one device allocation (the caller's
 // workspace or the library's own cudaMalloc of the budget).  256-byte aligned.

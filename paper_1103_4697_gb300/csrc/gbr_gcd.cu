@@ -908,6 +908,7 @@ static int gcd_batch_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upo
 
 int gbr_gcd_cof_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upoly *q, gbr_bigpoly *out,
                        gbr_bigpoly *out_a, gbr_bigpoly *out_b) {
+    NvtxScope call("gbr: gcd batch");
     int st;
     const auto t0 = std::chrono::steady_clock::now();
     if (c->stats_on) cudaEventRecord(c->ev[0], c->stream);

@@ -101,6 +101,7 @@ static void parent_error(gbr_ctx *w, int st) {
 
 static void run_group(gbr_ctx *w, ServeState *S, std::vector<std::shared_ptr<ServeJob>> &grp) {
     if (grp.empty()) return;
+    NvtxScope call("gbr: serving batch");
     const int n = (int)grp.size();
     std::vector<gbr_bigpoly> out(n);
     int st;

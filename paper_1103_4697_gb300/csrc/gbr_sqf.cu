@@ -1015,6 +1015,7 @@ extern "C" int gbr_squarefree_batch(gbr_ctx *c, int n, const gbr_bigpoly *in, gb
         out[j].factors = nullptr;
     }
     if (n == 0) return GBR_OK;
+    NvtxScope call("gbr_squarefree_batch");
     std::lock_guard<std::mutex> lk(c->mu);
     cudaSetDevice(c->device);
     int st;
