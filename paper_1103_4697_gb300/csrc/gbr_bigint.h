@@ -142,6 +142,15 @@ inline void divmod_mag(const uint32_t *a, size_t na, const uint32_t *b, size_t n
         r.assign(a, a + na);
         return;
     }
+    if (na <= 4) {   // both below 2^128: one double-word division, no normalisation
+        unsigned __int128 A = 0, B = 0;
+        for (size_t i = na; i-- > 0;) A = (A << 32) | a[i];
+        for (size_t i = n; i-- > 0;) B = (B << 32) | b[i];
+        const unsigned __int128 Q = A / B, R = A - Q * B;
+        for (unsigned __int128 t = Q; t; t >>= 32) q.push_back((uint32_t)t);
+        for (unsigned __int128 t = R; t; t >>= 32) r.push_back((uint32_t)t);
+        return;
+    }
     const size_t m = na - n;
     if (n == 1) {
         q.assign(na, 0u);

@@ -24,14 +24,29 @@ static Limbs rnd(std::mt19937_64 &r, int n) {
     return a;
 }
 
+// operands of 1 to 5 limbs from boundary words (0, 1, 2^31 - 1, 2^31, all ones,
+// random): the double-word division path and both sides of its 4-limb limit
+static Limbs small(std::mt19937_64 &r) {
+    static const uint32_t words[] = {0u, 1u, 0x7FFFFFFFu, 0x80000000u, 0xFFFFFFFFu};
+    Limbs a(1 + r() % 5);
+    for (auto &x : a) x = r() % 3 ? words[r() % 5] : (uint32_t)r();
+    a.resize(top(a.data(), a.size()));
+    return a;
+}
+
 int main(int argc, char **argv) {
     const int N = argc > 1 ? std::atoi(argv[1]) : 1500;
+    const int M = argc > 2 ? std::atoi(argv[2]) : 0;   // small-operand cases after the N others
     std::mt19937_64 rng(20261203);
     Scratch S;
-    std::printf("%d\n", N);
-    for (int it = 0; it < N; ++it) {
+    std::printf("%d\n", N + M);
+    for (int it = 0; it < N + M; ++it) {
         Limbs a = rnd(rng, 1 + (int)(rng() % 40)), b = rnd(rng, 1 + (int)(rng() % 40));
-        switch (it % 5) {
+        if (it >= N) {
+            a = small(rng);
+            b = it % 7 == 0 ? a : small(rng);
+        }
+        switch (it < N ? it % 5 : -1) {
             case 1: {   // a large common factor
                 Limbs g = rnd(rng, 1 + (int)(rng() % 20));
                 if (!g.empty()) {

@@ -39,7 +39,7 @@ def _int(line):
 
 def test_bigint_division_and_gcd_match_python(tmp_path):
     exe = _build(tmp_path, "bigint_harness.cpp")
-    out = subprocess.run([exe, "1500"], check=True, capture_output=True, text=True).stdout.split("\n")
+    out = subprocess.run([exe, "1500", "2000"], check=True, capture_output=True, text=True).stdout.split("\n")
     n = int(out[0])
     i, bad = 1, []
     for case in range(n):
@@ -47,7 +47,7 @@ def test_bigint_division_and_gcd_match_python(tmp_path):
         i += 6
         if (q, r) != divmod(a, b) or g1 != math.gcd(a, b) or g2 != math.gcd(a, b):
             bad.append(case)
-    assert n == 1500 and not bad, bad[:10]
+    assert n == 3500 and not bad, bad[:10]
 
 
 def test_host_pool_visits_every_index_once(tmp_path):
