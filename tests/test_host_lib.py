@@ -252,3 +252,72 @@ def test_header_is_plain_c_and_links_from_c(lib, tmp_path):
     assert out[4] == "disc 0 2 1 2"                    # f_y = 2y: D = min(1 * 2 + 2 * 0, 2 * 1) = 2
     assert out[5] == f"bad_var {N.EINVAL}"
     assert out[6] == "strerror " + lib.gbr_strerror(N.ELIMIT).decode()
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every structure of include/gbres.h has the same size, field names, field
+    order and field offsets in the binding's ctypes classes as a C compiler
+    gives it (tests/native/struct_layout.c)."""
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if not gcc:
+        pytest.skip("gcc not available")
+    exe = str(tmp_path / "struct_layout")
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                    "-o", exe, os.path.join(ROOT, "tests", "native", "struct_layout.c")], check=True,
+                   capture_output=True, text=True)
+    lines = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = 0
+    for line in filter(None, lines):
+        name, size, *fields = line.split()
+        cls = getattr(N, name)
+        assert C.sizeof(cls) == int(size), name
+        c_fields = [(f.split(":")[0], int(f.split(":")[1])) for f in fields]
+        assert [f[0] for f in cls._fields_] == [f for f, _ in c_fields], name
+        for f, off in c_fields:
+            assert getattr(cls, f).offset == off, (name, f)
+        seen += 1
+    assert seen == 10
+
+
+_CTYPE_OF = {
+    "int": {C.c_int}, "int32_t": {C.c_int32, C.c_int}, "int64_t": {C.c_int64}, "uint64_t": {C.c_uint64},
+    "size_t": {C.c_size_t}, "double": {C.c_double}, "void": {None},
+}
+
+
+def _pointer_ok(ctype, c_decl):
+    """A C pointer parameter may be passed as c_void_p, as POINTER(...) of a matching
+    type, or (const char *) as c_char_p."""
+    if ctype in (C.c_void_p, C.c_char_p):
+        return True
+    return hasattr(ctype, "_type_") and isinstance(ctype._type_, type)
+
+
+def test_binding_signatures_match_the_header():
+    """Each prototype of include/gbres.h and the binding's ctypes declaration agree
+    on the return type, the number of arguments and each argument's kind (integer
+    width, floating point, or pointer)."""
+    text = open(os.path.join(ROOT, "include", "gbres.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    protos = re.findall(r"((?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**)\s*(gbr_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", text)
+    names = set()
+    for ret, name, params in protos:
+        names.add(name)
+        res, args = N.SIGNATURES[name]
+        ret = ret.strip()
+        if "*" in ret:
+            assert res in (C.c_char_p, C.c_void_p), name
+        else:
+            assert res in _CTYPE_OF[ret.replace("const", "").strip()], (name, ret)
+        params = [p.strip() for p in params.split(",")] if params.strip() not in ("", "void") else []
+        assert len(params) == len(args), name
+        for p, a in zip(params, args):
+            if "*" in p:
+                assert _pointer_ok(a, p), (name, p)
+            else:
+                base = re.sub(r"\b(const|unsigned)\b", "", p).split()[0]
+                assert a in _CTYPE_OF[base], (name, p, a)
+    assert names == set(N.SIGNATURES)
