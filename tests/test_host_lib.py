@@ -321,3 +321,17 @@ def test_binding_signatures_match_the_header():
                 base = re.sub(r"\b(const|unsigned)\b", "", p).split()[0]
                 assert a in _CTYPE_OF[base], (name, p, a)
     assert names == set(N.SIGNATURES)
+
+
+def test_binding_constants_match_the_header():
+    """Status codes, options and job kinds of the binding equal the header's
+    #define values (GBR_X in include/gbres.h is X in the binding)."""
+    text = open(os.path.join(ROOT, "include", "gbres.h")).read()
+    defs = dict(re.findall(r"#define\s+GBR_([A-Z0-9_]+)\s+(-?\d+)", text))
+    checked = 0
+    for name, value in defs.items():
+        if name.startswith("MAX_") or name.startswith("NOALLOC_"):
+            continue                                      # limits: not mirrored by the binding
+        assert getattr(N, name) == int(value), name
+        checked += 1
+    assert checked == 10 + 8 + 3                          # statuses, options, job kinds
