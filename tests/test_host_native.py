@@ -362,3 +362,88 @@ def test_kronecker_host_helpers(tmp_path):
                 got.append(u - (1 << (64 * W)) if u >> (64 * W - 1) else u)
             assert got == a
     assert seen["OVF"] > 0 and seen["LIMIT"] > 0
+
+
+def _table_primes(k):
+    """The k largest primes below 2^32 / 3 (the library's table starts there)."""
+    out, v = [], (2 ** 32 - 1) // 3
+    while len(out) < k:
+        if v % 2 and all(v % d for d in range(3, int(v ** 0.5) + 1, 2)):
+            out.append(v)
+        v -= 1
+    return out
+
+
+def test_elimination_routines_match_sylvester_determinants(tmp_path):
+    """The evaluation kernels' per-(prime, point) resultant, run on the CPU through
+    its host path: res_formal (every case of the formal-degree recursion) and the
+    register form res_chain<N> for N = 2..32 in all three shapes, against the
+    oracle's integer resultant reduced mod p - the Sylvester determinant with the
+    formal degrees where a leading coefficient vanishes, the subresultant sequence
+    over Z otherwise.  Cases: random residues, zero leading coefficients (one or
+    both), polynomials even in y (remainder sequences that are not normal), a
+    planted common root mod p, constants and small residues."""
+    import random
+
+    from oracle.resultant import det_bareiss, res_univariate, sylvester
+    from oracle.zpoly import ZZ
+
+    exe = _build(tmp_path, "elim_harness.cpp")
+    rng = random.Random(63)
+    primes = _table_primes(3)
+
+    def poly_mul_mod(a, b, p):
+        out = [0] * (len(a) + len(b) - 1)
+        for i, x in enumerate(a):
+            for j, y in enumerate(b):
+                out[i + j] = (out[i + j] + x * y) % p
+        return out
+
+    cases = []
+    for N in range(2, 33):
+        for m, n in ((N, N), (N, N - 1), (N - 1, N)):
+            for kind in ("rand", "rand", "even", "root"):
+                cases.append((m, n, kind))
+    for _ in range(500):
+        cases.append((rng.randint(0, 9), rng.randint(0, 9), rng.choice(["rand", "lc0", "lc00", "even", "root", "small"])))
+    lines, want = [], []
+    for m, n, kind in cases:
+        p = rng.choice(primes)
+        pick = (lambda: rng.choice([0, 1, 2, p - 1])) if kind == "small" else (lambda: rng.randrange(p))
+        f = [pick() for _ in range(m + 1)]
+        g = [pick() for _ in range(n + 1)]
+        if kind == "even":                               # only even powers of y
+            f = [c if k % 2 == 0 else 0 for k, c in enumerate(f)]
+            g = [c if k % 2 == 0 else 0 for k, c in enumerate(g)]
+        if kind == "root" and m >= 1 and n >= 1:         # a common root r mod p: the resultant is 0
+            r = rng.randrange(p)
+            f = poly_mul_mod([(p - r) % p, 1], [rng.randrange(p) for _ in range(m)], p)
+            g = poly_mul_mod([(p - r) % p, 1], [rng.randrange(p) for _ in range(n)], p)
+        if kind == "lc0":
+            f[-1] = 0
+        if kind == "lc00":
+            f[-1] = 0
+            g[-1] = 0
+        if f[-1] and g[-1]:
+            v = res_univariate(list(f), list(g), ZZ) if m and n else (g[0] ** m if not n else f[0] ** n)
+        else:
+            v = det_bareiss(sylvester(list(f), list(g), ZZ), ZZ)
+        want.append(v % p)
+        lines.append(" ".join(map(str, [p, m, n] + f + g)))
+    out = subprocess.run([exe], input="\n".join(lines) + "\n", check=True, capture_output=True, text=True).stdout
+    got = [tuple(int(t) for t in l.split()) for l in out.splitlines()]
+    assert len(got) == len(cases)
+    reg_ok = reg_total = 0
+    for (m, n, kind), w, (formal, ok, chain) in zip(cases, want, got):
+        assert formal == w, (m, n, kind)
+        N = max(m, n)
+        if 2 <= N <= 32 and {m, n} <= {N, N - 1}:
+            reg_total += 1
+            if ok:
+                reg_ok += 1
+                assert chain == w, (m, n, kind)
+            else:
+                # the register form declines only where a leading coefficient
+                # vanishes or the sequence is not normal (the kernel's redo pass)
+                assert kind in ("even", "lc0", "lc00", "small", "root") or w == 0, (m, n, kind)
+    assert reg_ok > reg_total // 2
