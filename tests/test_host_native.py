@@ -447,3 +447,55 @@ def test_elimination_routines_match_sylvester_determinants(tmp_path):
                 # vanishes or the sequence is not normal (the kernel's redo pass)
                 assert kind in ("even", "lc0", "lc00", "small", "root") or w == 0, (m, n, kind)
     assert reg_ok > reg_total // 2
+
+
+def test_montgomery_arithmetic_at_the_range_ends(tmp_path):
+    """The kernels' Montgomery arithmetic (host paths of gbr_modarith.cuh) for the
+    table's largest primes: products, the fused two- and three-product forms with
+    residues up to p (the sum stays below p 2^32 only because p < 2^32 / 3),
+    conversions, powers, inverses and multi-word two's-complement reduction
+    (including -2^511 and all-ones words), against Python's modular integers."""
+    import random
+
+    exe = _build(tmp_path, "modarith_harness.cpp")
+    rng = random.Random(64)
+    lines, want = [], []
+    for p in _table_primes(2) + [(1 << 30) + 3]:           # the largest table primes and one near 2^30
+        Ri = pow(1 << 32, -1, p)
+        ends = [0, 1, p - 1, p - 2, p // 2]
+
+        def r(upto=p - 1):
+            return rng.choice(ends + [upto]) if rng.random() < 0.5 else rng.randint(0, upto)
+
+        for _ in range(150):
+            a, b = r(), r()
+            lines.append(f"mul {p} {a} {b}"); want.append(a * b * Ri % p)
+            a, x, b, y = r(), r(), r(), r()
+            lines.append(f"mulsub {p} {a} {x} {b} {y}"); want.append((a * x - b * y) * Ri % p)
+            a, x, b, y = r(p), r(p), r(p), r(p)
+            lines.append(f"fma2 {p} {a} {x} {b} {y}"); want.append((a * x + b * y) * Ri % p)
+            a, x, b, y, c, z = r(p), r(p), r(p), r(p), r(p), r(p)
+            lines.append(f"fma3 {p} {a} {x} {b} {y} {c} {z}"); want.append((a * x + b * y + c * z) * Ri % p)
+            v = rng.choice([0, 1, (1 << 32) - 1, rng.getrandbits(32)])
+            lines.append(f"to {p} {v}"); want.append(v * (1 << 32) % p)
+            lines.append(f"from {p} {r()}"); want.append(None)
+            xx, e = r(), rng.randint(0, 70)
+            lines.append(f"pow {p} {xx} {e}"); want.append(pow(xx, e, p))
+            if xx:
+                lines.append(f"inv {p} {xx}"); want.append(pow(xx, -1, p))
+            W = rng.randint(1, 8)
+            v = rng.choice([-(1 << (64 * W - 1)), (1 << (64 * W - 1)) - 1, -1, 0, rng.getrandbits(64 * W - 1),
+                            -rng.getrandbits(64 * W - 1)])
+            u = v % (1 << (64 * W))
+            words = [(u >> (64 * i)) & ((1 << 64) - 1) for i in range(W)]
+            lines.append(f"words {p} {W} " + " ".join(map(str, words))); want.append(v % p)
+    out = subprocess.run([exe], input="\n".join(lines) + "\n", check=True, capture_output=True, text=True).stdout.split()
+    assert len(out) == len(lines)
+    for line, w, g in zip(lines, want, out):
+        g = int(g)
+        assert 0 <= g < int(line.split()[1]), line
+        if line.startswith("from"):
+            p, xv = (int(t) for t in line.split()[1:3])
+            assert g * (1 << 32) % p == xv % p, line        # from inverts the Montgomery map
+        else:
+            assert g == w, line
