@@ -499,3 +499,35 @@ def test_montgomery_arithmetic_at_the_range_ends(tmp_path):
             assert g * (1 << 32) % p == xv % p, line        # from inverts the Montgomery map
         else:
             assert g == w, line
+
+
+def test_routing_helpers(tmp_path):
+    """reg_shape sends exactly the shapes (N, N), (N, N-1), (N-1, N) with 2 <= N <= 32
+    to the register form; the symmetric points run 0, +1, -1, +2, -2, ... (the
+    unit grid otherwise); the even and odd interpolation matrices use the points
+    j^2 and (j + 1)^2; rows4 pads m + 1 rows to a multiple of 4."""
+    nvcc = shutil.which("nvcc")
+    cuda = os.environ.get("CUDA_HOME") or (os.path.dirname(os.path.dirname(nvcc)) if nvcc else "")
+    inc = os.path.join(cuda, "include")
+    if not os.path.exists(os.path.join(inc, "cuda_runtime.h")):
+        pytest.skip("CUDA headers not found")
+    exe = _build(tmp_path, "routing_harness.cpp", ["-I", inc])
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.splitlines()
+    seen = {"reg": 0, "pt": 0, "rows4": 0}
+    for line in out:
+        t = line.split()
+        seen[t[0]] += 1
+        v = [int(x) for x in t[1:]]
+        if t[0] == "reg":
+            m, n, N = v
+            top = max(m, n)
+            want = top if 2 <= top <= 32 and min(m, n) >= top - 1 else 0
+            assert N == want, line
+        elif t[0] == "pt":
+            j, grid, sym, vsym, even, odd = v
+            s = 0 if j == 0 else ((j + 1) // 2 if j % 2 else -(j // 2))
+            assert (grid, sym, vsym, even, odd) == (j, s, s, j * j, (j + 1) ** 2), line
+        else:
+            m, r = v
+            assert r % 4 == 0 and m + 1 <= r < m + 5, line
+    assert seen == {"reg": 41 * 41, "pt": 64, "rows4": 131}
