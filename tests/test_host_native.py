@@ -531,3 +531,44 @@ def test_routing_helpers(tmp_path):
             m, r = v
             assert r % 4 == 0 and m + 1 <= r < m + 5, line
     assert seen == {"reg": 41 * 41, "pt": 64, "rows4": 131}
+
+
+def test_host_constant_tables(tmp_path):
+    """The host-built tables every Chinese remaindering and Newton interpolation
+    launch reads: the table primes (the largest primes below 2^32 / 3, in
+    descending order) with pinv = -p^-1 mod 2^32, r1 = 2^32 mod p, r2 = 2^64 mod p;
+    the Garner prefix table ((p_0 ... p_{i-1})^-1 and p_j mod p_i, Montgomery form);
+    the inverse table (1/t mod p_i, Montgomery form), against their definitions."""
+    if not os.path.exists(N.LIB_PATH):
+        from paper_1103_4697_gb300.build import build
+        build()
+    nvcc = shutil.which("nvcc")
+    cuda = os.environ.get("CUDA_HOME") or (os.path.dirname(os.path.dirname(nvcc)) if nvcc else "")
+    inc = os.path.join(cuda, "include")
+    if not os.path.exists(os.path.join(inc, "cuda_runtime.h")):
+        pytest.skip("CUDA headers not found")
+    libdir = os.path.dirname(N.LIB_PATH)
+    exe = _build(tmp_path, "tables_harness.cpp", ["-I", inc, "-L", libdir, "-lgbres", "-Wl,-rpath," + libdir])
+    K, T = 40, 300
+    out = subprocess.run([exe, str(K), str(T)], check=True, capture_output=True, text=True).stdout.split("\n")
+    assert int(out[0]) == 2048
+    mods = [tuple(int(v) for v in out[1 + i].split()) for i in range(K)]
+    ps = [m[0] for m in mods]
+    assert ps == _table_primes(K)
+    R = 1 << 32
+    for p, pinv, r1, r2 in mods:
+        assert (p * pinv) % R == R - 1 and r1 == R % p and r2 == (R * R) % p
+    g = [int(v) for v in out[1 + K].split()]
+    assert len(g) == K + K * (K - 1) // 2
+    for i, p in enumerate(ps):
+        prod = 1
+        for j in range(i):
+            assert g[K + i * (i - 1) // 2 + j] == ps[j] % p * R % p
+            prod = prod * ps[j] % p
+        assert g[i] == pow(prod, -1, p) * R % p
+    inv = [int(v) for v in out[2 + K].split()]
+    assert len(inv) == K * T
+    for i, p in enumerate(ps):
+        assert inv[i * T] == 0
+        for t in range(1, T):
+            assert inv[i * T + t] == pow(t, -1, p) * R % p
