@@ -281,10 +281,10 @@ size_t gbr::prime_table_bytes() {
     return (size_t)num_primes() * (sizeof(ModP) + sizeof(uint2)) + (size_t)kCrtTabWords * 4;
 }
 
-cudaError_t gbr::upload_prime_table(ModP *d) {
+void gbr::build_prime_table(std::vector<char> &buf) {
     const int NP = num_primes();
     const ModP *hm = host_mods();
-    std::vector<char> buf(prime_table_bytes());
+    buf.assign(prime_table_bytes(), 0);
     std::memcpy(buf.data(), hm, sizeof(ModP) * NP);
     uint2 *r34 = (uint2 *)(buf.data() + sizeof(ModP) * NP);
     for (int i = 0; i < NP; ++i) {
@@ -323,6 +323,11 @@ cudaError_t gbr::upload_prime_table(ModP *d) {
         while (i <= KF && T[(size_t)l * kCrtFastRow + i] == 0u) ++i;
         I0[l] = (uint32_t)(i & ~3);
     }
+}
+
+cudaError_t gbr::upload_prime_table(ModP *d) {
+    std::vector<char> buf;
+    build_prime_table(buf);
     return cudaMemcpy(d, buf.data(), buf.size(), cudaMemcpyHostToDevice);
 }
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/gbres.h"
 #include "gbr_modarith.cuh"
@@ -15,6 +16,8 @@ namespace gbr {
 int num_primes();
 const ModP *host_mods();              // ModP for every table prime, p_0 > p_1 > ...
 size_t prime_table_bytes();             // device prime table: ModP[num_primes()], uint2 (R^3, R^4)[num_primes()],
+// the device prime table's bytes, built on the host (layout of prime_table_bytes)
+void build_prime_table(std::vector<char> &buf);
 cudaError_t upload_prime_table(ModP *d);  // then the CRT tables of the first kCrtFastK primes
 const uint2 *prime_r34(const ModP *d);
 const uint32_t *prime_crt_tables(const ModP *d);

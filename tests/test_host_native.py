@@ -572,3 +572,59 @@ def test_host_constant_tables(tmp_path):
         assert inv[i * T] == 0
         for t in range(1, T):
             assert inv[i * T + t] == pow(t, -1, p) * R % p
+
+
+def test_device_prime_table_bytes(tmp_path):
+    """The device prime table as the host builds it: (R^3, R^4) mod p per prime, and
+    the Chinese-remaindering tables of the first 64 primes that the fast path
+    reads - Garner row i at crt_gd_off(i) holds (-prod_{l<j} p_l) R mod p_i for
+    j < i and zeros in its padding; limb l of prod_{j<i} p_j for i <= 64; the first
+    non-zero column of each limb row, rounded down to a multiple of 4."""
+    if not os.path.exists(N.LIB_PATH):
+        from paper_1103_4697_gb300.build import build
+        build()
+    nvcc = shutil.which("nvcc")
+    cuda = os.environ.get("CUDA_HOME") or (os.path.dirname(os.path.dirname(nvcc)) if nvcc else "")
+    inc = os.path.join(cuda, "include")
+    if not os.path.exists(os.path.join(inc, "cuda_runtime.h")):
+        pytest.skip("CUDA headers not found")
+    libdir = os.path.dirname(N.LIB_PATH)
+    exe = _build(tmp_path, "prime_table_harness.cpp", ["-I", inc, "-L", libdir, "-lgbres", "-Wl,-rpath," + libdir])
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
+    NP, size = (int(v) for v in out[0].split())
+    K, ROW, L = 64, 68, 62
+    R = 1 << 32
+    ps = []
+    for i in range(K):
+        p, r3, r4 = (int(v) for v in out[1 + i].split())
+        assert r3 == pow(R, 3, p) and r4 == pow(R, 4, p)
+        ps.append(p)
+    assert ps == _table_primes(K)
+
+    def gd_off(i):
+        if i <= 0:
+            return 0
+        q, r = (i - 1) // 4, (i - 1) % 4
+        return 8 * q * (q + 1) + 4 * r * (q + 1)
+
+    gd = [int(v) for v in out[1 + K].split()]
+    assert len(gd) == gd_off(K)
+    expect = [0] * gd_off(K)
+    for i in range(1, K):
+        C = 1
+        for j in range(i):
+            expect[gd_off(i) + j] = (-C) % ps[i] * R % ps[i]
+            C = C * ps[j] % ps[i]
+    assert gd == expect
+    T = [[int(v) for v in out[2 + K + l].split()] for l in range(L)]
+    prod = 1
+    for i in range(K + 1):
+        for l in range(L):
+            assert T[l][i] == (prod >> (32 * l)) & (R - 1), (l, i)
+        if i < K:
+            prod *= ps[i]
+    I0 = [int(v) for v in out[2 + K + L].split()]
+    for l in range(L):
+        first = next((i for i in range(K + 1) if T[l][i]), K + 1)    # a row of zeros: past the end
+        assert I0[l] == first & ~3
+    assert size == NP * (16 + 8) + (gd_off(K) + L * ROW + L) * 4
