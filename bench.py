@@ -231,14 +231,18 @@ def serving_run(ctx, n_burst: int = 1500, n_stream: int = 6000, load: float = 0.
 # --------------------------------------------------------------------------- our arm
 
 
-def traffic_for(kernel_src: str) -> float | None:
+def traffic_for() -> float | None:
     """Per-launch DRAM bytes of the evaluation kernel from the committed ncu summary,
-    if that summary was taken on the current kernel source."""
+    if that summary describes the current kernel source (the hash of its source
+    files, in the order the summary lists them)."""
     path = os.path.join(ROOT, "profiles", "evalres_dram.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
-    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    files = d.get("source_files") or []
+    if not files or not all(os.path.exists(os.path.join(ROOT, f)) for f in files):
+        return None
+    h = hashlib.sha256(b"".join(open(os.path.join(ROOT, f), "rb").read() for f in files)).hexdigest()[:16]
     return d.get("bytes_per_launch_full") if d.get("source_sha") == h else None
 
 
@@ -350,7 +354,6 @@ def run_ours(args) -> None:
     ctx.close()
     if rank != 0:
         return
-    kernel_src = os.path.join(ROOT, "paper_1103_4697_gb300", "csrc", "gbr_evalres.cu")
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -361,7 +364,7 @@ def run_ours(args) -> None:
                    "(256 MiB write)", "parallelism": "replicas" if world > 1 else "single GPU"},
         "clocks": clk, "e2e": e2e, "gpu_launches": kernels,
         "roofline": {"bound": "alu", "kernel": "k_evalres_reg<20> (+ k_evalres_redo)", "achieved": achieved / 1e12, "peak": peak / 1e12,
-                     "unit": "Tmodmul/s", "frac": achieved / peak, "traffic": traffic_for(kernel_src),
+                     "unit": "Tmodmul/s", "frac": achieved / peak, "traffic": traffic_for(),
                      "peak_source": "measured on this GPU by gbr_calibrate: best of modmul, 2 x fused mulsub, "
                                     "3 x fused 3-product rate (modular products per second)",
                      "algorithmic_modmul_per_launch": modmul},

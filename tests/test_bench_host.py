@@ -101,3 +101,22 @@ def test_reference_arm_line_and_other_ranks():
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
     assert "workload" in line["config"]
+
+
+def test_traffic_figure_tracks_the_kernel_source(tmp_path, monkeypatch):
+    """bench.py reports the committed ncu traffic of the evaluation kernel only while
+    the hash of its source files matches the summary's; any edit of either file
+    drops it to null."""
+    import shutil
+
+    assert bench.traffic_for() is not None                      # the committed summary matches the sources
+    root = tmp_path / "r"
+    for rel in ("profiles/evalres_dram.json", "paper_1103_4697_gb300/csrc/gbr_evalres.cu",
+                "paper_1103_4697_gb300/csrc/gbr_elim.cuh"):
+        (root / rel).parent.mkdir(parents=True, exist_ok=True)
+        shutil.copy(os.path.join(bench.ROOT, rel), root / rel)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench.traffic_for() is not None
+    with open(root / "paper_1103_4697_gb300/csrc/gbr_elim.cuh", "a") as fh:
+        fh.write("\n")
+    assert bench.traffic_for() is None
