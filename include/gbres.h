@@ -363,18 +363,22 @@ int gbr_get_serve_stats(gbr_ctx *ctx, gbr_serve_stats *out);
 
 /* Measured arithmetic ceilings of this GPU for the library's own Montgomery
  * arithmetic (integer pipes), used as the roofline denominators of the
- * evaluation, elimination and interpolation stages: independent chains of one
- * Montgomery multiplication, of the fused two-product multiply-subtract and of
- * the fused three-product reduction, timed with CUDA events on the context's
- * stream.  Results in operations per second (an operation of the fused kinds
- * does two or three modular products); sm_clock_mhz is the clock the driver
- * reports for the device (cudaDevAttrClockRate). */
+ * evaluation, elimination and interpolation stages: independent chains (each
+ * reads only its own value and fixed multipliers; best of 4, 8 and 16 chains
+ * per thread) of one Montgomery multiplication, of the fused two-product
+ * multiply-subtract, of the fused three-product reduction and of one Horner
+ * step with a fixed multiplier in Shoup's form (the evaluation's step, no
+ * reduction), timed with CUDA events on the context's stream.  Results in
+ * operations per second (an operation of the fused kinds does two or three
+ * modular products); sm_clock_mhz is the clock the driver reports for the
+ * device (cudaDevAttrClockRate). */
 typedef struct {
     double modmul_per_s;
     double mulsub_per_s;
     double sm_clock_mhz;
     int32_t sms;
     double fma3_per_s;
+    double shoup_per_s;
 } gbr_calib;
 int gbr_calibrate(gbr_ctx *ctx, gbr_calib *out);
 
@@ -408,7 +412,10 @@ int gbr_calibrate(gbr_ctx *ctx, gbr_calib *out);
  * Behaviour: asynchronous on `stream` (NULL: the legacy default stream);
  * results are ready when the stream reaches that point.  The first call on a
  * device, with that device current, looks up the device address of the fixed
- * array (cudaGetSymbolAddress); make that first call before any stream
+ * array (cudaGetSymbolAddress).  CUDA loads a library's device code lazily by
+ * default, so that first call is also when the 4 MiB array is mapped on the
+ * device: make it before the caller reserves the rest of its device memory
+ * (a device with no room left then gets GBR_EDEVICE) and before any stream
  * capture begins.  Every call uses the same fixed array and leaves its last
  * contents there; calls whose kernels overlap on the GPU (other streams, other
  * host threads) overwrite each other's digits and give wrong results, so

@@ -1689,6 +1689,8 @@ int gbr_run_resident_finish(gbr_ctx *c, gbr_resident *r) {
         e = cudaMemcpyAsync(hredo.data(), r->d_redo, 8 * (size_t)r->pend_nredo, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "resultant stages", e);
+    if (herr[0] == kErrTensorStall)
+        return c->fail(GBR_EDEVICE, "tensor-core interpolation stalled (a bounded wait gave up; no results written)");
     if (herr[0]) return c->fail(GBR_EDEVICE, "device-side consistency check failed");
     st.dropped_points = (int64_t)((uint64_t)(uint32_t)herr[2] | ((uint64_t)(uint32_t)herr[3] << 32));
     st.redo_warps = 0;

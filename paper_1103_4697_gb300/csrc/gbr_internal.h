@@ -12,6 +12,12 @@
 
 namespace gbr {
 
+// Codes the resultant kernels leave in the context's device error word (the
+// call then returns GBR_EDEVICE with the matching message).
+constexpr int kErrCrtLimbs = 2;       // a lifted coefficient needed more limbs than planned
+constexpr int kErrSpareShort = 5;     // drop mode ran out of spare points
+constexpr int kErrTensorStall = 6;    // a tensor-core wait gave up (interpolation skipped its results)
+
 // ------------------------------------------------------------------ prime table (host)
 int num_primes();
 const ModP *host_mods();              // ModP for every table prime, p_0 > p_1 > ...

@@ -66,6 +66,10 @@ __host__ __device__ constexpr uint32_t tc_idesc() {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
 }
 
+// Bounded wait on an mbarrier phase.  Every barrier here completes through this
+// CTA's own tcgen05.commit, so a wait that gives up means the tensor cores have
+// stalled: the caller then stops issuing work, skips every read of the
+// accumulators and every result write, and reports the stall in the error word.
 __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
     uint32_t done = 0;
     for (int it = 0; it < (1 << 24) && !done; ++it)
@@ -143,7 +147,7 @@ __global__ void __launch_bounds__(256, 1) k_interp_tc(ResLaunch L, const char *p
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tbase = tmem_slot;
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(tsm);
-    bool ok = true;
+    bool stalled = false;   // CTA-uniform: a stage wait gave up, no further chunk is issued
     // software pipeline: the loads of chunk kc + 1 (operand rows: 32 per warp,
     // lanes along K; the 16 KB matrix block) are in flight while chunk kc is
     // split into digits and multiplied
@@ -177,18 +181,24 @@ __global__ void __launch_bounds__(256, 1) k_interp_tc(ResLaunch L, const char *p
     for (int kc = 0; kc < nkc; ++kc) {
         const int s = kc & 1;
         unsigned char *st = tsm + s * TC_STAGE;
-        if (kc >= 2 && !tc_wait((uint32_t)__cvta_generic_to_shared(&bar[s]), ((kc >> 1) - 1) & 1)) ok = false;
-        // the loaded chunk: operand (sums / differences, below p) into raw rows
-        // (pitch 33 words), the matrix block into the stage
+        // stage s is free once the MMAs of chunk kc - 2 have read it
+        const bool late = kc >= 2 && !tc_wait((uint32_t)__cvta_generic_to_shared(&bar[s]), ((kc >> 1) - 1) & 1);
+        // the loaded chunk's operand (sums / differences, below p) into raw rows
+        // (pitch 33 words, not read by the tensor cores)
 #pragma unroll
         for (int it = 0; it < TC_M / 8; ++it)
             raw[(warp + 8 * it) * 33 + lane] = mode == GEMM_ODD ? mp_sub(ra[it], rc[it], M.p) : mp_add(ra[it], rc[it], M.p);
+        // a wait that gave up on any thread ends the loop on all of them before
+        // anything is written into a stage an MMA may still be reading
+        if (__syncthreads_or(late)) {
+            stalled = true;
+            break;
+        }
         {
             uint4 *dst = reinterpret_cast<uint4 *>(st + 4 * TC_XPLANE);
 #pragma unroll
             for (int u = 0; u < 4 * TC_VPLANE / 16 / 256; ++u) dst[tid + 256 * u] = rv[u];
         }
-        __syncthreads();
         if (kc + 1 < nkc) preload(kc + 1);
         // each thread splits two K groups of its row into four digit planes
         {
@@ -233,17 +243,20 @@ __global__ void __launch_bounds__(256, 1) k_interp_tc(ResLaunch L, const char *p
                     }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 (uint32_t)__cvta_generic_to_shared(&bar[s])));
-            if (kc == nkc - 1)
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    (uint32_t)__cvta_generic_to_shared(&bar[2])));
         }
     }
-    if (!tc_wait((uint32_t)__cvta_generic_to_shared(&bar[2]), 0)) ok = false;
+    // one more commit tracks every MMA issued (after the last chunk, or after a
+    // stall); the accumulators are read only when all of them have completed
+    if (tid == 0)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            (uint32_t)__cvta_generic_to_shared(&bar[2])));
+    const bool drained = __syncthreads_and(tc_wait((uint32_t)__cvta_generic_to_shared(&bar[2]), 0)) != 0;
+    const bool ok = drained && !stalled;
     asm volatile("tcgen05.fence::after_thread_sync;");
     // epilogue: lane tid holds pair q0 + tid; combine the diagonals per coefficient
     const int ostride = mode == GEMM_PLAIN ? 1 : 2, ooff = mode == GEMM_ODD ? 1 : 0;
     const uint64_t off_lo = (uint64_t)M.p << 20, off_hi = (uint64_t)M.p << 11;
-    for (int c0 = half * (TC_N / 2); c0 < (half + 1) * (TC_N / 2); c0 += 8) {
+    for (int c0 = half * (TC_N / 2); ok && c0 < (half + 1) * (TC_N / 2); c0 += 8) {
         uint32_t v[TC_DIAG][8];
 #pragma unroll
         for (int u = 0; u < TC_DIAG; ++u) {
@@ -254,7 +267,7 @@ __global__ void __launch_bounds__(256, 1) k_interp_tc(ResLaunch L, const char *p
                          : "r"(addr));
         }
         asm volatile("tcgen05.wait::ld.sync.aligned;");
-        if (vb < 0 || !ok) continue;
+        if (vb < 0) continue;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const int r = T.c0 + c0 + e;
@@ -272,7 +285,7 @@ __global__ void __launch_bounds__(256, 1) k_interp_tc(ResLaunch L, const char *p
             L.cf[cb + (int64_t)r * ostride + ooff] = mp_add(rh, rl, M.p);
         }
     }
-    if (!ok && tid == 0) atomicExch(L.err, 6);
+    if (!ok && tid == 0) atomicExch(L.err, kErrTensorStall);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512));

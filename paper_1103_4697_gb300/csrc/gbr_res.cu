@@ -520,7 +520,7 @@ __global__ void k_interp(ResLaunch L, WorkList w, int maxP) {
                 }
                 cnt += __popc(bal);
             }
-            if (cnt < Pn && lane == 0) atomicExch(L.err, 5);
+            if (cnt < Pn && lane == 0) atomicExch(L.err, kErrSpareShort);
         }
         for (int t = lane; t < Pn; t += 32) Wp[t] = 0;
         __syncwarp();
@@ -802,7 +802,7 @@ __global__ void k_crt(ResLaunch L, WorkList w, int KM, int LM) {
                 if (++limb[l * BS] != 0u) break;
             if (l == nl && nl < LM) limb[(nl++) * BS] = 1u;
         }
-        if (nl > P.L) atomicExch(L.err, 2);
+        if (nl > P.L) atomicExch(L.err, kErrCrtLimbs);
         uint32_t *o = L.out + P.out_off + (int64_t)c * P.L;
         for (int l = 0; l < P.L; ++l) o[l] = l < nl ? limb[l * BS] : 0u;
         L.sign[P.sign_off + c] = nl == 0 ? 0 : (neg ? -1 : 1);

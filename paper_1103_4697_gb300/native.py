@@ -49,7 +49,7 @@ class Stats(C.Structure):
 
 class Calib(C.Structure):
     _fields_ = [("modmul_per_s", C.c_double), ("mulsub_per_s", C.c_double), ("sm_clock_mhz", C.c_double),
-                ("sms", C.c_int32), ("fma3_per_s", C.c_double)]
+                ("sms", C.c_int32), ("fma3_per_s", C.c_double), ("shoup_per_s", C.c_double)]
 
 
 class ResInfo(C.Structure):

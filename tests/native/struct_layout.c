@@ -24,7 +24,8 @@ int main(void) {
     F(gbr_stats, d2h_bytes); F(gbr_stats, dropped_points); F(gbr_stats, dropped_primes); F(gbr_stats, graph_replayed);
     F(gbr_stats, redo_warps); printf("\n");
     printf("Calib %zu", sizeof(gbr_calib)); F(gbr_calib, modmul_per_s); F(gbr_calib, mulsub_per_s);
-    F(gbr_calib, sm_clock_mhz); F(gbr_calib, sms); F(gbr_calib, fma3_per_s); printf("\n");
+    F(gbr_calib, sm_clock_mhz); F(gbr_calib, sms); F(gbr_calib, fma3_per_s);
+    F(gbr_calib, shoup_per_s); printf("\n");
     printf("ResInfo %zu", sizeof(gbr_res_info)); F(gbr_res_info, m); F(gbr_res_info, n); F(gbr_res_info, deg_bound);
     F(gbr_res_info, primes); F(gbr_res_info, limbs); F(gbr_res_info, log2_bound); printf("\n");
     printf("Job %zu", sizeof(gbr_job)); F(gbr_job, kind); F(gbr_job, var); F(gbr_job, f); F(gbr_job, g); F(gbr_job, p);

@@ -20,8 +20,9 @@ from paper_1103_4697_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def _noalloc(values, k, limbs):
-    """Residues of `values` modulo the first k table primes -> gbr_crt_noalloc -> ints."""
+def _noalloc(values, k, limbs, pad=0):
+    """Residues of `values` modulo the first k table primes -> gbr_crt_noalloc -> ints
+    (rows of the residue array `pad` words longer than the coefficient count)."""
     import torch
 
     from paper_1103_4697_gb300 import native as N
@@ -29,12 +30,16 @@ def _noalloc(values, k, limbs):
 
     ps = primes(k)
     n = len(values)
-    res = np.array([[v % p for v in values] for p in ps], dtype=np.uint32)
-    d_res = torch.from_numpy(res.view(np.int32)).cuda()
+    stride = n + pad
+    res = np.zeros((k, stride), dtype=np.uint32)
+    for i, p in enumerate(ps):
+        res[i, :n] = [v % p for v in values]
+        res[i, n:] = 0xFFFFFFFF                      # not a residue: must never be read
+    d_res = torch.from_numpy(res.reshape(-1).view(np.int32)).cuda()
     d_mag = torch.full((n * limbs,), -1, dtype=torch.int32, device="cuda")   # stale contents on purpose
     d_sign = torch.full((n,), 7, dtype=torch.int8, device="cuda")
     stream = torch.cuda.current_stream()
-    st = N.lib().gbr_crt_noalloc(C.c_void_p(d_res.data_ptr()), k, n, n, C.c_void_p(d_mag.data_ptr()), limbs,
+    st = N.lib().gbr_crt_noalloc(C.c_void_p(d_res.data_ptr()), k, n, stride, C.c_void_p(d_mag.data_ptr()), limbs,
                                  C.c_void_p(d_sign.data_ptr()), C.c_void_p(stream.cuda_stream))
     assert st == N.OK
     stream.synchronize()
@@ -59,6 +64,31 @@ def test_noalloc_crt_matches_resultant_entry_point():
     # two calls in a row on the same stream; the second sees the first's digits
     assert _noalloc(r1, i1["primes"], i1["limbs"]) == r1
     assert _noalloc(r2, i2["primes"], i2["limbs"]) == r2
+
+
+def test_noalloc_crt_at_its_limits():
+    """k = 64 primes and 16 384 coefficients fill the fixed array exactly; the row
+    stride is above the coefficient count; values include the ends of the symmetric
+    range (0, +-1, +-(M-1)/2, where the digit comparison and the +1 carry of negative
+    values decide), checked against Python integers on two calls in a row."""
+    import random
+
+    from paper_1103_4697_gb300.api import primes
+
+    k, n = 64, 16384
+    M = 1
+    for p in primes(k):
+        M *= p
+    h = (M - 1) // 2
+    rng = random.Random(64)
+    edge = [0, 1, -1, h, -h, h - 1, -(h - 1), 2, -2]
+    vals = edge + [rng.randrange(-h, h + 1) for _ in range(n - len(edge) - 64)]
+    vals += [rng.randrange(-2 ** rng.randrange(1, 1900), 2 ** rng.randrange(1, 1900)) for _ in range(64)]
+    assert len(vals) == n and all(-h <= v <= h for v in vals)
+    limbs = 64
+    assert _noalloc(vals, k, limbs, pad=37) == vals
+    rev = vals[::-1]
+    assert _noalloc(rev, k, limbs, pad=5) == rev
 
 
 def test_noalloc_rejects_sizes_beyond_its_array():
