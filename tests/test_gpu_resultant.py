@@ -161,37 +161,76 @@ def test_conic_curves_full(ctx):
     assert d == list(O.disc_res(f, "evalz"))
 
 
-def test_deg20_batch_sampled(ctx):
-    """The 4096-pair degree-20 batch in the launch configuration the benchmark
-    times: sampled pairs checked coefficient by coefficient and at random points."""
+@pytest.fixture(scope="module")
+def opool():
+    """Oracle workers on every host core (spawn: safe after CUDA initialisation)."""
+    import oracle_tasks as T
+
+    p = T.pool()
+    yield p
+    p.terminate()
+
+
+def _wide_points(rng, n=2):
+    return [rng.randint(-2 ** 31, 2 ** 31) for _ in range(n)]
+
+
+def _check_every_pair_at_points(opool, fs, gs, out, rng, skip=()):
+    """Every pair's result at two random 32-bit points against the oracle's exact R(a):
+    a wrong polynomial of degree <= D agrees at a random point with probability at
+    most D / 2^32."""
+    import oracle_tasks as T
+
+    idx = [q for q in range(len(out)) if q not in skip]
+    pts = {q: _wide_points(rng) for q in idx}
+    want = opool.map(T.res_points, [(fs[q], gs[q], pts[q]) for q in idx], chunksize=32)
+    for q, w in zip(idx, want):
+        got = [_poly_eval(out[q], a) for a in pts[q]]
+        assert got == w, f"pair {q} differs from the oracle at x = {pts[q]}"
+
+
+def test_deg20_batch_every_pair(ctx, opool):
+    """The 4096-pair degree-20 batch in the launch configuration the benchmark times:
+    every pair at two random points against the oracle, 16 pairs coefficient by
+    coefficient."""
+    import oracle_tasks as T
+
     F, G = W.deg20_batch_arrays(4096)
     res = ctx.upload_pairs(F, G)
     res.run()
     out = res.fetch()
-    rng = random.Random(11)
-    for q in rng.sample(range(4096), 2):
-        assert out[q] == list(O.res_evalz(F[q], G[q]))
-    for q in rng.sample(range(4096), 48):
-        for a in (rng.randint(-10 ** 6, 10 ** 6), rng.randint(-10 ** 6, 10 ** 6)):
-            assert _poly_eval(out[q], a) == O.res_at_prs(F[q], G[q], a)
     res.free()
+    rng = random.Random(11)
+    full = rng.sample(range(4096), 16)
+    want = opool.map(T.res_full, [(F[q], G[q]) for q in full], chunksize=1)
+    for q, w in zip(full, want):
+        assert out[q] == w, f"pair {q}"
+    _check_every_pair_at_points(opool, F, G, out, rng)
 
 
-def test_mixed_batch_sampled(ctx):
-    """Heterogeneous batch (degrees 4..16 per variable, 8..32-bit coefficients,
-    a quarter with planted common factors)."""
-    ps = W.mixed_batch(3, 512)
-    out = ctx.resultant_batch(ps.f, ps.g)
+def test_mixed_batch_every_pair(ctx, opool):
+    """The heterogeneous batch at its full size (4096 pairs, degrees 4..16 per variable,
+    8..32-bit coefficients, a quarter with planted common factors), as one resident
+    batch: every planted pair gives 0, every other pair is checked at two random
+    points, 16 of them coefficient by coefficient."""
+    import oracle_tasks as T
+
+    ps = W.mixed_batch(3, 4096)
+    res = ctx.upload_pairs(ps.f, ps.g)
+    res.run()
+    out = res.fetch()
+    res.free()
+    planted = {q for q, p in enumerate(ps.planted) if p}
+    assert len(planted) > 900
+    for q in planted:
+        assert out[q] == [], f"planted pair {q}"
     rng = random.Random(5)
-    for q, planted in enumerate(ps.planted):
-        if planted:
-            assert out[q] == []
-    for q in rng.sample(range(512), 24):
-        for a in (rng.randint(-10 ** 5, 10 ** 5),):
-            assert _poly_eval(out[q], a) == O.res_at_prs(ps.f[q], ps.g[q], a)
-    small = [q for q in range(512) if not ps.planted[q] and len(ps.f[q]) <= 8 and len(ps.f[q][0]) <= 8]
-    for q in small[:3]:
-        assert out[q] == list(O.res_evalz(ps.f[q], ps.g[q]))
+    others = [q for q in range(4096) if q not in planted]
+    full = rng.sample(others, 16)
+    want = opool.map(T.res_full, [(ps.f[q], ps.g[q]) for q in full], chunksize=1)
+    for q, w in zip(full, want):
+        assert out[q] == w, f"pair {q}"
+    _check_every_pair_at_points(opool, ps.f, ps.g, out, rng, skip=planted)
 
 
 def test_interpolation_contraction_matches_newton(ctx):

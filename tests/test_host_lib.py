@@ -335,3 +335,32 @@ def test_binding_constants_match_the_header():
         assert getattr(N, name) == int(value), name
         checked += 1
     assert checked == 10 + 8 + 3                          # statuses, options, job kinds
+
+
+def test_host_bound_at_least_the_exact_bound(lib):
+    """gbr_resultant_info's bound (double precision, host) against the oracle's exact
+    enclosure of the same Hadamard bound on the GPU test's shapes: the primes it plans
+    satisfy M > 2B + 1 for the exact B, and its log2 B is not below the exact value by
+    more than its double-precision rounding."""
+    from fractions import Fraction
+
+    import test_gpu_bound as TB
+    from oracle.bound import log2_floor_half_pred, resultant_bound_log2
+    from paper_1103_4697_gb300.api import primes, resultant_info
+
+    jobs = [(f, g, False) for f, g in TB.bound_pairs()[::2]] + [(f, None, True) for f in TB.disc_polys()]
+    table = primes(400)
+    checked = 0
+    for f, g, disc in jobs:
+        ex = resultant_bound_log2(f, O.deriv_y(f) if disc else g)
+        info = resultant_info(f, g, disc=disc)
+        if ex is None:
+            continue
+        hi = ex[1]
+        assert Fraction(info["log2_bound"]) >= hi - Fraction(1, 10 ** 9) * (1 + abs(hi)), (info, float(hi))
+        M = 1
+        for p in table[:info["primes"]]:
+            M *= p
+        assert log2_floor_half_pred(M) > hi, (info, float(hi))
+        checked += 1
+    assert checked >= 80

@@ -212,6 +212,122 @@ def test_coefficients_within_hadamard_bound(seed):
         assert c * c <= sf ** n * sg ** m
 
 
+# --------------------------------------------------------------------------- the planned coefficient bound
+
+
+def _log2_abs_interval(v: int):
+    from oracle.bound import log2_interval
+
+    return log2_interval(abs(v))
+
+
+def _bound(f, g):
+    from oracle.bound import resultant_bound_log2
+
+    return resultant_bound_log2(f, g)
+
+
+def test_bound_log2_interval_brackets():
+    """The exact log2 enclosure against math.log2 (rationals, a + b sqrt 2)."""
+    from fractions import Fraction
+
+    from oracle.bound import log2_interval
+
+    for x in (1, 2, 3, 5, 7, 1000, 2 ** 100 + 1, Fraction(1, 3), Fraction(7, 1024), Fraction(2 ** 90 - 1, 3 ** 40)):
+        x = Fraction(x)
+        lo, hi = log2_interval(x)
+        v = math.log2(x.numerator) - math.log2(x.denominator)
+        assert lo <= v + 1e-12 and v - 1e-12 <= hi and 0 < hi - lo < 1e-11
+    for a, b in ((0, 1), (1, 1), (3, 2), (Fraction(1, 8), 5)):
+        lo, hi = log2_interval(Fraction(a), Fraction(b))
+        v = math.log2(a + b * math.sqrt(2))
+        assert lo <= v + 1e-12 and v - 1e-12 <= hi
+    # exact powers of two sit inside their enclosure
+    for e in (0, 1, 17, 500, -30):
+        lo, hi = log2_interval(Fraction(2) ** e)
+        assert lo <= e <= hi
+
+
+@pytest.mark.parametrize("a", [1, 3, 2 ** 20 + 7, 2 ** 40, 2 ** 200 - 5])
+def test_bound_tight_two_by_two(a):
+    """f = y + a, g = y - a: R = -2a, and the column form of the Hadamard bound is 2|a|
+    for every lambda; f = y + a, g = a y - 1: R = -(1 + a^2), the row and column forms at
+    lambda = 1.  The bound equals |R| (inside its enclosure)."""
+    for f, g, r in (([[a], [1]], [[-a], [1]], 2 * a), ([[a], [1]], [[-1], [a]], 1 + a * a)):
+        R = list(O.res_bareiss(f, g))
+        assert R in ([-r], [r])
+        lo, hi = _bound(f, g)
+        l2lo, l2hi = _log2_abs_interval(r)
+        assert lo <= l2hi and l2lo <= hi, (a, float(lo), float(hi))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_bound_tight_constant_in_y(seed):
+    """f = f_0(x) (y-degree 0) gives R = f_0^n, and |R(1)| = f_0(1)^n when f_0 has
+    non-negative coefficients (|R(-1)| = |f_0(-1)|^n when they alternate): the bound
+    n/2 log2 G(f_0) is then attained, so it equals log2 |R(+-1)| in both operand orders."""
+    rng = random.Random(900 + seed)
+    dx = rng.randint(0, 6)
+    f0 = [rng.randint(0, 40) for _ in range(dx + 1)]
+    f0[-1] = f0[-1] or 1
+    alt = seed % 2 == 1
+    if alt:
+        f0 = [c if i % 2 == 0 else -c for i, c in enumerate(f0)]
+    n = rng.randint(1, 4)
+    g = [[rng.randint(-9, 9) for _ in range(rng.randint(1, 4))] for _ in range(n + 1)]
+    g[-1][0] = g[-1][0] or 3
+    x = -1 if alt else 1
+    for A, B in (([f0], g), (g, [f0])):
+        Rx = O.res_at(A, B, x)
+        assert abs(Rx) == abs(sum(c * x ** i for i, c in enumerate(f0))) ** n
+        lo, hi = _bound(A, B)
+        l2lo, l2hi = _log2_abs_interval(Rx)
+        assert lo <= l2hi and l2lo <= hi, (float(lo), float(hi), float(l2lo))
+
+
+def _check_covers(f, g):
+    R = O.res_subres(f, g)
+    b = _bound(f, g)
+    if not R:
+        return
+    assert b is not None
+    vals = [max(abs(c) for c in R), abs(O.zx_eval(R, 1)), abs(O.zx_eval(R, -1))]
+    for v in vals:
+        if v:
+            assert _log2_abs_interval(v)[0] <= b[1], (float(b[1]), v.bit_length())
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_bound_covers_resultants(seed):
+    """max |coef R|, |R(1)| and |R(-1)| never exceed the bound: random dense pairs of
+    mixed shapes (y-degree 0..5, x-degree 0..6, coefficients of 2..40 bits), pairs whose
+    rows grow geometrically with the power of y (the best lambda is then not 1), and
+    planted-roots pairs."""
+    rng = random.Random(700 + seed)
+    for _ in range(6):
+        m, n = rng.randint(0, 5), rng.randint(0, 5)
+        bits = rng.choice([2, 8, 20, 40])
+        f = _rand_bipoly(rng, m, rng.randint(0, 6), -(1 << bits), 1 << bits)
+        g = _rand_bipoly(rng, n, rng.randint(0, 6), -(1 << bits), 1 << bits)
+        f[-1][0] = f[-1][0] or 1
+        g[-1][0] = g[-1][0] or 1
+        _check_covers(f, g)
+    for s in (-12, -3, 5, 16):
+        f = [[rng.randint(-9, 9) << max(0, s * i) for _ in range(3)] for i in range(4)]
+        g = [[rng.randint(-9, 9) << max(0, -s * j) for _ in range(2)] for j in range(3)]
+        f[-1][0] = f[-1][0] or 1
+        g[-1][0] = g[-1][0] or 1
+        _check_covers(f, g)
+    f, g = W.planted_roots_pair(seed, 3, 2)[:2]
+    _check_covers(f, g)
+
+
+def test_bound_empty_column_and_degenerate():
+    """A zero input gives no bound; constants in y give 0 = log2 1 for R = 1."""
+    assert _bound([[0]], [[1], [2]]) is None
+    assert _bound([[5]], [[7]]) == (0, 0)
+
+
 # --------------------------------------------------------------------------- degree-6 workload
 
 

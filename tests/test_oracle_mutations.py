@@ -95,6 +95,15 @@ MUTATIONS = [
     ("primitive_part_keeps_content", "zpoly.py", "    g = content(a)\n    if a[-1] < 0:", "    g = 1\n    if a[-1] < 0:"),
     ("gcd_content_of_one_argument", "gcd.py", "c = math.gcd(content(p), content(q))", "c = content(p)"),
     ("yun_quotient_not_divided", "sqf.py", "        c = zx_divexact(c, ri)\n", "        c = c[1:] or c\n"),
+    # the coefficient bound (Hadamard's inequality on the scaled Sylvester matrix)
+    ("bound_autocorr_factor_two", "bound.py", "g += 2 * abs(", "g += abs("),
+    ("bound_autocorr_no_abs", "bound.py", "g += 2 * abs(sum(h[a] * h[a + k] for a in range(L - k)))",
+     "g += 2 * sum(h[a] * h[a + k] for a in range(L - k))"),
+    ("bound_lambda_power_dropped", "bound.py", "lam = Fraction(m * n * q, 4)", "lam = Fraction(m * n * q, 8)"),
+    ("bound_rows_counts_swapped", "bound.py", "for s, count in ((sf, n), (sg, m)):", "for s, count in ((sf, m), (sg, n)):"),
+    ("bound_column_index", "bound.py", "                x = sf[m - (c - r)]\n", "                x = sf[min(m, c - r)]\n"),
+    ("bound_sqrt2_low", "bound.py", "    hi = a + b * _S2_HI\n", "    hi = a + b\n"),
+    ("bound_log2_round_down", "bound.py", "return val + Fraction(2, 1 << _T) if up else val", "return val"),
 ]
 
 
