@@ -507,6 +507,68 @@ def _oracle_time(fn, *a) -> float:
     return time.perf_counter() - t
 
 
+def ntt_crossover(ctx, reps: int = 5) -> dict:
+    """Integer points (inverse-Vandermonde contraction or Newton) against roots of unity
+    (inverse transform) on batches of one shape each, x-degree bound D from 64 to 16 380:
+    device time per run (CUDA events around the resident run, median of `reps`), the
+    evaluation and interpolation stages, and what the automatic choice takes."""
+    import torch
+
+    from paper_1103_4697_gb300 import native as N
+
+    def pair(rng, m, dx, bits=12):
+        h = 1 << (bits - 1)
+        f = [[rng.randint(-h, h - 1) for _ in range(dx + 1)] for _ in range(m + 1)]
+        f[-1][-1] = f[-1][-1] or 1
+        return f
+
+    shapes = [(2, dx) for dx in (16, 32, 64, 100, 128, 200, 256, 512, 1024, 2048, 4095)]
+    shapes += [(8, dx) for dx in (8, 16, 32, 64, 128, 256, 512)]
+    shapes += [("dense", d) for d in (8, 12, 16, 20, 24)]
+    rows = []
+    stream = torch.cuda.current_stream()
+    for m, dx in shapes:
+        rng = random.Random(hash((m, dx)) & 0xffff)
+        if m == "dense":
+            from paper_1103_4697_gb300 import workloads as W
+            F, G = W.deg20_batch_arrays(1024, 5000 + dx, dx, 16)
+            fs, gs, label, D = F, G, f"dense total degree {dx}", dx * dx
+        else:
+            npairs = max(8, min(1024, 4_000_000 // (2 * m * dx * (m + 1) * (dx + 1))))
+            fs = [pair(rng, m, dx) for _ in range(npairs)]
+            gs = [pair(rng, m, dx) for _ in range(npairs)]
+            label, D = f"y-degree {m}, x-degree {dx}", 2 * m * dx
+        res = ctx.upload_pairs(fs, gs)
+        row = {"shape": label, "pairs": len(fs), "D": D}
+        outs = {}
+        for mode, name in ((1, "integer"), (2, "roots"), (0, "auto")):
+            ctx.set_option(N.OPT_POINTS, mode)
+            for _ in range(2):
+                res.run()
+            times = []
+            for _ in range(reps):
+                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s.record(stream)
+                res.run()
+                e.record(stream)
+                e.synchronize()
+                times.append(s.elapsed_time(e))
+            st = ctx.stats()
+            outs[name] = res.fetch(0, min(4, len(fs)))
+            row[name] = {"us_per_pair": statistics.median(times) * 1e3 / len(fs),
+                         "evalres_ms": st["evalres_ms"], "interp_ms": st["interp_ms"],
+                         "root_pairs": st["root_pairs"]}
+        assert outs["integer"] == outs["roots"] == outs["auto"], label
+        row["auto_picks"] = "roots" if row["auto"]["root_pairs"] else "integer"
+        row["faster"] = "roots" if row["roots"]["us_per_pair"] < row["integer"]["us_per_pair"] else "integer"
+        res.free()
+        rows.append(row)
+    ctx.set_option(N.OPT_POINTS, 0)
+    return {"ntt_crossover": rows,
+            "workload": "batches of random pairs per shape (12-bit coefficients; dense rows: 16-bit), "
+                        "integer points vs roots of unity vs automatic choice"}
+
+
 def run_config(args) -> None:
     """Measurements for the other workloads (one JSON line each):
     small   one dense degree-6 pair, res_y and gcd(f(x,0), g(x,0)), one call each;
@@ -748,6 +810,8 @@ def run_config(args) -> None:
                           "factor_degrees": [len(x) - 1 for x in facs], "sqf_ms": tc * 1e3}
         out["workload"] = ("2048 R = u r1 r2^2 r3^3, deg r_i ~ U{20..60}, U{4..16}, U{0..4}, 16-bit "
                            "(deg R 28..104, about 100-bit coefficients; seed 6); R = res_y(f, f_y) of 8 conics (seed 4)")
+    elif args.config == "ntt":
+        out.update(ntt_crossover(ctx))
     elif args.config == "serve":
         res_all = {}
         cap = None
@@ -772,7 +836,7 @@ def main():
     ap.add_argument("--mem-gb", type=int, default=24)
     ap.add_argument("--pairs", type=int, default=PAIRS, help="pairs per GPU (smaller only for profiling)")
     ap.add_argument("--config", choices=["headline", "small", "deg20", "mixed", "conic", "serve", "gcd", "sqf",
-                                                 "arrangement", "teissier"],
+                                                 "arrangement", "teissier", "ntt"],
                     default="headline", help="other workloads print their own JSON line")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--no-serve", action="store_true")

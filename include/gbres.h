@@ -127,6 +127,8 @@ typedef struct {
     int64_t graph_replayed;   /* 1 when the device stages ran as a CUDA graph (GBR_OPT_GRAPH) */
     int64_t redo_warps;       /* GBR_OPT_REGISTER_FORM: warps of 32 subproblems solved again on
                                  shared memory */
+    int64_t root_pairs;       /* pairs evaluated at roots of unity and interpolated by an inverse
+                                 transform (GBR_OPT_POINTS) */
 } gbr_stats;
 
 /* ------------------------------------------------------------------ context */
@@ -174,6 +176,16 @@ const char *gbr_last_error(gbr_ctx *ctx);
                                     polynomials in registers (warps that meet a vanishing leading
                                     coefficient or a non-normal remainder sequence are solved again
                                     on shared memory); 0: every subproblem on shared memory */
+#define GBR_OPT_POINTS       9   /* evaluation points of the resultant (Section 4: the evaluation
+                                    and interpolation stages of the modular method; the paper fixes
+                                    no point set).  0 (default): chosen per pair by estimated cost;
+                                    1: the integers 0, +-1, +-2, ... (interpolation by inverse-
+                                    Vandermonde contraction or Newton); 2: the N-th roots of unity
+                                    modulo each prime, N the power of two >= max(64, deg_x R + 1)
+                                    (every table prime is 1 mod 2^14, so N <= 16384 = GBR_MAX_POINTS),
+                                    interpolation by an inverse number-theoretic transform in
+                                    O(N log N).  Not used in drop mode (GBR_OPT_DROP_UNLUCKY).
+                                    Results are identical; values outside 0..2: GBR_EINVAL. */
 int gbr_set_option(gbr_ctx *ctx, int option, int64_t value);
 int gbr_get_stats(gbr_ctx *ctx, gbr_stats *out);
 
@@ -427,8 +439,9 @@ int gbr_crt_noalloc(const uint32_t *residues, int k, int ncoef, int64_t stride, 
 /* ------------------------------------------------------------------ host-side information */
 
 /* The fixed table of primes used by every context: p_0 > p_1 > ... are the
- * largest primes below 2^32 / 3 (about 30.4 bits each, so that three
- * products of residues fit one Montgomery reduction).  Host only. */
+ * largest primes below 2^32 / 3 that are 1 mod 2^14 (30.0 to 30.4 bits each:
+ * three products of residues fit one Montgomery reduction, and each prime has
+ * roots of unity of order up to 2^14 for GBR_OPT_POINTS).  Host only. */
 int gbr_num_primes(void);
 int gbr_prime(int index, uint32_t *p);
 

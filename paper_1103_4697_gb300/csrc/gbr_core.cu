@@ -76,13 +76,17 @@ static ModP make_mod(uint32_t p) {
     return M;
 }
 
-// The table holds the largest primes below 2^32 / 3: three Montgomery products
-// then fit one reduction (see gbr_modarith.cuh).
+// The table holds the largest primes below 2^32 / 3 that are 1 mod 2^kRootLog:
+// three Montgomery products then fit one reduction (see gbr_modarith.cuh), and
+// each prime has roots of unity of every order up to 2^kRootLog, so evaluation
+// at roots of unity and an inverse transform can replace interpolation (there
+// are 2087 such primes above 2^30, enough for GBR_MAX_PRIMES).
 static void init_primes() {
     g_mods.reserve(GBR_MAX_PRIMES);
-    uint32_t top = (uint32_t)(0xffffffffull / 3);
-    if (!(top & 1)) --top;
-    for (uint32_t c = top; (int)g_mods.size() < GBR_MAX_PRIMES; c -= 2)
+    const uint32_t step = 1u << kRootLog;
+    uint32_t c = (uint32_t)(0xffffffffull / 3) / step * step + 1u;
+    if (c >= 0xffffffffull / 3) c -= step;
+    for (; (int)g_mods.size() < GBR_MAX_PRIMES; c -= step)
         if (is_prime32(c)) g_mods.push_back(make_mod(c));
     g_log2pref.assign(g_mods.size() + 1, 0.0);
     for (size_t i = 0; i < g_mods.size(); ++i) g_log2pref[i + 1] = g_log2pref[i] + std::log2((double)g_mods[i].p);
@@ -278,7 +282,17 @@ int gbr_ctx::ensure_tables(int K, int T) {
 // Device prime table: the ModP entries of every table prime, followed by
 // (R^3 mod p, R^4 mod p) per prime for the one-reduction residue conversion.
 size_t gbr::prime_table_bytes() {
-    return (size_t)num_primes() * (sizeof(ModP) + sizeof(uint2)) + (size_t)kCrtTabWords * 4;
+    return (size_t)num_primes() * (sizeof(ModP) + sizeof(uint2)) + (size_t)kCrtTabWords * 4 +
+           (size_t)num_primes() * kRootTabWords * 4;
+}
+
+// A root of unity of order 2^kRootLog modulo p (p = 1 mod 2^kRootLog): g^((p - 1) /
+// 2^kRootLog) for the smallest quadratic non-residue g, whose 2^(kRootLog - 1)-th
+// power is then g^((p - 1) / 2) = -1.
+static uint32_t root_of_unity_host(uint32_t p) {
+    uint32_t g = 2;
+    while (powmod32(g, (p - 1) / 2, p) != p - 1) ++g;
+    return powmod32(g, (p - 1) >> kRootLog, p);
 }
 
 void gbr::build_prime_table(std::vector<char> &buf) {
@@ -323,6 +337,19 @@ void gbr::build_prime_table(std::vector<char> &buf) {
         while (i <= KF && T[(size_t)l * kCrtFastRow + i] == 0u) ++i;
         I0[l] = (uint32_t)(i & ~3);
     }
+    // root-of-unity powers per prime (Montgomery forms): T1[j] = w^j, T2[j] = w^(128 j)
+    uint32_t *RT = (uint32_t *)(buf.data() + buf.size()) - (size_t)NP * kRootTabWords;
+    for (int i = 0; i < NP; ++i) {
+        const uint32_t p = hm[i].p;
+        const uint64_t w = root_of_unity_host(p), w128 = powmod32((uint32_t)w, 128, p);
+        uint64_t x = 1, y = 1;
+        for (int j = 0; j < 128; ++j) {
+            RT[(size_t)i * kRootTabWords + j] = to_mont_host((uint32_t)x, p);
+            RT[(size_t)i * kRootTabWords + 128 + j] = to_mont_host((uint32_t)y, p);
+            x = x * w % p;
+            y = y * w128 % p;
+        }
+    }
 }
 
 cudaError_t gbr::upload_prime_table(ModP *d) {
@@ -333,6 +360,7 @@ cudaError_t gbr::upload_prime_table(ModP *d) {
 
 const uint2 *gbr::prime_r34(const ModP *d) { return (const uint2 *)(d + num_primes()); }
 const uint32_t *gbr::prime_crt_tables(const ModP *d) { return (const uint32_t *)(prime_r34(d) + num_primes()); }
+const uint32_t *gbr::prime_roots(const ModP *d) { return prime_crt_tables(d) + kCrtTabWords; }
 
 // Inverse Vandermonde matrices are cached per (size n, point set) for the first
 // K primes; the cache is bounded by a quarter of the context's budget (at least
@@ -718,6 +746,7 @@ extern "C" int gbr_create(gbr_ctx **out, int device, size_t budget, void *worksp
     if (e == cudaSuccess) e = configure_gcd_kernels();
     if (e == cudaSuccess) e = configure_sqf_kernels();
     if (e == cudaSuccess) e = configure_interp_tc_kernel();
+    if (e == cudaSuccess) e = configure_interp_ntt_kernel();
     if (e != cudaSuccess) {
         gbr_destroy(c);
         return GBR_EDEVICE;
@@ -760,6 +789,7 @@ gbr_ctx *gbr_make_worker(gbr_ctx *parent) {
     w->gemm_on = parent->gemm_on;
     w->reg_on = parent->reg_on;
     w->tc_on = parent->tc_on;
+    w->pts_mode = parent->pts_mode;
     w->graph_on = 0;   // serving batches differ every time; graphs would only add capture cost
     w->extra_primes = parent->extra_primes;
     cudaSetDevice(w->device);
@@ -805,6 +835,10 @@ extern "C" int gbr_set_option(gbr_ctx *c, int opt, int64_t v) {
         case GBR_OPT_INTERP_GEMM: c->gemm_on = (int)(v != 0); return GBR_OK;
         case GBR_OPT_REGISTER_FORM: c->reg_on = (int)(v != 0); return GBR_OK;
         case GBR_OPT_INTERP_TC: c->tc_on = (int)(v != 0); return GBR_OK;
+        case GBR_OPT_POINTS:
+            if (v < 0 || v > 2) return GBR_EINVAL;
+            c->pts_mode = (int)v;
+            return GBR_OK;
         case GBR_OPT_PIPELINE: c->pipe_on = (int)(v != 0); return GBR_OK;
         case GBR_OPT_EXTRA_PRIMES:
             if (v < 0 || v > 64) return GBR_EINVAL;
@@ -1102,6 +1136,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     L.mods = c->d_mods;
     L.r34 = prime_r34(c->d_mods);
     L.crtfast = prime_crt_tables(c->d_mods);
+    L.roots = prime_roots(c->d_mods);
     L.npairs = n;
     L.err = c->d_err;
     L.deg = r->d_deg;
@@ -1163,11 +1198,21 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
             p.Pe = drop ? p.P + std::max(b.lcdf, 0) + std::max(b.lcdg, 0) : p.P;
             // symmetric points 0, +-1, +-2, ... halve the evaluation work (lane pairs);
             // the drop mode keeps the unit grid so that spare points are 0..Pe-1
-            p.sym = drop ? 0 : 1;
+            p.sym = drop ? PTS_GRID : PTS_SYM;
             p.tiles = (p.P / 2 + 1 + 15) / 16;
             // a complete symmetric set 0, +-1, ..., +-h (h = P/2, one point more when P
             // is even) lets interpolation split into even and odd parts
             if (p.sym) p.Pe = 2 * (p.P / 2) + 1;
+            // roots of unity: Pe = N points (a power of two) and an inverse transform,
+            // when the transform saves more than the extra points cost
+            if (!drop && c->pts_mode != 1) {
+                const int N = root_points(p.P);
+                if (N <= kRootOrder && (c->pts_mode == 2 || roots_pay(p.P, N, b.tf, b.tg, b.m, b.n, c->tc_on))) {
+                    p.sym = PTS_ROOTS;
+                    p.Pe = N;
+                    p.tiles = N / 32;
+                }
+            }
             if (p.Pe > GBR_MAX_POINTS + 2 * 4096) {
                 perr[q] = 4;
                 continue;
@@ -1220,7 +1265,8 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     int64_t res_w = 0, val_w = 0, cf_w = 0, flag_b = 0, gtab_w = 0, out_w = 0, sign_b = 0;
     int Kmax = 1, Pmax = 1, Lmax = 1, Kdig = 1;   // Kdig: most primes of one pair
     int Puse = 1;   // most points one interpolation uses (Pmax also counts the spare points)
-    HostList red, interp, crt, crtf;
+    int Nntt = 1;   // largest transform of the root-of-unity pairs
+    HostList red, interp, crt, crtf, ntt;
     int Kdig_f = 1, Lmax_f = 1;
     // evaluation buckets by y-degree (key / 4), register-form buckets by N, and
     // contraction groups by (points, symmetric): flat tables in ascending key order
@@ -1234,7 +1280,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     crtf.start.reserve(n);
     std::vector<int32_t> mapped;                    // pairs with their own Garner table
     int kmapped = 0;
-    int64_t subproblems = 0;
+    int64_t subproblems = 0, root_pairs = 0;
     for (int q = 0; q < n; ++q) {
         const PairBound &b = hb[q];
         PairPlan &p = plan[q];
@@ -1274,8 +1320,15 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
         else evb_t[key / 4].add(q, p.sym ? (int64_t)k * p.tiles * 32 : (int64_t)k * p.Pe);
         // the contraction serves pairs whose points are exactly 0..P-1 and whose
         // primes are the table prefix
-        if (p.pmap_off < 0 && (p.sym || p.Pe == p.P)) pg_items.push_back({2 * p.P + p.sym, q});
-        else interp.add(q, k);
+        if (p.sym == PTS_ROOTS) {
+            ntt.add(q, k);
+            ++root_pairs;
+            Nntt = std::max(Nntt, p.Pe);
+        } else if (p.pmap_off < 0 && (p.sym || p.Pe == p.P)) {
+            pg_items.push_back({2 * p.P + p.sym, q});
+        } else {
+            interp.add(q, k);
+        }
         if (p.pmap_off < 0 && k <= kCrtFastK) {
             crtf.add(q, p.P);
             Kdig_f = std::max(Kdig_f, k);
@@ -1284,7 +1337,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
             crt.add(q, p.P);
         }
         subproblems += (int64_t)k * p.Pe;
-        int64_t ev = (int64_t)k * p.P * (b.tf + b.tg + 2LL * p.m * p.n);
+        int64_t ev = (int64_t)k * (p.sym == PTS_ROOTS ? p.Pe : p.P) * (b.tf + b.tg + 2LL * p.m * p.n);
         st.modmul_evalres += ev;
         st.modmul += ev + (int64_t)k * p.P * (p.P - 1) + (int64_t)p.P * k * (k - 1) / 2;
     }
@@ -1374,6 +1427,8 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     size_t o_red_p, o_red_s, o_int_p, o_int_s, o_crt_p, o_crt_s;
     put_list(blk, red, o_red_p, o_red_s);
     put_list(blk, interp, o_int_p, o_int_s);
+    size_t o_ntt_p, o_ntt_s;
+    put_list(blk, ntt, o_ntt_p, o_ntt_s);
     put_list(blk, crt, o_crt_p, o_crt_s);
     size_t o_crtf_p, o_crtf_s;
     put_list(blk, crtf, o_crtf_p, o_crtf_s);
@@ -1582,6 +1637,10 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
             x = launch_interp(L, mk(o_int_p, o_int_s, interp), Puse, q);
             kernels++;
         }
+        if (x == cudaSuccess && ntt.total > 0) {
+            x = launch_interp_ntt(L, mk(o_ntt_p, o_ntt_s, ntt), Nntt, q);
+            kernels++;
+        }
         if (x == cudaSuccess && !gtiles.empty()) {
             x = launch_interp_gemm(L, r->d_planblk, (const GemmGroup *)(r->d_planblk + o_ggroups),
                                    (const GemmTile *)(r->d_planblk + o_gtiles), (int)gtiles.size(), q);
@@ -1666,6 +1725,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     st.kernels = kernels;
     st.graph_replayed = replayed ? 1 : 0;
     st.subproblems = subproblems;
+    st.root_pairs = root_pairs;
     st.h2d_bytes = (int64_t)blk.size();
     st.d2h_bytes = (int64_t)sizeof(PairBound) * n + 4;
     r->pend_st = st;
@@ -1806,6 +1866,7 @@ static int res_batch_pipelined(gbr_ctx *c, int n, const gbr_bipoly *f, const gbr
         x->gemm_on = c->gemm_on;
         x->reg_on = c->reg_on;
         x->tc_on = c->tc_on;
+        x->pts_mode = c->pts_mode;
         x->extra_primes = c->extra_primes;
         x->stats_on = 0;
         for (auto &kv : c->tuned_evalres) x->tuned_evalres.insert(kv);
@@ -1847,6 +1908,7 @@ static int res_batch_pipelined(gbr_ctx *c, int n, const gbr_bipoly *f, const gbr
             total.dropped_points += w->stats.dropped_points;
             total.dropped_primes += w->stats.dropped_primes;
             total.redo_warps += w->stats.redo_warps;
+            total.root_pairs += w->stats.root_pairs;
         }
         gbr_free_resident_locked(w, r);
         rs[ci & 1] = nullptr;

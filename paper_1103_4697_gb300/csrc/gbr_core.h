@@ -82,6 +82,7 @@ struct gbr_ctx {
     size_t h_pin_cap[4] = {0, 0, 0, 0};
     cudaEvent_t ev[8] = {};
     int drop_unlucky = 0, stats_on = 0, graph_on = 1, extra_primes = 0, gemm_on = 1, reg_on = 1, tc_on = 1;
+    int pts_mode = 0;   // GBR_OPT_POINTS: 0 chosen per pair by cost, 1 integer points, 2 roots of unity
     gbr_stats stats{};
     std::map<uint64_t, cudaGraphExec_t> graphs;
     struct Vinv {

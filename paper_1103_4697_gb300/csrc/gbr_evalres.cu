@@ -121,18 +121,24 @@ __device__ __forceinline__ void evalres_item(const ResLaunch &L, const WorkList 
     const int32_t *dgf = L.rowdeg + P.rowdeg_f;
     const int32_t *dgg = L.rowdeg + P.rowdeg_g;
     if (P.sym) {
-        // lanes 0-15 take points +ii, lanes 16-31 take -ii (same ii); a lane
-        // evaluates even and odd parts of one polynomial at ii^2 and hands the
-        // partner its value: f-lanes do f, g-lanes do g
+        // lanes 0-15 take points +a, lanes 16-31 take -a (same a); a lane
+        // evaluates even and odd parts of one polynomial at a^2 and hands the
+        // partner its value: f-lanes do f, g-lanes do g.  a = ii (PTS_SYM) or
+        // u^ii (PTS_ROOTS, -u^ii = u^(ii + Pe/2))
         const int per = P.tiles * 32;
         const int i = (int)(local / per);
         const int r = (int)(local % per);
         const int lane = r & 31;
         const int ii = (r >> 5) * 16 + (lane & 15);
         const bool glane = lane >= 16;
-        const int j = ii == 0 ? (glane ? -1 : 0) : (glane ? 2 * ii : 2 * ii - 1);
-        const ModP M = L.mods[prime_of(P, L.pmap, i)];
-        const uint32_t a = mp_to((uint32_t)ii, M);
+        const bool roots = P.sym == PTS_ROOTS;
+        const int j = roots ? (ii < P.Pe / 2 ? (glane ? ii + P.Pe / 2 : ii) : -1)
+                            : ii == 0 ? (glane ? -1 : 0) : (glane ? 2 * ii : 2 * ii - 1);
+        const int pidx = prime_of(P, L.pmap, i);
+        const ModP M = L.mods[pidx];
+        const uint32_t a = roots ? root_pow(L.roots + (int64_t)pidx * kRootTabWords,
+                                            (ii * (kRootOrder / P.Pe)) & (kRootOrder - 1), M)
+                                 : mp_to((uint32_t)ii, M);
         const uint32_t b = mp_mul(a, a, M);
         const uint32_t *rbase = L.res + P.res_off + (int64_t)i * P.S;
         const uint32_t *rc = glane ? rbase + (int64_t)(P.dxf + 1) * rf4 : rbase;
@@ -201,11 +207,22 @@ __global__ void __launch_bounds__(256, reg_min_blocks(N)) k_evalres_reg(ResLaunc
         const int lane = r & 31;
         const int ii = (r >> 5) * 16 + (lane & 15);
         const bool glane = lane >= 16;
-        const int j = ii == 0 ? (glane ? -1 : 0) : (glane ? 2 * ii : 2 * ii - 1);
-        const ModP M = L.mods[prime_of(P, L.pmap, i)];
-        // even and odd parts at b = ii^2 (an exact integer below p) by Shoup steps on
-        // the stored c R^2 residues, so the parts come out as R^2 E and R^2 O
-        const uint32_t b = (uint32_t)ii * (uint32_t)ii;
+        const bool roots = P.sym == PTS_ROOTS;   // warp-uniform: a warp is one (pair, prime, tile)
+        const int j = roots ? (ii < P.Pe / 2 ? (glane ? ii + P.Pe / 2 : ii) : -1)
+                            : ii == 0 ? (glane ? -1 : 0) : (glane ? 2 * ii : 2 * ii - 1);
+        const int pidx = prime_of(P, L.pmap, i);
+        const ModP M = L.mods[pidx];
+        // the point a in normal form: ii (PTS_SYM), or u^ii for the primitive Pe-th
+        // root of unity u = w^(2^kRootLog / Pe) (PTS_ROOTS; the partner lane's point
+        // -a is u^(ii + Pe/2))
+        uint32_t a = (uint32_t)ii, b = (uint32_t)ii * (uint32_t)ii;
+        if (roots) {
+            a = mp_from(root_pow(L.roots + (int64_t)pidx * kRootTabWords,
+                                 (ii * (kRootOrder / P.Pe)) & (kRootOrder - 1), M), M);
+            b = mp_mul(mp_mul(a, a, M), M.r2, M);
+        }
+        // even and odd parts at b = a^2 (below p) by Shoup steps on the stored
+        // c R^2 residues, so the parts come out as R^2 E and R^2 O
         const uint32_t bp = (uint32_t)(((uint64_t)b << 32) / M.p);
         const uint32_t np = 0u - M.p;
         const int rf4 = rows4(P.m);
@@ -250,10 +267,10 @@ __global__ void __launch_bounds__(256, reg_min_blocks(N)) k_evalres_reg(ResLaunc
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 if (r0 + t <= N) {
-                    // R E = redc(R^2 E); R ii O = redc(R^2 O ii) (R^2 O < 3p, so
+                    // R E = redc(R^2 E); R a O = redc(R^2 O a) (R^2 O < 3p, so
                     // both inputs stay below p 2^32)
                     const uint32_t ev = mp_redc(e[t], 0u, M.p, M.pinv);
-                    const uint32_t io = mp_mul(o[t], (uint32_t)ii, M);
+                    const uint32_t io = mp_mul(o[t], a, M);
                     const uint32_t plus = mp_add(ev, io, M.p), minus = mp_sub(ev, io, M.p);
                     own[r0 + t] = glane ? minus : plus;
                     oth[r0 + t] = glane ? plus : minus;

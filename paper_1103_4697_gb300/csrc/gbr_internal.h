@@ -17,6 +17,7 @@ namespace gbr {
 constexpr int kErrCrtLimbs = 2;       // a lifted coefficient needed more limbs than planned
 constexpr int kErrSpareShort = 5;     // drop mode ran out of spare points
 constexpr int kErrTensorStall = 6;    // a tensor-core wait gave up (interpolation skipped its results)
+constexpr int kErrNttDegree = 8;      // an inverse transform left a coefficient above the degree bound
 
 // ------------------------------------------------------------------ prime table (host)
 int num_primes();
@@ -27,6 +28,19 @@ void build_prime_table(std::vector<char> &buf);
 cudaError_t upload_prime_table(ModP *d);  // then the CRT tables of the first kCrtFastK primes
 const uint2 *prime_r34(const ModP *d);
 const uint32_t *prime_crt_tables(const ModP *d);
+const uint32_t *prime_roots(const ModP *d);
+
+// Roots of unity.  Every table prime is 1 mod 2^kRootLog, so it has a root of
+// unity w of order 2^kRootLog (w^(2^(kRootLog - 1)) = -1).  The device prime
+// table holds per prime kRootTabWords words: T1[j] = w^j R mod p and
+// T2[j] = w^(128 j) R mod p for j < 128 (Montgomery forms), so that
+// w^e R = mp_mul(T1[e mod 128], T2[e / 128]) for every e < 2^kRootLog.
+constexpr int kRootLog = 14;
+constexpr int kRootOrder = 1 << kRootLog;
+constexpr int kRootTabWords = 256;
+GBR_HD uint32_t root_pow(const uint32_t *tab, int e, const ModP &M) {
+    return mp_mul(tab[e & 127], tab[128 + (e >> 7)], M);
+}
 
 // Chinese remaindering tables for pairs on the first kCrtFastK table primes:
 //   Garner rows: row i (at crt_gd_off(i), padded with zeros to a multiple of 4)
@@ -93,8 +107,10 @@ struct PairPlan {
     int32_t L;          // 32-bit limbs per output coefficient
     int32_t S;          // residue words per prime: (dxf+1) rows4(m) + (dxg+1) rows4(n)
     int32_t pmap_off;   // -1: primes are table entries 0..k-1; else their table indices at pmap[pmap_off..]
-    int32_t sym;        // 1: points are point_of(j) (0, 1, -1, 2, -2, ...), evaluated in +-i lane pairs
-    int32_t tiles;      // symmetric points: warp tiles of 16 values of i per prime
+    int32_t sym;        // point set (PTS_*): PTS_SYM points are point_of(j) (0, 1, -1, 2, -2, ...),
+                        // PTS_ROOTS points are u^j (u a primitive Pe-th root of unity); both are
+                        // evaluated in +-a lane pairs
+    int32_t tiles;      // PTS_SYM, PTS_ROOTS: warp tiles of 16 lane pairs per prime
     int64_t res_off;    // residues [prime][S]                       (u32 words)
     int64_t val_off;    // values [prime][Pe]                        (u32 words)
     int64_t cf_off;     // coefficients mod p [prime][P]             (u32 words)
@@ -107,6 +123,11 @@ struct PairPlan {
 };
 
 enum : int32_t { PLAN_ZERO = 1 };
+
+// Point sets: the unit grid 0..Pe-1 (drop mode), the symmetric integers
+// 0, +-1, +-2, ..., or the Pe-th roots of unity u^j with Pe a power of two
+// (interpolated by an inverse transform).
+enum : int32_t { PTS_GRID = 0, PTS_SYM = 1, PTS_ROOTS = 2 };
 
 // Residue rows of a polynomial of degree m in the eliminated variable, padded to
 // a multiple of 4 (the evaluation reads four rows per 16-byte load).
@@ -195,6 +216,32 @@ GBR_HD int32_t degree_bound(const PairBound &b) {
     return (int32_t)(d < 0 ? 0 : d);
 }
 
+// Size of a root-of-unity point set for P coefficients: the next power of two,
+// at least 64 (two warp tiles of lane pairs).
+GBR_HD int root_points(int P) {
+    int N = 64;
+    while (N < P) N <<= 1;
+    return N;
+}
+
+// Whether root-of-unity points pay for a pair with P coefficients (N points),
+// y-degrees m, n and t_f, t_g stored coefficients, by an estimate in modular
+// products per (pair, prime): the N - P extra points cost their evaluation
+// ((t_f + t_g) / 2 Horner steps) and elimination (about 1.5 m n products plus
+// the inverse), the inverse transform about N log2 N; the integer points'
+// inverse-Vandermonde contraction costs P^2 / 2 multiply-adds (even and odd
+// halves), each about half a product on the tensor cores (up to 2 kTcMaxN + 1
+// points) and a whole one on the integer pipes, and Newton interpolation (when
+// the matrices are too large to cache) about P^2.
+GBR_HD bool roots_pay(int P, int N, int tf, int tg, int m, int n, int tc) {
+    const double per_point = 0.5 * (tf + tg) + 1.5 * m * n + 5.0 * (m > n ? m : n) + 50.0;
+    int lg = 0;
+    while ((1 << lg) < N) ++lg;
+    const double roots = per_point * (N - P) + (double)N * lg;
+    const double per_mac = P <= 513 && tc ? 0.5 : P <= 4097 ? 1.0 : 2.0;
+    return roots < per_mac * 0.5 * (double)P * P;
+}
+
 // ------------------------------------------------------------------ kernel launchers
 struct ResLaunch {
     // device pointers
@@ -205,6 +252,7 @@ struct ResLaunch {
     const PairPlan *plan;
     const ModP *mods;
     const uint2 *r34;            // per prime (R^3 mod p, R^4 mod p), R = 2^32
+    const uint32_t *roots;       // per prime kRootTabWords words of root-of-unity powers
     const uint32_t *crtfast;     // CRT tables of the first kCrtFastK primes (Garner rows, T, I0)
     const uint32_t *garner;      // prefix Garner table (K + K(K-1)/2 words)
     int32_t garner_K;
@@ -271,6 +319,9 @@ GBR_HD int reg_shape(int m, int n) {
 cudaError_t launch_evalres_reg(const ResLaunch &L, const WorkList &w, int N, int block, unsigned long long *redo_n,
                                int64_t *redo, cudaStream_t s);
 cudaError_t launch_interp(const ResLaunch &L, const WorkList &w, int maxP, cudaStream_t s);
+// inverse transform for PTS_ROOTS pairs (one item per (pair, prime)); maxN = largest Pe
+cudaError_t launch_interp_ntt(const ResLaunch &L, const WorkList &w, int maxN, cudaStream_t s);
+cudaError_t configure_interp_ntt_kernel();
 cudaError_t launch_crt(const ResLaunch &L, const WorkList &w, int maxK, int maxL, cudaStream_t s);
 // pairs on the prime-table prefix with k <= kCrtFastK
 cudaError_t launch_crt_fast(const ResLaunch &L, const WorkList &w, int maxK, int maxL, cudaStream_t s);

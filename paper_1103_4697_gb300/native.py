@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libgbres.so")
 
 OK, EINVAL, ENOMEM, EDEVICE, ETIMEOUT, EAGAIN, EVERIFY, ELIMIT, ECANCELED, ENOTFOUND = range(10)
 OPT_DROP_UNLUCKY, OPT_STATS, OPT_GRAPH, OPT_EXTRA_PRIMES, OPT_INTERP_GEMM, OPT_REGISTER_FORM, OPT_INTERP_TC, \
-    OPT_PIPELINE = (1, 2, 3, 4, 5, 6, 7, 8)
+    OPT_PIPELINE, OPT_POINTS = (1, 2, 3, 4, 5, 6, 7, 8, 9)
 JOB_RESULTANT, JOB_DISC, JOB_GCD = 0, 1, 2
 
 
@@ -44,7 +44,7 @@ class Stats(C.Structure):
                 ("total_ms", C.c_double), ("kernels", C.c_int64), ("subproblems", C.c_int64),
                 ("modmul", C.c_int64), ("modmul_evalres", C.c_int64), ("h2d_bytes", C.c_int64),
                 ("d2h_bytes", C.c_int64), ("dropped_points", C.c_int64), ("dropped_primes", C.c_int64),
-                ("graph_replayed", C.c_int64), ("redo_warps", C.c_int64)]
+                ("graph_replayed", C.c_int64), ("redo_warps", C.c_int64), ("root_pairs", C.c_int64)]
 
 
 class Calib(C.Structure):

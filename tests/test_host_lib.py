@@ -67,13 +67,16 @@ def test_prime_table(lib):
     from paper_1103_4697_gb300.api import primes
 
     assert lib.gbr_num_primes() == 2048
-    ps = primes(300)
-    assert ps[0] < 2 ** 32 // 3 and not any(_is_prime(c) for c in range(ps[0] + 2, 2 ** 32 // 3 + 1, 2))
+    ps = primes(2048)
+    step = 1 << 14
+    # the largest primes below 2^32 / 3 that are 1 mod 2^14 (roots of unity of order 2^14)
+    assert ps[0] < 2 ** 32 // 3 and not any(_is_prime(c) for c in range(ps[0] + step, 2 ** 32 // 3 + 1, step))
     assert all(a > b for a, b in zip(ps, ps[1:]))
-    assert all(_is_prime(p) for p in ps)
-    # consecutive: no prime is skipped between table entries
+    assert all(p % step == 1 for p in ps) and ps[-1] > 2 ** 30
+    assert all(_is_prime(p) for p in ps[:300] + ps[-20:])
+    # consecutive: no such prime is skipped between table entries
     for a, b in zip(ps[:40], ps[1:41]):
-        assert not any(_is_prime(c) for c in range(b + 2, a, 2))
+        assert not any(_is_prime(c) for c in range(b + step, a, step))
     p = C.c_uint32()
     assert lib.gbr_prime(2048, C.byref(p)) == N.EINVAL
     assert lib.gbr_prime(-1, C.byref(p)) == N.EINVAL
@@ -227,7 +230,7 @@ def _is_prime(v):
 def test_header_is_plain_c_and_links_from_c(lib, tmp_path):
     """include/gbres.h compiles as C99 (-Wall -Wextra -pedantic -Werror) and a C
     program linked against libgbres.so gets the host-only answers: the table's
-    two largest primes below 2^32 / 3, prime counts (-1 beyond the table), the
+    two largest primes below 2^32 / 3 that are 1 mod 2^14, prime counts (-1 beyond the table), the
     plan of res_y(x^2 + y^2 - 25, y + x - 1) and of its projection resultant,
     GBR_EINVAL for var = 2, and a status string."""
     import shutil
@@ -242,8 +245,8 @@ def test_header_is_plain_c_and_links_from_c(lib, tmp_path):
                     "-o", exe, os.path.join(ROOT, "tests", "native", "c_abi_example.c"), "-L", libdir, "-lgbres",
                     "-Wl,-rpath," + libdir], check=True, capture_output=True, text=True)
     out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
-    top = (2 ** 32 - 1) // 3
-    want_p = [v for v in range(top, top - 200, -1) if _is_prime(v)][:2]
+    top = (2 ** 32 - 1) // 3 // (1 << 14) * (1 << 14) + 1
+    want_p = [v for v in range(top, top - 400 * (1 << 14), -(1 << 14)) if _is_prime(v)][:2]
     assert out[0] == "num_primes 2048"
     assert out[1] == f"primes 0 {want_p[0]} {want_p[1]}"
     assert out[2] == "primes_for_bits 4 -1"            # 3 primes give about 91 bits, 4 about 121
@@ -334,7 +337,7 @@ def test_binding_constants_match_the_header():
             continue                                      # limits: not mirrored by the binding
         assert getattr(N, name) == int(value), name
         checked += 1
-    assert checked == 10 + 8 + 3                          # statuses, options, job kinds
+    assert checked == 10 + 9 + 3                          # statuses, options, job kinds
 
 
 def test_host_bound_at_least_the_exact_bound(lib):

@@ -365,12 +365,13 @@ def test_kronecker_host_helpers(tmp_path):
 
 
 def _table_primes(k):
-    """The k largest primes below 2^32 / 3 (the library's table starts there)."""
-    out, v = [], (2 ** 32 - 1) // 3
+    """The k largest primes below 2^32 / 3 that are 1 mod 2^14 (the library's table)."""
+    step = 1 << 14
+    out, v = [], (2 ** 32 - 1) // 3 // step * step + 1
     while len(out) < k:
-        if v % 2 and all(v % d for d in range(3, int(v ** 0.5) + 1, 2)):
+        if all(v % d for d in range(3, int(v ** 0.5) + 1, 2)):
             out.append(v)
-        v -= 1
+        v -= step
     return out
 
 
@@ -535,8 +536,8 @@ def test_routing_helpers(tmp_path):
 
 def test_host_constant_tables(tmp_path):
     """The host-built tables every Chinese remaindering and Newton interpolation
-    launch reads: the table primes (the largest primes below 2^32 / 3, in
-    descending order) with pinv = -p^-1 mod 2^32, r1 = 2^32 mod p, r2 = 2^64 mod p;
+    launch reads: the table primes (the largest primes below 2^32 / 3 that are
+    1 mod 2^14, in descending order) with pinv = -p^-1 mod 2^32, r1 = 2^32 mod p, r2 = 2^64 mod p;
     the Garner prefix table ((p_0 ... p_{i-1})^-1 and p_j mod p_i, Montgomery form);
     the inverse table (1/t mod p_i, Montgomery form), against their definitions."""
     if not os.path.exists(N.LIB_PATH):
@@ -627,4 +628,15 @@ def test_device_prime_table_bytes(tmp_path):
     for l in range(L):
         first = next((i for i in range(K + 1) if T[l][i]), K + 1)    # a row of zeros: past the end
         assert I0[l] == first & ~3
-    assert size == NP * (16 + 8) + (gd_off(K) + L * ROW + L) * 4
+    # root-of-unity tables: per prime T1[j] = w^j R, T2[j] = w^(128 j) R (mod p) with w of
+    # order exactly 2^14
+    roots = [[int(v) for v in out[3 + K + L + t].split()] for t in range(K + 2)]
+    for t, row in enumerate(roots):
+        p = ps[t] if t < K else int(row[0])
+        vals = row[1:] if t >= K else row
+        assert len(vals) == 256
+        w = vals[1] * pow(R, -1, p) % p
+        assert pow(w, 1 << 14, p) == 1 and pow(w, 1 << 13, p) == p - 1
+        for j in range(128):
+            assert vals[j] == pow(w, j, p) * R % p and vals[128 + j] == pow(w, 128 * j, p) * R % p
+    assert size == NP * (16 + 8 + 256 * 4) + (gd_off(K) + L * ROW + L) * 4
