@@ -798,10 +798,10 @@ gbr_ctx *gbr_make_worker(gbr_ctx *parent) {
         return nullptr;
     }
     w->own_stream = true;
-    w->d_mods = (ModP *)w->dalloc(prime_table_bytes());
+    // the prime table is read-only after the parent uploaded it: workers share it
+    w->d_mods = parent->d_mods;
     w->d_err = (int32_t *)w->dalloc(64);
-    if (!w->d_mods || !w->d_err || upload_prime_table(w->d_mods) ||
-        cudaMemset(w->d_err, 0, 64)) {
+    if (!w->d_mods || !w->d_err || cudaMemset(w->d_err, 0, 64)) {
         gbr_destroy_worker(w);
         return nullptr;
     }
@@ -817,7 +817,7 @@ void gbr_destroy_worker(gbr_ctx *w) {
         w->dfree(kv.second.d);
         w->dfree(kv.second.tc);
     }
-    for (void *p : {(void *)w->d_mods, (void *)w->d_err, (void *)w->d_garner, (void *)w->d_invk}) w->dfree(p);
+    for (void *p : {(void *)w->d_err, (void *)w->d_garner, (void *)w->d_invk}) w->dfree(p);   // d_mods: the parent's
     for (int i = 0; i < 8; ++i)
         if (w->ev[i]) cudaEventDestroy(w->ev[i]);
     for (int i = 0; i < 4; ++i)
