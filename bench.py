@@ -150,83 +150,141 @@ def oracle_baseline(pairs_per_core: int = 1, cores: int | None = None) -> dict:
 # --------------------------------------------------------------------------- serving
 
 
+def _serve_prepare(reqs):
+    """Requests -> packed job descriptors (and the buffers they point into)."""
+    from paper_1103_4697_gb300 import api
+    from paper_1103_4697_gb300 import native as N
+
+    keep = api._Packed()
+    jobs = []
+    for r in reqs:
+        kind = N.JOB_RESULTANT if r.kind == "res" else N.JOB_GCD
+        jobs.append(api._job(kind, r.a, r.b, 1, keep))
+    return jobs, keep
+
+
+def _serve_run(ctx, jobs, arrivals):
+    """A submitter thread releases each job at its arrival time; this thread takes
+    finished jobs with gbr_wait_any (blocking in the library, without the GIL) and
+    keeps the library's completion time of each, on perf_counter's clock."""
+    from paper_1103_4697_gb300 import native as N
+
+    L = N.lib()
+    n = len(jobs)
+    done = [0.0] * n
+    index = {}
+    # both clocks are CLOCK_MONOTONIC on Linux; the offset removes any difference
+    off = time.perf_counter() - L.gbr_clock()
+    t0 = time.perf_counter() + 0.01
+
+    def submitter():
+        for i, j in enumerate(jobs):
+            delay = t0 + arrivals[i] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            t = C.c_uint64()
+            N.check(L.gbr_submit(ctx.handle, C.byref(j), C.byref(t)), ctx.handle)
+            index[t.value] = i
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    out = N.BigPoly()
+    tk = C.c_uint64()
+    td = C.c_double()
+    left = n
+    while left:
+        st = L.gbr_wait_any(ctx.handle, 100, C.byref(tk), C.byref(out), C.byref(td))
+        if st in (N.ETIMEOUT, N.EAGAIN, N.ENOTFOUND):
+            if st == N.ENOTFOUND:
+                time.sleep(1e-4)                    # nothing submitted yet
+            continue
+        assert st == N.OK, f"serving request failed with status {st}"
+        while tk.value not in index:                # the submitter records the ticket
+            time.sleep(1e-6)
+        done[index[tk.value]] = td.value + off
+        L.gbr_free_result(ctx.handle, C.byref(out))
+        left -= 1
+    th.join()
+    return t0, done
+
+
+def _latency(t0, done, arrivals, rate):
+    lat = sorted((done[i] - (t0 + arrivals[i])) * 1e3 for i in range(len(done)))
+    span = max(done) - t0
+    return {"p50_ms": lat[len(lat) // 2], "p99_ms": lat[int(len(lat) * 0.99)], "throughput_rps": len(done) / span,
+            "offered_rps": rate, "requests": len(done)}
+
+
 def serving_run(ctx, n_burst: int = 1500, n_stream: int = 6000, load: float = 0.8, seed: int = 5,
                 capacity: float | None = None) -> dict:
     """Open-loop Poisson stream of mixed resultant/gcd requests (degree log-uniform
     5..30, 8..64-bit coefficients, 10 % planted factors): capacity from a burst, then
     a stream at `load` x capacity; latency = completion - scheduled arrival."""
+    from paper_1103_4697_gb300 import workloads as W
+
+    if capacity is None:
+        burst = W.serving_stream(seed, n_burst, rate=1e12)
+        jb, kb = _serve_prepare(burst)
+        _serve_run(ctx, jb, [0.0] * len(jb))                   # warm-up: caches, tables, streams
+        t0, done = _serve_run(ctx, jb, [0.0] * len(jb))
+        capacity = len(jb) / (max(done) - t0)
+    rate = load * capacity
+    stream = W.serving_stream(seed + 1, n_stream, rate=rate)
+    js, ks = _serve_prepare(stream)
+    arrivals = [r.t_arrive for r in stream]
+    t0, done = _serve_run(ctx, js, arrivals)
+    out = _latency(t0, done, arrivals, rate)
+    out.update({"capacity_rps": capacity,
+                "mix": "50/50 res_y/gcd, degree log-uniform 5..30, 8..64-bit, 10% planted",
+                "stats": ctx.serve_stats()})
+    return out
+
+
+def serving_loads(ctx, n: int = 100_000, seed: int = 5, n_burst: int = 3000, n_single: int = 1000) -> dict:
+    """The serving configuration at its stated size: one Poisson stream of n mixed
+    requests (drawn once at unit rate; a load scales its arrival times), replayed at 0.5,
+    0.8 and 0.95 of the capacity measured on a burst; and the same mix run one request
+    per synchronous call (gbr_resultant / gbr_gcd) as the like-for-like baseline."""
     from paper_1103_4697_gb300 import api
     from paper_1103_4697_gb300 import native as N
     from paper_1103_4697_gb300 import workloads as W
 
     L = N.lib()
-
-    def prepare(reqs):
-        keep = api._Packed()
-        jobs = []
-        for r in reqs:
-            kind = N.JOB_RESULTANT if r.kind == "res" else N.JOB_GCD
-            jobs.append(api._job(kind, r.a, r.b, 1, keep))
-        return jobs, keep
-
-    def run(jobs, arrivals):
-        """A submitter thread releases each job at its arrival time; this thread takes
-        finished jobs with gbr_wait_any (blocking in the library, without the GIL) and
-        keeps the library's completion time of each, on perf_counter's clock."""
-        n = len(jobs)
-        done = [0.0] * n
-        index = {}
-        # both clocks are CLOCK_MONOTONIC on Linux; the offset removes any difference
-        off = time.perf_counter() - L.gbr_clock()
-        t0 = time.perf_counter() + 0.01
-
-        def submitter():
-            for i, j in enumerate(jobs):
-                delay = t0 + arrivals[i] - time.perf_counter()
-                if delay > 0:
-                    time.sleep(delay)
-                t = C.c_uint64()
-                N.check(L.gbr_submit(ctx.handle, C.byref(j), C.byref(t)), ctx.handle)
-                index[t.value] = i
-
-        th = threading.Thread(target=submitter)
-        th.start()
-        out = N.BigPoly()
-        tk = C.c_uint64()
-        td = C.c_double()
-        left = n
-        while left:
-            st = L.gbr_wait_any(ctx.handle, 100, C.byref(tk), C.byref(out), C.byref(td))
-            if st in (N.ETIMEOUT, N.EAGAIN, N.ENOTFOUND):
-                if st == N.ENOTFOUND:
-                    time.sleep(1e-4)                    # nothing submitted yet
-                continue
-            assert st == N.OK, f"serving request failed with status {st}"
-            while tk.value not in index:                # the submitter records the ticket
-                time.sleep(1e-6)
-            done[index[tk.value]] = td.value + off
-            L.gbr_free_result(ctx.handle, C.byref(out))
-            left -= 1
-        th.join()
-        return t0, done
-
-    if capacity is None:
-        burst = W.serving_stream(seed, n_burst, rate=1e12)
-        jb, kb = prepare(burst)
-        run(jb, [0.0] * len(jb))                   # warm-up: caches, tables, streams
-        t0, done = run(jb, [0.0] * len(jb))
-        capacity = len(jb) / (max(done) - t0)
-    rate = load * capacity
-    stream = W.serving_stream(seed + 1, n_stream, rate=rate)
-    js, ks = prepare(stream)
-    arrivals = [r.t_arrive for r in stream]
-    t0, done = run(js, arrivals)
-    lat = sorted((done[i] - (t0 + arrivals[i])) * 1e3 for i in range(len(js)))
-    span = max(done) - t0
-    return {"p50_ms": lat[len(lat) // 2], "p99_ms": lat[int(len(lat) * 0.99)], "throughput_rps": len(js) / span,
-            "offered_rps": rate, "capacity_rps": capacity, "requests": len(js),
-            "mix": "50/50 res_y/gcd, degree log-uniform 5..30, 8..64-bit, 10% planted",
-            "stats": ctx.serve_stats()}
+    burst = W.serving_stream(seed, n_burst, rate=1e12)
+    jb, kb = _serve_prepare(burst)
+    _serve_run(ctx, jb, [0.0] * len(jb))
+    t0, done = _serve_run(ctx, jb, [0.0] * len(jb))
+    capacity = len(jb) / (max(done) - t0)
+    t = time.perf_counter()
+    stream = W.serving_stream(seed + 1, n, rate=1.0)
+    js, ks = _serve_prepare(stream)
+    prep_s = time.perf_counter() - t
+    loads = {}
+    for load in (0.5, 0.8, 0.95):
+        rate = load * capacity
+        arrivals = [r.t_arrive / rate for r in stream]
+        t0, done = _serve_run(ctx, js, arrivals)
+        loads[str(load)] = _latency(t0, done, arrivals, rate)
+    # one request per call, the same mix
+    single = stream[:n_single]
+    keep = api._Packed()
+    t = time.perf_counter()
+    for r in single:
+        o = N.BigPoly()
+        if r.kind == "res":
+            df, dg = api.pack_bipolys([r.a], keep), api.pack_bipolys([r.b], keep)
+            N.check(L.gbr_resultant(ctx.handle, C.cast(api._ptr(df), C.POINTER(N.BiPoly)),
+                                    C.cast(api._ptr(dg), C.POINTER(N.BiPoly)), 1, C.byref(o)), ctx.handle)
+        else:
+            dp, dq = api.pack_upolys([r.a], keep), api.pack_upolys([r.b], keep)
+            N.check(L.gbr_gcd(ctx.handle, C.cast(api._ptr(dp), C.POINTER(N.UPoly)),
+                              C.cast(api._ptr(dq), C.POINTER(N.UPoly)), C.byref(o)), ctx.handle)
+        L.gbr_free_result(ctx.handle, C.byref(o))
+    one_rps = n_single / (time.perf_counter() - t)
+    return {"capacity_rps": capacity, "loads": loads, "requests_per_load": n,
+            "one_request_per_call_rps": one_rps, "one_request_per_call_sample": n_single,
+            "host_prepare_s": prep_s, "stats": ctx.serve_stats(),
+            "mix": "50/50 res_y/gcd, degree log-uniform 5..30, 8..64-bit, 10% planted (seed 6)"}
 
 
 # --------------------------------------------------------------------------- roofline counts
@@ -271,18 +329,19 @@ def evalres_roofline(F, G, plans: list[dict], table: list[int], cal: dict) -> di
 
     ops = {"shoup": 0.0, "mul": 0.0, "mulsub": 0.0, "fma3": 0.0}
     textbook = 0
+
+    def shape(A):
+        """(y-degree, stored coefficients) of rows A[j][i] (an array or ragged lists)."""
+        rows = [np.nonzero(np.asarray(r, dtype=object) != 0)[0] for r in A]
+        deg_y = max((j for j, xs in enumerate(rows) if len(xs)), default=-1)
+        return deg_y, sum((int(rows[r][-1]) + 1) if len(rows[r]) else 1 for r in range(deg_y + 1))
+
     for q in range(len(F)):
+        if plans[q]["primes"] <= 0:
+            continue
         points = plans[q]["deg_bound"] + 1
         primes = table[:plans[q]["primes"]]
-        shapes = []
-        for A in (F[q], G[q]):
-            nz = np.nonzero(np.any(A != 0, axis=1))[0]
-            deg_y = int(nz[-1]) if len(nz) else -1
-            t = 0
-            for r in range(deg_y + 1):
-                xs = np.nonzero(A[r])[0]
-                t += (int(xs[-1]) + 1) if len(xs) else 1
-            shapes.append((deg_y, t))
+        shapes = [shape(F[q]), shape(G[q])]
         (m, tf), (n, tg) = shapes
         textbook += len(primes) * points * (tf + tg + 2 * m * n)
         for p in primes:
@@ -293,6 +352,180 @@ def evalres_roofline(F, G, plans: list[dict], table: list[int], cal: dict) -> di
                + ops["mulsub"] / cal["mulsub_per_s"] + ops["fma3"] / cal["fma3_per_s"])
     return {"products": products, "textbook_products": textbook, "ideal_s": ideal_s,
             "ops": {k: v for k, v in ops.items()}}
+
+
+# --------------------------------------------------------------------------- the five configurations
+
+
+def _oracle_job(job):
+    """One oracle computation for the per-configuration CPU figures: (name, seconds)."""
+    import oracle as O
+    from paper_1103_4697_gb300 import workloads as W
+
+    kind, arg = job
+    t = time.perf_counter()
+    if kind == "c1_res":
+        f, g = W.small_dense_pair(1)
+        O.res_bareiss(f, g)
+    elif kind == "c1_gcd":
+        f, g = W.small_dense_pair(1)
+        O.gcd_z(list(f[0]), list(g[0]))
+    elif kind == "c2_res":
+        f, g = W.deg20_pair(2)
+        O.res_evalz(f, g)
+    elif kind == "c2_disc":
+        f, g = W.deg20_pair(2)
+        O.disc_res(f, "evalz")
+    elif kind == "c3_res":
+        ps = W.mixed_batch(3, arg + 1)
+        O.res_evalz(ps.f[arg], ps.g[arg])
+    elif kind == "c3_gcd":
+        P, Q, _ = W.gcd_batch(3, arg + 1)
+        O.gcd_z(P[arg], Q[arg])
+    elif kind == "c4_res":
+        f, g = W.conic_curves(4)
+        O.res_evalz(f, g)
+    elif kind == "c5":
+        reqs = W.serving_stream(5, arg + 1, rate=1.0)
+        r = reqs[arg]
+        (O.res_subres if r.kind == "res" else O.gcd_z)(r.a, r.b)
+    return kind, time.perf_counter() - t
+
+
+def _stage_roofline(ctx, st: dict, fs, gs, plans, cal: dict) -> dict:
+    """Stage times of the last run and the evaluation stage against its own operation mix
+    at the calibrated rates (register-form count; small runs are launch bound)."""
+    from paper_1103_4697_gb300 import api
+
+    rl = evalres_roofline(fs, gs, plans, api.primes(max(p["primes"] for p in plans) or 1), cal)
+    ms = st["evalres_ms"]
+    achieved = rl["products"] / (ms * 1e-3) if ms > 0 else 0.0
+    return {"stages_ms": {k: st[k] for k in ("bounds_ms", "reduce_ms", "evalres_ms", "interp_ms", "crt_ms")},
+            "evalres": {"bound": "alu", "products": rl["products"], "achieved_Tmodmul_s": achieved / 1e12,
+                        "peak_Tmodmul_s": rl["products"] / rl["ideal_s"] / 1e12 if rl["ideal_s"] else None,
+                        "frac": achieved * rl["ideal_s"] / rl["products"] if rl["products"] else None}}
+
+
+def configs_block(ctx, cal: dict, serve_requests: int = 100_000) -> dict:
+    """Every configuration measured on this GPU beside the plain one-pair-per-launch GPU
+    path and the oracle on the host cores (a bounded sample each, timed in a spawn pool
+    before any GPU work of this block):
+      1  one dense degree-6 pair: res_y(f, g) and gcd(f(x, 0), g(x, 0)), one call each;
+      2  one dense degree-20 pair: res_y(f, g) and res_y(f, f_y), one call each;
+      3  4096 mixed pairs (degrees 4..16, 8..32-bit, 25 % planted) as one resident batch
+         and 4096 gcds (degrees 30..200) through the C ABI, with their one-per-call rates;
+      4  the conic product against a dense degree-24 curve: res_y(f, g), res_y(f, f_y);
+      5  a Poisson stream of mixed requests at 0.5, 0.8 and 0.95 of the measured
+         capacity (p50/p99 latency, throughput), and the same mix one request per call."""
+    import torch
+
+    import oracle as O
+    from paper_1103_4697_gb300 import api
+    from paper_1103_4697_gb300 import native as N
+    from paper_1103_4697_gb300 import workloads as W
+
+    L = N.lib()
+    cores = os.cpu_count() or 1
+    jobs = [("c1_res", 0), ("c1_gcd", 0), ("c2_res", 0), ("c2_disc", 0), ("c4_res", 0)]
+    jobs += [("c3_res", i) for i in range(8)] + [("c3_gcd", i) for i in range(8)] + [("c5", i) for i in range(64)]
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        otimes = pool.map(_oracle_job, jobs, chunksize=1)
+    owall = time.perf_counter() - t0
+    per = {}
+    for k, s in otimes:
+        per.setdefault(k, []).append(s)
+
+    def oracle_rate(kind):
+        v = per[kind]
+        return {"s_per_job_1core": statistics.mean(v), "jobs": len(v)}
+
+    out = {"oracle_pool": {"cores": cores, "wall_s": owall, "kind": "oracle"}}
+    # 1: one dense degree-6 pair
+    f, g = W.small_dense_pair(1)
+    p, q = list(f[0]), list(g[0])
+    ctx.resultant(f, g)
+    ctx.gcd(p, q)
+    ctx.set_option(N.OPT_STATS, 1)
+    ctx.resultant(f, g)
+    rl1 = _stage_roofline(ctx, ctx.stats(), [f], [g], [api.resultant_info(f, g)], cal)
+    out["1"] = {"stage_roofline": rl1, "res_ms_per_call": _time_calls(lambda: ctx.resultant(f, g), 20) * 1e3,
+                "gcd_ms_per_call": _time_calls(lambda: ctx.gcd(p, q), 20) * 1e3,
+                "workload": "one dense pair of total degree 6, coefficients in [-128, 127] (seed 1); "
+                            "res_y(f, g) and gcd(f(x, 0), g(x, 0))",
+                "oracle_res_ms": per["c1_res"][0] * 1e3, "oracle_gcd_ms": per["c1_gcd"][0] * 1e3,
+                "note": "a single pair is the one-pair-per-launch path itself (launch bound)"}
+    # 2: one dense degree-20 pair
+    f2, g2 = W.deg20_pair(2)
+    ctx.resultant(f2, g2)
+    rl2 = _stage_roofline(ctx, ctx.stats(), [f2], [g2], [api.resultant_info(f2, g2)], cal)
+    out["2"] = {"stage_roofline": rl2, "res_ms_per_call": _time_calls(lambda: ctx.resultant(f2, g2), 10) * 1e3,
+                "disc_ms_per_call": _time_calls(lambda: ctx.discriminant_res(f2), 10) * 1e3,
+                "oracle_res_s": per["c2_res"][0], "oracle_disc_s": per["c2_disc"][0],
+                "workload": "one dense pair of total degree 20, 16-bit (seed 2); res_y(f, g), res_y(f, f_y)"}
+    # 3: the mixed batch, resident, and the gcd batch through the C ABI
+    ps = W.mixed_batch(3, PAIRS)
+    ctx.set_option(N.OPT_STATS, 1)
+    res = ctx.upload_pairs(ps.f, ps.g)
+    for _ in range(3):
+        res.run()
+    st = ctx.stats()
+    rl3 = _stage_roofline(ctx, st, ps.f, ps.g, res.plan(), cal)
+    sec = _time_calls(res.run, 10)
+    outs = res.fetch()
+    assert all(outs[i] == [] for i in range(PAIRS) if ps.planted[i])
+    res.free()
+    keep = api._Packed()
+    df, dg = api.pack_bipolys(ps.f, keep), api.pack_bipolys(ps.g, keep)
+    n1 = 64
+    t = time.perf_counter()
+    for i in range(n1):
+        o = N.BigPoly()
+        N.check(L.gbr_resultant(ctx.handle, C.cast(api._ptr(df[i:i + 1]), C.POINTER(N.BiPoly)),
+                                C.cast(api._ptr(dg[i:i + 1]), C.POINTER(N.BiPoly)), 1, C.byref(o)), ctx.handle)
+        L.gbr_free_result(ctx.handle, C.byref(o))
+    one_res = n1 / (time.perf_counter() - t)
+    P, Q, _H = W.gcd_batch(3, PAIRS)
+    dp, dq = api.pack_upolys(P, keep), api.pack_upolys(Q, keep)
+    gouts = (N.BigPoly * PAIRS)()
+    gtimes = []
+    for _ in range(4):
+        t = time.perf_counter()
+        N.check(L.gbr_gcd_batch(ctx.handle, PAIRS, api._ptr(dp), api._ptr(dq), gouts), ctx.handle)
+        gtimes.append(time.perf_counter() - t)
+        for i in range(PAIRS):
+            L.gbr_free_result(ctx.handle, C.byref(gouts[i]))
+    t = time.perf_counter()
+    for i in range(n1):
+        o = N.BigPoly()
+        N.check(L.gbr_gcd(ctx.handle, C.cast(api._ptr(dp[i:i + 1]), C.POINTER(N.UPoly)),
+                          C.cast(api._ptr(dq[i:i + 1]), C.POINTER(N.UPoly)), C.byref(o)), ctx.handle)
+        L.gbr_free_result(ctx.handle, C.byref(o))
+    one_gcd = n1 / (time.perf_counter() - t)
+    out["3"] = {"res_solves_per_s": PAIRS / sec, "res_ms_per_batch": sec * 1e3, "stage_roofline": rl3,
+                "res_one_pair_per_launch_per_s": one_res,
+                "gcd_jobs_per_s": PAIRS / statistics.median(gtimes[1:]),
+                "gcd_one_job_per_launch_per_s": one_gcd,
+                "oracle_res": oracle_rate("c3_res"), "oracle_gcd": oracle_rate("c3_gcd"),
+                "planted_zero": sum(1 for x in ps.planted if x),
+                "workload": "4096 pairs, deg_x, deg_y ~ U{4..16}, 8..32-bit, 25% planted (seed 3), one resident "
+                            "batch; 4096 gcds of degree 30..200 with a planted degree-5 factor"}
+    # 4: the conic product
+    f4, g4 = W.conic_curves(4)
+    ctx.resultant(f4, g4)
+    rl4 = _stage_roofline(ctx, ctx.stats(), [f4], [g4], [api.resultant_info(f4, g4)], cal)
+    out["4"] = {"stage_roofline": rl4, "res_ms_per_call": _time_calls(lambda: ctx.resultant(f4, g4), 5) * 1e3,
+                "disc_ms_per_call": _time_calls(lambda: ctx.discriminant_res(f4), 5) * 1e3,
+                "primes": {"res": api.resultant_info(f4, g4)["primes"],
+                           "disc": api.resultant_info(f4, None, disc=True)["primes"]},
+                "oracle_res_s": per["c4_res"][0],
+                "workload": "product of 8 circles/ellipses + 16 monomials (32-bit) vs dense degree 24, 64-bit "
+                            "(seed 4)"}
+    # 5: serving
+    if serve_requests > 0:
+        out["5"] = serving_loads(ctx, serve_requests)
+        out["5"]["oracle"] = oracle_rate("c5")
+    return out
 
 
 # --------------------------------------------------------------------------- our arm
@@ -410,7 +643,7 @@ def run_ours(args) -> None:
            "d2h_bytes_per_step": d2h, "api": "gbr_resultant_batch (host buffers)"}
     # the plain GPU path: one pair per call
     one = None
-    serving = None
+    configs = None
     if rank == 0:
         n1 = 64
         t = time.perf_counter()
@@ -420,9 +653,12 @@ def run_ours(args) -> None:
                                     C.cast(api._ptr(dg[q:q + 1]), C.POINTER(N.BiPoly)), 1, C.byref(o)), ctx.handle)
             L.gbr_free_result(ctx.handle, C.byref(o))
         one = {"value": n1 / (time.perf_counter() - t), "unit": "solves/s", "sample": f"{n1} pairs, one call each"}
-        if not args.no_serve:
-            serving = serving_run(ctx)
-    res.free()
+        if not args.no_configs:
+            res.free()
+            res = None
+            configs = configs_block(ctx, cal, 0 if args.no_serve else args.serve_requests)
+    if res is not None:
+        res.free()
     ctx.close()
     if rank != 0:
         return
@@ -450,7 +686,8 @@ def run_ours(args) -> None:
         "wall_ms_per_step": t_wall * 1e3 / args.steps,
         "calibration": cal,
         "one_pair_per_launch": one,
-        "serving": serving,
+        "configs": configs,
+        "serving": (configs or {}).get("5"),
         "parity": "8 pairs drawn from the whole batch x 2 random points vs the oracle's R(a) before timing; "
                   "every pair in tests -m gpu",
     }
@@ -524,15 +761,19 @@ def ntt_crossover(ctx, reps: int = 5) -> dict:
 
     shapes = [(2, dx) for dx in (16, 32, 64, 100, 128, 200, 256, 512, 1024, 2048, 4095)]
     shapes += [(8, dx) for dx in (8, 16, 32, 64, 128, 256, 512)]
-    shapes += [("dense", d) for d in (8, 12, 16, 20, 24)]
+    shapes += [("dense", d) for d in (8, 12, 16, 20, 24)] + [("mixed", 4096)]
     rows = []
     stream = torch.cuda.current_stream()
+    ctx.set_option(N.OPT_STATS, 1)
     for m, dx in shapes:
         rng = random.Random(hash((m, dx)) & 0xffff)
+        from paper_1103_4697_gb300 import workloads as W
         if m == "dense":
-            from paper_1103_4697_gb300 import workloads as W
             F, G = W.deg20_batch_arrays(1024, 5000 + dx, dx, 16)
             fs, gs, label, D = F, G, f"dense total degree {dx}", dx * dx
+        elif m == "mixed":
+            ps = W.mixed_batch(3, dx)
+            fs, gs, label, D = ps.f, ps.g, "heterogeneous batch (degrees 4..16, 25% planted)", 512
         else:
             npairs = max(8, min(1024, 4_000_000 // (2 * m * dx * (m + 1) * (dx + 1))))
             fs = [pair(rng, m, dx) for _ in range(npairs)]
@@ -556,7 +797,8 @@ def ntt_crossover(ctx, reps: int = 5) -> dict:
             st = ctx.stats()
             outs[name] = res.fetch(0, min(4, len(fs)))
             row[name] = {"us_per_pair": statistics.median(times) * 1e3 / len(fs),
-                         "evalres_ms": st["evalres_ms"], "interp_ms": st["interp_ms"],
+                         "stages_ms": {k: round(st[k], 4) for k in ("bounds_ms", "reduce_ms", "evalres_ms",
+                                                                     "interp_ms", "crt_ms")},
                          "root_pairs": st["root_pairs"]}
         assert outs["integer"] == outs["roots"] == outs["auto"], label
         row["auto_picks"] = "roots" if row["auto"]["root_pairs"] else "integer"
@@ -838,8 +1080,10 @@ def main():
     ap.add_argument("--config", choices=["headline", "small", "deg20", "mixed", "conic", "serve", "gcd", "sqf",
                                                  "arrangement", "teissier", "ntt"],
                     default="headline", help="other workloads print their own JSON line")
-    ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--serve-requests", type=int, default=100_000,
+                    help="requests per load of the serving configuration (default: its stated 100 000)")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="headline line without the per-configuration block")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -1203,21 +1203,31 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
             // a complete symmetric set 0, +-1, ..., +-h (h = P/2, one point more when P
             // is even) lets interpolation split into even and odd parts
             if (p.sym) p.Pe = 2 * (p.P / 2) + 1;
-            // roots of unity: Pe = N points (a power of two) and an inverse transform,
-            // when the transform saves more than the extra points cost
-            if (!drop && c->pts_mode != 1) {
-                const int N = root_points(p.P);
-                if (N <= kRootOrder && (c->pts_mode == 2 || roots_pay(p.P, N, b.tf, b.tg, b.m, b.n, c->tc_on))) {
-                    p.sym = PTS_ROOTS;
-                    p.Pe = N;
-                    p.tiles = N / 32;
-                }
-            }
             if (p.Pe > GBR_MAX_POINTS + 2 * 4096) {
                 perr[q] = 4;
                 continue;
             }
             kcl = std::max(kcl, p.k + 32);
+        }
+    }
+    // roots of unity: Pe = N points (a power of two) and an inverse transform, when
+    // the transform saves more than the extra points cost; the integer points'
+    // contraction cost depends on how many pairs share its point count
+    if (!drop && c->pts_mode != 1) {
+        std::unordered_map<int32_t, int> share;
+        for (int q = 0; q < n; ++q)
+            if (!perr[q] && !(plan[q].flags & PLAN_ZERO)) ++share[plan[q].P];
+        for (int q = 0; q < n; ++q) {
+            PairPlan &p = plan[q];
+            if (perr[q] || (p.flags & PLAN_ZERO)) continue;
+            const int N = root_points(p.P);
+            if (N > kRootOrder) continue;
+            if (c->pts_mode == 2 ||
+                roots_pay(p.P, N, hb[q].tf, hb[q].tg, p.m, p.n, share[p.P], c->tc_on && c->gemm_on, c->gemm_on)) {
+                p.sym = PTS_ROOTS;
+                p.Pe = N;
+                p.tiles = N / 32;
+            }
         }
     }
     for (int q = 0; q < n; ++q)
@@ -2076,6 +2086,8 @@ double lse2(const std::vector<double> &a) {   // log2 sum 2^a_i
     return mx + std::log2(s);
 }
 
+constexpr int kRowBufHost = 128;   // rows up to this length use the autocorrelation bound (k_bounds' kRowBuf)
+
 // row degrees and log2 row 1-norms of one polynomial in the eliminated-variable view
 void host_rows(const gbr_bipoly *p, int var, std::vector<int> &deg, std::vector<double> &nrm) {
     PolyDesc d = view_of(p, var, 0);
@@ -2092,8 +2104,9 @@ void host_rows(const gbr_bipoly *p, int var, std::vector<int> &deg, std::vector<
             }
         }
         nrm[r] = lse2(a);
-        if (d.words == 1 && deg[r] >= 0) {
+        if (d.words == 1 && deg[r] >= 0 && deg[r] < kRowBufHost) {
             // the autocorrelation bound of the device planner (k_bounds): |f_r(x)|^2 <= A_0 + 2 sum |A_k|
+            // (longer rows keep the 1-norm, as on the device)
             const int L = deg[r] + 1;
             const double gam = 2.0 * (L + 1) * 0x1p-53;
             double G = 0.0;

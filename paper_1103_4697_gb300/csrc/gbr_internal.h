@@ -225,20 +225,29 @@ GBR_HD int root_points(int P) {
 }
 
 // Whether root-of-unity points pay for a pair with P coefficients (N points),
-// y-degrees m, n and t_f, t_g stored coefficients, by an estimate in modular
-// products per (pair, prime): the N - P extra points cost their evaluation
-// ((t_f + t_g) / 2 Horner steps) and elimination (about 1.5 m n products plus
-// the inverse), the inverse transform about N log2 N; the integer points'
+// y-degrees m, n and t_f, t_g stored coefficients, `share` pairs of the batch
+// having the same P, by an estimate in modular products per (pair, prime): the
+// N - P extra points cost their evaluation ((t_f + t_g) / 2 Horner steps) and
+// elimination (about 1.5 m n products plus the inverse), the inverse transform
+// about 5 N log2 N (it is memory and barrier bound); the integer points'
 // inverse-Vandermonde contraction costs P^2 / 2 multiply-adds (even and odd
-// halves), each about half a product on the tensor cores (up to 2 kTcMaxN + 1
-// points) and a whole one on the integer pipes, and Newton interpolation (when
-// the matrices are too large to cache) about P^2.
-GBR_HD bool roots_pay(int P, int N, int tf, int tg, int m, int n, int tc) {
+// halves) at about half a product each on the tensor cores (up to 511 points,
+// tiles of 128 pairs) and 0.85 on the integer pipes (tiles of 64 pairs), inflated
+// by the unused part of its last tile;
+// above 4097 points the integer points fall back to Newton interpolation, which
+// one warp per (pair, prime) runs far slower.  (Constants fitted to the
+// measured crossover of this GPU.)
+GBR_HD bool roots_pay(int P, int N, int tf, int tg, int m, int n, int share, bool tc, bool gemm) {
     const double per_point = 0.5 * (tf + tg) + 1.5 * m * n + 5.0 * (m > n ? m : n) + 50.0;
     int lg = 0;
     while ((1 << lg) < N) ++lg;
-    const double roots = per_point * (N - P) + (double)N * lg;
-    const double per_mac = P <= 513 && tc ? 0.5 : P <= 4097 ? 1.0 : 2.0;
+    const double roots = per_point * (N - P) + 5.0 * N * lg;
+    if (!gemm || P > 4097) return true;
+    const int s = share < 1 ? 1 : share;
+    const bool on_tc = P <= 511 && tc;
+    const int tile = on_tc ? 128 : 64;
+    const double tile_waste = (double)((s + tile - 1) / tile * tile) / s;
+    const double per_mac = (on_tc ? 0.5 : 0.85) * tile_waste;
     return roots < per_mac * 0.5 * (double)P * P;
 }
 

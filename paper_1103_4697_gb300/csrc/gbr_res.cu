@@ -90,8 +90,9 @@ constexpr int kBoundsWarps = 4;
 // memory.  Coefficients of 2^56 and more: double sums with the error term
 // gamma sum |c_a c_{a+k}|, gamma = 2 (L+1) 2^-53 (covering the conversions,
 // products and the sum of L terms), so G stays an upper bound.  Wider
-// coefficients: log2 of the 1-norm by a log-sum-exp over the coefficients'
-// log2 magnitudes.
+// coefficients, and rows longer than kRowBuf (where the O(L^2) sums would
+// dominate the whole run): log2 of the 1-norm by a log-sum-exp over the
+// coefficients' log2 magnitudes (G <= 1-norm^2, so still an upper bound).
 constexpr int kRowBuf = 128;   // coefficients of one row staged per warp
 
 // log2 of a positive 128-bit integer hi 2^64 + lo, rounded up to a float: the
@@ -126,12 +127,15 @@ __device__ __forceinline__ float log2_up(double x) {
     return __fadd_ru((float)e, __fadd_ru(log2f(__double2float_ru(mant)), 0x1p-20f));
 }
 
+__device__ float row_l1_log2_up(const uint64_t *coef, const PolyDesc &P, int r, int lane, int &cmax);
+
 // An upper bound of log2 of the row norm used by the Hadamard bound, as a float
-// (-inf for a zero row).  Single-word rows: half the log2 of the autocorrelation
-// quantity G; with every |c| < 2^56, G is summed exactly (int64 terms below 2^27,
-// else 128-bit products; G < 2^127) and its log2 taken from its leading bits;
-// wider single-word coefficients use the double sum with its error term.
-// Multi-word rows: the log2 of the 1-norm by a log-sum-exp, rounded up.
+// (-inf for a zero row).  Single-word rows of at most kRowBuf coefficients: half
+// the log2 of the autocorrelation quantity G; with every |c| < 2^56, G is summed
+// exactly (int64 terms below 2^27, else 128-bit products; G < 2^127) and its log2
+// taken from its leading bits; wider single-word coefficients use the double sum
+// with its error term.  Multi-word rows and longer rows: the log2 of the 1-norm by
+// a log-sum-exp, rounded up.
 __device__ float row_log2_up(const uint64_t *coef, const PolyDesc &P, int r, int lane, int &cmax, int64_t *rb) {
     cmax = -1;
     if (P.words == 1) {
@@ -149,7 +153,8 @@ __device__ float row_log2_up(const uint64_t *coef, const PolyDesc &P, int r, int
         __syncwarp();
         if (cmax < 0) return -INFINITY;
         const int L = cmax + 1;
-        if (L <= kRowBuf && big < (1ull << 56)) {
+        if (L > kRowBuf) return row_l1_log2_up(coef, P, r, lane, cmax);
+        if (big < (1ull << 56)) {
             // exact: |A_k| < 128 * 2^112, G < 2^127
             unsigned __int128 acc = 0;
             for (int k = lane; k < L; k += 32) {
@@ -179,8 +184,8 @@ __device__ float row_log2_up(const uint64_t *coef, const PolyDesc &P, int r, int
         for (int k = lane; k < L; k += 32) {
             double sk = 0.0, tk = 0.0;
             for (int a = 0; a + k < L; ++a) {
-                const double x = (double)(L <= kRowBuf ? rb[a] : (int64_t)coef_ptr(coef, P, r, a)[0]);
-                const double y = (double)(L <= kRowBuf ? rb[a + k] : (int64_t)coef_ptr(coef, P, r, a + k)[0]);
+                const double x = (double)rb[a];
+                const double y = (double)rb[a + k];
                 sk = fma(x, y, sk);
                 tk = fma(fabs(x), fabs(y), tk);
             }
@@ -188,15 +193,20 @@ __device__ float row_log2_up(const uint64_t *coef, const PolyDesc &P, int r, int
         }
         for (int o = 16; o; o >>= 1) G += __shfl_xor_sync(0xffffffffu, G, o);
         __syncwarp();
-        // G: a lane's sum of about L / 32 non-negative terms plus five shuffle
-        // additions; a row whose norm enters the bound (m, n >= 1) has L <= 16384
-        // under the point limit, so the relative error stays below 2^-43
+        // G: a lane's sum of about L / 32 <= 4 non-negative terms plus five shuffle
+        // additions, so the relative error stays below 2^-43
         return 0.5f * log2_up(G * (1.0 + 0x1p-40));
     }
-    // multi-word: the 1-norm.  Each |c| <= m32 2^(e - 31) with m32 its top 32 bits
-    // (plus one when lower bits are set) and e its top bit; the terms are summed
-    // in float relative to the row's largest e, rounded up (terms below 2^-100 of
-    // it are raised to 2^-100, which only enlarges the sum)
+    return row_l1_log2_up(coef, P, r, lane, cmax);
+}
+
+// log2 of the 1-norm of row r, rounded up (-inf for a zero row; cmax gets the
+// row's degree).  Each |c| <= m32 2^(e - 31) with m32 its top 32 bits (plus one
+// when lower bits are set) and e its top bit; the terms are summed in float
+// relative to the row's largest e, rounded up (terms below 2^-100 of it are
+// raised to 2^-100, which only enlarges the sum).
+__device__ float row_l1_log2_up(const uint64_t *coef, const PolyDesc &P, int r, int lane, int &cmax) {
+    cmax = -1;
     int emax = -1;
     for (int c = lane; c <= P.cols; c += 32) {
         int e;
@@ -221,7 +231,8 @@ __device__ float row_log2_up(const uint64_t *coef, const PolyDesc &P, int r, int
         }
     }
     for (int o = 16; o; o >>= 1) sum = __fadd_ru(sum, __shfl_xor_sync(0xffffffffu, sum, o));
-    // sum in [1, 2^12): log2f within 1 ulp (below 2^-20), covered by 2^-19
+    // sum in [1, 2^15) (at most 16384 terms of at most 2): log2f within 1 ulp
+    // (at most 2^-20 below 16), covered by 2^-19
     return __fadd_ru((float)emax, __fadd_ru(log2f(sum), 0x1p-19f));
 }
 

@@ -1,7 +1,8 @@
 // Test harness (CPU): the planner's routing helpers of gbr_internal.h as the host
 // sees them - which shapes take the register form (reg_shape), the evaluation
 // point order (point_of), the point sets of the interpolation matrices
-// (vinv_point) and the padded row count of the residue layout (rows4).  Prints
+// (vinv_point), the padded row count of the residue layout (rows4), the size of a
+// root-of-unity point set (root_points) and the point-set choice (roots_pay).  Prints
 // them for a Python checker.  Built and run by test_host_native.py with the CUDA
 // toolkit's include directory (the header declares the launch wrappers).
 #include <cstdio>
@@ -17,5 +18,14 @@ int main() {
         std::printf("pt %d %d %d %d %d %d\n", j, point_of(0, j), point_of(1, j), vinv_point(VINV_SYM, j),
                     vinv_point(VINV_EVEN, j), vinv_point(VINV_ODD, j));
     for (int m = 0; m <= 130; ++m) std::printf("rows4 %d %d\n", m, rows4(m));
+    for (int P = 1; P <= 16384; P += (P < 1100 ? 1 : 97)) std::printf("rootn %d %d\n", P, root_points(P));
+    // the point-set choice for the shapes of the measured crossover: (P, tf, tg, m, n, pairs sharing P)
+    const int cases[][6] = {{401, 231, 231, 20, 20, 4096}, {577, 325, 325, 24, 24, 1024}, {257, 153, 153, 16, 16, 1024},
+                            {8193, 6147, 6147, 2, 2, 8},   {4097, 2307, 2307, 8, 8, 8},   {1025, 585, 585, 8, 8, 8},
+                            {401, 231, 231, 20, 20, 8},    {16001, 12003, 12003, 2, 2, 4000}};
+    for (auto &c : cases)
+        std::printf("roots %d %d %d %d %d %d %d %d\n", c[0], c[1], c[2], c[3], c[4], c[5],
+                    (int)roots_pay(c[0], root_points(c[0]), c[1], c[2], c[3], c[4], c[5], true, true),
+                    (int)roots_pay(c[0], root_points(c[0]), c[1], c[2], c[3], c[4], c[5], true, false));
     return 0;
 }

@@ -119,19 +119,28 @@ def test_results_wider_than_1280_limbs(ctx):
 
 def test_x_degree_bound_near_the_point_limit(ctx):
     """D = 16000 (16001 of the 16384 points) with leading coefficients of degree
-    4000: the default symmetric points and the drop mode (Newton interpolation on
+    4000: the default choice (roots of unity, N = 16384, inverse transform), the
+    symmetric integer points (Newton interpolation) and the drop mode (Newton on
     the integer grid with 8000 spare points) give the same result."""
-    from paper_1103_4697_gb300.native import OPT_DROP_UNLUCKY
+    from paper_1103_4697_gb300.native import OPT_DROP_UNLUCKY, OPT_POINTS, OPT_STATS
 
     rng = random.Random(84)
     f, g = _rows(rng, 2, 4000, 3), _rows(rng, 2, 4000, 3)
+    ctx.set_option(OPT_STATS, 1)
     r0 = ctx.resultant(f, g)
+    assert ctx.stats()["root_pairs"] == 1
+    ctx.set_option(OPT_POINTS, 1)
+    try:
+        r2 = ctx.resultant(f, g)
+        assert ctx.stats()["root_pairs"] == 0
+    finally:
+        ctx.set_option(OPT_POINTS, 0)
     ctx.set_option(OPT_DROP_UNLUCKY, 1)
     try:
         r1 = ctx.resultant(f, g)
     finally:
         ctx.set_option(OPT_DROP_UNLUCKY, 0)
-    assert r0 == r1
+    assert r0 == r1 == r2
     assert len(r0) - 1 <= 16000
     for a in _points(f, g, [0, 1, -1, 7, rng.randint(-10 ** 6, 10 ** 6)]):
         assert _ev(r0, a) == O.res_at_prs(f, g, a)

@@ -144,15 +144,16 @@ def test_roots_resident_graph_replay(ctx):
 
 def test_automatic_choice_and_drop_mode():
     """GBR_OPT_POINTS = 0 picks roots of unity for pairs whose interpolation dominates
-    (small y-degree, large x-degree bound) and integer points for the degree-20 pairs;
-    drop mode keeps the integer grid even when roots are forced; results agree."""
+    (small y-degree, large x-degree bound) and integer points for a full tile of
+    degree-20 pairs; drop mode keeps the integer grid even when roots are forced;
+    results agree."""
     from paper_1103_4697_gb300 import native as N
     from paper_1103_4697_gb300.api import Context
 
     rng = random.Random(11)
     long_f = [_sparse_long(rng, 2, 2000, 10) for _ in range(4)]
     long_g = [_sparse_long(rng, 2, 2000, 10) for _ in range(4)]
-    F, G = W.deg20_batch_arrays(8)
+    F, G = W.deg20_batch_arrays(128)
     with Context(device=0, mem_budget=8 << 30) as c:
         c.set_option(N.OPT_STATS, 1)
         auto_long = c.resultant_batch(long_f, long_g)
@@ -163,7 +164,7 @@ def test_automatic_choice_and_drop_mode():
         assert c.resultant_batch(long_f, long_g) == auto_long
         c.set_option(N.OPT_POINTS, 2)
         assert c.resultant_batch(F, G) == auto_d20
-        assert c.stats()["root_pairs"] == 8
+        assert c.stats()["root_pairs"] == 128
         c.set_option(N.OPT_DROP_UNLUCKY, 1)
         assert c.resultant_batch(F[:2], G[:2]) == auto_d20[:2]
         assert c.stats()["root_pairs"] == 0

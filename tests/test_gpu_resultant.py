@@ -238,8 +238,9 @@ def test_interpolation_contraction_matches_newton(ctx):
     contraction; with different coefficient sizes (so different prime counts) in one
     group and a ragged number of pairs.  Newton interpolation must agree, and both
     must equal the oracle."""
-    from paper_1103_4697_gb300.native import OPT_INTERP_GEMM
+    from paper_1103_4697_gb300.native import OPT_INTERP_GEMM, OPT_POINTS
 
+    ctx.set_option(OPT_POINTS, 1)          # integer points: the routes under test
     fs, gs = [], []
     for i in range(37):
         bits = 8 if i % 2 else 40
@@ -252,6 +253,7 @@ def test_interpolation_contraction_matches_newton(ctx):
         newton = ctx.resultant_batch(fs, gs)
     finally:
         ctx.set_option(OPT_INTERP_GEMM, 1)
+        ctx.set_option(OPT_POINTS, 0)
     assert got == newton
     for f, g, r in zip(fs, gs, got):
         assert r == list(O.res_bareiss(f, g))
@@ -263,8 +265,9 @@ def test_tensor_core_contraction_matches_integer_pipes(ctx):
     odd and even (a symmetric set one point larger), 150 pairs sharing one count
     (two pair tiles), and a count above the tensor-core limit in the same batch:
     the results equal those of the integer-pipe contraction and the oracle."""
-    from paper_1103_4697_gb300.native import OPT_INTERP_TC
+    from paper_1103_4697_gb300.native import OPT_INTERP_TC, OPT_POINTS
 
+    ctx.set_option(OPT_POINTS, 1)          # integer points: the routes under test
     fs, gs = [], []
     for i in range(150):                              # P = 17: two tiles of 128 pairs
         f, g = W.small_dense_pair(900 + i, 4, 12)
@@ -280,6 +283,7 @@ def test_tensor_core_contraction_matches_integer_pipes(ctx):
         ref = ctx.resultant_batch(fs, gs)
     finally:
         ctx.set_option(OPT_INTERP_TC, 1)
+        ctx.set_option(OPT_POINTS, 0)
     assert got == ref
     for q in (0, 77, 149, 150, 151):
         assert got[q] == list(O.res_bareiss(fs[q], gs[q]))

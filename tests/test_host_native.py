@@ -506,7 +506,9 @@ def test_routing_helpers(tmp_path):
     """reg_shape sends exactly the shapes (N, N), (N, N-1), (N-1, N) with 2 <= N <= 32
     to the register form; the symmetric points run 0, +1, -1, +2, -2, ... (the
     unit grid otherwise); the even and odd interpolation matrices use the points
-    j^2 and (j + 1)^2; rows4 pads m + 1 rows to a multiple of 4."""
+    j^2 and (j + 1)^2; rows4 pads m + 1 rows to a multiple of 4; a root-of-unity set
+    has the next power of two (at least 64) points, and the point-set choice follows
+    the measured crossover on its shapes."""
     nvcc = shutil.which("nvcc")
     cuda = os.environ.get("CUDA_HOME") or (os.path.dirname(os.path.dirname(nvcc)) if nvcc else "")
     inc = os.path.join(cuda, "include")
@@ -514,11 +516,24 @@ def test_routing_helpers(tmp_path):
         pytest.skip("CUDA headers not found")
     exe = _build(tmp_path, "routing_harness.cpp", ["-I", inc])
     out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.splitlines()
-    seen = {"reg": 0, "pt": 0, "rows4": 0}
+    seen = {"reg": 0, "pt": 0, "rows4": 0, "rootn": 0, "roots": 0}
+    # expected point-set choice per crossover shape: degree-20 and -24 batches and full
+    # tiles stay on integer points; small batches, long rows and point counts above the
+    # cached contraction's range take roots of unity; without the contraction, always roots
+    want_roots = {(401, 4096): 0, (577, 1024): 0, (257, 1024): 0, (8193, 8): 1, (4097, 8): 1, (1025, 8): 1,
+                  (401, 8): 1, (16001, 4000): 1}
     for line in out:
         t = line.split()
         seen[t[0]] += 1
         v = [int(x) for x in t[1:]]
+        if t[0] == "rootn":
+            P, N = v
+            assert N >= max(64, P) and N & (N - 1) == 0 and (N == 64 or N // 2 < P), line
+            continue
+        if t[0] == "roots":
+            P, tf, tg, m, n, share, auto, nogemm = v
+            assert auto == want_roots[(P, share)] and nogemm == 1, line
+            continue
         if t[0] == "reg":
             m, n, N = v
             top = max(m, n)
@@ -531,7 +546,8 @@ def test_routing_helpers(tmp_path):
         else:
             m, r = v
             assert r % 4 == 0 and m + 1 <= r < m + 5, line
-    assert seen == {"reg": 41 * 41, "pt": 64, "rows4": 131}
+    assert seen["reg"] == 41 * 41 and seen["pt"] == 64 and seen["rows4"] == 131 and seen["roots"] == 8
+    assert seen["rootn"] > 1100
 
 
 def test_host_constant_tables(tmp_path):
