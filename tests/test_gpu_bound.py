@@ -108,12 +108,18 @@ def _check(plans, exact, jobs):
         for p in table[:pl["primes"]]:
             M *= p
         assert log2_floor_half_pred(M) > hi, (q, pl["primes"], float(hi))
-        # with every coefficient below 2^56 the device sums the same row quantities
-        # exactly, so its bound may exceed the exact one only by its rounding margins
-        if _max_bits(jobs[q]) <= 56:
+        # with every coefficient below 2^56 and rows of at most 128 coefficients the
+        # device sums the same row quantities exactly (longer rows take the 1-norm), so
+        # its bound may exceed the exact one only by its rounding margins
+        if _max_bits(jobs[q]) <= 56 and _max_row(jobs[q]) <= 128:
             slack = 0.01 + 0.002 * (pl["m"] + pl["n"]) + 2 ** -9
             assert pl["log2_bound"] <= float(hi) + slack, (q, pl["log2_bound"], float(hi))
     return len(plans)
+
+
+def _max_row(job):
+    polys = job if isinstance(job, tuple) else (job,)
+    return max(len(row) for p in polys for row in p)
 
 
 def _max_bits(job):
