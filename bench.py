@@ -296,7 +296,7 @@ def _pow_cost(e: int) -> int:
 
 
 @functools.lru_cache(maxsize=None)
-def regform_ops(m: int, n: int, tf: int, tg: int, p: int) -> dict:
+def regform_ops(m: int, n: int, tf: int, tg: int, p: int, seg: int = 512) -> dict:
     """Operations the register-form kernel executes for one (prime, point) subproblem of
     a pair of y-degrees (m, n) in one of its shapes (N, N), (N, N-1), (N-1, N), counted
     from its code: the evaluation's Horner steps in Shoup form ((tf + tg) / 2 per point,
@@ -304,10 +304,12 @@ def regform_ops(m: int, n: int, tf: int, tg: int, p: int) -> dict:
     the combine E + i O (one product per row and point); elimination: for (N, N) the
     first multiply-subtract row and alpha^N, then N - 1 normal rounds (round of degree d:
     one fused two-product and d - 1 fused three-product updates, and the scalars z^2,
-    z alpha, q0, Q z^2 and, after the first round, the telescoped divisor), the final
-    products and the Fermat inverse x^(p-2)."""
+    z alpha, q0, Q z^2 and, after the first round, the telescoped divisor), the two
+    final products of numerator and denominator; then the batch inversion that forms
+    the quotient (four products per value, and per segment of `seg` values the scans
+    and one Fermat inverse x^(p-2))."""
     N = max(m, n)
-    mul = (m + n + 2) / 2 + 3 + _pow_cost(p - 2)
+    mul = (m + n + 2) / 2 + 2 + 4 + (12 + _pow_cost(p - 2)) / seg
     mulsub, fma2, fma3 = 0, 0, 0
     if m == n:
         mulsub += N
@@ -345,7 +347,7 @@ def evalres_roofline(F, G, plans: list[dict], table: list[int], cal: dict) -> di
         (m, tf), (n, tg) = shapes
         textbook += len(primes) * points * (tf + tg + 2 * m * n)
         for p in primes:
-            for k, v in regform_ops(m, n, tf, tg, p).items():
+            for k, v in regform_ops(m, n, tf, tg, p, min(points, 512)).items():
                 ops[k] += v * points
     products = ops["shoup"] + ops["mul"] + 2 * ops["mulsub"] + 3 * ops["fma3"]
     ideal_s = (ops["shoup"] / cal["shoup_per_s"] + ops["mul"] / cal["modmul_per_s"]

@@ -1058,7 +1058,8 @@ extern "C" int gbr_upload_arrangement(gbr_ctx *c, int n, const gbr_bipoly *f, in
 void gbr_free_resident_locked(gbr_ctx *c, gbr_resident *r) {
     if (!r) return;
     for (void *p : {(void *)r->d_coef, (void *)r->d_desc, (void *)r->d_rowdeg, (void *)r->d_bounds, (void *)r->d_deg,
-                    (void *)r->d_planblk, (void *)r->d_res, (void *)r->d_val, (void *)r->d_cf, (void *)r->d_out,
+                    (void *)r->d_planblk, (void *)r->d_res, (void *)r->d_val, (void *)r->d_den, (void *)r->d_cf,
+                    (void *)r->d_out,
                     (void *)r->d_sign, (void *)r->d_flags, (void *)r->d_gtab, (void *)r->d_redo})
         c->dfree(p);
     if (r->gexec) cudaGraphExecDestroy(r->gexec);
@@ -1276,7 +1277,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     int Kmax = 1, Pmax = 1, Lmax = 1, Kdig = 1;   // Kdig: most primes of one pair
     int Puse = 1;   // most points one interpolation uses (Pmax also counts the spare points)
     int Nntt = 1;   // largest transform of the root-of-unity pairs
-    HostList red, interp, crt, crtf, ntt;
+    HostList red, interp, crt, crtf, ntt, binv;
     int Kdig_f = 1, Lmax_f = 1;
     // evaluation buckets by y-degree (key / 4), register-form buckets by N, and
     // contraction groups by (points, symmetric): flat tables in ascending key order
@@ -1347,6 +1348,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
             crt.add(q, p.P);
         }
         subproblems += (int64_t)k * p.Pe;
+        binv.add(q, (int64_t)k * ((p.Pe + kInvSegment - 1) / kInvSegment));
         int64_t ev = (int64_t)k * (p.sym == PTS_ROOTS ? p.Pe : p.P) * (b.tf + b.tg + 2LL * p.m * p.n);
         st.modmul_evalres += ev;
         st.modmul += ev + (int64_t)k * p.P * (p.P - 1) + (int64_t)p.P * k * (k - 1) / 2;
@@ -1439,6 +1441,8 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     put_list(blk, interp, o_int_p, o_int_s);
     size_t o_ntt_p, o_ntt_s;
     put_list(blk, ntt, o_ntt_p, o_ntt_s);
+    size_t o_binv_p, o_binv_s;
+    put_list(blk, binv, o_binv_p, o_binv_s);
     put_list(blk, crt, o_crt_p, o_crt_s);
     size_t o_crtf_p, o_crtf_s;
     put_list(blk, crtf, o_crtf_p, o_crtf_s);
@@ -1512,6 +1516,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     if (ensure_buf(c, (void **)&r->d_planblk, &r->planblk_cap, blk.size()) ||
         ensure_buf(c, (void **)&r->d_res, &r->res_cap, res_w * 4) ||
         ensure_buf(c, (void **)&r->d_val, &r->val_cap, val_w * 4) ||
+        ensure_buf(c, (void **)&r->d_den, &r->den_cap, val_w * 4) ||
         ensure_buf(c, (void **)&r->d_cf, &r->cf_cap, cf_w * 4) ||
         ensure_buf(c, (void **)&r->d_flags, &r->flags_cap, flag_b) ||
         ensure_buf(c, (void **)&r->d_gtab, &r->gtab_cap, gtab_w * 4) ||
@@ -1539,6 +1544,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     L.invk_T = c->invk_T;
     L.res = r->d_res;
     L.val = r->d_val;
+    L.den = r->d_den;
     L.cf = r->d_cf;
     L.out = r->d_out;
     L.sign = r->d_sign;
@@ -1642,6 +1648,10 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
             roff += kv.second.total / 32;
             ++ri;
         }
+        if (x == cudaSuccess && binv.total > 0) {
+            x = launch_batch_inv(L, mk(o_binv_p, o_binv_s, binv), q);
+            kernels++;
+        }
         record(3, capturing, q);
         if (x == cudaSuccess && interp.total > 0) {
             x = launch_interp(L, mk(o_int_p, o_int_s, interp), Puse, q);
@@ -1677,6 +1687,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     if (c->graph_on && !r->oneshot) {
         // the plan block, every buffer and table pointer and the launch shapes fix the graph
         std::vector<uintptr_t> key = {(uintptr_t)r->d_planblk, (uintptr_t)r->d_res, (uintptr_t)r->d_val,
+                                      (uintptr_t)r->d_den,
                                       (uintptr_t)r->d_cf,      (uintptr_t)r->d_out, (uintptr_t)r->d_sign,
                                       (uintptr_t)r->d_deg,     (uintptr_t)r->d_flags, (uintptr_t)r->d_gtab,
                                       (uintptr_t)r->d_redo,

@@ -130,8 +130,8 @@ struct gbr_resident {
     std::vector<char> h_blk;            // host copy of the last plan block (storage reused)
     char *d_planblk = nullptr;
     size_t planblk_cap = 0;
-    uint32_t *d_res = nullptr, *d_val = nullptr, *d_cf = nullptr, *d_out = nullptr;
-    size_t res_cap = 0, val_cap = 0, cf_cap = 0, out_cap = 0;
+    uint32_t *d_res = nullptr, *d_val = nullptr, *d_cf = nullptr, *d_out = nullptr, *d_den = nullptr;
+    size_t res_cap = 0, val_cap = 0, cf_cap = 0, out_cap = 0, den_cap = 0;
     int8_t *d_sign = nullptr;
     size_t sign_cap = 0;
     uint8_t *d_flags = nullptr;

@@ -166,9 +166,11 @@ GBR_HD void chain_round(uint32_t (&U)[N + 1], const uint32_t (&V)[N + 1], const 
     }
 }
 
+// The register form as a fraction: the resultant is num / den (den != 0; den = 1
+// in Montgomery form when num = 0), so that the caller can batch the inversions.
 template <int N>
-GBR_HD uint32_t res_chain(const uint32_t (&F)[N + 1], const uint32_t (&G)[N + 1], int m, int n, const ModP &M,
-                          bool &ok) {
+GBR_HD uint32_t res_chain_frac(const uint32_t (&F)[N + 1], const uint32_t (&G)[N + 1], int m, int n, const ModP &M,
+                               bool &ok, uint32_t &den_out) {
     static_assert(N >= 2, "the register form starts at degree 2");
     const bool sw = m != N;   // (N-1, N): solve res(G, F)
     const int nb = sw ? m : n;
@@ -179,6 +181,7 @@ GBR_HD uint32_t res_chain(const uint32_t (&F)[N + 1], const uint32_t (&G)[N + 1]
         B[k] = sw ? F[k] : G[k];
     }
     ok = false;
+    den_out = M.r1;
     // (a constant index keeps B in registers)
     if (A[N] == 0u || (nb == N ? B[N] : B[N - 1]) == 0u) return 0u;   // a leading coefficient vanishes here
     uint32_t acc = M.r1, den = M.r1, Dq = M.r1, Q = M.r1;
@@ -207,8 +210,16 @@ GBR_HD uint32_t res_chain(const uint32_t (&F)[N + 1], const uint32_t (&G)[N + 1]
     if (done) return 0u;   // ok tells a zero resultant from a sequence that is not normal
     const uint32_t c = ((N - 2) % 2 == 0) ? A[0] : B[0];   // the last remainder, a constant
     acc = mp_mul(acc, c, M);
-    den = mp_mul(den, Dq, M);
-    return mp_mul(acc, mp_inv(den, M), M);
+    den_out = mp_mul(den, Dq, M);
+    return acc;
+}
+
+template <int N>
+GBR_HD uint32_t res_chain(const uint32_t (&F)[N + 1], const uint32_t (&G)[N + 1], int m, int n, const ModP &M,
+                          bool &ok) {
+    uint32_t den;
+    const uint32_t num = res_chain_frac<N>(F, G, m, n, M, ok, den);
+    return mp_mul(num, mp_inv(den, M), M);
 }
 
 }  // namespace gbr

@@ -4,7 +4,8 @@
 // are evaluated at the point (Horner, or even/odd parts at i^2 for the
 // symmetric points +-i in lane pairs), then res_{m,n}(F, G) over F_p with the
 // formal degrees is computed in shared memory by fraction-free remainder
-// steps.  Persistent grid-stride launch per degree bucket.
+// steps.  Persistent grid-stride launch per degree bucket.  Each value is
+// written as a numerator and a denominator; k_batch_inv forms the quotients.
 #include "gbr_device.cuh"
 #include "gbr_elim.cuh"
 
@@ -149,7 +150,10 @@ __device__ __forceinline__ void evalres_item(const ResLaunch &L, const WorkList 
         uint32_t *other = own + (glane ? -16 : 16);
         for (int r0 = 0; r0 < nrows; r0 += 4) eval4_sym(rc, r4, dg, nrows, r0, a, b, glane, M, own, other, BS);
         __syncwarp();
-        if (j >= 0 && j < P.Pe) L.val[P.val_off + (int64_t)i * P.Pe + j] = res_formal(Fs, P.m, Gs, P.n, BS, M);
+        if (j >= 0 && j < P.Pe) {
+            L.val[P.val_off + (int64_t)i * P.Pe + j] = res_formal(Fs, P.m, Gs, P.n, BS, M);
+            L.den[P.val_off + (int64_t)i * P.Pe + j] = M.r1;
+        }
         __syncwarp();
         return;
     }
@@ -170,6 +174,7 @@ __device__ __forceinline__ void evalres_item(const ResLaunch &L, const WorkList 
         if (unlucky) atomicAdd(L.dropped, 1ull);
     }
     L.val[P.val_off + (int64_t)i * P.Pe + j] = res_formal(Fs, P.m, Gs, P.n, BS, M);
+    L.den[P.val_off + (int64_t)i * P.Pe + j] = M.r1;
 }
 
 __global__ void k_evalres(ResLaunch L, WorkList w, int SF, int SG) {
@@ -285,12 +290,15 @@ __global__ void __launch_bounds__(256, reg_min_blocks(N)) k_evalres_reg(ResLaunc
             G[k] = glane ? own[k] : got;
         }
         bool ok;
-        const uint32_t v = res_chain<N>(F, G, P.m, P.n, M, ok);
+        uint32_t den;
+        const uint32_t v = res_chain_frac<N>(F, G, P.m, P.n, M, ok, den);
         const bool valid = j >= 0 && j < P.Pe;
         if (__ballot_sync(0xffffffffu, valid && !ok)) {
             if (lane == 0) redo[atomicAdd(redo_n, 1ull)] = item;
         } else if (valid) {
+            // the quotient v / den: k_batch_inv divides once the whole segment is in
             L.val[P.val_off + (int64_t)i * P.Pe + j] = v;
+            L.den[P.val_off + (int64_t)i * P.Pe + j] = den;
         }
     }
 }
@@ -306,6 +314,70 @@ __global__ void k_evalres_redo(ResLaunch L, WorkList w, int SF, const unsigned l
     const int lane = threadIdx.x & 31;
     for (int64_t e = (blockIdx.x * (int64_t)BS + threadIdx.x) >> 5; e < nw; e += ((int64_t)gridDim.x * BS) >> 5)
         evalres_item(L, w, redo[e] + lane, Fs, Gs, BS);
+}
+
+// The quotients of the register form (written as numerator and denominator by
+// k_evalres_reg): one warp per (pair, prime, segment of kInvSeg values), Montgomery's
+// batch inversion - the prefix products of the segment's denominators, one Fermat
+// inverse of their product, then every inverse from a prefix and a suffix - so
+// that a segment pays about four products per value instead of one inverse each.
+// Entries written by the other evaluation kernels carry the denominator 1 (R in
+// Montgomery form).
+constexpr int kInvSeg = kInvSegment;   // values per warp: 16 per lane, interleaved for coalescing
+
+__global__ void __launch_bounds__(256) k_batch_inv(ResLaunch L, WorkList w) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t item = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; item < w.total;
+         item += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int bi = wl_find(w.start, w.n, item);
+        const PairPlan &P = L.plan[w.pairs[bi]];
+        const int64_t local = item - w.start[bi];
+        const int nseg = (P.Pe + kInvSeg - 1) / kInvSeg;
+        const int i = (int)(local / nseg), sg = (int)(local % nseg);
+        const ModP M = L.mods[prime_of(P, L.pmap, i)];
+        const int64_t base = P.val_off + (int64_t)i * P.Pe + (int64_t)sg * kInvSeg;
+        const int cnt = min(kInvSeg, P.Pe - sg * kInvSeg);
+        uint32_t d[kInvSeg / 32], pre[kInvSeg / 32];
+        uint32_t run = M.r1;
+#pragma unroll
+        for (int u = 0; u < kInvSeg / 32; ++u) {
+            const int t = u * 32 + lane;
+            d[u] = t < cnt ? L.den[base + t] : M.r1;
+            run = mp_mul(run, d[u], M);
+            pre[u] = run;   // d[0] ... d[u]
+        }
+        // products of the lanes' runs: inclusive prefix, suffix, and the whole segment
+        uint32_t incl = run, suf = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t a = __shfl_up_sync(0xffffffffu, incl, o);
+            const uint32_t b = __shfl_down_sync(0xffffffffu, suf, o);
+            if (lane >= o) incl = mp_mul(incl, a, M);
+            if (lane + o < 32) suf = mp_mul(suf, b, M);
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        uint32_t before = __shfl_up_sync(0xffffffffu, incl, 1);
+        uint32_t after = __shfl_down_sync(0xffffffffu, suf, 1);
+        if (lane == 0) before = M.r1;
+        if (lane == 31) after = M.r1;
+        // 1 / (this lane's run) = (1 / total) (runs of the other lanes)
+        uint32_t inv = mp_mul(mp_mul(mp_inv(total, M), before, M), after, M);
+#pragma unroll
+        for (int u = kInvSeg / 32 - 1; u >= 0; --u) {
+            const int t = u * 32 + lane;
+            const uint32_t id = u > 0 ? mp_mul(inv, pre[u - 1], M) : inv;   // 1 / d[u]
+            if (t < cnt) L.val[base + t] = mp_mul(L.val[base + t], id, M);
+            inv = mp_mul(inv, d[u], M);
+        }
+    }
+}
+
+cudaError_t launch_batch_inv(const ResLaunch &L, const WorkList &w, cudaStream_t s) {
+    if (w.total <= 0) return cudaSuccess;
+    const int block = 256;
+    const int grid = persistent_grid(k_batch_inv, block, 0, (w.total * 32 + block - 1) / block);
+    k_batch_inv<<<grid, block, 0, s>>>(L, w);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_evalres(const ResLaunch &L, const WorkList &w, int SF, int SG, int block, cudaStream_t s) {

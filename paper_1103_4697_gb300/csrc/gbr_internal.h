@@ -268,7 +268,9 @@ struct ResLaunch {
     const uint32_t *invk;        // [prime][invk_T] inverses of 1..T-1
     int32_t invk_T;
     uint32_t *res;               // residues
-    uint32_t *val;               // values R(a) mod p at the points (Montgomery form)
+    uint32_t *val;               // values R(a) mod p at the points (Montgomery form; numerators until
+                                 // k_batch_inv divides them by den)
+    uint32_t *den;               // denominators of the values (Montgomery form, non-zero), same layout
     uint32_t *cf;                // coefficients of R mod p (normal form), same offsets as val
     uint32_t *out;               // output magnitudes
     int8_t *sign;                // output signs
@@ -328,6 +330,10 @@ GBR_HD int reg_shape(int m, int n) {
 cudaError_t launch_evalres_reg(const ResLaunch &L, const WorkList &w, int N, int block, unsigned long long *redo_n,
                                int64_t *redo, cudaStream_t s);
 cudaError_t launch_interp(const ResLaunch &L, const WorkList &w, int maxP, cudaStream_t s);
+// values = numerators / denominators, one warp per (pair, prime, segment of
+// kInvSegment values) of the work list (Montgomery's batch inversion)
+constexpr int kInvSegment = 512;
+cudaError_t launch_batch_inv(const ResLaunch &L, const WorkList &w, cudaStream_t s);
 // inverse transform for PTS_ROOTS pairs (one item per (pair, prime)); maxN = largest Pe
 cudaError_t launch_interp_ntt(const ResLaunch &L, const WorkList &w, int maxN, cudaStream_t s);
 cudaError_t configure_interp_ntt_kernel();

@@ -69,7 +69,9 @@ static size_t estimate_bytes(const ServeJob &j) {
     int64_t P = info.deg_bound + 1, k = info.primes, L = info.limbs;
     int64_t S = (int64_t)(info.m + 1 + info.n + 1) * (std::max(j.f.deg_x, j.f.deg_y) + 1);
     int64_t in = (int64_t)j.a.size() * 8 + (int64_t)j.b.size() * 8;
-    return (size_t)(k * S * 4 + k * P * 4 + P * L * 4 + P + in + 8192);
+    // residues, values and their denominators (up to 2 P points on roots of unity),
+    // coefficients mod p, output limbs
+    return (size_t)(k * S * 4 + 5 * k * P * 4 + P * L * 4 + P + in + 8192);
 }
 
 // marks j finished (caller holds S->mu) and queues its ticket for gbr_wait_any
