@@ -1488,15 +1488,27 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
         gg.npairs = gm.npairs;
         gg.mode = gm.mode;
         ggroups.push_back(gg);
-        if (gm.vtc) {
-            for (int i = 0; i < gm.K; ++i)
-                for (int c0 = 0; c0 < gm.rows; c0 += kTcTileM)
-                    for (int q0 = 0; q0 < gm.npairs; q0 += kTcTileN) ttiles.push_back({(int32_t)gi, c0, q0, i});
-        } else {
-            for (int i = 0; i < gm.K; ++i)
-                for (int c0 = 0; c0 < gm.rows; c0 += kGemmTileM)
-                    for (int q0 = 0; q0 < gm.npairs; q0 += kGemmTileN) gtiles.push_back({(int32_t)gi, c0, q0, i});
-        }
+    }
+    // tiles prime by prime; the even and odd contractions of one symmetric group are
+    // interleaved per prime, so both read the prime's values while they are in L2 and
+    // both halves of each 32-byte coefficient sector are written close together
+    for (size_t gi = 0; gi < gemms.size();) {
+        const size_t span = gemms[gi].mode == GEMM_EVEN && gi + 1 < gemms.size() && gemms[gi + 1].mode == GEMM_ODD &&
+                                    gemms[gi + 1].off == gemms[gi].off
+                                ? 2
+                                : 1;
+        for (int i = 0; i < gemms[gi].K; ++i)
+            for (size_t g = gi; g < gi + span; ++g) {
+                const Gemm &gm = gemms[g];
+                if (gm.vtc) {
+                    for (int c0 = 0; c0 < gm.rows; c0 += kTcTileM)
+                        for (int q0 = 0; q0 < gm.npairs; q0 += kTcTileN) ttiles.push_back({(int32_t)g, c0, q0, i});
+                } else {
+                    for (int c0 = 0; c0 < gm.rows; c0 += kGemmTileM)
+                        for (int q0 = 0; q0 < gm.npairs; q0 += kGemmTileN) gtiles.push_back({(int32_t)g, c0, q0, i});
+                }
+            }
+        gi += span;
     }
     size_t o_ggroups = (blk.size() + 15) / 16 * 16;
     blk.resize(o_ggroups + ggroups.size() * sizeof(GemmGroup) + 16);

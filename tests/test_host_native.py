@@ -656,3 +656,31 @@ def test_device_prime_table_bytes(tmp_path):
         for j in range(128):
             assert vals[j] == pow(w, j, p) * R % p and vals[128 + j] == pow(w, 128 * j, p) * R % p
     assert size == NP * (16 + 8 + 256 * 4) + (gd_off(K) + L * ROW + L) * 4
+
+
+def test_no_int8_tensor_mma_on_sm103a(tmp_path):
+    """The interpolation contraction uses bf16 digits because GB300 has no int8 MMA:
+    the assembler refuses tcgen05.mma kind::i8 for sm_103a (and accepts it for sm_100a),
+    while kind::f16 (the library's) and kind::f8f6f4 assemble for sm_103a."""
+    nvcc = shutil.which("nvcc")
+    if not nvcc:
+        pytest.skip("nvcc not available")
+    src = tmp_path / "mma_kinds.cu"
+
+    def kernel(kind):
+        return ('__global__ void k_%s(unsigned d, unsigned long long a, unsigned long long b, unsigned i, '
+                'unsigned c) { asm volatile("{\\n\\t.reg .pred p;\\n\\tsetp.ne.u32 p, %%4, 0;\\n\\t'
+                'tcgen05.mma.cta_group::1.kind::%s [%%0], %%1, %%2, %%3, p;\\n\\t}" :: "r"(d), "l"(a), "l"(b), '
+                '"r"(i), "r"(c)); }\n' % (kind, kind))
+
+    def assemble(arch, kind):
+        src.write_text(kernel(kind))
+        r = subprocess.run([nvcc, "-gencode", f"arch=compute_{arch},code=sm_{arch}", "-c", str(src), "-o",
+                            str(tmp_path / "k.o")], capture_output=True, text=True)
+        return r.returncode, r.stdout + r.stderr
+
+    rc, out = assemble("103a", "i8")
+    assert rc != 0 and "kind::i8" in out and "not supported" in out, out
+    assert assemble("100a", "i8")[0] == 0
+    assert assemble("103a", "f16")[0] == 0
+    assert assemble("103a", "f8f6f4")[0] == 0
