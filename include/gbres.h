@@ -124,7 +124,10 @@ typedef struct {
     int64_t h2d_bytes, d2h_bytes;
     int64_t dropped_points;   /* GBR_OPT_DROP_UNLUCKY: evaluation points flagged unlucky and replaced */
     int64_t dropped_primes;   /* GBR_OPT_DROP_UNLUCKY: primes skipped because a leading coefficient vanishes */
-    int64_t graph_replayed;   /* 1 when the device stages ran as a CUDA graph (GBR_OPT_GRAPH) */
+    int64_t graph_replayed;   /* 1 when the device stages ran as a CUDA graph (GBR_OPT_GRAPH); 2 when
+                                 the whole step (bounds, a check of the fresh bounds against those
+                                 the plan was made from, stages) ran as one graph with no host
+                                 planning in between */
     int64_t redo_warps;       /* GBR_OPT_REGISTER_FORM: warps of 32 subproblems solved again on
                                  shared memory */
     int64_t root_pairs;       /* pairs evaluated at roots of unity and interpolated by an inverse
@@ -160,7 +163,12 @@ const char *gbr_last_error(gbr_ctx *ctx);
 #define GBR_OPT_STATS        2   /* 1: record per-stage CUDA-event times (gbr_get_stats) */
 #define GBR_OPT_GRAPH        3   /* 1 (default): when a resident batch runs again with an unchanged
                                     plan, its device stages (after the bounds and the plan) are
-                                    captured into a CUDA graph once and replayed from then on */
+                                    captured into a CUDA graph once and replayed; from the fourth
+                                    run on, the whole step is one graph: the bounds kernel, a
+                                    device check that the fresh bounds equal those the plan was
+                                    made from, and the stages (which return at once on a mismatch,
+                                    after which the call plans again and reruns), with no host
+                                    round trip between the bounds and the stages */
 #define GBR_OPT_EXTRA_PRIMES 4   /* add this many primes beyond the bound (tests: k+1 == k) */
 #define GBR_OPT_INTERP_GEMM  5   /* 1 (default): pairs of a batch that share their number of points
                                     are interpolated by one inverse-Vandermonde contraction per

@@ -1063,6 +1063,8 @@ void gbr_free_resident_locked(gbr_ctx *c, gbr_resident *r) {
                     (void *)r->d_sign, (void *)r->d_flags, (void *)r->d_gtab, (void *)r->d_redo})
         c->dfree(p);
     if (r->gexec) cudaGraphExecDestroy(r->gexec);
+    if (r->fexec) cudaGraphExecDestroy(r->fexec);
+    c->dfree(r->d_bref);
     delete r;
 }
 
@@ -1117,6 +1119,36 @@ static void put_list(std::vector<char> &blk, const HostList &h, size_t &off_pair
     if (n) std::memcpy(blk.data() + off_pairs, h.pairs.data(), n * 4);
 }
 
+// What a captured step graph assumes of its context: the options that shape a plan
+// and the tables it reads.
+static std::vector<uintptr_t> step_signature(const gbr_ctx *c) {
+    return {(uintptr_t)c->drop_unlucky, (uintptr_t)c->pts_mode, (uintptr_t)c->extra_primes, (uintptr_t)c->gemm_on,
+            (uintptr_t)c->tc_on,        (uintptr_t)c->reg_on,   (uintptr_t)c->stats_on,     (uintptr_t)c->d_garner,
+            (uintptr_t)c->d_invk,       (uintptr_t)c->d_mods,   (uintptr_t)c->d_err,        (uintptr_t)c->garner_K,
+            (uintptr_t)c->invk_T};
+}
+
+// The step graph may run when the context still matches and every cached
+// inverse-Vandermonde matrix it reads is still cached at the same address
+// (another batch may have evicted it); those matrices are marked as used.
+static bool step_graph_valid(gbr_ctx *c, gbr_resident *r) {
+    if (r->fsig != step_signature(c)) return false;
+    for (const auto &v : r->fvinv) {
+        auto it = c->vinv.find(v.first);
+        if (it == c->vinv.end() || (const void *)it->second.d != v.second.first ||
+            (const void *)it->second.tc != v.second.second)
+            return false;
+    }
+    for (const auto &v : r->fvinv) c->vinv[v.first].last_use = ++c->vinv_clock;
+    return true;
+}
+
+static void drop_step_graph(gbr_resident *r) {
+    if (r->fexec) cudaGraphExecDestroy(r->fexec);
+    r->fexec = nullptr;
+    r->fstate = 0;
+}
+
 int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     const int n = r->n;
     cudaStream_t s = c->stream;
@@ -1126,6 +1158,24 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
         r->ran = true;
         return GBR_OK;
     }
+    // ---- a repeated step: one graph launch (bounds, plan check, stages), no host
+    // planning between the bounds and the stages
+    if (c->graph_on && !r->oneshot && r->fstate == 2 && r->fexec && step_graph_valid(c, r)) {
+        NvtxScope phase("gbr: step graph (A0-A5)");
+        e = cudaGraphLaunch(r->fexec, s);
+        if (e != cudaSuccess) {
+            drop_step_graph(r);
+            return c->fail(GBR_EDEVICE, "step graph launch", e);
+        }
+        r->pend_st = r->fast_st;
+        r->pend_nredo = r->fast_nredo;
+        r->pend_out_w = r->fast_out_w;
+        r->pend_sign_b = r->fast_sign_b;
+        r->fast_pending = true;
+        r->pending = true;
+        return GBR_OK;
+    }
+    r->fast_pending = false;
     if (c->stats_on) cudaEventRecord(c->ev[0], s);
     // ---- A0 (device half): measure degrees and bounds
     NvtxScope phase("gbr: bounds (A0, device)");
@@ -1695,7 +1745,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
         record(5, capturing, q);
         return x;
     };
-    bool replayed = false;
+    bool replayed = false, capture_step = false;
     if (c->graph_on && !r->oneshot) {
         // the plan block, every buffer and table pointer and the launch shapes fix the graph
         std::vector<uintptr_t> key = {(uintptr_t)r->d_planblk, (uintptr_t)r->d_res, (uintptr_t)r->d_val,
@@ -1717,11 +1767,13 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
             r->gkey = key;
             r->gblk = blk;
             r->gstate = 1;
+            drop_step_graph(r);
             e = enqueue(false, s);
         } else if (r->gstate == 2) {
             e = cudaGraphLaunch(r->gexec, s);
             replayed = true;
             kernels = r->graph_kernels;
+            capture_step = e == cudaSuccess && r->fstate != 2;
         } else {
             // the context's stream may be the legacy default stream, which cannot
             // be captured: capture on a private stream, launch on the context's
@@ -1766,6 +1818,56 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     r->pend_out_w = out_w;
     r->pend_sign_b = sign_b;
     r->pending = true;
+    if (capture_step) {
+        // the plan repeated and its stages replay from a graph: capture the whole
+        // step - bounds, the check of the fresh bounds against the ones this plan
+        // was made from, and the stages, which return at once on a mismatch
+        const size_t bb = sizeof(PairBound) * (size_t)n;
+        cudaGraph_t g = nullptr;
+        cudaError_t x = ensure_buf(c, (void **)&r->d_bref, &r->bref_cap, bb) ? cudaErrorMemoryAllocation
+                                                                              : cudaSuccess;
+        if (x == cudaSuccess) x = cudaMemcpyAsync(r->d_bref, r->d_bounds, bb, cudaMemcpyDeviceToDevice, s);
+        if (x == cudaSuccess) x = c->capture_stream_ready();
+        if (x == cudaSuccess) x = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (x == cudaSuccess) {
+            cudaStream_t q = c->cap_stream;
+            int32_t *flag = c->d_err + 4;
+            cudaError_t y = cudaMemsetAsync(flag, 0, sizeof(int32_t), q);
+            if (y == cudaSuccess && c->stats_on) y = cudaEventRecordWithFlags(c->ev[0], q, cudaEventRecordExternal);
+            if (y == cudaSuccess) y = launch_bounds(L, q);
+            if (y == cudaSuccess) y = launch_plan_check(r->d_bounds, r->d_bref, n, flag, q);
+            L.skip = flag;
+            if (y == cudaSuccess) y = enqueue(true, q);
+            L.skip = nullptr;
+            x = cudaStreamEndCapture(q, &g);
+            if (y != cudaSuccess) x = y;
+        }
+        if (x == cudaSuccess) x = cudaGraphInstantiate(&r->fexec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (x == cudaSuccess) {
+            r->fstate = 2;
+            r->fsig = step_signature(c);
+            r->fvinv.clear();
+            for (const Gemm &gm : gemms) {
+                for (const auto &kv : c->vinv)
+                    if ((const void *)kv.second.d == (const void *)gm.vinv)
+                        r->fvinv.push_back({kv.first, {(const void *)kv.second.d, (const void *)kv.second.tc}});
+            }
+            r->fast_st = st;
+            r->fast_st.kernels = kernels + 2;
+            r->fast_st.graph_replayed = 2;
+            r->fast_st.h2d_bytes = 0;
+            r->fast_st.d2h_bytes = 20;
+            r->fast_nredo = (int)evr.size();
+            r->fast_out_w = out_w;
+            r->fast_sign_b = sign_b;
+        } else {
+            // not fatal: later runs keep the plan-then-replay path
+            r->fexec = nullptr;
+            r->fstate = 0;
+            cudaGetLastError();
+        }
+    }
     return GBR_OK;
 }
 
@@ -1775,13 +1877,28 @@ int gbr_run_resident_finish(gbr_ctx *c, gbr_resident *r) {
     r->pending = false;
     cudaStream_t s = c->stream;
     gbr_stats st = r->pend_st;
-    int32_t herr[4] = {0, 0, 0, 0};
+    int32_t herr[5] = {0, 0, 0, 0, 0};
     std::vector<unsigned long long> hredo(r->pend_nredo);
-    cudaError_t e = cudaMemcpyAsync(herr, c->d_err, 16, cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaMemcpyAsync(herr, c->d_err, 20, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && r->pend_nredo)
         e = cudaMemcpyAsync(hredo.data(), r->d_redo, 8 * (size_t)r->pend_nredo, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return c->fail(GBR_EDEVICE, "resultant stages", e);
+    if (r->fast_pending && herr[4]) {
+        // the step graph found bounds that differ from its plan's and skipped its
+        // stages: plan again (plainly) and run
+        r->fast_pending = false;
+        drop_step_graph(r);
+        r->gstate = 0;
+        r->gkey.clear();
+        int st2 = gbr_run_resident_launch(c, r);
+        if (st2) {
+            r->pending = false;
+            return st2;
+        }
+        return gbr_run_resident_finish(c, r);
+    }
+    r->fast_pending = false;
     if (herr[0] == kErrTensorStall)
         return c->fail(GBR_EDEVICE, "tensor-core interpolation stalled (a bounded wait gave up; no results written)");
     if (herr[0]) return c->fail(GBR_EDEVICE, "device-side consistency check failed");

@@ -148,6 +148,19 @@ struct gbr_resident {
     int64_t graph_kernels = 0;
     std::vector<uintptr_t> gkey;        // pointers and launch shapes of the captured plan
     std::vector<char> gblk;             // plan block of the captured plan
+    // the whole step as one graph (bounds, plan check, stages), captured once the
+    // stage graph has replayed: later runs launch it with no host planning in
+    // between; the stages return at once if the fresh bounds differ from d_bref
+    cudaGraphExec_t fexec = nullptr;
+    int fstate = 0;                     // 0 none, 2 captured and valid for fsig
+    gbr::PairBound *d_bref = nullptr;   // the bounds the current plan was made from
+    size_t bref_cap = 0;
+    std::vector<uintptr_t> fsig;        // options and table pointers the step graph assumes
+    std::vector<std::pair<int64_t, std::pair<const void *, const void *>>> fvinv;   // cached matrices it reads
+    gbr_stats fast_st{};
+    int fast_nredo = 0;
+    int64_t fast_out_w = 0, fast_sign_b = 0, fast_kernels = 0;
+    bool fast_pending = false;          // the pending run is a step-graph launch
     // launched but not yet finished (gbr_run_resident_launch / _finish)
     bool pending = false;
     gbr_stats pend_st{};

@@ -178,6 +178,7 @@ __device__ __forceinline__ void evalres_item(const ResLaunch &L, const WorkList 
 }
 
 __global__ void k_evalres(ResLaunch L, WorkList w, int SF, int SG) {
+    if (stage_skipped(L)) return;
     extern __shared__ uint32_t smem[];
     const int BS = blockDim.x;
     uint32_t *Fs = smem + threadIdx.x;
@@ -200,6 +201,7 @@ constexpr int reg_min_blocks(int N) { return N <= 20 ? 3 : N <= 27 ? 2 : 1; }
 template <int N>
 __global__ void __launch_bounds__(256, reg_min_blocks(N)) k_evalres_reg(ResLaunch L, WorkList w, unsigned long long *redo_n,
                                                      int64_t *redo) {
+    if (stage_skipped(L)) return;
     for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < w.total;
          item += (int64_t)gridDim.x * blockDim.x) {
         const int bi = wl_find(w.start, w.n, item);
@@ -306,6 +308,7 @@ __global__ void __launch_bounds__(256, reg_min_blocks(N)) k_evalres_reg(ResLaunc
 // The warps listed by k_evalres_reg, solved on shared-memory columns.
 __global__ void k_evalres_redo(ResLaunch L, WorkList w, int SF, const unsigned long long *redo_n,
                                const int64_t *redo) {
+    if (stage_skipped(L)) return;
     extern __shared__ uint32_t smem[];
     const int BS = blockDim.x;
     uint32_t *Fs = smem + threadIdx.x;
@@ -326,6 +329,7 @@ __global__ void k_evalres_redo(ResLaunch L, WorkList w, int SF, const unsigned l
 constexpr int kInvSeg = kInvSegment;   // values per warp: 16 per lane, interleaved for coalescing
 
 __global__ void __launch_bounds__(256) k_batch_inv(ResLaunch L, WorkList w) {
+    if (stage_skipped(L)) return;
     const int lane = threadIdx.x & 31;
     for (int64_t item = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; item < w.total;
          item += ((int64_t)gridDim.x * blockDim.x) >> 5) {

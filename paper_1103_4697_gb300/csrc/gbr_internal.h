@@ -280,6 +280,8 @@ struct ResLaunch {
     uint8_t *pflags;             // unlucky-point flags (drop mode)
     const uint32_t *gtab;        // per-pair Garner tables (drop mode)
     unsigned long long *dropped; // count of flagged points
+    const int32_t *skip;         // null, or a device flag: non-zero makes every stage kernel return at once
+                                 // (a replayed step whose plan no longer matches its bounds)
     int32_t npairs;
     int32_t drop_unlucky;
 };
@@ -314,6 +316,10 @@ cudaError_t configure_gcd_kernels();
 cudaError_t configure_sqf_kernels();
 
 cudaError_t launch_bounds(const ResLaunch &L, cudaStream_t s);
+// *flag = 1 when the n bounds at a differ in any byte from those at b (the plan was made from b)
+cudaError_t launch_plan_check(const PairBound *a, const PairBound *b, int n, int32_t *flag, cudaStream_t s);
+// true when a replayed step must not run its stages
+__device__ __forceinline__ bool stage_skipped(const ResLaunch &L) { return L.skip && *(volatile const int32_t *)L.skip; }
 cudaError_t launch_reduce(const ResLaunch &L, const WorkList &w, cudaStream_t s);
 cudaError_t launch_evalres(const ResLaunch &L, const WorkList &w, int slots_f, int slots_g, int block,
                            cudaStream_t s);

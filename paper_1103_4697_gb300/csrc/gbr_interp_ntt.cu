@@ -21,6 +21,7 @@
 namespace gbr {
 
 __global__ void __launch_bounds__(256) k_interp_ntt(ResLaunch L, WorkList w) {
+    if (stage_skipped(L)) return;
     extern __shared__ uint32_t ns[];
     for (int64_t item = blockIdx.x; item < w.total; item += gridDim.x) {
         const int bi = wl_find(w.start, w.n, item);

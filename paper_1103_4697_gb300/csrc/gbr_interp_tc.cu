@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(256, 1) k_interp_tc(ResLaunch L, const char *p
     __shared__ __align__(8) uint64_t bar[3];   // stage 0, stage 1 released; all MMAs done
     __shared__ uint32_t tmem_slot;
     __shared__ int64_t vbs[TC_M];              // value base of each row's pair (-1: none)
+    if (stage_skipped(L)) return;                // whole CTA, before any tensor memory is taken
     const GemmTile T = tiles[blockIdx.x];
     const GemmGroup Gr = groups[T.group];
     const int n = Gr.n, rows = Gr.rows, mode = Gr.mode, i = T.prime;

@@ -424,9 +424,28 @@ cudaError_t launch_bounds(const ResLaunch &L, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// A replayed step re-measures its bounds and compares them, word by word, with
+// those its plan was made from; any difference stops the stages (the host then
+// plans again).
+__global__ void k_plan_check(const uint64_t *a, const uint64_t *b, int64_t words, int32_t *flag) {
+    bool diff = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < words; i += (int64_t)gridDim.x * blockDim.x)
+        diff = diff || a[i] != b[i];
+    if (__any_sync(0xffffffffu, diff) && (threadIdx.x & 31) == 0) atomicExch(flag, 1);
+}
+
+cudaError_t launch_plan_check(const PairBound *a, const PairBound *b, int n, int32_t *flag, cudaStream_t s) {
+    static_assert(sizeof(PairBound) % 8 == 0, "bounds compare as 64-bit words");
+    const int64_t words = (int64_t)n * sizeof(PairBound) / 8;
+    const int grid = (int)std::min<int64_t>((words + 255) / 256, 4 * (int64_t)sm_count());
+    k_plan_check<<<grid < 1 ? 1 : grid, 256, 0, s>>>((const uint64_t *)a, (const uint64_t *)b, words, flag);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ A1: modular reduction
 
 __global__ void k_reduce(ResLaunch L, WorkList w) {
+    if (stage_skipped(L)) return;
     for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < w.total;
          item += (int64_t)gridDim.x * blockDim.x) {
         int bi = wl_find(w.start, w.n, item);
@@ -497,6 +516,7 @@ __global__ void k_reduce(ResLaunch L, WorkList w) {
 // ------------------------------------------------------------------ A4: interpolation
 
 __global__ void k_interp(ResLaunch L, WorkList w, int maxP) {
+    if (stage_skipped(L)) return;
     extern __shared__ uint32_t smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     uint32_t *V = smem + (size_t)wid * 3 * maxP;
@@ -658,6 +678,7 @@ __global__ void __launch_bounds__(256, 3) k_interp_gemm(ResLaunch L, const char 
                                                        const GemmTile *tiles) {
     __shared__ uint32_t As[GT_K][GT_M + 1];
     __shared__ __align__(16) uint32_t Bs[GT_K][GT_N + 4];
+    if (stage_skipped(L)) return;
     __shared__ uint32_t Cs[GT_N][GT_M + 1];
     __shared__ int64_t colbase[GT_N], cfbase[GT_N];
     const GemmTile T = tiles[blockIdx.x];
@@ -756,6 +777,7 @@ __global__ void __launch_bounds__(256, 3) k_interp_gemm(ResLaunch L, const char 
 // there; the limbs of the magnitude follow in the same column.  KM = 0 (too
 // many primes for shared memory): the digits overwrite the residues in place.
 __global__ void k_crt(ResLaunch L, WorkList w, int KM, int LM) {
+    if (stage_skipped(L)) return;
     extern __shared__ uint32_t smem[];
     const int BS = blockDim.x;
     uint32_t *limb = smem + (size_t)KM * BS + threadIdx.x;
@@ -832,6 +854,7 @@ __global__ void k_crt(ResLaunch L, WorkList w, int KM, int LM) {
 // Digits live in shared memory as uint4 groups [i/4][thread], the tables are
 // staged in shared memory once per block.
 __global__ void k_crt_fast(ResLaunch L, WorkList w, int KD, int LD) {
+    if (stage_skipped(L)) return;
     extern __shared__ uint4 smem4[];
     uint32_t *sw = reinterpret_cast<uint32_t *>(smem4);
     const int BS = blockDim.x;
@@ -940,6 +963,7 @@ __global__ void k_unlucky_primes(ResLaunch L, int kc, uint8_t *out) {
 // Garner constants of a pair whose primes are not a prefix of the table
 // (same layout as the prefix table: k inverses, then the triangle).
 __global__ void k_pair_garner(ResLaunch L, const int32_t *pairs, int n, int kmax, uint32_t *gtab) {
+    if (stage_skipped(L)) return;
     const int64_t total = (int64_t)n * kmax;
     for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < total; it += (int64_t)gridDim.x * blockDim.x) {
         const PairPlan &P = L.plan[pairs[it / kmax]];

@@ -453,6 +453,45 @@ def test_graph_replay_and_autotuned_blocks(ctx):
         assert first[q] == list(O.res_subres(F[q], G[q]))
 
 
+def test_step_graph_replay(ctx):
+    """From the fourth run of a resident batch the whole step (bounds, plan check,
+    stages) is one graph launch with no host planning in between; its results equal
+    those of the planned runs and the oracle.  Changing an option that shapes the plan
+    (extra primes) goes back to planning; an interleaved other batch that evicts
+    nothing leaves the step graph valid."""
+    from paper_1103_4697_gb300.native import OPT_EXTRA_PRIMES, OPT_STATS
+
+    F, G = W.deg20_batch_arrays(160, 7000, d=9, bits=14)
+    ctx.set_option(OPT_STATS, 1)
+    res = ctx.upload_pairs(F, G)
+    outs, modes, kernels = [], [], []
+    for _ in range(5):
+        res.run()
+        st = ctx.stats()
+        outs.append(res.fetch())
+        modes.append(st["graph_replayed"])
+        kernels.append(st["kernels"])
+    assert modes == [0, 1, 1, 2, 2], modes
+    assert kernels[3] == kernels[2] + 2                  # the bounds kernel and the plan check join the graph
+    assert all(o == outs[0] for o in outs)
+    other = ctx.upload_pairs(*W.deg20_batch_arrays(8, 7500, d=5, bits=10))
+    other.run()
+    other.free()
+    res.run()
+    assert ctx.stats()["graph_replayed"] == 2 and res.fetch() == outs[0]
+    ctx.set_option(OPT_EXTRA_PRIMES, 1)
+    try:
+        res.run()
+        assert ctx.stats()["graph_replayed"] == 0 and res.fetch() == outs[0]
+    finally:
+        ctx.set_option(OPT_EXTRA_PRIMES, 0)
+        ctx.set_option(OPT_STATS, 0)
+    res.free()
+    rng = random.Random(4)
+    for q in rng.sample(range(160), 4):
+        assert outs[0][q] == list(O.res_subres(F[q], G[q]))
+
+
 def test_device_bound_is_rigorous_and_tight(ctx):
     """The device evaluates the scaled Hadamard bound in single precision with
     upward rounding and error margins; it must never fall below the host's
