@@ -73,6 +73,7 @@ struct gbr_ctx {
     std::mutex err_mu;
     std::string err;
     ModP *d_mods = nullptr;
+    double *d_l2pref = nullptr;         // sum_{i<k} log2 p_i, k = 0..num_primes (the step graphs' plan check)
     int32_t *d_err = nullptr;
     uint32_t *d_garner = nullptr;
     int garner_K = 0;
@@ -93,6 +94,7 @@ struct gbr_ctx {
         uint64_t last_use = 0;
     };
     std::map<int64_t, Vinv> vinv;  // inverse Vandermonde matrices, key 4 n + point-set mode
+    std::vector<gbr_resident *> shots;   // idle one-shot batches, oldest first (a repeated shape class reuses one)
     uint64_t vinv_clock = 0, vinv_run_mark = 0;
     const uint32_t *get_vinv(int n, int K, int mode);   // nullptr if it cannot be built
     const uint16_t *get_vinv_tc(int n, int K, int mode);   // digit tiles of a matrix get_vinv returned
@@ -143,6 +145,7 @@ struct gbr_resident {
     int64_t out_words = 0, sign_bytes = 0;
     bool ran = false;
     bool oneshot = false;               // created by a one-shot call: never captured
+    const void *shot_src = nullptr;     // one-shot cache: the host input of the call that last used it
     cudaGraphExec_t gexec = nullptr;    // captured device stages of the last plan
     int gstate = 0;                     // 0 no plan, 1 plan run once, 2 captured
     int64_t graph_kernels = 0;
@@ -150,11 +153,9 @@ struct gbr_resident {
     std::vector<char> gblk;             // plan block of the captured plan
     // the whole step as one graph (bounds, plan check, stages), captured once the
     // stage graph has replayed: later runs launch it with no host planning in
-    // between; the stages return at once if the fresh bounds differ from d_bref
+    // between; the stages return at once if the fresh bounds no longer fit the plan
     cudaGraphExec_t fexec = nullptr;
     int fstate = 0;                     // 0 none, 2 captured and valid for fsig
-    gbr::PairBound *d_bref = nullptr;   // the bounds the current plan was made from
-    size_t bref_cap = 0;
     std::vector<uintptr_t> fsig;        // options and table pointers the step graph assumes
     std::vector<std::pair<int64_t, std::pair<const void *, const void *>>> fvinv;   // cached matrices it reads
     gbr_stats fast_st{};
@@ -174,6 +175,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r);   // bounds, plan, sta
 int gbr_run_resident_finish(gbr_ctx *c, gbr_resident *r);   // wait, check, statistics
 int gbr_fetch_resident_locked(gbr_ctx *c, gbr_resident *r, int first, int count, gbr_bigpoly *out);
 void gbr_free_resident_locked(gbr_ctx *c, gbr_resident *r);
+void gbr_free_shots(gbr_ctx *c);   // the context's idle one-shot batches
 void gbr_serve_shutdown(gbr_ctx *c);
 void gbr_parallel_for(int n, int threads, const std::function<void(int, int)> &fn);   // fn(lo, hi) on threads
 bool gbr_alloc_results(gbr_bigpoly *out, int count);

@@ -316,8 +316,10 @@ cudaError_t configure_gcd_kernels();
 cudaError_t configure_sqf_kernels();
 
 cudaError_t launch_bounds(const ResLaunch &L, cudaStream_t s);
-// *flag = 1 when the n bounds at a differ in any byte from those at b (the plan was made from b)
-cudaError_t launch_plan_check(const PairBound *a, const PairBound *b, int n, int32_t *flag, cudaStream_t s);
+// *flag = 1 when the fresh bounds of some pair no longer fit its plan (degrees, points or
+// primes); l2pref[k] = sum_{i<k} log2 p_i on the device
+cudaError_t launch_plan_check(const PairBound *bounds, const PairPlan *plan, int n, const double *l2pref,
+                              int extra, int32_t *flag, cudaStream_t s);
 // true when a replayed step must not run its stages
 __device__ __forceinline__ bool stage_skipped(const ResLaunch &L) { return L.skip && *(volatile const int32_t *)L.skip; }
 cudaError_t launch_reduce(const ResLaunch &L, const WorkList &w, cudaStream_t s);

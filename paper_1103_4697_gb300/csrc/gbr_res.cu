@@ -424,21 +424,44 @@ cudaError_t launch_bounds(const ResLaunch &L, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// A replayed step re-measures its bounds and compares them, word by word, with
-// those its plan was made from; any difference stops the stages (the host then
-// plans again).
-__global__ void k_plan_check(const uint64_t *a, const uint64_t *b, int64_t words, int32_t *flag) {
-    bool diff = false;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < words; i += (int64_t)gridDim.x * blockDim.x)
-        diff = diff || a[i] != b[i];
-    if (__any_sync(0xffffffffu, diff) && (threadIdx.x & 31) == 0) atomicExch(flag, 1);
+// A replayed step re-measures its bounds and checks, pair by pair, that the plan
+// it replays still fits them: the same degrees in both variables, the same number
+// of points (the degree bound) and the same number of primes, computed from the
+// fresh bound exactly as the host planner does (the smallest k with
+// sum_{i<k} log2 p_i > log2 B (1 + 1e-9) + 2 + 1e-6; l2pref[k] is that sum).
+// Everything else a plan fixes follows from these, so a plan that passes is exact
+// for the new inputs; any pair that fails stops the stages (the host plans again).
+__global__ void k_plan_check(const PairBound *bounds, const PairPlan *plan, int n, const double *l2pref, int nprimes,
+                             int extra, int32_t *flag) {
+    bool bad = false;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        const PairBound B = bounds[q];
+        const PairPlan &p = plan[q];
+        if (p.flags & PLAN_ZERO) {
+            bad = bad || (B.m >= 0 && B.n >= 0);
+            continue;
+        }
+        if (B.m != p.m || B.n != p.n || max(B.dxf, 0) != p.dxf || max(B.dxg, 0) != p.dxg ||
+            (int64_t)degree_bound(B) + 1 != p.P) {
+            bad = true;
+            continue;
+        }
+        const double bits = B.log2B * (1.0 + 1e-9) + 2.0 + 1e-6;
+        int lo = 1, hi = nprimes + 1;   // first k in [1, nprimes] with l2pref[k] > bits, else nprimes + 1
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (l2pref[mid] > bits) hi = mid;
+            else lo = mid + 1;
+        }
+        bad = bad || lo + extra != p.k;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(flag, 1);
 }
 
-cudaError_t launch_plan_check(const PairBound *a, const PairBound *b, int n, int32_t *flag, cudaStream_t s) {
-    static_assert(sizeof(PairBound) % 8 == 0, "bounds compare as 64-bit words");
-    const int64_t words = (int64_t)n * sizeof(PairBound) / 8;
-    const int grid = (int)std::min<int64_t>((words + 255) / 256, 4 * (int64_t)sm_count());
-    k_plan_check<<<grid < 1 ? 1 : grid, 256, 0, s>>>((const uint64_t *)a, (const uint64_t *)b, words, flag);
+cudaError_t launch_plan_check(const PairBound *bounds, const PairPlan *plan, int n, const double *l2pref,
+                              int extra, int32_t *flag, cudaStream_t s) {
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 4 * (int64_t)sm_count());
+    k_plan_check<<<grid < 1 ? 1 : grid, 256, 0, s>>>(bounds, plan, n, l2pref, num_primes(), extra, flag);
     return cudaGetLastError();
 }
 

@@ -492,6 +492,42 @@ def test_step_graph_replay(ctx):
         assert outs[0][q] == list(O.res_subres(F[q], G[q]))
 
 
+def test_one_shot_calls_reuse_their_graphs():
+    """gbr_resultant_batch called again with inputs of the same shape keeps its batch,
+    plan and graphs: from the fifth call the whole step is one graph.  New contents in
+    the same buffers whose plan still fits (each row reversed: same degrees and bounds)
+    run from that graph and give their own, correct results; contents that need more
+    primes make the device check decline the graph, and the call plans again."""
+    from paper_1103_4697_gb300.api import Context
+    from paper_1103_4697_gb300.native import OPT_STATS
+
+    F, G = W.deg20_batch_arrays(200, 8100, d=8, bits=12)
+    F[:, :, 0][F[:, :, 0] == 0] = 1          # reversed rows keep their degrees
+    with Context(device=0, mem_budget=2 << 30) as c:
+        c.set_option(OPT_STATS, 1)
+        modes, outs = [], []
+        for _ in range(6):
+            outs.append(c.resultant_batch(F, G))
+            modes.append(c.stats()["graph_replayed"])
+        assert modes == [0, 0, 1, 1, 2, 2], modes
+        assert all(o == outs[0] for o in outs)
+        rng = random.Random(6)
+        for q in rng.sample(range(200), 3):
+            assert outs[0][q] == list(O.res_subres(F[q], G[q]))
+        for j in range(9):                                  # reverse row j (x-degree 8 - j) in place
+            F[:, j, :9 - j] = F[:, j, 8 - j::-1].copy()
+        got = c.resultant_batch(F, G)
+        assert c.stats()["graph_replayed"] == 2
+        for q in rng.sample(range(200), 6):
+            a = rng.randint(-2 ** 31, 2 ** 31)
+            assert _poly_eval(got[q], a) == O.res_at_prs(F[q], G[q], a), q
+        F[7] <<= 30                                          # pair 7 now needs more primes
+        got2 = c.resultant_batch(F, G)
+        assert c.stats()["graph_replayed"] == 0
+        assert got2[7] == list(O.res_subres(F[7], G[7]))
+        assert got2[:7] == got[:7] and got2[8:] == got[8:]
+
+
 def test_device_bound_is_rigorous_and_tight(ctx):
     """The device evaluates the scaled Hadamard bound in single precision with
     upward rounding and error margins; it must never fall below the host's
