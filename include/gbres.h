@@ -236,6 +236,20 @@ int gbr_gcd_batch(gbr_ctx *ctx, int n, const gbr_upoly *p, const gbr_upoly *q, g
 int gbr_gcd_cofactors_batch(gbr_ctx *ctx, int n, const gbr_upoly *p, const gbr_upoly *q, gbr_bigpoly *g,
                             gbr_bigpoly *p_over_g, gbr_bigpoly *q_over_g);
 
+/* Resultants and gcds submitted as one batch (Section 4: the two symbolic
+ * operations the algorithm relies on; a workload such as a curve analysis asks
+ * for both at once): res_out[i] = res_var(f[i], g[i]) as gbr_resultant_batch
+ * computes it and gcd_out[i] = gcd(p[i], q[i]) as gbr_gcd_batch computes it.
+ * The gcd batch runs on a private worker stream in a host thread of its own
+ * while the resultant batch runs on the context's stream (or its pipeline
+ * workers), so their device stages and host planning overlap.  Inputs are
+ * caller-owned and read during the call; results are library-owned (free each
+ * with gbr_free_result).  On any error both output arrays are left empty
+ * (deg = -1) and the first failing half's status is returned; the errors of
+ * gbr_resultant_batch and gbr_gcd_batch apply.  nres or ngcd may be 0. */
+int gbr_mixed_batch(gbr_ctx *ctx, int nres, const gbr_bipoly *f, const gbr_bipoly *g, int var,
+                    gbr_bigpoly *res_out, int ngcd, const gbr_upoly *p, const gbr_upoly *q, gbr_bigpoly *gcd_out);
+
 /* ------------------------------------------------------------------ bivariate gcd, Teissier resultant */
 
 /* An exact polynomial in Z[x, y]: coefficient of x^i y^j at index j (deg_x + 1) + i

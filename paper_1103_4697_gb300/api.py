@@ -343,6 +343,17 @@ class Context:
         N.check(N.lib().gbr_gcd_batch(self.handle, n, _ptr(dp), _ptr(dq), outs), self.handle)
         return self._collect(outs, n)
 
+    def mixed_batch(self, fs, gs, ps, qs, var: int = 1) -> tuple[list[list[int]], list[list[int]]]:
+        """gbr_mixed_batch: res_var(fs[i], gs[i]) and gcd(ps[j], qs[j]) in one call."""
+        keep = _Packed()
+        df, dg = pack_bipolys(fs, keep), pack_bipolys(gs, keep)
+        dp, dq = pack_upolys(ps, keep), pack_upolys(qs, keep)
+        nr, ng = len(df), len(dp)
+        ro, go = (N.BigPoly * max(nr, 1))(), (N.BigPoly * max(ng, 1))()
+        N.check(N.lib().gbr_mixed_batch(self.handle, nr, _ptr(df), _ptr(dg), var, ro, ng, _ptr(dp), _ptr(dq), go),
+                self.handle)
+        return self._collect(ro, nr), self._collect(go, ng)
+
     def gcd(self, p, q) -> list[int]:
         return self.gcd_batch([p], [q])[0]
 

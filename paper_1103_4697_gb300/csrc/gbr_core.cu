@@ -768,6 +768,7 @@ extern "C" void gbr_destroy(gbr_ctx *c) {
     if (!c) return;
     gbr_serve_shutdown(c);
     for (int w = 0; w < 2; ++w) gbr_destroy_worker(c->pipe[w]);
+    gbr_destroy_worker(c->mixw);
     gbr_free_shots(c);
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
@@ -2313,6 +2314,53 @@ extern "C" int gbr_resultant_batch(gbr_ctx *c, int n, const gbr_bipoly *f, const
 
 extern "C" int gbr_discriminant_res_batch(gbr_ctx *c, int n, const gbr_bipoly *f, int var, gbr_bigpoly *out) {
     return res_batch_impl(c, n, f, nullptr, var, 1, out);
+}
+
+extern "C" int gbr_mixed_batch(gbr_ctx *c, int nres, const gbr_bipoly *f, const gbr_bipoly *g, int var,
+                               gbr_bigpoly *res_out, int ngcd, const gbr_upoly *p, const gbr_upoly *q,
+                               gbr_bigpoly *gcd_out) {
+    if (!c || nres < 0 || ngcd < 0 || (nres && (!f || !g || !res_out)) || (ngcd && (!p || !q || !gcd_out)))
+        return GBR_EINVAL;
+    NvtxScope call("gbr_mixed_batch");
+    for (int i = 0; i < ngcd; ++i) gcd_out[i] = gbr_bigpoly{-1, 0, nullptr, nullptr};
+    gbr_ctx *w = nullptr;
+    if (ngcd) {
+        std::lock_guard<std::mutex> lk(c->mu);
+        if (!c->mixw) c->mixw = gbr_make_worker(c);
+        w = c->mixw;
+        if (!w) return c->fail(GBR_EDEVICE, "could not create the gcd worker of a mixed batch");
+        w->stats_on = c->stats_on;
+    }
+    int gst = GBR_OK;
+    std::thread th;
+    if (w) {
+        th = std::thread([&]() {
+            std::lock_guard<std::mutex> lk(w->mu);
+            cudaSetDevice(w->device);
+            gst = gbr_gcd_cof_locked(w, ngcd, p, q, gcd_out, nullptr, nullptr);
+        });
+    }
+    const int rst = nres ? res_batch_impl(c, nres, f, g, var, 0, res_out) : GBR_OK;
+    if (th.joinable()) th.join();
+    if (rst || gst) {
+        for (int i = 0; i < nres; ++i) gbr_free_result(c, &res_out[i]);
+        for (int i = 0; i < ngcd; ++i) gbr_free_result(c, &gcd_out[i]);
+        if (rst) return rst;
+        std::string msg;
+        {
+            std::lock_guard<std::mutex> g2(w->err_mu);
+            msg = w->err;
+        }
+        return c->fail(gst, ("mixed batch, gcd half: " + msg).c_str());
+    }
+    if (w) {
+        std::lock_guard<std::mutex> lk(c->mu);
+        c->stats.gcd_ms = w->stats.gcd_ms;
+        c->stats.kernels += w->stats.kernels;
+        c->stats.h2d_bytes += w->stats.h2d_bytes;
+        c->stats.d2h_bytes += w->stats.d2h_bytes;
+    }
+    return GBR_OK;
 }
 
 // ------------------------------------------------------------------ host-side planning info

@@ -100,6 +100,7 @@ struct gbr_ctx {
     const uint16_t *get_vinv_tc(int n, int K, int mode);   // digit tiles of a matrix get_vinv returned
     gbr::ServeState *serve = nullptr;
     gbr_ctx *pipe[2] = {nullptr, nullptr};   // private workers that pipeline large one-shot batches
+    gbr_ctx *mixw = nullptr;                 // private worker for the gcd half of gbr_mixed_batch
     int64_t gcd_kernels = 0, gcd_subproblems = 0, gcd_h2d = 0, gcd_d2h = 0;   // counters of the last gcd call
     int pipe_on = 1;
     std::map<int, int> tuned_evalres;   // degree bucket -> block size chosen by the autotuner

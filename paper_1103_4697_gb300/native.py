@@ -81,6 +81,8 @@ SIGNATURES = {
     "gbr_resultant_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(BigPoly)]),
     "gbr_discriminant_res_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(BigPoly)]),
     "gbr_gcd_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(BigPoly)]),
+    "gbr_mixed_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(BigPoly), C.c_int,
+                                  C.c_void_p, C.c_void_p, C.POINTER(BigPoly)]),
     "gbr_gcd_cofactors_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(BigPoly),
                                           C.POINTER(BigPoly), C.POINTER(BigPoly)]),
     "gbr_gcd2_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(BigBiPoly),

@@ -144,3 +144,22 @@ def test_gcd_batch_every_job(ctx):
     assert all(ok), [i for i in range(4096) if not ok[i]][:10]
     for i, w in zip(exact, want):
         assert out[i] == w, i
+
+
+def test_mixed_batch_equals_separate_calls(ctx):
+    """gbr_mixed_batch (the gcd half on a worker stream beside the resultant half) gives
+    exactly what gbr_resultant_batch and gbr_gcd_batch give: the heterogeneous resultant
+    batch at its full 4096 pairs (pipelined over the context's workers) with the 4096
+    gcd jobs; planted pairs give 0; either half may be empty."""
+    ps = W.mixed_batch(3, 4096)
+    P, Q, H = W.gcd_batch(3, 4096)
+    res, gcds = ctx.mixed_batch(ps.f, ps.g, P, Q)
+    assert res == ctx.resultant_batch(ps.f, ps.g)
+    assert gcds == ctx.gcd_batch(P, Q)
+    assert all(res[i] == [] for i in range(4096) if ps.planted[i])
+    for i in range(0, 4096, 1024):
+        assert gcds[i] == list(O.gcd_z(P[i], Q[i]))
+    r2, g2 = ctx.mixed_batch([], [], P[:3], Q[:3])
+    assert r2 == [] and g2 == gcds[:3]
+    r3, g3 = ctx.mixed_batch(ps.f[:5], ps.g[:5], [], [])
+    assert r3 == res[:5] and g3 == []
