@@ -523,7 +523,32 @@ def configs_block(ctx, cal: dict, serve_requests: int = 100_000) -> dict:
                           C.cast(api._ptr(dq[i:i + 1]), C.POINTER(N.UPoly)), C.byref(o)), ctx.handle)
         L.gbr_free_result(ctx.handle, C.byref(o))
     one_gcd = n1 / (time.perf_counter() - t)
+    # both halves as one batch (gbr_mixed_batch) against the two one-shot calls in turn,
+    # through the C ABI with packed host buffers; freeing the results is not timed
+    rr, rg = (N.BigPoly * PAIRS)(), (N.BigPoly * PAIRS)()
+
+    def free_all():
+        for i in range(PAIRS):
+            L.gbr_free_result(ctx.handle, C.byref(rr[i]))
+            L.gbr_free_result(ctx.handle, C.byref(rg[i]))
+
+    def timed(fn, reps=5):
+        ts = []
+        for _ in range(reps):
+            t = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t)
+            free_all()
+        return statistics.median(ts[1:])
+
+    mixed_s = timed(lambda: N.check(L.gbr_mixed_batch(ctx.handle, PAIRS, api._ptr(df), api._ptr(dg), 1, rr, PAIRS,
+                                                      api._ptr(dp), api._ptr(dq), rg), ctx.handle))
+    sep_s = timed(lambda: (N.check(L.gbr_resultant_batch(ctx.handle, PAIRS, api._ptr(df), api._ptr(dg), 1, rr),
+                                   ctx.handle),
+                           N.check(L.gbr_gcd_batch(ctx.handle, PAIRS, api._ptr(dp), api._ptr(dq), rg), ctx.handle)))
     out["3"] = {"res_solves_per_s": PAIRS / sec, "res_ms_per_batch": sec * 1e3, "stage_roofline": rl3,
+                "one_batch_res_plus_gcd_ms": mixed_s * 1e3, "two_calls_res_then_gcd_ms": sep_s * 1e3,
+                "one_batch_jobs_per_s": 2 * PAIRS / mixed_s,
                 "res_one_pair_per_launch_per_s": one_res,
                 "gcd_jobs_per_s": PAIRS / statistics.median(gtimes[1:]),
                 "gcd_one_job_per_launch_per_s": one_gcd,

@@ -15,8 +15,8 @@
 //
 // Tile: 128 pairs (tensor-memory lanes) x 64 coefficients (columns); the seven
 // diagonals take 7 x 64 of the 512 tensor-memory columns.  The K dimension runs
-// in chunks of 32 through two shared-memory stages: all 128 threads split the
-// operand of their own pair into digits while thread 0 issues the 32 MMAs
+// in chunks of 32 through two shared-memory stages: the CTA's threads (four per
+// pair) split the operands into digits while thread 0 issues the 32 MMAs
 // (16 digit pairs x 2 k-steps of 16) of the previous stage; tcgen05.commit
 // releases a stage when its MMAs have read it.  Operand tiles use the
 // no-swizzle K-major layout: core matrices of 8 rows x 8 elements (128 bytes),
@@ -35,6 +35,12 @@ constexpr int TC_XPLANE = TC_M * TC_KC * 2;        // bytes of one digit plane o
 constexpr int TC_VPLANE = TC_N * TC_KC * 2;        // bytes of one digit plane of the matrix tile
 constexpr int TC_STAGE = 4 * TC_XPLANE + 4 * TC_VPLANE;   // 48 KB
 constexpr int TC_VTILE_WORDS = 4 * TC_VPLANE / 4;         // uint32 words of one prepared matrix tile
+constexpr int TC_THREADS = 512;                           // 16 warps share the staging of each chunk
+constexpr int TC_WARPS = TC_THREADS / 32;
+constexpr int TC_PER_ROW = TC_THREADS / TC_M;             // threads per operand row (tensor-memory lane)
+constexpr int TC_KG = TC_KC / 8 / TC_PER_ROW;             // K groups of 8 each thread splits per chunk
+constexpr int TC_CPT = TC_N / TC_PER_ROW;                 // epilogue columns per thread
+static_assert(TC_KG >= 1 && TC_CPT % 8 == 0 && TC_M % TC_WARPS == 0, "staging split");
 
 // element (r, k) of a rows x 32 digit plane, in bf16 units
 __host__ __device__ inline int tc_elem(int r, int k) { return (r >> 3) * 256 + (k >> 3) * 64 + (r & 7) * 8 + (k & 7); }
@@ -103,7 +109,7 @@ __global__ void k_vinv_tc(const uint32_t *vinv, int n, int rows, int K, int nct,
     }
 }
 
-__global__ void __launch_bounds__(256, 1) k_interp_tc(ResLaunch L, const char *planblk, const GemmGroup *groups,
+__global__ void __launch_bounds__(TC_THREADS, 1) k_interp_tc(ResLaunch L, const char *planblk, const GemmGroup *groups,
                                                      const GemmTile *tiles) {
     extern __shared__ __align__(1024) unsigned char tsm[];
     __shared__ __align__(8) uint64_t bar[3];   // stage 0, stage 1 released; all MMAs done
@@ -116,9 +122,9 @@ __global__ void __launch_bounds__(256, 1) k_interp_tc(ResLaunch L, const char *p
     const int nkc = (n + TC_KC - 1) / TC_KC, nct = (n + TC_N - 1) / TC_N;   // tiles cover all n rows
     const int tid = threadIdx.x, warp = tid >> 5;
     const ModP M = L.mods[i];
-    // this thread's pair (tensor-memory lane row = tid mod 128); threads tid and
-    // tid + 128 share the row and split its K groups and its columns
-    const int row = tid & (TC_M - 1), half = tid >> 7;
+    // this thread's pair (tensor-memory lane row = tid mod 128); the threads
+    // tid + 128 t share the row and split its K groups and its columns
+    const int row = tid & (TC_M - 1), part = tid >> 7;
     const int32_t *gpairs = (const int32_t *)(planblk + Gr.pairs_off);
     int64_t vb = -1, cb = 0;
     if (T.q0 + row < Gr.npairs) {
@@ -128,7 +134,7 @@ __global__ void __launch_bounds__(256, 1) k_interp_tc(ResLaunch L, const char *p
             cb = pp.cf_off + (int64_t)i * pp.P;
         }
     }
-    if (half == 0) vbs[row] = vb;
+    if (part == 0) vbs[row] = vb;
     uint32_t *raw = reinterpret_cast<uint32_t *>(tsm + 2 * TC_STAGE);   // TC_M x 33 words
     const uint32_t *vt = (const uint32_t *)Gr.vtc + ((int64_t)i * nct + T.c0 / TC_N) * nkc * TC_VTILE_WORDS;
     if (warp == 0) {
@@ -149,17 +155,17 @@ __global__ void __launch_bounds__(256, 1) k_interp_tc(ResLaunch L, const char *p
     const uint32_t tbase = tmem_slot;
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(tsm);
     bool stalled = false;   // CTA-uniform: a stage wait gave up, no further chunk is issued
-    // software pipeline: the loads of chunk kc + 1 (operand rows: 32 per warp,
-    // lanes along K; the 16 KB matrix block) are in flight while chunk kc is
-    // split into digits and multiplied
+    // software pipeline: the loads of chunk kc + 1 (operand rows: TC_M / TC_WARPS
+    // per warp, lanes along K; the 16 KB matrix block) are in flight while chunk kc
+    // is split into digits and multiplied
     const int lane = tid & 31;
-    uint32_t ra[TC_M / 8], rc[TC_M / 8];
-    uint4 rv[4 * TC_VPLANE / 16 / 256];
+    uint32_t ra[TC_M / TC_WARPS], rc[TC_M / TC_WARPS];
+    uint4 rv[4 * TC_VPLANE / 16 / TC_THREADS];
     auto preload = [&](int kc) {
         const int j = kc * TC_KC + lane;
 #pragma unroll
-        for (int it = 0; it < TC_M / 8; ++it) {
-            const int64_t b = vbs[warp + 8 * it];
+        for (int it = 0; it < TC_M / TC_WARPS; ++it) {
+            const int64_t b = vbs[warp + TC_WARPS * it];
             uint32_t x = 0u, y = 0u;
             if (b >= 0 && j < n) {
                 if (mode == GEMM_PLAIN) x = L.val[b + j];
@@ -176,7 +182,7 @@ __global__ void __launch_bounds__(256, 1) k_interp_tc(ResLaunch L, const char *p
         }
         const uint4 *src = reinterpret_cast<const uint4 *>(vt + (int64_t)kc * TC_VTILE_WORDS);
 #pragma unroll
-        for (int u = 0; u < 4 * TC_VPLANE / 16 / 256; ++u) rv[u] = __ldg(src + tid + 256 * u);
+        for (int u = 0; u < 4 * TC_VPLANE / 16 / TC_THREADS; ++u) rv[u] = __ldg(src + tid + TC_THREADS * u);
     };
     preload(0);
     for (int kc = 0; kc < nkc; ++kc) {
@@ -187,8 +193,9 @@ __global__ void __launch_bounds__(256, 1) k_interp_tc(ResLaunch L, const char *p
         // the loaded chunk's operand (sums / differences, below p) into raw rows
         // (pitch 33 words, not read by the tensor cores)
 #pragma unroll
-        for (int it = 0; it < TC_M / 8; ++it)
-            raw[(warp + 8 * it) * 33 + lane] = mode == GEMM_ODD ? mp_sub(ra[it], rc[it], M.p) : mp_add(ra[it], rc[it], M.p);
+        for (int it = 0; it < TC_M / TC_WARPS; ++it)
+            raw[(warp + TC_WARPS * it) * 33 + lane] =
+                mode == GEMM_ODD ? mp_sub(ra[it], rc[it], M.p) : mp_add(ra[it], rc[it], M.p);
         // a wait that gave up on any thread ends the loop on all of them before
         // anything is written into a stage an MMA may still be reading
         if (__syncthreads_or(late)) {
@@ -198,17 +205,17 @@ __global__ void __launch_bounds__(256, 1) k_interp_tc(ResLaunch L, const char *p
         {
             uint4 *dst = reinterpret_cast<uint4 *>(st + 4 * TC_XPLANE);
 #pragma unroll
-            for (int u = 0; u < 4 * TC_VPLANE / 16 / 256; ++u) dst[tid + 256 * u] = rv[u];
+            for (int u = 0; u < 4 * TC_VPLANE / 16 / TC_THREADS; ++u) dst[tid + TC_THREADS * u] = rv[u];
         }
         if (kc + 1 < nkc) preload(kc + 1);
-        // each thread splits two K groups of its row into four digit planes
+        // each thread splits TC_KG K groups of its row into four digit planes
         {
-            uint32_t pk[4][2][4];   // [digit][k-group][word]: two bf16 per word
+            uint32_t pk[4][TC_KG][4];   // [digit][k-group][word]: two bf16 per word
 #pragma unroll
-            for (int g = 0; g < 2; ++g)
+            for (int g = 0; g < TC_KG; ++g)
 #pragma unroll
                 for (int h = 0; h < 4; ++h) {
-                    const int kk = (2 * half + g) * 8 + h * 2;
+                    const int kk = (TC_KG * part + g) * 8 + h * 2;
                     uint32_t dlo[4], dhi[4];
                     tc_digits(raw[row * 33 + kk], dlo[0], dlo[1], dlo[2], dlo[3]);
                     tc_digits(raw[row * 33 + kk + 1], dhi[0], dhi[1], dhi[2], dhi[3]);
@@ -218,8 +225,8 @@ __global__ void __launch_bounds__(256, 1) k_interp_tc(ResLaunch L, const char *p
 #pragma unroll
             for (int t = 0; t < 4; ++t)
 #pragma unroll
-                for (int g = 0; g < 2; ++g)
-                    *reinterpret_cast<uint4 *>(st + t * TC_XPLANE + 2 * tc_elem(row, (2 * half + g) * 8)) =
+                for (int g = 0; g < TC_KG; ++g)
+                    *reinterpret_cast<uint4 *>(st + t * TC_XPLANE + 2 * tc_elem(row, (TC_KG * part + g) * 8)) =
                         make_uint4(pk[t][g][0], pk[t][g][1], pk[t][g][2], pk[t][g][3]);
         }
         asm volatile("fence.proxy.async.shared::cta;");
@@ -257,7 +264,7 @@ __global__ void __launch_bounds__(256, 1) k_interp_tc(ResLaunch L, const char *p
     // epilogue: lane tid holds pair q0 + tid; combine the diagonals per coefficient
     const int ostride = mode == GEMM_PLAIN ? 1 : 2, ooff = mode == GEMM_ODD ? 1 : 0;
     const uint64_t off_lo = (uint64_t)M.p << 20, off_hi = (uint64_t)M.p << 11;
-    for (int c0 = half * (TC_N / 2); ok && c0 < (half + 1) * (TC_N / 2); c0 += 8) {
+    for (int c0 = part * TC_CPT; ok && c0 < (part + 1) * TC_CPT; c0 += 8) {
         uint32_t v[TC_DIAG][8];
 #pragma unroll
         for (int u = 0; u < TC_DIAG; ++u) {
@@ -313,7 +320,7 @@ cudaError_t launch_interp_tc(const ResLaunch &L, const char *planblk, const Gemm
     if (ntiles <= 0) return cudaSuccess;
     const size_t smem = (size_t)120 * 1024;
     static_assert(2 * TC_STAGE + TC_M * 33 * 4 <= 120 * 1024, "two stages and the raw rows fit the request");
-    k_interp_tc<<<ntiles, 256, smem, s>>>(L, planblk, groups, tiles);
+    k_interp_tc<<<ntiles, TC_THREADS, smem, s>>>(L, planblk, groups, tiles);
     return cudaGetLastError();
 }
 
