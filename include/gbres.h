@@ -132,6 +132,8 @@ typedef struct {
                                  shared memory */
     int64_t root_pairs;       /* pairs evaluated at roots of unity and interpolated by an inverse
                                  transform (GBR_OPT_POINTS) */
+    int64_t quad_pairs;       /* pairs evaluated on the quartic point set 0, +-a, +-i a and
+                                 interpolated by four quarter-size contractions (GBR_OPT_POINTS) */
 } gbr_stats;
 
 /* ------------------------------------------------------------------ context */
@@ -186,14 +188,21 @@ const char *gbr_last_error(gbr_ctx *ctx);
                                     on shared memory); 0: every subproblem on shared memory */
 #define GBR_OPT_POINTS       9   /* evaluation points of the resultant (Section 4: the evaluation
                                     and interpolation stages of the modular method; the paper fixes
-                                    no point set).  0 (default): chosen per pair by estimated cost;
-                                    1: the integers 0, +-1, +-2, ... (interpolation by inverse-
-                                    Vandermonde contraction or Newton); 2: the N-th roots of unity
-                                    modulo each prime, N the power of two >= max(64, deg_x R + 1)
-                                    (every table prime is 1 mod 2^14, so N <= 16384 = GBR_MAX_POINTS),
-                                    interpolation by an inverse number-theoretic transform in
-                                    O(N log N).  Not used in drop mode (GBR_OPT_DROP_UNLUCKY).
-                                    Results are identical; values outside 0..2: GBR_EINVAL. */
+                                    no point set).  0 (default): chosen per pair: roots of unity
+                                    where the estimated cost says so, else the quartic set when its
+                                    matrices can be cached, else the symmetric integers;
+                                    1: the integers 0, +-1, +-2, ... (interpolation by even and odd
+                                    inverse-Vandermonde contractions, or Newton); 2: the N-th roots
+                                    of unity modulo each prime, N the power of two
+                                    >= max(64, deg_x R + 1) (every table prime is 1 mod 2^14, so
+                                    N <= 16384 = GBR_MAX_POINTS), interpolation by an inverse
+                                    number-theoretic transform in O(N log N); 3: the quartic set
+                                    0, +-a, +-i a (a = 1..ceil(deg_x R / 4), i^2 = -1 mod p): four
+                                    quarter-size contractions give R(x) = sum_t x^t R_t(x^4) (half
+                                    the multiply-adds of 1), used where its matrices can be
+                                    cached (else as 1).  Not used in drop mode
+                                    (GBR_OPT_DROP_UNLUCKY).  Results are identical; values outside
+                                    0..3: GBR_EINVAL. */
 int gbr_set_option(gbr_ctx *ctx, int option, int64_t value);
 int gbr_get_stats(gbr_ctx *ctx, gbr_stats *out);
 

@@ -367,7 +367,7 @@ const uint32_t *gbr::prime_roots(const ModP *d) { return prime_crt_tables(d) + k
 // 256 MiB), least recently used entries are dropped.
 const uint32_t *gbr_ctx::get_vinv(int n, int K, int mode) {
     const size_t kVinvCacheBytes = std::max<size_t>((size_t)256 << 20, budget / 4);
-    const int64_t key = 4 * (int64_t)n + mode;
+    const int64_t key = 8 * (int64_t)n + mode;   // modes 0..7
     auto it = vinv.find(key);
     if (it != vinv.end() && it->second.K >= K) {
         it->second.last_use = ++vinv_clock;
@@ -418,7 +418,7 @@ const uint32_t *gbr_ctx::get_vinv(int n, int K, int mode) {
 // tensor-core path or the memory is not there
 const uint16_t *gbr_ctx::get_vinv_tc(int n, int K, int mode) {
     if (n > kTcMaxN) return nullptr;
-    auto it = vinv.find(4 * (int64_t)n + mode);
+    auto it = vinv.find(8 * (int64_t)n + mode);
     if (it == vinv.end() || it->second.K < K) return nullptr;
     Vinv &v = it->second;
     if (v.tc) return v.tc;
@@ -847,7 +847,7 @@ extern "C" int gbr_set_option(gbr_ctx *c, int opt, int64_t v) {
         case GBR_OPT_REGISTER_FORM: c->reg_on = (int)(v != 0); return GBR_OK;
         case GBR_OPT_INTERP_TC: c->tc_on = (int)(v != 0); return GBR_OK;
         case GBR_OPT_POINTS:
-            if (v < 0 || v > 2) return GBR_EINVAL;
+            if (v < 0 || v > 3) return GBR_EINVAL;
             c->pts_mode = (int)v;
             return GBR_OK;
         case GBR_OPT_PIPELINE: c->pipe_on = (int)(v != 0); return GBR_OK;
@@ -1379,10 +1379,14 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
             kcl = std::max(kcl, p.k + 32);
         }
     }
+    // the matrices of this run are marked from here on (the point-set choice below
+    // already builds some)
+    c->vinv_run_mark = c->vinv_clock;
     // roots of unity: Pe = N points (a power of two) and an inverse transform, when
     // the transform saves more than the extra points cost; the integer points'
     // contraction cost depends on how many pairs share its point count
-    if (!drop && c->pts_mode != 1) {
+    const bool quad_ok = !drop && c->gemm_on && (c->pts_mode == 0 || c->pts_mode == 3);
+    if (!drop && (c->pts_mode == 0 || c->pts_mode == 2)) {
         std::unordered_map<int32_t, int> share;
         for (int q = 0; q < n; ++q)
             if (!perr[q] && !(plan[q].flags & PLAN_ZERO)) ++share[plan[q].P];
@@ -1391,12 +1395,36 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
             if (perr[q] || (p.flags & PLAN_ZERO)) continue;
             const int N = root_points(p.P);
             if (N > kRootOrder) continue;
-            if (c->pts_mode == 2 ||
-                roots_pay(p.P, N, hb[q].tf, hb[q].tg, p.m, p.n, share[p.P], c->tc_on && c->gemm_on, c->gemm_on)) {
+            if (c->pts_mode == 2 || roots_pay(p.P, N, hb[q].tf, hb[q].tg, p.m, p.n, share[p.P],
+                                              c->tc_on && c->gemm_on, c->gemm_on, quad_ok)) {
                 p.sym = PTS_ROOTS;
                 p.Pe = N;
                 p.tiles = N / 32;
             }
+        }
+    }
+    // the quartic set for the remaining integer-point pairs whose point count's four
+    // quarter matrices can be cached (their interpolation has no Newton fallback);
+    // the others keep the symmetric integers
+    if (quad_ok) {
+        std::unordered_map<int32_t, int> kq;   // points -> most primes among the candidates
+        for (int q = 0; q < n; ++q)
+            if (!perr[q] && !(plan[q].flags & PLAN_ZERO) && plan[q].sym == PTS_SYM)
+                kq[plan[q].P] = std::max(kq[plan[q].P], plan[q].k);
+        std::unordered_map<int32_t, bool> fits;
+        for (const auto &e : kq) {
+            const int P = e.first, h = quad_h(P);
+            bool ok = true;
+            for (int t = 0; t < 4 && ok; ++t)
+                if (quad_rows(P, t) > 0) ok = c->get_vinv(t ? h : h + 1, e.second, VINV_Q0 + t) != nullptr;
+            fits[P] = ok;
+        }
+        for (int q = 0; q < n; ++q) {
+            PairPlan &p = plan[q];
+            if (perr[q] || (p.flags & PLAN_ZERO) || p.sym != PTS_SYM || !fits[p.P]) continue;
+            p.sym = PTS_QUAD;
+            p.Pe = quad_pe(p.P);
+            p.tiles = (quad_pairs(p.P) + 15) / 16;
         }
     }
     for (int q = 0; q < n; ++q)
@@ -1451,7 +1479,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     // contraction groups by (points, symmetric): flat tables in ascending key order
     std::vector<HostList> evb_t((GBR_MAX_YDEG + 5) / 4 + 1);
     std::vector<HostList> evr_t(kRegMaxN + 1);
-    std::vector<std::pair<int, int32_t>> pg_items;   // (2 P + sym, pair)
+    std::vector<std::pair<int, int32_t>> pg_items;   // (4 P + sym, pair)
     pg_items.reserve(n);
     red.pairs.reserve(n);
     red.start.reserve(n);
@@ -1459,7 +1487,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     crtf.start.reserve(n);
     std::vector<int32_t> mapped;                    // pairs with their own Garner table
     int kmapped = 0;
-    int64_t subproblems = 0, root_pairs = 0;
+    int64_t subproblems = 0, root_pairs = 0, quad_pairs = 0;
     for (int q = 0; q < n; ++q) {
         const PairBound &b = hb[q];
         PairPlan &p = plan[q];
@@ -1504,7 +1532,8 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
             ++root_pairs;
             Nntt = std::max(Nntt, p.Pe);
         } else if (p.pmap_off < 0 && (p.sym || p.Pe == p.P)) {
-            pg_items.push_back({2 * p.P + p.sym, q});
+            pg_items.push_back({4 * p.P + p.sym, q});
+            quad_pairs += p.sym == PTS_QUAD;
         } else {
             interp.add(q, k);
         }
@@ -1517,7 +1546,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
         }
         subproblems += (int64_t)k * p.Pe;
         binv.add(q, (int64_t)k * ((p.Pe + kInvSegment - 1) / kInvSegment));
-        int64_t ev = (int64_t)k * (p.sym == PTS_ROOTS ? p.Pe : p.P) * (b.tf + b.tg + 2LL * p.m * p.n);
+        int64_t ev = (int64_t)k * (p.sym >= PTS_ROOTS ? p.Pe : p.P) * (b.tf + b.tg + 2LL * p.m * p.n);
         st.modmul_evalres += ev;
         st.modmul += ev + (int64_t)k * p.P * (p.P - 1) + (int64_t)p.P * k * (k - 1) / 2;
     }
@@ -1552,15 +1581,28 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     };
     std::vector<Gemm> gemms;
     std::vector<int32_t> gemm_pairs;
-    c->vinv_run_mark = c->vinv_clock;
     for (auto &kv : pgroups) {
         const std::vector<int32_t> &qs = kv.second;
         int K = 0;
         for (int q : qs) K = std::max(K, plan[q].k);
-        const int gP = kv.first / 2, gsym = kv.first & 1;
+        const int gP = kv.first / 4, gsym = kv.first & 3;
         const size_t off = gemm_pairs.size();
+        const size_t g0 = gemms.size();
         bool done = false;
-        if ((int)qs.size() >= kGemmMinPairs && c->gemm_on) {
+        if (gsym == PTS_QUAD) {
+            // four quarter contractions; the planner made sure their matrices are cached
+            const int h = quad_h(gP);
+            bool all = true;
+            for (int t = 0; t < 4 && all; ++t) {
+                const int rows = quad_rows(gP, t), nn = t ? h : h + 1;
+                if (rows <= 0) continue;
+                const uint32_t *vi = c->get_vinv(nn, K, VINV_Q0 + t);
+                all = vi != nullptr;
+                if (all) gemms.push_back({nn, rows, GEMM_Q0 + t, K, vi, off, (int)qs.size(), nullptr});
+            }
+            if (!all) return c->fail(GBR_ENOMEM, "interpolation matrices of a quartic point set");
+            done = true;
+        } else if ((int)qs.size() >= kGemmMinPairs && c->gemm_on) {
             if (gsym) {
                 // R(x) = E(x^2) + x O(x^2): E has D/2 + 1 coefficients from h + 1 sums,
                 // O has (D + 1)/2 from h differences (D = P - 1, h = P/2)
@@ -1584,12 +1626,9 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
         if (done) gemm_pairs.insert(gemm_pairs.end(), qs.begin(), qs.end());
         if (done && c->tc_on) {
             // digit tiles for the tensor cores (each matrix of the group, or none)
-            const size_t g0 = gemms.size() - (gsym && gemms.back().mode == GEMM_ODD ? 2 : 1);
             bool all = true;
             for (size_t gi = g0; gi < gemms.size(); ++gi) {
-                const int vmode = gemms[gi].mode == GEMM_EVEN ? VINV_EVEN : gemms[gi].mode == GEMM_ODD ? VINV_ODD
-                                  : gsym                     ? VINV_SYM
-                                                             : VINV_GRID;
+                const int vmode = gemm_vinv_mode(gemms[gi].mode, gsym);
                 gemms[gi].vtc = c->get_vinv_tc(gemms[gi].n, K, vmode);
                 all = all && gemms[gi].vtc;
             }
@@ -1657,14 +1696,13 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
         gg.mode = gm.mode;
         ggroups.push_back(gg);
     }
-    // tiles prime by prime; the even and odd contractions of one symmetric group are
-    // interleaved per prime, so both read the prime's values while they are in L2 and
-    // both halves of each 32-byte coefficient sector are written close together
+    // tiles prime by prime; the contractions of one group of pairs (even and odd
+    // halves, or the four quarter parts) are interleaved per prime, so all read the
+    // prime's values while they are in L2 and the parts of each 32-byte coefficient
+    // sector are written close together
     for (size_t gi = 0; gi < gemms.size();) {
-        const size_t span = gemms[gi].mode == GEMM_EVEN && gi + 1 < gemms.size() && gemms[gi + 1].mode == GEMM_ODD &&
-                                    gemms[gi + 1].off == gemms[gi].off
-                                ? 2
-                                : 1;
+        size_t span = 1;   // the contractions of one group of pairs
+        while (gi + span < gemms.size() && gemms[gi + span].off == gemms[gi].off) ++span;
         for (int i = 0; i < gemms[gi].K; ++i)
             for (size_t g = gi; g < gi + span; ++g) {
                 const Gemm &gm = gemms[g];
@@ -1929,6 +1967,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     st.graph_replayed = replayed ? 1 : 0;
     st.subproblems = subproblems;
     st.root_pairs = root_pairs;
+    st.quad_pairs = quad_pairs;
     st.h2d_bytes = (int64_t)blk.size();
     st.d2h_bytes = (int64_t)sizeof(PairBound) * n + 4;
     r->pend_st = st;
@@ -2177,6 +2216,7 @@ static int res_batch_pipelined(gbr_ctx *c, int n, const gbr_bipoly *f, const gbr
             total.dropped_primes += w->stats.dropped_primes;
             total.redo_warps += w->stats.redo_warps;
             total.root_pairs += w->stats.root_pairs;
+            total.quad_pairs += w->stats.quad_pairs;
         }
         if (x) gbr_free_resident_locked(w, r);
         else shot_release(w, r);

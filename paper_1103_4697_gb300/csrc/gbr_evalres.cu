@@ -132,14 +132,25 @@ __device__ __forceinline__ void evalres_item(const ResLaunch &L, const WorkList 
         const int lane = r & 31;
         const int ii = (r >> 5) * 16 + (lane & 15);
         const bool glane = lane >= 16;
-        const bool roots = P.sym == PTS_ROOTS;
-        const int j = roots ? (ii < P.Pe / 2 ? (glane ? ii + P.Pe / 2 : ii) : -1)
-                            : ii == 0 ? (glane ? -1 : 0) : (glane ? 2 * ii : 2 * ii - 1);
+        const bool roots = P.sym == PTS_ROOTS, quad = P.sym == PTS_QUAD;
         const int pidx = prime_of(P, L.pmap, i);
         const ModP M = L.mods[pidx];
-        const uint32_t a = roots ? root_pow(L.roots + (int64_t)pidx * kRootTabWords,
-                                            (ii * (kRootOrder / P.Pe)) & (kRootOrder - 1), M)
-                                 : mp_to((uint32_t)ii, M);
+        int j;
+        uint32_t a;   // this lane pair's point x (Montgomery form); lanes 16-31 take -x
+        if (roots) {
+            j = ii < P.Pe / 2 ? (glane ? ii + P.Pe / 2 : ii) : -1;
+            a = root_pow(L.roots + (int64_t)pidx * kRootTabWords, (ii * (kRootOrder / P.Pe)) & (kRootOrder - 1), M);
+        } else if (quad) {
+            // ii = 0: x = 0; ii = 2 (aa - 1) + 1 + k0: x = i^k0 aa, value index 1 + 4 (aa - 1) + k0 (+2 for -x)
+            const int aa = (ii + 1) >> 1, k0 = (ii - 1) & 1;
+            j = ii == 0 ? (glane ? -1 : 0) : ii < quad_pairs(P.P) ? 1 + 4 * (aa - 1) + k0 + (glane ? 2 : 0) : -1;
+            const uint32_t im = iota_mont(L, pidx);
+            a = mp_to((uint32_t)aa, M);
+            if (ii > 0 && k0) a = mp_mul(a, im, M);
+        } else {
+            j = ii == 0 ? (glane ? -1 : 0) : (glane ? 2 * ii : 2 * ii - 1);
+            a = mp_to((uint32_t)ii, M);
+        }
         const uint32_t b = mp_mul(a, a, M);
         const uint32_t *rbase = L.res + P.res_off + (int64_t)i * P.S;
         const uint32_t *rc = glane ? rbase + (int64_t)(P.dxf + 1) * rf4 : rbase;
@@ -214,19 +225,31 @@ __global__ void __launch_bounds__(256, reg_min_blocks(N)) k_evalres_reg(ResLaunc
         const int lane = r & 31;
         const int ii = (r >> 5) * 16 + (lane & 15);
         const bool glane = lane >= 16;
-        const bool roots = P.sym == PTS_ROOTS;   // warp-uniform: a warp is one (pair, prime, tile)
-        const int j = roots ? (ii < P.Pe / 2 ? (glane ? ii + P.Pe / 2 : ii) : -1)
-                            : ii == 0 ? (glane ? -1 : 0) : (glane ? 2 * ii : 2 * ii - 1);
+        // warp-uniform: a warp is one (pair, prime, tile)
+        const bool roots = P.sym == PTS_ROOTS, quad = P.sym == PTS_QUAD;
         const int pidx = prime_of(P, L.pmap, i);
         const ModP M = L.mods[pidx];
-        // the point a in normal form: ii (PTS_SYM), or u^ii for the primitive Pe-th
-        // root of unity u = w^(2^kRootLog / Pe) (PTS_ROOTS; the partner lane's point
-        // -a is u^(ii + Pe/2))
+        // the point a in normal form: ii (PTS_SYM); u^ii for the primitive Pe-th root
+        // of unity u = w^(2^kRootLog / Pe) (PTS_ROOTS; the partner lane's point -a is
+        // u^(ii + Pe/2)); aa or i aa (PTS_QUAD, pair index ii = 2 (aa - 1) + 1 + k0,
+        // i^2 = -1, so b = a^2 is aa^2 or p - aa^2)
+        int j = ii == 0 ? (glane ? -1 : 0) : (glane ? 2 * ii : 2 * ii - 1);
         uint32_t a = (uint32_t)ii, b = (uint32_t)ii * (uint32_t)ii;
         if (roots) {
+            j = ii < P.Pe / 2 ? (glane ? ii + P.Pe / 2 : ii) : -1;
             a = mp_from(root_pow(L.roots + (int64_t)pidx * kRootTabWords,
                                  (ii * (kRootOrder / P.Pe)) & (kRootOrder - 1), M), M);
             b = mp_mul(mp_mul(a, a, M), M.r2, M);
+        } else if (quad) {
+            const int aa = (ii + 1) >> 1, k0 = (ii - 1) & 1;
+            const uint32_t im = iota_mont(L, pidx);
+            if (ii > 0) j = ii < quad_pairs(P.P) ? 1 + 4 * (aa - 1) + k0 + (glane ? 2 : 0) : -1;
+            a = (uint32_t)aa;
+            b = (uint32_t)aa * (uint32_t)aa;
+            if (ii > 0 && k0) {
+                a = mp_mul(im, a, M);
+                b = M.p - b;
+            }
         }
         // even and odd parts at b = a^2 (below p) by Shoup steps on the stored
         // c R^2 residues, so the parts come out as R^2 E and R^2 O

@@ -125,9 +125,21 @@ struct PairPlan {
 enum : int32_t { PLAN_ZERO = 1 };
 
 // Point sets: the unit grid 0..Pe-1 (drop mode), the symmetric integers
-// 0, +-1, +-2, ..., or the Pe-th roots of unity u^j with Pe a power of two
-// (interpolated by an inverse transform).
-enum : int32_t { PTS_GRID = 0, PTS_SYM = 1, PTS_ROOTS = 2 };
+// 0, +-1, +-2, ..., the Pe-th roots of unity u^j with Pe a power of two
+// (interpolated by an inverse transform), or the quartic set 0, +-a, +-i a
+// (a = 1..h, i^2 = -1 mod p), whose values at i^k a give the four quarter parts
+// R_t of R(x) = sum_t x^t R_t(x^4) by a 4-point transform.
+enum : int32_t { PTS_GRID = 0, PTS_SYM = 1, PTS_ROOTS = 2, PTS_QUAD = 3 };
+
+// Quartic set: value index 0 is x = 0, index 1 + 4 (a - 1) + k is x = i^k a
+// (k = 0: a, 1: i a, 2: -a, 3: -i a).  The evaluation kernels take the set in
+// +-x lane pairs: pair index ii = 0 is x = 0, ii = 2 (a - 1) + 1 + k0 is x = i^k0 a
+// (k0 = 0, 1), whose partner -x has index + 2.
+GBR_HD int quad_h(int P) { return (P - 1 + 3) / 4; }          // a = 1..h covers P - 1 points
+GBR_HD int quad_pe(int P) { return 4 * quad_h(P) + 1; }
+GBR_HD int quad_pairs(int P) { return 2 * quad_h(P) + 1; }    // +-x lane pairs
+// coefficients of the quarter part R_t of a resultant with P coefficients (degree P - 1)
+GBR_HD int quad_rows(int P, int t) { return P - 1 >= t ? (P - 1 - t) / 4 + 1 : 0; }
 
 // Residue rows of a polynomial of degree m in the eliminated variable, padded to
 // a multiple of 4 (the evaluation reads four rows per 16-byte load).
@@ -231,24 +243,25 @@ GBR_HD int root_points(int P) {
 // elimination (about 1.5 m n products plus the inverse), the inverse transform
 // about 5 N log2 N (it is memory and barrier bound); the integer points'
 // inverse-Vandermonde contraction costs P^2 / 2 multiply-adds (even and odd
-// halves) at about half a product each on the tensor cores (up to 511 points,
-// tiles of 128 pairs) and 0.85 on the integer pipes (tiles of 64 pairs), inflated
-// by the unused part of its last tile;
+// halves; P^2 / 4 for the four quarter parts of a quartic set) at about half a
+// product each on the tensor cores (matrices up to 256 points, tiles of 128 pairs)
+// and 0.85 on the integer pipes (tiles of 64 pairs), inflated by the unused part of
+// its last tile;
 // above 4097 points the integer points fall back to Newton interpolation, which
 // one warp per (pair, prime) runs far slower.  (Constants fitted to the
 // measured crossover of this GPU.)
-GBR_HD bool roots_pay(int P, int N, int tf, int tg, int m, int n, int share, bool tc, bool gemm) {
+GBR_HD bool roots_pay(int P, int N, int tf, int tg, int m, int n, int share, bool tc, bool gemm, bool quad) {
     const double per_point = 0.5 * (tf + tg) + 1.5 * m * n + 5.0 * (m > n ? m : n) + 50.0;
     int lg = 0;
     while ((1 << lg) < N) ++lg;
     const double roots = per_point * (N - P) + 5.0 * N * lg;
     if (!gemm || P > 4097) return true;
     const int s = share < 1 ? 1 : share;
-    const bool on_tc = P <= 511 && tc;
+    const bool on_tc = (quad ? P <= 1021 : P <= 511) && tc;
     const int tile = on_tc ? 128 : 64;
     const double tile_waste = (double)((s + tile - 1) / tile * tile) / s;
     const double per_mac = (on_tc ? 0.5 : 0.85) * tile_waste;
-    return roots < per_mac * 0.5 * (double)P * P;
+    return roots < per_mac * (quad ? 0.25 : 0.5) * (double)P * P;
 }
 
 // ------------------------------------------------------------------ kernel launchers
@@ -362,14 +375,26 @@ cudaError_t launch_pair_garner(const ResLaunch &L, const int32_t *pairs, int n, 
 // With values v(+-i) at a complete symmetric point set, R(x) = E(x^2) + x O(x^2)
 // where E(i^2) = (v(i) + v(-i)) / 2 and O(i^2) = (v(i) - v(-i)) / (2 i): the
 // EVEN and ODD matrices applied to the sums and differences give E and O.
-enum { VINV_GRID = 0, VINV_SYM = 1, VINV_EVEN = 2, VINV_ODD = 3 };
+//   VINV_Q0    x_j = j^4, columns j >= 1 scaled by 1/4
+//   VINV_Qt    x_j = (j+1)^4, column j scaled by 1/(4 (j+1)^t)   (t = 1, 2, 3)
+// With values v(i^k a) at a complete quartic set, R(x) = sum_t x^t R_t(x^4) and
+// sum_k i^(-k t) v(i^k a) = 4 a^t R_t(a^4): the Qt matrices applied to those
+// transforms give the R_t.
+enum { VINV_GRID = 0, VINV_SYM = 1, VINV_EVEN = 2, VINV_ODD = 3, VINV_Q0 = 4 };
 GBR_HD int vinv_point(int mode, int j) {
     return mode == VINV_EVEN ? j * j : mode == VINV_ODD ? (j + 1) * (j + 1) : point_of(mode, j);
 }
 
 // one contraction: coefficients (rows of the matrix) x operand (n entries per
-// pair and prime, formed from the values according to mode)
-enum { GEMM_PLAIN = 0, GEMM_EVEN = 1, GEMM_ODD = 2 };
+// pair and prime, formed from the values according to mode); GEMM_Q0 + t is the
+// quarter part R_t of a quartic set (coefficient r of R_t is coefficient 4 r + t)
+enum { GEMM_PLAIN = 0, GEMM_EVEN = 1, GEMM_ODD = 2, GEMM_Q0 = 3 };
+GBR_HD int gemm_ostride(int mode) { return mode == GEMM_PLAIN ? 1 : mode < GEMM_Q0 ? 2 : 4; }
+GBR_HD int gemm_ooff(int mode) { return mode == GEMM_ODD ? 1 : mode >= GEMM_Q0 ? mode - GEMM_Q0 : 0; }
+GBR_HD int gemm_vinv_mode(int mode, int sym) {
+    return mode == GEMM_EVEN ? VINV_EVEN : mode == GEMM_ODD ? VINV_ODD : mode >= GEMM_Q0 ? VINV_Q0 + mode - GEMM_Q0
+         : sym ? VINV_SYM : VINV_GRID;
+}
 struct GemmGroup {
     const uint32_t *vinv;   // [prime][n][n] inverse Vandermonde matrices
     const uint16_t *vtc;    // the same matrices as bf16 digit tiles (tensor-core path), or null

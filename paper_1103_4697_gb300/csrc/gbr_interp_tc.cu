@@ -159,26 +159,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_interp_tc(ResLaunch L, const 
     // per warp, lanes along K; the 16 KB matrix block) are in flight while chunk kc
     // is split into digits and multiplied
     const int lane = tid & 31;
-    uint32_t ra[TC_M / TC_WARPS], rc[TC_M / TC_WARPS];
+    const uint32_t iota = mode >= GEMM_Q0 ? iota_mont(L, i) : 0u;
+    uint32_t ra[TC_M / TC_WARPS][4];
     uint4 rv[4 * TC_VPLANE / 16 / TC_THREADS];
     auto preload = [&](int kc) {
         const int j = kc * TC_KC + lane;
 #pragma unroll
         for (int it = 0; it < TC_M / TC_WARPS; ++it) {
             const int64_t b = vbs[warp + TC_WARPS * it];
-            uint32_t x = 0u, y = 0u;
-            if (b >= 0 && j < n) {
-                if (mode == GEMM_PLAIN) x = L.val[b + j];
-                else if (mode == GEMM_EVEN) {
-                    x = L.val[j == 0 ? b : b + 2 * j - 1];
-                    y = j == 0 ? 0u : L.val[b + 2 * j];
-                } else {
-                    x = L.val[b + 2 * j + 1];
-                    y = L.val[b + 2 * j + 2];
-                }
-            }
-            ra[it] = x;
-            rc[it] = y;
+            if (b >= 0 && j < n) operand_loads(L.val + b, mode, j, ra[it]);
+            else ra[it][0] = ra[it][1] = ra[it][2] = ra[it][3] = 0u;
         }
         const uint4 *src = reinterpret_cast<const uint4 *>(vt + (int64_t)kc * TC_VTILE_WORDS);
 #pragma unroll
@@ -190,12 +180,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_interp_tc(ResLaunch L, const 
         unsigned char *st = tsm + s * TC_STAGE;
         // stage s is free once the MMAs of chunk kc - 2 have read it
         const bool late = kc >= 2 && !tc_wait((uint32_t)__cvta_generic_to_shared(&bar[s]), ((kc >> 1) - 1) & 1);
-        // the loaded chunk's operand (sums / differences, below p) into raw rows
+        // the loaded chunk's operand (formed from its values, below p) into raw rows
         // (pitch 33 words, not read by the tensor cores)
 #pragma unroll
         for (int it = 0; it < TC_M / TC_WARPS; ++it)
-            raw[(warp + TC_WARPS * it) * 33 + lane] =
-                mode == GEMM_ODD ? mp_sub(ra[it], rc[it], M.p) : mp_add(ra[it], rc[it], M.p);
+            raw[(warp + TC_WARPS * it) * 33 + lane] = operand_combine(ra[it], mode, iota, M);
         // a wait that gave up on any thread ends the loop on all of them before
         // anything is written into a stage an MMA may still be reading
         if (__syncthreads_or(late)) {
@@ -262,7 +251,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_interp_tc(ResLaunch L, const 
     const bool ok = drained && !stalled;
     asm volatile("tcgen05.fence::after_thread_sync;");
     // epilogue: lane tid holds pair q0 + tid; combine the diagonals per coefficient
-    const int ostride = mode == GEMM_PLAIN ? 1 : 2, ooff = mode == GEMM_ODD ? 1 : 0;
+    const int ostride = gemm_ostride(mode), ooff = gemm_ooff(mode);
     const uint64_t off_lo = (uint64_t)M.p << 20, off_hi = (uint64_t)M.p << 11;
     for (int c0 = part * TC_CPT; ok && c0 < (part + 1) * TC_CPT; c0 += 8) {
         uint32_t v[TC_DIAG][8];

@@ -634,6 +634,14 @@ __device__ __forceinline__ uint32_t mont_of_int(int v, const ModP &M) {
     return mp_to(v >= 0 ? (uint32_t)v : M.p - (uint32_t)(-v), M);
 }
 
+// Point x_j of matrix mode `mode` in Montgomery form (the quartic modes' points
+// a^4 exceed 32 bits, so they are formed mod p).
+__device__ __forceinline__ uint32_t vinv_point_mont(int mode, int j, const ModP &M) {
+    if (mode < VINV_Q0) return mont_of_int(vinv_point(mode, j), M);
+    const uint32_t a = mp_to((uint32_t)(mode == VINV_Q0 ? j : j + 1), M), a2 = mp_mul(a, a, M);
+    return mp_mul(a2, a2, M);
+}
+
 __global__ void k_vinv(const ModP *mods, int n, int mode, uint32_t *out) {
     extern __shared__ uint32_t sh[];
     uint32_t *W = sh;             // n + 1 words, Montgomery form
@@ -642,7 +650,7 @@ __global__ void k_vinv(const ModP *mods, int n, int mode, uint32_t *out) {
     for (int t = threadIdx.x; t <= n; t += blockDim.x) W[t] = t == 0 ? M.r1 : 0u;
     __syncthreads();
     for (int j = 0; j < n; ++j) {                 // W <- W (x - x_j), degree j -> j + 1
-        const uint32_t jm = mont_of_int(vinv_point(mode, j), M);
+        const uint32_t jm = vinv_point_mont(mode, j, M);
         uint32_t nv[4];
         int cnt = 0;
         for (int t = threadIdx.x; t <= j + 1 && cnt < 4; t += blockDim.x, ++cnt) {
@@ -656,15 +664,22 @@ __global__ void k_vinv(const ModP *mods, int n, int mode, uint32_t *out) {
     }
     uint32_t *o = out + (int64_t)i * n * n;
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const int xj = vinv_point(mode, j);
+        const uint32_t jm = vinv_point_mont(mode, j, M);
         uint32_t d = M.r1;
         for (int t = 0; t < n; ++t)
-            if (t != j) d = mp_mul(d, mont_of_int(xj - vinv_point(mode, t), M), M);
-        // column scale 1/2 (EVEN, j >= 1) or 1/(2 (j+1)) (ODD) joins the denominator
-        const int den = mode == VINV_EVEN ? (j ? 2 : 1) : mode == VINV_ODD ? 2 * (j + 1) : 1;
-        if (den != 1) d = mp_mul(d, mont_of_int(den, M), M);
+            if (t != j) d = mp_mul(d, mp_sub(jm, vinv_point_mont(mode, t, M), M.p), M);
+        // column scale 1/2 (EVEN, j >= 1), 1/(2 (j+1)) (ODD), 1/4 (Q0, j >= 1) or
+        // 1/(4 (j+1)^t) (Qt) joins the denominator
+        if (mode < VINV_Q0) {
+            const int den = mode == VINV_EVEN ? (j ? 2 : 1) : mode == VINV_ODD ? 2 * (j + 1) : 1;
+            if (den != 1) d = mp_mul(d, mont_of_int(den, M), M);
+        } else if (mode > VINV_Q0 || j) {
+            uint32_t den = mp_to(4u, M);
+            const uint32_t a = mp_to((uint32_t)(j + 1), M);
+            for (int t = 0; t < mode - VINV_Q0; ++t) den = mp_mul(den, a, M);
+            d = mp_mul(d, den, M);
+        }
         const uint32_t id = mp_inv(d, M);
-        const uint32_t jm = mont_of_int(xj, M);
         uint32_t q = W[n];
         o[(int64_t)(n - 1) * n + j] = mp_from(mp_mul(q, id, M), M);
         for (int t = n - 1; t >= 1; --t) {
@@ -727,6 +742,7 @@ __global__ void __launch_bounds__(256, 3) k_interp_gemm(ResLaunch L, const char 
     }
     __syncthreads();
     const uint32_t *A = vinv + (int64_t)i * n * n;
+    const uint32_t iota = mode >= GEMM_Q0 ? iota_mont(L, i) : 0u;
     uint32_t a0[16], a1[16], a2[16];
 #pragma unroll
     for (int t = 0; t < 16; ++t) a0[t] = a1[t] = a2[t] = 0u;
@@ -742,13 +758,7 @@ __global__ void __launch_bounds__(256, 3) k_interp_gemm(ResLaunch L, const char 
             const int c = c0 + r, j = j0 + kk;
             ra[u] = (c < rows && j < n) ? A[(int64_t)c * n + j] : 0u;
             const int64_t b = colbase[r];
-            uint32_t v = 0u;
-            if (b >= 0 && j < n) {
-                if (mode == GEMM_PLAIN) v = L.val[b + j];
-                else if (mode == GEMM_EVEN) v = j == 0 ? L.val[b] : L.val[b + 2 * j - 1] + L.val[b + 2 * j];
-                else v = L.val[b + 2 * j + 1] + (M.p - L.val[b + 2 * j + 2]);
-            }
-            rb[u] = v;
+            rb[u] = b >= 0 && j < n ? contraction_operand(L.val + b, mode, j, iota, M) : 0u;
         }
     };
     load_chunk(0);
@@ -785,7 +795,7 @@ __global__ void __launch_bounds__(256, 3) k_interp_gemm(ResLaunch L, const char 
             Cs[tx * 4 + cc][ty * 4 + r] = mp_add(hi, lo, M.p);
         }
     __syncthreads();
-    const int ostride = mode == GEMM_PLAIN ? 1 : 2, ooff = mode == GEMM_ODD ? 1 : 0;
+    const int ostride = gemm_ostride(mode), ooff = gemm_ooff(mode);
     for (int e = threadIdx.x; e < GT_N * GT_M; e += 256) {
         int qq = e / GT_M, r = e % GT_M;
         int64_t b = colbase[qq];

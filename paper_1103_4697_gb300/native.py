@@ -44,7 +44,8 @@ class Stats(C.Structure):
                 ("total_ms", C.c_double), ("kernels", C.c_int64), ("subproblems", C.c_int64),
                 ("modmul", C.c_int64), ("modmul_evalres", C.c_int64), ("h2d_bytes", C.c_int64),
                 ("d2h_bytes", C.c_int64), ("dropped_points", C.c_int64), ("dropped_primes", C.c_int64),
-                ("graph_replayed", C.c_int64), ("redo_warps", C.c_int64), ("root_pairs", C.c_int64)]
+                ("graph_replayed", C.c_int64), ("redo_warps", C.c_int64), ("root_pairs", C.c_int64),
+                ("quad_pairs", C.c_int64)]
 
 
 class Calib(C.Structure):

@@ -25,7 +25,11 @@ int main() {
                             {401, 231, 231, 20, 20, 8},    {16001, 12003, 12003, 2, 2, 4000}};
     for (auto &c : cases)
         std::printf("roots %d %d %d %d %d %d %d %d\n", c[0], c[1], c[2], c[3], c[4], c[5],
-                    (int)roots_pay(c[0], root_points(c[0]), c[1], c[2], c[3], c[4], c[5], true, true),
-                    (int)roots_pay(c[0], root_points(c[0]), c[1], c[2], c[3], c[4], c[5], true, false));
+                    (int)roots_pay(c[0], root_points(c[0]), c[1], c[2], c[3], c[4], c[5], true, true, false),
+                    (int)roots_pay(c[0], root_points(c[0]), c[1], c[2], c[3], c[4], c[5], true, false, false));
+    // quartic sets: value count, lane pairs and the rows of the quarter parts
+    for (int P = 1; P <= 64; ++P)
+        std::printf("quad %d %d %d %d %d %d %d %d\n", P, quad_h(P), quad_pe(P), quad_pairs(P), quad_rows(P, 0),
+                    quad_rows(P, 1), quad_rows(P, 2), quad_rows(P, 3));
     return 0;
 }

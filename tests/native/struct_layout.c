@@ -22,7 +22,8 @@ int main(void) {
     F(gbr_stats, interp_ms); F(gbr_stats, crt_ms); F(gbr_stats, gcd_ms); F(gbr_stats, total_ms); F(gbr_stats, kernels);
     F(gbr_stats, subproblems); F(gbr_stats, modmul); F(gbr_stats, modmul_evalres); F(gbr_stats, h2d_bytes);
     F(gbr_stats, d2h_bytes); F(gbr_stats, dropped_points); F(gbr_stats, dropped_primes); F(gbr_stats, graph_replayed);
-    F(gbr_stats, redo_warps); F(gbr_stats, root_pairs); printf("\n");
+    F(gbr_stats, redo_warps); F(gbr_stats, root_pairs); F(gbr_stats, quad_pairs);
+    printf("\n");
     printf("Calib %zu", sizeof(gbr_calib)); F(gbr_calib, modmul_per_s); F(gbr_calib, mulsub_per_s);
     F(gbr_calib, sm_clock_mhz); F(gbr_calib, sms); F(gbr_calib, fma3_per_s);
     F(gbr_calib, shoup_per_s); printf("\n");

@@ -169,4 +169,4 @@ def test_automatic_choice_and_drop_mode():
         assert c.resultant_batch(F[:2], G[:2]) == auto_d20[:2]
         assert c.stats()["root_pairs"] == 0
         with pytest.raises(Exception):
-            c.set_option(N.OPT_POINTS, 3)
+            c.set_option(N.OPT_POINTS, 4)

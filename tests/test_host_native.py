@@ -516,7 +516,7 @@ def test_routing_helpers(tmp_path):
         pytest.skip("CUDA headers not found")
     exe = _build(tmp_path, "routing_harness.cpp", ["-I", inc])
     out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.splitlines()
-    seen = {"reg": 0, "pt": 0, "rows4": 0, "rootn": 0, "roots": 0}
+    seen = {"reg": 0, "pt": 0, "rows4": 0, "rootn": 0, "roots": 0, "quad": 0}
     # expected point-set choice per crossover shape: degree-20 and -24 batches and full
     # tiles stay on integer points; small batches, long rows and point counts above the
     # cached contraction's range take roots of unity; without the contraction, always roots
@@ -534,6 +534,15 @@ def test_routing_helpers(tmp_path):
             P, tf, tg, m, n, share, auto, nogemm = v
             assert auto == want_roots[(P, share)] and nogemm == 1, line
             continue
+        if t[0] == "quad":
+            # the points 0 and i^k a (a = 1..h) cover the P coefficients; R_t holds the
+            # coefficients 4 r + t < P
+            P, h, pe, pairs, r0, r1, r2, r3 = v
+            assert 4 * h + 1 >= P > 4 * (h - 1) + 1 or (P == 1 and h == 0), line
+            assert pe == 4 * h + 1 and pairs == 2 * h + 1, line
+            assert [r0, r1, r2, r3] == [len(range(t, P, 4)) for t in range(4)], line
+            assert r0 <= h + 1 and max(r1, r2, r3) <= h, line
+            continue
         if t[0] == "reg":
             m, n, N = v
             top = max(m, n)
@@ -547,6 +556,7 @@ def test_routing_helpers(tmp_path):
             m, r = v
             assert r % 4 == 0 and m + 1 <= r < m + 5, line
     assert seen["reg"] == 41 * 41 and seen["pt"] == 64 and seen["rows4"] == 131 and seen["roots"] == 8
+    assert seen["quad"] == 64
     assert seen["rootn"] > 1100
 
 
@@ -655,6 +665,9 @@ def test_device_prime_table_bytes(tmp_path):
         assert pow(w, 1 << 14, p) == 1 and pow(w, 1 << 13, p) == p - 1
         for j in range(128):
             assert vals[j] == pow(w, j, p) * R % p and vals[128 + j] == pow(w, 128 * j, p) * R % p
+        # the quartic point set reads i = w^(2^12) (R i) straight from T2[32]: i^2 = -1
+        iota = vals[128 + 32] * pow(R, -1, p) % p
+        assert iota * iota % p == p - 1 and vals[0] == R % p
     assert size == NP * (16 + 8 + 256 * 4) + (gd_off(K) + L * ROW + L) * 4
 
 
