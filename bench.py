@@ -299,12 +299,15 @@ def _pow_cost(e: int) -> int:
 
 
 @functools.lru_cache(maxsize=None)
-def regform_ops(m: int, n: int, tf: int, tg: int, p: int, seg: int = 512) -> dict:
+def regform_ops(m: int, n: int, tf: int, tg: int, p: int, seg: int = 512, radix: int = 2) -> dict:
     """Operations the register-form kernel executes for one (prime, point) subproblem of
     a pair of y-degrees (m, n) in one of its shapes (N, N), (N, N-1), (N-1, N), counted
-    from its code: the evaluation's Horner steps in Shoup form ((tf + tg) / 2 per point,
-    tf and tg the numbers of stored coefficients, rows of x-degree e counting e + 1) and
-    the combine E + i O (one product per row and point); elimination: for (N, N) the
+    from its code: the evaluation's Horner steps in Shoup form ((tf + tg) / radix per
+    point, tf and tg the numbers of stored coefficients, rows of x-degree e counting
+    e + 1; radix 2: even and odd parts for +-a, radix 4: the four parts in x^4 for the
+    quartic set's +-a, +-i a) and the combine (radix 2: E + a O, one product per row and
+    point pair; radix 4: a^t P_t and i (A_1 - A_3), four products per row and point
+    quadruple, plus a^3, a^4 per point); elimination: for (N, N) the
     first multiply-subtract row and alpha^N, then N - 1 normal rounds (round of degree d:
     one fused two-product and d - 1 fused three-product updates, and the scalars z^2,
     z alpha, q0, Q z^2 and, after the first round, the telescoped divisor), the two
@@ -313,6 +316,8 @@ def regform_ops(m: int, n: int, tf: int, tg: int, p: int, seg: int = 512) -> dic
     and one Fermat inverse x^(p-2))."""
     N = max(m, n)
     mul = (m + n + 2) / 2 + 2 + 4 + (12 + _pow_cost(p - 2)) / seg
+    if radix == 4:
+        mul += (m + n + 2) / 2 + 4
     mulsub, fma2, fma3 = 0, 0, 0
     if m == n:
         mulsub += N
@@ -322,14 +327,15 @@ def regform_ops(m: int, n: int, tf: int, tg: int, p: int, seg: int = 512) -> dic
         mulsub += 1
         fma2 += 1
         fma3 += d - 1
-    return {"shoup": (tf + tg) / 2, "mul": mul, "mulsub": mulsub + fma2, "fma3": fma3}
+    return {"shoup": (tf + tg) / radix, "mul": mul, "mulsub": mulsub + fma2, "fma3": fma3}
 
 
-def evalres_roofline(F, G, plans: list[dict], table: list[int], cal: dict) -> dict:
+def evalres_roofline(F, G, plans: list[dict], table: list[int], cal: dict, quartic: bool = False) -> dict:
     """Modular products the evaluation + elimination stage executes for a batch of
-    dense pairs (pair q on the first plans[q]["primes"] primes of the table and at
-    deg_bound + 1 points), and the time they would take if every operation ran at its
-    calibrated rate on this GPU."""
+    dense pairs (pair q on the first plans[q]["primes"] primes of the table, at the
+    points of its set: the symmetric integers 0, +-1, ... covering deg_bound + 1, or with
+    `quartic` the set 0, +-a, +-i a, a = 1..ceil(deg_bound / 4), in radix 4), and the time
+    they would take if every operation ran at its calibrated rate on this GPU."""
     import numpy as np
 
     ops = {"shoup": 0.0, "mul": 0.0, "mulsub": 0.0, "fma3": 0.0}
@@ -344,13 +350,14 @@ def evalres_roofline(F, G, plans: list[dict], table: list[int], cal: dict) -> di
     for q in range(len(F)):
         if plans[q]["primes"] <= 0:
             continue
-        points = plans[q]["deg_bound"] + 1
+        D = plans[q]["deg_bound"]
+        points = 4 * ((D + 3) // 4) + 1 if quartic else 2 * ((D + 1) // 2) + 1
         primes = table[:plans[q]["primes"]]
         shapes = [shape(F[q]), shape(G[q])]
         (m, tf), (n, tg) = shapes
-        textbook += len(primes) * points * (tf + tg + 2 * m * n)
+        textbook += len(primes) * (D + 1) * (tf + tg + 2 * m * n)
         for p in primes:
-            for k, v in regform_ops(m, n, tf, tg, p, min(points, 512)).items():
+            for k, v in regform_ops(m, n, tf, tg, p, min(points, 512), 4 if quartic else 2).items():
                 ops[k] += v * points
     products = ops["shoup"] + ops["mul"] + 2 * ops["mulsub"] + 3 * ops["fma3"]
     ideal_s = (ops["shoup"] / cal["shoup_per_s"] + ops["mul"] / cal["modmul_per_s"]
@@ -402,7 +409,8 @@ def _stage_roofline(ctx, st: dict, fs, gs, plans, cal: dict) -> dict:
     at the calibrated rates (register-form count; small runs are launch bound)."""
     from paper_1103_4697_gb300 import api
 
-    rl = evalres_roofline(fs, gs, plans, api.primes(max(p["primes"] for p in plans) or 1), cal)
+    rl = evalres_roofline(fs, gs, plans, api.primes(max(p["primes"] for p in plans) or 1), cal,
+                          st.get("quad_pairs", 0) * 2 > len(fs))
     ms = st["evalres_ms"]
     achieved = rl["products"] / (ms * 1e-3) if ms > 0 else 0.0
     return {"stages_ms": {k: st[k] for k in ("bounds_ms", "reduce_ms", "evalres_ms", "interp_ms", "crt_ms")},
@@ -663,7 +671,8 @@ def run_ours(args) -> None:
     # launch, against the rate this GPU reaches for the same mix of operations
     # (each kind at its calibrated rate)
     plans = res.plan()
-    rl = evalres_roofline(F, G, plans, api.primes(max(p["primes"] for p in plans)), cal)
+    quartic = st["quad_pairs"] == NP            # the point set the planner chose
+    rl = evalres_roofline(F, G, plans, api.primes(max(p["primes"] for p in plans)), cal, quartic)
     achieved = rl["products"] / (evalres_ms * 1e-3)
     peak = rl["products"] / rl["ideal_s"]
     best_single = max(cal["modmul_per_s"], 2 * cal["mulsub_per_s"], 3 * cal["fma3_per_s"], cal["shoup_per_s"])
@@ -726,6 +735,7 @@ def run_ours(args) -> None:
                      "textbook_products_per_launch": rl["textbook_products"],
                      "frac_of_best_single_form": achieved / best_single,
                      "points": plans[0]["deg_bound"] + 1,
+                     "point_set": "quartic 0, +-a, +-i a (radix-4 evaluation)" if quartic else "symmetric integers",
                      "primes": [min(p["primes"] for p in plans), max(p["primes"] for p in plans)]},
         "cpu_baseline": cpu,
         "stages_ms": {k: v / args.steps for k, v in stage.items()},

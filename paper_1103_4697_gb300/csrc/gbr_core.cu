@@ -1424,7 +1424,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
             if (perr[q] || (p.flags & PLAN_ZERO) || p.sym != PTS_SYM || !fits[p.P]) continue;
             p.sym = PTS_QUAD;
             p.Pe = quad_pe(p.P);
-            p.tiles = (quad_pairs(p.P) + 15) / 16;
+            p.tiles = quad_warps(p.P, p.k);
         }
     }
     for (int q = 0; q < n; ++q)
@@ -1523,8 +1523,10 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
         red.add(q, p.S);
         int key = ((std::max(p.m, p.n) + 1) + 3) / 4 * 4;
         const int rN = p.sym && c->reg_on ? reg_shape(p.m, p.n) : 0;
-        if (rN) evr_t[rN].add(q, (int64_t)k * p.tiles * 32);
-        else evb_t[key / 4].add(q, p.sym ? (int64_t)k * p.tiles * 32 : (int64_t)k * p.Pe);
+        // lanes: 32 per warp tile of each prime (a quartic set's warps span its primes)
+        const int64_t lanes = p.sym == PTS_QUAD ? (int64_t)p.tiles * 32 : (int64_t)k * p.tiles * 32;
+        if (rN) evr_t[rN].add(q, lanes);
+        else evb_t[key / 4].add(q, p.sym ? lanes : (int64_t)k * p.Pe);
         // the contraction serves pairs whose points are exactly 0..P-1 and whose
         // primes are the table prefix
         if (p.sym == PTS_ROOTS) {

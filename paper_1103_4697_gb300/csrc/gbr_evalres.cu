@@ -126,13 +126,20 @@ __device__ __forceinline__ void evalres_item(const ResLaunch &L, const WorkList 
         // evaluates even and odd parts of one polynomial at a^2 and hands the
         // partner its value: f-lanes do f, g-lanes do g.  a = ii (PTS_SYM) or
         // u^ii (PTS_ROOTS, -u^ii = u^(ii + Pe/2))
-        const int per = P.tiles * 32;
-        const int i = (int)(local / per);
-        const int r = (int)(local % per);
+        const bool roots = P.sym == PTS_ROOTS, quad = P.sym == PTS_QUAD;
+        const int per = P.tiles * 32;      // lanes per prime (a quartic set's warps span its primes)
+        int i = quad ? 0 : (int)(local / per);
+        const int r = quad ? (int)(local & 31) : (int)(local % per);
         const int lane = r & 31;
         const int ii = (r >> 5) * 16 + (lane & 15);
         const bool glane = lane >= 16;
-        const bool roots = P.sym == PTS_ROOTS, quad = P.sym == PTS_QUAD;
+        QuadLane ql{0, 0, false};
+        if (quad) {
+            // lane pair l = 2 qi + k0 of the warp takes x = i^k0 a of quadruple qi, its
+            // partner -x = i^(k0+2) a
+            ql = quad_lane(P.P, P.k, local >> 5, (lane & 15) >> 1);
+            i = ql.i;
+        }
         const int pidx = prime_of(P, L.pmap, i);
         const ModP M = L.mods[pidx];
         int j;
@@ -141,12 +148,11 @@ __device__ __forceinline__ void evalres_item(const ResLaunch &L, const WorkList 
             j = ii < P.Pe / 2 ? (glane ? ii + P.Pe / 2 : ii) : -1;
             a = root_pow(L.roots + (int64_t)pidx * kRootTabWords, (ii * (kRootOrder / P.Pe)) & (kRootOrder - 1), M);
         } else if (quad) {
-            // ii = 0: x = 0; ii = 2 (aa - 1) + 1 + k0: x = i^k0 aa, value index 1 + 4 (aa - 1) + k0 (+2 for -x)
-            const int aa = (ii + 1) >> 1, k0 = (ii - 1) & 1;
-            j = ii == 0 ? (glane ? -1 : 0) : ii < quad_pairs(P.P) ? 1 + 4 * (aa - 1) + k0 + (glane ? 2 : 0) : -1;
+            const int k0 = lane & 1;
+            j = quad_index(ql, k0 + (glane ? 2 : 0));
             const uint32_t im = iota_mont(L, pidx);
-            a = mp_to((uint32_t)aa, M);
-            if (ii > 0 && k0) a = mp_mul(a, im, M);
+            a = mp_to((uint32_t)ql.a, M);
+            if (k0) a = mp_mul(a, im, M);
         } else {
             j = ii == 0 ? (glane ? -1 : 0) : (glane ? 2 * ii : 2 * ii - 1);
             a = mp_to((uint32_t)ii, M);
@@ -199,8 +205,9 @@ __global__ void k_evalres(ResLaunch L, WorkList w, int SF, int SG) {
 }
 
 // Symmetric pairs of shape (N, N), (N, N-1) or (N-1, N): the same lane pairs
-// as k_evalres, but the evaluated columns stay in registers (handed across by
-// shuffles) and res_chain solves in registers.  A warp with a lane whose
+// as k_evalres (or, on the quartic set, quadruples of lanes evaluating in radix
+// 4), but the evaluated columns stay in registers (handed across by shuffles or
+// the warp's exchange buffer) and res_chain solves in registers.  A warp with a lane whose
 // subproblem needs the general solver is appended to `redo` and written by
 // k_evalres_redo instead (whole warps, since lane pairs share evaluations).
 // blocks of 256 per SM the register allocation must allow: three (80 registers,
@@ -209,111 +216,214 @@ __global__ void k_evalres(ResLaunch L, WorkList w, int SF, int SG) {
 // 4096-pair degree-20 batch); larger N need more registers than that
 constexpr int reg_min_blocks(int N) { return N <= 20 ? 3 : N <= 27 ? 2 : 1; }
 
+// Quartic set, radix 4: lane 8 role + qi of the warp takes the point i^role a of
+// quadruple qi (quad_lane).  The four lanes of a quadruple evaluate 4-row chunks of
+// f and g at all four of its points at once: with c = a^4 a row is
+// P_0(c) + x P_1(c) + x^2 P_2(c) + x^3 P_3(c) at x = i^k a, P_t its part of the
+// powers x^(4 s + t), each by Shoup steps at c on the stored c R^2 residues.  Slot s
+// holds the chunk positions f 2s, g 2s, f 2s+1, g 2s+1, taken by roles 0..3 (s even)
+// or 3..0 (s odd), which evens out the shorter rows of total-degree inputs.  The
+// values meet in the warp's exchange buffer (per position, row and quadruple the
+// four points), where each lane picks those at its own point.
+template <int N>
+__device__ __forceinline__ void quad_eval4(const ResLaunch &L, const PairPlan &P, int64_t local, int lane, uint4 *xb,
+                                           uint32_t (&F)[N + 1], uint32_t (&G)[N + 1], int &i, int &j, ModP &M) {
+    const int role = lane >> 3, qi = lane & 7;
+    const QuadLane ql = quad_lane(P.P, P.k, local >> 5, qi);
+    i = ql.i;
+    j = quad_index(ql, role);
+    const int pidx = prime_of(P, L.pmap, i);
+    M = L.mods[pidx];
+    const uint32_t im = iota_mont(L, pidx);   // i R
+    // powers of a in normal form (a <= 4096, so a^2 < 2^24 < p)
+    const uint32_t a1 = (uint32_t)ql.a, a2 = a1 * a1;
+    const uint32_t a3 = mp_mul(mp_mul(a2, a1, M), M.r2, M), a4 = mp_mul(mp_mul(a2, a2, M), M.r2, M);
+    const uint32_t c4p = (uint32_t)(((uint64_t)a4 << 32) / M.p);
+    const uint32_t np = 0u - M.p;
+    const uint32_t *rf = L.res + P.res_off + (int64_t)i * P.S;
+    const uint32_t *rg = rf + (int64_t)(P.dxf + 1) * rows4(P.m);
+    const uint32_t *xw = reinterpret_cast<const uint32_t *>(xb);
+    constexpr int CF = (N + 1 + 3) / 4;    // 4-row chunks of one polynomial, at most
+    constexpr int SL = (2 * CF + 3) / 4;   // slots of four chunks
+#pragma unroll
+    for (int s = 0; s < SL; ++s) {
+        const int pos = (s & 1) ? 3 - role : role;
+        const bool gp = pos & 1;
+        const int c = 2 * s + (pos >> 1), r0 = 4 * c;
+        const int nrows = (gp ? P.n : P.m) + 1;
+        uint32_t e[4][4];   // [part t][row of the chunk]: R^2 P_t(c), below 3p
+#pragma unroll
+        for (int t = 0; t < 4; ++t) e[t][0] = e[t][1] = e[t][2] = e[t][3] = 0u;
+        if (c < CF && r0 < nrows) {
+            const int32_t *dg = L.rowdeg + (gp ? P.rowdeg_g : P.rowdeg_f);
+            const int step = rows4(gp ? P.n : P.m) >> 2;
+            const uint4 *cp = reinterpret_cast<const uint4 *>((gp ? rg : rf) + r0);
+            int dmax = -1;
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (r0 + t < nrows) dmax = max(dmax, dg[r0 + t]);
+            if (dmax >= 0) {
+                int g = dmax >> 2;   // top group of four powers: only those up to dmax
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    if (4 * g + t <= dmax) {
+                        const uint4 v = cp[(int64_t)(4 * g + t) * step];
+                        e[t][0] = v.x;
+                        e[t][1] = v.y;
+                        e[t][2] = v.z;
+                        e[t][3] = v.w;
+                    }
+                for (--g; g >= 0; --g) {
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const uint4 v = cp[(int64_t)(4 * g + t) * step];
+                        e[t][0] = shoup_step(e[t][0], a4, c4p, v.x, np);
+                        e[t][1] = shoup_step(e[t][1], a4, c4p, v.y, np);
+                        e[t][2] = shoup_step(e[t][2], a4, c4p, v.z, np);
+                        e[t][3] = shoup_step(e[t][3], a4, c4p, v.w, np);
+                    }
+                }
+            }
+        }
+        // the row at x = a, i a, -a, -i a (R-form, below p): with A_t = a^t P_t,
+        // (P_0 + A_2) +- (A_1 + A_3) and (P_0 - A_2) +- i (A_1 - A_3)
+        uint4 out[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t p0 = mp_redc(e[0][q], 0u, M.p, M.pinv);
+            const uint32_t A1 = mp_mul(e[1][q], a1, M), A2 = mp_mul(e[2][q], a2, M), A3 = mp_mul(e[3][q], a3, M);
+            const uint32_t u = mp_add(p0, A2, M.p), v = mp_sub(p0, A2, M.p);
+            const uint32_t sm = mp_add(A1, A3, M.p), d = mp_mul(mp_sub(A1, A3, M.p), im, M);
+            out[q] = make_uint4(mp_add(u, sm, M.p), mp_add(v, d, M.p), mp_sub(u, sm, M.p), mp_sub(v, d, M.p));
+        }
+        __syncwarp();   // the previous slot's reads are done
+#pragma unroll
+        for (int q = 0; q < 4; ++q) xb[(pos * 4 + q) * 8 + qi] = out[q];
+        __syncwarp();
+#pragma unroll
+        for (int ps = 0; ps < 4; ++ps) {
+            const int cc = 2 * s + (ps >> 1);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int row = 4 * cc + q;
+                if (row <= N) {
+                    const uint32_t v = xw[((ps * 4 + q) * 8 + qi) * 4 + role];
+                    if (ps & 1) G[row] = v;
+                    else F[row] = v;
+                }
+            }
+        }
+    }
+}
+
+// Integer points and roots of unity in +-a lane pairs: lane l < 16 and its partner
+// l + 16 take a and -a; the f-lane evaluates f's rows, the g-lane g's, each at both
+// points from the even and odd parts at a^2, and they hand each other the values.
+template <int N>
+__device__ __forceinline__ void pair_eval(const ResLaunch &L, const PairPlan &P, int64_t local, int lane,
+                                          uint32_t (&F)[N + 1], uint32_t (&G)[N + 1], int &i, int &j, ModP &M) {
+    const int per = P.tiles * 32;
+    i = (int)(local / per);
+    const int r = (int)(local % per);
+    const int ii = (r >> 5) * 16 + (lane & 15);
+    const bool glane = lane >= 16;
+    const bool roots = P.sym == PTS_ROOTS;   // warp-uniform: a warp is one (pair, prime, tile)
+    const int pidx = prime_of(P, L.pmap, i);
+    M = L.mods[pidx];
+    // the point a in normal form: ii (PTS_SYM), or u^ii for the primitive Pe-th root
+    // of unity u = w^(2^kRootLog / Pe) (PTS_ROOTS; the partner lane's point -a is
+    // u^(ii + Pe/2))
+    j = ii == 0 ? (glane ? -1 : 0) : (glane ? 2 * ii : 2 * ii - 1);
+    uint32_t a = (uint32_t)ii, b = (uint32_t)ii * (uint32_t)ii;
+    if (roots) {
+        j = ii < P.Pe / 2 ? (glane ? ii + P.Pe / 2 : ii) : -1;
+        a = mp_from(root_pow(L.roots + (int64_t)pidx * kRootTabWords, (ii * (kRootOrder / P.Pe)) & (kRootOrder - 1),
+                             M),
+                    M);
+        b = mp_mul(mp_mul(a, a, M), M.r2, M);
+    }
+    // even and odd parts at b = a^2 (below p) by Shoup steps on the stored
+    // c R^2 residues, so the parts come out as R^2 E and R^2 O
+    const uint32_t bp = (uint32_t)(((uint64_t)b << 32) / M.p);
+    const uint32_t np = 0u - M.p;
+    const int rf4 = rows4(P.m);
+    const uint32_t *rbase = L.res + P.res_off + (int64_t)i * P.S;
+    const uint32_t *rc = glane ? rbase + (int64_t)(P.dxf + 1) * rf4 : rbase;
+    const int32_t *dg = L.rowdeg + (glane ? P.rowdeg_g : P.rowdeg_f);
+    const int nrows = (glane ? P.n : P.m) + 1;
+    const int step = (glane ? rows4(P.n) : rf4) >> 2;
+    // own[k]: this lane's polynomial at its own point; oth[k]: at the partner's
+    uint32_t own[N + 1], oth[N + 1];
+#pragma unroll
+    for (int r0 = 0; r0 <= N; r0 += 4) {
+        uint32_t e[4] = {0u, 0u, 0u, 0u}, o[4] = {0u, 0u, 0u, 0u};
+        if (r0 < nrows) {
+            int dmax = -1;
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (r0 + t < nrows) dmax = max(dmax, dg[r0 + t]);
+            const uint4 *c = reinterpret_cast<const uint4 *>(rc + r0);
+            int x = dmax;
+            if (x >= 0 && (x & 1) == 0) {
+                const uint4 v = c[(int64_t)x * step];
+                e[0] = v.x;
+                e[1] = v.y;
+                e[2] = v.z;
+                e[3] = v.w;
+                --x;
+            }
+            for (; x >= 1; x -= 2) {
+                const uint4 vo = c[(int64_t)x * step];
+                const uint4 ve = c[(int64_t)(x - 1) * step];
+                o[0] = shoup_step(o[0], b, bp, vo.x, np);
+                o[1] = shoup_step(o[1], b, bp, vo.y, np);
+                o[2] = shoup_step(o[2], b, bp, vo.z, np);
+                o[3] = shoup_step(o[3], b, bp, vo.w, np);
+                e[0] = shoup_step(e[0], b, bp, ve.x, np);
+                e[1] = shoup_step(e[1], b, bp, ve.y, np);
+                e[2] = shoup_step(e[2], b, bp, ve.z, np);
+                e[3] = shoup_step(e[3], b, bp, ve.w, np);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            if (r0 + t <= N) {
+                // R E = redc(R^2 E); R a O = redc(R^2 O a) (R^2 O < 3p, so
+                // both inputs stay below p 2^32)
+                const uint32_t ev = mp_redc(e[t], 0u, M.p, M.pinv);
+                const uint32_t io = mp_mul(o[t], a, M);
+                const uint32_t plus = mp_add(ev, io, M.p), minus = mp_sub(ev, io, M.p);
+                own[r0 + t] = glane ? minus : plus;
+                oth[r0 + t] = glane ? plus : minus;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k <= N; ++k) {
+        const uint32_t got = __shfl_xor_sync(0xffffffffu, oth[k], 16);
+        F[k] = glane ? got : own[k];
+        G[k] = glane ? own[k] : got;
+    }
+}
+
 template <int N>
 __global__ void __launch_bounds__(256, reg_min_blocks(N)) k_evalres_reg(ResLaunch L, WorkList w, unsigned long long *redo_n,
                                                      int64_t *redo) {
     if (stage_skipped(L)) return;
+    __shared__ uint4 xq[256 / 32][4 * 4 * 8];   // per warp: the quartic exchange buffer
     for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < w.total;
          item += (int64_t)gridDim.x * blockDim.x) {
         const int bi = wl_find(w.start, w.n, item);
         const int q = w.pairs[bi];
         const int64_t local = item - w.start[bi];
         const PairPlan &P = L.plan[q];
-        const int per = P.tiles * 32;
-        const int i = (int)(local / per);
-        const int r = (int)(local % per);
-        const int lane = r & 31;
-        const int ii = (r >> 5) * 16 + (lane & 15);
-        const bool glane = lane >= 16;
-        // warp-uniform: a warp is one (pair, prime, tile)
-        const bool roots = P.sym == PTS_ROOTS, quad = P.sym == PTS_QUAD;
-        const int pidx = prime_of(P, L.pmap, i);
-        const ModP M = L.mods[pidx];
-        // the point a in normal form: ii (PTS_SYM); u^ii for the primitive Pe-th root
-        // of unity u = w^(2^kRootLog / Pe) (PTS_ROOTS; the partner lane's point -a is
-        // u^(ii + Pe/2)); aa or i aa (PTS_QUAD, pair index ii = 2 (aa - 1) + 1 + k0,
-        // i^2 = -1, so b = a^2 is aa^2 or p - aa^2)
-        int j = ii == 0 ? (glane ? -1 : 0) : (glane ? 2 * ii : 2 * ii - 1);
-        uint32_t a = (uint32_t)ii, b = (uint32_t)ii * (uint32_t)ii;
-        if (roots) {
-            j = ii < P.Pe / 2 ? (glane ? ii + P.Pe / 2 : ii) : -1;
-            a = mp_from(root_pow(L.roots + (int64_t)pidx * kRootTabWords,
-                                 (ii * (kRootOrder / P.Pe)) & (kRootOrder - 1), M), M);
-            b = mp_mul(mp_mul(a, a, M), M.r2, M);
-        } else if (quad) {
-            const int aa = (ii + 1) >> 1, k0 = (ii - 1) & 1;
-            const uint32_t im = iota_mont(L, pidx);
-            if (ii > 0) j = ii < quad_pairs(P.P) ? 1 + 4 * (aa - 1) + k0 + (glane ? 2 : 0) : -1;
-            a = (uint32_t)aa;
-            b = (uint32_t)aa * (uint32_t)aa;
-            if (ii > 0 && k0) {
-                a = mp_mul(im, a, M);
-                b = M.p - b;
-            }
-        }
-        // even and odd parts at b = a^2 (below p) by Shoup steps on the stored
-        // c R^2 residues, so the parts come out as R^2 E and R^2 O
-        const uint32_t bp = (uint32_t)(((uint64_t)b << 32) / M.p);
-        const uint32_t np = 0u - M.p;
-        const int rf4 = rows4(P.m);
-        const uint32_t *rbase = L.res + P.res_off + (int64_t)i * P.S;
-        const uint32_t *rc = glane ? rbase + (int64_t)(P.dxf + 1) * rf4 : rbase;
-        const int32_t *dg = L.rowdeg + (glane ? P.rowdeg_g : P.rowdeg_f);
-        const int nrows = (glane ? P.n : P.m) + 1;
-        const int step = (glane ? rows4(P.n) : rf4) >> 2;
-        // own[k]: this lane's polynomial at its own point; oth[k]: at the partner's
-        uint32_t own[N + 1], oth[N + 1];
-#pragma unroll
-        for (int r0 = 0; r0 <= N; r0 += 4) {
-            uint32_t e[4] = {0u, 0u, 0u, 0u}, o[4] = {0u, 0u, 0u, 0u};
-            if (r0 < nrows) {
-                int dmax = -1;
-#pragma unroll
-                for (int t = 0; t < 4; ++t)
-                    if (r0 + t < nrows) dmax = max(dmax, dg[r0 + t]);
-                const uint4 *c = reinterpret_cast<const uint4 *>(rc + r0);
-                int x = dmax;
-                if (x >= 0 && (x & 1) == 0) {
-                    const uint4 v = c[(int64_t)x * step];
-                    e[0] = v.x;
-                    e[1] = v.y;
-                    e[2] = v.z;
-                    e[3] = v.w;
-                    --x;
-                }
-                for (; x >= 1; x -= 2) {
-                    const uint4 vo = c[(int64_t)x * step];
-                    const uint4 ve = c[(int64_t)(x - 1) * step];
-                    o[0] = shoup_step(o[0], b, bp, vo.x, np);
-                    o[1] = shoup_step(o[1], b, bp, vo.y, np);
-                    o[2] = shoup_step(o[2], b, bp, vo.z, np);
-                    o[3] = shoup_step(o[3], b, bp, vo.w, np);
-                    e[0] = shoup_step(e[0], b, bp, ve.x, np);
-                    e[1] = shoup_step(e[1], b, bp, ve.y, np);
-                    e[2] = shoup_step(e[2], b, bp, ve.z, np);
-                    e[3] = shoup_step(e[3], b, bp, ve.w, np);
-                }
-            }
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                if (r0 + t <= N) {
-                    // R E = redc(R^2 E); R a O = redc(R^2 O a) (R^2 O < 3p, so
-                    // both inputs stay below p 2^32)
-                    const uint32_t ev = mp_redc(e[t], 0u, M.p, M.pinv);
-                    const uint32_t io = mp_mul(o[t], a, M);
-                    const uint32_t plus = mp_add(ev, io, M.p), minus = mp_sub(ev, io, M.p);
-                    own[r0 + t] = glane ? minus : plus;
-                    oth[r0 + t] = glane ? plus : minus;
-                }
-            }
-        }
+        const int lane = (int)(local & 31);   // a pair's lanes start at a multiple of 32
         uint32_t F[N + 1], G[N + 1];
-#pragma unroll
-        for (int k = 0; k <= N; ++k) {
-            const uint32_t got = __shfl_xor_sync(0xffffffffu, oth[k], 16);
-            F[k] = glane ? got : own[k];
-            G[k] = glane ? own[k] : got;
-        }
+        int i, j;
+        ModP M;
+        // warp-uniform: a warp is within one pair
+        if (P.sym == PTS_QUAD) quad_eval4<N>(L, P, local, lane, xq[threadIdx.x >> 5], F, G, i, j, M);
+        else pair_eval<N>(L, P, local, lane, F, G, i, j, M);
         bool ok;
         uint32_t den;
         const uint32_t v = res_chain_frac<N>(F, G, P.m, P.n, M, ok, den);
