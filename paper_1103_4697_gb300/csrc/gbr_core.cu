@@ -1679,6 +1679,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     // one group and prime are adjacent so its V^-1 rows stay in L2)
     std::vector<GemmGroup> ggroups;
     std::vector<GemmTile> gtiles, ttiles;   // integer-pipe and tensor-core contraction tiles
+    int tc_xslots = 2;                        // operand slots the tensor-core launch needs
     {
         size_t nt = 0;
         for (const Gemm &gm : gemms)
@@ -1708,7 +1709,11 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
         for (int i = 0; i < gemms[gi].K; ++i)
             for (size_t g = gi; g < gi + span; ++g) {
                 const Gemm &gm = gemms[g];
-                if (gm.vtc) {
+                if (gm.vtc && gm.n <= kTcResidentN) {
+                    // every row tile in one CTA on the resident operand
+                    for (int q0 = 0; q0 < gm.npairs; q0 += kTcTileN) ttiles.push_back({(int32_t)g, -1, q0, i});
+                    tc_xslots = std::max(tc_xslots, (gm.n + 31) / 32);
+                } else if (gm.vtc) {
                     for (int c0 = 0; c0 < gm.rows; c0 += kTcTileM)
                         for (int q0 = 0; q0 < gm.npairs; q0 += kTcTileN) ttiles.push_back({(int32_t)g, c0, q0, i});
                 } else {
@@ -1888,7 +1893,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
         }
         if (x == cudaSuccess && !ttiles.empty()) {
             x = launch_interp_tc(L, r->d_planblk, (const GemmGroup *)(r->d_planblk + o_ggroups),
-                                 (const GemmTile *)(r->d_planblk + o_ttiles), (int)ttiles.size(), q);
+                                 (const GemmTile *)(r->d_planblk + o_ttiles), (int)ttiles.size(), tc_xslots, q);
             kernels++;
         }
         record(4, capturing, q);

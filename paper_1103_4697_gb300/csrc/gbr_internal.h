@@ -430,12 +430,15 @@ struct GemmTile {
     int32_t group, c0, q0, prime;
 };
 constexpr int kGemmTileM = 64, kGemmTileN = 64;
-// tensor-core contraction (gbr_interp_tc.cu): tiles of 64 coefficients x 128 pairs
+// tensor-core contraction (gbr_interp_tc.cu): tiles of 64 coefficients x 128 pairs;
+// matrices of at most kTcResidentN points run every row tile in one CTA on the
+// operand held in shared memory (tile c0 = -1)
 constexpr int kTcTileM = 64, kTcTileN = 128, kTcMaxN = 256;
+constexpr int kTcResidentChunks = 5, kTcResidentN = 32 * kTcResidentChunks;
 size_t vinv_tc_bytes(int n, int rows, int K);
 cudaError_t launch_vinv_tc(const uint32_t *vinv, int n, int rows, int K, uint16_t *out, cudaStream_t s);
 cudaError_t launch_interp_tc(const ResLaunch &L, const char *planblk, const GemmGroup *groups, const GemmTile *tiles,
-                             int ntiles, cudaStream_t s);
+                             int ntiles, int xslots, cudaStream_t s);
 cudaError_t configure_interp_tc_kernel();
 cudaError_t launch_interp_gemm(const ResLaunch &L, const char *planblk, const GemmGroup *groups,
                                const GemmTile *tiles, int ntiles, cudaStream_t s);

@@ -18,7 +18,11 @@
 // in chunks of 32 through two shared-memory stages: the CTA's threads (four per
 // pair) split the operands into digits while thread 0 issues the 32 MMAs
 // (16 digit pairs x 2 k-steps of 16) of the previous stage; tcgen05.commit
-// releases a stage when its MMAs have read it.  Operand tiles use the
+// releases a stage when its MMAs have read it.  When the operand's whole K
+// extent fits (at most kTcResidentChunks chunks) its digits stay in shared memory
+// and one CTA computes every row tile of the matrix against them, streaming only
+// the matrix tiles, so the operand is loaded and split once instead of once per
+// row tile.  Operand tiles use the
 // no-swizzle K-major layout: core matrices of 8 rows x 8 elements (128 bytes),
 // consecutive along K (LBO = 128 B), row groups 512 B apart (SBO).  The matrix
 // digits are prepared once per cached matrix (k_vinv_tc) in exactly that layout.
@@ -33,14 +37,17 @@ constexpr int TC_DIAG = 7;
 constexpr uint32_t TC_LBO = 128, TC_SBO = 512;
 constexpr int TC_XPLANE = TC_M * TC_KC * 2;        // bytes of one digit plane of the operand tile
 constexpr int TC_VPLANE = TC_N * TC_KC * 2;        // bytes of one digit plane of the matrix tile
-constexpr int TC_STAGE = 4 * TC_XPLANE + 4 * TC_VPLANE;   // 48 KB
+constexpr int TC_XSLOT = 4 * TC_XPLANE;                   // 32 KB: the four digit planes of one chunk
+constexpr int TC_VSLOT = 4 * TC_VPLANE;                   // 16 KB
+constexpr int TC_RAW = TC_M * 33 * 4;                     // raw operand rows of one chunk
+static_assert(kTcResidentChunks * TC_KC == kTcResidentN, "resident operand size");
 constexpr int TC_VTILE_WORDS = 4 * TC_VPLANE / 4;         // uint32 words of one prepared matrix tile
 constexpr int TC_THREADS = 512;                           // 16 warps share the staging of each chunk
 constexpr int TC_WARPS = TC_THREADS / 32;
 constexpr int TC_PER_ROW = TC_THREADS / TC_M;             // threads per operand row (tensor-memory lane)
 constexpr int TC_KG = TC_KC / 8 / TC_PER_ROW;             // K groups of 8 each thread splits per chunk
 constexpr int TC_CPT = TC_N / TC_PER_ROW;                 // epilogue columns per thread
-static_assert(TC_KG >= 1 && TC_CPT % 8 == 0 && TC_M % TC_WARPS == 0, "staging split");
+static_assert(TC_KG >= 1 && TC_CPT % 4 == 0 && TC_M % TC_WARPS == 0, "staging split");
 
 // element (r, k) of a rows x 32 digit plane, in bf16 units
 __host__ __device__ inline int tc_elem(int r, int k) { return (r >> 3) * 256 + (k >> 3) * 64 + (r & 7) * 8 + (k & 7); }
@@ -135,8 +142,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_interp_tc(ResLaunch L, const 
         }
     }
     if (part == 0) vbs[row] = vb;
-    uint32_t *raw = reinterpret_cast<uint32_t *>(tsm + 2 * TC_STAGE);   // TC_M x 33 words
-    const uint32_t *vt = (const uint32_t *)Gr.vtc + ((int64_t)i * nct + T.c0 / TC_N) * nkc * TC_VTILE_WORDS;
+    // resident operand (tile c0 < 0): the operand's digits for all of K stay in
+    // shared memory (one slot per chunk) and the CTA runs every row tile of the
+    // matrix against them; otherwise one row tile, operand and matrix streamed
+    // through two stages
+    const bool resident = T.c0 < 0;
+    const int nrt = resident ? (rows + TC_N - 1) / TC_N : 1, ct0 = resident ? 0 : T.c0 / TC_N;
+    const int xslots = resident ? nkc : 2, steps = nrt * nkc;
+    unsigned char *xsm = tsm;                                        // X digit planes, per slot
+    unsigned char *vsm = tsm + (size_t)xslots * TC_XSLOT;            // V digit planes, two stages
+    uint32_t *raw = reinterpret_cast<uint32_t *>(vsm + 2 * TC_VSLOT);   // TC_M x 33 words
+    const uint32_t *vt = (const uint32_t *)Gr.vtc + ((int64_t)i * nct + ct0) * nkc * TC_VTILE_WORDS;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          (uint32_t)__cvta_generic_to_shared(&tmem_slot)),
@@ -153,38 +169,82 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_interp_tc(ResLaunch L, const 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tbase = tmem_slot;
-    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(tsm);
-    bool stalled = false;   // CTA-uniform: a stage wait gave up, no further chunk is issued
-    // software pipeline: the loads of chunk kc + 1 (operand rows: TC_M / TC_WARPS
-    // per warp, lanes along K; the 16 KB matrix block) are in flight while chunk kc
-    // is split into digits and multiplied
+    const uint32_t xbase = (uint32_t)__cvta_generic_to_shared(xsm), vbase = (uint32_t)__cvta_generic_to_shared(vsm);
+    bool stalled = false;   // CTA-uniform: a wait gave up, no further MMA is issued
+    bool acc_pending = false;   // a commit of the accumulators is issued and not yet seen complete
+    int acc_phase = 0;          // completions of bar[2] seen (one per row tile)
+    // software pipeline over steps (row tile, chunk): the loads of step st + 1
+    // (operand rows: TC_M / TC_WARPS per warp, lanes along K, only while the operand
+    // is still being staged; the 16 KB matrix block) are in flight while step st is
+    // split into digits and multiplied, and during a row tile's epilogue
     const int lane = tid & 31;
     const uint32_t iota = mode >= GEMM_Q0 ? iota_mont(L, i) : 0u;
     uint32_t ra[TC_M / TC_WARPS][4];
     uint4 rv[4 * TC_VPLANE / 16 / TC_THREADS];
-    auto preload = [&](int kc) {
-        const int j = kc * TC_KC + lane;
+    auto preload = [&](int st) {
+        const int c = st / nkc, kc = st - c * nkc;
+        if (!resident || c == 0) {
+            const int j = kc * TC_KC + lane;
 #pragma unroll
-        for (int it = 0; it < TC_M / TC_WARPS; ++it) {
-            const int64_t b = vbs[warp + TC_WARPS * it];
-            if (b >= 0 && j < n) operand_loads(L.val + b, mode, j, ra[it]);
-            else ra[it][0] = ra[it][1] = ra[it][2] = ra[it][3] = 0u;
+            for (int it = 0; it < TC_M / TC_WARPS; ++it) {
+                const int64_t b = vbs[warp + TC_WARPS * it];
+                if (b >= 0 && j < n) operand_loads(L.val + b, mode, j, ra[it]);
+                else ra[it][0] = ra[it][1] = ra[it][2] = ra[it][3] = 0u;
+            }
         }
-        const uint4 *src = reinterpret_cast<const uint4 *>(vt + (int64_t)kc * TC_VTILE_WORDS);
+        const uint4 *src = reinterpret_cast<const uint4 *>(vt + ((int64_t)c * nkc + kc) * TC_VTILE_WORDS);
 #pragma unroll
         for (int u = 0; u < 4 * TC_VPLANE / 16 / TC_THREADS; ++u) rv[u] = __ldg(src + tid + TC_THREADS * u);
     };
+    const int ostride = gemm_ostride(mode), ooff = gemm_ooff(mode);
+    const uint64_t off_lo = (uint64_t)M.p << 20, off_hi = (uint64_t)M.p << 11;
+    // epilogue of row tile ct: lane tid holds pair q0 + tid; combine the diagonals
+    // per coefficient
+    auto epilogue = [&](int ct) {
+        for (int c0 = part * TC_CPT; c0 < (part + 1) * TC_CPT; c0 += 4) {
+            uint32_t v[TC_DIAG][4];
+#pragma unroll
+            for (int u = 0; u < TC_DIAG; ++u) {
+                const uint32_t addr = tbase + ((uint32_t)((warp & 3) * 32) << 16) + u * TC_N + c0;
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                             : "=r"(v[u][0]), "=r"(v[u][1]), "=r"(v[u][2]), "=r"(v[u][3])
+                             : "r"(addr));
+            }
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (vb < 0) continue;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int r = ct * TC_N + c0 + e;
+                if (r >= rows) break;
+                int64_t d[TC_DIAG];
+#pragma unroll
+                for (int u = 0; u < TC_DIAG; ++u) d[u] = (int64_t)__float2int_rn(__uint_as_float(v[u][e]));
+                // C = hi 2^32 + lo with |lo| < 2^49, |hi| < 2^41; both made positive by
+                // multiples of p, then coef = hi + lo R^-1 (mod p)
+                const int64_t lo = d[0] + (d[1] << 8) + (d[2] << 16) + (d[3] << 24);
+                const int64_t hi = d[4] + (d[5] << 8) + (d[6] << 16);
+                const uint64_t tl = (uint64_t)lo + off_lo, th = (uint64_t)hi + off_hi;
+                const uint32_t rl = mp_redc((uint32_t)tl, (uint32_t)(tl >> 32), M.p, M.pinv);
+                const uint32_t rh = mp_mul(mp_redc((uint32_t)th, (uint32_t)(th >> 32), M.p, M.pinv), M.r2, M);
+                L.cf[cb + (int64_t)r * ostride + ooff] = mp_add(rh, rl, M.p);
+            }
+        }
+    };
     preload(0);
-    for (int kc = 0; kc < nkc; ++kc) {
-        const int s = kc & 1;
-        unsigned char *st = tsm + s * TC_STAGE;
-        // stage s is free once the MMAs of chunk kc - 2 have read it
-        const bool late = kc >= 2 && !tc_wait((uint32_t)__cvta_generic_to_shared(&bar[s]), ((kc >> 1) - 1) & 1);
+    for (int st = 0; st < steps; ++st) {
+        const int c = st / nkc, kc = st - c * nkc, s = st & 1;
+        const bool stage_x = !resident || c == 0;
+        const int xs_slot = resident ? kc : s;
+        // stage s (and the streamed operand slot s) is free once the MMAs of step
+        // st - 2 have read it
+        const bool late = st >= 2 && !tc_wait((uint32_t)__cvta_generic_to_shared(&bar[s]), ((st >> 1) - 1) & 1);
         // the loaded chunk's operand (formed from its values, below p) into raw rows
         // (pitch 33 words, not read by the tensor cores)
+        if (stage_x) {
 #pragma unroll
-        for (int it = 0; it < TC_M / TC_WARPS; ++it)
-            raw[(warp + TC_WARPS * it) * 33 + lane] = operand_combine(ra[it], mode, iota, M);
+            for (int it = 0; it < TC_M / TC_WARPS; ++it)
+                raw[(warp + TC_WARPS * it) * 33 + lane] = operand_combine(ra[it], mode, iota, M);
+        }
         // a wait that gave up on any thread ends the loop on all of them before
         // anything is written into a stage an MMA may still be reading
         if (__syncthreads_or(late)) {
@@ -192,13 +252,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_interp_tc(ResLaunch L, const 
             break;
         }
         {
-            uint4 *dst = reinterpret_cast<uint4 *>(st + 4 * TC_XPLANE);
+            uint4 *dst = reinterpret_cast<uint4 *>(vsm + (size_t)s * TC_VSLOT);
 #pragma unroll
             for (int u = 0; u < 4 * TC_VPLANE / 16 / TC_THREADS; ++u) dst[tid + TC_THREADS * u] = rv[u];
         }
-        if (kc + 1 < nkc) preload(kc + 1);
+        if (st + 1 < steps) preload(st + 1);
         // each thread splits TC_KG K groups of its row into four digit planes
-        {
+        if (stage_x) {
+            unsigned char *xd = xsm + (size_t)xs_slot * TC_XSLOT;
             uint32_t pk[4][TC_KG][4];   // [digit][k-group][word]: two bf16 per word
 #pragma unroll
             for (int g = 0; g < TC_KG; ++g)
@@ -215,14 +276,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_interp_tc(ResLaunch L, const 
             for (int t = 0; t < 4; ++t)
 #pragma unroll
                 for (int g = 0; g < TC_KG; ++g)
-                    *reinterpret_cast<uint4 *>(st + t * TC_XPLANE + 2 * tc_elem(row, (TC_KG * part + g) * 8)) =
+                    *reinterpret_cast<uint4 *>(xd + t * TC_XPLANE + 2 * tc_elem(row, (TC_KG * part + g) * 8)) =
                         make_uint4(pk[t][g][0], pk[t][g][1], pk[t][g][2], pk[t][g][3]);
         }
         asm volatile("fence.proxy.async.shared::cta;");
         __syncthreads();
+        const bool last = kc == nkc - 1;   // row tile c complete after this step
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t xs = sbase + s * TC_STAGE, vs = xs + 4 * TC_XPLANE;
+            const uint32_t xs = xbase + xs_slot * TC_XSLOT, vs = vbase + s * TC_VSLOT;
 #pragma unroll
             for (int ks = 0; ks < TC_KC / 16; ++ks)
 #pragma unroll
@@ -240,49 +302,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_interp_tc(ResLaunch L, const 
                     }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 (uint32_t)__cvta_generic_to_shared(&bar[s])));
+            // the accumulators of the row tile are complete when every MMA so far is
+            if (last)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    (uint32_t)__cvta_generic_to_shared(&bar[2])));
+        }
+        if (last) {
+            acc_pending = true;
+            if (!__syncthreads_and(tc_wait((uint32_t)__cvta_generic_to_shared(&bar[2]), acc_phase & 1))) {
+                stalled = true;
+                break;
+            }
+            acc_pending = false;
+            ++acc_phase;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            epilogue(ct0 + c);
+            // every read of the accumulators is done before the next row tile's
+            // first MMA overwrites them
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
         }
     }
-    // one more commit tracks every MMA issued (after the last chunk, or after a
-    // stall); the accumulators are read only when all of them have completed
-    if (tid == 0)
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            (uint32_t)__cvta_generic_to_shared(&bar[2])));
-    const bool drained = __syncthreads_and(tc_wait((uint32_t)__cvta_generic_to_shared(&bar[2]), 0)) != 0;
-    const bool ok = drained && !stalled;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    // epilogue: lane tid holds pair q0 + tid; combine the diagonals per coefficient
-    const int ostride = gemm_ostride(mode), ooff = gemm_ooff(mode);
-    const uint64_t off_lo = (uint64_t)M.p << 20, off_hi = (uint64_t)M.p << 11;
-    for (int c0 = part * TC_CPT; ok && c0 < (part + 1) * TC_CPT; c0 += 8) {
-        uint32_t v[TC_DIAG][8];
-#pragma unroll
-        for (int u = 0; u < TC_DIAG; ++u) {
-            const uint32_t addr = tbase + ((uint32_t)((warp & 3) * 32) << 16) + u * TC_N + c0;
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                         : "=r"(v[u][0]), "=r"(v[u][1]), "=r"(v[u][2]), "=r"(v[u][3]), "=r"(v[u][4]), "=r"(v[u][5]),
-                           "=r"(v[u][6]), "=r"(v[u][7])
-                         : "r"(addr));
-        }
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
-        if (vb < 0) continue;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int r = T.c0 + c0 + e;
-            if (r >= rows) break;
-            int64_t d[TC_DIAG];
-#pragma unroll
-            for (int u = 0; u < TC_DIAG; ++u) d[u] = (int64_t)__float2int_rn(__uint_as_float(v[u][e]));
-            // C = hi 2^32 + lo with |lo| < 2^49, |hi| < 2^41; both made positive by
-            // multiples of p, then coef = hi + lo R^-1 (mod p)
-            const int64_t lo = d[0] + (d[1] << 8) + (d[2] << 16) + (d[3] << 24);
-            const int64_t hi = d[4] + (d[5] << 8) + (d[6] << 16);
-            const uint64_t tl = (uint64_t)lo + off_lo, th = (uint64_t)hi + off_hi;
-            const uint32_t rl = mp_redc((uint32_t)tl, (uint32_t)(tl >> 32), M.p, M.pinv);
-            const uint32_t rh = mp_mul(mp_redc((uint32_t)th, (uint32_t)(th >> 32), M.p, M.pinv), M.r2, M);
-            L.cf[cb + (int64_t)r * ostride + ooff] = mp_add(rh, rl, M.p);
-        }
+    if (stalled) {
+        // one more commit tracks every MMA issued, unless the row tile's own commit
+        // is still outstanding; nothing is read or written, the tensor memory is
+        // given back only when they have completed (or that wait gives up too)
+        if (tid == 0 && !acc_pending)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                (uint32_t)__cvta_generic_to_shared(&bar[2])));
+        __syncthreads_and(tc_wait((uint32_t)__cvta_generic_to_shared(&bar[2]), acc_phase & 1));
+        if (tid == 0) atomicExch(L.err, kErrTensorStall);
     }
-    if (!ok && tid == 0) atomicExch(L.err, kErrTensorStall);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(512));
@@ -301,20 +351,24 @@ cudaError_t launch_vinv_tc(const uint32_t *vinv, int n, int rows, int K, uint16_
     return cudaGetLastError();
 }
 
-// One CTA per tile (the tile's c0 a multiple of 64, q0 of 128); the shared
-// memory request (two stages, rounded up past half the SM) keeps one CTA per
-// SM, which also owns the SM's 512 tensor-memory columns.
+// One CTA per tile (q0 a multiple of 128; c0 a multiple of 64, or -1 for every row
+// tile on a resident operand of at most kTcResidentChunks chunks).  The shared
+// memory request (operand slots, two matrix stages, the raw rows; at least past half
+// the SM) keeps one CTA per SM, which also owns the SM's 512 tensor-memory columns.
+constexpr size_t kTcSmemMax = (size_t)kTcResidentChunks * TC_XSLOT + 2 * TC_VSLOT + TC_RAW;
+static_assert(kTcSmemMax <= 227 * 1024, "the resident operand fits one CTA's shared memory");
+
 cudaError_t launch_interp_tc(const ResLaunch &L, const char *planblk, const GemmGroup *groups, const GemmTile *tiles,
-                             int ntiles, cudaStream_t s) {
+                             int ntiles, int xslots, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
-    const size_t smem = (size_t)120 * 1024;
-    static_assert(2 * TC_STAGE + TC_M * 33 * 4 <= 120 * 1024, "two stages and the raw rows fit the request");
+    if (xslots < 2 || xslots > kTcResidentChunks) return cudaErrorInvalidValue;
+    const size_t smem = std::max<size_t>((size_t)xslots * TC_XSLOT + 2 * TC_VSLOT + TC_RAW, (size_t)120 * 1024);
     k_interp_tc<<<ntiles, TC_THREADS, smem, s>>>(L, planblk, groups, tiles);
     return cudaGetLastError();
 }
 
 cudaError_t configure_interp_tc_kernel() {
-    return cudaFuncSetAttribute(k_interp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 120 * 1024);
+    return cudaFuncSetAttribute(k_interp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax);
 }
 
 }  // namespace gbr

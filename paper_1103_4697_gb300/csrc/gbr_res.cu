@@ -469,26 +469,33 @@ cudaError_t launch_plan_check(const PairBound *bounds, const PairPlan *plan, int
 
 __global__ void k_reduce(ResLaunch L, WorkList w) {
     if (stage_skipped(L)) return;
-    for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < w.total;
-         item += (int64_t)gridDim.x * blockDim.x) {
-        int bi = wl_find(w.start, w.n, item);
-        int q = w.pairs[bi];
-        int64_t s = item - w.start[bi];
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x - lane; base < w.total; base += stride) {
+        // a warp's items are consecutive: one search for its first item, and each
+        // lane steps over the pair boundaries after it
+        int bi = lane == 0 ? wl_find(w.start, w.n, base) : 0;
+        bi = __shfl_sync(0xffffffffu, bi, 0);
+        const int64_t item = base + lane;
+        if (item >= w.total) continue;
+        while (bi + 1 < w.n && item >= w.start[bi + 1]) ++bi;
+        const int q = w.pairs[bi];
+        const int s = (int)(item - w.start[bi]);   // below S < 2^31
         const PairPlan &P = L.plan[q];
         const PairDesc &D = L.desc[q];
         const int rf4 = rows4(P.m), rg4 = rows4(P.n);
-        const int64_t nf = (int64_t)(P.dxf + 1) * rf4;
+        const int nf = (P.dxf + 1) * rf4;
         const PolyDesc *src;
         int row, col, mult = 0, nrows;
         if (s < nf) {
             src = &D.f;
-            col = (int)(s / rf4);
-            row = (int)(s % rf4);
+            col = s / rf4;
+            row = s - col * rf4;
             nrows = P.m + 1;
         } else {
-            int64_t s2 = s - nf;
-            col = (int)(s2 / rg4);
-            row = (int)(s2 % rg4);
+            const int s2 = s - nf;
+            col = s2 / rg4;
+            row = s2 - col * rg4;
             nrows = P.n + 1;
             if (D.disc) {
                 src = &D.f;
@@ -498,40 +505,49 @@ __global__ void k_reduce(ResLaunch L, WorkList w) {
             }
         }
         uint32_t *dst = L.res + P.res_off + s;
+        const int K = P.k, S = P.S;
         if (row >= nrows) {                       // padding rows hold zeros
-            for (int i = 0; i < P.k; ++i) dst[(int64_t)i * P.S] = 0u;
+            for (int i = 0; i < K; ++i, dst += S) *dst = 0u;
             continue;
         }
         const uint64_t *cp = coef_ptr(L.coef, *src, mult ? row + 1 : row, col);
         int W = src->words;
         if (W == 1) {
             // |c| = hi 2^32 + lo: c R^2 = redc(hi R^4 + lo R^3); the sum is below
-            // 2p 2^32, so the reduction leaves a value below 3p
+            // 2p 2^32, so the reduction leaves a value below 3p.  With hi = 0 (every
+            // coefficient of the warp below 2^32) one product: redc(lo R^3) < 2p.
             const int64_t v = (int64_t)cp[0];
             const bool neg = v < 0;
             const uint64_t av = neg ? 0ull - (uint64_t)v : (uint64_t)v;
             const uint32_t hi = (uint32_t)(av >> 32), lo = (uint32_t)av;
-            for (int i = 0; i < P.k; ++i) {
-                const int pi = prime_of(P, L.pmap, i);
+            const bool wide = __any_sync(__activemask(), hi != 0u);
+            const int32_t *pm = P.pmap_off < 0 ? nullptr : L.pmap + P.pmap_off;
+            for (int i = 0; i < K; ++i, dst += S) {
+                const int pi = pm ? pm[i] : i;
                 const ModP M = L.mods[pi];
                 const uint2 r34 = L.r34[pi];
-                const uint64_t t = (uint64_t)hi * r34.y + (uint64_t)lo * r34.x;
-                const uint32_t m = (uint32_t)t * M.pinv;
-                uint32_t r = (uint32_t)((t + (uint64_t)m * M.p) >> 32);
-                r = min(r, r - M.p);
+                uint32_t r;
+                if (wide) {
+                    const uint64_t t = (uint64_t)hi * r34.y + (uint64_t)lo * r34.x;
+                    const uint32_t m = (uint32_t)t * M.pinv;
+                    r = (uint32_t)((t + (uint64_t)m * M.p) >> 32);
+                    r = min(r, r - M.p);
+                } else {
+                    r = mp_redc(lo * r34.x, __umulhi(lo, r34.x), M.p, M.pinv);
+                }
                 r = min(r, r - M.p);
                 if (mult) r = mp_mul(r, mp_to((uint32_t)mult, M), M);
-                dst[(int64_t)i * P.S] = neg ? mp_neg(r, M.p) : r;
+                *dst = neg ? mp_neg(r, M.p) : r;
             }
             continue;
         }
         uint64_t wbuf[8];
         for (int i = 0; i < W; ++i) wbuf[i] = cp[i];
-        for (int i = 0; i < P.k; ++i) {
+        for (int i = 0; i < K; ++i, dst += S) {
             ModP M = L.mods[prime_of(P, L.pmap, i)];
             uint32_t r = mp_from_words(wbuf, W, M);
             if (mult) r = mp_mul(r, mp_to((uint32_t)mult, M), M);
-            dst[(int64_t)i * P.S] = mp_mul(r, M.r2, M);   // c R^2: one reduction per Horner step
+            *dst = mp_mul(r, M.r2, M);   // c R^2: one reduction per Horner step
         }
     }
 }
@@ -902,66 +918,103 @@ __global__ void k_crt_fast(ResLaunch L, WorkList w, int KD, int LD) {
     __syncthreads();
     uint32_t *dw = reinterpret_cast<uint32_t *>(dig);
     auto dslot = [&](int i) -> uint32_t & { return dw[((size_t)(i >> 2) * BS + threadIdx.x) * 4 + (i & 3)]; };
-    for (int64_t item = blockIdx.x * (int64_t)BS + threadIdx.x; item < w.total; item += (int64_t)gridDim.x * BS) {
-        const int bi = wl_find(w.start, w.n, item);
-        const int q = w.pairs[bi];
-        const int c = (int)(item - w.start[bi]);
-        const PairPlan &P = L.plan[q];
-        const int k = P.k, Pn = P.P, k4 = (k + 3) >> 2;
-        const uint32_t *src = L.cf + P.cf_off + c;
-        dslot(0) = src[0];
-        for (int i = k; i < 4 * k4; ++i) dslot(i) = 0u;   // the last group's unused digits
-        for (int i = 1; i < k; ++i) {
-            const ModP M = L.mods[i];
-            uint32_t a0 = 0u, a1 = src[(int64_t)i * Pn], a2 = 0u;
-            const uint4 *row = reinterpret_cast<const uint4 *>(Gd + crt_gd_off(i));
-            for (int g = 0; g < ((i + 3) >> 2); ++g) {
-                const uint4 d = dig[(size_t)g * BS + threadIdx.x], e = row[g];
-                mac96(a0, a1, a2, d.x, e.x);
-                mac96(a0, a1, a2, d.y, e.y);
-                mac96(a0, a1, a2, d.z, e.z);
-                mac96(a0, a1, a2, d.w, e.w);
+    // per warp the limbs of its 32 coefficients (pitch LD + 1), written out together
+    const int lane = threadIdx.x & 31, opitch = LD + 1;
+    uint32_t *ow = reinterpret_cast<uint32_t *>(dig + (size_t)((KD + 3) >> 2) * BS) + (size_t)(threadIdx.x >> 5) * 32 * opitch;
+    for (int64_t base = blockIdx.x * (int64_t)BS + threadIdx.x - lane; base < w.total; base += (int64_t)gridDim.x * BS) {
+        // a warp's items are consecutive: one search for its first item, and each
+        // lane steps over the pair boundaries after it
+        int bi = lane == 0 ? wl_find(w.start, w.n, base) : 0;
+        bi = __shfl_sync(0xffffffffu, bi, 0);
+        const int64_t item = base + lane;
+        const bool valid = item < w.total;
+        if (valid)
+            while (bi + 1 < w.n && item >= w.start[bi + 1]) ++bi;
+        const int q = valid ? w.pairs[bi] : -1;
+        int top = -1, Lp = 0;    // this coefficient's index if non-zero; its limbs
+        int64_t obase = 0;       // where its limbs go
+        if (valid) {
+            const int c = (int)(item - w.start[bi]);
+            const PairPlan &P = L.plan[q];
+            const int k = P.k, Pn = P.P, k4 = (k + 3) >> 2;
+            const uint32_t *src = L.cf + P.cf_off + c;
+            dslot(0) = src[0];
+            for (int i = k; i < 4 * k4; ++i) dslot(i) = 0u;   // the last group's unused digits
+            for (int i = 1; i < k; ++i) {
+                const ModP M = L.mods[i];
+                uint32_t a0 = 0u, a1 = src[(int64_t)i * Pn], a2 = 0u;
+                const uint4 *row = reinterpret_cast<const uint4 *>(Gd + crt_gd_off(i));
+                for (int g = 0; g < ((i + 3) >> 2); ++g) {
+                    const uint4 d = dig[(size_t)g * BS + threadIdx.x], e = row[g];
+                    mac96(a0, a1, a2, d.x, e.x);
+                    mac96(a0, a1, a2, d.y, e.y);
+                    mac96(a0, a1, a2, d.z, e.z);
+                    mac96(a0, a1, a2, d.w, e.w);
+                }
+                // (a2 2^32 + a1) + a0 2^-32 = R (r_i - S) 2^-32 = r_i - S (mod p_i)
+                const uint32_t hi = mp_mul(mp_redc(a1, a2, M.p, M.pinv), M.r2, M);
+                const uint32_t y = mp_add(hi, mp_redc(a0, 0u, M.p, M.pinv), M.p);
+                dslot(i) = mp_mul(y, L.garner[i], M);
             }
-            // (a2 2^32 + a1) + a0 2^-32 = R (r_i - S) 2^-32 = r_i - S (mod p_i)
-            const uint32_t hi = mp_mul(mp_redc(a1, a2, M.p, M.pinv), M.r2, M);
-            const uint32_t y = mp_add(hi, mp_redc(a0, 0u, M.p, M.pinv), M.p);
-            dslot(i) = mp_mul(y, L.garner[i], M);
-        }
-        // symmetric lift: X > (M-1)/2 <=> digits compare above (p_i - 1)/2 from the top
-        int cmp = 0;
-        for (int i = k - 1; i >= 0 && cmp == 0; --i) {
-            const uint32_t d = dslot(i), h = (L.mods[i].p - 1u) >> 1;
-            cmp = (d > h) - (d < h);
-        }
-        const bool neg = cmp > 0;
-        uint32_t *o = L.out + P.out_off + (int64_t)c * P.L;
-        uint32_t c0 = 0u, c1 = 0u, borrow = 0u;
-        int nl = 0;
-        for (int l = 0; l < P.L; ++l) {
-            uint32_t a0 = c0, a1 = c1, a2 = 0u;
-            const uint32_t *Tl = T + (size_t)l * kCrtFastRow;
-            for (int g = (int)(I0[l] >> 2); g < k4; ++g) {
-                const uint4 d = dig[(size_t)g * BS + threadIdx.x];
-                const uint4 e = *reinterpret_cast<const uint4 *>(Tl + 4 * g);
-                mac96(a0, a1, a2, d.x, e.x);
-                mac96(a0, a1, a2, d.y, e.y);
-                mac96(a0, a1, a2, d.z, e.z);
-                mac96(a0, a1, a2, d.w, e.w);
+            // symmetric lift: X > (M-1)/2 <=> digits compare above (p_i - 1)/2 from the top
+            int cmp = 0;
+            for (int i = k - 1; i >= 0 && cmp == 0; --i) {
+                const uint32_t d = dslot(i), h = (L.mods[i].p - 1u) >> 1;
+                cmp = (d > h) - (d < h);
             }
-            c0 = a1;
-            c1 = a2;
-            uint32_t x = a0;
-            if (neg) {
-                const uint32_t m = Tl[k];
-                const uint64_t t = (uint64_t)m - x - borrow;
-                x = (uint32_t)t;
-                borrow = (uint32_t)(t >> 63);
+            const bool neg = cmp > 0;
+            uint32_t *o = ow + lane * opitch;
+            uint32_t c0 = 0u, c1 = 0u, borrow = 0u;
+            int nl = 0;
+            for (int l = 0; l < P.L; ++l) {
+                uint32_t a0 = c0, a1 = c1, a2 = 0u;
+                const uint32_t *Tl = T + (size_t)l * kCrtFastRow;
+                for (int g = (int)(I0[l] >> 2); g < k4; ++g) {
+                    const uint4 d = dig[(size_t)g * BS + threadIdx.x];
+                    const uint4 e = *reinterpret_cast<const uint4 *>(Tl + 4 * g);
+                    mac96(a0, a1, a2, d.x, e.x);
+                    mac96(a0, a1, a2, d.y, e.y);
+                    mac96(a0, a1, a2, d.z, e.z);
+                    mac96(a0, a1, a2, d.w, e.w);
+                }
+                c0 = a1;
+                c1 = a2;
+                uint32_t x = a0;
+                if (neg) {
+                    const uint32_t m = Tl[k];
+                    const uint64_t t = (uint64_t)m - x - borrow;
+                    x = (uint32_t)t;
+                    borrow = (uint32_t)(t >> 63);
+                }
+                o[l] = x;
+                if (x) nl = l + 1;
             }
-            o[l] = x;
-            if (x) nl = l + 1;
+            L.sign[P.sign_off + c] = nl == 0 ? 0 : (neg ? -1 : 1);
+            top = nl > 0 ? c : -1;
+            Lp = P.L;
+            obase = P.out_off + (int64_t)c * P.L;
         }
-        L.sign[P.sign_off + c] = nl == 0 ? 0 : (neg ? -1 : 1);
-        if (nl > 0) atomicMax(L.deg + q, c);
+        __syncwarp();
+        // when the warp's coefficients are consecutive ones of one pair (its valid
+        // lanes are a prefix), their limbs are one run of memory: store it
+        // coalesced, and raise the pair's degree once
+        const int q0 = __shfl_sync(0xffffffffu, q, 0), L0 = __shfl_sync(0xffffffffu, Lp, 0);
+        const int64_t ob0 = __shfl_sync(0xffffffffu, obase, 0);
+        const bool run = __all_sync(0xffffffffu, !valid || (q == q0 && obase == ob0 + (int64_t)lane * L0));
+        if (run) {
+            const int nv = __popc(__ballot_sync(0xffffffffu, valid));
+            const int tmax = __reduce_max_sync(0xffffffffu, top);
+            if (lane == 0 && tmax >= 0) atomicMax(L.deg + q0, tmax);
+            int j = lane / L0, l = lane - j * L0;   // word e = j L0 + l of the run
+            for (int e = lane; e < nv * L0; e += 32) {
+                L.out[ob0 + e] = ow[j * opitch + l];
+                for (l += 32; l >= L0; l -= L0) ++j;
+            }
+        } else if (valid) {
+            if (top >= 0) atomicMax(L.deg + q, top);
+            for (int l = 0; l < Lp; ++l) L.out[obase + l] = ow[lane * opitch + l];
+        }
+        __syncwarp();
     }
 }
 
@@ -1074,7 +1127,8 @@ cudaError_t launch_crt_fast(const ResLaunch &L, const WorkList &w, int maxK, int
     if (maxK > kCrtFastK || maxL > kCrtFastL) return cudaErrorInvalidValue;
     const int block = 128, k4 = (maxK + 3) / 4;
     const size_t tab = (size_t)((crt_gd_off(maxK) + 3) & ~3) + (size_t)maxL * kCrtFastRow + ((maxL + 3) & ~3);
-    const size_t smem = tab * 4 + (size_t)k4 * block * 16;
+    // tables, digits (k4 per thread) and the staged output limbs (maxL + 1 per thread)
+    const size_t smem = tab * 4 + (size_t)k4 * block * 16 + (size_t)block * (maxL + 1) * 4;
     if (smem > kMaxDynSmem) return cudaErrorInvalidValue;
     int grid = persistent_grid(k_crt_fast, block, smem, (w.total + block - 1) / block);
     k_crt_fast<<<grid, block, smem, s>>>(L, w, maxK, maxL);
