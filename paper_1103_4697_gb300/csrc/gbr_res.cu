@@ -467,8 +467,24 @@ cudaError_t launch_plan_check(const PairBound *bounds, const PairPlan *plan, int
 
 // ------------------------------------------------------------------ A1: modular reduction
 
+// Shoup constants of c -> c R^2 for the first kReduceSmemPrimes table primes: with
+// W = R^2 mod p, floor(W 2^32 / p) = (W 2^32 - R^3 mod p) / p is congruent to
+// -(R^3 mod p) p^-1 = (R^3 mod p) pinv modulo 2^32, and is below 2^32.
+// (The table holds more primes than that: its CRT tables already cover the first
+// kCrtFastK.)
+constexpr int kReduceSmemPrimes = 64;
+static_assert(kReduceSmemPrimes <= kCrtFastK, "the table holds the primes whose constants are staged");
+
 __global__ void k_reduce(ResLaunch L, WorkList w) {
     if (stage_skipped(L)) return;
+    __shared__ uint32_t sp[kReduceSmemPrimes], sw[kReduceSmemPrimes], swp[kReduceSmemPrimes];
+    for (int t = threadIdx.x; t < kReduceSmemPrimes; t += blockDim.x) {
+        const ModP M = L.mods[t];
+        sp[t] = M.p;
+        sw[t] = M.r2;
+        swp[t] = L.r34[t].x * M.pinv;
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = blockIdx.x * (int64_t)blockDim.x + threadIdx.x - lane; base < w.total; base += stride) {
@@ -522,6 +538,16 @@ __global__ void k_reduce(ResLaunch L, WorkList w) {
             const uint32_t hi = (uint32_t)(av >> 32), lo = (uint32_t)av;
             const bool wide = __any_sync(__activemask(), hi != 0u);
             const int32_t *pm = P.pmap_off < 0 ? nullptr : L.pmap + P.pmap_off;
+            if (!wide && !mult && !pm && K <= kReduceSmemPrimes) {
+                // one Shoup product lo W - q p with q = floor(lo W' / 2^32): in [0, 2p)
+                for (int i = 0; i < K; ++i, dst += S) {
+                    const uint32_t p = sp[i];
+                    uint32_t r = lo * sw[i] - __umulhi(lo, swp[i]) * p;
+                    r = min(r, r - p);
+                    *dst = neg ? mp_neg(r, p) : r;
+                }
+                continue;
+            }
             for (int i = 0; i < K; ++i, dst += S) {
                 const int pi = pm ? pm[i] : i;
                 const ModP M = L.mods[pi];

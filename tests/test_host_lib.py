@@ -82,6 +82,24 @@ def test_prime_table(lib):
     assert lib.gbr_prime(-1, C.byref(p)) == N.EINVAL
 
 
+def test_reduction_shoup_constant(lib):
+    """The reduction kernel forms c R^2 mod p (R = 2^32) of a one-word coefficient by one
+    Shoup product with W = R^2 mod p, taking floor(W 2^32 / p) as (R^3 mod p) times
+    -p^-1 modulo 2^32 (W 2^32 = floor(W 2^32 / p) p + (R^3 mod p), an exact division).
+    For every 32-bit c the product c W - floor(c W' / 2^32) p lies in [0, 2p)."""
+    from paper_1103_4697_gb300.api import primes
+
+    R = 1 << 32
+    rng = random.Random(5)
+    for p in primes(64):
+        W, t3 = R * R % p, R ** 3 % p
+        wp = t3 * ((-pow(p, -1, R)) % R) % R
+        assert wp == W * R // p
+        for c in [0, 1, p - 1, p, p + 1, 2 ** 31, R - 1] + [rng.randrange(R) for _ in range(100)]:
+            r = (c * W - ((c * wp) >> 32) * p) % R
+            assert r < 2 * p and r % p == c * W % p
+
+
 @pytest.mark.parametrize("bits", [0.0, 1.0, 30.0, 31.0, 61.9, 100.0, 860.0, 9500.0])
 def test_primes_for_bits(lib, bits):
     from paper_1103_4697_gb300.api import primes
