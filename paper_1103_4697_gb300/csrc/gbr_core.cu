@@ -1492,6 +1492,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
         const PairBound &b = hb[q];
         PairPlan &p = plan[q];
         p.res_off = res_w;
+        if (p.sym == PTS_QUAD) val_w = (val_w + 3) & ~(int64_t)3;   // 16-byte aligned point quadruples
         p.val_off = val_w;
         p.cf_off = cf_w;
         p.out_off = out_w;

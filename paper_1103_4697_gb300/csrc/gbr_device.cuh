@@ -26,14 +26,16 @@ __device__ __forceinline__ uint32_t quad_point_mont(int j, uint32_t iota_m, cons
     return (k & 2) ? mp_neg(x, M.p) : x;
 }
 
-// Entry j of the contraction operand of group `mode` from one pair's values v
-// (Montgomery form, below p): GEMM_PLAIN v_j; GEMM_EVEN v(0) (j = 0) or
+// Entry j of the contraction operand of group `mode` (n points) from one pair's
+// values v (Montgomery form, below p): GEMM_PLAIN v_j; GEMM_EVEN v(0) (j = 0) or
 // v(j) + v(-j); GEMM_ODD v(j+1) - v(-(j+1)); GEMM_Q0 v(0) (j = 0) or
 // sum_k v(i^k j); GEMM_Q0 + t (t = 1, 2, 3) sum_k i^(-k t) v(i^k (j+1)).  In two
 // steps, so that a pipelined caller can keep the loads in flight: operand_loads
-// fetches the (up to four) values, operand_combine forms the entry (below p, in
-// the values' form; iota is i in Montgomery form, read by the quartic modes only).
-__device__ __forceinline__ void operand_loads(const uint32_t *v, int mode, int j, uint32_t (&x)[4]) {
+// fetches the (up to four) values, a quartic quadruple as one 16-byte load (v is
+// 16-byte aligned for quartic pairs; the point 0 sits at 4 h = 4 (n - 1) for
+// GEMM_Q0), operand_combine forms the entry (below p, in the values' form; iota is i
+// in Montgomery form, read by the quartic modes only).
+__device__ __forceinline__ void operand_loads(const uint32_t *v, int mode, int j, int n, uint32_t (&x)[4]) {
     x[1] = x[2] = x[3] = 0u;
     if (mode == GEMM_PLAIN) {
         x[0] = v[j];
@@ -44,13 +46,13 @@ __device__ __forceinline__ void operand_loads(const uint32_t *v, int mode, int j
         x[0] = v[2 * j + 1];
         x[1] = v[2 * j + 2];
     } else if (mode == GEMM_Q0 && j == 0) {
-        x[0] = v[0];
+        x[0] = v[4 * (n - 1)];
     } else {
-        const uint32_t *q = v + 1 + 4 * (mode == GEMM_Q0 ? j - 1 : j);
-        x[0] = q[0];
-        x[1] = q[1];
-        x[2] = q[2];
-        x[3] = q[3];
+        const uint4 q = *reinterpret_cast<const uint4 *>(v + 4 * (mode == GEMM_Q0 ? j - 1 : j));
+        x[0] = q.x;
+        x[1] = q.y;
+        x[2] = q.z;
+        x[3] = q.w;
     }
 }
 
@@ -65,10 +67,10 @@ __device__ __forceinline__ uint32_t operand_combine(const uint32_t (&x)[4], int 
     return t == 1 ? mp_sub(d, e, M.p) : mp_add(d, e, M.p);
 }
 
-__device__ __forceinline__ uint32_t contraction_operand(const uint32_t *v, int mode, int j, uint32_t iota,
+__device__ __forceinline__ uint32_t contraction_operand(const uint32_t *v, int mode, int j, int n, uint32_t iota,
                                                         const ModP &M) {
     uint32_t x[4];
-    operand_loads(v, mode, j, x);
+    operand_loads(v, mode, j, n, x);
     return operand_combine(x, mode, iota, M);
 }
 

@@ -132,34 +132,39 @@ enum : int32_t { PLAN_ZERO = 1 };
 // R_t of R(x) = sum_t x^t R_t(x^4) by a 4-point transform.
 enum : int32_t { PTS_GRID = 0, PTS_SYM = 1, PTS_ROOTS = 2, PTS_QUAD = 3 };
 
-// Quartic set: value index 0 is x = 0, index 1 + 4 (a - 1) + k is x = i^k a
-// (k = 0: a, 1: i a, 2: -a, 3: -i a).  The evaluation kernels take the set by
-// quadruples: quadruple Q = i (h + 1) + a of a pair holds the points i^k a of prime
-// i (a = 0: the point 0 alone), the pair's quadruples over all its primes are laid
-// out flat, eight to a warp (quad_warps warps per pair; a warp may span two
-// primes), and the four points of one quadruple stay in one warp.
+// Quartic set: value index 4 (a - 1) + k is x = i^k a (k = 0: a, 1: i a, 2: -a,
+// 3: -i a; a = 1..h), index 4 h is x = 0, and 4 h + 1 .. 4 h + 3 are pads (they
+// receive copies of the value at 0), so that a point quadruple is 16-byte aligned
+// (the planner aligns a quartic pair's values to 4 words) and the interpolation
+// loads it at once.  The evaluation kernels take the set by quadruples: quadruple
+// Q = i (h + 1) + a of a pair holds the points i^k a of prime i (a = 0: the point 0
+// and the pads), the pair's quadruples over all its primes are laid out flat, eight
+// to a warp (quad_warps warps per pair; a warp may span two primes), and the four
+// points of one quadruple stay in one warp.
 GBR_HD int quad_h(int P) { return (P - 1 + 3) / 4; }          // a = 1..h covers P - 1 points
-GBR_HD int quad_pe(int P) { return 4 * quad_h(P) + 1; }
+GBR_HD int quad_pe(int P) { return 4 * quad_h(P) + 4; }
 GBR_HD int quad_pairs(int P) { return 2 * quad_h(P) + 1; }    // +-x lane pairs
 GBR_HD int quad_warps(int P, int k) { return (int)(((int64_t)k * (quad_h(P) + 1) + 7) / 8); }
 // Lane `lane` of warp w of a pair's quartic work: its quadruple's prime i (clamped
 // to k - 1 past the last one), base a, and whether the quadruple exists.
 struct QuadLane {
-    int i, a;
+    int i, a, h;
     bool live;
 };
 GBR_HD QuadLane quad_lane(int P, int k, int64_t w, int qi) {
-    const int hq = quad_h(P) + 1;
+    const int h = quad_h(P), hq = h + 1;
     const int64_t Q = w * 8 + qi;
     QuadLane r;
+    r.h = h;
     r.live = Q < (int64_t)k * hq;
     r.i = r.live ? (int)(Q / hq) : k - 1;
     r.a = r.live ? (int)(Q - (int64_t)r.i * hq) : 0;
     return r;
 }
-// value index of the point i^kk a of a quadruple (-1: none)
+// value index of the point i^kk a of a quadruple (a = 0: the point 0 and the pads;
+// -1: none)
 GBR_HD int quad_index(const QuadLane &q, int kk) {
-    return !q.live ? -1 : q.a == 0 ? (kk == 0 ? 0 : -1) : 1 + 4 * (q.a - 1) + kk;
+    return !q.live ? -1 : q.a == 0 ? 4 * q.h + kk : 4 * (q.a - 1) + kk;
 }
 // coefficients of the quarter part R_t of a resultant with P coefficients (degree P - 1)
 GBR_HD int quad_rows(int P, int t) { return P - 1 >= t ? (P - 1 - t) / 4 + 1 : 0; }

@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_interp_tc(ResLaunch L, const 
 #pragma unroll
             for (int it = 0; it < TC_M / TC_WARPS; ++it) {
                 const int64_t b = vbs[warp + TC_WARPS * it];
-                if (b >= 0 && j < n) operand_loads(L.val + b, mode, j, ra[it]);
+                if (b >= 0 && j < n) operand_loads(L.val + b, mode, j, n, ra[it]);
                 else ra[it][0] = ra[it][1] = ra[it][2] = ra[it][3] = 0u;
             }
         }

@@ -800,7 +800,7 @@ __global__ void __launch_bounds__(256, 3) k_interp_gemm(ResLaunch L, const char 
             const int c = c0 + r, j = j0 + kk;
             ra[u] = (c < rows && j < n) ? A[(int64_t)c * n + j] : 0u;
             const int64_t b = colbase[r];
-            rb[u] = b >= 0 && j < n ? contraction_operand(L.val + b, mode, j, iota, M) : 0u;
+            rb[u] = b >= 0 && j < n ? contraction_operand(L.val + b, mode, j, n, iota, M) : 0u;
         }
     };
     load_chunk(0);

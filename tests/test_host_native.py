@@ -539,7 +539,7 @@ def test_routing_helpers(tmp_path):
             # coefficients 4 r + t < P
             P, h, pe, pairs, r0, r1, r2, r3 = v
             assert 4 * h + 1 >= P > 4 * (h - 1) + 1 or (P == 1 and h == 0), line
-            assert pe == 4 * h + 1 and pairs == 2 * h + 1, line
+            assert pe == 4 * h + 4 and pairs == 2 * h + 1, line   # three pads after the point 0
             assert [r0, r1, r2, r3] == [len(range(t, P, 4)) for t in range(4)], line
             assert r0 <= h + 1 and max(r1, r2, r3) <= h, line
             continue
