@@ -26,6 +26,15 @@ prod over the m g-rows of sqrt(sum_j lambda^(2j) G(g_j)), cols(lambda) the
 product over the m + n columns of sqrt(sum of lambda^(2 deg) G(entry)).  The
 bound is the minimum over the thirteen values log2 lambda in LOG2_LAMBDA; a
 column without entries makes the determinant 0 (bound -inf).
+
+Summed forms (small shapes).  For a row or a column with entries h_e scaled by
+w_e = lambda^(2 deg e), the squared norm at x = e^{it} is sum_e w_e |h_e(x)|^2 =
+C_0 + 2 sum_{k>=1} C_k cos kt with C_k = sum_e w_e A_k(h_e), hence at most
+C_0 + 2 sum_k |C_k|: the absolute values taken after the sum over the entries, which
+is never more than sum_e w_e G(h_e).  The library evaluates these forms for small
+shapes (y-degrees at most SUMMED_MAX_Y, entries of x-degree at most SUMMED_MAX_X,
+coefficients below 2^SUMMED_COEF_BITS in magnitude) at lambda = 1 and 2^(1/8), and
+the bound is the least of all forms.
 """
 
 from __future__ import annotations
@@ -42,6 +51,68 @@ _T = 40             # binary digits of log2 computed
 _SQRT2_BITS = 320
 _S2_LO = Fraction(isqrt(2 << (2 * _SQRT2_BITS)), 1 << _SQRT2_BITS)   # <= sqrt 2
 _S2_HI = _S2_LO + Fraction(1, 1 << _SQRT2_BITS)                       # > sqrt 2
+
+
+SUMMED_MAX_Y = 24
+SUMMED_MAX_X = 24
+SUMMED_COEF_BITS = 28
+SUMMED_Q8 = (0, 1)       # 8 log2 lambda of the summed forms: lambda = 1 and 2^(1/8)
+_Q4 = 320
+_R4_LO = Fraction(isqrt(isqrt(2 << (4 * _Q4))), 1 << _Q4)   # <= 2^(1/4)
+_R4_HI = _R4_LO + Fraction(1, 1 << _Q4)                       # > 2^(1/4)
+
+
+def autocorr(row) -> list[int]:
+    """A_k = sum_a h_a h_{a+k} for k = 0 .. len(row) - 1."""
+    h = [int(c) for c in row]
+    L = len(h)
+    return [sum(h[a] * h[a + k] for a in range(L - k)) for k in range(L)]
+
+
+def summed_eligible(F: list, G: list) -> bool:
+    """Whether the summed forms apply: y-degrees at most SUMMED_MAX_Y, every entry of
+    x-degree at most SUMMED_MAX_X, every coefficient below 2^SUMMED_COEF_BITS."""
+    if len(F) - 1 > SUMMED_MAX_Y or len(G) - 1 > SUMMED_MAX_Y:
+        return False
+    for row in list(F) + list(G):
+        nz = [i for i, c in enumerate(row) if c]
+        if nz and nz[-1] > SUMMED_MAX_X:
+            return False
+        if any(abs(int(c)) >= 1 << SUMMED_COEF_BITS for c in row):
+            return False
+    return True
+
+
+def _abs_enclosure(I: list) -> tuple[Fraction, Fraction]:
+    """[lo, hi] containing |I_0 + I_1 2^(1/4) + I_2 2^(1/2) + I_3 2^(3/4)| for integers I_r."""
+    pw = ((Fraction(1), Fraction(1)), (_R4_LO, _R4_HI), (_S2_LO, _S2_HI), (_R4_LO * _S2_LO, _R4_HI * _S2_HI))
+    lo = hi = Fraction(0)
+    for (a, b), v in zip(pw, I):
+        if v >= 0:
+            lo, hi = lo + v * a, hi + v * b
+        else:
+            lo, hi = lo + v * b, hi + v * a
+    if lo >= 0:
+        return lo, hi
+    if hi <= 0:
+        return -hi, -lo
+    return Fraction(0), max(-lo, hi)
+
+
+def summed_log2(entries: list, q8: int) -> tuple[Fraction, Fraction]:
+    """Enclosure of log2(C_0 + 2 sum_k |C_k|) for entries [(A, deg)] (A the entry's
+    autocorrelation) weighted by lambda^(2 deg) = 2^(deg q8 / 4)."""
+    K = max(len(A) for A, _ in entries)
+    I = [[0, 0, 0, 0] for _ in range(K)]
+    for A, d in entries:
+        t = d * q8
+        for k, a in enumerate(A):
+            I[k][t % 4] += a << (t // 4)
+    slo, shi = _abs_enclosure(I[0])
+    for k in range(1, K):
+        lo, hi = _abs_enclosure(I[k])
+        slo, shi = slo + 2 * lo, shi + 2 * hi
+    return _log2_digits(slo.numerator, slo.denominator, False), _log2_digits(shi.numerator, shi.denominator, True)
 
 
 def autocorr_g(row) -> int:
@@ -101,11 +172,11 @@ def _scaled(gval: int, deg: int, q: int) -> tuple[Fraction, Fraction]:
     return Fraction(0), Fraction(gval) * Fraction(2) ** ((t - 1) // 2)
 
 
-def hadamard_log2(F: list, G: list) -> tuple[Fraction, Fraction] | None:
+def hadamard_log2(F: list, G: list, summed: bool = True) -> tuple[Fraction, Fraction] | None:
     """Enclosure [lo, hi] of log2 of the bound for the y-coefficient lists F (f_0..f_m)
     and G (g_0..g_n), each entry a list of x-coefficients, with m, n the y-degrees
     (F[m], G[n] non-zero); None when a Sylvester column is empty (R = 0); (0, 0) when
-    m = n = 0 (R = 1)."""
+    m = n = 0 (R = 1).  summed=False leaves out the summed forms (for comparison)."""
     m, n = len(F) - 1, len(G) - 1
     if m <= 0 and n <= 0:
         return Fraction(0), Fraction(0)
@@ -148,6 +219,26 @@ def hadamard_log2(F: list, G: list) -> tuple[Fraction, Fraction] | None:
         hi_q = min(row[1], chi) - lam
         best_lo = lo_q if best_lo is None else min(best_lo, lo_q)
         best_hi = hi_q if best_hi is None else min(best_hi, hi_q)
+    if summed and summed_eligible(F, G):
+        af = [autocorr(r) for r in F]
+        ag = [autocorr(r) for r in G]
+        for q8 in SUMMED_Q8:
+            lo = hi = Fraction(0)
+            for A, count in ((af, n), (ag, m)):
+                if count:
+                    l, h = summed_log2([(A[i], i) for i in range(len(A))], q8)
+                    lo += Fraction(count, 2) * l
+                    hi += Fraction(count, 2) * h
+            clo = chi = Fraction(0)
+            for c in range(m + n):
+                ents = [(af[m - (c - r)], m - (c - r)) for r in range(max(0, c - m), min(n - 1, c) + 1)]
+                ents += [(ag[n - (c - r)], n - (c - r)) for r in range(max(0, c - n), min(m - 1, c) + 1)]
+                l, h = summed_log2(ents, q8)
+                clo += l / 2
+                chi += h / 2
+            lam = Fraction(m * n * q8, 8)
+            best_lo = min(best_lo, min(lo, clo) - lam)
+            best_hi = min(best_hi, min(hi, chi) - lam)
     return best_lo, best_hi
 
 

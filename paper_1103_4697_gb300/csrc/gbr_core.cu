@@ -6,6 +6,7 @@
 // points P = D + 1, the number of primes k with prod p > 2B + 1, buffer
 // offsets and degree-bucketed work lists.  Everything after that runs in the
 // stage kernels of gbr_res.cu.
+#include <array>
 #include <algorithm>
 #include <atomic>
 #include <condition_variable>
@@ -1835,14 +1836,14 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     };
     // ---- the device stages; replayed from a captured CUDA graph when the plan repeats
     phase.next("gbr: device stages (A1-A5)");
-    int64_t kernels = 1;
+    int64_t kernels = 2;   // the two bounds kernels
     auto record = [&](int idx, bool capturing, cudaStream_t q) {
         if (!c->stats_on) return;
         if (capturing) cudaEventRecordWithFlags(c->ev[idx], q, cudaEventRecordExternal);
         else cudaEventRecord(c->ev[idx], q);
     };
     auto enqueue = [&](bool capturing, cudaStream_t q) -> cudaError_t {
-        kernels = 1;
+        kernels = 2;
         cudaError_t x = cudaMemsetAsync(r->d_deg, 0xff, sizeof(int32_t) * n, q);
         if (x == cudaSuccess) x = cudaMemsetAsync(c->d_err, 0, 16, q);
         record(1, capturing, q);
@@ -2015,7 +2016,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
                         r->fvinv.push_back({kv.first, {(const void *)kv.second.d, (const void *)kv.second.tc}});
             }
             r->fast_st = st;
-            r->fast_st.kernels = kernels + 2;
+            r->fast_st.kernels = kernels + 1;   // the stages, the two bounds kernels and the plan check
             r->fast_st.graph_replayed = 2;
             r->fast_st.h2d_bytes = 0;
             r->fast_st.d2h_bytes = 20;
@@ -2484,6 +2485,87 @@ void host_rows(const gbr_bipoly *p, int var, std::vector<int> &deg, std::vector<
 }
 }  // namespace
 
+// The summed forms of the bound for small shapes, as k_bounds_summed evaluates them on
+// the device (y-degrees at most 24, entries of x-degree at most 24, one-word
+// coefficients below 2^28 in magnitude; lambda = 1 and 2^(1/8)): per Sylvester row or
+// column C_k = sum_e lambda^(2 deg e) A_k(h_e) in exact 128-bit class sums (the weight
+// 2^(t/4) as 2^(t div 4) times one of 2^(r/4), r = t mod 4), each |C_k| in double with an
+// error term above the conversions' and the four-term sum's roundings, every sum raised
+// by a relative margin.  Returns +inf when the shapes do not qualify.
+static double summed_bound_host(const gbr_bipoly *f, const gbr_bipoly *g, int var, int disc, int m, int n, int dxf,
+                                int dxg) {
+    constexpr int kMaxY = 24, kMaxX = 24, K = kMaxX + 1;
+    constexpr long long kLim = 1ll << 28;
+    if (m < 0 || n < 0 || m > kMaxY || n > kMaxY || (m == 0 && n == 0) || dxf > kMaxX || dxg > kMaxX) return INFINITY;
+    const PolyDesc pf = view_of(f, var, 0);
+    PolyDesc pg = pf;
+    if (!disc) pg = view_of(g, var, 0);
+    if (pf.words != 1 || pg.words != 1) return INFINITY;
+    const uint64_t *wf = (const uint64_t *)f->coef, *wg = disc ? wf : (const uint64_t *)g->coef;
+    auto at = [](const PolyDesc &d, const uint64_t *w, int r, int c) -> long long {
+        return (r <= d.rows && c <= d.cols) ? (long long)w[(int64_t)r * d.rstride + (int64_t)c * d.cstride] : 0ll;
+    };
+    // entries f_0..f_m, then g_0..g_n (for disc g_j = (j + 1) f_{j+1})
+    std::vector<std::array<long long, K>> A(m + n + 2);
+    for (int e = 0; e <= m + n + 1; ++e) {
+        const bool gside = e > m;
+        const int i = gside ? e - m - 1 : e;
+        long long c[K];
+        for (int x = 0; x < K; ++x) {
+            c[x] = !gside ? at(pf, wf, i, x) : !disc ? at(pg, wg, i, x) : (long long)(i + 1) * at(pf, wf, i + 1, x);
+            if (c[x] >= kLim || c[x] <= -kLim) return INFINITY;
+        }
+        for (int k = 0; k < K; ++k) {
+            long long a = 0;
+            for (int t = 0; t + k < K; ++t) a += c[t] * c[t + k];
+            A[e][k] = a;
+        }
+    }
+    const double s4[4] = {1.0, 1.189207115002721, 1.4142135623730951, 1.681792830507429};
+    auto form = [&](const std::vector<std::pair<int, int>> &ents, int q8) -> double {
+        double s = 0.0;
+        for (int k = 0; k < K; ++k) {
+            __int128 I[4] = {0, 0, 0, 0};
+            for (const auto &ed : ents) {
+                const int t = ed.second * q8;
+                I[t & 3] += (__int128)A[ed.first][k] << (t >> 2);
+            }
+            double d[4], mag = 0.0, c = 0.0;
+            for (int r = 0; r < 4; ++r) {
+                d[r] = (double)I[r];
+                c += s4[r] * d[r];
+                mag += (r ? 2.0 : 1.0) * std::fabs(d[r]);
+            }
+            s += (k ? 2.0 : 1.0) * (std::fabs(c) + mag * 0x1p-49);
+        }
+        return std::log2(s * (1.0 + 0x1p-40)) + 0x1p-40;
+    };
+    double best = INFINITY;
+    std::vector<std::pair<int, int>> ents;
+    for (int q8 = 0; q8 <= 1; ++q8) {
+        double row = 0.0, col = 0.0;
+        if (n > 0) {
+            ents.clear();
+            for (int i = 0; i <= m; ++i) ents.push_back({i, i});
+            row += 0.5 * n * form(ents, q8);
+        }
+        if (m > 0) {
+            ents.clear();
+            for (int j = 0; j <= n; ++j) ents.push_back({m + 1 + j, j});
+            row += 0.5 * m * form(ents, q8);
+        }
+        for (int c = 0; c < m + n; ++c) {
+            ents.clear();
+            for (int r = std::max(0, c - m); r <= std::min(n - 1, c); ++r) ents.push_back({m - (c - r), m - (c - r)});
+            for (int r = std::max(0, c - n); r <= std::min(m - 1, c); ++r) ents.push_back({m + 1 + n - (c - r), n - (c - r)});
+            col += 0.5 * form(ents, q8);
+        }
+        const double v = std::min(row, col) * (1.0 + 0x1p-40) - (double)m * n * q8 / 8.0;
+        best = std::min(best, v);
+    }
+    return best;
+}
+
 extern "C" int gbr_resultant_info(const gbr_bipoly *f, const gbr_bipoly *g, int var, int disc, gbr_res_info *out) {
     if (!out || (var != 0 && var != 1) || check_bipoly(f) || (!disc && check_bipoly(g))) return GBR_EINVAL;
     std::vector<int> df, dg;
@@ -2523,6 +2605,7 @@ extern "C" int gbr_resultant_info(const gbr_bipoly *f, const gbr_bipoly *g, int 
     if (b.m > GBR_MAX_YDEG || b.n > GBR_MAX_YDEG) return GBR_ELIMIT;
     std::vector<double> ef(b.m + 2), eg(b.n + 2);
     b.log2B = best_scaled_bound(nf.data(), b.m, ng.data(), b.n, ef.data(), eg.data());
+    b.log2B = std::min(b.log2B, summed_bound_host(f, g, var, disc, b.m, b.n, b.dxf, b.dxg));
     out->deg_bound = degree_bound(b);
     out->log2_bound = b.log2B;
     out->primes = primes_for_bits(b.log2B * (1.0 + 1e-9) + 2.0);

@@ -416,11 +416,187 @@ __global__ void __launch_bounds__(kBoundsWarps * 32, 7) k_bounds(ResLaunch L) {
     if (lane == 0) L.bounds[warp] = B;
 }
 
+// Summed forms of the bound for small shapes (y-degrees at most kSumMaxY, entries of
+// x-degree at most kSumMaxX, coefficients below 2^28 in magnitude; one-word inputs).
+// For a row or a column of the Sylvester matrix with entries h_e scaled by
+// w_e = lambda^(2 deg e), the squared norm at x = e^{it} is C_0 + 2 sum_k C_k cos kt with
+// C_k = sum_e w_e A_k(h_e) (A_k the autocorrelation of h_e's x-coefficients), at most
+// C_0 + 2 sum_k |C_k|: the absolute values taken after the sum over the entries, never
+// more than the per-entry form k_bounds uses.  One warp per pair, after k_bounds: the
+// autocorrelations exactly in 64-bit integers (|A_k| < 25 2^56), then one lane per
+// column (and per row form), each C_k in single precision with an error term (|C_k|
+// bounded by |computed C_k| + 2^-16 times the sum of the terms' magnitudes: the
+// conversion of A_k, the rounded weight and the at most 50 roundings of the sum stay
+// below 2^-18.3 of it), every further sum rounded upward, log2f padded by 2^-13 (its
+// error is 1 ulp), the products over rows and columns summed in 2^-17 fixed point; at
+// lambda = 1 and 2^(1/8) (weights 2^(deg / 4), from a table rounded to nearest).  The
+// pair's log2 B is lowered when a summed form is smaller.
+constexpr int kSumMaxY = 24, kSumMaxX = 24, kSumK = kSumMaxX + 1, kSumWarps = 1;
+constexpr long long kSumCoefLimit = 1ll << 28;
+__constant__ float c_sum_w[kSumMaxY + 1] = {
+    1.0f,         1.18920712f,  1.41421356f,  1.68179283f,  2.0f,         2.37841423f,  2.82842712f,
+    3.36358566f,  4.0f,         4.75682846f,  5.65685425f,  6.72717132f,  8.0f,         9.51365692f,
+    11.3137085f,  13.45434264f, 16.0f,        19.02731384f, 22.627417f,   26.90868529f, 32.0f,
+    38.05462768f, 45.254834f,   53.81737058f, 64.0f};   // 2^(d / 4)
+
+__device__ __forceinline__ long long sum_coef(const ResLaunch &L, const PolyDesc &P, int r, int c) {
+    return (r <= P.rows && c <= P.cols) ? (long long)coef_ptr(L.coef, P, r, c)[0] : 0ll;
+}
+
+__global__ void __launch_bounds__(kSumWarps * 32) k_bounds_summed(ResLaunch L) {
+    __shared__ float sA[kSumWarps][2 * (kSumMaxY + 1)][kSumK];
+    __shared__ int sc[kSumWarps][2 * (kSumMaxY + 1)][kSumK];   // eligible coefficients fit 32 bits
+    __shared__ float sw[kSumMaxY + 1];   // the weights, read with a different index per lane
+    // prefix (sP, sT) and suffix (sQ, sU) sums of w A_k and w |A_k| over each polynomial's entries
+    __shared__ float sP[kSumWarps][2][kSumMaxY + 2][kSumK], sT[kSumWarps][2][kSumMaxY + 2][kSumK];
+    __shared__ float sQ[kSumWarps][2][kSumMaxY + 2][kSumK], sU[kSumWarps][2][kSumMaxY + 2][kSumK];
+    for (int t = threadIdx.x; t <= kSumMaxY; t += blockDim.x) sw[t] = c_sum_w[t];
+    __syncthreads();
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int pair = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (pair >= L.npairs) return;
+    PairBound B = L.bounds[pair];
+    const PairDesc D = L.desc[pair];
+    const int m = B.m, n = B.n;
+    if (m < 0 || n < 0 || m > kSumMaxY || n > kSumMaxY || (m == 0 && n == 0) || B.dxf > kSumMaxX ||
+        B.dxg > kSumMaxX || D.f.words != 1 || (!D.disc && D.g.words != 1) || !(B.log2B > -INFINITY))
+        return;
+    // entries: f_0..f_m (index i), then g_0..g_n (index m + 1 + j); for disc g_j = (j+1) f_{j+1}
+    // every entry's coefficients first (lane = power of x; all loads in flight), then
+    // the autocorrelations
+    bool ok = true;
+    const int ne_all = m + n + 2;
+    if (lane < kSumK)
+        for (int e = 0; e < ne_all; ++e) {
+            const bool gside = e > m;
+            const int i = gside ? e - m - 1 : e;
+            long long c;
+            if (!gside) c = sum_coef(L, D.f, i, lane);
+            else if (!D.disc) c = sum_coef(L, D.g, i, lane);
+            else c = (long long)(i + 1) * sum_coef(L, D.f, i + 1, lane);
+            ok = ok && c < kSumCoefLimit && c > -kSumCoefLimit;
+            sc[wib][e][lane] = (int)c;   // used only when every coefficient is in range
+        }
+    if (!__all_sync(0xffffffffu, ok)) return;
+    __syncwarp();
+    if (lane < kSumK)
+        for (int e = 0; e < ne_all; ++e) {
+            long long a = 0;
+            for (int t = 0; t + lane < kSumK; ++t) a += (long long)sc[wib][e][t] * sc[wib][e][t + lane];
+            sA[wib][e][lane] = (float)a;
+        }
+    __syncwarp();
+    const int nforms = m + n + 2;   // columns 0..m+n-1, then f's row form, g's row form
+    long long best = LLONG_MAX;
+    for (int q8 = 0; q8 <= 1; ++q8) {
+        // prefix and suffix sums over each polynomial's entries, per power k (lane = k):
+        // sP[0][i][k] = sum_{i' < i} w_i' A_k(f_i'), sQ[0][i][k] = sum_{i' >= i}, sT and sU
+        // the same of |A_k|; [1] for g.  A Sylvester column's entries of one polynomial
+        // start at its first entry or end at its last (both unless m != n), so C_k is one
+        // prefix or one suffix value, within 2^-19.2 of the magnitude sum of its own
+        // range (27 roundings at most); an interior range takes a difference of prefixes
+        // and the magnitude sums of both
+        __syncwarp();
+        if (lane < kSumK) {
+            for (int side = 0; side < 2; ++side) {
+                const int top = side ? n : m, e0 = side ? m + 1 : 0;
+                float p = 0.0f, t = 0.0f;
+                sP[wib][side][0][lane] = sT[wib][side][0][lane] = 0.0f;
+                for (int i = 0; i <= top; ++i) {
+                    const float w = q8 ? sw[i] : 1.0f, a = sA[wib][e0 + i][lane];
+                    p = fmaf(w, a, p);
+                    t = fmaf(w, fabsf(a), t);
+                    sP[wib][side][i + 1][lane] = p;
+                    sT[wib][side][i + 1][lane] = t;
+                }
+                p = t = 0.0f;
+                sQ[wib][side][top + 1][lane] = sU[wib][side][top + 1][lane] = 0.0f;
+                for (int i = top; i >= 0; --i) {
+                    const float w = q8 ? sw[i] : 1.0f, a = sA[wib][e0 + i][lane];
+                    p = fmaf(w, a, p);
+                    t = fmaf(w, fabsf(a), t);
+                    sQ[wib][side][i][lane] = p;
+                    sU[wib][side][i][lane] = t;
+                }
+            }
+        }
+        __syncwarp();
+        // C_k and the magnitude sum that bounds its error, over entries lo..hi of one side
+        auto range = [&](int side, int lo, int hi, int top, int k, float &c, float &t) {
+            if (lo == 0) {
+                c += sP[wib][side][hi + 1][k];
+                t += sT[wib][side][hi + 1][k];
+            } else if (hi == top) {
+                c += sQ[wib][side][lo][k];
+                t += sU[wib][side][lo][k];
+            } else {
+                c += sP[wib][side][hi + 1][k] - sP[wib][side][lo][k];
+                t += sT[wib][side][hi + 1][k] + sT[wib][side][lo][k];
+            }
+        };
+        long long row = 0, col = 0;   // 2^-17 fixed point
+        for (int base = 0; base < nforms; base += 32) {
+            const int fi = base + lane;
+            long long mine = 0;
+            if (fi < nforms && !(fi == m + n && n == 0) && !(fi == m + n + 1 && m == 0)) {
+                // the entries of this form: f_i for i in [ilo, ihi], g_j for j in [jlo, jhi]
+                int ilo, ihi, jlo, jhi;
+                if (fi < m + n) {
+                    // column c: f-row r holds f_{m - (c - r)}, g-row r holds g_{n - (c - r)}
+                    const int c = fi;
+                    ilo = m - c + max(0, c - m);
+                    ihi = m - c + min(n - 1, c);
+                    jlo = n - c + max(0, c - n);
+                    jhi = n - c + min(m - 1, c);
+                } else if (fi == m + n) {
+                    ilo = 0, ihi = m, jlo = 0, jhi = -1;
+                } else {
+                    ilo = 0, ihi = -1, jlo = 0, jhi = n;
+                }
+                const bool hf = ilo <= ihi, hg = jlo <= jhi;
+                float S = 0.0f;
+                for (int k = 0; k < kSumK; ++k) {
+                    // |C_k| at most |computed| (1 + 2^-22) (the one or two roundings of
+                    // joining the pieces) + 2^-17 (the magnitude sums, within 2^-19.2)
+                    float c = 0.0f, t = 0.0f;
+                    if (hf) range(0, ilo, ihi, m, k, c, t);
+                    if (hg) range(1, jlo, jhi, n, k, c, t);
+                    float up = __fadd_ru(__fmul_ru(fabsf(c), 1.0f + 0x1p-22f), __fmul_ru(t, 0x1p-17f));
+                    if (k) up = __fmul_ru(up, 2.0f);
+                    S = __fadd_ru(S, up);
+                }
+                const float l2 = __fadd_ru(log2f(S), 0x1p-13f);
+                mine = __float2ll_ru(l2 * 65536.0f);   // 0.5 log2 in 2^-17 units, upward
+                if (fi == m + n) mine *= n;             // n copies of f's row
+                else if (fi == m + n + 1) mine *= m;    // m copies of g's
+            }
+            // sums over the lanes: columns and rows apart (exact integers)
+            long long cpart = fi < m + n ? mine : 0, rpart = fi >= m + n ? mine : 0;
+            for (int o = 16; o; o >>= 1) {
+                cpart += __shfl_xor_sync(0xffffffffu, cpart, o);
+                rpart += __shfl_xor_sync(0xffffffffu, rpart, o);
+            }
+            col += cpart;
+            row += rpart;
+        }
+        // lambda^(-mn) = 2^(-mn q8 / 8), exact in 2^-17 units
+        const long long v = (row < col ? row : col) - (long long)m * n * q8 * (131072 / 8);
+        best = v < best ? v : best;
+    }
+    const double nb = (double)best * 0x1p-17 + 0x1p-10;
+    if (lane == 0 && nb < B.log2B) L.bounds[pair].log2B = nb;
+}
+
 cudaError_t launch_bounds(const ResLaunch &L, cudaStream_t s) {
     if (L.npairs <= 0) return cudaSuccess;
     int threads = kBoundsWarps * 32;
     int blocks = (L.npairs * 32 + threads - 1) / threads;
     k_bounds<<<blocks, threads, 0, s>>>(L);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    threads = kSumWarps * 32;
+    blocks = (L.npairs * 32 + threads - 1) / threads;
+    k_bounds_summed<<<blocks, threads, 0, s>>>(L);
     return cudaGetLastError();
 }
 

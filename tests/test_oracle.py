@@ -322,6 +322,50 @@ def test_bound_covers_resultants(seed):
     _check_covers(f, g)
 
 
+def test_summed_form_closed_forms():
+    """The summed forms take the absolute values after summing the entries'
+    autocorrelations.  h_0 = 1 + x and h_1 = 1 - x (A = [2, 1] and [2, -1]): at lambda = 1
+    C_0 = 4 and C_1 = 0, so C_0 + 2|C_1| = 4 where the per-entry form gives 8; with the
+    weights 1 and 2^(1/4) (lambda = 2^(1/8), degrees 0 and 1) C_0 = 2 + 2^(5/4) and
+    C_1 = 1 - 2^(1/4), so C_0 + 2|C_1| = 2^(9/4)."""
+    from fractions import Fraction
+
+    from oracle import bound as B
+
+    assert B.autocorr([1, 1]) == [2, 1] and B.autocorr([1, -1]) == [2, -1]
+    for ents, q8, want in (([([2, 1], 0), ([2, -1], 0)], 0, Fraction(2)),
+                           ([([2, 1], 0), ([2, -1], 1)], 1, Fraction(9, 4)),
+                           ([([9, 2, -1], 2), ([1], 0)], 0, Fraction(4))):   # (9 + 1) + 2 (2 + 1) = 16
+        lo, hi = B.summed_log2(ents, q8)
+        assert lo <= want <= hi and hi - lo < Fraction(1, 2 ** 30), (ents, q8, float(lo), float(hi))
+    assert B.autocorr_g([1, 1]) + B.autocorr_g([1, -1]) == 8
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_summed_forms_cover_and_tighten(seed):
+    """On random pairs inside the summed forms' shapes (rows with cancelling
+    autocorrelations among them) the bound with the summed forms still covers max |coef R|,
+    |R(1)|, |R(-1)|, and it is never above the bound of the per-entry forms alone."""
+    from oracle import bound as B
+
+    rng = random.Random(1700 + seed)
+    for _ in range(4):
+        m, n = rng.randint(1, 5), rng.randint(1, 5)
+        f = _rand_bipoly(rng, m, rng.randint(1, 6), -(1 << 12), 1 << 12)
+        g = _rand_bipoly(rng, n, rng.randint(1, 6), -(1 << 12), 1 << 12)
+        f[-1][0] = f[-1][0] or 1
+        g[-1][0] = g[-1][0] or 1
+        assert B.summed_eligible(f, g)
+        _check_covers(f, g)
+        both = B.hadamard_log2(f, g)
+        old = B.hadamard_log2(f, g, summed=False)
+        assert both[1] <= old[1]
+    # a pair where they are strictly tighter: f = (1 + x) + (1 - x) y
+    f, g = [[1, 1], [1, -1]], [[-3], [1]]
+    assert B.hadamard_log2(f, g)[1] < B.hadamard_log2(f, g, summed=False)[0]
+    _check_covers(f, g)
+
+
 def test_bound_empty_column_and_degenerate():
     """A zero input gives no bound; constants in y give 0 = log2 1 for R = 1."""
     assert _bound([[0]], [[1], [2]]) is None

@@ -97,6 +97,12 @@ MUTATIONS = [
     ("yun_quotient_not_divided", "sqf.py", "        c = zx_divexact(c, ri)\n", "        c = c[1:] or c\n"),
     # the coefficient bound (Hadamard's inequality on the scaled Sylvester matrix)
     ("bound_autocorr_factor_two", "bound.py", "g += 2 * abs(", "g += abs("),
+    # the summed forms: |C_k| after the sum over the entries, lambda^(2 deg), the factor 2
+    ("summed_abs_per_entry", "bound.py", "            I[k][t % 4] += a << (t // 4)\n",
+     "            I[k][t % 4] += abs(a) << (t // 4)\n"),
+    ("summed_lambda_exponent", "bound.py", "        t = d * q8\n", "        t = 2 * d * q8\n"),
+    ("summed_factor_two", "bound.py", "        slo, shi = slo + 2 * lo, shi + 2 * hi\n",
+     "        slo, shi = slo + lo, shi + hi\n"),
     ("bound_autocorr_no_abs", "bound.py", "g += 2 * abs(sum(h[a] * h[a + k] for a in range(L - k)))",
      "g += 2 * sum(h[a] * h[a + k] for a in range(L - k))"),
     ("bound_lambda_power_dropped", "bound.py", "lam = Fraction(m * n * q, 4)", "lam = Fraction(m * n * q, 8)"),
