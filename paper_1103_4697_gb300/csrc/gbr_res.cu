@@ -423,14 +423,15 @@ __global__ void __launch_bounds__(kBoundsWarps * 32, 7) k_bounds(ResLaunch L) {
 // C_k = sum_e w_e A_k(h_e) (A_k the autocorrelation of h_e's x-coefficients), at most
 // C_0 + 2 sum_k |C_k|: the absolute values taken after the sum over the entries, never
 // more than the per-entry form k_bounds uses.  One warp per pair, after k_bounds: the
-// autocorrelations exactly in 64-bit integers (|A_k| < 25 2^56), then one lane per
-// column (and per row form), each C_k in single precision with an error term (|C_k|
-// bounded by |computed C_k| + 2^-16 times the sum of the terms' magnitudes: the
-// conversion of A_k, the rounded weight and the at most 50 roundings of the sum stay
-// below 2^-18.3 of it), every further sum rounded upward, log2f padded by 2^-13 (its
-// error is 1 ulp), the products over rows and columns summed in 2^-17 fixed point; at
-// lambda = 1 and 2^(1/8) (weights 2^(deg / 4), from a table rounded to nearest).  The
-// pair's log2 B is lowered when a summed form is smaller.
+// autocorrelations exactly in 64-bit integers (|A_k| < 25 2^56; a lane per entry, the
+// entry's coefficients in registers), then one lane per column (and per row form), each
+// C_k in single precision with an error term (|C_k| bounded by |computed C_k| + 2^-16
+// times the sum of the terms' magnitudes: the conversion of A_k, the rounded weight and
+// the at most 50 roundings of the sum stay below 2^-18.3 of it), every further sum
+// rounded upward, log2f padded by 2^-13 (its error is 1 ulp), the products over rows and
+// columns summed in 2^-17 fixed point; at lambda = 1 and 2^(1/8) (weights 2^(deg / 4),
+// from a table rounded to nearest).  The pair's log2 B is lowered when a summed form is
+// smaller.
 constexpr int kSumMaxY = 24, kSumMaxX = 24, kSumK = kSumMaxX + 1, kSumWarps = 1;
 constexpr long long kSumCoefLimit = 1ll << 28;
 __constant__ float c_sum_w[kSumMaxY + 1] = {
@@ -443,9 +444,35 @@ __device__ __forceinline__ long long sum_coef(const ResLaunch &L, const PolyDesc
     return (r <= P.rows && c <= P.cols) ? (long long)coef_ptr(L.coef, P, r, c)[0] : 0ll;
 }
 
+// The autocorrelation A_0..A_{kSumK-1} of one entry's x-coefficients (zero past its
+// degree) into sA[e][.], exactly in 64-bit integers, then rounded to float.  false when
+// a coefficient is out of range.
+__device__ __forceinline__ bool sum_autocorr(const ResLaunch &L, const PairDesc &D, int m, int e, float *sAe) {
+    const bool gside = e > m;
+    const int i = gside ? e - m - 1 : e;
+    int c[kSumK];
+    bool ok = true;
+#pragma unroll
+    for (int x = 0; x < kSumK; ++x) {
+        long long v;
+        if (!gside) v = sum_coef(L, D.f, i, x);
+        else if (!D.disc) v = sum_coef(L, D.g, i, x);
+        else v = (long long)(i + 1) * sum_coef(L, D.f, i + 1, x);
+        ok = ok && v < kSumCoefLimit && v > -kSumCoefLimit;
+        c[x] = (int)v;
+    }
+#pragma unroll
+    for (int k = 0; k < kSumK; ++k) {
+        long long a = 0;
+#pragma unroll
+        for (int t = 0; t + k < kSumK; ++t) a += (long long)c[t] * c[t + k];
+        sAe[k] = (float)a;
+    }
+    return ok;
+}
+
 __global__ void __launch_bounds__(kSumWarps * 32) k_bounds_summed(ResLaunch L) {
     __shared__ float sA[kSumWarps][2 * (kSumMaxY + 1)][kSumK];
-    __shared__ int sc[kSumWarps][2 * (kSumMaxY + 1)][kSumK];   // eligible coefficients fit 32 bits
     __shared__ float sw[kSumMaxY + 1];   // the weights, read with a different index per lane
     // prefix (sP, sT) and suffix (sQ, sU) sums of w A_k and w |A_k| over each polynomial's entries
     __shared__ float sP[kSumWarps][2][kSumMaxY + 2][kSumK], sT[kSumWarps][2][kSumMaxY + 2][kSumK];
@@ -462,29 +489,10 @@ __global__ void __launch_bounds__(kSumWarps * 32) k_bounds_summed(ResLaunch L) {
         B.dxg > kSumMaxX || D.f.words != 1 || (!D.disc && D.g.words != 1) || !(B.log2B > -INFINITY))
         return;
     // entries: f_0..f_m (index i), then g_0..g_n (index m + 1 + j); for disc g_j = (j+1) f_{j+1}
-    // every entry's coefficients first (lane = power of x; all loads in flight), then
-    // the autocorrelations
-    bool ok = true;
     const int ne_all = m + n + 2;
-    if (lane < kSumK)
-        for (int e = 0; e < ne_all; ++e) {
-            const bool gside = e > m;
-            const int i = gside ? e - m - 1 : e;
-            long long c;
-            if (!gside) c = sum_coef(L, D.f, i, lane);
-            else if (!D.disc) c = sum_coef(L, D.g, i, lane);
-            else c = (long long)(i + 1) * sum_coef(L, D.f, i + 1, lane);
-            ok = ok && c < kSumCoefLimit && c > -kSumCoefLimit;
-            sc[wib][e][lane] = (int)c;   // used only when every coefficient is in range
-        }
+    bool ok = true;
+    for (int e = lane; e < ne_all; e += 32) ok = sum_autocorr(L, D, m, e, sA[wib][e]) && ok;
     if (!__all_sync(0xffffffffu, ok)) return;
-    __syncwarp();
-    if (lane < kSumK)
-        for (int e = 0; e < ne_all; ++e) {
-            long long a = 0;
-            for (int t = 0; t + lane < kSumK; ++t) a += (long long)sc[wib][e][t] * sc[wib][e][t + lane];
-            sA[wib][e][lane] = (float)a;
-        }
     __syncwarp();
     const int nforms = m + n + 2;   // columns 0..m+n-1, then f's row form, g's row form
     long long best = LLONG_MAX;
@@ -495,7 +503,9 @@ __global__ void __launch_bounds__(kSumWarps * 32) k_bounds_summed(ResLaunch L) {
         // start at its first entry or end at its last (both unless m != n), so C_k is one
         // prefix or one suffix value, within 2^-19.2 of the magnitude sum of its own
         // range (27 roundings at most); an interior range takes a difference of prefixes
-        // and the magnitude sums of both
+        // and the magnitude sums of both.  (A suffix taken as the difference of two
+        // prefixes would carry the rounding error of the whole sum, which can exceed a
+        // short range's own value by orders of magnitude.)
         __syncwarp();
         if (lane < kSumK) {
             for (int side = 0; side < 2; ++side) {
