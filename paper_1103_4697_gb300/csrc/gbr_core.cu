@@ -141,6 +141,34 @@ void garner_prefix_table(int K, uint32_t *out) {
     }
 }
 
+size_t crt_warp_words(int K) { return (size_t)K * (K - 1) / 2 + (size_t)K * crt_warp_limbs(K); }
+
+void crt_warp_table(int K, uint32_t *out) {
+    const ModP *M = host_mods();
+    for (int i = 1; i < K; ++i) {
+        const uint64_t pi = M[i].p;
+        uint64_t C = 1;   // prod_{l<j} p_l mod p_i
+        uint32_t *row = out + (size_t)i * (i - 1) / 2;
+        for (int j = 0; j < i; ++j) {
+            row[j] = to_mont_host((uint32_t)((pi - C) % pi), (uint32_t)pi);
+            C = C * (M[j].p % pi) % pi;
+        }
+    }
+    const int LW = crt_warp_limbs(K);
+    uint32_t *T = out + (size_t)K * (K - 1) / 2;
+    std::vector<uint32_t> P(LW + 1, 0u);   // prod_{j<i} p_j in 32-bit limbs
+    P[0] = 1;
+    for (int i = 0; i < K; ++i) {
+        std::memcpy(T + (size_t)i * LW, P.data(), (size_t)LW * 4);
+        uint64_t carry = 0;
+        for (int l = 0; l <= LW; ++l) {
+            const uint64_t t = (uint64_t)P[l] * M[i].p + carry;
+            P[l] = (uint32_t)t;
+            carry = t >> 32;
+        }
+    }
+}
+
 void inverse_table(int K, int T, uint32_t *out) {
     const ModP *M = host_mods();
     std::vector<uint64_t> inv(T > 2 ? T : 2);
@@ -246,7 +274,7 @@ void *gbr_ctx::pinned(size_t bytes, int slot) {
     return h_pin[slot];
 }
 
-int gbr_ctx::ensure_tables(int K, int T) {
+int gbr_ctx::ensure_tables(int K, int T, int KW) {
     if (K > garner_K) {
         int newK = std::max(K, std::max(64, garner_K * 2));
         if (newK > num_primes()) newK = num_primes();
@@ -260,6 +288,20 @@ int gbr_ctx::ensure_tables(int K, int T) {
         dfree(d_garner);
         d_garner = (uint32_t *)d;
         garner_K = newK;
+    }
+    if (KW > crtw_K) {
+        int newK = std::max(KW, std::max(2 * kCrtFastK, crtw_K * 2));
+        newK = std::min(newK, std::min(kCrtWarpK, num_primes()));
+        const size_t words = crt_warp_words(newK);
+        std::vector<uint32_t> h(words);
+        crt_warp_table(newK, h.data());
+        void *d = dalloc(words * 4);
+        if (!d) return fail(GBR_ENOMEM, "device budget too small for the Chinese remaindering table");
+        cudaError_t e = cudaMemcpy(d, h.data(), words * 4, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(GBR_EDEVICE, "upload Chinese remaindering table", e);
+        dfree(d_crtw);
+        d_crtw = (uint32_t *)d;
+        crtw_K = newK;
     }
     if (K > invk_K || T > invk_T) {
         int nK = std::max(K, invk_K), nT = std::max(T, invk_T);
@@ -829,7 +871,7 @@ void gbr_destroy_worker(gbr_ctx *w) {
         w->dfree(kv.second.d);
         w->dfree(kv.second.tc);
     }
-    for (void *p : {(void *)w->d_err, (void *)w->d_garner, (void *)w->d_invk}) w->dfree(p);   // d_mods: the parent's
+    for (void *p : {(void *)w->d_err, (void *)w->d_garner, (void *)w->d_invk, (void *)w->d_crtw}) w->dfree(p);   // d_mods: the parent's
     for (int i = 0; i < 8; ++i)
         if (w->ev[i]) cudaEventDestroy(w->ev[i]);
     for (int i = 0; i < 4; ++i)
@@ -1244,7 +1286,7 @@ static std::vector<uintptr_t> step_signature(const gbr_ctx *c) {
     return {(uintptr_t)c->drop_unlucky, (uintptr_t)c->pts_mode, (uintptr_t)c->extra_primes, (uintptr_t)c->gemm_on,
             (uintptr_t)c->tc_on,        (uintptr_t)c->reg_on,   (uintptr_t)c->stats_on,     (uintptr_t)c->d_garner,
             (uintptr_t)c->d_invk,       (uintptr_t)c->d_mods,   (uintptr_t)c->d_err,        (uintptr_t)c->garner_K,
-            (uintptr_t)c->invk_T};
+            (uintptr_t)c->invk_T,       (uintptr_t)c->d_crtw,   (uintptr_t)c->crtw_K};
 }
 
 // The step graph may run when the context still matches and every cached
@@ -1474,8 +1516,8 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     int Kmax = 1, Pmax = 1, Lmax = 1, Kdig = 1;   // Kdig: most primes of one pair
     int Puse = 1;   // most points one interpolation uses (Pmax also counts the spare points)
     int Nntt = 1;   // largest transform of the root-of-unity pairs
-    HostList red, interp, crt, crtf, ntt, binv;
-    int Kdig_f = 1, Lmax_f = 1;
+    HostList red, interp, crt, crtf, crtw, ntt, binv;
+    int Kdig_f = 1, Lmax_f = 1, Kdig_w = 0, Lmax_w = 1;
     // evaluation buckets by y-degree (key / 4), register-form buckets by N, and
     // contraction groups by (points, symmetric): flat tables in ascending key order
     std::vector<HostList> evb_t((GBR_MAX_YDEG + 5) / 4 + 1);
@@ -1545,6 +1587,10 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
             crtf.add(q, p.P);
             Kdig_f = std::max(Kdig_f, k);
             Lmax_f = std::max(Lmax_f, p.L);
+        } else if (p.pmap_off < 0 && k <= std::min(kCrtWarpK, num_primes())) {
+            crtw.add(q, p.P);
+            Kdig_w = std::max(Kdig_w, k);
+            Lmax_w = std::max(Lmax_w, p.L);
         } else {
             crt.add(q, p.P);
         }
@@ -1571,7 +1617,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
         for (size_t t = i; t < j; ++t) v.push_back(pg_items[t].second);
         i = j;
     }
-    int rc = c->ensure_tables(Kmax, Pmax);
+    int rc = c->ensure_tables(Kmax, Pmax, Kdig_w);
     if (rc) return rc;
     // interpolation: groups of pairs sharing P use the inverse-Vandermonde
     // contraction; the rest (and groups whose matrices do not fit the cache)
@@ -1657,6 +1703,8 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     put_list(blk, crt, o_crt_p, o_crt_s);
     size_t o_crtf_p, o_crtf_s;
     put_list(blk, crtf, o_crtf_p, o_crtf_s);
+    size_t o_crtw_p, o_crtw_s;
+    put_list(blk, crtw, o_crtw_p, o_crtw_s);
     std::vector<std::pair<size_t, size_t>> o_ev;
     for (auto &kv : evb) {
         size_t a, b2;
@@ -1767,6 +1815,8 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     L.plan = (const PairPlan *)r->d_planblk;
     L.garner = c->d_garner;
     L.garner_K = c->garner_K;
+    L.crtw = c->d_crtw;
+    L.crtw_K = c->crtw_K;
     L.invk = c->d_invk;
     L.invk_T = c->invk_T;
     L.res = r->d_res;
@@ -1903,6 +1953,10 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
             x = launch_crt_fast(L, mk(o_crtf_p, o_crtf_s, crtf), Kdig_f, Lmax_f, q);
             kernels++;
         }
+        if (x == cudaSuccess && crtw.total > 0) {
+            x = launch_crt_warp(L, mk(o_crtw_p, o_crtw_s, crtw), Kdig_w, Lmax_w, q);
+            kernels++;
+        }
         if (x == cudaSuccess && crt.total > 0) {
             x = launch_crt(L, mk(o_crt_p, o_crt_s, crt), Kdig, Lmax, q);
             kernels++;
@@ -1919,7 +1973,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
                                       (uintptr_t)r->d_deg,     (uintptr_t)r->d_flags, (uintptr_t)r->d_gtab,
                                       (uintptr_t)r->d_redo,
                                       (uintptr_t)c->d_garner,  (uintptr_t)c->d_invk, (uintptr_t)c->d_err,
-                                      (uintptr_t)c->d_mods,    (uintptr_t)c->stats_on};
+                                      (uintptr_t)c->d_mods,    (uintptr_t)c->stats_on, (uintptr_t)c->d_crtw};
         for (const Gemm &gm : gemms) {
             key.push_back((uintptr_t)gm.vinv);
             key.push_back((uintptr_t)gm.vtc);

@@ -77,6 +77,8 @@ struct gbr_ctx {
     int32_t *d_err = nullptr;
     uint32_t *d_garner = nullptr;
     int garner_K = 0;
+    uint32_t *d_crtw = nullptr;          // warp Chinese remaindering tables (crt_warp_table)
+    int crtw_K = 0;
     uint32_t *d_invk = nullptr;
     int invk_K = 0, invk_T = 0;
     void *h_pin[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -116,7 +118,7 @@ struct gbr_ctx {
     void dfree(void *p);
     gbr::Arena &mem() { return parent ? parent->arena : arena; }
     void *pinned(size_t bytes, int slot);   // grow-only pinned staging buffer per slot
-    int ensure_tables(int K, int T);
+    int ensure_tables(int K, int T, int KW = 0);   // KW: primes of the warp Chinese remaindering
 };
 
 struct gbr_resident {

@@ -63,6 +63,15 @@ int primes_for_bits(double bits);     // smallest k with sum_{i<k} log2 p_i > bi
 // cinv[i] = (p_0 ... p_{i-1})^-1 mod p_i and pm[i*(i-1)/2 + j] = p_j mod p_i (j < i),
 // both in Montgomery form modulo p_i.  Layout: cinv[0..K) then pm.
 void garner_prefix_table(int K, uint32_t *out);   // out has K + K*(K-1)/2 words
+// Tables of the warp-per-coefficient Chinese remaindering for pairs on the first K
+// (kCrtFastK < K <= kCrtWarpK) table primes: Garner rows, row i (at i(i-1)/2) holding
+// (-prod_{l<j} p_l mod p_i) R mod p_i for j < i, then the limb table, row i (i < K,
+// crt_warp_limbs(K) words each) holding the 32-bit limbs of prod_{j<i} p_j.
+constexpr int kCrtWarpK = 512;
+// every prime is below 2^31, so prod_{j<i} p_j with i <= K fits (31 K + 31) / 32 limbs
+GBR_HD int crt_warp_limbs(int K) { return (31 * K + 31) / 32; }
+size_t crt_warp_words(int K);
+void crt_warp_table(int K, uint32_t *out);
 
 // Inverses 1/t mod p_i for t = 1..T-1 in Montgomery form, t = 0 slot unused:
 // out[i*T + t].
@@ -306,6 +315,8 @@ struct ResLaunch {
     const uint32_t *crtfast;     // CRT tables of the first kCrtFastK primes (Garner rows, T, I0)
     const uint32_t *garner;      // prefix Garner table (K + K(K-1)/2 words)
     int32_t garner_K;
+    const uint32_t *crtw;        // warp Chinese remaindering tables of the first crtw_K primes
+    int32_t crtw_K;
     const uint32_t *invk;        // [prime][invk_T] inverses of 1..T-1
     int32_t invk_T;
     uint32_t *res;               // residues
@@ -389,6 +400,7 @@ cudaError_t configure_interp_ntt_kernel();
 cudaError_t launch_crt(const ResLaunch &L, const WorkList &w, int maxK, int maxL, cudaStream_t s);
 // pairs on the prime-table prefix with k <= kCrtFastK
 cudaError_t launch_crt_fast(const ResLaunch &L, const WorkList &w, int maxK, int maxL, cudaStream_t s);
+cudaError_t launch_crt_warp(const ResLaunch &L, const WorkList &w, int maxK, int maxL, cudaStream_t s);
 cudaError_t launch_vinv(const ModP *mods, int n, int K, int mode, uint32_t *out, cudaStream_t s);
 cudaError_t launch_unlucky_primes(const ResLaunch &L, int kc, uint8_t *out, cudaStream_t s);
 cudaError_t launch_pair_garner(const ResLaunch &L, const int32_t *pairs, int n, int kmax, uint32_t *gtab,

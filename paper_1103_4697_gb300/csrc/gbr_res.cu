@@ -1230,6 +1230,108 @@ __global__ void k_crt_fast(ResLaunch L, WorkList w, int KD, int LD) {
     }
 }
 
+// Chinese remaindering for pairs on the first crtw_K table primes with more than
+// kCrtFastK of them, one warp per output coefficient (a one-thread form leaves a few
+// hundred coefficients with k^2 serial steps each).  Garner digit i is
+//   v_i = (r_i - sum_{j<i} v_j prod_{l<j} p_l) (prod_{l<i} p_l)^-1 mod p_i,
+// its dot product split over the lanes (each lane an exact 96-bit sum of its terms with
+// the table row (-prod_{l<j} p_l) R mod p_i, lane 0 adding r_i 2^32, reduced to a residue
+// mod p_i; the lanes' residues summed by shuffles); the digits stay in shared memory.
+// The symmetric lift compares the digits from the top with (p_i - 1) / 2 (a ballot per
+// 32 digits); the magnitude X (or prod p_i - X, i.e. the digits p_i - 1 - v_i plus one)
+// is sum_i d_i prod_{j<i} p_j: each lane forms the exact 96-bit column sums of its limbs
+// from the limb table, and one lane adds them up with their carries.
+constexpr int kCrtWarpBlock = 128;
+__global__ void __launch_bounds__(kCrtWarpBlock) k_crt_warp(ResLaunch L, WorkList w, int KD, int LD) {
+    if (stage_skipped(L)) return;
+    extern __shared__ uint32_t smw[];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    uint32_t *dig = smw + (size_t)wib * (KD + 3 * LD);   // KD digits, then LD 96-bit column sums
+    uint32_t *col = dig + KD;
+    const int KW = L.crtw_K, LW = crt_warp_limbs(KW);
+    const uint32_t *T = L.crtw + (size_t)KW * (KW - 1) / 2;
+    for (int64_t item = (int64_t)blockIdx.x * nw + wib; item < w.total; item += (int64_t)gridDim.x * nw) {
+        const int bi = wl_find(w.start, w.n, item);
+        const int q = w.pairs[bi];
+        const int c = (int)(item - w.start[bi]);
+        const PairPlan &P = L.plan[q];
+        const int k = P.k, Pn = P.P, Lp = P.L;
+        const uint32_t *src = L.cf + P.cf_off + c;
+        __syncwarp();
+        for (int i = lane; i < k; i += 32) dig[i] = src[(int64_t)i * Pn];   // residues, then digits in place
+        __syncwarp();
+        for (int i = 1; i < k; ++i) {
+            const ModP M = L.mods[i];
+            const uint32_t *Gi = L.crtw + (size_t)i * (i - 1) / 2;
+            uint32_t a0 = 0u, a1 = lane == 0 ? dig[i] : 0u, a2 = 0u;
+            for (int j = lane; j < i; j += 32) mac96(a0, a1, a2, dig[j], Gi[j]);
+            // this lane's (a2 2^64 + a1 2^32 + a0) 2^-32 mod p_i: (a2 2^32 + a1) + a0 2^-32
+            uint32_t y = mp_add(mp_mul(mp_redc(a1, a2, M.p, M.pinv), M.r2, M), mp_redc(a0, 0u, M.p, M.pinv), M.p);
+            for (int o = 16; o; o >>= 1) y = mp_add(y, __shfl_xor_sync(0xffffffffu, y, o), M.p);
+            const uint32_t v = mp_mul(y, L.garner[i], M);
+            __syncwarp();
+            if (lane == 0) dig[i] = v;
+            __syncwarp();
+        }
+        // symmetric lift: X > (M - 1) / 2 <=> the digits compare above (p_i - 1) / 2 from the top
+        int cmp = 0;
+        for (int base = (k - 1) & ~31; base >= 0; base -= 32) {
+            const int i = base + lane;
+            int sgn = 0;
+            if (i < k) {
+                const uint32_t d = dig[i], h = (L.mods[i].p - 1u) >> 1;
+                sgn = (d > h) - (d < h);
+            }
+            const unsigned nz = __ballot_sync(0xffffffffu, sgn != 0);
+            if (nz) {
+                cmp = __shfl_sync(0xffffffffu, sgn, 31 - __clz(nz));
+                break;
+            }
+        }
+        const bool neg = cmp > 0;
+        // column sums of limbs l = lane, lane + 32, ...: limb l of prod_{j<i} p_j is zero
+        // while prod_{j<i} p_j < 2^(32 l), in particular for 31 i < 32 l (every p_j < 2^31)
+        for (int l = lane; l < Lp; l += 32) {
+            uint32_t a0 = 0u, a1 = 0u, a2 = 0u;
+            for (int i = (32 * l) / 31; i < k; ++i) {
+                uint32_t d = dig[i];
+                if (neg) d = L.mods[i].p - 1u - d;
+                mac96(a0, a1, a2, d, T[(size_t)i * LW + l]);
+            }
+            col[3 * l] = a0;
+            col[3 * l + 1] = a1;
+            col[3 * l + 2] = a2;
+        }
+        __syncwarp();
+        int nl = 0;
+        bool over = false;
+        if (lane == 0) {
+            // limb l of X (plus one for a negative value) = column l plus the carry; col[l]
+            // takes the limb once column l / 3 (<= l) has been read
+            unsigned __int128 acc = neg ? 1u : 0u;
+            for (int l = 0; l < Lp; ++l) {
+                acc += (unsigned __int128)col[3 * l] | ((unsigned __int128)col[3 * l + 1] << 32) |
+                       ((unsigned __int128)col[3 * l + 2] << 64);
+                const uint32_t limb = (uint32_t)acc;
+                acc >>= 32;
+                col[l] = limb;
+                if (limb) nl = l + 1;
+            }
+            over = acc != 0;
+        }
+        __syncwarp();
+        nl = __shfl_sync(0xffffffffu, nl, 0);
+        over = __shfl_sync(0xffffffffu, over, 0);
+        uint32_t *o = L.out + P.out_off + (int64_t)c * Lp;
+        for (int l = lane; l < Lp; l += 32) o[l] = col[l];
+        if (lane == 0) {
+            if (over) atomicExch(L.err, kErrCrtLimbs);
+            L.sign[P.sign_off + c] = nl == 0 ? 0 : (neg ? -1 : 1);
+            if (nl > 0) atomicMax(L.deg + q, c);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ A6: unlucky primes
 
 // Flags prime c of pair q when the leading row of f or of g vanishes identically
@@ -1292,6 +1394,7 @@ cudaError_t configure_res_kernels() {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_interp, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_crt, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_crt_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_crt_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_vinv, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
     return e;
 }
@@ -1361,6 +1464,17 @@ cudaError_t launch_pair_garner(const ResLaunch &L, const int32_t *pairs, int n, 
     if (total <= 0) return cudaSuccess;
     int grid = (int)std::min<int64_t>((total + 255) / 256, 4096);
     k_pair_garner<<<grid, 256, 0, s>>>(L, pairs, n, kmax, gtab);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_crt_warp(const ResLaunch &L, const WorkList &w, int maxK, int maxL, cudaStream_t s) {
+    if (w.total <= 0) return cudaSuccess;
+    if (maxK > L.crtw_K || !L.crtw) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)(kCrtWarpBlock / 32) * (maxK + 3 * maxL) * sizeof(uint32_t);
+    if (smem > kMaxDynSmem) return cudaErrorInvalidValue;
+    const int64_t blocks = (w.total + kCrtWarpBlock / 32 - 1) / (kCrtWarpBlock / 32);
+    const int grid = persistent_grid(k_crt_warp, kCrtWarpBlock, smem, blocks);
+    k_crt_warp<<<grid, kCrtWarpBlock, smem, s>>>(L, w, maxK, maxL);
     return cudaGetLastError();
 }
 

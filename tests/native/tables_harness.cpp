@@ -1,6 +1,6 @@
 // Test harness (CPU): the host-built constant tables of libgbres - the first K
-// table primes with their Montgomery constants, the Garner prefix table and the
-// inverse table - printed for a Python checker (linked against libgbres.so).
+// table primes with their Montgomery constants, the Garner prefix table, the
+// inverse table and the warp Chinese remaindering table - printed for a Python checker (linked against libgbres.so).
 // Built and run by test_host_native.py.
 #include <cstdio>
 #include <cstdlib>
@@ -19,6 +19,11 @@ int main(int argc, char **argv) {
     for (uint32_t v : g) std::printf("%u ", v);
     std::printf("\n");
     for (uint32_t v : inv) std::printf("%u ", v);
+    std::printf("\n");
+    std::vector<uint32_t> w(gbr::crt_warp_words(K));
+    gbr::crt_warp_table(K, w.data());
+    std::printf("%d\n", gbr::crt_warp_limbs(K));
+    for (uint32_t v : w) std::printf("%u ", v);
     std::printf("\n");
     return 0;
 }

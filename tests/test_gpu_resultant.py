@@ -161,6 +161,47 @@ def test_conic_curves_full(ctx):
     assert d == list(O.disc_res(f, "evalz"))
 
 
+def _bimul(a, b):
+    """Product in Z[x][y] of rows a[i] (coefficients of y^i, lists over x)."""
+    out = [[0] * (len(a[0]) + len(b[0]) - 1) for _ in range(len(a) + len(b) - 1)]
+    for i, ra in enumerate(a):
+        for j, rb in enumerate(b):
+            for s, x in enumerate(ra):
+                for t, y in enumerate(rb):
+                    out[i + j][s + t] += x * y
+    return out
+
+
+def test_warp_chinese_remaindering_prime_counts(ctx):
+    """Results that need between 65 and 512 primes take the Chinese remaindering with one
+    warp per coefficient (digit dot products split over the lanes, limb column sums);
+    pairs of several prime counts in one resident batch, a planted common factor, and a
+    one-shot call, every coefficient against the oracle."""
+    rng = random.Random(11)
+    shapes = [(3, 3, 1, 500), (4, 3, 2, 480), (6, 6, 1, 500), (8, 7, 1, 500), (12, 12, 1, 500), (2, 2, 3, 500),
+              (5, 5, 0, 400)]
+    fs, gs = [], []
+    for m, n, dx, b in shapes:
+        fs.append([[rng.randint(-2 ** b, 2 ** b) for _ in range(dx + 1)] for _ in range(m + 1)])
+        gs.append([[rng.randint(-2 ** b, 2 ** b) for _ in range(dx + 1)] for _ in range(n + 1)])
+    h = [[rng.randint(-9, 9), 1], [rng.randint(1, 9), rng.randint(-9, 9)]]   # y-degree 1: a common factor
+    fs.append(_bimul(fs[2], h))
+    gs.append(_bimul(gs[1], h))
+    res = ctx.upload_pairs(fs, gs)
+    try:
+        res.run()
+        got = res.fetch()
+        plans = res.plan()
+    finally:
+        res.free()
+    ks = [p["primes"] for p in plans]
+    assert sum(64 < k <= 512 for k in ks) >= 5, ks
+    for f, g, r in zip(fs, gs, got):
+        assert r == _oracle(f, g)
+    assert got[-1] == []
+    assert ctx.resultant(fs[4], gs[4]) == got[4]
+
+
 @pytest.fixture(scope="module")
 def opool():
     """Oracle workers on every host core (spawn: safe after CUDA initialisation)."""

@@ -565,7 +565,9 @@ def test_host_constant_tables(tmp_path):
     launch reads: the table primes (the largest primes below 2^32 / 3 that are
     1 mod 2^14, in descending order) with pinv = -p^-1 mod 2^32, r1 = 2^32 mod p, r2 = 2^64 mod p;
     the Garner prefix table ((p_0 ... p_{i-1})^-1 and p_j mod p_i, Montgomery form);
-    the inverse table (1/t mod p_i, Montgomery form), against their definitions."""
+    the inverse table (1/t mod p_i, Montgomery form); the warp Chinese remaindering
+    table (Garner rows (-p_0 ... p_{j-1}) R mod p_i, limbs of p_0 ... p_{i-1}),
+    against their definitions."""
     if not os.path.exists(N.LIB_PATH):
         from paper_1103_4697_gb300.build import build
         build()
@@ -599,6 +601,21 @@ def test_host_constant_tables(tmp_path):
         assert inv[i * T] == 0
         for t in range(1, T):
             assert inv[i * T + t] == pow(t, -1, p) * R % p
+    LW = int(out[3 + K])
+    assert LW == (31 * K + 31) // 32
+    w = [int(v) for v in out[4 + K].split()]
+    assert len(w) == K * (K - 1) // 2 + K * LW
+    for i, p in enumerate(ps):
+        for j in range(i):
+            prod = 1
+            for t in range(j):
+                prod *= ps[t]
+            assert w[i * (i - 1) // 2 + j] == (-prod) % p * R % p
+    prod = 1
+    for i in range(K):
+        row = w[K * (K - 1) // 2 + i * LW:K * (K - 1) // 2 + (i + 1) * LW]
+        assert sum(v << (32 * l) for l, v in enumerate(row)) == prod
+        prod *= ps[i]
 
 
 def test_device_prime_table_bytes(tmp_path):
