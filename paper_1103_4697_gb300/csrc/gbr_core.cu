@@ -1564,7 +1564,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
         Pmax = std::max(Pmax, p.Pe);
         Puse = std::max(Puse, p.P);
         Lmax = std::max(Lmax, p.L);
-        red.add(q, p.S);
+        red.add(q, (int64_t)p.S * ((k + 31) / 32));   // k_reduce: a thread per slot and 32 primes
         int key = ((std::max(p.m, p.n) + 1) + 3) / 4 * 4;
         const int rN = p.sym && c->reg_on ? reg_shape(p.m, p.n) : 0;
         // lanes: 32 per warp tile of each prime (a quartic set's warps span its primes)

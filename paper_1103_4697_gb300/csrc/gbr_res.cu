@@ -7,14 +7,16 @@
 // (3) interpolation in x and Chinese remaindering recover the integer result.
 // Stages:
 //   bounds   (A0) actual degrees and the Hadamard bound, one warp per pair
-//   reduce   (A1) coefficients -> residues mod every prime (Montgomery form)
+//   reduce   (A1) coefficients -> residues mod every prime (Montgomery form), one
+//            thread per (pair, coefficient slot, run of 32 primes)
 //   evalres  (A2+A3) one thread per (pair, prime, point): Horner evaluation of
 //            every y-coefficient at x = point, then the univariate resultant with
 //            formal degrees by fraction-free remainder steps
 //   interp   (A4) one warp per (pair, prime): Newton interpolation on the
 //            points 0..P-1 and conversion to monomial coefficients
-//   crt      (A5) one thread per (pair, coefficient): Garner mixed-radix digits,
-//            symmetric lift, magnitude limbs
+//   crt      (A5) one thread per (pair, coefficient) on up to 64 primes (one warp per
+//            coefficient up to 512): Garner mixed-radix digits, symmetric lift,
+//            magnitude limbs
 #include <limits.h>
 #include <math.h>
 
@@ -682,9 +684,13 @@ __global__ void k_reduce(ResLaunch L, WorkList w) {
         if (item >= w.total) continue;
         while (bi + 1 < w.n && item >= w.start[bi + 1]) ++bi;
         const int q = w.pairs[bi];
-        const int s = (int)(item - w.start[bi]);   // below S < 2^31
         const PairPlan &P = L.plan[q];
         const PairDesc &D = L.desc[q];
+        // item = chunk S + s: slot s for the primes 32 chunk .. 32 chunk + 31 (results
+        // on many primes spread over more threads)
+        const int64_t local = item - w.start[bi];
+        const int chunk = (int)(local / P.S);
+        const int s = (int)(local - (int64_t)chunk * P.S);   // below S < 2^31
         const int rf4 = rows4(P.m), rg4 = rows4(P.n);
         const int nf = (P.dxf + 1) * rf4;
         const PolyDesc *src;
@@ -706,10 +712,10 @@ __global__ void k_reduce(ResLaunch L, WorkList w) {
                 src = &D.g;
             }
         }
-        uint32_t *dst = L.res + P.res_off + s;
-        const int K = P.k, S = P.S;
+        const int S = P.S, I0 = 32 * chunk, K = min(P.k, I0 + 32);
+        uint32_t *dst = L.res + P.res_off + s + (int64_t)I0 * S;
         if (row >= nrows) {                       // padding rows hold zeros
-            for (int i = 0; i < K; ++i, dst += S) *dst = 0u;
+            for (int i = I0; i < K; ++i, dst += S) *dst = 0u;
             continue;
         }
         const uint64_t *cp = coef_ptr(L.coef, *src, mult ? row + 1 : row, col);
@@ -726,7 +732,7 @@ __global__ void k_reduce(ResLaunch L, WorkList w) {
             const int32_t *pm = P.pmap_off < 0 ? nullptr : L.pmap + P.pmap_off;
             if (!wide && !mult && !pm && K <= kReduceSmemPrimes) {
                 // one Shoup product lo W - q p with q = floor(lo W' / 2^32): in [0, 2p)
-                for (int i = 0; i < K; ++i, dst += S) {
+                for (int i = I0; i < K; ++i, dst += S) {
                     const uint32_t p = sp[i];
                     uint32_t r = lo * sw[i] - __umulhi(lo, swp[i]) * p;
                     r = min(r, r - p);
@@ -734,7 +740,7 @@ __global__ void k_reduce(ResLaunch L, WorkList w) {
                 }
                 continue;
             }
-            for (int i = 0; i < K; ++i, dst += S) {
+            for (int i = I0; i < K; ++i, dst += S) {
                 const int pi = pm ? pm[i] : i;
                 const ModP M = L.mods[pi];
                 const uint2 r34 = L.r34[pi];
@@ -755,7 +761,7 @@ __global__ void k_reduce(ResLaunch L, WorkList w) {
         }
         uint64_t wbuf[8];
         for (int i = 0; i < W; ++i) wbuf[i] = cp[i];
-        for (int i = 0; i < K; ++i, dst += S) {
+        for (int i = I0; i < K; ++i, dst += S) {
             ModP M = L.mods[prime_of(P, L.pmap, i)];
             uint32_t r = mp_from_words(wbuf, W, M);
             if (mult) r = mp_mul(r, mp_to((uint32_t)mult, M), M);
