@@ -83,6 +83,7 @@ __device__ __forceinline__ const uint64_t *coef_ptr(const uint64_t *coef, const 
 // directed rounding and explicit error margins (each value is an upper bound)
 // and keeps the smallest (the FP64 pipe of this part is slow).
 constexpr int kBoundsWarps = 4;
+constexpr int kBoundsTeamPairs = 256;   // batches up to this size: four warps per pair
 
 // Row quantity of the Hadamard bound.  For a row f_r(x) = sum_a c_a x^a with
 // int64 coefficients: G = A_0 + 2 sum_{k>0} |A_k|, A_k = sum_a c_a c_{a+k} (the
@@ -337,17 +338,54 @@ __device__ long long scaled_hadamard_fx(const float *lf, int m, const float *lg,
     return (row < col ? row : col) - lam;
 }
 
+// Degree statistics of one polynomial from the row degrees rd[0..rows] (-1: zero row),
+// warp-parallel over the rows: the degree, the largest x-degree, the total degree, the
+// coefficient count up to the degree, the leading row's x-degree.
+__device__ void row_stats(const int32_t *rd, int rows, int lane, int &mdeg, int &dxmax, int &td, int &terms_upto,
+                          int &lcd) {
+    int md = -1, dx = -1, t = -1;
+    for (int r = lane; r <= rows; r += 32) {
+        const int c = rd[r];
+        if (c >= 0) {
+            md = max(md, r);
+            dx = max(dx, c);
+            t = max(t, r + c);
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        md = max(md, __shfl_xor_sync(0xffffffffu, md, o));
+        dx = max(dx, __shfl_xor_sync(0xffffffffu, dx, o));
+        t = max(t, __shfl_xor_sync(0xffffffffu, t, o));
+    }
+    int terms = 0;
+    for (int r = lane; r <= md; r += 32) terms += rd[r] + 1;
+    for (int o = 16; o; o >>= 1) terms += __shfl_xor_sync(0xffffffffu, terms, o);
+    mdeg = md;
+    dxmax = dx;
+    td = t;
+    terms_upto = md >= 0 ? terms : 0;
+    lcd = md >= 0 ? rd[md] : -1;
+}
+
+// One warp per pair (four pairs per block), or, for batches of at most
+// kBoundsTeamPairs pairs, four warps per pair (a block per pair: the rows and the
+// scalings lambda split over the warps, the row statistics taken from the row degrees
+// afterwards, the smallest bound over the warps): the same quantities either way, the
+// team only shortens a small batch's latency.
 // (at most 72 registers: seven 4-warp blocks per SM, so a batch of 4096 pairs
 // runs in one wave on 152 SMs)
-__global__ void __launch_bounds__(kBoundsWarps * 32, 7) k_bounds(ResLaunch L) {
+__global__ void __launch_bounds__(kBoundsWarps * 32, 7) k_bounds(ResLaunch L, int team) {
     __shared__ float lff[kBoundsWarps][GBR_MAX_YDEG + 2], lgf[kBoundsWarps][GBR_MAX_YDEG + 2];
     __shared__ float tbuf[kBoundsWarps][2][GBR_MAX_YDEG + 2];
     __shared__ float xbuf[kBoundsWarps][2][GBR_MAX_YDEG + 2];
     __shared__ int64_t rbuf[kBoundsWarps][kRowBuf];
+    __shared__ long long tbest[kBoundsWarps];
     const int wib = threadIdx.x >> 5;
-    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (warp >= L.npairs) return;
+    const int lane = threadIdx.x & 31;
+    // team: warp wt of T = kBoundsWarps shares pair blockIdx.x; else T = 1, wt = 0
+    const int T = team ? kBoundsWarps : 1, wt = team ? wib : 0, slot = team ? 0 : wib;
+    const int warp = team ? blockIdx.x : (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (warp >= L.npairs) return;   // (a team's block is never past the end: the grid is the batch)
     const PairDesc D = L.desc[warp];
     PairBound B;
     B.tg = 0;
@@ -356,10 +394,10 @@ __global__ void __launch_bounds__(kBoundsWarps * 32, 7) k_bounds(ResLaunch L) {
     for (int which = 0; which < 2; ++which) {
         if (which == 1 && D.disc) break;
         const PolyDesc &P = which ? D.g : D.f;
-        float *ln_out = which ? lgf[wib] : lff[wib];
+        float *ln_out = which ? lgf[slot] : lff[slot];
         int mdeg = -1, dxmax = -1, td = -1, terms = 0, terms_upto = 0, lcd = -1;
         int mdeg_g = -1, dx_g = -1, td_g = -1, terms_g = 0, terms_g_upto = 0, lcd_g = -1;
-        for (int r = 0; r <= P.rows; ++r) {
+        for (int r = wt; r <= P.rows; r += T) {
             int cmax;
             const float ln = row_log2_up(L.coef, P, r, lane, cmax, rbuf[wib]);
             if (lane == 0) {
@@ -379,7 +417,7 @@ __global__ void __launch_bounds__(kBoundsWarps * 32, 7) k_bounds(ResLaunch L) {
                 if (lane == 0) {
                     L.rowdeg[D.g.rowdeg_off + r - 1] = cmax;
                     if (r - 1 <= GBR_MAX_YDEG)
-                        lgf[wib][r - 1] =
+                        lgf[slot][r - 1] =
                             ln == -INFINITY ? -INFINITY : __fadd_ru(ln, __fadd_ru(log2f((float)r), 0x1p-19f));
                 }
                 terms_g += cmax + 1;
@@ -391,6 +429,14 @@ __global__ void __launch_bounds__(kBoundsWarps * 32, 7) k_bounds(ResLaunch L) {
                     td_g = max(td_g, r - 1 + cmax);
                 }
             }
+        }
+        if (team) {
+            // the rows were split over the warps: the statistics from the row degrees
+            // every warp wrote (visible to the block after the barrier)
+            __syncthreads();
+            row_stats(L.rowdeg + P.rowdeg_off, P.rows, lane, mdeg, dxmax, td, terms_upto, lcd);
+            if (which == 0 && D.disc)
+                row_stats(L.rowdeg + D.g.rowdeg_off, P.rows - 1, lane, mdeg_g, dx_g, td_g, terms_g_upto, lcd_g);
         }
         __syncwarp();
         if (which == 0) {
@@ -407,15 +453,22 @@ __global__ void __launch_bounds__(kBoundsWarps * 32, 7) k_bounds(ResLaunch L) {
     if (B.m >= 0 && B.n >= 0 && B.m <= GBR_MAX_YDEG && B.n <= GBR_MAX_YDEG && (B.m > 0 || B.n > 0)) {
         // every lambda gives a valid bound; each evaluation is itself an upper bound
         long long best = LLONG_MAX;
-        for (int l = 0; l < kBoundLambdas; ++l) {
-            const long long v = scaled_hadamard_fx(lff[wib], B.m, lgf[wib], B.n, bound_lambda_f(l), tbuf[wib][0],
+        for (int l = wt; l < kBoundLambdas; l += T) {
+            const long long v = scaled_hadamard_fx(lff[slot], B.m, lgf[slot], B.n, bound_lambda_f(l), tbuf[wib][0],
                                                    tbuf[wib][1], xbuf[wib][0], xbuf[wib][1], lane);
             best = v < best ? v : best;
         }
+        if (team) {
+            if (lane == 0) tbest[wib] = best;
+            __syncthreads();
+            for (int t = 0; t < kBoundsWarps; ++t) best = tbest[t] < best ? tbest[t] : best;
+        }
         lb = best == LLONG_MIN ? -INFINITY : (double)best * 0x1p-17 + 0x1p-10;
+    } else if (team) {
+        __syncthreads();   // (uniform over the block: every warp of the team sees the same B)
     }
     B.log2B = lb;
-    if (lane == 0) L.bounds[warp] = B;
+    if (lane == 0 && wt == 0) L.bounds[warp] = B;
 }
 
 // Summed forms of the bound for small shapes (y-degrees at most kSumMaxY, entries of
@@ -602,8 +655,9 @@ __global__ void __launch_bounds__(kSumWarps * 32) k_bounds_summed(ResLaunch L) {
 cudaError_t launch_bounds(const ResLaunch &L, cudaStream_t s) {
     if (L.npairs <= 0) return cudaSuccess;
     int threads = kBoundsWarps * 32;
-    int blocks = (L.npairs * 32 + threads - 1) / threads;
-    k_bounds<<<blocks, threads, 0, s>>>(L);
+    const int team = L.npairs <= kBoundsTeamPairs;
+    int blocks = team ? L.npairs : (L.npairs * 32 + threads - 1) / threads;
+    k_bounds<<<blocks, threads, 0, s>>>(L, team);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     threads = kSumWarps * 32;
@@ -1252,7 +1306,17 @@ __global__ void __launch_bounds__(kCrtWarpBlock) k_crt_warp(ResLaunch L, WorkLis
     if (stage_skipped(L)) return;
     extern __shared__ uint32_t smw[];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    uint32_t *dig = smw + (size_t)wib * (KD + 3 * LD);   // KD digits, then LD 96-bit column sums
+    // the primes' constants, staged once per block: p, -p^-1, R^2 mod p, (prod_{j<i} p_j)^-1 R
+    uint32_t *cp = smw, *cpinv = cp + KD, *cr2 = cpinv + KD, *cgi = cr2 + KD;
+    for (int i = threadIdx.x; i < KD; i += blockDim.x) {
+        const ModP M = L.mods[i];
+        cp[i] = M.p;
+        cpinv[i] = M.pinv;
+        cr2[i] = M.r2;
+        cgi[i] = L.garner[i];
+    }
+    __syncthreads();
+    uint32_t *dig = smw + 4 * (size_t)KD + (size_t)wib * (KD + 3 * LD);   // KD digits, then LD 96-bit column sums
     uint32_t *col = dig + KD;
     const int KW = L.crtw_K, LW = crt_warp_limbs(KW);
     const uint32_t *T = L.crtw + (size_t)KW * (KW - 1) / 2;
@@ -1266,15 +1330,21 @@ __global__ void __launch_bounds__(kCrtWarpBlock) k_crt_warp(ResLaunch L, WorkLis
         __syncwarp();
         for (int i = lane; i < k; i += 32) dig[i] = src[(int64_t)i * Pn];   // residues, then digits in place
         __syncwarp();
+        // the first table entry of each row this lane reads (j = lane) is loaded one digit
+        // ahead, so that the row's latency overlaps the previous digit's reduction
+        uint32_t gnext = lane < 1 ? L.crtw[lane] : 0u;
         for (int i = 1; i < k; ++i) {
-            const ModP M = L.mods[i];
+            const ModP M{cp[i], cpinv[i], 0u, cr2[i]};
             const uint32_t *Gi = L.crtw + (size_t)i * (i - 1) / 2;
+            const uint32_t g0 = gnext;
+            if (i + 1 < k) gnext = lane < i + 1 ? Gi[i + lane] : 0u;   // row i + 1 starts i words after row i
             uint32_t a0 = 0u, a1 = lane == 0 ? dig[i] : 0u, a2 = 0u;
-            for (int j = lane; j < i; j += 32) mac96(a0, a1, a2, dig[j], Gi[j]);
+            if (lane < i) mac96(a0, a1, a2, dig[lane], g0);
+            for (int j = lane + 32; j < i; j += 32) mac96(a0, a1, a2, dig[j], Gi[j]);
             // this lane's (a2 2^64 + a1 2^32 + a0) 2^-32 mod p_i: (a2 2^32 + a1) + a0 2^-32
             uint32_t y = mp_add(mp_mul(mp_redc(a1, a2, M.p, M.pinv), M.r2, M), mp_redc(a0, 0u, M.p, M.pinv), M.p);
             for (int o = 16; o; o >>= 1) y = mp_add(y, __shfl_xor_sync(0xffffffffu, y, o), M.p);
-            const uint32_t v = mp_mul(y, L.garner[i], M);
+            const uint32_t v = mp_mul(y, cgi[i], M);
             __syncwarp();
             if (lane == 0) dig[i] = v;
             __syncwarp();
@@ -1285,7 +1355,7 @@ __global__ void __launch_bounds__(kCrtWarpBlock) k_crt_warp(ResLaunch L, WorkLis
             const int i = base + lane;
             int sgn = 0;
             if (i < k) {
-                const uint32_t d = dig[i], h = (L.mods[i].p - 1u) >> 1;
+                const uint32_t d = dig[i], h = (cp[i] - 1u) >> 1;
                 sgn = (d > h) - (d < h);
             }
             const unsigned nz = __ballot_sync(0xffffffffu, sgn != 0);
@@ -1299,9 +1369,10 @@ __global__ void __launch_bounds__(kCrtWarpBlock) k_crt_warp(ResLaunch L, WorkLis
         // while prod_{j<i} p_j < 2^(32 l), in particular for 31 i < 32 l (every p_j < 2^31)
         for (int l = lane; l < Lp; l += 32) {
             uint32_t a0 = 0u, a1 = 0u, a2 = 0u;
+#pragma unroll 4
             for (int i = (32 * l) / 31; i < k; ++i) {
                 uint32_t d = dig[i];
-                if (neg) d = L.mods[i].p - 1u - d;
+                if (neg) d = cp[i] - 1u - d;
                 mac96(a0, a1, a2, d, T[(size_t)i * LW + l]);
             }
             col[3 * l] = a0;
@@ -1476,7 +1547,7 @@ cudaError_t launch_pair_garner(const ResLaunch &L, const int32_t *pairs, int n, 
 cudaError_t launch_crt_warp(const ResLaunch &L, const WorkList &w, int maxK, int maxL, cudaStream_t s) {
     if (w.total <= 0) return cudaSuccess;
     if (maxK > L.crtw_K || !L.crtw) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)(kCrtWarpBlock / 32) * (maxK + 3 * maxL) * sizeof(uint32_t);
+    const size_t smem = (4 * (size_t)maxK + (size_t)(kCrtWarpBlock / 32) * (maxK + 3 * maxL)) * sizeof(uint32_t);
     if (smem > kMaxDynSmem) return cudaErrorInvalidValue;
     const int64_t blocks = (w.total + kCrtWarpBlock / 32 - 1) / (kCrtWarpBlock / 32);
     const int grid = persistent_grid(k_crt_warp, kCrtWarpBlock, smem, blocks);

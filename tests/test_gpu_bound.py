@@ -147,3 +147,34 @@ def test_device_bound_at_least_the_exact_bound():
         d.free()
     n = _check(plans, exact, pairs) + _check(dplans, dexact, polys)
     assert n >= 200
+
+
+def test_bound_same_in_small_and_large_batches():
+    """Batches of at most 256 pairs take the bound with four warps per pair (rows and
+    scalings split over the warps), larger ones with one warp per pair: every job gets
+    the same plan (degrees, bound, primes) either way, for resultants and res(f, f_y)."""
+    from paper_1103_4697_gb300.api import Context
+
+    pairs = bound_pairs()
+    polys = disc_polys()
+    with Context(device=0, mem_budget=4 << 30) as ctx:
+        def plans(fs, gs, disc=False):
+            r = ctx.upload_pairs(fs, gs, disc=disc)
+            try:
+                r.run()
+                return r.plan()
+            finally:
+                r.free()
+
+        jobs = pairs * 2
+        assert len(jobs) > 256
+        big = plans([f for f, _ in jobs], [g for _, g in jobs])
+        small = []
+        for i in range(0, len(pairs), 7):
+            chunk = pairs[i:i + 7]
+            small += plans([f for f, _ in chunk], [g for _, g in chunk])
+        assert big[:len(pairs)] == small and big[len(pairs):] == small
+        dbig = plans(polys * 17, None, disc=True)
+        assert len(polys) * 17 > 256
+        dsmall = [p for f in polys for p in plans([f], None, disc=True)]
+        assert dbig[:len(polys)] == dsmall
