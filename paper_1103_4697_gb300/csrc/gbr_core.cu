@@ -2620,7 +2620,10 @@ static double summed_bound_host(const gbr_bipoly *f, const gbr_bipoly *g, int va
     return best;
 }
 
-extern "C" int gbr_resultant_info(const gbr_bipoly *f, const gbr_bipoly *g, int var, int disc, gbr_res_info *out) {
+// summed = false leaves out the summed forms: a bound at least as large for a cheaper
+// estimate (the serving admission sizes a job's buffers from it on the submitting thread,
+// where the exact class sums of the summed forms cost more than the request's copy).
+int resultant_info_impl(const gbr_bipoly *f, const gbr_bipoly *g, int var, int disc, gbr_res_info *out, bool summed) {
     if (!out || (var != 0 && var != 1) || check_bipoly(f) || (!disc && check_bipoly(g))) return GBR_EINVAL;
     std::vector<int> df, dg;
     std::vector<double> nf, ng;
@@ -2659,10 +2662,14 @@ extern "C" int gbr_resultant_info(const gbr_bipoly *f, const gbr_bipoly *g, int 
     if (b.m > GBR_MAX_YDEG || b.n > GBR_MAX_YDEG) return GBR_ELIMIT;
     std::vector<double> ef(b.m + 2), eg(b.n + 2);
     b.log2B = best_scaled_bound(nf.data(), b.m, ng.data(), b.n, ef.data(), eg.data());
-    b.log2B = std::min(b.log2B, summed_bound_host(f, g, var, disc, b.m, b.n, b.dxf, b.dxg));
+    if (summed) b.log2B = std::min(b.log2B, summed_bound_host(f, g, var, disc, b.m, b.n, b.dxf, b.dxg));
     out->deg_bound = degree_bound(b);
     out->log2_bound = b.log2B;
     out->primes = primes_for_bits(b.log2B * (1.0 + 1e-9) + 2.0);
     out->limbs = (31 * out->primes + 31) / 32;
     return GBR_OK;
+}
+
+extern "C" int gbr_resultant_info(const gbr_bipoly *f, const gbr_bipoly *g, int var, int disc, gbr_res_info *out) {
+    return resultant_info_impl(f, g, var, disc, out, true);
 }

@@ -189,4 +189,6 @@ int gbr_gcd_cof_locked(gbr_ctx *c, int n, const gbr_upoly *p, const gbr_upoly *q
 char *gbr_pinned_result_block(size_t bytes, size_t *got);
 void gbr_register_result_block(char *base, size_t size, int64_t refs, bool pinned);
 gbr_ctx *gbr_make_worker(gbr_ctx *parent);    // own stream and tables, parent's arena
+// gbr_resultant_info, with the summed forms of the bound (small shapes) or without them
+int resultant_info_impl(const gbr_bipoly *f, const gbr_bipoly *g, int var, int disc, gbr_res_info *out, bool summed);
 void gbr_destroy_worker(gbr_ctx *w);

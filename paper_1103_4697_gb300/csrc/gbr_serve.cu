@@ -63,7 +63,8 @@ static size_t estimate_bytes(const ServeJob &j) {
         return (size_t)(k * S * 4 * 2 + (dp + dq + 2) * 8 * 2 + 4096);
     }
     gbr_res_info info{};
-    if (gbr_resultant_info(&j.f, j.kind == GBR_JOB_DISC ? &j.f : &j.g, j.var, j.kind == GBR_JOB_DISC, &info) ||
+    // the per-entry bound alone: never fewer primes than the plan takes, and cheap
+    if (resultant_info_impl(&j.f, j.kind == GBR_JOB_DISC ? &j.f : &j.g, j.var, j.kind == GBR_JOB_DISC, &info, false) ||
         info.m < 0 || info.n < 0)
         return 4096;
     int64_t P = info.deg_bound + 1, k = info.primes, L = info.limbs;
