@@ -1364,6 +1364,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
     std::vector<PairPlan> &plan = r->h_plan;
     plan.assign(n, PairPlan{});
     r->h_log2B.assign(n, 0.0);
+    r->h_deg.assign(n, -1);
     const bool drop = c->drop_unlucky != 0;
     // per pair: degrees, points, primes; the first failing pair decides the error
     // (a serial loop: waking the host workers costs more than this work)
@@ -1397,6 +1398,7 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
                 continue;
             }
             p.P = (int32_t)(D + 1);
+            r->h_deg[q] = (int32_t)D;
             r->h_log2B[q] = b.log2B;
             double bits = b.log2B * (1.0 + 1e-9) + 2.0;
             int k = primes_for_bits(bits);
@@ -1420,6 +1422,40 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
                 continue;
             }
             kcl = std::max(kcl, p.k + 32);
+        }
+    }
+    // close point counts are shared: a group of pairs with one point count shares its
+    // interpolation matrices and fills the contraction's tiles of kTcTileN pairs, and a
+    // group of a few pairs costs about as much as a full one per prime and part, so
+    // groups of fewer than kTcTileN pairs take the next larger point count of the batch
+    // while that stays within 1/16 (at least 4 points) above the smallest count taken
+    // (a degree bound may always be raised: the extra coefficients interpolate to 0)
+    if (!drop && c->gemm_on) {
+        std::map<int32_t, int> cnt;
+        for (int q = 0; q < n; ++q)
+            if (!perr[q] && !(plan[q].flags & PLAN_ZERO)) ++cnt[plan[q].P];
+        std::unordered_map<int32_t, int32_t> to;
+        const std::vector<std::pair<int32_t, int>> v(cnt.begin(), cnt.end());
+        size_t start = 0;
+        int acc = 0;
+        for (size_t i = 0; i < v.size(); ++i) {
+            acc += v[i].second;
+            const int32_t lo = v[start].first;
+            const bool more = i + 1 < v.size() && acc < kTcTileN &&
+                              v[i + 1].first <= lo + std::max<int32_t>(4, lo / 16);
+            if (more) continue;
+            for (size_t j = start; j <= i; ++j) to[v[j].first] = v[i].first;
+            start = i + 1;
+            acc = 0;
+        }
+        for (int q = 0; q < n; ++q) {
+            PairPlan &p = plan[q];
+            if (perr[q] || (p.flags & PLAN_ZERO)) continue;
+            const int32_t P2 = to[p.P];
+            if (P2 == p.P) continue;
+            p.P = P2;
+            p.Pe = 2 * (p.P / 2) + 1;   // the symmetric set (the drop mode is excluded above)
+            p.tiles = (p.P / 2 + 1 + 15) / 16;
         }
     }
     // the matrices of this run are marked from here on (the point-set choice below
@@ -2368,7 +2404,7 @@ extern "C" int gbr_resident_plan(gbr_ctx *c, gbr_resident *r, int first, int cou
         o.m = p.m;
         o.n = p.n;
         const bool zero = (p.flags & PLAN_ZERO) != 0;
-        o.deg_bound = zero ? -1 : p.P - 1;
+        o.deg_bound = zero ? -1 : r->h_deg[first + i];   // (the plan may use more points)
         o.primes = zero ? 0 : p.k;
         o.limbs = zero ? 0 : p.L;
         o.log2_bound = zero ? 0.0 : r->h_log2B[first + i];

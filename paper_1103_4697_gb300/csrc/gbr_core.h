@@ -132,6 +132,7 @@ struct gbr_resident {
     std::vector<gbr::PairDesc> h_desc;
     std::vector<gbr::PairPlan> h_plan;
     std::vector<double> h_log2B;        // the device's coefficient bound per job (log2)
+    std::vector<int32_t> h_deg;         // the degree bound per job (the plan's points may be more)
     std::vector<char> h_blk;            // host copy of the last plan block (storage reused)
     char *d_planblk = nullptr;
     size_t planblk_cap = 0;

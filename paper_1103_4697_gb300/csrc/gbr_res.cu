@@ -683,8 +683,10 @@ __global__ void k_plan_check(const PairBound *bounds, const PairPlan *plan, int 
             bad = bad || (B.m >= 0 && B.n >= 0);
             continue;
         }
+        // the plan's points must cover the degree bound (a planned point count may be
+        // larger: close counts of a batch are shared)
         if (B.m != p.m || B.n != p.n || max(B.dxf, 0) != p.dxf || max(B.dxg, 0) != p.dxg ||
-            (int64_t)degree_bound(B) + 1 != p.P) {
+            (int64_t)degree_bound(B) + 1 > p.P) {
             bad = true;
             continue;
         }
