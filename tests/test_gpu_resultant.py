@@ -202,6 +202,31 @@ def test_warp_chinese_remaindering_prime_counts(ctx):
     assert ctx.resultant(fs[4], gs[4]) == got[4]
 
 
+def test_close_point_counts_share_a_group(ctx):
+    """Pairs whose degree bounds lie within a few points of each other share one point
+    count (one contraction group): every result equals the oracle, the plan reports each
+    pair's own degree bound, and replays from the step graph keep the results."""
+    from paper_1103_4697_gb300.api import resultant_info
+
+    rng = random.Random(23)
+    fs, gs = [], []
+    for dy, dx in ((5, 6), (6, 5), (3, 10), (4, 8), (2, 16), (5, 7), (7, 5), (4, 9), (6, 6), (3, 11)) * 2:
+        fs.append([[rng.randint(-999, 999) for _ in range(dx + 1)] for _ in range(dy + 1)])
+        gs.append([[rng.randint(-999, 999) for _ in range(dx + 1)] for _ in range(dy + 1)])
+    want = [_oracle(f, g) for f, g in zip(fs, gs)]
+    res = ctx.upload_pairs(fs, gs)
+    try:
+        for _ in range(5):
+            res.run()
+            assert res.fetch() == want
+        plans = res.plan()
+    finally:
+        res.free()
+    bounds = [resultant_info(f, g)["deg_bound"] for f, g in zip(fs, gs)]
+    assert [p["deg_bound"] for p in plans] == bounds
+    assert len(set(bounds)) > 2
+
+
 @pytest.fixture(scope="module")
 def opool():
     """Oracle workers on every host core (spawn: safe after CUDA initialisation)."""
