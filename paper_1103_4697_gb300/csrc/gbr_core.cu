@@ -1424,30 +1424,18 @@ int gbr_run_resident_launch(gbr_ctx *c, gbr_resident *r) {
             kcl = std::max(kcl, p.k + 32);
         }
     }
-    // close point counts are shared: a group of pairs with one point count shares its
-    // interpolation matrices and fills the contraction's tiles of kTcTileN pairs, and a
-    // group of a few pairs costs about as much as a full one per prime and part, so
-    // groups of fewer than kTcTileN pairs take the next larger point count of the batch
-    // while that stays within 1/16 (at least 4 points) above the smallest count taken
-    // (a degree bound may always be raised: the extra coefficients interpolate to 0)
+    // close point counts are shared (share_point_counts): a group of pairs with one
+    // point count shares its interpolation matrices and fills the contraction's tiles of
+    // kTcTileN pairs (a degree bound may always be raised: the extra coefficients
+    // interpolate to 0)
     if (!drop && c->gemm_on) {
         std::map<int32_t, int> cnt;
         for (int q = 0; q < n; ++q)
             if (!perr[q] && !(plan[q].flags & PLAN_ZERO)) ++cnt[plan[q].P];
-        std::unordered_map<int32_t, int32_t> to;
         const std::vector<std::pair<int32_t, int>> v(cnt.begin(), cnt.end());
-        size_t start = 0;
-        int acc = 0;
-        for (size_t i = 0; i < v.size(); ++i) {
-            acc += v[i].second;
-            const int32_t lo = v[start].first;
-            const bool more = i + 1 < v.size() && acc < kTcTileN &&
-                              v[i + 1].first <= lo + std::max<int32_t>(4, lo / 16);
-            if (more) continue;
-            for (size_t j = start; j <= i; ++j) to[v[j].first] = v[i].first;
-            start = i + 1;
-            acc = 0;
-        }
+        const std::vector<int32_t> raised = share_point_counts(v, kTcTileN);
+        std::unordered_map<int32_t, int32_t> to;
+        for (size_t i = 0; i < v.size(); ++i) to[v[i].first] = raised[i];
         for (int q = 0; q < n; ++q) {
             PairPlan &p = plan[q];
             if (perr[q] || (p.flags & PLAN_ZERO)) continue;

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/gbres.h"
@@ -271,6 +272,29 @@ GBR_HD int root_points(int P) {
     int N = 64;
     while (N < P) N <<= 1;
     return N;
+}
+
+// Shared point counts of a batch.  counts: the batch's distinct point counts in
+// ascending order with their numbers of pairs.  Returns the count each one is raised to:
+// runs of consecutive counts take the run's largest, a run growing while it holds fewer
+// than `tile` pairs and the next count stays within 1/16 (at least 4 points) above the
+// run's smallest.  (A contraction group of a few pairs costs about as much as a full
+// tile; a degree bound may always be raised.)
+inline std::vector<int32_t> share_point_counts(const std::vector<std::pair<int32_t, int>> &counts, int tile) {
+    std::vector<int32_t> to(counts.size());
+    size_t start = 0;
+    int64_t acc = 0;
+    for (size_t i = 0; i < counts.size(); ++i) {
+        acc += counts[i].second;
+        const int32_t lo = counts[start].first;
+        const bool more = i + 1 < counts.size() && acc < tile &&
+                          counts[i + 1].first <= lo + (lo / 16 > 4 ? lo / 16 : 4);
+        if (more) continue;
+        for (size_t j = start; j <= i; ++j) to[j] = counts[i].first;
+        start = i + 1;
+        acc = 0;
+    }
+    return to;
 }
 
 // Whether root-of-unity points pay for a pair with P coefficients (N points),

@@ -2,7 +2,8 @@
 // sees them - which shapes take the register form (reg_shape), the evaluation
 // point order (point_of), the point sets of the interpolation matrices
 // (vinv_point), the padded row count of the residue layout (rows4), the size of a
-// root-of-unity point set (root_points) and the point-set choice (roots_pay).  Prints
+// root-of-unity point set (root_points), the point-set choice (roots_pay) and the
+// shared point counts of a batch (share_point_counts).  Prints
 // them for a Python checker.  Built and run by test_host_native.py with the CUDA
 // toolkit's include directory (the header declares the launch wrappers).
 #include <cstdio>
@@ -31,5 +32,18 @@ int main() {
     for (int P = 1; P <= 64; ++P)
         std::printf("quad %d %d %d %d %d %d %d %d\n", P, quad_h(P), quad_pe(P), quad_pairs(P), quad_rows(P, 0),
                     quad_rows(P, 1), quad_rows(P, 2), quad_rows(P, 3));
+    // shared point counts: a few batches of (point count, pairs)
+    const std::vector<std::vector<std::pair<int32_t, int>>> batches = {
+        {{61, 6}, {65, 4}, {67, 2}, {71, 4}, {73, 4}},
+        {{401, 4096}},
+        {{33, 200}, {35, 10}, {37, 10}},
+        {{100, 50}, {104, 50}, {106, 50}, {108, 50}},
+        {{1000, 3}, {1030, 3}, {1062, 3}, {1070, 3}, {1200, 3}},
+        {{5, 1}, {6, 1}, {9, 1}, {10, 1}, {14, 1}}};
+    for (size_t b = 0; b < batches.size(); ++b) {
+        const std::vector<int32_t> to = share_point_counts(batches[b], 128);
+        for (size_t i = 0; i < to.size(); ++i)
+            std::printf("share %zu %d %d %d\n", b, batches[b][i].first, batches[b][i].second, to[i]);
+    }
     return 0;
 }

@@ -508,7 +508,9 @@ def test_routing_helpers(tmp_path):
     unit grid otherwise); the even and odd interpolation matrices use the points
     j^2 and (j + 1)^2; rows4 pads m + 1 rows to a multiple of 4; a root-of-unity set
     has the next power of two (at least 64) points, and the point-set choice follows
-    the measured crossover on its shapes."""
+    the measured crossover on its shapes; shared point counts only raise a count to a
+    larger one of the same batch, in runs that stay within 1/16 (at least 4 points) of
+    their smallest count and stop growing at a full tile of 128 pairs."""
     nvcc = shutil.which("nvcc")
     cuda = os.environ.get("CUDA_HOME") or (os.path.dirname(os.path.dirname(nvcc)) if nvcc else "")
     inc = os.path.join(cuda, "include")
@@ -516,7 +518,8 @@ def test_routing_helpers(tmp_path):
         pytest.skip("CUDA headers not found")
     exe = _build(tmp_path, "routing_harness.cpp", ["-I", inc])
     out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.splitlines()
-    seen = {"reg": 0, "pt": 0, "rows4": 0, "rootn": 0, "roots": 0, "quad": 0}
+    seen = {"reg": 0, "pt": 0, "rows4": 0, "rootn": 0, "roots": 0, "quad": 0, "share": 0}
+    shared = {}
     # expected point-set choice per crossover shape: degree-20 and -24 batches and full
     # tiles stay on integer points; small batches, long rows and point counts above the
     # cached contraction's range take roots of unity; without the contraction, always roots
@@ -533,6 +536,10 @@ def test_routing_helpers(tmp_path):
         if t[0] == "roots":
             P, tf, tg, m, n, share, auto, nogemm = v
             assert auto == want_roots[(P, share)] and nogemm == 1, line
+            continue
+        if t[0] == "share":
+            b, P, pairs, to = v
+            shared.setdefault(b, []).append((P, pairs, to))
             continue
         if t[0] == "quad":
             # the points 0 and i^k a (a = 1..h) cover the P coefficients; R_t holds the
@@ -557,6 +564,30 @@ def test_routing_helpers(tmp_path):
             assert r % 4 == 0 and m + 1 <= r < m + 5, line
     assert seen["reg"] == 41 * 41 and seen["pt"] == 64 and seen["rows4"] == 131 and seen["roots"] == 8
     assert seen["quad"] == 64
+    for b, rows in shared.items():
+        counts = [P for P, _, _ in rows]
+        for P, _, to in rows:
+            assert to >= P and to in counts
+        runs = {}
+        for P, pairs, to in rows:
+            runs.setdefault(to, []).append((P, pairs))
+        tos = sorted(runs)
+        for k, to in enumerate(tos):
+            members = sorted(runs[to])
+            lo = members[0][0]
+            assert members[-1][0] == to and to <= lo + max(4, lo // 16), (b, members)
+            # consecutive counts of the batch; every count but the last joined while the
+            # run held fewer than 128 pairs
+            i0 = counts.index(lo)
+            assert [P for P, _ in members] == counts[i0:i0 + len(members)]
+            assert sum(p for _, p in members[:-1]) < 128, (b, members)
+            # a run ends at a full tile, at the batch's end, or before a count too far away
+            if k + 1 < len(tos):
+                nxt = sorted(runs[tos[k + 1]])[0][0]
+                assert sum(p for _, p in members) >= 128 or nxt > lo + max(4, lo // 16), (b, members, nxt)
+    assert shared[0] == [(61, 6, 65), (65, 4, 65), (67, 2, 71), (71, 4, 71), (73, 4, 73)]
+    assert shared[1] == [(401, 4096, 401)]
+    assert [to for _, _, to in shared[2]] == [33, 37, 37]
     assert seen["rootn"] > 1100
 
 
