@@ -2600,13 +2600,31 @@ static double summed_bound_host(const gbr_bipoly *f, const gbr_bipoly *g, int va
         }
     }
     const double s4[4] = {1.0, 1.189207115002721, 1.4142135623730951, 1.681792830507429};
-    auto form = [&](const std::vector<std::pair<int, int>> &ents, int q8) -> double {
+    // exact prefix sums over each polynomial's entries of the weighted autocorrelations in
+    // the four classes of the weight 2^(t/4) = 2^(t div 4) 2^(r/4), r = t mod 4 (t = deg q8):
+    // PF[i][k][r] over f_0..f_{i-1}, PG[j][k][r] over g_0..g_{j-1}.  A Sylvester row or
+    // column holds a contiguous range of each polynomial's entries, so its class sums are
+    // differences of two prefix sums: the same integers as summing its entries one by one.
+    std::vector<__int128> PF((size_t)(m + 2) * K * 4), PG((size_t)(n + 2) * K * 4);
+    auto at4 = [](std::vector<__int128> &P, int i, int k, int r) -> __int128 & { return P[((size_t)i * K + k) * 4 + r]; };
+    auto prefix = [&](std::vector<__int128> &P, int e0, int top, int q8) {
+        std::fill(P.begin(), P.end(), (__int128)0);
+        for (int i = 0; i <= top; ++i) {
+            const int t = i * q8;
+            for (int k = 0; k < K; ++k) {
+                for (int r = 0; r < 4; ++r) at4(P, i + 1, k, r) = at4(P, i, k, r);
+                at4(P, i + 1, k, t & 3) += (__int128)A[e0 + i][k] << (t >> 2);
+            }
+        }
+    };
+    // log2 of C_0 + 2 sum_k |C_k| (with its error margin) for f_ilo..f_ihi and g_jlo..g_jhi
+    auto form = [&](int ilo, int ihi, int jlo, int jhi) -> double {
         double s = 0.0;
         for (int k = 0; k < K; ++k) {
             __int128 I[4] = {0, 0, 0, 0};
-            for (const auto &ed : ents) {
-                const int t = ed.second * q8;
-                I[t & 3] += (__int128)A[ed.first][k] << (t >> 2);
+            for (int r = 0; r < 4; ++r) {
+                if (ilo <= ihi) I[r] += at4(PF, ihi + 1, k, r) - at4(PF, ilo, k, r);
+                if (jlo <= jhi) I[r] += at4(PG, jhi + 1, k, r) - at4(PG, jlo, k, r);
             }
             double d[4], mag = 0.0, c = 0.0;
             for (int r = 0; r < 4; ++r) {
@@ -2619,24 +2637,17 @@ static double summed_bound_host(const gbr_bipoly *f, const gbr_bipoly *g, int va
         return std::log2(s * (1.0 + 0x1p-40)) + 0x1p-40;
     };
     double best = INFINITY;
-    std::vector<std::pair<int, int>> ents;
     for (int q8 = 0; q8 <= 1; ++q8) {
+        prefix(PF, 0, m, q8);
+        prefix(PG, m + 1, n, q8);
         double row = 0.0, col = 0.0;
-        if (n > 0) {
-            ents.clear();
-            for (int i = 0; i <= m; ++i) ents.push_back({i, i});
-            row += 0.5 * n * form(ents, q8);
-        }
-        if (m > 0) {
-            ents.clear();
-            for (int j = 0; j <= n; ++j) ents.push_back({m + 1 + j, j});
-            row += 0.5 * m * form(ents, q8);
-        }
+        if (n > 0) row += 0.5 * n * form(0, m, 0, -1);
+        if (m > 0) row += 0.5 * m * form(0, -1, 0, n);
         for (int c = 0; c < m + n; ++c) {
-            ents.clear();
-            for (int r = std::max(0, c - m); r <= std::min(n - 1, c); ++r) ents.push_back({m - (c - r), m - (c - r)});
-            for (int r = std::max(0, c - n); r <= std::min(m - 1, c); ++r) ents.push_back({m + 1 + n - (c - r), n - (c - r)});
-            col += 0.5 * form(ents, q8);
+            // column c: f-row r holds f_{m - (c - r)}, g-row r holds g_{n - (c - r)}
+            const int ilo = m - c + std::max(0, c - m), ihi = m - c + std::min(n - 1, c);
+            const int jlo = n - c + std::max(0, c - n), jhi = n - c + std::min(m - 1, c);
+            col += 0.5 * form(ilo, ihi, jlo, jhi);
         }
         const double v = std::min(row, col) * (1.0 + 0x1p-40) - (double)m * n * q8 / 8.0;
         best = std::min(best, v);
