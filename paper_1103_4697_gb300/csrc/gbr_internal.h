@@ -278,8 +278,10 @@ GBR_HD int root_points(int P) {
 // ascending order with their numbers of pairs.  Returns the count each one is raised to:
 // runs of consecutive counts take the run's largest, a run growing while it holds fewer
 // than `tile` pairs and the next count stays within 1/16 (at least 4 points) above the
-// run's smallest.  (A contraction group of a few pairs costs about as much as a full
-// tile; a degree bound may always be raised.)
+// run's smallest and, from 512 points on (where roots of unity can pay), needs the
+// same root-of-unity set (root_points), so that a pair evaluated at roots of unity never
+// doubles its points.  (A contraction group of a few
+// pairs costs about as much as a full tile; a degree bound may always be raised.)
 inline std::vector<int32_t> share_point_counts(const std::vector<std::pair<int32_t, int>> &counts, int tile) {
     std::vector<int32_t> to(counts.size());
     size_t start = 0;
@@ -288,7 +290,8 @@ inline std::vector<int32_t> share_point_counts(const std::vector<std::pair<int32
         acc += counts[i].second;
         const int32_t lo = counts[start].first;
         const bool more = i + 1 < counts.size() && acc < tile &&
-                          counts[i + 1].first <= lo + (lo / 16 > 4 ? lo / 16 : 4);
+                          counts[i + 1].first <= lo + (lo / 16 > 4 ? lo / 16 : 4) &&
+                          (lo < 512 || root_points(counts[i + 1].first) == root_points(lo));
         if (more) continue;
         for (size_t j = start; j <= i; ++j) to[j] = counts[i].first;
         start = i + 1;

@@ -39,7 +39,8 @@ int main() {
         {{33, 200}, {35, 10}, {37, 10}},
         {{100, 50}, {104, 50}, {106, 50}, {108, 50}},
         {{1000, 3}, {1030, 3}, {1062, 3}, {1070, 3}, {1200, 3}},
-        {{5, 1}, {6, 1}, {9, 1}, {10, 1}, {14, 1}}};
+        {{5, 1}, {6, 1}, {9, 1}, {10, 1}, {14, 1}},
+        {{1020, 8}, {1024, 8}, {1030, 4}, {1050, 4}}};
     for (size_t b = 0; b < batches.size(); ++b) {
         const std::vector<int32_t> to = share_point_counts(batches[b], 128);
         for (size_t i = 0; i < to.size(); ++i)

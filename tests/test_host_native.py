@@ -510,7 +510,9 @@ def test_routing_helpers(tmp_path):
     has the next power of two (at least 64) points, and the point-set choice follows
     the measured crossover on its shapes; shared point counts only raise a count to a
     larger one of the same batch, in runs that stay within 1/16 (at least 4 points) of
-    their smallest count and stop growing at a full tile of 128 pairs."""
+    their smallest count, from 512 points on never cross a power of two (the root-of-unity
+    set) and
+    stop growing at a full tile of 128 pairs."""
     nvcc = shutil.which("nvcc")
     cuda = os.environ.get("CUDA_HOME") or (os.path.dirname(os.path.dirname(nvcc)) if nvcc else "")
     inc = os.path.join(cuda, "include")
@@ -576,6 +578,8 @@ def test_routing_helpers(tmp_path):
             members = sorted(runs[to])
             lo = members[0][0]
             assert members[-1][0] == to and to <= lo + max(4, lo // 16), (b, members)
+            rootn = lambda P: max(64, 1 << (P - 1).bit_length())
+            assert lo < 512 or rootn(to) == rootn(lo), (b, members)
             # consecutive counts of the batch; every count but the last joined while the
             # run held fewer than 128 pairs
             i0 = counts.index(lo)
@@ -584,10 +588,12 @@ def test_routing_helpers(tmp_path):
             # a run ends at a full tile, at the batch's end, or before a count too far away
             if k + 1 < len(tos):
                 nxt = sorted(runs[tos[k + 1]])[0][0]
-                assert sum(p for _, p in members) >= 128 or nxt > lo + max(4, lo // 16), (b, members, nxt)
+                assert (sum(p for _, p in members) >= 128 or nxt > lo + max(4, lo // 16)
+                        or (lo >= 512 and rootn(nxt) != rootn(lo))), (b, members, nxt)
     assert shared[0] == [(61, 6, 65), (65, 4, 65), (67, 2, 71), (71, 4, 71), (73, 4, 73)]
     assert shared[1] == [(401, 4096, 401)]
     assert [to for _, _, to in shared[2]] == [33, 37, 37]
+    assert [to for _, _, to in shared[6]] == [1024, 1024, 1050, 1050]
     assert seen["rootn"] > 1100
 
 
