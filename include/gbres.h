@@ -499,8 +499,10 @@ typedef struct {
 int gbr_resultant_info(const gbr_bipoly *f, const gbr_bipoly *g, int var, int disc, gbr_res_info *out);
 
 /* The plan the device made for jobs [first, first + count) of a resident batch
- * in its last gbr_run_resident: actual degrees, x-degree bound (deg_bound =
- * points - 1), primes used (including GBR_OPT_EXTRA_PRIMES), output limbs, and
+ * in its last gbr_run_resident: actual degrees, x-degree bound of the result
+ * (deg_bound; the run may interpolate at more points than deg_bound + 1 when jobs of
+ * the batch with close degree bounds share one point count, the coefficients above
+ * deg_bound then being 0), primes used (including GBR_OPT_EXTRA_PRIMES), output limbs, and
  * the log2 of the coefficient bound computed on the device (an upper bound of
  * the same scaled Hadamard bound gbr_resultant_info evaluates, in single
  * precision with directed rounding).  A zero result has deg_bound = -1 and

@@ -182,8 +182,8 @@ class Resident:
         return self.ctx._collect(outs, count)
 
     def plan(self, first: int = 0, count: int | None = None) -> list[dict]:
-        """gbr_resident_plan: the device's plan per job after a run (degrees, points - 1,
-        primes, limbs, log2 of the coefficient bound)."""
+        """gbr_resident_plan: the device's plan per job after a run (degrees, the degree
+        bound of the result, primes, limbs, log2 of the coefficient bound)."""
         count = self.n - first if count is None else count
         outs = (N.ResInfo * max(count, 1))()
         N.check(N.lib().gbr_resident_plan(self.ctx.handle, self.handle, first, count, outs), self.ctx.handle)
