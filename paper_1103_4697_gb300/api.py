@@ -40,26 +40,24 @@ def _to_words(arr, W: int) -> np.ndarray:
         else arr.ravel()
     if W == 1:
         return np.asarray(flat, dtype=np.int64).view(np.uint64)
-    out = np.empty(len(flat) * W, dtype=np.uint64)
+    # each value's two's complement in W words, least significant first
     mask = (1 << (64 * W)) - 1
-    for k, v in enumerate(flat):
-        u = int(v) & mask
-        for w in range(W):
-            out[k * W + w] = (u >> (64 * w)) & _M64
-    return out
+    raw = b"".join((int(v) & mask).to_bytes(8 * W, "little") for v in flat)
+    return np.frombuffer(raw, dtype="<u8").astype(np.uint64)
 
 
 def _as_2d(f):
     if isinstance(f, np.ndarray) and f.ndim == 2:
         return f
-    rows = [list(r) for r in f]
+    rows = [[int(c) for c in r] for r in f]
     width = max((len(r) for r in rows), default=1) or 1
-    big = any(int(c) >= 2 ** 63 or int(c) < -(2 ** 63) for r in rows for c in r)
-    a = np.zeros((max(len(rows), 1), width), dtype=object if big else np.int64)
-    for j, r in enumerate(rows):
-        for i, c in enumerate(r):
-            a[j, i] = int(c)
-    return a
+    padded = [r + [0] * (width - len(r)) for r in rows] or [[0] * width]
+    try:
+        return np.array(padded, dtype=np.int64)    # every coefficient fits a signed word
+    except OverflowError:
+        a = np.empty((len(padded), width), dtype=object)
+        a[:, :] = padded
+        return a
 
 
 class _Packed:
@@ -129,11 +127,12 @@ def bigpoly_to_ints(b: N.BigPoly) -> list[int]:
     n, L = b.deg + 1, b.limbs
     mag = np.ctypeslib.as_array(b.mag, shape=(n * L,)).reshape(n, L)
     sgn = np.ctypeslib.as_array(b.sign, shape=(n,))
-    raw = mag.astype("<u4").tobytes()
-    out = []
-    for i in range(n):
-        v = int.from_bytes(raw[i * 4 * L:(i + 1) * 4 * L], "little")
-        out.append(-v if sgn[i] < 0 else v)
+    raw = memoryview(mag.astype("<u4").tobytes())   # slices of a memoryview are not copies
+    step = 4 * L
+    out = [int.from_bytes(raw[i * step:(i + 1) * step], "little") for i in range(n)]
+    for i, sg in enumerate(sgn.tolist()):
+        if sg < 0:
+            out[i] = -out[i]
     while out and out[-1] == 0:
         out.pop()
     return out

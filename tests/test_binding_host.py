@@ -60,6 +60,29 @@ def test_bivariate_inputs_round_trip_through_the_descriptors():
         assert got == [c for r in dense for c in r]
 
 
+def test_word_boundaries_and_ragged_rows():
+    """Coefficients at the ends of a signed word (2^63 - 1 and -2^63 stay one word, 2^63
+    and -2^63 - 1 take two), ragged rows padded with zeros, an empty polynomial, and
+    numpy integers as input, each read back through the descriptor."""
+    cases = [[[(1 << 63) - 1, -(1 << 63)], [1]],
+             [[1 << 63], [-(1 << 63) - 1, 0, 7]],
+             [[np.int64(-5), np.int64(3)], [np.int64(2)]],
+             [],
+             [[0]],
+             [[1, 2, 3], [], [4]]]
+    keep = A._Packed()
+    desc = A.pack_bipolys(cases, keep)
+    for f, d in zip(cases, desc):
+        rows = [[int(c) for c in r] for r in f] or [[0]]
+        width = max(len(r) for r in rows) or 1
+        dense = [r + [0] * (width - len(r)) for r in rows]
+        assert (int(d["deg_x"]), int(d["deg_y"])) == (width - 1, len(dense) - 1)
+        W = int(d["words"])
+        flat = [c for r in dense for c in r]
+        assert W == (1 if all(-(1 << 63) <= c < (1 << 63) for c in flat) else A._words_for(flat))
+        assert _decode(_read_words(d["coef"], width * len(dense) * W), W) == flat
+
+
 def test_int64_batch_array_descriptors():
     rng = np.random.default_rng(92)
     arr = rng.integers(-(1 << 62), 1 << 62, size=(5, 4, 3), dtype=np.int64)
